@@ -1,0 +1,191 @@
+/*
+ * ek.h -- C ABI of the GB300 lattice electrokinetics library (libek.so).
+ *
+ * The library advances the moving-boundary lattice electrokinetics method of
+ * Kuron et al., "Moving Charged Particles in Lattice Boltzmann-Based
+ * Electrokinetics" (arXiv 1607.04572), on one GPU.  One call of ek_step(ctx, n)
+ * runs n time steps, each made of
+ *
+ *   S1  charge assembly and periodic FFT Poisson solve           (Sec. III.C, Eq. 3;
+ *                                                                  particle charge Eq. 21)
+ *   S2  Capuani link fluxes (diffusion + migration, partial       (Eqs. 13, 20, 16)
+ *       volumes) and their force on the fluid, fused with the
+ *       D3Q19 TRT/BGK collision (Guo force term) and push stream  (Sec. III.A, Eqs. 5-9)
+ *       with velocity bounce-back and momentum exchange           (Eq. 12, Eqs. 10-11)
+ *   S3  species update: flux divergence + volume-of-fluid         (Eq. 15, Sec. III.C)
+ *       advection
+ *   S4  particle force (momentum exchange, electrostatic, fluid   (Sec. III.B)
+ *       create/destroy) and symplectic Euler integration
+ *   S5  re-flagging, octree partial volumes Psi, fluid            (Sec. III.B, III.D,
+ *       create/destroy, solute expulsion and refill                Eqs. 17-18)
+ *
+ * Units: lattice units, grid spacing a = 1, time step tau = 1, k_B T = 1,
+ * elementary charge e = 1 (the paper's energy unit is k_B T, Table I).
+ *
+ * Layout of every field exchanged through this ABI: structure of arrays, FP64,
+ * node index  x + nx*(y + ny*z)  (x fastest).  A vector or multi-component field
+ * is component-major: component c of node i at [c*N + i], N = nx*ny*nz.
+ *
+ * Ownership: the context owns all of its device memory (allocated in ek_create,
+ * freed in ek_destroy).  Every pointer passed in is owned by the caller and only
+ * read or written during the call; host pointers must stay valid for the call,
+ * device pointers must be device memory of the context's GPU.
+ *
+ * Errors: every entry point returns an ek_status and never throws, aborts or
+ * exits.  On failure ek_last_error(ctx) gives a human-readable reason.  A
+ * device-side condition (non-finite value, overlapping particles, nowhere to
+ * expel solute) is recorded in a device status word and returned by the next
+ * ek_step / ek_sync / ek_get_* call; the context is then unusable except for
+ * ek_get_* and ek_destroy.
+ *
+ * Threading: a context is not thread-safe; use one context per host thread.
+ * All work is enqueued on the context's stream (the legacy default stream
+ * unless ek_set_stream was called).
+ */
+#ifndef EK_H
+#define EK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EK_MAX_SPECIES 4
+
+typedef struct ek_ctx ek_ctx;
+
+typedef enum {
+  EK_OK = 0,
+  EK_ERR_ARG = -1,       /* invalid argument (null pointer, size, range)          */
+  EK_ERR_NOMEM = -2,     /* device or host allocation failed                      */
+  EK_ERR_CUDA = -3,      /* a CUDA runtime call failed                            */
+  EK_ERR_UNSTABLE = -4,  /* a non-finite density or velocity was produced         */
+  EK_ERR_OVERLAP = -5,   /* a node lies inside two particles                      */
+  EK_ERR_EXPEL = -6,     /* a newly covered node has no fluid neighbour           */
+  EK_ERR_STATE = -8      /* call not valid in the context's state, or a capacity  */
+} ek_status;
+
+/* ek_params.flags */
+enum {
+  EK_PV = 1,             /* partial-volume flux, Eq. 20, and Psi-smeared particle
+                            charge, Eq. 21 (the paper's enhanced scheme); without
+                            it: Eq. 13 fluxes and charge spread evenly over the
+                            particle's boundary nodes (the simple scheme)          */
+  EK_VACATE_ZERO = 2,    /* vacated nodes are left empty instead of refilled by
+                            Eqs. 17-18 (allowed with EK_PV, Sec. III.D.2)          */
+  EK_CHARGE_NORM_VP = 4, /* Eq. 21 literally: divide by the continuous volume V_p;
+                            default divides by sum Psi_p so the charge is exactly Z */
+  EK_NEUTRALIZE = 8      /* at fill time add counter-ions of the first species of
+                            opposite valence so the box is neutral                 */
+};
+
+typedef struct {
+  int nx, ny, nz;        /* periodic box, each in [8, 1024]                        */
+  double nu;             /* kinematic viscosity; tau_e = 3 nu + 1/2 (Sec. III.A)   */
+  double rho0;           /* fluid rest density                                     */
+  double bjerrum;        /* Bjerrum length l_B (Eq. 4)                             */
+  double magic;          /* TRT magic product Lambda (the paper's 3/16); <= 0 or
+                            NaN selects BGK, lambda_o = lambda_e                   */
+  int nspecies;          /* K in [0, EK_MAX_SPECIES]; 0 runs the fluid alone        */
+  int valence[EK_MAX_SPECIES];   /* z_k                                            */
+  double D[EK_MAX_SPECIES];      /* diffusion coefficients, each in (0, 0.39]      */
+  double bulk[EK_MAX_SPECIES];   /* initial density on fluid nodes                 */
+  unsigned flags;        /* EK_PV | EK_VACATE_ZERO | EK_CHARGE_NORM_VP | EK_NEUTRALIZE */
+} ek_params;
+
+typedef enum {
+  /* readable and writable */
+  EK_FIELD_SPECIES = 0,     /* density rho_k of species `component`, N values         */
+  EK_FIELD_POPULATIONS = 1, /* f_i, 19*N values, direction-major (see ek_lattice_dirs) */
+  EK_FIELD_VELOCITY = 2,    /* set: f = f^eq(current rho, u) on fluid nodes; get: the
+                               fluid velocity u = (sum f c + f_ext/2)/rho of the last
+                               collision; 3*N values                                 */
+  EK_FIELD_E_EXT = 3,       /* uniform external field E, 3 values                      */
+  EK_FIELD_BODY_FORCE = 4,  /* uniform body force density on the fluid, 3 values      */
+  EK_FIELD_WALL = 5,        /* static boundary mask, N values (nonzero = wall); set
+                               re-flags and refills like ek_add_particle             */
+  EK_FIELD_WALL_CHARGE = 6, /* static boundary charge density rho_b, N values          */
+  /* read only */
+  EK_FIELD_DENSITY = 7,     /* fluid density sum_i f_i, N values                       */
+  EK_FIELD_PHI = 8,         /* electrostatic potential of the last solve, N values     */
+  EK_FIELD_PSI = 9,         /* overlap fraction Psi = min(1, sum_p Psi_p), N values    */
+  EK_FIELD_OWNER = 10,      /* node class as doubles: -1 fluid, -2 wall, p >= 0 inside
+                               particle p; N values                                  */
+  EK_FIELD_CHARGE = 11      /* charge density q of the last Poisson solve, N values    */
+} ek_field;
+
+typedef struct {
+  double pos[3], vel[3], omega[3];
+  double force[3], torque[3];  /* total force/torque of the last integration        */
+  double radius, charge, rho_p;
+  int fixed;
+} ek_particle;
+
+/* Create a context.  Copies *p; allocates all device state on the current CUDA
+ * device; fills populations with the rest equilibrium f^eq(rho0, 0) and species
+ * with their bulk densities.  Returns EK_ERR_ARG for invalid parameters. */
+ek_status ek_create(const ek_params* p, ek_ctx** out);
+ek_status ek_destroy(ek_ctx* ctx);
+
+/* Add a sphere of radius R and charge Z (units of e) at pos (wrapped into the
+ * box) with velocity vel and angular velocity omega (Sec. III.B).  Mass
+ * rho_p (4/3) pi R^3, moment of inertia (2/5) m R^2.  fixed != 0: the particle
+ * is a stationary boundary moving with vel (the co-moving frame of Sec. IV.A).
+ * Requires 2R + 6 <= min(nx, ny, nz).  Re-flags the lattice and refills it:
+ * species back to bulk on fluid nodes (plus counter-ions with EK_NEUTRALIZE),
+ * populations to rest equilibrium.  *out_id (may be NULL) receives the index. */
+ek_status ek_add_particle(ek_ctx* ctx, const double pos[3], const double vel[3],
+                          const double omega[3], double radius, double charge,
+                          double rho_p, int fixed, int* out_id);
+
+/* Write a field (see ek_field).  count must equal the field's size; src is a
+ * host pointer, or a device pointer when src_on_device != 0. */
+ek_status ek_set_field(ek_ctx* ctx, ek_field which, int component, const double* src,
+                       size_t count, int src_on_device);
+
+/* Read a field into dst (host, or device when dst_on_device != 0); synchronises
+ * the context's stream. */
+ek_status ek_get_fields(ek_ctx* ctx, ek_field which, int component, double* dst,
+                        size_t count, int dst_on_device);
+
+/* Enqueue nsteps full time steps (S1-S5) on the context's stream, then wait for
+ * them and check the device status word. */
+ek_status ek_step(ek_ctx* ctx, int nsteps);
+
+/* Enqueue nsteps full time steps without waiting (no status check). */
+ek_status ek_step_async(ek_ctx* ctx, int nsteps);
+
+/* Run one stage of a time step on the current state (1..5 = S1..S5; S2 includes
+ * the buffer swap of populations and species that closes S2/S3).  For
+ * stage-by-stage comparisons; ek_step runs S1..S5 in order. */
+ek_status ek_run_stage(ek_ctx* ctx, int stage);
+
+/* Copy up to count particle records to host memory dst (synchronises). */
+ek_status ek_get_particles(ek_ctx* ctx, ek_particle* dst, int count);
+int ek_num_particles(const ek_ctx* ctx);
+
+/* Use the CUDA stream `stream` (a cudaStream_t) for all later work. */
+ek_status ek_set_stream(ek_ctx* ctx, void* stream);
+/* Wait for all enqueued work and check the device status word. */
+ek_status ek_sync(ek_ctx* ctx);
+/* Reason of the last failure, or "" (the string is owned by the context). */
+const char* ek_last_error(const ek_ctx* ctx);
+
+/* The D3Q19 velocity set used for EK_FIELD_POPULATIONS: c[3*i + a], i = 0..18. */
+void ek_lattice_dirs(int c[57]);
+
+/* Standalone periodic Poisson solve of Eq. 3 on the device (S1 without the
+ * charge assembly): phi = solution of lap_7 phi = -4 pi l_B (q - mean q) with
+ * the 7-point Laplacian, mean(phi) = 0.  q and phi are device arrays of
+ * nx*ny*nz doubles (may alias); spectrum is caller-allocated device scratch of
+ * at least ek_poisson_scratch_bytes(nx, ny, nz) bytes; stream is a
+ * cudaStream_t or NULL.  Supported edges: 2^a 3^b, 8 <= n <= 1024. */
+size_t ek_poisson_scratch_bytes(int nx, int ny, int nz);
+ek_status ek_poisson_solve(const double* q, double* phi, int nx, int ny, int nz,
+                           double bjerrum, void* spectrum, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EK_H */

@@ -321,8 +321,9 @@ class EKOracle:
         (bulk on fluid nodes, plus neutralising counter-ions), populations to
         rest equilibrium on fluid nodes, Poisson re-solved on the next step."""
         n = self.n
-        if 2.0 * radius + 4.0 > n.min():
-            raise OracleError("particle does not fit the box")
+        if 2.0 * radius + 6.0 > n.min():
+            # the union of a particle's old and new boxes must not wrap onto itself
+            raise OracleError("particle does not fit the box (2R + 6 > box edge)")
         p = Particle(np.mod(pos, n), vel, omega, radius, charge, rho_p, fixed)
         self.particles.append(p)
         self._reflag_setup()

@@ -1,0 +1,690 @@
+// Host side of the C ABI declared in include/ek.h: context, device memory,
+// the time-step driver and field / particle exchange.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+
+#include "ek_internal.cuh"
+
+using namespace ek;
+
+struct ek_ctx {
+  ek_params p;
+  Grid g;
+  Phys ph;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  double* f[2] = {nullptr, nullptr};
+  double* rho[2] = {nullptr, nullptr};
+  double* phi = nullptr;
+  double* psi = nullptr;
+  double* qpart = nullptr;
+  double* qwall = nullptr;
+  double* u = nullptr;
+  double* tmp = nullptr;
+  int* owner = nullptr;
+  int* owner_prev = nullptr;
+  unsigned char* wall = nullptr;
+  double2* spectrum = nullptr;
+  PoissonPlan plan;
+  DevParticle* dparts = nullptr;
+  int P = 0;
+  int Pcap = 0;
+  std::vector<DevParticle> hparts;
+  double* psibox = nullptr;
+  int boxmax = 0;
+  size_t psibox_cap = 0;  // doubles allocated for psibox
+  Transfer* xfer = nullptr;
+  int* xfer_count = nullptr;
+  int xfer_cap = 0;
+  int* status = nullptr;
+  int cur = 0;
+  bool setup_pending = true;
+  bool has_qwall = false;
+  bool broken = false;
+  std::string err;
+};
+
+namespace {
+
+ek_status fail(ek_ctx* c, ek_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define EK_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(ctx, EK_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+__global__ void k_set_velocity(Grid g, const int* owner, double* f, const double* u) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.N || owner[n] != FLUID) return;
+  double rho = 0.0;
+  for (int i = 0; i < Q; ++i) rho += f[i * g.N + n];
+  const double ux = u[n], uy = u[g.N + n], uz = u[2 * g.N + n];
+  const double usq = ux * ux + uy * uy + uz * uz;
+  for (int i = 0; i < Q; ++i) {
+    const double cu = CX[i] * ux + CY[i] * uy + CZ[i] * uz;
+    f[i * g.N + n] = wgt(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+  }
+}
+
+__global__ void k_density(Grid g, const double* f, double* out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  double rho = 0.0;
+  for (int i = 0; i < Q; ++i) rho += f[i * g.N + n];
+  out[n] = rho;
+}
+
+__global__ void k_int_to_double(Grid g, const int* in, double* out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < g.N) out[n] = (double)in[n];
+}
+
+__global__ void k_u8_to_double(Grid g, const unsigned char* in, double* out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < g.N) out[n] = (double)in[n];
+}
+
+__global__ void k_double_to_u8(Grid g, const double* in, unsigned char* out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < g.N) out[n] = in[n] != 0.0 ? 1 : 0;
+}
+
+__global__ void k_psi_clamped(Grid g, const double* psi, double* out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < g.N) out[n] = fmin(psi[n], 1.0);
+}
+
+__global__ void k_count_fluid(Grid g, const int* owner, unsigned long long* count) {
+  __shared__ unsigned int s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < g.N && owner[n] == FLUID) atomicAdd(&s, 1u);
+  __syncthreads();
+  if (threadIdx.x == 0 && s) atomicAdd(count, (unsigned long long)s);
+}
+
+unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
+
+bool edge_ok(int n) {
+  if (n < 8 || n > 1024) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+ek_status check_status(ek_ctx* ctx) {
+  int st = 0;
+  EK_CUDA(cudaMemcpyAsync(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  EK_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (st == 0) return EK_OK;
+  ctx->broken = true;
+  if (st & ST_OVERLAP) return fail(ctx, EK_ERR_OVERLAP, "a node lies inside two particles (or a particle and a wall)");
+  if (st & ST_EXPEL) return fail(ctx, EK_ERR_EXPEL, "a newly covered node has no fluid neighbour to expel solute to");
+  if (st & ST_CAPACITY) return fail(ctx, EK_ERR_STATE, "transition record capacity exceeded (particle moved more than one cell per step?)");
+  return fail(ctx, EK_ERR_UNSTABLE, "non-finite density, velocity or particle position");
+}
+
+PartArgs part_args(ek_ctx* ctx) {
+  PartArgs a;
+  a.g = ctx->g;
+  a.ph = ctx->ph;
+  a.parts = ctx->dparts;
+  a.P = ctx->P;
+  a.boxmax = ctx->boxmax;
+  a.psibox = ctx->psibox;
+  a.owner = ctx->owner;
+  a.owner_prev = ctx->owner_prev;
+  a.psi = ctx->psi;
+  a.qpart = ctx->qpart;
+  a.f = ctx->f[ctx->cur];
+  a.fw = ctx->f[ctx->cur];
+  a.rho = ctx->rho[ctx->cur];
+  a.phi = ctx->phi;
+  a.wall = ctx->wall;
+  a.xfer = ctx->xfer;
+  a.xfer_count = ctx->xfer_count;
+  a.xfer_cap = ctx->xfer_cap;
+  a.status = ctx->status;
+  return a;
+}
+
+LBArgs lb_args(ek_ctx* ctx) {
+  LBArgs a;
+  a.g = ctx->g;
+  a.ph = ctx->ph;
+  a.f_in = ctx->f[ctx->cur];
+  a.f_out = ctx->f[1 - ctx->cur];
+  a.rho_in = ctx->rho[ctx->cur];
+  a.rho_out = ctx->rho[1 - ctx->cur];
+  a.phi = ctx->phi;
+  a.psi = ctx->psi;
+  a.owner = ctx->owner;
+  a.u = ctx->u;
+  a.parts = ctx->dparts;
+  a.status = ctx->status;
+  return a;
+}
+
+// pull the device particle records into the host copy
+ek_status download_particles(ek_ctx* ctx) {
+  if (ctx->P == 0) return EK_OK;
+  ctx->hparts.resize(ctx->P);
+  EK_CUDA(cudaMemcpyAsync(ctx->hparts.data(), ctx->dparts, ctx->P * sizeof(DevParticle),
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  EK_CUDA(cudaStreamSynchronize(ctx->stream));
+  return EK_OK;
+}
+
+// Re-flag the whole lattice from the particle positions and refill it
+// (species at bulk + counter-ions, populations at rest): runs before the first
+// step after particles or walls changed.
+ek_status run_setup(ek_ctx* ctx) {
+  if (!ctx->setup_pending) return EK_OK;
+  double rmax = 0.0;
+  for (const DevParticle& q : ctx->hparts) rmax = std::max(rmax, q.radius);
+  const int edge = (int)floor(2.0 * rmax) + 4;
+  const int boxmax = ctx->P ? edge * edge * edge : 0;
+  if (ctx->P && (size_t)ctx->P * boxmax > ctx->psibox_cap) {
+    if (ctx->psibox) cudaFree(ctx->psibox);
+    ctx->psibox = nullptr;
+    ctx->psibox_cap = 0;
+    const size_t cap = (size_t)ctx->Pcap * boxmax;
+    EK_CUDA(cudaMalloc(&ctx->psibox, cap * sizeof(double)));
+    ctx->psibox_cap = cap;
+  }
+  ctx->boxmax = boxmax;
+  if (ctx->P) {
+    EK_CUDA(cudaMemcpyAsync(ctx->dparts, ctx->hparts.data(), ctx->P * sizeof(DevParticle),
+                            cudaMemcpyHostToDevice, ctx->stream));
+  }
+  PartArgs a = part_args(ctx);
+  EK_CUDA(launch_reflag(a, false, ctx->stream));
+  // neutralising counter-ions (reading of "bulk density": initial density on fluid nodes)
+  unsigned long long* dcount = reinterpret_cast<unsigned long long*>(ctx->tmp);
+  EK_CUDA(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), ctx->stream));
+  k_count_fluid<<<nblk(ctx->g.N), 256, 0, ctx->stream>>>(ctx->g, ctx->owner, dcount);
+  unsigned long long nf = 0;
+  EK_CUDA(cudaMemcpyAsync(&nf, dcount, sizeof(nf), cudaMemcpyDeviceToHost, ctx->stream));
+  EK_CUDA(cudaStreamSynchronize(ctx->stream));
+  double bulk[EK_MAX_SPECIES] = {0, 0, 0, 0};
+  for (int k = 0; k < ctx->p.nspecies; ++k) bulk[k] = ctx->p.bulk[k];
+  if ((ctx->p.flags & EK_NEUTRALIZE) && nf > 0) {
+    double net = 0.0;
+    for (const DevParticle& q : ctx->hparts) net += q.charge;
+    if (ctx->has_qwall) {
+      std::vector<double> qw(ctx->g.N);
+      EK_CUDA(cudaMemcpy(qw.data(), ctx->qwall, ctx->g.N * sizeof(double), cudaMemcpyDeviceToHost));
+      double s = 0.0;
+      for (double v : qw) s += v;
+      net += s;
+    }
+    double zb = 0.0;
+    for (int k = 0; k < ctx->p.nspecies; ++k) zb += ctx->p.valence[k] * ctx->p.bulk[k];
+    net += zb * (double)nf;
+    if (net != 0.0) {
+      int s = -1;
+      for (int k = 0; k < ctx->p.nspecies; ++k)
+        if (ctx->p.valence[k] * net < 0.0) { s = k; break; }
+      if (s < 0) return fail(ctx, EK_ERR_ARG, "no species can neutralise the box");
+      bulk[s] = bulk[s] - net / (ctx->p.valence[s] * (double)nf);
+    }
+  }
+  EK_CUDA(launch_fill(ctx->g, ctx->ph, ctx->owner, ctx->f[ctx->cur], ctx->rho[ctx->cur], bulk,
+                      ctx->stream));
+  ctx->setup_pending = false;
+  ek_status st = check_status(ctx);
+  if (st != EK_OK) return st;
+  return download_particles(ctx);
+}
+
+ek_status enqueue_stage(ek_ctx* ctx, int stage) {
+  cudaStream_t s = ctx->stream;
+  switch (stage) {
+    case 1:
+      EK_CUDA(poisson_solve(ctx->plan, nullptr, ctx->rho[ctx->cur],
+                            ctx->has_qwall ? ctx->qwall : nullptr, ctx->qpart, ctx->ph, ctx->phi,
+                            ctx->spectrum, s));
+      return EK_OK;
+    case 2: {
+      LBArgs a = lb_args(ctx);
+      EK_CUDA(launch_lb_fused(a, s));
+      EK_CUDA(launch_advection(a, s));
+      ctx->cur = 1 - ctx->cur;
+      return EK_OK;
+    }
+    case 4: {
+      PartArgs a = part_args(ctx);
+      EK_CUDA(launch_particle_forces(a, s));
+      return EK_OK;
+    }
+    case 5: {
+      PartArgs a = part_args(ctx);
+      if (ctx->P) EK_CUDA(launch_reflag(a, true, s));
+      return EK_OK;
+    }
+    default:
+      return fail(ctx, EK_ERR_ARG, "stage must be 1, 2, 4 or 5");
+  }
+}
+
+ek_status ready(ek_ctx* ctx) {
+  if (!ctx) return EK_ERR_ARG;
+  if (ctx->broken) return fail(ctx, EK_ERR_STATE, "context is in an error state: " + ctx->err);
+  EK_CUDA(cudaSetDevice(ctx->device));
+  return run_setup(ctx);
+}
+
+size_t field_size(const ek_ctx* ctx, ek_field w) {
+  const size_t N = (size_t)ctx->g.N;
+  switch (w) {
+    case EK_FIELD_POPULATIONS: return 19 * N;
+    case EK_FIELD_VELOCITY: return 3 * N;
+    case EK_FIELD_E_EXT:
+    case EK_FIELD_BODY_FORCE: return 3;
+    default: return N;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+ek_status ek_create(const ek_params* p, ek_ctx** out) {
+  if (!p || !out) return EK_ERR_ARG;
+  *out = nullptr;
+  if (!edge_ok(p->nx) || !edge_ok(p->ny) || !edge_ok(p->nz) || p->nx % 2) return EK_ERR_ARG;
+  if (!(p->nu > 0.0) || !(p->rho0 > 0.0) || !(p->bjerrum >= 0.0)) return EK_ERR_ARG;
+  if (p->nspecies < 0 || p->nspecies > EK_MAX_SPECIES) return EK_ERR_ARG;
+  for (int k = 0; k < p->nspecies; ++k)
+    if (!(p->D[k] > 0.0 && p->D[k] <= 0.39) || !(p->bulk[k] >= 0.0)) return EK_ERR_ARG;
+  ek_ctx* ctx = new (std::nothrow) ek_ctx();
+  if (!ctx) return EK_ERR_NOMEM;
+  ctx->p = *p;
+  cudaGetDevice(&ctx->device);
+  Grid& g = ctx->g;
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.nz = p->nz;
+  g.N = (long long)p->nx * p->ny * p->nz;
+  Phys& ph = ctx->ph;
+  memset(&ph, 0, sizeof(ph));
+  ph.rho0 = p->rho0;
+  const double tau_e = 3.0 * p->nu + 0.5;
+  double tau_o = tau_e;
+  if (p->magic > 0.0) tau_o = 0.5 + p->magic / (tau_e - 0.5);
+  ph.lam_e = -1.0 / tau_e;
+  ph.lam_o = -1.0 / tau_o;
+  ph.bjerrum = p->bjerrum;
+  ph.K = p->nspecies;
+  ph.pv = (p->flags & EK_PV) ? 1 : 0;
+  ph.flags = p->flags;
+  const double A0 = 1.0 + 2.0 * sqrt(2.0);
+  for (int k = 0; k < p->nspecies; ++k) {
+    ph.z[k] = (double)p->valence[k];
+    ph.D[k] = p->D[k];
+    ph.dcoef[k] = p->D[k] / A0;
+    ph.hinvD[k] = 0.5 / p->D[k];
+  }
+  std::string perr;
+  if (poisson_plan_create(ctx->plan, g.nx, g.ny, g.nz, perr) != cudaSuccess) {
+    delete ctx;
+    return EK_ERR_ARG;
+  }
+  const size_t N = (size_t)g.N;
+  const int K = std::max(p->nspecies, 1);
+  bool ok = true;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (ok && cudaMalloc(ptr, bytes) != cudaSuccess) ok = false;
+  };
+  for (int b = 0; b < 2; ++b) {
+    alloc((void**)&ctx->f[b], 19 * N * sizeof(double));
+    alloc((void**)&ctx->rho[b], K * N * sizeof(double));
+  }
+  alloc((void**)&ctx->phi, N * sizeof(double));
+  alloc((void**)&ctx->psi, N * sizeof(double));
+  alloc((void**)&ctx->qpart, N * sizeof(double));
+  alloc((void**)&ctx->qwall, N * sizeof(double));
+  alloc((void**)&ctx->u, 3 * N * sizeof(double));
+  alloc((void**)&ctx->tmp, N * sizeof(double));
+  alloc((void**)&ctx->owner, N * sizeof(int));
+  alloc((void**)&ctx->owner_prev, N * sizeof(int));
+  alloc((void**)&ctx->wall, N);
+  alloc((void**)&ctx->spectrum, poisson_spectrum_bytes(g.nx, g.ny, g.nz));
+  ctx->xfer_cap = (int)std::min<long long>(19LL * g.N, 1LL << 22);
+  alloc((void**)&ctx->xfer, (size_t)ctx->xfer_cap * sizeof(Transfer));
+  alloc((void**)&ctx->xfer_count, sizeof(int));
+  alloc((void**)&ctx->status, sizeof(int));
+  if (!ok) {
+    ek_destroy(ctx);
+    return EK_ERR_NOMEM;
+  }
+  cudaMemset(ctx->wall, 0, N);
+  cudaMemset(ctx->qwall, 0, N * sizeof(double));
+  cudaMemset(ctx->phi, 0, N * sizeof(double));
+  cudaMemset(ctx->u, 0, 3 * N * sizeof(double));
+  cudaMemset(ctx->xfer_count, 0, sizeof(int));
+  cudaMemset(ctx->status, 0, sizeof(int));
+  for (int b = 0; b < 2; ++b) {
+    cudaMemset(ctx->f[b], 0, 19 * N * sizeof(double));
+    cudaMemset(ctx->rho[b], 0, K * N * sizeof(double));
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    ek_destroy(ctx);
+    return EK_ERR_CUDA;
+  }
+  ek_status st = run_setup(ctx);
+  if (st != EK_OK) {
+    ek_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return EK_OK;
+}
+
+ek_status ek_destroy(ek_ctx* ctx) {
+  if (!ctx) return EK_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  void* ptrs[] = {ctx->f[0], ctx->f[1], ctx->rho[0], ctx->rho[1], ctx->phi, ctx->psi, ctx->qpart,
+                  ctx->qwall, ctx->u, ctx->tmp, ctx->owner, ctx->owner_prev, ctx->wall,
+                  ctx->spectrum, ctx->dparts, ctx->psibox, ctx->xfer, ctx->xfer_count,
+                  ctx->status};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  poisson_plan_destroy(ctx->plan);
+  delete ctx;
+  return EK_OK;
+}
+
+ek_status ek_add_particle(ek_ctx* ctx, const double pos[3], const double vel[3],
+                          const double omega[3], double radius, double charge, double rho_p,
+                          int fixed, int* out_id) {
+  if (!ctx || !pos) return EK_ERR_ARG;
+  if (ctx->broken) return fail(ctx, EK_ERR_STATE, "context is in an error state");
+  const int nmin = std::min(ctx->g.nx, std::min(ctx->g.ny, ctx->g.nz));
+  if (!(radius > 0.0) || 2.0 * radius + 6.0 > (double)nmin)
+    return fail(ctx, EK_ERR_ARG, "radius must be positive with 2R + 6 <= min(nx, ny, nz)");
+  if (!(rho_p > 0.0) || !isfinite(charge)) return fail(ctx, EK_ERR_ARG, "bad rho_p or charge");
+  EK_CUDA(cudaSetDevice(ctx->device));
+  if (!ctx->setup_pending) {
+    ek_status st = download_particles(ctx);
+    if (st != EK_OK) return st;
+  }
+  DevParticle q;
+  memset(&q, 0, sizeof(q));
+  const int nn[3] = {ctx->g.nx, ctx->g.ny, ctx->g.nz};
+  for (int d = 0; d < 3; ++d) {
+    if (!isfinite(pos[d])) return fail(ctx, EK_ERR_ARG, "non-finite position");
+    double x = fmod(pos[d], (double)nn[d]);
+    if (x < 0.0) x += nn[d];
+    if (x >= nn[d]) x -= nn[d];
+    q.pos[d] = x;
+    q.vel[d] = vel ? vel[d] : 0.0;
+    q.omega[d] = omega ? omega[d] : 0.0;
+  }
+  q.radius = radius;
+  q.charge = charge;
+  q.mass = rho_p * 4.0 / 3.0 * M_PI * pow(radius, 3.0);
+  q.inertia = 0.4 * q.mass * pow(radius, 2.0);
+  q.fixed = fixed ? 1 : 0;
+  ctx->hparts.resize(ctx->P);
+  ctx->hparts.push_back(q);
+  if (ctx->P + 1 > ctx->Pcap) {
+    const int cap = std::max(16, 2 * ctx->Pcap);
+    DevParticle* nd = nullptr;
+    EK_CUDA(cudaMalloc(&nd, cap * sizeof(DevParticle)));
+    if (ctx->dparts) cudaFree(ctx->dparts);
+    ctx->dparts = nd;
+    ctx->Pcap = cap;
+  }
+  ctx->P += 1;
+  ctx->setup_pending = true;
+  if (out_id) *out_id = ctx->P - 1;
+  return EK_OK;
+}
+
+ek_status ek_set_field(ek_ctx* ctx, ek_field which, int component, const double* src,
+                       size_t count, int src_on_device) {
+  ek_status st = ready(ctx);
+  if (st != EK_OK) return st;
+  if (!src) return fail(ctx, EK_ERR_ARG, "null source");
+  if (count != field_size(ctx, which)) return fail(ctx, EK_ERR_ARG, "count does not match the field size");
+  const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t N = (size_t)ctx->g.N;
+  cudaStream_t s = ctx->stream;
+  switch (which) {
+    case EK_FIELD_SPECIES:
+      if (component < 0 || component >= ctx->p.nspecies) return fail(ctx, EK_ERR_ARG, "bad species index");
+      EK_CUDA(cudaMemcpyAsync(ctx->rho[ctx->cur] + component * N, src, N * sizeof(double), kind, s));
+      break;
+    case EK_FIELD_POPULATIONS:
+      EK_CUDA(cudaMemcpyAsync(ctx->f[ctx->cur], src, 19 * N * sizeof(double), kind, s));
+      break;
+    case EK_FIELD_VELOCITY:
+      EK_CUDA(cudaMemcpyAsync(ctx->u, src, 3 * N * sizeof(double), kind, s));
+      k_set_velocity<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->owner, ctx->f[ctx->cur], ctx->u);
+      EK_CUDA(cudaGetLastError());
+      break;
+    case EK_FIELD_E_EXT:
+    case EK_FIELD_BODY_FORCE: {
+      double v[3];
+      EK_CUDA(cudaMemcpyAsync(v, src, 3 * sizeof(double),
+                              src_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+      EK_CUDA(cudaStreamSynchronize(s));
+      for (int d = 0; d < 3; ++d) {
+        if (!isfinite(v[d])) return fail(ctx, EK_ERR_ARG, "non-finite vector");
+        if (which == EK_FIELD_E_EXT) ctx->ph.E[d] = v[d];
+        else ctx->ph.g[d] = v[d];
+      }
+      break;
+    }
+    case EK_FIELD_WALL:
+      EK_CUDA(cudaMemcpyAsync(ctx->tmp, src, N * sizeof(double), kind, s));
+      k_double_to_u8<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->tmp, ctx->wall);
+      EK_CUDA(cudaGetLastError());
+      ctx->setup_pending = true;
+      return run_setup(ctx);
+    case EK_FIELD_WALL_CHARGE:
+      EK_CUDA(cudaMemcpyAsync(ctx->qwall, src, N * sizeof(double), kind, s));
+      ctx->has_qwall = true;
+      break;
+    default:
+      return fail(ctx, EK_ERR_ARG, "field is read-only");
+  }
+  EK_CUDA(cudaStreamSynchronize(s));
+  return EK_OK;
+}
+
+ek_status ek_get_fields(ek_ctx* ctx, ek_field which, int component, double* dst, size_t count,
+                        int dst_on_device) {
+  if (!ctx) return EK_ERR_ARG;
+  if (!ctx->broken) {
+    ek_status st = ready(ctx);
+    if (st != EK_OK) return st;
+  }
+  if (!dst) return fail(ctx, EK_ERR_ARG, "null destination");
+  if (count != field_size(ctx, which)) return fail(ctx, EK_ERR_ARG, "count does not match the field size");
+  const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t N = (size_t)ctx->g.N;
+  cudaStream_t s = ctx->stream;
+  const double* srcp = nullptr;
+  size_t bytes = N * sizeof(double);
+  switch (which) {
+    case EK_FIELD_SPECIES:
+      if (component < 0 || component >= ctx->p.nspecies) return fail(ctx, EK_ERR_ARG, "bad species index");
+      srcp = ctx->rho[ctx->cur] + component * N;
+      break;
+    case EK_FIELD_POPULATIONS:
+      srcp = ctx->f[ctx->cur];
+      bytes = 19 * N * sizeof(double);
+      break;
+    case EK_FIELD_VELOCITY:
+      srcp = ctx->u;
+      bytes = 3 * N * sizeof(double);
+      break;
+    case EK_FIELD_E_EXT:
+    case EK_FIELD_BODY_FORCE: {
+      const double* v = which == EK_FIELD_E_EXT ? ctx->ph.E : ctx->ph.g;
+      EK_CUDA(cudaMemcpyAsync(dst, v, 3 * sizeof(double),
+                              dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
+      EK_CUDA(cudaStreamSynchronize(s));
+      return EK_OK;
+    }
+    case EK_FIELD_WALL:
+      k_u8_to_double<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->wall, ctx->tmp);
+      srcp = ctx->tmp;
+      break;
+    case EK_FIELD_WALL_CHARGE:
+      srcp = ctx->qwall;
+      break;
+    case EK_FIELD_DENSITY:
+      k_density<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->f[ctx->cur], ctx->tmp);
+      srcp = ctx->tmp;
+      break;
+    case EK_FIELD_PHI:
+      srcp = ctx->phi;
+      break;
+    case EK_FIELD_PSI:
+      k_psi_clamped<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->psi, ctx->tmp);
+      srcp = ctx->tmp;
+      break;
+    case EK_FIELD_OWNER:
+      k_int_to_double<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->owner, ctx->tmp);
+      srcp = ctx->tmp;
+      break;
+    case EK_FIELD_CHARGE:
+      EK_CUDA(charge_density(ctx->g, ctx->ph, ctx->rho[ctx->cur], ctx->has_qwall ? ctx->qwall : nullptr,
+                             ctx->qpart, ctx->tmp, s));
+      srcp = ctx->tmp;
+      break;
+    default:
+      return fail(ctx, EK_ERR_ARG, "unknown field");
+  }
+  EK_CUDA(cudaGetLastError());
+  EK_CUDA(cudaMemcpyAsync(dst, srcp, bytes, kind, s));
+  EK_CUDA(cudaStreamSynchronize(s));
+  return EK_OK;
+}
+
+ek_status ek_step_async(ek_ctx* ctx, int nsteps) {
+  ek_status st = ready(ctx);
+  if (st != EK_OK) return st;
+  if (nsteps < 0) return fail(ctx, EK_ERR_ARG, "nsteps < 0");
+  for (int t = 0; t < nsteps; ++t) {
+    for (int stage : {1, 2, 4, 5}) {
+      st = enqueue_stage(ctx, stage);
+      if (st != EK_OK) return st;
+    }
+  }
+  return EK_OK;
+}
+
+ek_status ek_step(ek_ctx* ctx, int nsteps) {
+  ek_status st = ek_step_async(ctx, nsteps);
+  if (st != EK_OK) return st;
+  return check_status(ctx);
+}
+
+ek_status ek_run_stage(ek_ctx* ctx, int stage) {
+  ek_status st = ready(ctx);
+  if (st != EK_OK) return st;
+  st = enqueue_stage(ctx, stage);
+  if (st != EK_OK) return st;
+  return check_status(ctx);
+}
+
+ek_status ek_get_particles(ek_ctx* ctx, ek_particle* dst, int count) {
+  if (!ctx || (!dst && count > 0) || count < 0) return EK_ERR_ARG;
+  if (!ctx->broken) {
+    ek_status st = ready(ctx);
+    if (st != EK_OK) return st;
+  }
+  ek_status st = download_particles(ctx);
+  if (st != EK_OK) return st;
+  for (int i = 0; i < std::min(count, ctx->P); ++i) {
+    const DevParticle& q = ctx->hparts[i];
+    ek_particle& o = dst[i];
+    for (int d = 0; d < 3; ++d) {
+      o.pos[d] = q.pos[d];
+      o.vel[d] = q.vel[d];
+      o.omega[d] = q.omega[d];
+      o.force[d] = q.force[d];
+      o.torque[d] = q.torque[d];
+    }
+    o.radius = q.radius;
+    o.charge = q.charge;
+    o.rho_p = q.mass / (4.0 / 3.0 * M_PI * pow(q.radius, 3.0));
+    o.fixed = q.fixed;
+  }
+  return EK_OK;
+}
+
+int ek_num_particles(const ek_ctx* ctx) { return ctx ? ctx->P : 0; }
+
+ek_status ek_set_stream(ek_ctx* ctx, void* stream) {
+  if (!ctx) return EK_ERR_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return EK_OK;
+}
+
+ek_status ek_sync(ek_ctx* ctx) {
+  if (!ctx) return EK_ERR_ARG;
+  return check_status(ctx);
+}
+
+const char* ek_last_error(const ek_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void ek_lattice_dirs(int c[57]) {
+  for (int i = 0; i < Q; ++i) {
+    c[3 * i] = HCX[i];
+    c[3 * i + 1] = HCY[i];
+    c[3 * i + 2] = HCZ[i];
+  }
+}
+
+size_t ek_poisson_scratch_bytes(int nx, int ny, int nz) { return poisson_spectrum_bytes(nx, ny, nz); }
+
+ek_status ek_poisson_solve(const double* q, double* phi, int nx, int ny, int nz, double bjerrum,
+                           void* spectrum, void* stream) {
+  if (!q || !phi || !spectrum || !edge_ok(nx) || !edge_ok(ny) || !edge_ok(nz) || nx % 2 ||
+      !(bjerrum >= 0.0))
+    return EK_ERR_ARG;
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, PoissonPlan> plans;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return EK_ERR_CUDA;
+  PoissonPlan plan;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(dev, nx, ny, nz);
+    auto it = plans.find(key);
+    if (it == plans.end()) {
+      std::string err;
+      PoissonPlan p;
+      if (poisson_plan_create(p, nx, ny, nz, err) != cudaSuccess) return EK_ERR_CUDA;
+      it = plans.emplace(key, p).first;
+    }
+    plan = it->second;
+  }
+  Phys ph;
+  memset(&ph, 0, sizeof(ph));
+  ph.bjerrum = bjerrum;
+  if (poisson_solve(plan, q, nullptr, nullptr, nullptr, ph, phi, (double2*)spectrum,
+                    (cudaStream_t)stream) != cudaSuccess)
+    return EK_ERR_CUDA;
+  return EK_OK;
+}
+
+}  // extern "C"

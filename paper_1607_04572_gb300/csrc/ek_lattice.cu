@@ -1,0 +1,321 @@
+// S2 (Capuani link fluxes + coupling force fused with the TRT/BGK collision,
+// Guo force term and push streaming with velocity bounce-back) and S3 (species
+// update: flux divergence + volume-of-fluid advection), FP64 form.
+//
+// One thread per lattice node, node index x + nx*(y + ny*z).  Populations and
+// species are structure-of-arrays (direction- / species-major), so every load
+// and store of a warp touches consecutive x: coalesced 8-byte accesses.  The
+// neighbour loads of the flux stencil are served by L1/L2 (each value is read
+// by up to 19 threads of neighbouring warps).
+#include <math.h>
+
+#include "ek_internal.cuh"
+
+namespace ek {
+
+namespace {
+
+struct Nbr {
+  int xm, xp, ym, yp, zm, zp;  // wrapped neighbour coordinates
+};
+
+__device__ __forceinline__ long long nbr_index(int d, int x, int y, int z, const Nbr& b,
+                                               int nx, int ny) {
+  const int X = CX[d] > 0 ? b.xp : (CX[d] < 0 ? b.xm : x);
+  const int Y = CY[d] > 0 ? b.yp : (CY[d] < 0 ? b.ym : y);
+  const int Z = CZ[d] > 0 ? b.zp : (CZ[d] < 0 ? b.zm : z);
+  return (long long)X + (long long)nx * ((long long)Y + (long long)ny * Z);
+}
+
+// Boundary velocity v_b = v + omega x (r_b - r) of particle p at wrapped node
+// (xb, yb, zb) (Eq. 10).  The node is unwrapped into the particle's box
+// [lo, lo + n) so that r_b - r is never taken across the periodic seam.
+__device__ __forceinline__ void boundary_velocity(const DevParticle& P, int xb, int yb, int zb,
+                                                  const Grid& g, double vb[3]) {
+  const double X = (double)(P.lo[0] + wrapi(xb - P.lo[0], g.nx));
+  const double Y = (double)(P.lo[1] + wrapi(yb - P.lo[1], g.ny));
+  const double Z = (double)(P.lo[2] + wrapi(zb - P.lo[2], g.nz));
+  const double dx = X - P.pos[0], dy = Y - P.pos[1], dz = Z - P.pos[2];
+  vb[0] = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
+  vb[1] = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
+  vb[2] = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
+}
+
+template <int K, bool PV>
+__global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
+  const long long N = a.g.N;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const int x = (int)(n % nx);
+  const long long t = n / nx;
+  const int y = (int)(t % ny);
+  const int z = (int)(t / ny);
+
+  if (a.owner[n] != FLUID) {
+    // boundary node: no fluid, no solute transport
+#pragma unroll
+    for (int k = 0; k < K; ++k) a.rho_out[k * N + n] = a.rho_in[k * N + n];
+    a.u[n] = 0.0;
+    a.u[N + n] = 0.0;
+    a.u[2 * N + n] = 0.0;
+    return;
+  }
+  Nbr b;
+  b.xm = x == 0 ? nx - 1 : x - 1;
+  b.xp = x == nx - 1 ? 0 : x + 1;
+  b.ym = y == 0 ? ny - 1 : y - 1;
+  b.yp = y == ny - 1 ? 0 : y + 1;
+  b.zm = z == 0 ? nz - 1 : z - 1;
+  b.zp = z == nz - 1 ? 0 : z + 1;
+
+  // ---- S2a: diffusive + migrative link fluxes (Eq. 20; Eq. 13 without PV) ----
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  double div[K > 0 ? K : 1];
+  double r0[K > 0 ? K : 1];
+  double om0 = 1.0;
+  if (PV) om0 = 1.0 - fmin(a.psi[n], 1.0);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    div[k] = 0.0;
+    r0[k] = a.rho_in[k * N + n];
+    if (PV && om0 != 1.0) r0[k] = r0[k] / om0;
+  }
+  if (K > 0) {
+    const double phi0 = a.phi[n];
+#pragma unroll
+    for (int d = 1; d < Q; ++d) {
+      const long long m = nbr_index(d, x, y, z, b, nx, ny);
+      if (a.owner[m] != FLUID) continue;  // no flux into or out of boundary nodes
+      double omj = 1.0;
+      if (PV) omj = 1.0 - fmin(a.psi[m], 1.0);
+      const double sc = om0 * omj;
+      const double ec = a.ph.E[0] * CX[d] + a.ph.E[1] * CY[d] + a.ph.E[2] * CZ[d];
+      const double dphi = (phi0 - a.phi[m]) + ec;
+      const double inv_len = (d < 7) ? 1.0 : 0.70710678118654752;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        double rb = a.rho_in[k * N + m];
+        if (PV && omj != 1.0) rb = rb / omj;
+        const double br = (r0[k] - rb) + a.ph.z[k] * (0.5 * (r0[k] + rb)) * dphi;
+        const double J = a.ph.dcoef[k] * inv_len * br * sc;
+        div[k] += J;
+        const double jd = J * a.ph.hinvD[k];  // coupling force, Eq. 16 with the 1/2
+        if (CX[d]) fx += CX[d] * jd;
+        if (CY[d]) fy += CY[d] * jd;
+        if (CZ[d]) fz += CZ[d] * jd;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) a.rho_out[k * N + n] = a.rho_in[k * N + n] - div[k];
+
+  // ---- S2b: collision (Eqs. 8-9) ----
+  double f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = a.f_in[i * N + n];
+  double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rho += f[i];
+    if (CX[i]) jx += CX[i] * f[i];
+    if (CY[i]) jy += CY[i] * f[i];
+    if (CZ[i]) jz += CZ[i] * f[i];
+  }
+  const double Fx = fx + a.ph.g[0], Fy = fy + a.ph.g[1], Fz = fz + a.ph.g[2];
+  const double irho = 1.0 / rho;
+  const double ux = (jx + 0.5 * Fx) * irho;
+  const double uy = (jy + 0.5 * Fy) * irho;
+  const double uz = (jz + 0.5 * Fz) * irho;
+  const double usq = ux * ux + uy * uy + uz * uz;
+  const double uF = ux * Fx + uy * Fy + uz * Fz;
+  const double gg = 2.0 * (1.0 + 0.5 * a.ph.lam_e);  // 2 (1 + lambda_e / 2)
+  const double le = a.ph.lam_e, lo = a.ph.lam_o;
+  double fs[Q];
+  {
+    const double w = wgt(0);
+    const double eqp = w * rho * (1.0 - 1.5 * usq);
+    fs[0] = f[0] + le * (f[0] - eqp) + w * (-1.5 * gg * uF);
+  }
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const int o = i + 1;
+    const double w = wgt(i);
+    const double cu = CX[i] * ux + CY[i] * uy + CZ[i] * uz;
+    const double cj = CX[i] * jx + CY[i] * jy + CZ[i] * jz;
+    const double cf = CX[i] * Fx + CY[i] * Fy + CZ[i] * Fz;
+    const double fp = 0.5 * (f[i] + f[o]);
+    const double fm = 0.5 * (f[i] - f[o]);
+    const double eqp = w * rho * (1.0 + 4.5 * cu * cu - 1.5 * usq);
+    const double eqm = w * 3.0 * cj;
+    const double dp = w * (4.5 * gg * cu * cf - 1.5 * gg * uF);
+    const double dm = w * 3.0 * cf;
+    const double ep = le * (fp - eqp) + dp;
+    const double em = lo * (fm - eqm) + dm;
+    fs[i] = f[i] + ep + em;
+    fs[o] = f[o] + ep - em;
+  }
+  if (!isfinite(rho) || !isfinite(usq)) atomicOr(a.status, ST_NONFINITE);
+  a.u[n] = ux;
+  a.u[N + n] = uy;
+  a.u[2 * N + n] = uz;
+
+  // ---- push stream with velocity bounce-back (Eq. 12) ----
+  a.f_out[n] = fs[0];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const long long m = nbr_index(i, x, y, z, b, nx, ny);
+    const int om = a.owner[m];
+    if (om == FLUID) {
+      a.f_out[i * N + m] = fs[i];
+    } else {
+      double cvb = 0.0;
+      if (om >= 0) {
+        const int xb = CX[i] > 0 ? b.xp : (CX[i] < 0 ? b.xm : x);
+        const int yb = CY[i] > 0 ? b.yp : (CY[i] < 0 ? b.ym : y);
+        const int zb = CZ[i] > 0 ? b.zp : (CZ[i] < 0 ? b.zm : z);
+        double vb[3];
+        boundary_velocity(a.parts[om], xb, yb, zb, a.g, vb);
+        cvb = CX[i] * vb[0] + CY[i] * vb[1] + CZ[i] * vb[2];
+      }
+      a.f_out[opp(i) * N + n] = fs[i] - 6.0 * wgt(i) * a.ph.rho0 * cvb;
+    }
+  }
+}
+
+// S3: rho' = (rho - div J) + volume-of-fluid advection.  rho_out holds
+// rho - div J (written by S2) and is updated in place; rho_in is the species
+// field at the start of the step (the advected one).
+template <int K>
+__global__ void __launch_bounds__(256) k_advect(LBArgs a) {
+  const long long N = a.g.N;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  if (a.owner[n] != FLUID) return;
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const int x = (int)(n % nx);
+  const long long t = n / nx;
+  const int y = (int)(t % ny);
+  const int z = (int)(t / ny);
+  double acc[K];
+  double rs[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    acc[k] = a.rho_out[k * N + n];
+    rs[k] = a.rho_in[k * N + n];
+  }
+  // outflow of this cell: offsets s with s_a in {0, sign(u_a)}
+  const double ux = a.u[n], uy = a.u[N + n], uz = a.u[2 * N + n];
+  const int sx = ux > 0.0 ? 1 : (ux < 0.0 ? -1 : 0);
+  const int sy = uy > 0.0 ? 1 : (uy < 0.0 ? -1 : 0);
+  const int sz = uz > 0.0 ? 1 : (uz < 0.0 ? -1 : 0);
+  const double ax = fabs(ux), ay = fabs(uy), az = fabs(uz);
+  for (int oz = 0; oz <= (sz != 0); ++oz) {
+    for (int oy = 0; oy <= (sy != 0); ++oy) {
+      for (int ox = 0; ox <= (sx != 0); ++ox) {
+        if (!ox && !oy && !oz) continue;
+        const double frac = (ox ? ax : 1.0 - ax) * (oy ? ay : 1.0 - ay) * (oz ? az : 1.0 - az);
+        const int X = wrapi(x + (ox ? sx : 0), nx);
+        const int Y = wrapi(y + (oy ? sy : 0), ny);
+        const int Z = wrapi(z + (oz ? sz : 0), nz);
+        const long long m = X + (long long)nx * (Y + (long long)ny * Z);
+        if (a.owner[m] != FLUID) continue;  // share aimed at a boundary stays here
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] -= rs[k] * frac;
+      }
+    }
+  }
+  // inflow from the 26 neighbours y = x - s
+  for (int qz = -1; qz <= 1; ++qz) {
+    for (int qy = -1; qy <= 1; ++qy) {
+      for (int qx = -1; qx <= 1; ++qx) {
+        if (!qx && !qy && !qz) continue;
+        const int X = wrapi(x - qx, nx);
+        const int Y = wrapi(y - qy, ny);
+        const int Z = wrapi(z - qz, nz);
+        const long long m = X + (long long)nx * (Y + (long long)ny * Z);
+        if (a.owner[m] != FLUID) continue;
+        const double vx = a.u[m], vy = a.u[N + m], vz = a.u[2 * N + m];
+        double wx, wy, wz;
+        if (qx == 0) wx = 1.0 - fabs(vx);
+        else if ((vx > 0.0 && qx > 0) || (vx < 0.0 && qx < 0)) wx = fabs(vx);
+        else continue;
+        if (qy == 0) wy = 1.0 - fabs(vy);
+        else if ((vy > 0.0 && qy > 0) || (vy < 0.0 && qy < 0)) wy = fabs(vy);
+        else continue;
+        if (qz == 0) wz = 1.0 - fabs(vz);
+        else if ((vz > 0.0 && qz > 0) || (vz < 0.0 && qz < 0)) wz = fabs(vz);
+        else continue;
+        const double frac = wx * wy * wz;
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += a.rho_in[k * N + m] * frac;
+      }
+    }
+  }
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    a.rho_out[k * N + n] = acc[k];
+    bad |= !isfinite(acc[k]);
+  }
+  if (bad) atomicOr(a.status, ST_NONFINITE);
+}
+
+__global__ void k_fill(Grid g, const int* owner, double* f, double* rho, int K, double rho0,
+                       double b0, double b1, double b2, double b3) {
+  const long long N = g.N;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const bool fl = owner[n] == FLUID;
+  const double bk[4] = {b0, b1, b2, b3};
+  for (int k = 0; k < K; ++k) rho[k * N + n] = fl ? bk[k] : 0.0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i * N + n] = fl ? wgt(i) * rho0 : 0.0;
+}
+
+unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_lb_fused(const LBArgs& a, cudaStream_t s) {
+  const unsigned nb = blocks_for(a.g.N, 256);
+  const bool pv = a.ph.pv != 0;
+  switch (a.ph.K) {
+#define EK_CASE(KK)                                                   \
+  case KK:                                                            \
+    if (pv) k_lb_fused<KK, true><<<nb, 256, 0, s>>>(a);               \
+    else k_lb_fused<KK, false><<<nb, 256, 0, s>>>(a);                 \
+    break;
+    EK_CASE(0)
+    EK_CASE(1)
+    EK_CASE(2)
+    EK_CASE(3)
+    EK_CASE(4)
+#undef EK_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advection(const LBArgs& a, cudaStream_t s) {
+  const unsigned nb = blocks_for(a.g.N, 256);
+  switch (a.ph.K) {
+    case 0: return cudaSuccess;
+    case 1: k_advect<1><<<nb, 256, 0, s>>>(a); break;
+    case 2: k_advect<2><<<nb, 256, 0, s>>>(a); break;
+    case 3: k_advect<3><<<nb, 256, 0, s>>>(a); break;
+    case 4: k_advect<4><<<nb, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(const Grid& g, const Phys& ph, const int* owner, double* f, double* rho,
+                        const double* bulk_k, cudaStream_t s) {
+  k_fill<<<blocks_for(g.N, 256), 256, 0, s>>>(g, owner, f, rho, ph.K, ph.rho0, bulk_k[0],
+                                                 bulk_k[1], bulk_k[2], bulk_k[3]);
+  return cudaGetLastError();
+}
+
+}  // namespace ek

@@ -1,0 +1,511 @@
+// S4 (particle forces and symplectic Euler integration) and S5 (re-flagging,
+// octree partial volumes Psi, Psi-smeared particle charge, fluid
+// create/destroy and solute expulsion/refill), FP64.
+//
+// All particle work is box-local: particle p touches only the cells of its
+// box [lo, hi) = [floor(r - R) - 1, floor(r + R) + 2) per axis (unwrapped
+// coordinates, so r_b - r never crosses the periodic seam), or of the union of
+// its previous and current boxes in S5.  Grids are (particle, chunk of 256
+// box cells).  Reductions over a particle (force, torque) run in one CTA in a
+// fixed order, so they are deterministic; sums of Psi are dyadic fractions and
+// exact in any order.
+#include <math.h>
+
+#include "ek_internal.cuh"
+
+namespace ek {
+
+namespace {
+
+constexpr int PT = 256;  // threads per particle CTA
+
+__device__ __forceinline__ int box_cells(const int lo[3], const int hi[3]) {
+  return (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+}
+
+__device__ __forceinline__ void box_coord(int c, const int lo[3], const int hi[3], int& X, int& Y,
+                                          int& Z) {
+  const int bx = hi[0] - lo[0], by = hi[1] - lo[1];
+  X = lo[0] + c % bx;
+  Y = lo[1] + (c / bx) % by;
+  Z = lo[2] + c / (bx * by);
+}
+
+__device__ __forceinline__ long long node_of(int X, int Y, int Z, const Grid& g) {
+  return (long long)wrapi(X, g.nx) +
+         (long long)g.nx * ((long long)wrapi(Y, g.ny) + (long long)g.ny * wrapi(Z, g.nz));
+}
+
+// squared distance, evaluated left to right without contraction so every
+// inside/outside decision is reproducible bit for bit
+__device__ __forceinline__ double dist2(double dx, double dy, double dz) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+enum { CUBE_IN = 0, CUBE_OUT = 1, CUBE_UNDECIDED = 2 };
+
+// Cube of centre c and half-width h against the sphere (r, R^2).  Inside: all
+// 8 corners strictly inside; it suffices to test the farthest corner, whose
+// rounded distance bounds the rounded distance of every other corner.
+// Outside: the closest point of the cube is at distance >= R.
+__device__ __forceinline__ int classify(double cx, double cy, double cz, double h,
+                                        const double r[3], double R2) {
+  const double ax = __dsub_rn(__dsub_rn(cx, h), r[0]), bx = __dsub_rn(__dadd_rn(cx, h), r[0]);
+  const double ay = __dsub_rn(__dsub_rn(cy, h), r[1]), by = __dsub_rn(__dadd_rn(cy, h), r[1]);
+  const double az = __dsub_rn(__dsub_rn(cz, h), r[2]), bz = __dsub_rn(__dadd_rn(cz, h), r[2]);
+  const double fx = fabs(ax) > fabs(bx) ? ax : bx;
+  const double fy = fabs(ay) > fabs(by) ? ay : by;
+  const double fz = fabs(az) > fabs(bz) ? az : bz;
+  if (dist2(fx, fy, fz) < R2) return CUBE_IN;
+  const double px = __dsub_rn(fmin(fmax(r[0], __dsub_rn(cx, h)), __dadd_rn(cx, h)), r[0]);
+  const double py = __dsub_rn(fmin(fmax(r[1], __dsub_rn(cy, h)), __dadd_rn(cy, h)), r[1]);
+  const double pz = __dsub_rn(fmin(fmax(r[2], __dsub_rn(cz, h)), __dadd_rn(cz, h)), r[2]);
+  if (dist2(px, py, pz) >= R2) return CUBE_OUT;
+  return CUBE_UNDECIDED;
+}
+
+constexpr int PSI_DEPTH = 4;
+
+// Volume fraction of the unit cell centred at (X, Y, Z) inside the sphere
+// (Sec. III.D.2): the cell is split into 8 sub-cells, each classified as
+// inside or outside; undecided ones are split again, down to depth 4 (edge
+// 1/16), where an undecided cube counts half.  Depth-first with an explicit
+// stack of child counters.
+__device__ double psi_cell(double X, double Y, double Z, const double r[3], double R2) {
+  const int s0 = classify(X, Y, Z, 0.5, r, R2);
+  if (s0 == CUBE_IN) return 1.0;
+  if (s0 == CUBE_OUT) return 0.0;
+  double bx[PSI_DEPTH + 1], by[PSI_DEPTH + 1], bz[PSI_DEPTH + 1];
+  int child[PSI_DEPTH + 1];
+  bx[0] = X;
+  by[0] = Y;
+  bz[0] = Z;
+  int l = 1;
+  child[1] = 0;
+  double total = 0.0;
+  while (l >= 1) {
+    if (child[l] == 8) {
+      --l;
+      if (l >= 1) ++child[l];
+      continue;
+    }
+    const double h = ldexp(1.0, -(l + 1));   // half-width at level l
+    const double vol = ldexp(1.0, -3 * l);   // volume at level l
+    const int c = child[l];
+    const double cx = bx[l - 1] + ((c & 1) ? h : -h);
+    const double cy = by[l - 1] + ((c & 2) ? h : -h);
+    const double cz = bz[l - 1] + ((c & 4) ? h : -h);
+    const int s = classify(cx, cy, cz, h, r, R2);
+    if (s == CUBE_IN) {
+      total += vol;
+      ++child[l];
+    } else if (s == CUBE_OUT) {
+      ++child[l];
+    } else if (l == PSI_DEPTH) {
+      total += 0.5 * vol;
+      ++child[l];
+    } else {
+      bx[l] = cx;
+      by[l] = cy;
+      bz[l] = cz;
+      ++l;
+      child[l] = 0;
+    }
+  }
+  return total;
+}
+
+__device__ __forceinline__ bool node_inside(int X, int Y, int Z, const DevParticle& P) {
+  const double dx = (double)X - P.pos[0], dy = (double)Y - P.pos[1], dz = (double)Z - P.pos[2];
+  return dist2(dx, dy, dz) < __dmul_rn(P.radius, P.radius);
+}
+
+// block-wide sum of NV doubles, fixed order; result valid in thread 0
+template <int NV>
+__device__ void block_sum(double (&v)[NV]) {
+  __shared__ double red[PT / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double s = v[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp][j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double s = 0.0;
+      for (int w = 0; w < PT / 32; ++w) s += red[w][j];
+      v[j] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S4: forces and integration, one CTA per particle
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PT) k_particle_forces(PartArgs a) {
+  const int p = blockIdx.x;
+  DevParticle& P = a.parts[p];
+  const Grid g = a.g;
+  const long long N = g.N;
+  const int ncell = box_cells(P.lo, P.hi);
+  const bool pv = a.ph.pv != 0;
+  double qnorm = 0.0;
+  if (pv) {
+    qnorm = (a.ph.flags & EK_CHARGE_NORM_VP)
+                ? P.charge / (4.0 / 3.0 * M_PI * P.radius * P.radius * P.radius)
+                : (P.psisum > 0.0 ? P.charge / P.psisum : 0.0);
+  } else {
+    qnorm = P.nb > 0 ? P.charge / (double)P.nb : 0.0;
+  }
+  // Fh(3) Th(3) Fe(3) Te(3)
+  double acc[12];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) acc[j] = 0.0;
+  for (int c = threadIdx.x; c < ncell; c += PT) {
+    int X, Y, Z;
+    box_coord(c, P.lo, P.hi, X, Y, Z);
+    const long long n = node_of(X, Y, Z, g);
+    const int own = a.owner[n];
+    if (own == FLUID) {
+      // momentum exchange on every link from this fluid node into the particle (Eq. 11)
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const long long m = node_of(X + CX[i], Y + CY[i], Z + CZ[i], g);
+        if (a.owner[m] != p) continue;
+        const double dx = (double)(X + CX[i]) - P.pos[0];
+        const double dy = (double)(Y + CY[i]) - P.pos[1];
+        const double dz = (double)(Z + CZ[i]) - P.pos[2];
+        const double vbx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
+        const double vby = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
+        const double vbz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
+        const double cvb = CX[i] * vbx + CY[i] * vby + CZ[i] * vbz;
+        const double refl = a.f[(long long)opp(i) * N + n];
+        const double fs = refl + 6.0 * wgt(i) * a.ph.rho0 * cvb;  // the population that hit the wall
+        const double mom = fs + refl;
+        const double px = CX[i] * mom, py = CY[i] * mom, pz = CZ[i] * mom;
+        acc[0] += px;
+        acc[1] += py;
+        acc[2] += pz;
+        acc[3] += dy * pz - dz * py;
+        acc[4] += dz * px - dx * pz;
+        acc[5] += dx * py - dy * px;
+      }
+    }
+    // electrostatic force on the particle's charge in this cell
+    double qq = 0.0;
+    if (pv) qq = qnorm * a.psibox[(long long)p * a.boxmax + c];
+    else if (own == p) qq = qnorm;
+    if (qq != 0.0) {
+      const long long nxp = node_of(X + 1, Y, Z, g), nxm = node_of(X - 1, Y, Z, g);
+      const long long nyp = node_of(X, Y + 1, Z, g), nym = node_of(X, Y - 1, Z, g);
+      const long long nzp = node_of(X, Y, Z + 1, g), nzm = node_of(X, Y, Z - 1, g);
+      const double gx = 0.5 * (a.phi[nxp] - a.phi[nxm]);
+      const double gy = 0.5 * (a.phi[nyp] - a.phi[nym]);
+      const double gz = 0.5 * (a.phi[nzp] - a.phi[nzm]);
+      const double frx = qq * (a.ph.E[0] - gx), fry = qq * (a.ph.E[1] - gy), frz = qq * (a.ph.E[2] - gz);
+      const double dx = (double)X - P.pos[0], dy = (double)Y - P.pos[1], dz = (double)Z - P.pos[2];
+      acc[6] += frx;
+      acc[7] += fry;
+      acc[8] += frz;
+      acc[9] += dy * frz - dz * fry;
+      acc[10] += dz * frx - dx * frz;
+      acc[11] += dx * fry - dy * frx;
+    }
+  }
+  block_sum<12>(acc);
+  if (threadIdx.x == 0) {
+    double F[3], T[3];
+    for (int d = 0; d < 3; ++d) {
+      F[d] = acc[d] + acc[6 + d] + P.ftrans[d];
+      T[d] = acc[3 + d] + acc[9 + d];
+      P.force[d] = F[d];
+      P.torque[d] = T[d];
+      P.ftrans[d] = 0.0;
+    }
+    if (!P.fixed) {
+      const int nn[3] = {g.nx, g.ny, g.nz};
+      for (int d = 0; d < 3; ++d) {
+        P.vel[d] = P.vel[d] + F[d] / P.mass;
+        P.omega[d] = P.omega[d] + T[d] / P.inertia;
+        P.pos[d] = P.pos[d] + P.vel[d];
+        if (P.pos[d] >= (double)nn[d]) P.pos[d] -= (double)nn[d];
+        else if (P.pos[d] < 0.0) P.pos[d] += (double)nn[d];
+      }
+      if (!isfinite(P.pos[0] + P.pos[1] + P.pos[2])) atomicOr(a.status, ST_NONFINITE);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S5 and set-up
+// ---------------------------------------------------------------------------
+__global__ void k_box_update(PartArgs a, bool setup) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.P) return;
+  DevParticle& P = a.parts[p];
+  for (int d = 0; d < 3; ++d) {
+    const int lo = (int)floor(P.pos[d] - P.radius) - 1;
+    const int hi = (int)floor(P.pos[d] + P.radius) + 2;
+    P.ulo[d] = setup ? lo : min(lo, P.lo[d]);
+    P.uhi[d] = setup ? hi : max(hi, P.hi[d]);
+    P.lo[d] = lo;
+    P.hi[d] = hi;
+  }
+  P.psisum = 0.0;
+  P.nb = 0;
+}
+
+__global__ void k_save_prev(PartArgs a) {
+  const DevParticle& P = a.parts[blockIdx.x];
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= box_cells(P.ulo, P.uhi)) return;
+  int X, Y, Z;
+  box_coord(c, P.ulo, P.uhi, X, Y, Z);
+  const long long n = node_of(X, Y, Z, a.g);
+  a.owner_prev[n] = a.owner[n];
+}
+
+__global__ void k_clear(PartArgs a) {
+  const DevParticle& P = a.parts[blockIdx.x];
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= box_cells(P.ulo, P.uhi)) return;
+  int X, Y, Z;
+  box_coord(c, P.ulo, P.uhi, X, Y, Z);
+  const long long n = node_of(X, Y, Z, a.g);
+  if (a.owner[n] >= 0) a.owner[n] = FLUID;
+  a.psi[n] = 0.0;
+  a.qpart[n] = 0.0;
+}
+
+__global__ void k_reset_all(PartArgs a) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.g.N) return;
+  a.owner[n] = (a.wall && a.wall[n]) ? WALL : FLUID;
+  a.psi[n] = 0.0;
+  a.qpart[n] = 0.0;
+}
+
+// boundary nodes (cell centre strictly inside) and Psi_p of the current box
+__global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
+  const int p = blockIdx.x;
+  DevParticle& P = a.parts[p];
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  const int ncell = box_cells(P.lo, P.hi);
+  double ps = 0.0;
+  int inside = 0;
+  if (c < ncell) {
+    int X, Y, Z;
+    box_coord(c, P.lo, P.hi, X, Y, Z);
+    const long long n = node_of(X, Y, Z, a.g);
+    const double R2 = __dmul_rn(P.radius, P.radius);
+    if (node_inside(X, Y, Z, P)) {
+      inside = 1;
+      const int old = atomicCAS(a.owner + n, FLUID, p);
+      if (old != FLUID) atomicOr(a.status, ST_OVERLAP);
+    }
+    ps = psi_cell((double)X, (double)Y, (double)Z, P.pos, R2);
+    a.psibox[(long long)p * a.boxmax + c] = ps;
+    if (ps != 0.0) atomicAdd(a.psi + n, ps);
+  }
+  double v[2] = {ps, (double)inside};
+  block_sum<2>(v);
+  if (threadIdx.x == 0) {
+    if (v[0] != 0.0) atomicAdd(&P.psisum, v[0]);  // dyadic: exact in any order
+    if (v[1] != 0.0) atomicAdd(&P.nb, (int)v[1]);
+  }
+}
+
+// Psi-smeared particle charge (Eq. 21), or spread over the boundary nodes
+__global__ void k_charge_scatter(PartArgs a) {
+  const int p = blockIdx.x;
+  const DevParticle& P = a.parts[p];
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= box_cells(P.lo, P.hi)) return;
+  int X, Y, Z;
+  box_coord(c, P.lo, P.hi, X, Y, Z);
+  const long long n = node_of(X, Y, Z, a.g);
+  double q = 0.0;
+  if (a.ph.pv) {
+    const double ps = a.psibox[(long long)p * a.boxmax + c];
+    if (ps == 0.0) return;
+    if (a.ph.flags & EK_CHARGE_NORM_VP)
+      q = P.charge * ps / (4.0 / 3.0 * M_PI * P.radius * P.radius * P.radius);
+    else
+      q = P.charge * ps / P.psisum;
+  } else {
+    if (a.owner[n] != p || P.nb == 0) return;
+    q = P.charge / (double)P.nb;
+  }
+  atomicAdd(a.qpart + n, q);
+}
+
+__device__ __forceinline__ bool steady_fluid(const PartArgs& a, long long m) {
+  return a.owner_prev[m] == FLUID && a.owner[m] == FLUID;
+}
+
+// Newly covered / uncovered nodes of particle p (Sec. III.B, III.D.1).  Solute
+// transfers are computed from the values before the transitions and recorded;
+// k_apply_transfers adds them afterwards.
+__global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
+  const int p = blockIdx.x;
+  DevParticle& P = a.parts[p];
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= box_cells(P.ulo, P.uhi)) return;
+  int X, Y, Z;
+  box_coord(c, P.ulo, P.uhi, X, Y, Z);
+  const Grid g = a.g;
+  const long long N = g.N;
+  const long long n = node_of(X, Y, Z, g);
+  const int old = a.owner_prev[n], nw = a.owner[n];
+  const bool covered = old == FLUID && nw == p;
+  const bool uncovered = old == p && nw == FLUID;
+  if (!covered && !uncovered) return;
+  const int K = a.ph.K;
+  long long rec[Q];
+  int nf = 0;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const long long m = node_of(X + CX[i], Y + CY[i], Z + CZ[i], g);
+    if (steady_fluid(a, m)) rec[nf++] = m;
+  }
+  if (covered) {
+    // destroyed fluid: its momentum goes to the particle
+    double mx = 0.0, my = 0.0, mz = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double fi = a.fw[(long long)i * N + n];
+      if (CX[i]) mx += CX[i] * fi;
+      if (CY[i]) my += CY[i] * fi;
+      if (CZ[i]) mz += CZ[i] * fi;
+      a.fw[(long long)i * N + n] = 0.0;
+    }
+    atomicAdd(&P.ftrans[0], mx);
+    atomicAdd(&P.ftrans[1], my);
+    atomicAdd(&P.ftrans[2], mz);
+    if (nf == 0) {
+      atomicOr(a.status, ST_EXPEL);
+      return;
+    }
+    if (K == 0) return;
+    const int slot = atomicAdd(a.xfer_count, 1 + nf);
+    if (slot + 1 + nf > a.xfer_cap) {
+      atomicOr(a.status, ST_CAPACITY);
+      return;
+    }
+    Transfer self;
+    self.node = n;
+    double share[EK_MAX_SPECIES];
+    for (int k = 0; k < EK_MAX_SPECIES; ++k) {
+      const double r = k < K ? a.rho[k * N + n] : 0.0;
+      self.amount[k] = -r;
+      share[k] = r / (double)nf;
+    }
+    a.xfer[slot] = self;
+    for (int j = 0; j < nf; ++j) {
+      Transfer t;
+      t.node = rec[j];
+      for (int k = 0; k < EK_MAX_SPECIES; ++k) t.amount[k] = share[k];
+      a.xfer[slot + 1 + j] = t;
+    }
+  } else {
+    // created fluid: f^eq(mean neighbour density, v_b), momentum taken from the particle
+    double rbar = a.ph.rho0;
+    if (nf > 0) {
+      double s = 0.0;
+      for (int j = 0; j < nf; ++j) {
+        double d = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d += a.fw[(long long)i * N + rec[j]];
+        s += d;
+      }
+      rbar = s / (double)nf;
+    }
+    // v_b at this node, unwrapped into the particle's current box
+    const double Xu = (double)(P.lo[0] + wrapi(wrapi(X, g.nx) - P.lo[0], g.nx));
+    const double Yu = (double)(P.lo[1] + wrapi(wrapi(Y, g.ny) - P.lo[1], g.ny));
+    const double Zu = (double)(P.lo[2] + wrapi(wrapi(Z, g.nz) - P.lo[2], g.nz));
+    const double dx = Xu - P.pos[0], dy = Yu - P.pos[1], dz = Zu - P.pos[2];
+    const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
+    const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
+    const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
+    const double usq = vx * vx + vy * vy + vz * vz;
+    double mx = 0.0, my = 0.0, mz = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double cu = CX[i] * vx + CY[i] * vy + CZ[i] * vz;
+      const double fi = wgt(i) * rbar * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+      a.fw[(long long)i * N + n] = fi;
+      if (CX[i]) mx += CX[i] * fi;
+      if (CY[i]) my += CY[i] * fi;
+      if (CZ[i]) mz += CZ[i] * fi;
+    }
+    atomicAdd(&P.ftrans[0], -mx);
+    atomicAdd(&P.ftrans[1], -my);
+    atomicAdd(&P.ftrans[2], -mz);
+    if ((a.ph.flags & EK_VACATE_ZERO) || nf == 0 || K == 0) return;
+    // refill, Eqs. 17-18: each neighbour gives rho/(N_f + 1)
+    const int slot = atomicAdd(a.xfer_count, 2 * nf);
+    if (slot + 2 * nf > a.xfer_cap) {
+      atomicOr(a.status, ST_CAPACITY);
+      return;
+    }
+    for (int j = 0; j < nf; ++j) {
+      Transfer give, take;
+      give.node = rec[j];
+      take.node = n;
+      for (int k = 0; k < EK_MAX_SPECIES; ++k) {
+        const double sh = k < K ? a.rho[k * N + rec[j]] / (double)(nf + 1) : 0.0;
+        give.amount[k] = -sh;
+        take.amount[k] = sh;
+      }
+      a.xfer[slot + 2 * j] = give;
+      a.xfer[slot + 2 * j + 1] = take;
+    }
+  }
+}
+
+__global__ void k_apply_transfers(PartArgs a) {
+  const int count = min(*a.xfer_count, a.xfer_cap);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < count; r += gridDim.x * blockDim.x) {
+    const Transfer t = a.xfer[r];
+    for (int k = 0; k < a.ph.K; ++k) atomicAdd(a.rho + k * a.g.N + t.node, t.amount[k]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s) {
+  if (a.P == 0) return cudaSuccess;
+  k_particle_forces<<<a.P, PT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s) {
+  const Grid& g = a.g;
+  if (!transitions) {
+    k_reset_all<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(a);
+  }
+  if (a.P == 0) return cudaGetLastError();
+  k_box_update<<<(a.P + 127) / 128, 128, 0, s>>>(a, !transitions);
+  // union boxes are at most one cell wider than a box per axis
+  const int edge = (int)round(cbrt((double)a.boxmax)) + 1;
+  const unsigned uchunks = (unsigned)((edge * edge * edge + PT - 1) / PT);
+  const unsigned bchunks = (unsigned)((a.boxmax + PT - 1) / PT);
+  if (transitions) {
+    k_save_prev<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
+    k_clear<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
+  }
+  k_claim<<<dim3(a.P, bchunks), PT, 0, s>>>(a);
+  k_charge_scatter<<<dim3(a.P, bchunks), PT, 0, s>>>(a);
+  if (transitions) {
+    k_transitions<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
+    k_apply_transfers<<<152, 256, 0, s>>>(a);
+    cudaMemsetAsync(a.xfer_count, 0, sizeof(int), s);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ek

@@ -1,0 +1,272 @@
+"""Python binding of the C ABI in include/ek.h (libek.so): argument marshalling only.
+
+Every step of the time step runs in the CUDA library; this module converts
+numpy arrays and torch tensors to pointers and status codes to exceptions.
+There is no CPU fallback: if libek.so is missing or cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libek.so")
+
+EK_MAX_SPECIES = 4
+
+# ek_params.flags
+EK_PV = 1
+EK_VACATE_ZERO = 2
+EK_CHARGE_NORM_VP = 4
+EK_NEUTRALIZE = 8
+
+# ek_field
+FIELD_SPECIES = 0
+FIELD_POPULATIONS = 1
+FIELD_VELOCITY = 2
+FIELD_E_EXT = 3
+FIELD_BODY_FORCE = 4
+FIELD_WALL = 5
+FIELD_WALL_CHARGE = 6
+FIELD_DENSITY = 7
+FIELD_PHI = 8
+FIELD_PSI = 9
+FIELD_OWNER = 10
+FIELD_CHARGE = 11
+
+STATUS = {0: "EK_OK", -1: "EK_ERR_ARG", -2: "EK_ERR_NOMEM", -3: "EK_ERR_CUDA",
+          -4: "EK_ERR_UNSTABLE", -5: "EK_ERR_OVERLAP", -6: "EK_ERR_EXPEL", -8: "EK_ERR_STATE"}
+
+# entry points declared in include/ek.h
+EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get_fields",
+           "ek_step", "ek_step_async", "ek_run_stage", "ek_get_particles", "ek_num_particles",
+           "ek_set_stream", "ek_sync", "ek_last_error", "ek_lattice_dirs",
+           "ek_poisson_scratch_bytes", "ek_poisson_solve"]
+
+
+class EKError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("nu", ctypes.c_double), ("rho0", ctypes.c_double), ("bjerrum", ctypes.c_double),
+                ("magic", ctypes.c_double), ("nspecies", ctypes.c_int),
+                ("valence", ctypes.c_int * EK_MAX_SPECIES),
+                ("D", ctypes.c_double * EK_MAX_SPECIES),
+                ("bulk", ctypes.c_double * EK_MAX_SPECIES),
+                ("flags", ctypes.c_uint)]
+
+
+class ParticleRec(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_double * 3), ("vel", ctypes.c_double * 3),
+                ("omega", ctypes.c_double * 3), ("force", ctypes.c_double * 3),
+                ("torque", ctypes.c_double * 3), ("radius", ctypes.c_double),
+                ("charge", ctypes.c_double), ("rho_p", ctypes.c_double), ("fixed", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libek.so (building it first if the CUDA toolkit is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        from . import build as _build
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.ek_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(vp)]
+    lib.ek_destroy.argtypes = [vp]
+    lib.ek_add_particle.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(dp),
+                                    dp, dp, dp, ip, ctypes.POINTER(ip)]
+    lib.ek_set_field.argtypes = [vp, ip, ip, vp, ctypes.c_size_t, ip]
+    lib.ek_get_fields.argtypes = [vp, ip, ip, vp, ctypes.c_size_t, ip]
+    lib.ek_step.argtypes = [vp, ip]
+    lib.ek_step_async.argtypes = [vp, ip]
+    lib.ek_run_stage.argtypes = [vp, ip]
+    lib.ek_get_particles.argtypes = [vp, ctypes.POINTER(ParticleRec), ip]
+    lib.ek_num_particles.argtypes = [vp]
+    lib.ek_num_particles.restype = ip
+    lib.ek_set_stream.argtypes = [vp, vp]
+    lib.ek_sync.argtypes = [vp]
+    lib.ek_last_error.argtypes = [vp]
+    lib.ek_last_error.restype = ctypes.c_char_p
+    lib.ek_lattice_dirs.argtypes = [ctypes.POINTER(ip)]
+    lib.ek_lattice_dirs.restype = None
+    lib.ek_poisson_scratch_bytes.argtypes = [ip, ip, ip]
+    lib.ek_poisson_scratch_bytes.restype = ctypes.c_size_t
+    lib.ek_poisson_solve.argtypes = [vp, vp, ip, ip, ip, dp, vp, vp]
+    for name in EXPORTS:
+        if name not in ("ek_num_particles", "ek_last_error", "ek_lattice_dirs",
+                        "ek_poisson_scratch_bytes"):
+            getattr(lib, name).restype = ip
+    _lib = lib
+    return lib
+
+
+def lattice_dirs() -> np.ndarray:
+    """The (19, 3) D3Q19 velocity set in the library's population order."""
+    lib = load_library()
+    c = (ctypes.c_int * 57)()
+    lib.ek_lattice_dirs(c)
+    return np.array(list(c), dtype=np.int64).reshape(19, 3)
+
+
+def _buf(values, on_device_ok=True):
+    """(pointer, count, on_device, keepalive) of a numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(values, torch.Tensor):
+            if values.dtype != torch.float64 or not values.is_contiguous():
+                raise TypeError("torch tensors must be contiguous float64")
+            return values.data_ptr(), values.numel(), int(values.is_cuda), values
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(values, dtype=np.float64)
+    return arr.ctypes.data, arr.size, 0, arr
+
+
+class EKSystem:
+    """One electrokinetic box on the GPU (an ek_ctx)."""
+
+    def __init__(self, shape, nu=1.0 / 6.0, rho0=1.0, bjerrum=0.7, valence=(1, -1),
+                 D=(0.3, 0.3), bulk=(1e-3, 1e-3), flags=EK_PV | EK_NEUTRALIZE, magic=0.0):
+        self.lib = load_library()
+        p = Params()
+        p.nx, p.ny, p.nz = (int(v) for v in shape)
+        p.nu, p.rho0, p.bjerrum = float(nu), float(rho0), float(bjerrum)
+        p.magic = float(magic or 0.0)
+        K = len(valence)
+        p.nspecies = K
+        for k in range(K):
+            p.valence[k] = int(valence[k])
+            p.D[k] = float(D[k])
+            p.bulk[k] = float(bulk[k])
+        p.flags = int(flags)
+        self.params = p
+        self.shape = (p.nx, p.ny, p.nz)
+        self.N = p.nx * p.ny * p.nz
+        self.K = K
+        self.ctx = ctypes.c_void_p()
+        st = self.lib.ek_create(ctypes.byref(p), ctypes.byref(self.ctx))
+        if st != 0:
+            raise EKError(st, "ek_create failed")
+
+    # -- helpers ---------------------------------------------------------------
+    def _check(self, st):
+        if st != 0:
+            raise EKError(st, self.lib.ek_last_error(self.ctx).decode())
+
+    def close(self):
+        if self.ctx:
+            self.lib.ek_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field_size(self, which):
+        if which == FIELD_POPULATIONS:
+            return 19 * self.N
+        if which == FIELD_VELOCITY:
+            return 3 * self.N
+        if which in (FIELD_E_EXT, FIELD_BODY_FORCE):
+            return 3
+        return self.N
+
+    # -- ABI calls ---------------------------------------------------------------
+    def add_particle(self, pos, vel=(0, 0, 0), radius=4.0, charge=0.0, rho_p=2.0, fixed=False,
+                     omega=(0, 0, 0)):
+        D3 = ctypes.c_double * 3
+        out = ctypes.c_int(-1)
+        self._check(self.lib.ek_add_particle(self.ctx, D3(*pos), D3(*vel), D3(*omega),
+                                             float(radius), float(charge), float(rho_p),
+                                             int(bool(fixed)), ctypes.byref(out)))
+        return out.value
+
+    def set_field(self, which, values, component=0):
+        ptr, n, dev, keep = _buf(values)
+        self._check(self.lib.ek_set_field(self.ctx, which, component, ctypes.c_void_p(ptr), n, dev))
+        del keep
+
+    def get_fields(self, which, component=0, out=None):
+        """Read a field; returns a numpy array shaped like the field, or fills
+        `out` (numpy array or torch tensor, host or device)."""
+        n = self.field_size(which)
+        if out is None:
+            arr = np.empty(n, dtype=np.float64)
+            self._check(self.lib.ek_get_fields(self.ctx, which, component,
+                                               ctypes.c_void_p(arr.ctypes.data), n, 0))
+            nx, ny, nz = self.shape
+            if n == 3:
+                return arr
+            if n == self.N:
+                return arr.reshape(nz, ny, nx)
+            return arr.reshape(n // self.N, nz, ny, nx)
+        ptr, cnt, dev, keep = _buf(out)
+        if cnt != n:
+            raise ValueError("output size does not match the field")
+        self._check(self.lib.ek_get_fields(self.ctx, which, component, ctypes.c_void_p(ptr), n, dev))
+        return out
+
+    def step(self, n=1):
+        self._check(self.lib.ek_step(self.ctx, int(n)))
+
+    def step_async(self, n=1):
+        self._check(self.lib.ek_step_async(self.ctx, int(n)))
+
+    def run_stage(self, stage):
+        self._check(self.lib.ek_run_stage(self.ctx, int(stage)))
+
+    def sync(self):
+        self._check(self.lib.ek_sync(self.ctx))
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an integer handle, or None."""
+        h = 0
+        if stream is not None:
+            h = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.ek_set_stream(self.ctx, ctypes.c_void_p(int(h))))
+
+    def num_particles(self):
+        return self.lib.ek_num_particles(self.ctx)
+
+    def get_particles(self):
+        P = self.num_particles()
+        recs = (ParticleRec * max(P, 1))()
+        self._check(self.lib.ek_get_particles(self.ctx, recs, P))
+        out = []
+        for r in recs[:P]:
+            out.append(dict(pos=np.array(r.pos[:]), vel=np.array(r.vel[:]),
+                            omega=np.array(r.omega[:]), force=np.array(r.force[:]),
+                            torque=np.array(r.torque[:]), radius=r.radius, charge=r.charge,
+                            rho_p=r.rho_p, fixed=bool(r.fixed)))
+        return out
+
+
+def poisson_scratch_bytes(nx, ny, nz):
+    return load_library().ek_poisson_scratch_bytes(nx, ny, nz)
+
+
+def poisson_solve(q, phi, shape, bjerrum, spectrum, stream=None):
+    """Standalone Poisson solve on device tensors (torch, float64): see ek.h."""
+    lib = load_library()
+    nx, ny, nz = shape
+    h = 0 if stream is None else getattr(stream, "cuda_stream", stream)
+    st = lib.ek_poisson_solve(ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                              nx, ny, nz, float(bjerrum), ctypes.c_void_p(spectrum.data_ptr()),
+                              ctypes.c_void_p(int(h)))
+    if st != 0:
+        raise EKError(st, "ek_poisson_solve failed")

@@ -496,7 +496,7 @@ def _naive_step_parts(o):
 
 
 def test_brute_force_against_naive_loops():
-    o = EKOracle(9, 8, 10, bulk=(2e-3, 1e-3), magic=3.0 / 16.0)
+    o = EKOracle(10, 10, 12, bulk=(2e-3, 1e-3), magic=3.0 / 16.0)
     o.E = np.array([0.01, 0.002, -0.004])
     o.g = np.array([1e-5, 0.0, 2e-5])
     o.add_particle((4.2, 3.9, 5.1), vel=(0.01, -0.02, 0.015), omega=(0.001, 0.002, -0.003),
