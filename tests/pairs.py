@@ -3,7 +3,10 @@ from the same seeded inputs, and compare their fields.
 
 Tolerance (the parity metric for the FP64 path): per element
     |x_gpu - x_ref| <= TOL * max(|x_ref|, 1e-3 * max|x_ref|),  TOL = 1e-11,
-the floor keeps zero crossings of Phi and u from dividing by ~0.
+the floor keeps zero crossings of Phi from dividing by ~0.  The fluid velocity
+u = (sum_i f_i c_i + f/2)/rho is a difference of populations of size w_i rho,
+so its per-node rounding grows like rho/|u| (~1e3 and more); it is compared
+normwise instead: max|u_gpu - u_ref| <= TOL * max|u_ref|.
 """
 import numpy as np
 
@@ -67,14 +70,14 @@ def make_pair(ek, case, flags=O.PV | O.NEUTRALIZE, magic=None, perturb=0.01, see
     return o, s
 
 
-def rel_err(a, b):
-    """max over elements of |a - b| / max(|b|, 1e-3 max|b|) (0 for b == 0 == a)."""
+def rel_err(a, b, floor=1e-3):
+    """max over elements of |a - b| / max(|b|, floor * max|b|) (0 for b == 0 == a)."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     scale = np.max(np.abs(b)) if b.size else 0.0
     if scale == 0.0:
         return float(np.max(np.abs(a))) if a.size else 0.0
-    den = np.maximum(np.abs(b), 1e-3 * scale)
+    den = np.maximum(np.abs(b), floor * scale)
     return float(np.max(np.abs(a - b) / den))
 
 
@@ -94,7 +97,7 @@ def compare(ek, o, s, tol=TOL, what=("species", "populations", "velocity", "phi"
         fg = s.get_fields(ek.FIELD_POPULATIONS)[perm]
         errs["f"] = rel_err(fg[:, fluid], o.f[:, fluid])
     if "velocity" in what:
-        errs["u"] = rel_err(s.get_fields(ek.FIELD_VELOCITY)[:, fluid], o.u[:, fluid])
+        errs["u"] = rel_err(s.get_fields(ek.FIELD_VELOCITY)[:, fluid], o.u[:, fluid], floor=1.0)
     if "phi" in what:
         errs["phi"] = rel_err(s.get_fields(ek.FIELD_PHI), o.phi)
     if "psi" in what:
