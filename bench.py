@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Throughput of the full moving-boundary electrokinetics step (S1-S5) on GB300.
+
+Workload (default): the single-sphere electrophoresis box -- 128^3 periodic
+lattice, D3Q19 BGK tau = 1, 2 ion species (z = +1/-1, D = 0.3, bulk 1e-3,
+neutralised), Bjerrum length 0.7, one sphere R = 8, Z = -300 at a seeded
+off-centre position, free to move, E = 0.005 along x; FP64 form.  A step is one
+full time step: Poisson, fused flux + LB, advection, particle forces and
+integration, re-flagging and transitions.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  `value` is MLUPS (million lattice-node updates
+per second, boundary nodes included) over all ranks; with N > 1 every rank
+runs its own replica of the box (weak scaling, no collective on the data path).
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS per full EK step and % of HBM roofline, FP32/batched vs plain FP64 at 1e-3 mobility"
+FLUSH_NOTE = "state > L2 (FP64 populations 2 x 19 x 8 B x N = 637 MB at 128^3), no flush needed"
+
+# Algorithmic work of the fused flux + LB kernel (k_lb_fused), per fluid node,
+# two species, partial volumes on, bulk node (all 18 links fluid): bytes that
+# must cross HBM once per step and FP64 operations of the formulas.
+LB_BYTES_PER_NODE = 2 * 19 * 8 + 2 * 2 * 8 + 8 + 8 + 4 + 3 * 8   # f r/w, rho r/w, psi, phi, owner, u
+LB_FP64_FLOP_PER_NODE = 950
+# FP64 peak derived from the unit counts: 152 SMs x 2.07 GHz x 4 flop/clk/SM
+# (2 DFMA per clock per SM); a DFMA probe on this pool measured 1.19 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+
+# DRAM traffic of one k_lb_fused launch from an ncu capture (profiles/), valid
+# only for the kernel source it was taken on.
+TRAFFIC = {"k_lb_fused": {"bytes_per_launch": None, "source_sha": None}}
+
+
+def src_sha(name: str) -> str:
+    p = os.path.join(ROOT, "paper_1607_04572_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def build_system(ek, w):
+    s = ek.EKSystem(w["shape"], nu=w["nu"], rho0=w["rho0"], bjerrum=w["bjerrum"],
+                    valence=w["valence"], D=w["D"], bulk=w["bulk"],
+                    flags=ek.EK_PV | ek.EK_NEUTRALIZE)
+    for p in w["particles"]:
+        s.add_particle(p["pos"], radius=p["radius"], charge=p["charge"], rho_p=w["rho_p"])
+    import numpy as np
+    s.set_field(ek.FIELD_E_EXT, np.array(w["E"], dtype=np.float64))
+    return s
+
+
+def build_oracle(w):
+    import numpy as np
+    from oracle.ek_oracle import EKOracle, NEUTRALIZE, PV
+    o = EKOracle(*w["shape"], nu=w["nu"], rho0=w["rho0"], bjerrum=w["bjerrum"],
+                 valence=w["valence"], D=w["D"], bulk=w["bulk"], flags=PV | NEUTRALIZE)
+    for p in w["particles"]:
+        o.add_particle(p["pos"], radius=p["radius"], charge=p["charge"], rho_p=w["rho_p"])
+    o.E = np.array(w["E"], dtype=np.float64)
+    return o
+
+
+def time_oracle(w, max_steps, budget_s, warmup=1):
+    """Oracle MLUPS on the host: `warmup` untimed steps, then up to max_steps
+    timed steps or until budget_s seconds are spent."""
+    o = build_oracle(w)
+    for _ in range(warmup):
+        o.step()
+    nodes = w["shape"][0] * w["shape"][1] * w["shape"][2]
+    t0 = time.perf_counter()
+    done = 0
+    while done < max_steps:
+        o.step()
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return nodes * done / dt / 1e6, done, dt
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    nodes = w["shape"][0] * w["shape"][1] * w["shape"][2]
+    # each oracle step of the 128^3 box takes seconds: time a bounded sample
+    value, done, dt = time_oracle(w, args.steps, budget_s=120.0, warmup=min(args.warmup, 1))
+    sample = (f"{done} timed of {args.steps} requested steps of the {w['shape'][0]}^3 workload "
+              f"after {min(args.warmup, 1)} warm-up step(s); numpy FP64 oracle, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": done, "warmup": min(args.warmup, 1),
+            "ms_per_step": round(dt / done * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "single-sphere electrophoresis 128^3, R=8, Z=-300, 2 species, "
+                                   "E=0.005, FP64", "nodes": nodes, "parallelism": "replicas",
+                       "l2": FLUSH_NOTE},
+            "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    import workloads
+    w = workloads.workload("single")
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1607_04572_gb300 import ek
+
+    nodes = w["shape"][0] * w["shape"][1] * w["shape"][2]
+    s = build_system(ek, w)
+    stream = torch.cuda.Stream()
+    s.set_stream(stream)
+    s.step(max(args.warmup, 3))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed region: K full steps, inputs resident in HBM ----
+    clk = ClockSampler(local)
+    barrier()
+    clk.start()
+    launches0 = s.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step_async(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    barrier()
+    clocks = clk.stop()
+    launches = s.kernel_launches() - launches0
+    s.sync()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nodes * args.steps * ws / (ms / 1e3) / 1e6
+
+    # ---- per-stage device times (CUDA events between stages on the same stream) ----
+    kst = max(10, min(args.steps, 50))
+    stage = s.step_timed(kst)
+    lb_ms = stage[1] / kst
+
+    # ---- end to end through the public API with host buffers ----
+    # every step: the field E goes host -> device from pinned memory, the step
+    # runs, the particle records (the mobility observable) come back to the host
+    e_host = torch.tensor(w["E"], dtype=torch.float64).pin_memory()
+    e2e_steps = max(5, min(args.steps, 50))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_field(ek.FIELD_E_EXT, e_host)
+        s.step_async(1)
+        parts = s.get_particles()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = nodes * e2e_steps * ws / e2e_s / 1e6
+    h2d = 3 * 8
+    d2h = len(parts) * ctypes_sizeof_particle(ek)
+
+    peaks, peak_kind = measured_peaks()
+    achieved_tflops = LB_FP64_FLOP_PER_NODE * nodes / (lb_ms / 1e3) / 1e12
+    achieved_gbs = LB_BYTES_PER_NODE * nodes / (lb_ms / 1e3) / 1e9
+    traffic = TRAFFIC["k_lb_fused"]
+    tr = traffic["bytes_per_launch"] if traffic["source_sha"] == src_sha("ek_lattice.cu") else None
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "single-sphere electrophoresis 128^3, R=8, Z=-300, 2 species, "
+                               "E=0.005, FP64", "nodes": nodes, "particles": len(w["particles"]),
+                   "parallelism": "replicas" if ws > 1 else "single", "l2": FLUSH_NOTE},
+        "roofline": {"bound": "alu", "kernel": "k_lb_fused", "achieved": round(achieved_tflops, 4),
+                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s (FP64)",
+                     "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
+                     "traffic": tr, "algorithmic_bytes": LB_BYTES_PER_NODE * nodes,
+                     "hbm": {"achieved": round(achieved_gbs, 1), "peak": peaks.get("hbm_gbs"),
+                             "unit": "GB/s", "frac": round(achieved_gbs / peaks.get("hbm_gbs"), 4),
+                             "peak_kind": peak_kind},
+                     "kernel_ms": round(lb_ms, 4)},
+        "stages_ms_per_step": {k: round(v / kst, 4) for k, v in
+                               zip(["S1_poisson", "S2_flux_lb", "S3_advection", "S4_particles",
+                                    "S5_reflag", "total"], stage)},
+        "e2e": {"value": round(e2e_value, 3), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, done, dt = time_oracle(w, 3, budget_s=20.0, warmup=0)
+        line["cpu_baseline"] = {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                "sample": f"{done} steps of the {w['shape'][0]}^3 workload, "
+                                          f"{dt:.1f} s, numpy FP64 oracle, single thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def ctypes_sizeof_particle(ek):
+    import ctypes
+    return ctypes.sizeof(ek.ParticleRec)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -165,6 +165,16 @@ ek_status ek_run_stage(ek_ctx* ctx, int stage);
 ek_status ek_get_particles(ek_ctx* ctx, ek_particle* dst, int count);
 int ek_num_particles(const ek_ctx* ctx);
 
+/* Run nsteps steps like ek_step, recording CUDA events on the context's stream
+ * between the stages, and add the device time of each to stage_ms (caller
+ * owned, 6 doubles): [0] S1 Poisson, [1] S2 fused flux/LB kernel, [2] S3
+ * advection, [3] S4, [4] S5, [5] the whole nsteps steps.  Waits for the work. */
+ek_status ek_step_timed(ek_ctx* ctx, int nsteps, double stage_ms[6]);
+
+/* Number of kernels (and device memsets) the library has enqueued on this
+ * context since it was created. */
+long long ek_kernel_launches(const ek_ctx* ctx);
+
 /* Use the CUDA stream `stream` (a cudaStream_t) for all later work. */
 ek_status ek_set_stream(ek_ctx* ctx, void* stream);
 /* Wait for all enqueued work and check the device status word. */

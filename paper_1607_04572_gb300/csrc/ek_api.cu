@@ -44,6 +44,7 @@ struct ek_ctx {
   int xfer_cap = 0;
   int* status = nullptr;
   int cur = 0;
+  long long launches = 0;  // kernels and memsets enqueued so far
   bool setup_pending = true;
   bool has_qwall = false;
   bool broken = false;
@@ -249,29 +250,38 @@ ek_status run_setup(ek_ctx* ctx) {
   return download_particles(ctx);
 }
 
-ek_status enqueue_stage(ek_ctx* ctx, int stage) {
+// stage 3 (advection) is enqueued separately only by the timed driver; stage 2
+// of ek_run_stage / ek_step runs S2 and S3 and swaps the buffers.
+ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
   cudaStream_t s = ctx->stream;
   switch (stage) {
     case 1:
       EK_CUDA(poisson_solve(ctx->plan, nullptr, ctx->rho[ctx->cur],
                             ctx->has_qwall ? ctx->qwall : nullptr, ctx->qpart, ctx->ph, ctx->phi,
                             ctx->spectrum, s));
+      ctx->launches += 5;
       return EK_OK;
     case 2: {
       LBArgs a = lb_args(ctx);
       EK_CUDA(launch_lb_fused(a, s));
+      if (mid) EK_CUDA(cudaEventRecord(mid, s));
       EK_CUDA(launch_advection(a, s));
+      ctx->launches += ctx->p.nspecies > 0 ? 2 : 1;
       ctx->cur = 1 - ctx->cur;
       return EK_OK;
     }
     case 4: {
       PartArgs a = part_args(ctx);
       EK_CUDA(launch_particle_forces(a, s));
+      ctx->launches += ctx->P > 0 ? 1 : 0;
       return EK_OK;
     }
     case 5: {
       PartArgs a = part_args(ctx);
-      if (ctx->P) EK_CUDA(launch_reflag(a, true, s));
+      if (ctx->P) {
+        EK_CUDA(launch_reflag(a, true, s));
+        ctx->launches += 8;
+      }
       return EK_OK;
     }
     default:
@@ -596,6 +606,45 @@ ek_status ek_step(ek_ctx* ctx, int nsteps) {
   if (st != EK_OK) return st;
   return check_status(ctx);
 }
+
+ek_status ek_step_timed(ek_ctx* ctx, int nsteps, double stage_ms[6]) {
+  ek_status st = ready(ctx);
+  if (st != EK_OK) return st;
+  if (nsteps < 0 || !stage_ms) return fail(ctx, EK_ERR_ARG, "bad arguments");
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) EK_CUDA(cudaEventCreate(&ev[i]));
+  double acc[5] = {0, 0, 0, 0, 0};
+  cudaEvent_t first = nullptr;
+  EK_CUDA(cudaEventCreate(&first));
+  EK_CUDA(cudaEventRecord(first, ctx->stream));
+  for (int t = 0; t < nsteps && st == EK_OK; ++t) {
+    EK_CUDA(cudaEventRecord(ev[0], ctx->stream));
+    st = enqueue_stage(ctx, 1);
+    if (st == EK_OK) { EK_CUDA(cudaEventRecord(ev[1], ctx->stream)); st = enqueue_stage(ctx, 2, ev[2]); }
+    if (st == EK_OK) { EK_CUDA(cudaEventRecord(ev[3], ctx->stream)); st = enqueue_stage(ctx, 4); }
+    if (st == EK_OK) { EK_CUDA(cudaEventRecord(ev[4], ctx->stream)); st = enqueue_stage(ctx, 5); }
+    if (st != EK_OK) break;
+    EK_CUDA(cudaEventRecord(ev[5], ctx->stream));
+    EK_CUDA(cudaEventSynchronize(ev[5]));
+    float ms;
+    for (int i = 0; i < 5; ++i) {
+      EK_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      acc[i] += ms;
+    }
+  }
+  float total = 0.0f;
+  EK_CUDA(cudaEventRecord(ev[5], ctx->stream));
+  EK_CUDA(cudaEventSynchronize(ev[5]));
+  EK_CUDA(cudaEventElapsedTime(&total, first, ev[5]));
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  cudaEventDestroy(first);
+  if (st != EK_OK) return st;
+  for (int i = 0; i < 5; ++i) stage_ms[i] += acc[i];
+  stage_ms[5] += total;
+  return check_status(ctx);
+}
+
+long long ek_kernel_launches(const ek_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 ek_status ek_run_stage(ek_ctx* ctx, int stage) {
   ek_status st = ready(ctx);

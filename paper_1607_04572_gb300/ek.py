@@ -44,7 +44,8 @@ STATUS = {0: "EK_OK", -1: "EK_ERR_ARG", -2: "EK_ERR_NOMEM", -3: "EK_ERR_CUDA",
 EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get_fields",
            "ek_step", "ek_step_async", "ek_run_stage", "ek_get_particles", "ek_num_particles",
            "ek_set_stream", "ek_sync", "ek_last_error", "ek_lattice_dirs",
-           "ek_poisson_scratch_bytes", "ek_poisson_solve"]
+           "ek_poisson_scratch_bytes", "ek_poisson_solve", "ek_step_timed",
+           "ek_kernel_launches"]
 
 
 class EKError(RuntimeError):
@@ -105,9 +106,12 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ek_poisson_scratch_bytes.argtypes = [ip, ip, ip]
     lib.ek_poisson_scratch_bytes.restype = ctypes.c_size_t
     lib.ek_poisson_solve.argtypes = [vp, vp, ip, ip, ip, dp, vp, vp]
+    lib.ek_step_timed.argtypes = [vp, ip, ctypes.POINTER(dp)]
+    lib.ek_kernel_launches.argtypes = [vp]
+    lib.ek_kernel_launches.restype = ctypes.c_longlong
     for name in EXPORTS:
         if name not in ("ek_num_particles", "ek_last_error", "ek_lattice_dirs",
-                        "ek_poisson_scratch_bytes"):
+                        "ek_poisson_scratch_bytes", "ek_kernel_launches"):
             getattr(lib, name).restype = ip
     _lib = lib
     return lib
@@ -226,6 +230,16 @@ class EKSystem:
 
     def step_async(self, n=1):
         self._check(self.lib.ek_step_async(self.ctx, int(n)))
+
+    def step_timed(self, n=1):
+        """Run n steps; returns device ms per stage: S1, S2 (fused LB kernel),
+        S3 (advection), S4, S5, total."""
+        acc = (ctypes.c_double * 6)()
+        self._check(self.lib.ek_step_timed(self.ctx, int(n), acc))
+        return list(acc)
+
+    def kernel_launches(self):
+        return int(self.lib.ek_kernel_launches(self.ctx))
 
     def run_stage(self, stage):
         self._check(self.lib.ek_run_stage(self.ctx, int(stage)))
