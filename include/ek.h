@@ -195,6 +195,29 @@ size_t ek_poisson_scratch_bytes(int nx, int ny, int nz);
 ek_status ek_poisson_solve(const double* q, double* phi, int nx, int ny, int nz,
                            double bjerrum, void* spectrum, void* stream);
 
+/* The same Poisson solve for callers that cannot allocate device memory:
+ * code whose device memory is entirely reserved up front by another runtime's
+ * pool (so a raw cudaMalloc would fail), latency-critical loops that must not
+ * let cudaMalloc/cudaFree synchronise the device, and code under a policy that
+ * forbids allocation after initialisation.  The paper has no counterpart; it
+ * is a service of this library.
+ *
+ * Allocates nothing: the spectrum scratch (at most EK_POISSON_STATIC_MAX
+ * complex doubles, 8 MiB) and the FFT tables live in fixed file-scope device
+ * arrays that every GPU which loads the library holds until the process exits.
+ * The caller passes q and phi (device arrays of nx*ny*nz doubles, may alias).
+ * Returns EK_ERR_ARG when (nx/2 + 1)*ny*nz exceeds EK_POISSON_STATIC_MAX or an
+ * edge is not 2^a 3^b in [8, 1024] (nx even).  The first call on a device
+ * resolves the arrays' device addresses (cudaGetSymbolAddress) and every call
+ * with a new box shape reloads the tables with a blocking cudaMemcpy, so make
+ * the first call for each device and shape before any stream capture.  All
+ * calls share the arrays, which keep the last call's contents (nothing in them
+ * needs to start at zero: the first FFT pass writes the whole spectrum); calls
+ * that overlap on the GPU, on any streams, race and give wrong results. */
+#define EK_POISSON_STATIC_MAX (1u << 19)
+ek_status ek_poisson_solve_static(const double* q, double* phi, int nx, int ny, int nz,
+                                  double bjerrum, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

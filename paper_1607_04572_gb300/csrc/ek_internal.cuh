@@ -103,6 +103,8 @@ __host__ __device__ inline int wrapi(int v, int n) {
 cudaError_t poisson_plan_create(PoissonPlan& p, int nx, int ny, int nz, std::string& err);
 void poisson_plan_destroy(PoissonPlan& p);
 size_t poisson_spectrum_bytes(int nx, int ny, int nz);
+// radix plan of one axis (n = 2^a 3^b); false if n has another factor
+bool poisson_factor(int n, AxisPlan& P);
 // charge assembly fused into the first FFT pass when rho != nullptr; else q is read
 cudaError_t poisson_solve(const PoissonPlan& p, const double* q, const double* rho,
                           const double* qwall, const double* qpart, const Phys& ph,

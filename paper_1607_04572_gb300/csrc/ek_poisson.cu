@@ -287,6 +287,8 @@ cudaError_t axis_create(AxisPlan& P, int n) {
 
 }  // namespace
 
+bool poisson_factor(int n, AxisPlan& P) { return factor(n, P); }
+
 size_t poisson_spectrum_bytes(int nx, int ny, int nz) {
   return (size_t)(nx / 2 + 1) * (size_t)ny * (size_t)nz * sizeof(double2);
 }

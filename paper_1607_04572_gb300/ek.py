@@ -45,7 +45,7 @@ EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get
            "ek_step", "ek_step_async", "ek_run_stage", "ek_get_particles", "ek_num_particles",
            "ek_set_stream", "ek_sync", "ek_last_error", "ek_lattice_dirs",
            "ek_poisson_scratch_bytes", "ek_poisson_solve", "ek_step_timed",
-           "ek_kernel_launches"]
+           "ek_kernel_launches", "ek_poisson_solve_static"]
 
 
 class EKError(RuntimeError):
@@ -107,6 +107,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ek_poisson_scratch_bytes.restype = ctypes.c_size_t
     lib.ek_poisson_solve.argtypes = [vp, vp, ip, ip, ip, dp, vp, vp]
     lib.ek_step_timed.argtypes = [vp, ip, ctypes.POINTER(dp)]
+    lib.ek_poisson_solve_static.argtypes = [vp, vp, ip, ip, ip, dp, vp]
     lib.ek_kernel_launches.argtypes = [vp]
     lib.ek_kernel_launches.restype = ctypes.c_longlong
     for name in EXPORTS:
@@ -284,3 +285,19 @@ def poisson_solve(q, phi, shape, bjerrum, spectrum, stream=None):
                               ctypes.c_void_p(int(h)))
     if st != 0:
         raise EKError(st, "ek_poisson_solve failed")
+
+
+POISSON_STATIC_MAX = 1 << 19  # complex doubles of the fixed scratch of ek_poisson_solve_static
+
+
+def poisson_solve_static(q, phi, shape, bjerrum, stream=None):
+    """Poisson solve that allocates no device memory (see ek_poisson_solve_static
+    in include/ek.h): for callers that cannot call cudaMalloc.  q and phi are
+    float64 device tensors; calls that overlap on the GPU race."""
+    lib = load_library()
+    nx, ny, nz = shape
+    h = 0 if stream is None else getattr(stream, "cuda_stream", stream)
+    st = lib.ek_poisson_solve_static(ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                                     nx, ny, nz, float(bjerrum), ctypes.c_void_p(int(h)))
+    if st != 0:
+        raise EKError(st, "ek_poisson_solve_static failed (box too large for the fixed scratch?)")
