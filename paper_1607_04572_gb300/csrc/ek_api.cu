@@ -39,6 +39,8 @@ struct ek_ctx {
   double* psibox = nullptr;
   int boxmax = 0;
   size_t psibox_cap = 0;  // doubles allocated for psibox
+  double* fpart = nullptr;  // S4 partial sums, P * fchunks * 12
+  int fchunks = 0;
   Transfer* xfer = nullptr;
   int* xfer_count = nullptr;
   int xfer_cap = 0;
@@ -157,8 +159,15 @@ PartArgs part_args(ek_ctx* ctx) {
   a.xfer = ctx->xfer;
   a.xfer_count = ctx->xfer_count;
   a.xfer_cap = ctx->xfer_cap;
+  a.fpart = ctx->fpart;
+  a.fchunks = ctx->fchunks;
   a.status = ctx->status;
   return a;
+}
+
+// constants that follow from E and the species: E . c_i per direction
+void update_derived(Phys& ph) {
+  for (int i = 0; i < Q; ++i) ph.ec[i] = ph.E[0] * HCX[i] + ph.E[1] * HCY[i] + ph.E[2] * HCZ[i];
 }
 
 LBArgs lb_args(ek_ctx* ctx) {
@@ -199,11 +208,16 @@ ek_status run_setup(ek_ctx* ctx) {
   const int boxmax = ctx->P ? edge * edge * edge : 0;
   if (ctx->P && (size_t)ctx->P * boxmax > ctx->psibox_cap) {
     if (ctx->psibox) cudaFree(ctx->psibox);
+    if (ctx->fpart) cudaFree(ctx->fpart);
     ctx->psibox = nullptr;
+    ctx->fpart = nullptr;
     ctx->psibox_cap = 0;
     const size_t cap = (size_t)ctx->Pcap * boxmax;
+    const int fchunks = (boxmax + FORCE_CHUNK - 1) / FORCE_CHUNK;
     EK_CUDA(cudaMalloc(&ctx->psibox, cap * sizeof(double)));
+    EK_CUDA(cudaMalloc(&ctx->fpart, (size_t)ctx->Pcap * fchunks * 12 * sizeof(double)));
     ctx->psibox_cap = cap;
+    ctx->fchunks = fchunks;
   }
   ctx->boxmax = boxmax;
   if (ctx->P) {
@@ -273,7 +287,7 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
     case 4: {
       PartArgs a = part_args(ctx);
       EK_CUDA(launch_particle_forces(a, s));
-      ctx->launches += ctx->P > 0 ? 1 : 0;
+      ctx->launches += ctx->P > 0 ? 2 : 0;
       return EK_OK;
     }
     case 5: {
@@ -346,7 +360,9 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
     ph.D[k] = p->D[k];
     ph.dcoef[k] = p->D[k] / A0;
     ph.hinvD[k] = 0.5 / p->D[k];
+    ph.hz[k] = 0.5 * (double)p->valence[k];
   }
+  update_derived(ph);
   std::string perr;
   if (poisson_plan_create(ctx->plan, g.nx, g.ny, g.nz, perr) != cudaSuccess) {
     delete ctx;
@@ -409,8 +425,8 @@ ek_status ek_destroy(ek_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   void* ptrs[] = {ctx->f[0], ctx->f[1], ctx->rho[0], ctx->rho[1], ctx->phi, ctx->psi, ctx->qpart,
                   ctx->qwall, ctx->u, ctx->tmp, ctx->owner, ctx->owner_prev, ctx->wall,
-                  ctx->spectrum, ctx->dparts, ctx->psibox, ctx->xfer, ctx->xfer_count,
-                  ctx->status};
+                  ctx->spectrum, ctx->dparts, ctx->psibox, ctx->fpart, ctx->xfer,
+                  ctx->xfer_count, ctx->status};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);
@@ -498,6 +514,7 @@ ek_status ek_set_field(ek_ctx* ctx, ek_field which, int component, const double*
         if (which == EK_FIELD_E_EXT) ctx->ph.E[d] = v[d];
         else ctx->ph.g[d] = v[d];
       }
+      update_derived(ctx->ph);
       break;
     }
     case EK_FIELD_WALL:

@@ -67,7 +67,9 @@ struct Phys {
   double z[EK_MAX_SPECIES], D[EK_MAX_SPECIES];
   double dcoef[EK_MAX_SPECIES];  // D_k / A_0 (face links; edge links get 1/sqrt 2 more)
   double hinvD[EK_MAX_SPECIES];  // 1 / (2 D_k), coupling-force weight of a link flux
+  double hz[EK_MAX_SPECIES];     // z_k / 2
   double E[3], g[3];
+  double ec[19];                 // E . c_i per direction
 };
 
 // Transition record: one solute transfer of S5 (target node, amount per species).
@@ -150,8 +152,12 @@ struct PartArgs {
   Transfer* xfer;
   int* xfer_count;
   int xfer_cap;
+  double* fpart;   // per (particle, chunk) partial force/torque sums of S4
+  int fchunks;     // chunks per particle in fpart
   int* status;
 };
+// cells per CTA of the S4 force kernel; fpart holds P * fchunks * 12 doubles
+constexpr int FORCE_CHUNK = 128;
 cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s);  // S4
 cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s);  // S5
 cudaError_t launch_fill(const Grid& g, const Phys& ph, const int* owner, double* f, double* rho,

@@ -70,90 +70,106 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
   b.zp = z == nz - 1 ? 0 : z + 1;
 
   // ---- S2a: diffusive + migrative link fluxes (Eq. 20; Eq. 13 without PV) ----
-  double fx = 0.0, fy = 0.0, fz = 0.0;
-  double div[K > 0 ? K : 1];
+  // Link flux J_k = (D_k / A_0) * s_l * [(a - b) + z_k/2 (a + b) dphi],
+  // s_l = (1 - Psi)(1 - Psi') / |c_l|.  Accumulated per species as
+  // S_k = sum_l s_l [..] (the divergence is D_k/A_0 S_k) and, over species,
+  // G = sum_l c_l sum_k s_l [..]; the coupling force (Eq. 16 with the 1/2 of a
+  // link seen from both ends) is sum_k J_k c / (2 D_k) = G / (2 A_0).
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  double S[K > 0 ? K : 1];
   double r0[K > 0 ? K : 1];
   double om0 = 1.0;
-  if (PV) om0 = 1.0 - fmin(a.psi[n], 1.0);
+  if (PV) om0 = 1.0 - a.psi[n];  // psi is clamped to [0, 1] by S5
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    div[k] = 0.0;
+    S[k] = 0.0;
     r0[k] = a.rho_in[k * N + n];
-    if (PV && om0 != 1.0) r0[k] = r0[k] / om0;
+  }
+  if (PV && om0 != 1.0) {
+    const double inv = 1.0 / om0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r0[k] *= inv;
   }
   if (K > 0) {
     const double phi0 = a.phi[n];
+    const double s_face = om0, s_edge = om0 * 0.70710678118654752;
 #pragma unroll
     for (int d = 1; d < Q; ++d) {
       const long long m = nbr_index(d, x, y, z, b, nx, ny);
       if (a.owner[m] != FLUID) continue;  // no flux into or out of boundary nodes
       double omj = 1.0;
-      if (PV) omj = 1.0 - fmin(a.psi[m], 1.0);
-      const double sc = om0 * omj;
-      const double ec = a.ph.E[0] * CX[d] + a.ph.E[1] * CY[d] + a.ph.E[2] * CZ[d];
-      const double dphi = (phi0 - a.phi[m]) + ec;
-      const double inv_len = (d < 7) ? 1.0 : 0.70710678118654752;
+      if (PV) omj = 1.0 - a.psi[m];
+      const double sl = (d < 7 ? s_face : s_edge) * omj;
+      const double dphi = (phi0 - a.phi[m]) + a.ph.ec[d];
+      double tsum = 0.0;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         double rb = a.rho_in[k * N + m];
         if (PV && omj != 1.0) rb = rb / omj;
-        const double br = (r0[k] - rb) + a.ph.z[k] * (0.5 * (r0[k] + rb)) * dphi;
-        const double J = a.ph.dcoef[k] * inv_len * br * sc;
-        div[k] += J;
-        const double jd = J * a.ph.hinvD[k];  // coupling force, Eq. 16 with the 1/2
-        if (CX[d]) fx += CX[d] * jd;
-        if (CY[d]) fy += CY[d] * jd;
-        if (CZ[d]) fz += CZ[d] * jd;
+        const double br = fma(r0[k] + rb, a.ph.hz[k] * dphi, r0[k] - rb);
+        const double T = br * sl;
+        S[k] += T;
+        tsum += T;
       }
+      if (CX[d]) gx += CX[d] * tsum;
+      if (CY[d]) gy += CY[d] * tsum;
+      if (CZ[d]) gz += CZ[d] * tsum;
     }
   }
 #pragma unroll
-  for (int k = 0; k < K; ++k) a.rho_out[k * N + n] = a.rho_in[k * N + n] - div[k];
+  for (int k = 0; k < K; ++k) a.rho_out[k * N + n] = a.rho_in[k * N + n] - a.ph.dcoef[k] * S[k];
+  constexpr double HALF_INV_A0 = 0.13060193748187072;  // 1 / (2 (1 + 2 sqrt 2))
 
-  // ---- S2b: collision (Eqs. 8-9) ----
+  // ---- S2b: collision (Eqs. 8-9), TRT in pair form ----
+  // With s = f_i + f_ibar, d = f_i - f_ibar and the equilibrium/force parts
+  //   Ep = Delta+_i - lambda_e f^eq+_i,  Em = Delta-_i - lambda_o f^eq-_i,
+  // f*_i    = f_i    + lambda_e s/2 + lambda_o d/2 + Ep + Em,
+  // f*_ibar = f_ibar + lambda_e s/2 - lambda_o d/2 + Ep - Em.
   double f[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) f[i] = a.f_in[i * N + n];
-  double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+  double ps[Q], pd[Q];
+  double rho = f[0], jx = 0.0, jy = 0.0, jz = 0.0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    rho += f[i];
-    if (CX[i]) jx += CX[i] * f[i];
-    if (CY[i]) jy += CY[i] * f[i];
-    if (CZ[i]) jz += CZ[i] * f[i];
+  for (int i = 1; i < Q; i += 2) {
+    ps[i] = f[i] + f[i + 1];
+    pd[i] = f[i] - f[i + 1];
+    rho += ps[i];
+    if (CX[i]) jx += CX[i] * pd[i];
+    if (CY[i]) jy += CY[i] * pd[i];
+    if (CZ[i]) jz += CZ[i] * pd[i];
   }
-  const double Fx = fx + a.ph.g[0], Fy = fy + a.ph.g[1], Fz = fz + a.ph.g[2];
+  const double Fx = gx * HALF_INV_A0 + a.ph.g[0];
+  const double Fy = gy * HALF_INV_A0 + a.ph.g[1];
+  const double Fz = gz * HALF_INV_A0 + a.ph.g[2];
   const double irho = 1.0 / rho;
   const double ux = (jx + 0.5 * Fx) * irho;
   const double uy = (jy + 0.5 * Fy) * irho;
   const double uz = (jz + 0.5 * Fz) * irho;
   const double usq = ux * ux + uy * uy + uz * uz;
   const double uF = ux * Fx + uy * Fy + uz * Fz;
-  const double gg = 2.0 * (1.0 + 0.5 * a.ph.lam_e);  // 2 (1 + lambda_e / 2)
   const double le = a.ph.lam_e, lo = a.ph.lam_o;
+  const double gg = 2.0 + le;  // 2 (1 + lambda_e / 2)
+  // odd part: Em = 3 w c.(F - lambda_o j)
+  const double qx = fma(-lo, jx, Fx), qy = fma(-lo, jy, Fy), qz = fma(-lo, jz, Fz);
+  // even part per weight class: Ep = cu (4.5 w gg cf - 4.5 w rho lambda_e cu)
+  //                                  + w (-1.5 gg uF - lambda_e rho (1 - 1.5 usq))
+  const double base = fma(-1.5 * gg, uF, -le * rho * fma(-1.5, usq, 1.0));
+  const double hle = 0.5 * le, hlo = 0.5 * lo;
   double fs[Q];
-  {
-    const double w = wgt(0);
-    const double eqp = w * rho * (1.0 - 1.5 * usq);
-    fs[0] = f[0] + le * (f[0] - eqp) + w * (-1.5 * gg * uF);
-  }
+  fs[0] = fma(1.0 + le, f[0], wgt(0) * base);
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
-    const int o = i + 1;
     const double w = wgt(i);
     const double cu = CX[i] * ux + CY[i] * uy + CZ[i] * uz;
-    const double cj = CX[i] * jx + CY[i] * jy + CZ[i] * jz;
     const double cf = CX[i] * Fx + CY[i] * Fy + CZ[i] * Fz;
-    const double fp = 0.5 * (f[i] + f[o]);
-    const double fm = 0.5 * (f[i] - f[o]);
-    const double eqp = w * rho * (1.0 + 4.5 * cu * cu - 1.5 * usq);
-    const double eqm = w * 3.0 * cj;
-    const double dp = w * (4.5 * gg * cu * cf - 1.5 * gg * uF);
-    const double dm = w * 3.0 * cf;
-    const double ep = le * (fp - eqp) + dp;
-    const double em = lo * (fm - eqm) + dm;
-    fs[i] = f[i] + ep + em;
-    fs[o] = f[o] + ep - em;
+    const double cq = CX[i] * qx + CY[i] * qy + CZ[i] * qz;
+    const double Ep = w * fma(cu, fma(4.5 * gg, cf, -4.5 * le * rho * cu), base);
+    const double Em = 3.0 * w * cq;
+    const double X = fma(hle, ps[i], Ep);
+    const double Y = fma(hlo, pd[i], Em);
+    fs[i] = f[i] + (X + Y);
+    fs[i + 1] = f[i + 1] + (X - Y);
   }
   if (!isfinite(rho) || !isfinite(usq)) atomicOr(a.status, ST_NONFINITE);
   a.u[n] = ux;

@@ -5,10 +5,10 @@
 // All particle work is box-local: particle p touches only the cells of its
 // box [lo, hi) = [floor(r - R) - 1, floor(r + R) + 2) per axis (unwrapped
 // coordinates, so r_b - r never crosses the periodic seam), or of the union of
-// its previous and current boxes in S5.  Grids are (particle, chunk of 256
-// box cells).  Reductions over a particle (force, torque) run in one CTA in a
-// fixed order, so they are deterministic; sums of Psi are dyadic fractions and
-// exact in any order.
+// its previous and current boxes in S5.  Grids are (particle, chunk of box
+// cells).  Reductions over a particle (force, torque) run in a fixed order
+// (per CTA, then over chunks), so they are deterministic; sums of Psi are
+// dyadic fractions and exact in any order.
 #include <math.h>
 
 #include "ek_internal.cuh"
@@ -17,7 +17,8 @@ namespace ek {
 
 namespace {
 
-constexpr int PT = 256;  // threads per particle CTA
+constexpr int PT = 256;      // threads per particle CTA
+constexpr int CLAIM_T = 64;  // threads per CTA of the octree (Psi) kernel
 
 __device__ __forceinline__ int box_cells(const int lo[3], const int hi[3]) {
   return (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
@@ -66,20 +67,50 @@ __device__ __forceinline__ int classify(double cx, double cy, double cz, double 
 
 constexpr int PSI_DEPTH = 4;
 
+// Single-precision pre-test of classify().  (ox, oy, oz) is the cube centre
+// relative to the sphere centre, rounded to float and accumulated over at most
+// 4 levels of dyadic offsets (absolute error per component below
+// 6 * 2^-24 (R + 2)); the float squared distances of the farthest corner and
+// of the closest point are then within 3e-6 (R + 2)^2 of the exact ones, so
+// whenever they are more than `margin` = 4e-5 (R + 2)^2 away from R^2 the FP64
+// decision is already known.  Returns -1 when the exact test is needed.
+__device__ __forceinline__ int classify_f32(float ox, float oy, float oz, float h, float R2,
+                                            float margin) {
+  const float ax = fabsf(ox), ay = fabsf(oy), az = fabsf(oz);
+  const float fx = ax + h, fy = ay + h, fz = az + h;
+  const float dfar = fx * fx + fy * fy + fz * fz;
+  if (dfar < R2 - margin) return CUBE_IN;
+  const bool not_in = dfar > R2 + margin;
+  const float px = fmaxf(ax - h, 0.0f), py = fmaxf(ay - h, 0.0f), pz = fmaxf(az - h, 0.0f);
+  const float dnear = px * px + py * py + pz * pz;
+  if (not_in) {
+    if (dnear > R2 + margin) return CUBE_OUT;
+    if (dnear < R2 - margin) return CUBE_UNDECIDED;
+  }
+  return -1;
+}
+
 // Volume fraction of the unit cell centred at (X, Y, Z) inside the sphere
 // (Sec. III.D.2): the cell is split into 8 sub-cells, each classified as
 // inside or outside; undecided ones are split again, down to depth 4 (edge
 // 1/16), where an undecided cube counts half.  Depth-first with an explicit
-// stack of child counters.
+// stack of child counters.  Every decision equals that of the FP64 classify():
+// the float pre-test only answers where the FP64 answer is certain, and the
+// FP64 test sees the exact (dyadic) cube centre.
 __device__ double psi_cell(double X, double Y, double Z, const double r[3], double R2) {
-  const int s0 = classify(X, Y, Z, 0.5, r, R2);
+  const float R2f = (float)R2;
+  const float Rp2 = sqrtf(R2f) + 2.0f;
+  const float margin = 4e-5f * Rp2 * Rp2;
+  const float ox0 = (float)(X - r[0]), oy0 = (float)(Y - r[1]), oz0 = (float)(Z - r[2]);
+  int s0 = classify_f32(ox0, oy0, oz0, 0.5f, R2f, margin);
+  if (s0 < 0) s0 = classify(X, Y, Z, 0.5, r, R2);
   if (s0 == CUBE_IN) return 1.0;
   if (s0 == CUBE_OUT) return 0.0;
-  double bx[PSI_DEPTH + 1], by[PSI_DEPTH + 1], bz[PSI_DEPTH + 1];
+  float fx[PSI_DEPTH + 1], fy[PSI_DEPTH + 1], fz[PSI_DEPTH + 1];
   int child[PSI_DEPTH + 1];
-  bx[0] = X;
-  by[0] = Y;
-  bz[0] = Z;
+  fx[0] = ox0;
+  fy[0] = oy0;
+  fz[0] = oz0;
   int l = 1;
   child[1] = 0;
   double total = 0.0;
@@ -89,25 +120,36 @@ __device__ double psi_cell(double X, double Y, double Z, const double r[3], doub
       if (l >= 1) ++child[l];
       continue;
     }
-    const double h = ldexp(1.0, -(l + 1));   // half-width at level l
-    const double vol = ldexp(1.0, -3 * l);   // volume at level l
+    const float h = ldexpf(1.0f, -(l + 1));  // half-width at level l
     const int c = child[l];
-    const double cx = bx[l - 1] + ((c & 1) ? h : -h);
-    const double cy = by[l - 1] + ((c & 2) ? h : -h);
-    const double cz = bz[l - 1] + ((c & 4) ? h : -h);
-    const int s = classify(cx, cy, cz, h, r, R2);
+    const float cx = fx[l - 1] + ((c & 1) ? h : -h);
+    const float cy = fy[l - 1] + ((c & 2) ? h : -h);
+    const float cz = fz[l - 1] + ((c & 4) ? h : -h);
+    int s = classify_f32(cx, cy, cz, h, R2f, margin);
+    if (s < 0) {
+      // exact centre: the cell centre plus the dyadic offsets of the path
+      double ex = X, ey = Y, ez = Z;
+      for (int m = 1; m <= l; ++m) {
+        const double hm = ldexp(1.0, -(m + 1));
+        const int cm = child[m];
+        ex += (cm & 1) ? hm : -hm;
+        ey += (cm & 2) ? hm : -hm;
+        ez += (cm & 4) ? hm : -hm;
+      }
+      s = classify(ex, ey, ez, ldexp(1.0, -(l + 1)), r, R2);
+    }
     if (s == CUBE_IN) {
-      total += vol;
+      total += ldexp(1.0, -3 * l);
       ++child[l];
     } else if (s == CUBE_OUT) {
       ++child[l];
     } else if (l == PSI_DEPTH) {
-      total += 0.5 * vol;
+      total += ldexp(0.5, -3 * l);
       ++child[l];
     } else {
-      bx[l] = cx;
-      by[l] = cy;
-      bz[l] = cz;
+      fx[l] = cx;
+      fy[l] = cy;
+      fz[l] = cz;
       ++l;
       child[l] = 0;
     }
@@ -125,6 +167,7 @@ template <int NV>
 __device__ void block_sum(double (&v)[NV]) {
   __shared__ double red[PT / 32][NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     double s = v[j];
@@ -136,21 +179,26 @@ __device__ void block_sum(double (&v)[NV]) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
       double s = 0.0;
-      for (int w = 0; w < PT / 32; ++w) s += red[w][j];
+      for (int w = 0; w < nwarps; ++w) s += red[w][j];
       v[j] = s;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// S4: forces and integration, one CTA per particle
+// S4: forces and integration.  k_particle_forces: grid (particle, chunk of
+// FORCE_CHUNK box cells), one partial sum per CTA; k_particle_integrate: one
+// thread per particle adds the partial sums in chunk order (deterministic)
+// and integrates.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(PT) k_particle_forces(PartArgs a) {
+__global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
   const int p = blockIdx.x;
-  DevParticle& P = a.parts[p];
+  const DevParticle& P = a.parts[p];
   const Grid g = a.g;
   const long long N = g.N;
   const int ncell = box_cells(P.lo, P.hi);
+  const int c = blockIdx.y * FORCE_CHUNK + threadIdx.x;
+  if (blockIdx.y * FORCE_CHUNK >= ncell) return;  // whole CTA beyond the box
   const bool pv = a.ph.pv != 0;
   double qnorm = 0.0;
   if (pv) {
@@ -164,7 +212,7 @@ __global__ void __launch_bounds__(PT) k_particle_forces(PartArgs a) {
   double acc[12];
 #pragma unroll
   for (int j = 0; j < 12; ++j) acc[j] = 0.0;
-  for (int c = threadIdx.x; c < ncell; c += PT) {
+  if (c < ncell) {
     int X, Y, Z;
     box_coord(c, P.lo, P.hi, X, Y, Z);
     const long long n = node_of(X, Y, Z, g);
@@ -217,26 +265,41 @@ __global__ void __launch_bounds__(PT) k_particle_forces(PartArgs a) {
   }
   block_sum<12>(acc);
   if (threadIdx.x == 0) {
-    double F[3], T[3];
-    for (int d = 0; d < 3; ++d) {
-      F[d] = acc[d] + acc[6 + d] + P.ftrans[d];
-      T[d] = acc[3 + d] + acc[9 + d];
-      P.force[d] = F[d];
-      P.torque[d] = T[d];
-      P.ftrans[d] = 0.0;
-    }
-    if (!P.fixed) {
-      const int nn[3] = {g.nx, g.ny, g.nz};
-      for (int d = 0; d < 3; ++d) {
-        P.vel[d] = P.vel[d] + F[d] / P.mass;
-        P.omega[d] = P.omega[d] + T[d] / P.inertia;
-        P.pos[d] = P.pos[d] + P.vel[d];
-        if (P.pos[d] >= (double)nn[d]) P.pos[d] -= (double)nn[d];
-        else if (P.pos[d] < 0.0) P.pos[d] += (double)nn[d];
-      }
-      if (!isfinite(P.pos[0] + P.pos[1] + P.pos[2])) atomicOr(a.status, ST_NONFINITE);
-    }
+    double* out = a.fpart + ((long long)p * a.fchunks + blockIdx.y) * 12;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) out[j] = acc[j];
   }
+}
+
+__global__ void k_particle_integrate(PartArgs a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.P) return;
+  DevParticle& P = a.parts[p];
+  const int nchunk = (box_cells(P.lo, P.hi) + FORCE_CHUNK - 1) / FORCE_CHUNK;
+  double acc[12];
+  for (int j = 0; j < 12; ++j) acc[j] = 0.0;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const double* v = a.fpart + ((long long)p * a.fchunks + ch) * 12;
+    for (int j = 0; j < 12; ++j) acc[j] += v[j];
+  }
+  double F[3], T[3];
+  for (int d = 0; d < 3; ++d) {
+    F[d] = acc[d] + acc[6 + d] + P.ftrans[d];
+    T[d] = acc[3 + d] + acc[9 + d];
+    P.force[d] = F[d];
+    P.torque[d] = T[d];
+    P.ftrans[d] = 0.0;
+  }
+  if (P.fixed) return;
+  const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
+  for (int d = 0; d < 3; ++d) {
+    P.vel[d] = P.vel[d] + F[d] / P.mass;
+    P.omega[d] = P.omega[d] + T[d] / P.inertia;
+    P.pos[d] = P.pos[d] + P.vel[d];
+    if (P.pos[d] >= (double)nn[d]) P.pos[d] -= (double)nn[d];
+    else if (P.pos[d] < 0.0) P.pos[d] += (double)nn[d];
+  }
+  if (!isfinite(P.pos[0] + P.pos[1] + P.pos[2])) atomicOr(a.status, ST_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------
@@ -327,6 +390,9 @@ __global__ void k_charge_scatter(PartArgs a) {
   int X, Y, Z;
   box_coord(c, P.lo, P.hi, X, Y, Z);
   const long long n = node_of(X, Y, Z, a.g);
+  // all Psi_p have been added (k_claim): clamp the sum to 1 once, so readers
+  // of psi need no min (idempotent where boxes overlap)
+  if (a.psi[n] > 1.0) a.psi[n] = 1.0;
   double q = 0.0;
   if (a.ph.pv) {
     const double ps = a.psibox[(long long)p * a.boxmax + c];
@@ -479,7 +545,8 @@ __global__ void k_apply_transfers(PartArgs a) {
 
 cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s) {
   if (a.P == 0) return cudaSuccess;
-  k_particle_forces<<<a.P, PT, 0, s>>>(a);
+  k_particle_forces<<<dim3(a.P, a.fchunks), FORCE_CHUNK, 0, s>>>(a);
+  k_particle_integrate<<<(a.P + 127) / 128, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -494,11 +561,13 @@ cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s) {
   const int edge = (int)round(cbrt((double)a.boxmax)) + 1;
   const unsigned uchunks = (unsigned)((edge * edge * edge + PT - 1) / PT);
   const unsigned bchunks = (unsigned)((a.boxmax + PT - 1) / PT);
+  // Psi needs an octree per surface cell: small CTAs spread it over more SMs
+  const unsigned cchunks = (unsigned)((a.boxmax + CLAIM_T - 1) / CLAIM_T);
   if (transitions) {
     k_save_prev<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
     k_clear<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
   }
-  k_claim<<<dim3(a.P, bchunks), PT, 0, s>>>(a);
+  k_claim<<<dim3(a.P, cchunks), CLAIM_T, 0, s>>>(a);
   k_charge_scatter<<<dim3(a.P, bchunks), PT, 0, s>>>(a);
   if (transitions) {
     k_transitions<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
