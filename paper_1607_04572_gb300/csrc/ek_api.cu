@@ -41,6 +41,8 @@ struct ek_ctx {
   size_t psibox_cap = 0;  // doubles allocated for psibox
   double* fpart = nullptr;  // S4 partial sums, P * fchunks * 12
   int fchunks = 0;
+  int2* surf = nullptr;     // surface-cell list of S5, P * boxmax entries
+  int* surf_count = nullptr;
   Transfer* xfer = nullptr;
   int* xfer_count = nullptr;
   int xfer_cap = 0;
@@ -75,7 +77,7 @@ __global__ void k_set_velocity(Grid g, const int* owner, double* f, const double
   const double ux = u[n], uy = u[g.N + n], uz = u[2 * g.N + n];
   const double usq = ux * ux + uy * uy + uz * uz;
   for (int i = 0; i < Q; ++i) {
-    const double cu = CX[i] * ux + CY[i] * uy + CZ[i] * uz;
+    const double cu = cdot(i, ux, uy, uz);
     f[i * g.N + n] = wgt(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
   }
 }
@@ -161,6 +163,9 @@ PartArgs part_args(ek_ctx* ctx) {
   a.xfer_cap = ctx->xfer_cap;
   a.fpart = ctx->fpart;
   a.fchunks = ctx->fchunks;
+  a.surf = ctx->surf;
+  a.surf_count = ctx->surf_count;
+  a.surf_cap = (int)std::min<size_t>(ctx->psibox_cap, (size_t)1 << 30);
   a.status = ctx->status;
   return a;
 }
@@ -209,13 +214,16 @@ ek_status run_setup(ek_ctx* ctx) {
   if (ctx->P && (size_t)ctx->P * boxmax > ctx->psibox_cap) {
     if (ctx->psibox) cudaFree(ctx->psibox);
     if (ctx->fpart) cudaFree(ctx->fpart);
+    if (ctx->surf) cudaFree(ctx->surf);
     ctx->psibox = nullptr;
     ctx->fpart = nullptr;
+    ctx->surf = nullptr;
     ctx->psibox_cap = 0;
     const size_t cap = (size_t)ctx->Pcap * boxmax;
     const int fchunks = (boxmax + FORCE_CHUNK - 1) / FORCE_CHUNK;
     EK_CUDA(cudaMalloc(&ctx->psibox, cap * sizeof(double)));
     EK_CUDA(cudaMalloc(&ctx->fpart, (size_t)ctx->Pcap * fchunks * 12 * sizeof(double)));
+    EK_CUDA(cudaMalloc(&ctx->surf, cap * sizeof(int2)));
     ctx->psibox_cap = cap;
     ctx->fchunks = fchunks;
   }
@@ -294,7 +302,7 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
       PartArgs a = part_args(ctx);
       if (ctx->P) {
         EK_CUDA(launch_reflag(a, true, s));
-        ctx->launches += 8;
+        ctx->launches += 10;
       }
       return EK_OK;
     }
@@ -391,6 +399,7 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   ctx->xfer_cap = (int)std::min<long long>(19LL * g.N, 1LL << 22);
   alloc((void**)&ctx->xfer, (size_t)ctx->xfer_cap * sizeof(Transfer));
   alloc((void**)&ctx->xfer_count, sizeof(int));
+  alloc((void**)&ctx->surf_count, sizeof(int));
   alloc((void**)&ctx->status, sizeof(int));
   if (!ok) {
     ek_destroy(ctx);
@@ -425,8 +434,8 @@ ek_status ek_destroy(ek_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   void* ptrs[] = {ctx->f[0], ctx->f[1], ctx->rho[0], ctx->rho[1], ctx->phi, ctx->psi, ctx->qpart,
                   ctx->qwall, ctx->u, ctx->tmp, ctx->owner, ctx->owner_prev, ctx->wall,
-                  ctx->spectrum, ctx->dparts, ctx->psibox, ctx->fpart, ctx->xfer,
-                  ctx->xfer_count, ctx->status};
+                  ctx->spectrum, ctx->dparts, ctx->psibox, ctx->fpart, ctx->surf, ctx->xfer,
+                  ctx->xfer_count, ctx->surf_count, ctx->status};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);

@@ -16,9 +16,34 @@ namespace ek {
 // D3Q19 (Sec. III.A): rest, 6 faces, 12 edges; opposite pairs (i, i+1) for odd i.
 // ---------------------------------------------------------------------------
 constexpr int Q = 19;
-constexpr __device__ int CX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-constexpr __device__ int CY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-constexpr __device__ int CZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+// Components as compile-time functions: in unrolled loops every c_i folds
+// into an add, a subtract or nothing (no table load, no multiply by +-1).
+__host__ __device__ constexpr int dcx(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int dcy(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int dcz(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+// +v or -v by the sign of a (nonzero) component
+__host__ __device__ __forceinline__ double csgn(int c, double v) { return c > 0 ? v : -v; }
+// c_i . v with neither multiplications nor additions of zero: an edge is one
+// add, a face a signed copy (after unrolling i is a constant)
+__host__ __device__ __forceinline__ double cdot(int i, double x, double y, double z) {
+  const int a = dcx(i), b = dcy(i), c = dcz(i);
+  if (a && b) return csgn(a, x) + csgn(b, y);
+  if (a && c) return csgn(a, x) + csgn(c, z);
+  if (b && c) return csgn(b, y) + csgn(c, z);
+  if (a) return csgn(a, x);
+  if (b) return csgn(b, y);
+  if (c) return csgn(c, z);
+  return 0.0;
+}
 constexpr int HCX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
 constexpr int HCY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
 constexpr int HCZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
@@ -154,6 +179,9 @@ struct PartArgs {
   int xfer_cap;
   double* fpart;   // per (particle, chunk) partial force/torque sums of S4
   int fchunks;     // chunks per particle in fpart
+  int2* surf;      // (particle, box cell) of the cells cut by a sphere surface
+  int* surf_count;
+  int surf_cap;
   int* status;
 };
 // cells per CTA of the S4 force kernel; fpart holds P * fchunks * 12 doubles

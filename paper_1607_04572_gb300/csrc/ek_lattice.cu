@@ -21,9 +21,9 @@ struct Nbr {
 
 __device__ __forceinline__ long long nbr_index(int d, int x, int y, int z, const Nbr& b,
                                                int nx, int ny) {
-  const int X = CX[d] > 0 ? b.xp : (CX[d] < 0 ? b.xm : x);
-  const int Y = CY[d] > 0 ? b.yp : (CY[d] < 0 ? b.ym : y);
-  const int Z = CZ[d] > 0 ? b.zp : (CZ[d] < 0 ? b.zm : z);
+  const int X = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
+  const int Y = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
+  const int Z = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
   return (long long)X + (long long)nx * ((long long)Y + (long long)ny * Z);
 }
 
@@ -111,9 +111,9 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
         S[k] += T;
         tsum += T;
       }
-      if (CX[d]) gx += CX[d] * tsum;
-      if (CY[d]) gy += CY[d] * tsum;
-      if (CZ[d]) gz += CZ[d] * tsum;
+      if (dcx(d)) gx += csgn(dcx(d), tsum);
+      if (dcy(d)) gy += csgn(dcy(d), tsum);
+      if (dcz(d)) gz += csgn(dcz(d), tsum);
     }
   }
 #pragma unroll
@@ -135,9 +135,9 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
     ps[i] = f[i] + f[i + 1];
     pd[i] = f[i] - f[i + 1];
     rho += ps[i];
-    if (CX[i]) jx += CX[i] * pd[i];
-    if (CY[i]) jy += CY[i] * pd[i];
-    if (CZ[i]) jz += CZ[i] * pd[i];
+    if (dcx(i)) jx += csgn(dcx(i), pd[i]);
+    if (dcy(i)) jy += csgn(dcy(i), pd[i]);
+    if (dcz(i)) jz += csgn(dcz(i), pd[i]);
   }
   const double Fx = gx * HALF_INV_A0 + a.ph.g[0];
   const double Fy = gy * HALF_INV_A0 + a.ph.g[1];
@@ -161,9 +161,9 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     const double w = wgt(i);
-    const double cu = CX[i] * ux + CY[i] * uy + CZ[i] * uz;
-    const double cf = CX[i] * Fx + CY[i] * Fy + CZ[i] * Fz;
-    const double cq = CX[i] * qx + CY[i] * qy + CZ[i] * qz;
+    const double cu = cdot(i, ux, uy, uz);
+    const double cf = cdot(i, Fx, Fy, Fz);
+    const double cq = cdot(i, qx, qy, qz);
     const double Ep = w * fma(cu, fma(4.5 * gg, cf, -4.5 * le * rho * cu), base);
     const double Em = 3.0 * w * cq;
     const double X = fma(hle, ps[i], Ep);
@@ -187,21 +187,34 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
     } else {
       double cvb = 0.0;
       if (om >= 0) {
-        const int xb = CX[i] > 0 ? b.xp : (CX[i] < 0 ? b.xm : x);
-        const int yb = CY[i] > 0 ? b.yp : (CY[i] < 0 ? b.ym : y);
-        const int zb = CZ[i] > 0 ? b.zp : (CZ[i] < 0 ? b.zm : z);
+        const int xb = dcx(i) > 0 ? b.xp : (dcx(i) < 0 ? b.xm : x);
+        const int yb = dcy(i) > 0 ? b.yp : (dcy(i) < 0 ? b.ym : y);
+        const int zb = dcz(i) > 0 ? b.zp : (dcz(i) < 0 ? b.zm : z);
         double vb[3];
         boundary_velocity(a.parts[om], xb, yb, zb, a.g, vb);
-        cvb = CX[i] * vb[0] + CY[i] * vb[1] + CZ[i] * vb[2];
+        cvb = cdot(i, vb[0], vb[1], vb[2]);
       }
       a.f_out[opp(i) * N + n] = fs[i] - 6.0 * wgt(i) * a.ph.rho0 * cvb;
     }
   }
 }
 
+// sign (-1, 0, +1) and magnitude of a double from its bits: integer work
+// only, so the advection's tests cost no FP64 instructions (-0 counts as 0)
+__device__ __forceinline__ int sgn_bits(double v) {
+  const long long b = __double_as_longlong(v);
+  if ((b << 1) == 0) return 0;
+  return b < 0 ? -1 : 1;
+}
+__device__ __forceinline__ double abs_bits(double v) {
+  return __longlong_as_double(__double_as_longlong(v) & 0x7fffffffffffffffLL);
+}
+
 // S3: rho' = (rho - div J) + volume-of-fluid advection.  rho_out holds
 // rho - div J (written by S2) and is updated in place; rho_in is the species
-// field at the start of the step (the advected one).
+// field at the start of the step (the advected one).  The cell displaced by
+// u overlaps the neighbours at offsets s with s_a in {0, sign(u_a)}; the share
+// of offset s is prod_a w_a, w_a = 1 - |u_a| (s_a = 0) or |u_a|.
 template <int K>
 __global__ void __launch_bounds__(256) k_advect(LBArgs a) {
   const long long N = a.g.N;
@@ -220,28 +233,28 @@ __global__ void __launch_bounds__(256) k_advect(LBArgs a) {
     acc[k] = a.rho_out[k * N + n];
     rs[k] = a.rho_in[k * N + n];
   }
-  // outflow of this cell: offsets s with s_a in {0, sign(u_a)}
+  // outflow of this cell
   const double ux = a.u[n], uy = a.u[N + n], uz = a.u[2 * N + n];
-  const int sx = ux > 0.0 ? 1 : (ux < 0.0 ? -1 : 0);
-  const int sy = uy > 0.0 ? 1 : (uy < 0.0 ? -1 : 0);
-  const int sz = uz > 0.0 ? 1 : (uz < 0.0 ? -1 : 0);
-  const double ax = fabs(ux), ay = fabs(uy), az = fabs(uz);
+  const int sx = sgn_bits(ux), sy = sgn_bits(uy), sz = sgn_bits(uz);
+  const double ax = abs_bits(ux), ay = abs_bits(uy), az = abs_bits(uz);
+  const double bx = 1.0 - ax, by = 1.0 - ay, bz = 1.0 - az;
   for (int oz = 0; oz <= (sz != 0); ++oz) {
     for (int oy = 0; oy <= (sy != 0); ++oy) {
       for (int ox = 0; ox <= (sx != 0); ++ox) {
         if (!ox && !oy && !oz) continue;
-        const double frac = (ox ? ax : 1.0 - ax) * (oy ? ay : 1.0 - ay) * (oz ? az : 1.0 - az);
-        const int X = wrapi(x + (ox ? sx : 0), nx);
-        const int Y = wrapi(y + (oy ? sy : 0), ny);
-        const int Z = wrapi(z + (oz ? sz : 0), nz);
+        const int X = ox ? wrapi(x + sx, nx) : x;
+        const int Y = oy ? wrapi(y + sy, ny) : y;
+        const int Z = oz ? wrapi(z + sz, nz) : z;
         const long long m = X + (long long)nx * (Y + (long long)ny * Z);
         if (a.owner[m] != FLUID) continue;  // share aimed at a boundary stays here
+        const double frac = (ox ? ax : bx) * (oy ? ay : by) * (oz ? az : bz);
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] -= rs[k] * frac;
       }
     }
   }
-  // inflow from the 26 neighbours y = x - s
+  // inflow from the 26 neighbours y = x - s: only those whose velocity points
+  // here along every nonzero component of s contribute
   for (int qz = -1; qz <= 1; ++qz) {
     for (int qy = -1; qy <= 1; ++qy) {
       for (int qx = -1; qx <= 1; ++qx) {
@@ -252,16 +265,11 @@ __global__ void __launch_bounds__(256) k_advect(LBArgs a) {
         const long long m = X + (long long)nx * (Y + (long long)ny * Z);
         if (a.owner[m] != FLUID) continue;
         const double vx = a.u[m], vy = a.u[N + m], vz = a.u[2 * N + m];
-        double wx, wy, wz;
-        if (qx == 0) wx = 1.0 - fabs(vx);
-        else if ((vx > 0.0 && qx > 0) || (vx < 0.0 && qx < 0)) wx = fabs(vx);
-        else continue;
-        if (qy == 0) wy = 1.0 - fabs(vy);
-        else if ((vy > 0.0 && qy > 0) || (vy < 0.0 && qy < 0)) wy = fabs(vy);
-        else continue;
-        if (qz == 0) wz = 1.0 - fabs(vz);
-        else if ((vz > 0.0 && qz > 0) || (vz < 0.0 && qz < 0)) wz = fabs(vz);
-        else continue;
+        if ((qx && sgn_bits(vx) != qx) || (qy && sgn_bits(vy) != qy) || (qz && sgn_bits(vz) != qz))
+          continue;
+        const double wx = qx ? abs_bits(vx) : 1.0 - abs_bits(vx);
+        const double wy = qy ? abs_bits(vy) : 1.0 - abs_bits(vy);
+        const double wz = qz ? abs_bits(vz) : 1.0 - abs_bits(vz);
         const double frac = wx * wy * wz;
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] += a.rho_in[k * N + m] * frac;

@@ -17,8 +17,7 @@ namespace ek {
 
 namespace {
 
-constexpr int PT = 256;      // threads per particle CTA
-constexpr int CLAIM_T = 64;  // threads per CTA of the octree (Psi) kernel
+constexpr int PT = 256;  // threads per particle CTA
 
 __device__ __forceinline__ int box_cells(const int lo[3], const int hi[3]) {
   return (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
@@ -90,71 +89,50 @@ __device__ __forceinline__ int classify_f32(float ox, float oy, float oz, float 
   return -1;
 }
 
-// Volume fraction of the unit cell centred at (X, Y, Z) inside the sphere
-// (Sec. III.D.2): the cell is split into 8 sub-cells, each classified as
-// inside or outside; undecided ones are split again, down to depth 4 (edge
-// 1/16), where an undecided cube counts half.  Depth-first with an explicit
-// stack of child counters.  Every decision equals that of the FP64 classify():
-// the float pre-test only answers where the FP64 answer is certain, and the
-// FP64 test sees the exact (dyadic) cube centre.
-__device__ double psi_cell(double X, double Y, double Z, const double r[3], double R2) {
-  const float R2f = (float)R2;
-  const float Rp2 = sqrtf(R2f) + 2.0f;
-  const float margin = 4e-5f * Rp2 * Rp2;
-  const float ox0 = (float)(X - r[0]), oy0 = (float)(Y - r[1]), oz0 = (float)(Z - r[2]);
-  int s0 = classify_f32(ox0, oy0, oz0, 0.5f, R2f, margin);
-  if (s0 < 0) s0 = classify(X, Y, Z, 0.5, r, R2);
-  if (s0 == CUBE_IN) return 1.0;
-  if (s0 == CUBE_OUT) return 0.0;
-  float fx[PSI_DEPTH + 1], fy[PSI_DEPTH + 1], fz[PSI_DEPTH + 1];
-  int child[PSI_DEPTH + 1];
-  fx[0] = ox0;
-  fy[0] = oy0;
-  fz[0] = oz0;
-  int l = 1;
-  child[1] = 0;
-  double total = 0.0;
-  while (l >= 1) {
-    if (child[l] == 8) {
-      --l;
-      if (l >= 1) ++child[l];
-      continue;
-    }
-    const float h = ldexpf(1.0f, -(l + 1));  // half-width at level l
-    const int c = child[l];
-    const float cx = fx[l - 1] + ((c & 1) ? h : -h);
-    const float cy = fy[l - 1] + ((c & 2) ? h : -h);
-    const float cz = fz[l - 1] + ((c & 4) ? h : -h);
-    int s = classify_f32(cx, cy, cz, h, R2f, margin);
-    if (s < 0) {
-      // exact centre: the cell centre plus the dyadic offsets of the path
-      double ex = X, ey = Y, ez = Z;
-      for (int m = 1; m <= l; ++m) {
-        const double hm = ldexp(1.0, -(m + 1));
-        const int cm = child[m];
-        ex += (cm & 1) ? hm : -hm;
-        ey += (cm & 2) ? hm : -hm;
-        ez += (cm & 4) ? hm : -hm;
-      }
-      s = classify(ex, ey, ez, ldexp(1.0, -(l + 1)), r, R2);
-    }
-    if (s == CUBE_IN) {
-      total += ldexp(1.0, -3 * l);
-      ++child[l];
-    } else if (s == CUBE_OUT) {
-      ++child[l];
-    } else if (l == PSI_DEPTH) {
-      total += ldexp(0.5, -3 * l);
-      ++child[l];
-    } else {
-      fx[l] = cx;
-      fy[l] = cy;
-      fz[l] = cz;
-      ++l;
-      child[l] = 0;
-    }
+// Octree partial volume Psi_p of one cell (Sec. III.D.2): the cell is split
+// into 8 sub-cells, each classified as completely inside or completely
+// outside; undecided ones are split again, down to depth 4 (edge 1/16), where
+// an undecided cube counts half.  Level 0 (the cell itself) is decided by
+// k_claim; cells still undecided there go to k_psi_surface, where one warp
+// walks the levels breadth first: the 8^l sub-cubes of a level are spread over
+// the lanes, and the undecided ones are compacted (ballot) into the next
+// level's list.  Volumes are counted in units of 1/8192 (half a level-4
+// cube), so the sum is an exact integer in any order.
+constexpr int PSI_UNITS = 8192;
+
+// relative (float) and exact (double) centre of sub-cube `path` at level l of
+// the cell centred at (X, Y, Z); path holds 3 bits per level, level 1 highest
+__device__ __forceinline__ void subcube_centre_f(int path, int l, float ox, float oy, float oz,
+                                                 float& cx, float& cy, float& cz) {
+  cx = ox;
+  cy = oy;
+  cz = oz;
+  for (int m = 1; m <= l; ++m) {
+    const int bits = (path >> (3 * (l - m))) & 7;
+    const float hm = ldexpf(1.0f, -(m + 1));
+    cx += (bits & 1) ? hm : -hm;
+    cy += (bits & 2) ? hm : -hm;
+    cz += (bits & 4) ? hm : -hm;
   }
-  return total;
+}
+
+__device__ __forceinline__ void subcube_centre_d(int path, int l, double X, double Y, double Z,
+                                                 double& cx, double& cy, double& cz) {
+  cx = X;
+  cy = Y;
+  cz = Z;
+  for (int m = 1; m <= l; ++m) {
+    const int bits = (path >> (3 * (l - m))) & 7;
+    const double hm = ldexp(1.0, -(m + 1));
+    cx += (bits & 1) ? hm : -hm;
+    cy += (bits & 2) ? hm : -hm;
+    cz += (bits & 4) ? hm : -hm;
+  }
+}
+
+__device__ __forceinline__ float psi_margin(double R2) {
+  const float Rp2 = sqrtf((float)R2) + 2.0f;
+  return 4e-5f * Rp2 * Rp2;
 }
 
 __device__ __forceinline__ bool node_inside(int X, int Y, int Z, const DevParticle& P) {
@@ -221,19 +199,21 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
       // momentum exchange on every link from this fluid node into the particle (Eq. 11)
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
-        const long long m = node_of(X + CX[i], Y + CY[i], Z + CZ[i], g);
+        const long long m = node_of(X + dcx(i), Y + dcy(i), Z + dcz(i), g);
         if (a.owner[m] != p) continue;
-        const double dx = (double)(X + CX[i]) - P.pos[0];
-        const double dy = (double)(Y + CY[i]) - P.pos[1];
-        const double dz = (double)(Z + CZ[i]) - P.pos[2];
+        const double dx = (double)(X + dcx(i)) - P.pos[0];
+        const double dy = (double)(Y + dcy(i)) - P.pos[1];
+        const double dz = (double)(Z + dcz(i)) - P.pos[2];
         const double vbx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
         const double vby = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
         const double vbz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
-        const double cvb = CX[i] * vbx + CY[i] * vby + CZ[i] * vbz;
+        const double cvb = cdot(i, vbx, vby, vbz);
         const double refl = a.f[(long long)opp(i) * N + n];
         const double fs = refl + 6.0 * wgt(i) * a.ph.rho0 * cvb;  // the population that hit the wall
         const double mom = fs + refl;
-        const double px = CX[i] * mom, py = CY[i] * mom, pz = CZ[i] * mom;
+        const double px = dcx(i) ? csgn(dcx(i), mom) : 0.0;
+        const double py = dcy(i) ? csgn(dcy(i), mom) : 0.0;
+        const double pz = dcz(i) ? csgn(dcz(i), mom) : 0.0;
         acc[0] += px;
         acc[1] += py;
         acc[2] += pz;
@@ -351,7 +331,9 @@ __global__ void k_reset_all(PartArgs a) {
   a.qpart[n] = 0.0;
 }
 
-// boundary nodes (cell centre strictly inside) and Psi_p of the current box
+// boundary nodes (cell centre strictly inside) and the level-0 octree test of
+// every cell of the current box; cells cut by the surface are queued for
+// k_psi_surface
 __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
   const int p = blockIdx.x;
   DevParticle& P = a.parts[p];
@@ -369,15 +351,94 @@ __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
       const int old = atomicCAS(a.owner + n, FLUID, p);
       if (old != FLUID) atomicOr(a.status, ST_OVERLAP);
     }
-    ps = psi_cell((double)X, (double)Y, (double)Z, P.pos, R2);
+    const float ox = (float)((double)X - P.pos[0]);
+    const float oy = (float)((double)Y - P.pos[1]);
+    const float oz = (float)((double)Z - P.pos[2]);
+    int s0 = classify_f32(ox, oy, oz, 0.5f, (float)R2, psi_margin(R2));
+    if (s0 < 0) s0 = classify((double)X, (double)Y, (double)Z, 0.5, P.pos, R2);
+    if (s0 == CUBE_IN) {
+      ps = 1.0;
+      atomicAdd(a.psi + n, 1.0);
+    } else if (s0 == CUBE_UNDECIDED) {
+      const int slot = atomicAdd(a.surf_count, 1);
+      if (slot < a.surf_cap) a.surf[slot] = make_int2(p, c);
+      else atomicOr(a.status, ST_CAPACITY);
+    }
     a.psibox[(long long)p * a.boxmax + c] = ps;
-    if (ps != 0.0) atomicAdd(a.psi + n, ps);
   }
   double v[2] = {ps, (double)inside};
   block_sum<2>(v);
   if (threadIdx.x == 0) {
     if (v[0] != 0.0) atomicAdd(&P.psisum, v[0]);  // dyadic: exact in any order
     if (v[1] != 0.0) atomicAdd(&P.nb, (int)v[1]);
+  }
+}
+
+constexpr int PSI_WARPS = 4;  // warps per CTA of k_psi_surface
+
+__global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
+  __shared__ unsigned short queue[PSI_WARPS][2][512];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int count = min(*a.surf_count, a.surf_cap);
+  for (int e = blockIdx.x * PSI_WARPS + wid; e < count; e += gridDim.x * PSI_WARPS) {
+    const int2 pc = a.surf[e];
+    DevParticle& P = a.parts[pc.x];
+    int X, Y, Z;
+    box_coord(pc.y, P.lo, P.hi, X, Y, Z);
+    const double R2 = __dmul_rn(P.radius, P.radius);
+    const float R2f = (float)R2, margin = psi_margin(R2);
+    const float ox = (float)((double)X - P.pos[0]);
+    const float oy = (float)((double)Y - P.pos[1]);
+    const float oz = (float)((double)Z - P.pos[2]);
+    unsigned short* cur = queue[wid][0];
+    unsigned short* nxt = queue[wid][1];
+    if (lane == 0) cur[0] = 0;
+    __syncwarp();
+    int qlen = 1;
+    int units = 0;
+    for (int l = 1; l <= PSI_DEPTH && qlen > 0; ++l) {
+      const int ntask = qlen * 8;
+      const float h = ldexpf(1.0f, -(l + 1));
+      int newlen = 0;
+      for (int t0 = 0; t0 < ntask; t0 += 32) {
+        const int t = t0 + lane;
+        bool und = false;
+        int path = 0;
+        if (t < ntask) {
+          path = ((int)cur[t >> 3] << 3) | (t & 7);
+          float cx, cy, cz;
+          subcube_centre_f(path, l, ox, oy, oz, cx, cy, cz);
+          int st = classify_f32(cx, cy, cz, h, R2f, margin);
+          if (st < 0) {
+            double ex, ey, ez;
+            subcube_centre_d(path, l, (double)X, (double)Y, (double)Z, ex, ey, ez);
+            st = classify(ex, ey, ez, ldexp(1.0, -(l + 1)), P.pos, R2);
+          }
+          if (st == CUBE_IN) units += 2 << (3 * (PSI_DEPTH - l));
+          else if (st == CUBE_UNDECIDED) {
+            if (l == PSI_DEPTH) units += 1;
+            else und = true;
+          }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, und);
+        if (und) nxt[newlen + __popc(mask & ((1u << lane) - 1u))] = (unsigned short)path;
+        newlen += __popc(mask);
+      }
+      __syncwarp();
+      unsigned short* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+      qlen = newlen;
+    }
+    for (int o = 16; o > 0; o >>= 1) units += __shfl_xor_sync(0xffffffffu, units, o);
+    if (lane == 0 && units > 0) {
+      const double ps = ldexp((double)units, -13);  // units / PSI_UNITS
+      const long long n = node_of(X, Y, Z, a.g);
+      a.psibox[(long long)pc.x * a.boxmax + pc.y] = ps;
+      atomicAdd(a.psi + n, ps);
+      atomicAdd(&P.psisum, ps);
+    }
+    __syncwarp();
   }
 }
 
@@ -434,7 +495,7 @@ __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
   int nf = 0;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const long long m = node_of(X + CX[i], Y + CY[i], Z + CZ[i], g);
+    const long long m = node_of(X + dcx(i), Y + dcy(i), Z + dcz(i), g);
     if (steady_fluid(a, m)) rec[nf++] = m;
   }
   if (covered) {
@@ -443,9 +504,9 @@ __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double fi = a.fw[(long long)i * N + n];
-      if (CX[i]) mx += CX[i] * fi;
-      if (CY[i]) my += CY[i] * fi;
-      if (CZ[i]) mz += CZ[i] * fi;
+      if (dcx(i)) mx += csgn(dcx(i), fi);
+      if (dcy(i)) my += csgn(dcy(i), fi);
+      if (dcz(i)) mz += csgn(dcz(i), fi);
       a.fw[(long long)i * N + n] = 0.0;
     }
     atomicAdd(&P.ftrans[0], mx);
@@ -501,12 +562,12 @@ __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
     double mx = 0.0, my = 0.0, mz = 0.0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const double cu = CX[i] * vx + CY[i] * vy + CZ[i] * vz;
+      const double cu = cdot(i, vx, vy, vz);
       const double fi = wgt(i) * rbar * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
       a.fw[(long long)i * N + n] = fi;
-      if (CX[i]) mx += CX[i] * fi;
-      if (CY[i]) my += CY[i] * fi;
-      if (CZ[i]) mz += CZ[i] * fi;
+      if (dcx(i)) mx += csgn(dcx(i), fi);
+      if (dcy(i)) my += csgn(dcy(i), fi);
+      if (dcz(i)) mz += csgn(dcz(i), fi);
     }
     atomicAdd(&P.ftrans[0], -mx);
     atomicAdd(&P.ftrans[1], -my);
@@ -561,13 +622,13 @@ cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s) {
   const int edge = (int)round(cbrt((double)a.boxmax)) + 1;
   const unsigned uchunks = (unsigned)((edge * edge * edge + PT - 1) / PT);
   const unsigned bchunks = (unsigned)((a.boxmax + PT - 1) / PT);
-  // Psi needs an octree per surface cell: small CTAs spread it over more SMs
-  const unsigned cchunks = (unsigned)((a.boxmax + CLAIM_T - 1) / CLAIM_T);
   if (transitions) {
     k_save_prev<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
     k_clear<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
   }
-  k_claim<<<dim3(a.P, cchunks), CLAIM_T, 0, s>>>(a);
+  cudaMemsetAsync(a.surf_count, 0, sizeof(int), s);
+  k_claim<<<dim3(a.P, bchunks), PT, 0, s>>>(a);
+  k_psi_surface<<<4 * 152, 32 * PSI_WARPS, 0, s>>>(a);
   k_charge_scatter<<<dim3(a.P, bchunks), PT, 0, s>>>(a);
   if (transitions) {
     k_transitions<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
