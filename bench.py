@@ -44,7 +44,8 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 
 # DRAM traffic of one k_lb_fused launch from an ncu capture (profiles/), valid
 # only for the kernel source it was taken on.
-TRAFFIC = {"k_lb_fused": {"bytes_per_launch": None, "source_sha": None}}
+TRAFFIC = {"k_lb_fused": {"bytes_per_launch": 755997696,  # profiles/fp64_k_lb_fused_k_advect_single128.md
+                           "source_sha": "85d705496daa5794"}}
 
 
 def src_sha(name: str) -> str:
