@@ -4,9 +4,11 @@
 Workload (default): the single-sphere electrophoresis box -- 128^3 periodic
 lattice, D3Q19 BGK tau = 1, 2 ion species (z = +1/-1, D = 0.3, bulk 1e-3,
 neutralised), Bjerrum length 0.7, one sphere R = 8, Z = -300 at a seeded
-off-centre position, free to move, E = 0.005 along x; FP64 form.  A step is one
-full time step: Poisson, fused flux + LB, advection, particle forces and
-integration, re-flagging and transitions.
+off-centre position, free to move, E = 0.005 along x.  A step is one full time
+step: Poisson, fused flux + LB, advection, particle forces and integration,
+re-flagging and transitions.  `value` is the FP32-storage form (float
+populations, int32 fixed-point species, FP64 particle sums and integrator);
+the plain FP64 form is measured beside it under "fp64_form".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -31,13 +33,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS per full EK step and % of HBM roofline, FP32/batched vs plain FP64 at 1e-3 mobility"
-FLUSH_NOTE = "state > L2 (FP64 populations 2 x 19 x 8 B x N = 637 MB at 128^3), no flush needed"
+FLUSH_NOTE = ("state > L2 (populations 2 x 19 x 4 B x N = 319 MB in the FP32 form, 637 MB in "
+              "FP64, at 128^3; L2 129 MB), no flush needed")
 
 # Algorithmic work of the fused flux + LB kernel (k_lb_fused), per fluid node,
 # two species, partial volumes on, bulk node (all 18 links fluid): bytes that
 # must cross HBM once per step and FP64 operations of the formulas.
 LB_BYTES_PER_NODE = 2 * 19 * 8 + 2 * 2 * 8 + 8 + 8 + 4 + 3 * 8   # f r/w, rho r/w, psi, phi, owner, u
 LB_FP64_FLOP_PER_NODE = 950
+# the same for the FP32-storage kernel (k_lb32): float populations, int32 species
+LB32_BYTES_PER_NODE = 2 * 19 * 4 + 2 * 2 * 4 + 4 + 4 + 4 + 3 * 4
 # FP64 peak derived from the unit counts: 152 SMs x 2.07 GHz x 4 flop/clk/SM
 # (2 DFMA per clock per SM); a DFMA probe on this pool measured 1.19 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
@@ -45,7 +50,8 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 # DRAM traffic of one k_lb_fused launch from an ncu capture (profiles/), valid
 # only for the kernel source it was taken on.
 TRAFFIC = {"k_lb_fused": {"bytes_per_launch": 755997696,  # profiles/fp64_k_lb_fused_k_advect_single128.md
-                           "source_sha": "85d705496daa5794"}}
+                           "source_sha": "85d705496daa5794", "file": "ek_lattice.cu"},
+           "k_lb32": {"bytes_per_launch": None, "source_sha": None, "file": "ek_lattice32.cu"}}
 
 
 def src_sha(name: str) -> str:
@@ -116,10 +122,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def build_system(ek, w):
+def build_system(ek, w, fp32=True):
+    flags = ek.EK_PV | ek.EK_NEUTRALIZE | (ek.EK_FP32 if fp32 else 0)
     s = ek.EKSystem(w["shape"], nu=w["nu"], rho0=w["rho0"], bjerrum=w["bjerrum"],
-                    valence=w["valence"], D=w["D"], bulk=w["bulk"],
-                    flags=ek.EK_PV | ek.EK_NEUTRALIZE)
+                    valence=w["valence"], D=w["D"], bulk=w["bulk"], flags=flags)
     for p in w["particles"]:
         s.add_particle(p["pos"], radius=p["radius"], charge=p["charge"], rho_p=w["rho_p"])
     import numpy as np
@@ -212,10 +218,7 @@ def main():
     from paper_1607_04572_gb300 import ek
 
     nodes = w["shape"][0] * w["shape"][1] * w["shape"][2]
-    s = build_system(ek, w)
     stream = torch.cuda.Stream()
-    s.set_stream(stream)
-    s.step(max(args.warmup, 3))
 
     def barrier():
         torch.cuda.synchronize()
@@ -223,34 +226,48 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # ---- device-timed region: K full steps, inputs resident in HBM ----
-    clk = ClockSampler(local)
-    barrier()
-    clk.start()
-    launches0 = s.kernel_launches()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    s.step_async(args.steps)
-    ev1.record(stream)
-    ev1.synchronize()
-    barrier()
-    clocks = clk.stop()
-    launches = s.kernel_launches() - launches0
-    s.sync()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nodes * args.steps * ws / (ms / 1e3) / 1e6
+        return float(t.item())
 
-    # ---- per-stage device times (CUDA events between stages on the same stream) ----
-    kst = max(10, min(args.steps, 50))
-    stage = s.step_timed(kst)
-    lb_ms = stage[1] / kst
+    def measure(fp32):
+        """Warm-up, then K steps timed with CUDA events on the context's stream
+        (inputs resident in HBM); then a per-stage split of more steps."""
+        s = build_system(ek, w, fp32)
+        s.set_stream(stream)
+        s.step(max(args.warmup, 3))
+        clk = ClockSampler(local)
+        barrier()
+        clk.start()
+        launches0 = s.kernel_launches()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.step_async(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        barrier()
+        clocks = clk.stop()
+        launches = s.kernel_launches() - launches0
+        s.sync()
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        kst = max(10, min(args.steps, 50))
+        stage = s.step_timed(kst)
+        return dict(system=s, ms=ms, value=nodes * args.steps * ws / (ms / 1e3) / 1e6,
+                    launches=launches, clocks=clocks,
+                    stages={k: round(v / kst, 4) for k, v in
+                            zip(["S1_poisson", "S2_flux_lb", "S3_advection", "S4_particles",
+                                 "S5_reflag", "total"], stage)},
+                    lb_ms=stage[1] / kst)
 
-    # ---- end to end through the public API with host buffers ----
+    r32 = measure(True)
+    r64 = measure(False)
+    s = r32["system"]
+
+    # ---- end to end through the public API with host buffers (FP32 form) ----
     # every step: the field E goes host -> device from pinned memory, the step
     # runs, the particle records (the mobility observable) come back to the host
     e_host = torch.tensor(w["E"], dtype=torch.float64).pin_memory()
@@ -262,44 +279,54 @@ def main():
         s.step_async(1)
         parts = s.get_particles()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = nodes * e2e_steps * ws / e2e_s / 1e6
     h2d = 3 * 8
     d2h = len(parts) * ctypes_sizeof_particle(ek)
 
     peaks, peak_kind = measured_peaks()
-    achieved_tflops = LB_FP64_FLOP_PER_NODE * nodes / (lb_ms / 1e3) / 1e12
-    achieved_gbs = LB_BYTES_PER_NODE * nodes / (lb_ms / 1e3) / 1e9
-    traffic = TRAFFIC["k_lb_fused"]
-    tr = traffic["bytes_per_launch"] if traffic["source_sha"] == src_sha("ek_lattice.cu") else None
+    hbm_peak = float(peaks.get("hbm_gbs"))
+
+    def traffic(kernel):
+        t = TRAFFIC[kernel]
+        return t["bytes_per_launch"] if t["source_sha"] == src_sha(t["file"]) else None
+
+    gbs32 = LB32_BYTES_PER_NODE * nodes / (r32["lb_ms"] / 1e3) / 1e9
+    tflops64 = LB_FP64_FLOP_PER_NODE * nodes / (r64["lb_ms"] / 1e3) / 1e12
+    gbs64 = LB_BYTES_PER_NODE * nodes / (r64["lb_ms"] / 1e3) / 1e9
 
     line = {
-        "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": ws,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
+        "metric": METRIC, "value": round(r32["value"], 3), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(r32["ms"] / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (int32 species, f64 particle sums)", "data": "synthetic",
         "config": {"workload": "single-sphere electrophoresis 128^3, R=8, Z=-300, 2 species, "
-                               "E=0.005, FP64", "nodes": nodes, "particles": len(w["particles"]),
+                               "E=0.005; FP32-storage form (FP64 form beside it)",
+                   "nodes": nodes, "particles": len(w["particles"]),
                    "parallelism": "replicas" if ws > 1 else "single", "l2": FLUSH_NOTE},
-        "roofline": {"bound": "alu", "kernel": "k_lb_fused", "achieved": round(achieved_tflops, 4),
-                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s (FP64)",
-                     "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
-                     "traffic": tr, "algorithmic_bytes": LB_BYTES_PER_NODE * nodes,
-                     "hbm": {"achieved": round(achieved_gbs, 1), "peak": peaks.get("hbm_gbs"),
-                             "unit": "GB/s", "frac": round(achieved_gbs / peaks.get("hbm_gbs"), 4),
-                             "peak_kind": peak_kind},
-                     "kernel_ms": round(lb_ms, 4)},
-        "stages_ms_per_step": {k: round(v / kst, 4) for k, v in
-                               zip(["S1_poisson", "S2_flux_lb", "S3_advection", "S4_particles",
-                                    "S5_reflag", "total"], stage)},
+        "roofline": {"bound": "hbm", "kernel": "k_lb32", "achieved": round(gbs32, 1),
+                     "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs32 / hbm_peak, 4),
+                     "peak_kind": peak_kind, "traffic": traffic("k_lb32"),
+                     "algorithmic_bytes": LB32_BYTES_PER_NODE * nodes,
+                     "kernel_ms": round(r32["lb_ms"], 4)},
+        "stages_ms_per_step": r32["stages"],
+        "fp64_form": {
+            "value": round(r64["value"], 3), "unit": "MLUPS",
+            "ms_per_step": round(r64["ms"] / args.steps, 4), "stages_ms_per_step": r64["stages"],
+            "gpu_launches": r64["launches"], "clocks": r64["clocks"],
+            "roofline": {"bound": "alu", "kernel": "k_lb_fused", "achieved": round(tflops64, 4),
+                         "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s (FP64)",
+                         "frac": round(tflops64 / FP64_PEAK_TFLOPS, 4),
+                         "traffic": traffic("k_lb_fused"),
+                         "algorithmic_bytes": LB_BYTES_PER_NODE * nodes,
+                         "hbm": {"achieved": round(gbs64, 1), "frac": round(gbs64 / hbm_peak, 4)},
+                         "kernel_ms": round(r64["lb_ms"], 4)}},
+        "speedup_vs_fp64": round(r32["value"] / r64["value"], 2),
         "e2e": {"value": round(e2e_value, 3), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-        "gpu_launches": launches,
-        "clocks": clocks,
+        "gpu_launches": r32["launches"],
+        "clocks": r32["clocks"],
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, done, dt = time_oracle(w, 3, budget_s=20.0, warmup=0)

@@ -76,8 +76,17 @@ enum {
                             Eqs. 17-18 (allowed with EK_PV, Sec. III.D.2)          */
   EK_CHARGE_NORM_VP = 4, /* Eq. 21 literally: divide by the continuous volume V_p;
                             default divides by sum Psi_p so the charge is exactly Z */
-  EK_NEUTRALIZE = 8      /* at fill time add counter-ions of the first species of
+  EK_NEUTRALIZE = 8,     /* at fill time add counter-ions of the first species of
                             opposite valence so the box is neutral                 */
+  EK_FP32 = 16           /* FP32-storage form: populations stored as f_i - w_i rho0
+                            in float, species as int32 multiples of a per-species
+                            unit 2^-e (e = ceil(20 - log2 bulk_k): at least 2^20
+                            units per bulk density), Phi, Psi, u, charges and the
+                            FFT in float, arithmetic in float; particle forces,
+                            torques and the integrator stay FP64.  Every species
+                            transfer moves whole units between nodes, so the
+                            species totals are conserved exactly.  Fields are
+                            still exchanged as FP64 (converted on set/get).      */
 };
 
 typedef struct {
@@ -91,7 +100,8 @@ typedef struct {
   int valence[EK_MAX_SPECIES];   /* z_k                                            */
   double D[EK_MAX_SPECIES];      /* diffusion coefficients, each in (0, 0.39]      */
   double bulk[EK_MAX_SPECIES];   /* initial density on fluid nodes                 */
-  unsigned flags;        /* EK_PV | EK_VACATE_ZERO | EK_CHARGE_NORM_VP | EK_NEUTRALIZE */
+  unsigned flags;        /* EK_PV | EK_VACATE_ZERO | EK_CHARGE_NORM_VP | EK_NEUTRALIZE
+                            | EK_FP32                                              */
 } ek_params;
 
 typedef enum {

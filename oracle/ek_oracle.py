@@ -209,6 +209,7 @@ def _cube_outside(cx, cy, cz, h, r, R2):
 
 
 PSI_DEPTH = 4
+FORCE_MARGIN = 4  # cells added to ceil(R) around a particle's box for its solute force
 
 
 def psi_cells(X, Y, Z, r, R):
@@ -582,39 +583,101 @@ class EKOracle:
         return out
 
     # ----- S4: particles ---------------------------------------------------------
-    def electrostatic_force(self, pid):
-        """F_el = sum_r q_p(r) (E - grad Phi(r)), central differences, and its
-        torque.  Reading: the paper gives no formula for this force (Sec. III.C)."""
+    def charge_field_force(self, pid):
+        """Force and torque of the external field E on the particle's own
+        charge distribution q_p(r) (Eq. 21 / the simple scheme's spread)."""
         p = self.particles[pid]
         lo, hi, ps, inside = self.psi_p[pid]
         qv = self.particle_charge(pid)
-        nx, ny, nz = self.n
-        F = np.zeros(3)
-        T = np.zeros(3)
-        for z in range(lo[2], hi[2]):
-            for y in range(lo[1], hi[1]):
-                for x in range(lo[0], hi[0]):
-                    qq = qv[z - lo[2], y - lo[1], x - lo[0]]
-                    if qq == 0.0:
-                        continue
-                    ix, iy, iz = x % nx, y % ny, z % nz
-                    gx = 0.5 * (self.phi[iz, iy, (ix + 1) % nx] - self.phi[iz, iy, (ix - 1) % nx])
-                    gy = 0.5 * (self.phi[iz, (iy + 1) % ny, ix] - self.phi[iz, (iy - 1) % ny, ix])
-                    gz = 0.5 * (self.phi[(iz + 1) % nz, iy, ix] - self.phi[(iz - 1) % nz, iy, ix])
-                    fr = qq * (self.E - np.array([gx, gy, gz]))
-                    d = np.array([x - p.pos[0], y - p.pos[1], z - p.pos[2]])
-                    F += fr
-                    T += np.cross(d, fr)
+        Z, Y, X = np.meshgrid(np.arange(lo[2], hi[2]), np.arange(lo[1], hi[1]),
+                              np.arange(lo[0], hi[0]), indexing="ij")
+        d = [X - p.pos[0], Y - p.pos[1], Z - p.pos[2]]
+        F = qv.sum() * self.E
+        T = np.array([((d[1] * self.E[2] - d[2] * self.E[1]) * qv).sum(),
+                      ((d[2] * self.E[0] - d[0] * self.E[2]) * qv).sum(),
+                      ((d[0] * self.E[1] - d[1] * self.E[0]) * qv).sum()])
         return F, T
 
-    def integrate(self, Fh, Th):
+    def min_image(self, coord, r, n):
+        """x - r wrapped to the nearest periodic image (|d| <= n/2)."""
+        d = coord - r
+        d = np.where(d > 0.5 * n, d - n, d)
+        d = np.where(d < -0.5 * n, d + n, d)
+        return d
+
+    def solute_forces(self, fext):
+        """Force and torque of the solute on every particle.
+
+        Reading: the paper adds "a force from electrostatics" to the drag
+        without a formula (Sec. III.C).  The solute is massless, so the force it
+        exerts on the particles (Coulomb force on the particle charge and the
+        ions' contact pressure on the surface) is the reaction of its internal
+        force on the fluid.  With i(r) = f_ext(r) - q_ions(r) E (the coupling
+        force of Eq. 16 minus the external field's direct push on the local ion
+        charge), particle p receives
+            F_p = Z_p E - sum_{r in V_p} i(r) - (unassigned remainder) / P,
+        where V_p are the fluid nodes of p's box widened by ceil(R) + 4 cells
+        for which p is the particle with the nearest surface (minimum image),
+        and the remainder is the sum of i over fluid nodes in no V_p.  Total
+        momentum then changes only by E times the total charge (zero in a
+        neutral box).  Torque: that of Z_p E on q_p(r) minus sum (r - r_p) x i.
+        Returns (F, T) arrays of shape (P, 3).
+        """
+        P = len(self.particles)
+        F = np.zeros((P, 3))
+        T = np.zeros((P, 3))
+        if P == 0:
+            return F, T
+        nx, ny, nz = self.n
+        fluid = self.owner == FLUID
+        q_ions = np.tensordot(self.valence, self.rho, axes=(0, 0)) if self.K else np.zeros(self.shape)
+        ifield = np.where(fluid[None], fext - q_ions[None] * self.E.reshape(3, 1, 1, 1), 0.0)
+        big = np.iinfo(np.int64).max
+        key = np.full(self.shape, big, dtype=np.int64)
+        regions = []
+        for pid, p in enumerate(self.particles):
+            lo, hi = particle_box(p.pos, p.radius)
+            m = int(math.ceil(p.radius)) + FORCE_MARGIN
+            iz = np.mod(np.arange(lo[2] - m, hi[2] + m), nz)
+            iy = np.mod(np.arange(lo[1] - m, hi[1] + m), ny)
+            ix = np.mod(np.arange(lo[0] - m, hi[0] + m), nx)
+            Zc, Yc, Xc = np.meshgrid(iz, iy, ix, indexing="ij")
+            dx = self.min_image(Xc.astype(np.float64), p.pos[0], nx)
+            dy = self.min_image(Yc.astype(np.float64), p.pos[1], ny)
+            dz = self.min_image(Zc.astype(np.float64), p.pos[2], nz)
+            dsurf = np.sqrt(dx * dx + dy * dy + dz * dz) - p.radius
+            kq = np.floor((dsurf + 1024.0) * 1048576.0).astype(np.int64)
+            k = (kq << 20) | pid
+            flat = (Xc + nx * (Yc + ny * Zc)).ravel()
+            np.minimum.at(key.ravel(), flat, k.ravel())
+            regions.append((flat, dx.ravel(), dy.ravel(), dz.ravel()))
+        assigned = np.zeros(3)
+        for pid, p in enumerate(self.particles):
+            flat, dx, dy, dz = regions[pid]
+            flat_u, first = np.unique(flat, return_index=True)
+            dx, dy, dz = dx[first], dy[first], dz[first]
+            mine = ((key.ravel()[flat_u] & ((1 << 20) - 1)) == pid) & fluid.ravel()[flat_u]
+            ix_ = ifield[0].ravel()[flat_u][mine]
+            iy_ = ifield[1].ravel()[flat_u][mine]
+            iz_ = ifield[2].ravel()[flat_u][mine]
+            s = np.array([ix_.sum(), iy_.sum(), iz_.sum()])
+            assigned += s
+            Fq, Tq = self.charge_field_force(pid)
+            F[pid] = Fq - s
+            ax, ay, az = dx[mine], dy[mine], dz[mine]
+            T[pid] = Tq - np.array([(ay * iz_ - az * iy_).sum(), (az * ix_ - ax * iz_).sum(),
+                                    (ax * iy_ - ay * ix_).sum()])
+        remainder = ifield.reshape(3, -1).sum(axis=1) - assigned
+        F -= remainder / P
+        return F, T
+
+    def integrate(self, Fh, Th, Fs, Ts):
         """Symplectic Euler (Sec. III.B): v += F/m, r += v, omega += T/I, with
-        F = momentum exchange + electrostatic + last step's create/destroy
+        F = momentum exchange + solute force + last step's create/destroy
         momentum.  Fixed particles keep their position and velocity."""
         for pid, p in enumerate(self.particles):
-            Fe, Te = self.electrostatic_force(pid)
-            p.force = Fh[pid] + Fe + p.f_trans
-            p.torque = Th[pid] + Te
+            p.force = Fh[pid] + Fs[pid] + p.f_trans
+            p.torque = Th[pid] + Ts[pid]
             p.f_trans = np.zeros(3)
             if p.fixed:
                 continue
@@ -709,6 +772,7 @@ class EKOracle:
             # S2a
             J = self.link_fluxes()
             fext = self.coupling_force(J)
+            Fs, Ts = self.solute_forces(fext)
             # S2b
             fnew, u, Fh, Th = self.lb_step(fext)
             # S3
@@ -718,7 +782,7 @@ class EKOracle:
             self.f = fnew
             self.u = u
             # S4
-            self.integrate(Fh, Th)
+            self.integrate(Fh, Th, Fs, Ts)
             # S5
             old = self.owner
             self._reflag_setup()

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libek.so")
-SOURCES = ["ek_api.cu", "ek_lattice.cu", "ek_poisson.cu", "ek_particles.cu",
+SOURCES = ["ek_api.cu", "ek_lattice.cu", "ek_lattice32.cu", "ek_poisson.cu", "ek_particles.cu",
            "ek_poisson_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -19,18 +19,26 @@ struct ek_ctx {
   Phys ph;
   cudaStream_t stream = nullptr;
   int device = 0;
-  double* f[2] = {nullptr, nullptr};
-  double* rho[2] = {nullptr, nullptr};
-  double* phi = nullptr;
-  double* psi = nullptr;
-  double* qpart = nullptr;
-  double* qwall = nullptr;
-  double* u = nullptr;
-  double* tmp = nullptr;
+  int fp32 = 0;  // storage form (EK_FP32)
+  // field storage: double (FP64 form) or float / int32 species (FP32 form)
+  void* f[2] = {nullptr, nullptr};
+  void* rho[2] = {nullptr, nullptr};
+  void* phi = nullptr;
+  void* psi = nullptr;
+  void* qpart = nullptr;
+  void* qwall = nullptr;
+  void* u = nullptr;
+  void* ifield = nullptr;              // 3N reals: internal solute force on the fluid (S2)
+  double* ipart = nullptr;             // 3 doubles per lattice block: its sums
+  int nipart = 0;
+  unsigned long long* fkey = nullptr;  // N: nearest-particle keys of S4
+  int emax = 0;                        // cells of the widest widened box
+  double* tmp = nullptr;  // N doubles of staging for conversions
+  size_t rsz = 8;         // bytes of a real (double / float)
   int* owner = nullptr;
   int* owner_prev = nullptr;
   unsigned char* wall = nullptr;
-  double2* spectrum = nullptr;
+  void* spectrum = nullptr;
   PoissonPlan plan;
   DevParticle* dparts = nullptr;
   int P = 0;
@@ -39,8 +47,9 @@ struct ek_ctx {
   double* psibox = nullptr;
   int boxmax = 0;
   size_t psibox_cap = 0;  // doubles allocated for psibox
-  double* fpart = nullptr;  // S4 partial sums, P * fchunks * 12
+  double* fpart = nullptr;  // S4 partial sums, P * fchunks * FPART
   int fchunks = 0;
+  double* psum = nullptr;   // (Pcap + 1) * FPART
   int2* surf = nullptr;     // surface-cell list of S5, P * boxmax entries
   int* surf_count = nullptr;
   Transfer* xfer = nullptr;
@@ -137,7 +146,7 @@ ek_status check_status(ek_ctx* ctx) {
   ctx->broken = true;
   if (st & ST_OVERLAP) return fail(ctx, EK_ERR_OVERLAP, "a node lies inside two particles (or a particle and a wall)");
   if (st & ST_EXPEL) return fail(ctx, EK_ERR_EXPEL, "a newly covered node has no fluid neighbour to expel solute to");
-  if (st & ST_CAPACITY) return fail(ctx, EK_ERR_STATE, "transition record capacity exceeded (particle moved more than one cell per step?)");
+  if (st & ST_CAPACITY) return fail(ctx, EK_ERR_STATE, "a capacity was exceeded (transition records, surface cells, or an FP32-form species value out of int32 range)");
   return fail(ctx, EK_ERR_UNSTABLE, "non-finite density, velocity or particle position");
 }
 
@@ -154,7 +163,6 @@ PartArgs part_args(ek_ctx* ctx) {
   a.psi = ctx->psi;
   a.qpart = ctx->qpart;
   a.f = ctx->f[ctx->cur];
-  a.fw = ctx->f[ctx->cur];
   a.rho = ctx->rho[ctx->cur];
   a.phi = ctx->phi;
   a.wall = ctx->wall;
@@ -163,6 +171,12 @@ PartArgs part_args(ek_ctx* ctx) {
   a.xfer_cap = ctx->xfer_cap;
   a.fpart = ctx->fpart;
   a.fchunks = ctx->fchunks;
+  a.emax = ctx->emax;
+  a.ifield = ctx->ifield;
+  a.ipart = ctx->ipart;
+  a.nipart = ctx->nipart;
+  a.fkey = ctx->fkey;
+  a.psum = ctx->psum;
   a.surf = ctx->surf;
   a.surf_count = ctx->surf_count;
   a.surf_cap = (int)std::min<size_t>(ctx->psibox_cap, (size_t)1 << 30);
@@ -187,6 +201,8 @@ LBArgs lb_args(ek_ctx* ctx) {
   a.psi = ctx->psi;
   a.owner = ctx->owner;
   a.u = ctx->u;
+  a.ifield = ctx->ifield;
+  a.ipart = ctx->ipart;
   a.parts = ctx->dparts;
   a.status = ctx->status;
   return a;
@@ -211,23 +227,29 @@ ek_status run_setup(ek_ctx* ctx) {
   for (const DevParticle& q : ctx->hparts) rmax = std::max(rmax, q.radius);
   const int edge = (int)floor(2.0 * rmax) + 4;
   const int boxmax = ctx->P ? edge * edge * edge : 0;
-  if (ctx->P && (size_t)ctx->P * boxmax > ctx->psibox_cap) {
+  const int eedge = edge + 2 * ((int)ceil(rmax) + FORCE_MARGIN);
+  const int emax = ctx->P ? eedge * eedge * eedge : 0;
+  const int fchunks = (emax + FORCE_CHUNK - 1) / FORCE_CHUNK;
+  if (ctx->P && ((size_t)ctx->P * boxmax > ctx->psibox_cap || fchunks > ctx->fchunks)) {
     if (ctx->psibox) cudaFree(ctx->psibox);
     if (ctx->fpart) cudaFree(ctx->fpart);
     if (ctx->surf) cudaFree(ctx->surf);
+    if (ctx->psum) cudaFree(ctx->psum);
+    ctx->psum = nullptr;
     ctx->psibox = nullptr;
     ctx->fpart = nullptr;
     ctx->surf = nullptr;
     ctx->psibox_cap = 0;
     const size_t cap = (size_t)ctx->Pcap * boxmax;
-    const int fchunks = (boxmax + FORCE_CHUNK - 1) / FORCE_CHUNK;
     EK_CUDA(cudaMalloc(&ctx->psibox, cap * sizeof(double)));
-    EK_CUDA(cudaMalloc(&ctx->fpart, (size_t)ctx->Pcap * fchunks * 12 * sizeof(double)));
+    EK_CUDA(cudaMalloc(&ctx->fpart, (size_t)ctx->Pcap * fchunks * FPART * sizeof(double)));
+    EK_CUDA(cudaMalloc(&ctx->psum, (size_t)(ctx->Pcap + 1) * FPART * sizeof(double)));
     EK_CUDA(cudaMalloc(&ctx->surf, cap * sizeof(int2)));
     ctx->psibox_cap = cap;
     ctx->fchunks = fchunks;
   }
   ctx->boxmax = boxmax;
+  ctx->emax = emax;
   if (ctx->P) {
     EK_CUDA(cudaMemcpyAsync(ctx->dparts, ctx->hparts.data(), ctx->P * sizeof(DevParticle),
                             cudaMemcpyHostToDevice, ctx->stream));
@@ -247,10 +269,16 @@ ek_status run_setup(ek_ctx* ctx) {
     double net = 0.0;
     for (const DevParticle& q : ctx->hparts) net += q.charge;
     if (ctx->has_qwall) {
-      std::vector<double> qw(ctx->g.N);
-      EK_CUDA(cudaMemcpy(qw.data(), ctx->qwall, ctx->g.N * sizeof(double), cudaMemcpyDeviceToHost));
       double s = 0.0;
-      for (double v : qw) s += v;
+      if (ctx->fp32) {
+        std::vector<float> qw(ctx->g.N);
+        EK_CUDA(cudaMemcpy(qw.data(), ctx->qwall, ctx->g.N * sizeof(float), cudaMemcpyDeviceToHost));
+        for (float v : qw) s += (double)v;
+      } else {
+        std::vector<double> qw(ctx->g.N);
+        EK_CUDA(cudaMemcpy(qw.data(), ctx->qwall, ctx->g.N * sizeof(double), cudaMemcpyDeviceToHost));
+        for (double v : qw) s += v;
+      }
       net += s;
     }
     double zb = 0.0;
@@ -264,8 +292,19 @@ ek_status run_setup(ek_ctx* ctx) {
       bulk[s] = bulk[s] - net / (ctx->p.valence[s] * (double)nf);
     }
   }
-  EK_CUDA(launch_fill(ctx->g, ctx->ph, ctx->owner, ctx->f[ctx->cur], ctx->rho[ctx->cur], bulk,
-                      ctx->stream));
+  if (ctx->fp32) {
+    int units[EK_MAX_SPECIES] = {0, 0, 0, 0};
+    for (int k = 0; k < ctx->p.nspecies; ++k) {
+      const double v = rint(bulk[k] / ctx->ph.qscale[k]);
+      if (!(v >= 0.0 && v < 2147483647.0)) return fail(ctx, EK_ERR_ARG, "bulk density out of the FP32 form's range");
+      units[k] = (int)v;
+    }
+    EK_CUDA(launch_fill32(ctx->g, ctx->ph, ctx->owner, (float*)ctx->f[ctx->cur],
+                          (int*)ctx->rho[ctx->cur], units, ctx->stream));
+  } else {
+    EK_CUDA(launch_fill(ctx->g, ctx->ph, ctx->owner, (double*)ctx->f[ctx->cur],
+                        (double*)ctx->rho[ctx->cur], bulk, ctx->stream));
+  }
   ctx->setup_pending = false;
   ek_status st = check_status(ctx);
   if (st != EK_OK) return st;
@@ -278,16 +317,24 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
   cudaStream_t s = ctx->stream;
   switch (stage) {
     case 1:
-      EK_CUDA(poisson_solve(ctx->plan, nullptr, ctx->rho[ctx->cur],
-                            ctx->has_qwall ? ctx->qwall : nullptr, ctx->qpart, ctx->ph, ctx->phi,
-                            ctx->spectrum, s));
+      if (ctx->fp32) {
+        EK_CUDA(poisson_solve_f32(ctx->plan, (const int*)ctx->rho[ctx->cur],
+                                  ctx->has_qwall ? (const float*)ctx->qwall : nullptr,
+                                  (const float*)ctx->qpart, ctx->ph, (float*)ctx->phi,
+                                  (float2*)ctx->spectrum, s));
+      } else {
+        EK_CUDA(poisson_solve(ctx->plan, nullptr, (const double*)ctx->rho[ctx->cur],
+                              ctx->has_qwall ? (const double*)ctx->qwall : nullptr,
+                              (const double*)ctx->qpart, ctx->ph, (double*)ctx->phi,
+                              (double2*)ctx->spectrum, s));
+      }
       ctx->launches += 5;
       return EK_OK;
     case 2: {
       LBArgs a = lb_args(ctx);
-      EK_CUDA(launch_lb_fused(a, s));
+      EK_CUDA(ctx->fp32 ? launch_lb32(a, s) : launch_lb_fused(a, s));
       if (mid) EK_CUDA(cudaEventRecord(mid, s));
-      EK_CUDA(launch_advection(a, s));
+      EK_CUDA(ctx->fp32 ? launch_advection32(a, s) : launch_advection(a, s));
       ctx->launches += ctx->p.nspecies > 0 ? 2 : 1;
       ctx->cur = 1 - ctx->cur;
       return EK_OK;
@@ -295,7 +342,7 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
     case 4: {
       PartArgs a = part_args(ctx);
       EK_CUDA(launch_particle_forces(a, s));
-      ctx->launches += ctx->P > 0 ? 2 : 0;
+      ctx->launches += ctx->P > 0 ? 5 : 0;
       return EK_OK;
     }
     case 5: {
@@ -362,6 +409,15 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   ph.K = p->nspecies;
   ph.pv = (p->flags & EK_PV) ? 1 : 0;
   ph.flags = p->flags;
+  ctx->fp32 = (p->flags & EK_FP32) ? 1 : 0;
+  ph.fp32 = ctx->fp32;
+  ctx->rsz = ctx->fp32 ? sizeof(float) : sizeof(double);
+  // FP32 form: one species unit is 2^-e with 2^20 units or more per bulk density
+  for (int k = 0; k < EK_MAX_SPECIES; ++k) {
+    int e = 30;
+    if (k < p->nspecies && p->bulk[k] > 0.0) e = (int)ceil(20.0 - log2(p->bulk[k]));
+    ph.qscale[k] = ldexp(1.0, -e);
+  }
   const double A0 = 1.0 + 2.0 * sqrt(2.0);
   for (int k = 0; k < p->nspecies; ++k) {
     ph.z[k] = (double)p->valence[k];
@@ -382,20 +438,29 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   auto alloc = [&](void** ptr, size_t bytes) {
     if (ok && cudaMalloc(ptr, bytes) != cudaSuccess) ok = false;
   };
+  const size_t rsz = ctx->rsz;  // populations, Phi, Psi, charges and u share the real size
+  const size_t ssz = ctx->fp32 ? sizeof(int) : sizeof(double);
   for (int b = 0; b < 2; ++b) {
-    alloc((void**)&ctx->f[b], 19 * N * sizeof(double));
-    alloc((void**)&ctx->rho[b], K * N * sizeof(double));
+    alloc(&ctx->f[b], 19 * N * rsz);
+    alloc(&ctx->rho[b], K * N * ssz);
   }
-  alloc((void**)&ctx->phi, N * sizeof(double));
-  alloc((void**)&ctx->psi, N * sizeof(double));
-  alloc((void**)&ctx->qpart, N * sizeof(double));
-  alloc((void**)&ctx->qwall, N * sizeof(double));
-  alloc((void**)&ctx->u, 3 * N * sizeof(double));
+  alloc(&ctx->phi, N * rsz);
+  alloc(&ctx->psi, N * rsz);
+  alloc(&ctx->qpart, N * rsz);
+  alloc(&ctx->qwall, N * rsz);
+  alloc(&ctx->u, 3 * N * rsz);
+  alloc(&ctx->ifield, 3 * N * rsz);
+  {
+    const dim3 lg = lattice_grid(g);
+    ctx->nipart = (int)(lg.x * lg.y * lg.z);
+  }
+  alloc((void**)&ctx->ipart, (size_t)ctx->nipart * 3 * sizeof(double));
+  alloc((void**)&ctx->fkey, N * sizeof(unsigned long long));
   alloc((void**)&ctx->tmp, N * sizeof(double));
   alloc((void**)&ctx->owner, N * sizeof(int));
   alloc((void**)&ctx->owner_prev, N * sizeof(int));
   alloc((void**)&ctx->wall, N);
-  alloc((void**)&ctx->spectrum, poisson_spectrum_bytes(g.nx, g.ny, g.nz));
+  alloc(&ctx->spectrum, poisson_spectrum_bytes(g.nx, g.ny, g.nz));
   ctx->xfer_cap = (int)std::min<long long>(19LL * g.N, 1LL << 22);
   alloc((void**)&ctx->xfer, (size_t)ctx->xfer_cap * sizeof(Transfer));
   alloc((void**)&ctx->xfer_count, sizeof(int));
@@ -406,14 +471,16 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
     return EK_ERR_NOMEM;
   }
   cudaMemset(ctx->wall, 0, N);
-  cudaMemset(ctx->qwall, 0, N * sizeof(double));
-  cudaMemset(ctx->phi, 0, N * sizeof(double));
-  cudaMemset(ctx->u, 0, 3 * N * sizeof(double));
+  cudaMemset(ctx->qwall, 0, N * rsz);
+  cudaMemset(ctx->phi, 0, N * rsz);
+  cudaMemset(ctx->u, 0, 3 * N * rsz);
+  cudaMemset(ctx->ifield, 0, 3 * N * rsz);
+  cudaMemset(ctx->fkey, 0xFF, N * sizeof(unsigned long long));
   cudaMemset(ctx->xfer_count, 0, sizeof(int));
   cudaMemset(ctx->status, 0, sizeof(int));
   for (int b = 0; b < 2; ++b) {
-    cudaMemset(ctx->f[b], 0, 19 * N * sizeof(double));
-    cudaMemset(ctx->rho[b], 0, K * N * sizeof(double));
+    cudaMemset(ctx->f[b], 0, 19 * N * rsz);
+    cudaMemset(ctx->rho[b], 0, K * N * ssz);
   }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     ek_destroy(ctx);
@@ -435,7 +502,8 @@ ek_status ek_destroy(ek_ctx* ctx) {
   void* ptrs[] = {ctx->f[0], ctx->f[1], ctx->rho[0], ctx->rho[1], ctx->phi, ctx->psi, ctx->qpart,
                   ctx->qwall, ctx->u, ctx->tmp, ctx->owner, ctx->owner_prev, ctx->wall,
                   ctx->spectrum, ctx->dparts, ctx->psibox, ctx->fpart, ctx->surf, ctx->xfer,
-                  ctx->xfer_count, ctx->surf_count, ctx->status};
+                  ctx->xfer_count, ctx->surf_count, ctx->status, ctx->ifield, ctx->ipart,
+                  ctx->fkey, ctx->psum};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);
@@ -498,19 +566,43 @@ ek_status ek_set_field(ek_ctx* ctx, ek_field which, int component, const double*
   if (count != field_size(ctx, which)) return fail(ctx, EK_ERR_ARG, "count does not match the field size");
   const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const size_t N = (size_t)ctx->g.N;
+  const Grid& g = ctx->g;
   cudaStream_t s = ctx->stream;
+  const bool f32 = ctx->fp32 != 0;
   switch (which) {
     case EK_FIELD_SPECIES:
       if (component < 0 || component >= ctx->p.nspecies) return fail(ctx, EK_ERR_ARG, "bad species index");
-      EK_CUDA(cudaMemcpyAsync(ctx->rho[ctx->cur] + component * N, src, N * sizeof(double), kind, s));
+      if (f32) {
+        EK_CUDA(cudaMemcpyAsync(ctx->tmp, src, N * sizeof(double), kind, s));
+        EK_CUDA(convert32(CONV_SPC_FROM_F64, g, 0, ctx->ph.qscale[component], ctx->tmp,
+                          (int*)ctx->rho[ctx->cur] + component * N, ctx->status, s));
+      } else {
+        EK_CUDA(cudaMemcpyAsync((double*)ctx->rho[ctx->cur] + component * N, src, N * sizeof(double), kind, s));
+      }
       break;
     case EK_FIELD_POPULATIONS:
-      EK_CUDA(cudaMemcpyAsync(ctx->f[ctx->cur], src, 19 * N * sizeof(double), kind, s));
+      if (f32) {
+        for (int i = 0; i < Q; ++i) {
+          EK_CUDA(cudaMemcpyAsync(ctx->tmp, src + i * N, N * sizeof(double), kind, s));
+          EK_CUDA(convert32(CONV_POP_FROM_F64, g, i, ctx->ph.rho0, ctx->tmp, ctx->f[ctx->cur], ctx->status, s));
+        }
+      } else {
+        EK_CUDA(cudaMemcpyAsync(ctx->f[ctx->cur], src, 19 * N * sizeof(double), kind, s));
+      }
       break;
     case EK_FIELD_VELOCITY:
-      EK_CUDA(cudaMemcpyAsync(ctx->u, src, 3 * N * sizeof(double), kind, s));
-      k_set_velocity<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->owner, ctx->f[ctx->cur], ctx->u);
-      EK_CUDA(cudaGetLastError());
+      if (f32) {
+        // stage the FP64 velocity in the idle population buffer (19 N floats >= 3 N doubles)
+        double* u3 = (double*)ctx->f[1 - ctx->cur];
+        EK_CUDA(cudaMemcpyAsync(u3, src, 3 * N * sizeof(double), kind, s));
+        EK_CUDA(set_velocity32(g, ctx->owner, (float*)ctx->f[ctx->cur], u3, ctx->ph.rho0, s));
+        for (int d = 0; d < 3; ++d)
+          EK_CUDA(convert32(CONV_F64_TO_F32, g, 0, 0.0, u3 + d * N, (float*)ctx->u + d * N, ctx->status, s));
+      } else {
+        EK_CUDA(cudaMemcpyAsync(ctx->u, src, 3 * N * sizeof(double), kind, s));
+        k_set_velocity<<<nblk(g.N), 256, 0, s>>>(g, ctx->owner, (double*)ctx->f[ctx->cur], (const double*)ctx->u);
+        EK_CUDA(cudaGetLastError());
+      }
       break;
     case EK_FIELD_E_EXT:
     case EK_FIELD_BODY_FORCE: {
@@ -528,19 +620,24 @@ ek_status ek_set_field(ek_ctx* ctx, ek_field which, int component, const double*
     }
     case EK_FIELD_WALL:
       EK_CUDA(cudaMemcpyAsync(ctx->tmp, src, N * sizeof(double), kind, s));
-      k_double_to_u8<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->tmp, ctx->wall);
+      k_double_to_u8<<<nblk(g.N), 256, 0, s>>>(g, ctx->tmp, ctx->wall);
       EK_CUDA(cudaGetLastError());
       ctx->setup_pending = true;
       return run_setup(ctx);
     case EK_FIELD_WALL_CHARGE:
-      EK_CUDA(cudaMemcpyAsync(ctx->qwall, src, N * sizeof(double), kind, s));
+      if (f32) {
+        EK_CUDA(cudaMemcpyAsync(ctx->tmp, src, N * sizeof(double), kind, s));
+        EK_CUDA(convert32(CONV_F64_TO_F32, g, 0, 0.0, ctx->tmp, ctx->qwall, ctx->status, s));
+      } else {
+        EK_CUDA(cudaMemcpyAsync(ctx->qwall, src, N * sizeof(double), kind, s));
+      }
       ctx->has_qwall = true;
       break;
     default:
       return fail(ctx, EK_ERR_ARG, "field is read-only");
   }
   EK_CUDA(cudaStreamSynchronize(s));
-  return EK_OK;
+  return check_status(ctx);
 }
 
 ek_status ek_get_fields(ek_ctx* ctx, ek_field which, int component, double* dst, size_t count,
@@ -554,62 +651,90 @@ ek_status ek_get_fields(ek_ctx* ctx, ek_field which, int component, double* dst,
   if (count != field_size(ctx, which)) return fail(ctx, EK_ERR_ARG, "count does not match the field size");
   const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const size_t N = (size_t)ctx->g.N;
+  const Grid& g = ctx->g;
   cudaStream_t s = ctx->stream;
-  const double* srcp = nullptr;
-  size_t bytes = N * sizeof(double);
+  const bool f32 = ctx->fp32 != 0;
+  // copy one converted N-element block (tmp) to dst + offset
+  auto out_block = [&](size_t offset) -> cudaError_t {
+    return cudaMemcpyAsync(dst + offset, ctx->tmp, N * sizeof(double), kind, s);
+  };
+  // a real field of the current form -> dst + offset
+  auto out_real = [&](const void* src, size_t offset) -> cudaError_t {
+    if (!f32) return cudaMemcpyAsync(dst + offset, src, N * sizeof(double), kind, s);
+    cudaError_t e = convert32(CONV_F32_TO_F64, g, 0, 0.0, src, ctx->tmp, ctx->status, s);
+    return e != cudaSuccess ? e : out_block(offset);
+  };
   switch (which) {
     case EK_FIELD_SPECIES:
       if (component < 0 || component >= ctx->p.nspecies) return fail(ctx, EK_ERR_ARG, "bad species index");
-      srcp = ctx->rho[ctx->cur] + component * N;
+      if (f32) {
+        EK_CUDA(convert32(CONV_SPC_TO_F64, g, 0, ctx->ph.qscale[component],
+                          (const int*)ctx->rho[ctx->cur] + component * N, ctx->tmp, ctx->status, s));
+        EK_CUDA(out_block(0));
+      } else {
+        EK_CUDA(cudaMemcpyAsync(dst, (const double*)ctx->rho[ctx->cur] + component * N,
+                                N * sizeof(double), kind, s));
+      }
       break;
     case EK_FIELD_POPULATIONS:
-      srcp = ctx->f[ctx->cur];
-      bytes = 19 * N * sizeof(double);
+      if (f32) {
+        for (int i = 0; i < Q; ++i) {
+          EK_CUDA(convert32(CONV_POP_TO_F64, g, i, ctx->ph.rho0, ctx->f[ctx->cur], ctx->tmp, ctx->status, s));
+          EK_CUDA(out_block(i * N));
+        }
+      } else {
+        EK_CUDA(cudaMemcpyAsync(dst, ctx->f[ctx->cur], 19 * N * sizeof(double), kind, s));
+      }
       break;
     case EK_FIELD_VELOCITY:
-      srcp = ctx->u;
-      bytes = 3 * N * sizeof(double);
+      for (int d = 0; d < 3; ++d) EK_CUDA(out_real((const char*)ctx->u + d * N * ctx->rsz, d * N));
       break;
     case EK_FIELD_E_EXT:
     case EK_FIELD_BODY_FORCE: {
       const double* v = which == EK_FIELD_E_EXT ? ctx->ph.E : ctx->ph.g;
       EK_CUDA(cudaMemcpyAsync(dst, v, 3 * sizeof(double),
                               dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
-      EK_CUDA(cudaStreamSynchronize(s));
-      return EK_OK;
+      break;
     }
     case EK_FIELD_WALL:
-      k_u8_to_double<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->wall, ctx->tmp);
-      srcp = ctx->tmp;
+      k_u8_to_double<<<nblk(g.N), 256, 0, s>>>(g, ctx->wall, ctx->tmp);
+      EK_CUDA(cudaGetLastError());
+      EK_CUDA(out_block(0));
       break;
     case EK_FIELD_WALL_CHARGE:
-      srcp = ctx->qwall;
+      EK_CUDA(out_real(ctx->qwall, 0));
       break;
     case EK_FIELD_DENSITY:
-      k_density<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->f[ctx->cur], ctx->tmp);
-      srcp = ctx->tmp;
+      if (f32) EK_CUDA(density32(g, (const float*)ctx->f[ctx->cur], ctx->ph.rho0, ctx->tmp, s));
+      else k_density<<<nblk(g.N), 256, 0, s>>>(g, (const double*)ctx->f[ctx->cur], ctx->tmp);
+      EK_CUDA(cudaGetLastError());
+      EK_CUDA(out_block(0));
       break;
     case EK_FIELD_PHI:
-      srcp = ctx->phi;
+      EK_CUDA(out_real(ctx->phi, 0));
       break;
     case EK_FIELD_PSI:
-      k_psi_clamped<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->psi, ctx->tmp);
-      srcp = ctx->tmp;
+      if (f32) {
+        EK_CUDA(out_real(ctx->psi, 0));  // clamped to 1 by S5
+      } else {
+        k_psi_clamped<<<nblk(g.N), 256, 0, s>>>(g, (const double*)ctx->psi, ctx->tmp);
+        EK_CUDA(cudaGetLastError());
+        EK_CUDA(out_block(0));
+      }
       break;
     case EK_FIELD_OWNER:
-      k_int_to_double<<<nblk(ctx->g.N), 256, 0, s>>>(ctx->g, ctx->owner, ctx->tmp);
-      srcp = ctx->tmp;
+      k_int_to_double<<<nblk(g.N), 256, 0, s>>>(g, ctx->owner, ctx->tmp);
+      EK_CUDA(cudaGetLastError());
+      EK_CUDA(out_block(0));
       break;
     case EK_FIELD_CHARGE:
-      EK_CUDA(charge_density(ctx->g, ctx->ph, ctx->rho[ctx->cur], ctx->has_qwall ? ctx->qwall : nullptr,
+      EK_CUDA(charge_density(g, ctx->ph, ctx->rho[ctx->cur], ctx->has_qwall ? ctx->qwall : nullptr,
                              ctx->qpart, ctx->tmp, s));
-      srcp = ctx->tmp;
+      EK_CUDA(out_block(0));
       break;
     default:
       return fail(ctx, EK_ERR_ARG, "unknown field");
   }
-  EK_CUDA(cudaGetLastError());
-  EK_CUDA(cudaMemcpyAsync(dst, srcp, bytes, kind, s));
   EK_CUDA(cudaStreamSynchronize(s));
   return EK_OK;
 }

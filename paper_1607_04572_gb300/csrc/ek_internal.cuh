@@ -75,7 +75,12 @@ struct DevParticle {
   int fixed;
   int lo[3], hi[3];  // box [lo, hi) in unwrapped coordinates, current position
   int ulo[3], uhi[3];  // union of the previous and current boxes (transitions)
+  int elo[3], ehi[3];  // box widened by ceil(R) + FORCE_MARGIN (solute force region)
 };
+
+// cells added to ceil(R) around a particle's box for the region whose solute
+// force it receives
+constexpr int FORCE_MARGIN = 4;
 
 // Box geometry common to the kernels.
 struct Grid {
@@ -95,6 +100,25 @@ struct Phys {
   double hz[EK_MAX_SPECIES];     // z_k / 2
   double E[3], g[3];
   double ec[19];                 // E . c_i per direction
+  int fp32;                      // storage form: 0 FP64, 1 FP32 populations / int32 species
+  double qscale[EK_MAX_SPECIES]; // FP32 form: density of one species unit (a power of 2)
+};
+
+// Storage forms.  FP64: every field double.  FP32: populations stored as the
+// deviation f_i - w_i rho0 in float, species as int32 multiples of qscale_k
+// (exact conservation: every transfer is an integer moved from one node to
+// another), Phi, Psi, u and the charge fields in float.
+struct FormF64 {
+  using pop_t = double;
+  using spc_t = double;
+  using real_t = double;
+  static constexpr bool fp32 = false;
+};
+struct FormF32 {
+  using pop_t = float;
+  using spc_t = int;
+  using real_t = float;
+  static constexpr bool fp32 = true;
 };
 
 // Transition record: one solute transfer of S5 (target node, amount per species).
@@ -105,11 +129,13 @@ struct Transfer {
 
 // FFT plan of one axis.
 struct AxisPlan {
-  int n;
-  int nrad;
-  int radix[16];
-  double2* tw;   // exp(-2 pi i k / n), k = 0..n-1 (device)
-  double* lam;   // 2 - 2 cos(2 pi k / n), k = 0..n-1 (device)
+  int n = 0;
+  int nrad = 0;
+  int radix[16] = {};
+  double2* tw = nullptr;   // exp(-2 pi i k / n), k = 0..n-1 (device)
+  double* lam = nullptr;   // 2 - 2 cos(2 pi k / n), k = 0..n-1 (device)
+  float2* tw32 = nullptr;  // the same tables rounded to float (FP32 form)
+  float* lam32 = nullptr;
 };
 
 struct PoissonPlan {
@@ -123,6 +149,38 @@ __host__ __device__ inline int wrapi(int v, int n) {
   return r < 0 ? r + n : r;
 }
 
+// Lattice kernels run on a 3D grid of 32 x 8 thread tiles (x, y) per z plane:
+// no integer division to find a node's coordinates, and a warp covers 32
+// consecutive x (coalesced).
+constexpr int TILE_X = 32, TILE_Y = 8;
+inline dim3 lattice_grid(const Grid& g) {
+  return dim3((unsigned)((g.nx + TILE_X - 1) / TILE_X), (unsigned)((g.ny + TILE_Y - 1) / TILE_Y),
+              (unsigned)g.nz);
+}
+inline dim3 lattice_block() { return dim3(TILE_X, TILE_Y, 1); }
+
+// wrapped neighbour coordinates of (x, y, z)
+struct Nbr {
+  int xm, xp, ym, yp, zm, zp;
+};
+__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const Grid& g) {
+  Nbr b;
+  b.xm = x == 0 ? g.nx - 1 : x - 1;
+  b.xp = x == g.nx - 1 ? 0 : x + 1;
+  b.ym = y == 0 ? g.ny - 1 : y - 1;
+  b.yp = y == g.ny - 1 ? 0 : y + 1;
+  b.zm = z == 0 ? g.nz - 1 : z - 1;
+  b.zp = z == g.nz - 1 ? 0 : z + 1;
+  return b;
+}
+// coordinate + offset in {-1, 0, 1}, wrapped
+__device__ __forceinline__ int nb_x(const Nbr& b, int x, int o) { return o > 0 ? b.xp : (o < 0 ? b.xm : x); }
+__device__ __forceinline__ int nb_y(const Nbr& b, int y, int o) { return o > 0 ? b.yp : (o < 0 ? b.ym : y); }
+__device__ __forceinline__ int nb_z(const Nbr& b, int z, int o) { return o > 0 ? b.zp : (o < 0 ? b.zm : z); }
+__device__ __forceinline__ long long node_index(const Grid& g, int x, int y, int z) {
+  return (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+}
+
 // ---------------------------------------------------------------------------
 // launchers (each file implements its stage)
 // ---------------------------------------------------------------------------
@@ -132,30 +190,56 @@ void poisson_plan_destroy(PoissonPlan& p);
 size_t poisson_spectrum_bytes(int nx, int ny, int nz);
 // radix plan of one axis (n = 2^a 3^b); false if n has another factor
 bool poisson_factor(int n, AxisPlan& P);
-// charge assembly fused into the first FFT pass when rho != nullptr; else q is read
+// charge assembly fused into the first FFT pass when rho != nullptr; else q is read.
+// FP64 form: double fields, double2 spectrum.
 cudaError_t poisson_solve(const PoissonPlan& p, const double* q, const double* rho,
                           const double* qwall, const double* qpart, const Phys& ph,
                           double* phi, double2* spectrum, cudaStream_t s);
-cudaError_t charge_density(const Grid& g, const Phys& ph, const double* rho, const double* qwall,
-                           const double* qpart, double* q, cudaStream_t s);
+// FP32 form: int32 species, float charge fields, float2 spectrum, float phi
+cudaError_t poisson_solve_f32(const PoissonPlan& p, const int* rho, const float* qwall,
+                              const float* qpart, const Phys& ph, float* phi, float2* spectrum,
+                              cudaStream_t s);
+cudaError_t charge_density(const Grid& g, const Phys& ph, const void* rho, const void* qwall,
+                           const void* qpart, double* q, cudaStream_t s);
 
 // S2 + S3
 struct LBArgs {
   Grid g;
   Phys ph;
-  const double* f_in;
-  double* f_out;
-  const double* rho_in;
-  double* rho_out;
-  const double* phi;
-  const double* psi;
+  const void* f_in;
+  void* f_out;
+  const void* rho_in;
+  void* rho_out;
+  const void* phi;
+  const void* psi;
   const int* owner;
-  double* u;
+  void* u;
+  void* ifield;    // real_t, 3N: solute force on the fluid minus q_ions E (fluid nodes)
+  double* ipart;   // per-block sums of ifield (3 per block of the lattice grid)
   const DevParticle* parts;
   int* status;
 };
 cudaError_t launch_lb_fused(const LBArgs& a, cudaStream_t s);
 cudaError_t launch_advection(const LBArgs& a, cudaStream_t s);
+// FP32-storage form
+cudaError_t launch_lb32(const LBArgs& a, cudaStream_t s);
+cudaError_t launch_advection32(const LBArgs& a, cudaStream_t s);
+cudaError_t launch_fill32(const Grid& g, const Phys& ph, const int* owner, float* f, int* rho,
+                          const int* units, cudaStream_t s);
+enum {
+  CONV_POP_TO_F64 = 0,    // direction `index` of the stored deviations -> f (double)
+  CONV_POP_FROM_F64 = 1,  // f (double) -> direction `index` of the deviations
+  CONV_SPC_TO_F64 = 2,    // int units -> density (scale = qscale)
+  CONV_SPC_FROM_F64 = 3,  // density -> int units (scale = qscale)
+  CONV_F32_TO_F64 = 4,
+  CONV_F64_TO_F32 = 5,
+};
+// N-element conversion; `scale` is rho0 for populations, qscale for species
+cudaError_t convert32(int op, const Grid& g, int index, double scale, const void* in, void* out,
+                      int* status, cudaStream_t s);
+cudaError_t set_velocity32(const Grid& g, const int* owner, float* f, const double* u3, double rho0,
+                           cudaStream_t s);
+cudaError_t density32(const Grid& g, const float* f, double rho0, double* out, cudaStream_t s);
 
 // S4 / S5 / set-up
 struct PartArgs {
@@ -167,25 +251,31 @@ struct PartArgs {
   double* psibox;  // P * boxmax: Psi_p over the current box
   int* owner;
   int* owner_prev;
-  double* psi;
-  double* qpart;
-  const double* f;  // populations after the stream (S4 reads, S5 writes uncovered)
-  double* fw;
-  double* rho;      // species after S3 (S5 transitions)
-  const double* phi;
+  void* psi;        // real_t
+  void* qpart;      // real_t
+  void* f;          // pop_t: populations after the stream (S4 reads, S5 writes)
+  void* rho;        // spc_t: species after S3 (S5 transitions)
+  const void* phi;  // real_t
   const unsigned char* wall;
   Transfer* xfer;
   int* xfer_count;
   int xfer_cap;
   double* fpart;   // per (particle, chunk) partial force/torque sums of S4
   int fchunks;     // chunks per particle in fpart
+  int emax;        // capacity (cells) of one particle's widened box
+  const void* ifield;        // real_t, 3N (written by S2)
+  const double* ipart;       // 3 per lattice block
+  int nipart;                // number of lattice blocks
+  unsigned long long* fkey;  // N: (surface distance, particle) of the nearest particle
+  double* psum;              // (P + 1) * FPART: per-particle sums, then the lattice total
   int2* surf;      // (particle, box cell) of the cells cut by a sphere surface
   int* surf_count;
   int surf_cap;
   int* status;
 };
-// cells per CTA of the S4 force kernel; fpart holds P * fchunks * 12 doubles
+// cells per CTA of the S4 force kernel; fpart holds P * fchunks * FPART doubles
 constexpr int FORCE_CHUNK = 128;
+constexpr int FPART = 18;  // Fh Th (momentum exchange) Fs Ts (solute) Fq Tq (field on charge)
 cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s);  // S4
 cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s);  // S5
 cudaError_t launch_fill(const Grid& g, const Phys& ph, const int* owner, double* f, double* rho,

@@ -15,10 +15,6 @@ namespace ek {
 
 namespace {
 
-struct Nbr {
-  int xm, xp, ym, yp, zm, zp;  // wrapped neighbour coordinates
-};
-
 __device__ __forceinline__ long long nbr_index(int d, int x, int y, int z, const Nbr& b,
                                                int nx, int ny) {
   const int X = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
@@ -41,33 +37,34 @@ __device__ __forceinline__ void boundary_velocity(const DevParticle& P, int xb, 
   vb[2] = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
 }
 
+// One fluid node of S2.  iv receives the node's internal solute force on the
+// fluid, i = f_ext - q_ions E (zero off the fluid), also stored in ifield.
 template <int K, bool PV>
-__global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
+__device__ __forceinline__ void lb_node(const LBArgs& a, int x, int y, int z, double (&iv)[3]) {
+  const double* f_in = (const double*)a.f_in;
+  double* f_out = (double*)a.f_out;
+  const double* rho_in = (const double*)a.rho_in;
+  double* rho_out = (double*)a.rho_out;
+  const double* phi = (const double*)a.phi;
+  const double* psi = (const double*)a.psi;
+  double* u = (double*)a.u;
   const long long N = a.g.N;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const int x = (int)(n % nx);
-  const long long t = n / nx;
-  const int y = (int)(t % ny);
-  const int z = (int)(t / ny);
-
+  const int nx = a.g.nx, ny = a.g.ny;
+  const long long n = node_index(a.g, x, y, z);
+  double* ifield = (double*)a.ifield;
   if (a.owner[n] != FLUID) {
     // boundary node: no fluid, no solute transport
 #pragma unroll
-    for (int k = 0; k < K; ++k) a.rho_out[k * N + n] = a.rho_in[k * N + n];
-    a.u[n] = 0.0;
-    a.u[N + n] = 0.0;
-    a.u[2 * N + n] = 0.0;
+    for (int k = 0; k < K; ++k) rho_out[k * N + n] = rho_in[k * N + n];
+    u[n] = 0.0;
+    u[N + n] = 0.0;
+    u[2 * N + n] = 0.0;
+    ifield[n] = 0.0;
+    ifield[N + n] = 0.0;
+    ifield[2 * N + n] = 0.0;
     return;
   }
-  Nbr b;
-  b.xm = x == 0 ? nx - 1 : x - 1;
-  b.xp = x == nx - 1 ? 0 : x + 1;
-  b.ym = y == 0 ? ny - 1 : y - 1;
-  b.yp = y == ny - 1 ? 0 : y + 1;
-  b.zm = z == 0 ? nz - 1 : z - 1;
-  b.zp = z == nz - 1 ? 0 : z + 1;
+  const Nbr b = make_nbr(x, y, z, a.g);
 
   // ---- S2a: diffusive + migrative link fluxes (Eq. 20; Eq. 13 without PV) ----
   // Link flux J_k = (D_k / A_0) * s_l * [(a - b) + z_k/2 (a + b) dphi],
@@ -79,11 +76,11 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
   double S[K > 0 ? K : 1];
   double r0[K > 0 ? K : 1];
   double om0 = 1.0;
-  if (PV) om0 = 1.0 - a.psi[n];  // psi is clamped to [0, 1] by S5
+  if (PV) om0 = 1.0 - psi[n];  // psi is clamped to [0, 1] by S5
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     S[k] = 0.0;
-    r0[k] = a.rho_in[k * N + n];
+    r0[k] = rho_in[k * N + n];
   }
   if (PV && om0 != 1.0) {
     const double inv = 1.0 / om0;
@@ -91,20 +88,20 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
     for (int k = 0; k < K; ++k) r0[k] *= inv;
   }
   if (K > 0) {
-    const double phi0 = a.phi[n];
+    const double phi0 = phi[n];
     const double s_face = om0, s_edge = om0 * 0.70710678118654752;
 #pragma unroll
     for (int d = 1; d < Q; ++d) {
       const long long m = nbr_index(d, x, y, z, b, nx, ny);
       if (a.owner[m] != FLUID) continue;  // no flux into or out of boundary nodes
       double omj = 1.0;
-      if (PV) omj = 1.0 - a.psi[m];
+      if (PV) omj = 1.0 - psi[m];
       const double sl = (d < 7 ? s_face : s_edge) * omj;
-      const double dphi = (phi0 - a.phi[m]) + a.ph.ec[d];
+      const double dphi = (phi0 - phi[m]) + a.ph.ec[d];
       double tsum = 0.0;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        double rb = a.rho_in[k * N + m];
+        double rb = rho_in[k * N + m];
         if (PV && omj != 1.0) rb = rb / omj;
         const double br = fma(r0[k] + rb, a.ph.hz[k] * dphi, r0[k] - rb);
         const double T = br * sl;
@@ -117,7 +114,7 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
     }
   }
 #pragma unroll
-  for (int k = 0; k < K; ++k) a.rho_out[k * N + n] = a.rho_in[k * N + n] - a.ph.dcoef[k] * S[k];
+  for (int k = 0; k < K; ++k) rho_out[k * N + n] = rho_in[k * N + n] - a.ph.dcoef[k] * S[k];
   constexpr double HALF_INV_A0 = 0.13060193748187072;  // 1 / (2 (1 + 2 sqrt 2))
 
   // ---- S2b: collision (Eqs. 8-9), TRT in pair form ----
@@ -127,7 +124,7 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
   // f*_ibar = f_ibar + lambda_e s/2 - lambda_o d/2 + Ep - Em.
   double f[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] = a.f_in[i * N + n];
+  for (int i = 0; i < Q; ++i) f[i] = f_in[i * N + n];
   double ps[Q], pd[Q];
   double rho = f[0], jx = 0.0, jy = 0.0, jz = 0.0;
 #pragma unroll
@@ -138,6 +135,18 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
     if (dcx(i)) jx += csgn(dcx(i), pd[i]);
     if (dcy(i)) jy += csgn(dcy(i), pd[i]);
     if (dcz(i)) jz += csgn(dcz(i), pd[i]);
+  }
+  {
+    // internal solute force: coupling force minus the field's push on the local ion charge
+    double qion = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) qion += a.ph.z[k] * rho_in[k * N + n];
+    iv[0] = gx * HALF_INV_A0 - qion * a.ph.E[0];
+    iv[1] = gy * HALF_INV_A0 - qion * a.ph.E[1];
+    iv[2] = gz * HALF_INV_A0 - qion * a.ph.E[2];
+    ifield[n] = iv[0];
+    ifield[N + n] = iv[1];
+    ifield[2 * N + n] = iv[2];
   }
   const double Fx = gx * HALF_INV_A0 + a.ph.g[0];
   const double Fy = gy * HALF_INV_A0 + a.ph.g[1];
@@ -172,18 +181,18 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
     fs[i + 1] = f[i + 1] + (X - Y);
   }
   if (!isfinite(rho) || !isfinite(usq)) atomicOr(a.status, ST_NONFINITE);
-  a.u[n] = ux;
-  a.u[N + n] = uy;
-  a.u[2 * N + n] = uz;
+  u[n] = ux;
+  u[N + n] = uy;
+  u[2 * N + n] = uz;
 
   // ---- push stream with velocity bounce-back (Eq. 12) ----
-  a.f_out[n] = fs[0];
+  f_out[n] = fs[0];
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const long long m = nbr_index(i, x, y, z, b, nx, ny);
     const int om = a.owner[m];
     if (om == FLUID) {
-      a.f_out[i * N + m] = fs[i];
+      f_out[i * N + m] = fs[i];
     } else {
       double cvb = 0.0;
       if (om >= 0) {
@@ -194,9 +203,43 @@ __global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
         boundary_velocity(a.parts[om], xb, yb, zb, a.g, vb);
         cvb = cdot(i, vb[0], vb[1], vb[2]);
       }
-      a.f_out[opp(i) * N + n] = fs[i] - 6.0 * wgt(i) * a.ph.rho0 * cvb;
+      f_out[opp(i) * N + n] = fs[i] - 6.0 * wgt(i) * a.ph.rho0 * cvb;
     }
   }
+}
+
+// Sum of three doubles over a block of the lattice grid, fixed order; thread
+// 0 writes it to ipart[3 * block].
+__device__ __forceinline__ void block_sum3(double (&v)[3], double* ipart) {
+  __shared__ double red[TILE_X * TILE_Y / 32][3];
+  const int t = threadIdx.x + TILE_X * threadIdx.y;
+  const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double s = v[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp][c] = s;
+  }
+  __syncthreads();
+  if (t == 0) {
+    const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double s = 0.0;
+      for (int w = 0; w < TILE_X * TILE_Y / 32; ++w) s += red[w][c];
+      ipart[3 * blk + c] = s;
+    }
+  }
+}
+
+template <int K, bool PV>
+__global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
+  const int x = blockIdx.x * TILE_X + threadIdx.x;
+  const int y = blockIdx.y * TILE_Y + threadIdx.y;
+  const int z = blockIdx.z;
+  double iv[3] = {0.0, 0.0, 0.0};
+  if (x < a.g.nx && y < a.g.ny) lb_node<K, PV>(a, x, y, z, iv);
+  block_sum3(iv, a.ipart);
 }
 
 // sign (-1, 0, +1) and magnitude of a double from its bits: integer work
@@ -217,24 +260,26 @@ __device__ __forceinline__ double abs_bits(double v) {
 // of offset s is prod_a w_a, w_a = 1 - |u_a| (s_a = 0) or |u_a|.
 template <int K>
 __global__ void __launch_bounds__(256) k_advect(LBArgs a) {
+  const double* rho_in = (const double*)a.rho_in;
+  double* rho_out = (double*)a.rho_out;
+  const double* u = (const double*)a.u;
   const long long N = a.g.N;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
+  const int x = blockIdx.x * TILE_X + threadIdx.x;
+  const int y = blockIdx.y * TILE_Y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.g.nx || y >= a.g.ny) return;
+  const long long n = node_index(a.g, x, y, z);
   if (a.owner[n] != FLUID) return;
-  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const int x = (int)(n % nx);
-  const long long t = n / nx;
-  const int y = (int)(t % ny);
-  const int z = (int)(t / ny);
+  const Nbr b = make_nbr(x, y, z, a.g);
   double acc[K];
   double rs[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    acc[k] = a.rho_out[k * N + n];
-    rs[k] = a.rho_in[k * N + n];
+    acc[k] = rho_out[k * N + n];
+    rs[k] = rho_in[k * N + n];
   }
   // outflow of this cell
-  const double ux = a.u[n], uy = a.u[N + n], uz = a.u[2 * N + n];
+  const double ux = u[n], uy = u[N + n], uz = u[2 * N + n];
   const int sx = sgn_bits(ux), sy = sgn_bits(uy), sz = sgn_bits(uz);
   const double ax = abs_bits(ux), ay = abs_bits(uy), az = abs_bits(uz);
   const double bx = 1.0 - ax, by = 1.0 - ay, bz = 1.0 - az;
@@ -242,10 +287,8 @@ __global__ void __launch_bounds__(256) k_advect(LBArgs a) {
     for (int oy = 0; oy <= (sy != 0); ++oy) {
       for (int ox = 0; ox <= (sx != 0); ++ox) {
         if (!ox && !oy && !oz) continue;
-        const int X = ox ? wrapi(x + sx, nx) : x;
-        const int Y = oy ? wrapi(y + sy, ny) : y;
-        const int Z = oz ? wrapi(z + sz, nz) : z;
-        const long long m = X + (long long)nx * (Y + (long long)ny * Z);
+        const long long m = node_index(a.g, nb_x(b, x, ox ? sx : 0), nb_y(b, y, oy ? sy : 0),
+                                       nb_z(b, z, oz ? sz : 0));
         if (a.owner[m] != FLUID) continue;  // share aimed at a boundary stays here
         const double frac = (ox ? ax : bx) * (oy ? ay : by) * (oz ? az : bz);
 #pragma unroll
@@ -259,12 +302,9 @@ __global__ void __launch_bounds__(256) k_advect(LBArgs a) {
     for (int qy = -1; qy <= 1; ++qy) {
       for (int qx = -1; qx <= 1; ++qx) {
         if (!qx && !qy && !qz) continue;
-        const int X = wrapi(x - qx, nx);
-        const int Y = wrapi(y - qy, ny);
-        const int Z = wrapi(z - qz, nz);
-        const long long m = X + (long long)nx * (Y + (long long)ny * Z);
+        const long long m = node_index(a.g, nb_x(b, x, -qx), nb_y(b, y, -qy), nb_z(b, z, -qz));
         if (a.owner[m] != FLUID) continue;
-        const double vx = a.u[m], vy = a.u[N + m], vz = a.u[2 * N + m];
+        const double vx = u[m], vy = u[N + m], vz = u[2 * N + m];
         if ((qx && sgn_bits(vx) != qx) || (qy && sgn_bits(vy) != qy) || (qz && sgn_bits(vz) != qz))
           continue;
         const double wx = qx ? abs_bits(vx) : 1.0 - abs_bits(vx);
@@ -272,14 +312,14 @@ __global__ void __launch_bounds__(256) k_advect(LBArgs a) {
         const double wz = qz ? abs_bits(vz) : 1.0 - abs_bits(vz);
         const double frac = wx * wy * wz;
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += a.rho_in[k * N + m] * frac;
+        for (int k = 0; k < K; ++k) acc[k] += rho_in[k * N + m] * frac;
       }
     }
   }
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    a.rho_out[k * N + n] = acc[k];
+    rho_out[k * N + n] = acc[k];
     bad |= !isfinite(acc[k]);
   }
   if (bad) atomicOr(a.status, ST_NONFINITE);
@@ -302,13 +342,12 @@ unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads -
 }  // namespace
 
 cudaError_t launch_lb_fused(const LBArgs& a, cudaStream_t s) {
-  const unsigned nb = blocks_for(a.g.N, 256);
   const bool pv = a.ph.pv != 0;
   switch (a.ph.K) {
 #define EK_CASE(KK)                                                   \
   case KK:                                                            \
-    if (pv) k_lb_fused<KK, true><<<nb, 256, 0, s>>>(a);               \
-    else k_lb_fused<KK, false><<<nb, 256, 0, s>>>(a);                 \
+    if (pv) k_lb_fused<KK, true><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a);               \
+    else k_lb_fused<KK, false><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a);                 \
     break;
     EK_CASE(0)
     EK_CASE(1)
@@ -323,13 +362,12 @@ cudaError_t launch_lb_fused(const LBArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_advection(const LBArgs& a, cudaStream_t s) {
-  const unsigned nb = blocks_for(a.g.N, 256);
   switch (a.ph.K) {
     case 0: return cudaSuccess;
-    case 1: k_advect<1><<<nb, 256, 0, s>>>(a); break;
-    case 2: k_advect<2><<<nb, 256, 0, s>>>(a); break;
-    case 3: k_advect<3><<<nb, 256, 0, s>>>(a); break;
-    case 4: k_advect<4><<<nb, 256, 0, s>>>(a); break;
+    case 1: k_advect<1><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a); break;
+    case 2: k_advect<2><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a); break;
+    case 3: k_advect<3><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a); break;
+    case 4: k_advect<4><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

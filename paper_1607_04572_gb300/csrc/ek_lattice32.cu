@@ -1,0 +1,475 @@
+// S2 and S3 of the FP32-storage form: populations stored as the deviation
+// g_i = f_i - w_i rho0 in float, species as int32 multiples of qscale_k,
+// Phi / Psi / u in float, arithmetic in float.
+//
+// Exact conservation with 4-byte species: every link flux is quantised to an
+// integer number of units and computed with bitwise the same operations from
+// both of its end nodes (symmetric operands, no contraction), so the two ends
+// see exactly opposite integers and the lattice total never changes; the
+// volume-of-fluid shares are likewise computed identically by the source
+// (outflow) and the destination (inflow) thread.
+//
+// Partial-volume flux without divisions: with A = rho_x (1 - Psi_y) and
+// B = rho_y (1 - Psi_x), Eq. 20 becomes
+//   J = D/(A_0 |c|) [(A - B) + z/2 (A + B)(Phi_x - Phi_y + E.c)],
+// which is antisymmetric by construction.
+#include <math.h>
+
+#include "ek_internal.cuh"
+
+namespace ek {
+
+namespace {
+
+__device__ __forceinline__ long long nbr_index(int d, int x, int y, int z, const Nbr& b, int nx,
+                                               int ny) {
+  const int X = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
+  const int Y = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
+  const int Z = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
+  return (long long)X + (long long)nx * ((long long)Y + (long long)ny * Z);
+}
+
+__device__ __forceinline__ float csgnf(int c, float v) { return c > 0 ? v : -v; }
+__device__ __forceinline__ float cdotf(int i, float x, float y, float z) {
+  const int a = dcx(i), b = dcy(i), c = dcz(i);
+  if (a && b) return csgnf(a, x) + csgnf(b, y);
+  if (a && c) return csgnf(a, x) + csgnf(c, z);
+  if (b && c) return csgnf(b, y) + csgnf(c, z);
+  if (a) return csgnf(a, x);
+  if (b) return csgnf(b, y);
+  if (c) return csgnf(c, z);
+  return 0.0f;
+}
+
+// Constants of the FP32 kernels, rounded once on the host.
+struct Phys32 {
+  float rho0, lam_e, lam_o;
+  float qs[EK_MAX_SPECIES];  // density of one species unit
+  float cq[EK_MAX_SPECIES];  // D_k / (A_0 qs_k): flux in units per bracket value
+  float hz[EK_MAX_SPECIES];  // z_k / 2
+  float ec[19];              // E . c_i
+  float g[3];
+  float E[3];
+  float zq[EK_MAX_SPECIES];  // z_k qs_k: charge of one unit of species k
+};
+
+Phys32 make_phys32(const Phys& ph) {
+  Phys32 p;
+  p.rho0 = (float)ph.rho0;
+  p.lam_e = (float)ph.lam_e;
+  p.lam_o = (float)ph.lam_o;
+  for (int k = 0; k < EK_MAX_SPECIES; ++k) {
+    p.qs[k] = (float)ph.qscale[k];
+    p.cq[k] = ph.qscale[k] > 0.0 ? (float)(ph.dcoef[k] / ph.qscale[k]) : 0.0f;
+    p.hz[k] = (float)ph.hz[k];
+  }
+  for (int i = 0; i < 19; ++i) p.ec[i] = (float)ph.ec[i];
+  for (int d = 0; d < 3; ++d) {
+    p.g[d] = (float)ph.g[d];
+    p.E[d] = (float)ph.E[d];
+  }
+  for (int k = 0; k < EK_MAX_SPECIES; ++k) p.zq[k] = (float)(ph.z[k] * ph.qscale[k]);
+  return p;
+}
+
+template <int K, bool PV>
+__device__ __forceinline__ void lb32_node(const LBArgs& a, const Phys32& c, int x, int y, int z,
+                                          double (&iv)[3]) {
+  const float* g_in = (const float*)a.f_in;
+  float* g_out = (float*)a.f_out;
+  const int* n_in = (const int*)a.rho_in;
+  int* n_out = (int*)a.rho_out;
+  const float* phi = (const float*)a.phi;
+  const float* psi = (const float*)a.psi;
+  float* u = (float*)a.u;
+  const long long N = a.g.N;
+  const int nx = a.g.nx, ny = a.g.ny;
+  const long long n = node_index(a.g, x, y, z);
+  float* ifield = (float*)a.ifield;
+  if (a.owner[n] != FLUID) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) n_out[k * N + n] = n_in[k * N + n];
+    u[n] = 0.0f;
+    u[N + n] = 0.0f;
+    u[2 * N + n] = 0.0f;
+    ifield[n] = 0.0f;
+    ifield[N + n] = 0.0f;
+    ifield[2 * N + n] = 0.0f;
+    return;
+  }
+  const Nbr b = make_nbr(x, y, z, a.g);
+
+  // ---- S2a: quantised link fluxes and coupling force ----
+  float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+  int S[K > 0 ? K : 1];
+  float r0[K > 0 ? K : 1];
+  const float om0 = PV ? __fsub_rn(1.0f, psi[n]) : 1.0f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    S[k] = 0;
+    r0[k] = __fmul_rn((float)n_in[k * N + n], c.qs[k]);
+  }
+  if (K > 0) {
+    const float phi0 = phi[n];
+#pragma unroll
+    for (int d = 1; d < Q; ++d) {
+      const long long m = nbr_index(d, x, y, z, b, nx, ny);
+      if (a.owner[m] != FLUID) continue;  // no flux into or out of boundary nodes
+      const float omj = PV ? __fsub_rn(1.0f, psi[m]) : 1.0f;
+      const float dphi = __fadd_rn(__fsub_rn(phi0, phi[m]), c.ec[d]);
+      float tsum = 0.0f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float rb = __fmul_rn((float)n_in[k * N + m], c.qs[k]);
+        const float A = PV ? __fmul_rn(r0[k], omj) : r0[k];
+        const float B = PV ? __fmul_rn(rb, om0) : rb;
+        float br = fmaf(__fadd_rn(A, B), __fmul_rn(c.hz[k], dphi), __fsub_rn(A, B));
+        if (d >= 7) br = __fmul_rn(br, 0.70710678f);
+        S[k] += __float2int_rn(__fmul_rn(br, c.cq[k]));
+        tsum += br;
+      }
+      if (dcx(d)) gx += csgnf(dcx(d), tsum);
+      if (dcy(d)) gy += csgnf(dcy(d), tsum);
+      if (dcz(d)) gz += csgnf(dcz(d), tsum);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) n_out[k * N + n] = n_in[k * N + n] - S[k];
+  // coupling force: sum_k J_k c / (2 D_k) = G / (2 A_0) with the unquantised fluxes
+  constexpr float HALF_INV_A0 = 0.13060193748187072f;
+
+  // ---- S2b: TRT collision on the deviations (pair form) ----
+  float g[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) g[i] = g_in[i * N + n];
+  float ps[Q], pd[Q];
+  float drho = g[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    ps[i] = g[i] + g[i + 1];
+    pd[i] = g[i] - g[i + 1];
+    drho += ps[i];
+    if (dcx(i)) jx += csgnf(dcx(i), pd[i]);
+    if (dcy(i)) jy += csgnf(dcy(i), pd[i]);
+    if (dcz(i)) jz += csgnf(dcz(i), pd[i]);
+  }
+  {
+    // internal solute force: coupling force minus the field's push on the local ion charge
+    float qion = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) qion = fmaf(c.zq[k], (float)n_in[k * N + n], qion);
+    const float ix = gx * HALF_INV_A0 - qion * c.E[0];
+    const float iy = gy * HALF_INV_A0 - qion * c.E[1];
+    const float iz = gz * HALF_INV_A0 - qion * c.E[2];
+    ifield[n] = ix;
+    ifield[N + n] = iy;
+    ifield[2 * N + n] = iz;
+    iv[0] = ix;
+    iv[1] = iy;
+    iv[2] = iz;
+  }
+  const float rho = c.rho0 + drho;
+  const float Fx = fmaf(gx, HALF_INV_A0, c.g[0]);
+  const float Fy = fmaf(gy, HALF_INV_A0, c.g[1]);
+  const float Fz = fmaf(gz, HALF_INV_A0, c.g[2]);
+  const float irho = 1.0f / rho;
+  const float ux = (jx + 0.5f * Fx) * irho;
+  const float uy = (jy + 0.5f * Fy) * irho;
+  const float uz = (jz + 0.5f * Fz) * irho;
+  const float usq = ux * ux + uy * uy + uz * uz;
+  const float uF = ux * Fx + uy * Fy + uz * Fz;
+  const float le = c.lam_e, lo = c.lam_o;
+  const float gg = 2.0f + le;
+  const float qx = fmaf(-lo, jx, Fx), qy = fmaf(-lo, jy, Fy), qz = fmaf(-lo, jz, Fz);
+  // even part relative to w_i rho0: base = -1.5 gg u.F - lambda_e (drho - 1.5 rho u^2)
+  const float base = fmaf(-1.5f * gg, uF, -le * fmaf(-1.5f * rho, usq, drho));
+  const float hle = 0.5f * le, hlo = 0.5f * lo;
+  const float k45 = -4.5f * le * rho;
+  float gs[Q];
+  gs[0] = fmaf(1.0f + le, g[0], (float)wgt(0) * base);
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const float w = (float)wgt(i);
+    const float cu = cdotf(i, ux, uy, uz);
+    const float cf = cdotf(i, Fx, Fy, Fz);
+    const float cq = cdotf(i, qx, qy, qz);
+    const float Ep = w * fmaf(cu, fmaf(4.5f * gg, cf, k45 * cu), base);
+    const float Em = 3.0f * w * cq;
+    const float X = fmaf(hle, ps[i], Ep);
+    const float Y = fmaf(hlo, pd[i], Em);
+    gs[i] = g[i] + (X + Y);
+    gs[i + 1] = g[i + 1] + (X - Y);
+  }
+  if (!isfinite(rho) || !isfinite(usq)) atomicOr(a.status, ST_NONFINITE);
+  u[n] = ux;
+  u[N + n] = uy;
+  u[2 * N + n] = uz;
+
+  // ---- push stream with velocity bounce-back (Eq. 12); the w_i rho0 parts cancel ----
+  g_out[n] = gs[0];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const long long m = nbr_index(i, x, y, z, b, nx, ny);
+    const int om = a.owner[m];
+    if (om == FLUID) {
+      g_out[i * N + m] = gs[i];
+    } else {
+      float cvb = 0.0f;
+      if (om >= 0) {
+        const DevParticle& P = a.parts[om];
+        const int xb = dcx(i) > 0 ? b.xp : (dcx(i) < 0 ? b.xm : x);
+        const int yb = dcy(i) > 0 ? b.yp : (dcy(i) < 0 ? b.ym : y);
+        const int zb = dcz(i) > 0 ? b.zp : (dcz(i) < 0 ? b.zm : z);
+        const double X = (double)(P.lo[0] + wrapi(xb - P.lo[0], nx));
+        const double Y = (double)(P.lo[1] + wrapi(yb - P.lo[1], ny));
+        const double Z = (double)(P.lo[2] + wrapi(zb - P.lo[2], a.g.nz));
+        const double dx = X - P.pos[0], dy = Y - P.pos[1], dz = Z - P.pos[2];
+        const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
+        const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
+        const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
+        cvb = (float)cdot(i, vx, vy, vz);
+      }
+      g_out[opp(i) * N + n] = gs[i] - 6.0f * (float)wgt(i) * c.rho0 * cvb;
+    }
+  }
+}
+
+__device__ __forceinline__ void block_sum3(double (&v)[3], double* ipart) {
+  __shared__ double red[TILE_X * TILE_Y / 32][3];
+  const int t = threadIdx.x + TILE_X * threadIdx.y;
+  const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc) {
+    double s = v[cc];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp][cc] = s;
+  }
+  __syncthreads();
+  if (t == 0) {
+    const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      double s = 0.0;
+      for (int w = 0; w < TILE_X * TILE_Y / 32; ++w) s += red[w][cc];
+      ipart[3 * blk + cc] = s;
+    }
+  }
+}
+
+template <int K, bool PV>
+__global__ void __launch_bounds__(256) k_lb32(LBArgs a, Phys32 c) {
+  const int x = blockIdx.x * TILE_X + threadIdx.x;
+  const int y = blockIdx.y * TILE_Y + threadIdx.y;
+  const int z = blockIdx.z;
+  double iv[3] = {0.0, 0.0, 0.0};
+  if (x < a.g.nx && y < a.g.ny) lb32_node<K, PV>(a, c, x, y, z, iv);
+  block_sum3(iv, a.ipart);
+}
+
+// share of the cell displaced by velocity (vx, vy, vz) that lands at offset
+// (ox, oy, oz) in {0, sign(v_a)}^3; identical operations in the source and the
+// destination thread
+__device__ __forceinline__ float vof_share(float vx, float vy, float vz, int ox, int oy, int oz) {
+  const float wx = ox ? fabsf(vx) : __fsub_rn(1.0f, fabsf(vx));
+  const float wy = oy ? fabsf(vy) : __fsub_rn(1.0f, fabsf(vy));
+  const float wz = oz ? fabsf(vz) : __fsub_rn(1.0f, fabsf(vz));
+  return __fmul_rn(__fmul_rn(wx, wy), wz);
+}
+
+__device__ __forceinline__ int sgnf(float v) { return v > 0.0f ? 1 : (v < 0.0f ? -1 : 0); }
+
+template <int K>
+__global__ void __launch_bounds__(256) k_advect32(LBArgs a, Phys32 c) {
+  const int* n_in = (const int*)a.rho_in;
+  int* n_out = (int*)a.rho_out;
+  const float* u = (const float*)a.u;
+  const long long N = a.g.N;
+  const int x = blockIdx.x * TILE_X + threadIdx.x;
+  const int y = blockIdx.y * TILE_Y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.g.nx || y >= a.g.ny) return;
+  const long long n = node_index(a.g, x, y, z);
+  if (a.owner[n] != FLUID) return;
+  const Nbr b = make_nbr(x, y, z, a.g);
+  int acc[K];
+  float rs[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    acc[k] = n_out[k * N + n];
+    rs[k] = (float)n_in[k * N + n];
+  }
+  const float ux = u[n], uy = u[N + n], uz = u[2 * N + n];
+  const int sx = sgnf(ux), sy = sgnf(uy), sz = sgnf(uz);
+  for (int oz = 0; oz <= (sz != 0); ++oz) {
+    for (int oy = 0; oy <= (sy != 0); ++oy) {
+      for (int ox = 0; ox <= (sx != 0); ++ox) {
+        if (!ox && !oy && !oz) continue;
+        const long long m = node_index(a.g, nb_x(b, x, ox ? sx : 0), nb_y(b, y, oy ? sy : 0),
+                                       nb_z(b, z, oz ? sz : 0));
+        if (a.owner[m] != FLUID) continue;
+        const float frac = vof_share(ux, uy, uz, ox, oy, oz);
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] -= __float2int_rn(__fmul_rn(rs[k], frac));
+      }
+    }
+  }
+  for (int qz = -1; qz <= 1; ++qz) {
+    for (int qy = -1; qy <= 1; ++qy) {
+      for (int qx = -1; qx <= 1; ++qx) {
+        if (!qx && !qy && !qz) continue;
+        const long long m = node_index(a.g, nb_x(b, x, -qx), nb_y(b, y, -qy), nb_z(b, z, -qz));
+        if (a.owner[m] != FLUID) continue;
+        const float vx = u[m], vy = u[N + m], vz = u[2 * N + m];
+        if ((qx && sgnf(vx) != qx) || (qy && sgnf(vy) != qy) || (qz && sgnf(vz) != qz)) continue;
+        const float frac = vof_share(vx, vy, vz, qx != 0, qy != 0, qz != 0);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          acc[k] += __float2int_rn(__fmul_rn((float)n_in[k * N + m], frac));
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) n_out[k * N + n] = acc[k];
+}
+
+__global__ void k_fill32(Grid g, const int* owner, float* f, int* rho, int K, float rho0, int n0,
+                         int n1, int n2, int n3) {
+  const long long N = g.N;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const bool fl = owner[n] == FLUID;
+  const int nk[4] = {n0, n1, n2, n3};
+  for (int k = 0; k < K; ++k) rho[k * N + n] = fl ? nk[k] : 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i * N + n] = fl ? 0.0f : -(float)wgt(i) * rho0;
+}
+
+// field conversions between the FP64 exchange format and the FP32 storage
+__global__ void k_pop_to_f64(long long N, int i, float rho0, const float* g, double* out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N) out[n] = (double)g[i * N + n] + wgt(i) * (double)rho0;
+}
+__global__ void k_pop_from_f64(long long N, int i, float rho0, const double* in, float* g) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N) g[i * N + n] = (float)(in[n] - wgt(i) * (double)rho0);
+}
+__global__ void k_spc_to_f64(long long N, double q, const int* in, double* out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N) out[n] = (double)in[n] * q;
+}
+__global__ void k_spc_from_f64(long long N, double q, const double* in, int* out, int* status) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double v = rint(in[n] / q);
+  if (!(fabs(v) < 2147483647.0)) {
+    atomicOr(status, ST_CAPACITY);
+    out[n] = 0;
+    return;
+  }
+  out[n] = (int)v;
+}
+__global__ void k_f32_to_f64(long long N, const float* in, double* out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N) out[n] = (double)in[n];
+}
+__global__ void k_f64_to_f32(long long N, const double* in, float* out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N) out[n] = (float)in[n];
+}
+// f = f^eq(current rho, u) on fluid nodes, u given in FP64 (3 components)
+__global__ void k_set_velocity32(Grid g, const int* owner, float* f, const double* u3, float rho0) {
+  const long long N = g.N;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N || owner[n] != FLUID) return;
+  double drho = 0.0;
+  for (int i = 0; i < Q; ++i) drho += (double)f[i * N + n];
+  const double rho = (double)rho0 + drho;
+  const double ux = u3[n], uy = u3[N + n], uz = u3[2 * N + n];
+  const double usq = ux * ux + uy * uy + uz * uz;
+  for (int i = 0; i < Q; ++i) {
+    const double cu = cdot(i, ux, uy, uz);
+    f[i * N + n] = (float)(wgt(i) * (drho + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq)));
+  }
+}
+__global__ void k_density32(Grid g, const float* f, float rho0, double* out) {
+  const long long N = g.N;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double s = (double)rho0;
+  for (int i = 0; i < Q; ++i) s += (double)f[i * N + n];
+  out[n] = s;
+}
+
+unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_lb32(const LBArgs& a, cudaStream_t s) {
+  const Phys32 c = make_phys32(a.ph);
+  const bool pv = a.ph.pv != 0;
+  switch (a.ph.K) {
+#define EK_CASE(KK)                                           \
+  case KK:                                                    \
+    if (pv) k_lb32<KK, true><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c);        \
+    else k_lb32<KK, false><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c);          \
+    break;
+    EK_CASE(0)
+    EK_CASE(1)
+    EK_CASE(2)
+    EK_CASE(3)
+    EK_CASE(4)
+#undef EK_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advection32(const LBArgs& a, cudaStream_t s) {
+  const Phys32 c = make_phys32(a.ph);
+  switch (a.ph.K) {
+    case 0: return cudaSuccess;
+    case 1: k_advect32<1><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
+    case 2: k_advect32<2><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
+    case 3: k_advect32<3><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
+    case 4: k_advect32<4><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill32(const Grid& g, const Phys& ph, const int* owner, float* f, int* rho,
+                          const int* units, cudaStream_t s) {
+  k_fill32<<<blocks_for(g.N, 256), 256, 0, s>>>(g, owner, f, rho, ph.K, (float)ph.rho0, units[0],
+                                                   units[1], units[2], units[3]);
+  return cudaGetLastError();
+}
+
+cudaError_t convert32(int op, const Grid& g, int index, double scale, const void* in, void* out,
+                      int* status, cudaStream_t s) {
+  const long long N = g.N;
+  const unsigned nb = blocks_for(N, 256);
+  switch (op) {
+    case CONV_POP_TO_F64: k_pop_to_f64<<<nb, 256, 0, s>>>(N, index, (float)scale, (const float*)in, (double*)out); break;
+    case CONV_POP_FROM_F64: k_pop_from_f64<<<nb, 256, 0, s>>>(N, index, (float)scale, (const double*)in, (float*)out); break;
+    case CONV_SPC_TO_F64: k_spc_to_f64<<<nb, 256, 0, s>>>(N, scale, (const int*)in, (double*)out); break;
+    case CONV_SPC_FROM_F64: k_spc_from_f64<<<nb, 256, 0, s>>>(N, scale, (const double*)in, (int*)out, status); break;
+    case CONV_F32_TO_F64: k_f32_to_f64<<<nb, 256, 0, s>>>(N, (const float*)in, (double*)out); break;
+    case CONV_F64_TO_F32: k_f64_to_f32<<<nb, 256, 0, s>>>(N, (const double*)in, (float*)out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t set_velocity32(const Grid& g, const int* owner, float* f, const double* u3, double rho0,
+                           cudaStream_t s) {
+  k_set_velocity32<<<blocks_for(g.N, 256), 256, 0, s>>>(g, owner, f, u3, (float)rho0);
+  return cudaGetLastError();
+}
+
+cudaError_t density32(const Grid& g, const float* f, double rho0, double* out, cudaStream_t s) {
+  k_density32<<<blocks_for(g.N, 256), 256, 0, s>>>(g, f, (float)rho0, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ek

@@ -140,6 +140,25 @@ __device__ __forceinline__ bool node_inside(int X, int Y, int Z, const DevPartic
   return dist2(dx, dy, dz) < __dmul_rn(P.radius, P.radius);
 }
 
+// typed access to the fields of the two storage forms
+template <class FM>
+__device__ __forceinline__ double pop_abs(const void* f, int i, long long N, long long n, double rho0) {
+  const double v = (double)((const typename FM::pop_t*)f)[(long long)i * N + n];
+  return FM::fp32 ? v + wgt(i) * rho0 : v;
+}
+template <class FM>
+__device__ __forceinline__ double real_at(const void* p, long long n) {
+  return (double)((const typename FM::real_t*)p)[n];
+}
+template <class FM>
+__device__ __forceinline__ void real_set(void* p, long long n, double v) {
+  ((typename FM::real_t*)p)[n] = (typename FM::real_t)v;
+}
+template <class FM>
+__device__ __forceinline__ void real_add(void* p, long long n, double v) {
+  atomicAdd((typename FM::real_t*)p + n, (typename FM::real_t)v);
+}
+
 // block-wide sum of NV doubles, fixed order; result valid in thread 0
 template <int NV>
 __device__ void block_sum(double (&v)[NV]) {
@@ -164,19 +183,76 @@ __device__ void block_sum(double (&v)[NV]) {
 }
 
 // ---------------------------------------------------------------------------
-// S4: forces and integration.  k_particle_forces: grid (particle, chunk of
-// FORCE_CHUNK box cells), one partial sum per CTA; k_particle_integrate: one
-// thread per particle adds the partial sums in chunk order (deterministic)
-// and integrates.
+// S4: forces and integration.
+//   k_force_assign   every fluid node of a particle's widened box records the
+//                    particle with the nearest surface (minimum image): an
+//                    atomicMin on the key (quantised surface distance, index)
+//   k_particle_forces  grid (particle, chunk of FORCE_CHUNK widened-box cells):
+//                    momentum exchange (Eq. 11), the solute force on the
+//                    particle (reaction of the internal solute force on the
+//                    fluid of its nodes) and the field on its own charge
+//   k_particle_integrate  one block: remainder of the solute force on nodes
+//                    no particle claims, split evenly; symplectic Euler
+//   k_key_reset      clears the keys of the widened boxes
+// All sums run in a fixed order, so the result is deterministic.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double min_image(double d, int n) {
+  if (d > 0.5 * (double)n) return d - (double)n;
+  if (d < -0.5 * (double)n) return d + (double)n;
+  return d;
+}
+
+// cell c of the widened box: node index and minimum-image offset from the
+// centre.  Returns true for the first copy of a node (a widened box can be
+// wider than the lattice), so per-node sums count every node once.
+__device__ __forceinline__ bool ext_cell(const DevParticle& P, int c, const Grid& g, int& X, int& Y,
+                                        int& Z, long long& n, double& dx, double& dy, double& dz) {
+  box_coord(c, P.elo, P.ehi, X, Y, Z);
+  const bool first = X - P.elo[0] < g.nx && Y - P.elo[1] < g.ny && Z - P.elo[2] < g.nz;
+  const int x = wrapi(X, g.nx), y = wrapi(Y, g.ny), z = wrapi(Z, g.nz);
+  n = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+  dx = min_image(__dsub_rn((double)x, P.pos[0]), g.nx);
+  dy = min_image(__dsub_rn((double)y, P.pos[1]), g.ny);
+  dz = min_image(__dsub_rn((double)z, P.pos[2]), g.nz);
+  return first;
+}
+
+__global__ void k_force_assign(PartArgs a) {
+  const int p = blockIdx.x;
+  const DevParticle& P = a.parts[p];
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= box_cells(P.elo, P.ehi)) return;
+  int X, Y, Z;
+  long long n;
+  double dx, dy, dz;
+  ext_cell(P, c, a.g, X, Y, Z, n, dx, dy, dz);  // a repeated node gets the same key
+  const double dsurf = __dsub_rn(__dsqrt_rn(dist2(dx, dy, dz)), P.radius);
+  const long long kq = (long long)floor(__dmul_rn(__dadd_rn(dsurf, 1024.0), 1048576.0));
+  const unsigned long long key = ((unsigned long long)kq << 20) | (unsigned long long)p;
+  atomicMin(a.fkey + n, key);
+}
+
+__global__ void k_key_reset(PartArgs a) {
+  const int p = blockIdx.x;
+  const DevParticle& P = a.parts[p];
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= box_cells(P.elo, P.ehi)) return;
+  int X, Y, Z;
+  long long n;
+  double dx, dy, dz;
+  ext_cell(P, c, a.g, X, Y, Z, n, dx, dy, dz);
+  a.fkey[n] = ~0ULL;
+}
+
+template <class FM>
 __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
   const int p = blockIdx.x;
   const DevParticle& P = a.parts[p];
   const Grid g = a.g;
   const long long N = g.N;
-  const int ncell = box_cells(P.lo, P.hi);
+  const int ncell = box_cells(P.elo, P.ehi);
   const int c = blockIdx.y * FORCE_CHUNK + threadIdx.x;
-  if (blockIdx.y * FORCE_CHUNK >= ncell) return;  // whole CTA beyond the box
+  if (blockIdx.y * FORCE_CHUNK >= ncell) return;  // whole CTA beyond the widened box
   const bool pv = a.ph.pv != 0;
   double qnorm = 0.0;
   if (pv) {
@@ -186,16 +262,19 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
   } else {
     qnorm = P.nb > 0 ? P.charge / (double)P.nb : 0.0;
   }
-  // Fh(3) Th(3) Fe(3) Te(3)
-  double acc[12];
+  // Fh Th | Fs Ts | Fq Tq
+  double acc[FPART];
 #pragma unroll
-  for (int j = 0; j < 12; ++j) acc[j] = 0.0;
+  for (int j = 0; j < FPART; ++j) acc[j] = 0.0;
+  int X, Y, Z;
+  long long n;
+  double mx, my, mz;
   if (c < ncell) {
-    int X, Y, Z;
-    box_coord(c, P.lo, P.hi, X, Y, Z);
-    const long long n = node_of(X, Y, Z, g);
+    const bool first = ext_cell(P, c, g, X, Y, Z, n, mx, my, mz);
     const int own = a.owner[n];
-    if (own == FLUID) {
+    const bool in_box = X >= P.lo[0] && X < P.hi[0] && Y >= P.lo[1] && Y < P.hi[1] &&
+                        Z >= P.lo[2] && Z < P.hi[2];
+    if (own == FLUID && in_box) {
       // momentum exchange on every link from this fluid node into the particle (Eq. 11)
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
@@ -208,7 +287,7 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
         const double vby = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
         const double vbz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
         const double cvb = cdot(i, vbx, vby, vbz);
-        const double refl = a.f[(long long)opp(i) * N + n];
+        const double refl = pop_abs<FM>(a.f, opp(i), N, n, a.ph.rho0);
         const double fs = refl + 6.0 * wgt(i) * a.ph.rho0 * cvb;  // the population that hit the wall
         const double mom = fs + refl;
         const double px = dcx(i) ? csgn(dcx(i), mom) : 0.0;
@@ -222,64 +301,119 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
         acc[5] += dx * py - dy * px;
       }
     }
-    // electrostatic force on the particle's charge in this cell
-    double qq = 0.0;
-    if (pv) qq = qnorm * a.psibox[(long long)p * a.boxmax + c];
-    else if (own == p) qq = qnorm;
-    if (qq != 0.0) {
-      const long long nxp = node_of(X + 1, Y, Z, g), nxm = node_of(X - 1, Y, Z, g);
-      const long long nyp = node_of(X, Y + 1, Z, g), nym = node_of(X, Y - 1, Z, g);
-      const long long nzp = node_of(X, Y, Z + 1, g), nzm = node_of(X, Y, Z - 1, g);
-      const double gx = 0.5 * (a.phi[nxp] - a.phi[nxm]);
-      const double gy = 0.5 * (a.phi[nyp] - a.phi[nym]);
-      const double gz = 0.5 * (a.phi[nzp] - a.phi[nzm]);
-      const double frx = qq * (a.ph.E[0] - gx), fry = qq * (a.ph.E[1] - gy), frz = qq * (a.ph.E[2] - gz);
-      const double dx = (double)X - P.pos[0], dy = (double)Y - P.pos[1], dz = (double)Z - P.pos[2];
-      acc[6] += frx;
-      acc[7] += fry;
-      acc[8] += frz;
-      acc[9] += dy * frz - dz * fry;
-      acc[10] += dz * frx - dx * frz;
-      acc[11] += dx * fry - dy * frx;
+    // reaction of the internal solute force on the fluid nodes this particle claims
+    if (first && own == FLUID && (int)(a.fkey[n] & 0xFFFFFull) == p) {
+      const double ix = real_at<FM>(a.ifield, n);
+      const double iy = real_at<FM>(a.ifield, N + n);
+      const double iz = real_at<FM>(a.ifield, 2 * N + n);
+      acc[6] -= ix;
+      acc[7] -= iy;
+      acc[8] -= iz;
+      acc[9] -= my * iz - mz * iy;
+      acc[10] -= mz * ix - mx * iz;
+      acc[11] -= mx * iy - my * ix;
+    }
+    // the external field on the particle's own charge in this cell
+    if (in_box) {
+      double qq = 0.0;
+      if (pv) {
+        const int bx = P.hi[0] - P.lo[0], by = P.hi[1] - P.lo[1];
+        const int cb = (X - P.lo[0]) + bx * ((Y - P.lo[1]) + by * (Z - P.lo[2]));
+        qq = qnorm * a.psibox[(long long)p * a.boxmax + cb];
+      } else if (own == p) {
+        qq = qnorm;
+      }
+      if (qq != 0.0) {
+        const double fx = qq * a.ph.E[0], fy = qq * a.ph.E[1], fz = qq * a.ph.E[2];
+        const double dx = (double)X - P.pos[0], dy = (double)Y - P.pos[1], dz = (double)Z - P.pos[2];
+        acc[12] += fx;
+        acc[13] += fy;
+        acc[14] += fz;
+        acc[15] += dy * fz - dz * fy;
+        acc[16] += dz * fx - dx * fz;
+        acc[17] += dx * fy - dy * fx;
+      }
     }
   }
-  block_sum<12>(acc);
+  block_sum<FPART>(acc);
   if (threadIdx.x == 0) {
-    double* out = a.fpart + ((long long)p * a.fchunks + blockIdx.y) * 12;
+    double* out = a.fpart + ((long long)p * a.fchunks + blockIdx.y) * FPART;
 #pragma unroll
-    for (int j = 0; j < 12; ++j) out[j] = acc[j];
+    for (int j = 0; j < FPART; ++j) out[j] = acc[j];
   }
 }
 
-__global__ void k_particle_integrate(PartArgs a) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.P) return;
-  DevParticle& P = a.parts[p];
-  const int nchunk = (box_cells(P.lo, P.hi) + FORCE_CHUNK - 1) / FORCE_CHUNK;
-  double acc[12];
-  for (int j = 0; j < 12; ++j) acc[j] = 0.0;
-  for (int ch = 0; ch < nchunk; ++ch) {
-    const double* v = a.fpart + ((long long)p * a.fchunks + ch) * 12;
-    for (int j = 0; j < 12; ++j) acc[j] += v[j];
+constexpr int INTEGRATE_T = 512;
+constexpr int PSUM_T = 256;
+
+// Block p < P: the chunk partials of particle p, summed in a fixed order into
+// psum[p]; block P: the lattice-block sums of the internal solute force into
+// psum[P].  Thread t takes the items t, t + PSUM_T, ...; then a fixed tree.
+__global__ void __launch_bounds__(PSUM_T) k_psum(PartArgs a) {
+  __shared__ double red[PSUM_T];
+  const int p = blockIdx.x;
+  const bool lattice = p == a.P;
+  const int nitem = lattice ? a.nipart
+                            : (box_cells(a.parts[p].elo, a.parts[p].ehi) + FORCE_CHUNK - 1) / FORCE_CHUNK;
+  const int ncomp = lattice ? 3 : FPART;
+  for (int j = 0; j < ncomp; ++j) {
+    double v = 0.0;
+    for (int it = threadIdx.x; it < nitem; it += PSUM_T)
+      v += lattice ? a.ipart[3 * it + j] : a.fpart[((long long)p * a.fchunks + it) * FPART + j];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = PSUM_T / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) a.psum[(long long)p * FPART + j] = red[0];
+    __syncthreads();
   }
-  double F[3], T[3];
-  for (int d = 0; d < 3; ++d) {
-    F[d] = acc[d] + acc[6 + d] + P.ftrans[d];
-    T[d] = acc[3 + d] + acc[9 + d];
-    P.force[d] = F[d];
-    P.torque[d] = T[d];
-    P.ftrans[d] = 0.0;
+}
+
+__device__ __forceinline__ double block_sum_one(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+// remainder of the solute force (lattice total minus what the particles
+// claimed), split evenly; then symplectic Euler, one thread per particle
+__global__ void __launch_bounds__(INTEGRATE_T) k_particle_integrate(PartArgs a) {
+  __shared__ double red[INTEGRATE_T / 32];
+  double claimed[3] = {0.0, 0.0, 0.0};
+  for (int p = threadIdx.x; p < a.P; p += blockDim.x)
+    for (int d = 0; d < 3; ++d) claimed[d] -= a.psum[(long long)p * FPART + 6 + d];
+  double rem[3];
+  for (int d = 0; d < 3; ++d)
+    rem[d] = (a.psum[(long long)a.P * FPART + d] - block_sum_one(claimed[d], red)) / (double)a.P;
+  for (int p = threadIdx.x; p < a.P; p += blockDim.x) {
+    DevParticle& P = a.parts[p];
+    const double* acc = a.psum + (long long)p * FPART;
+    double F[3], T[3];
+    for (int d = 0; d < 3; ++d) {
+      F[d] = acc[d] + acc[6 + d] + acc[12 + d] - rem[d] + P.ftrans[d];
+      T[d] = acc[3 + d] + acc[9 + d] + acc[15 + d];
+      P.force[d] = F[d];
+      P.torque[d] = T[d];
+      P.ftrans[d] = 0.0;
+    }
+    if (P.fixed) continue;
+    const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
+    for (int d = 0; d < 3; ++d) {
+      P.vel[d] = P.vel[d] + F[d] / P.mass;
+      P.omega[d] = P.omega[d] + T[d] / P.inertia;
+      P.pos[d] = P.pos[d] + P.vel[d];
+      if (P.pos[d] >= (double)nn[d]) P.pos[d] -= (double)nn[d];
+      else if (P.pos[d] < 0.0) P.pos[d] += (double)nn[d];
+    }
+    if (!isfinite(P.pos[0] + P.pos[1] + P.pos[2])) atomicOr(a.status, ST_NONFINITE);
   }
-  if (P.fixed) return;
-  const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
-  for (int d = 0; d < 3; ++d) {
-    P.vel[d] = P.vel[d] + F[d] / P.mass;
-    P.omega[d] = P.omega[d] + T[d] / P.inertia;
-    P.pos[d] = P.pos[d] + P.vel[d];
-    if (P.pos[d] >= (double)nn[d]) P.pos[d] -= (double)nn[d];
-    else if (P.pos[d] < 0.0) P.pos[d] += (double)nn[d];
-  }
-  if (!isfinite(P.pos[0] + P.pos[1] + P.pos[2])) atomicOr(a.status, ST_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------
@@ -289,13 +423,23 @@ __global__ void k_box_update(PartArgs a, bool setup) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.P) return;
   DevParticle& P = a.parts[p];
+  const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
   for (int d = 0; d < 3; ++d) {
     const int lo = (int)floor(P.pos[d] - P.radius) - 1;
     const int hi = (int)floor(P.pos[d] + P.radius) + 2;
-    P.ulo[d] = setup ? lo : min(lo, P.lo[d]);
-    P.uhi[d] = setup ? hi : max(hi, P.hi[d]);
+    // the previous box, moved into the periodic image of the new one (the
+    // position wraps when the particle crosses the boundary)
+    int olo = P.lo[d], ohi = P.hi[d];
+    const int shift = (int)rint((double)(lo - olo) / (double)nn[d]) * nn[d];
+    olo += shift;
+    ohi += shift;
+    P.ulo[d] = setup ? lo : min(lo, olo);
+    P.uhi[d] = setup ? hi : max(hi, ohi);
     P.lo[d] = lo;
     P.hi[d] = hi;
+    const int m = (int)ceil(P.radius) + FORCE_MARGIN;
+    P.elo[d] = lo - m;
+    P.ehi[d] = hi + m;
   }
   P.psisum = 0.0;
   P.nb = 0;
@@ -311,6 +455,7 @@ __global__ void k_save_prev(PartArgs a) {
   a.owner_prev[n] = a.owner[n];
 }
 
+template <class FM>
 __global__ void k_clear(PartArgs a) {
   const DevParticle& P = a.parts[blockIdx.x];
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
@@ -319,21 +464,23 @@ __global__ void k_clear(PartArgs a) {
   box_coord(c, P.ulo, P.uhi, X, Y, Z);
   const long long n = node_of(X, Y, Z, a.g);
   if (a.owner[n] >= 0) a.owner[n] = FLUID;
-  a.psi[n] = 0.0;
-  a.qpart[n] = 0.0;
+  real_set<FM>(a.psi, n, 0.0);
+  real_set<FM>(a.qpart, n, 0.0);
 }
 
+template <class FM>
 __global__ void k_reset_all(PartArgs a) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.g.N) return;
   a.owner[n] = (a.wall && a.wall[n]) ? WALL : FLUID;
-  a.psi[n] = 0.0;
-  a.qpart[n] = 0.0;
+  real_set<FM>(a.psi, n, 0.0);
+  real_set<FM>(a.qpart, n, 0.0);
 }
 
 // boundary nodes (cell centre strictly inside) and the level-0 octree test of
 // every cell of the current box; cells cut by the surface are queued for
 // k_psi_surface
+template <class FM>
 __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
   const int p = blockIdx.x;
   DevParticle& P = a.parts[p];
@@ -358,7 +505,7 @@ __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
     if (s0 < 0) s0 = classify((double)X, (double)Y, (double)Z, 0.5, P.pos, R2);
     if (s0 == CUBE_IN) {
       ps = 1.0;
-      atomicAdd(a.psi + n, 1.0);
+      real_add<FM>(a.psi, n, 1.0);
     } else if (s0 == CUBE_UNDECIDED) {
       const int slot = atomicAdd(a.surf_count, 1);
       if (slot < a.surf_cap) a.surf[slot] = make_int2(p, c);
@@ -376,6 +523,7 @@ __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
 
 constexpr int PSI_WARPS = 4;  // warps per CTA of k_psi_surface
 
+template <class FM>
 __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
   __shared__ unsigned short queue[PSI_WARPS][2][512];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -432,10 +580,10 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
     }
     for (int o = 16; o > 0; o >>= 1) units += __shfl_xor_sync(0xffffffffu, units, o);
     if (lane == 0 && units > 0) {
-      const double ps = ldexp((double)units, -13);  // units / PSI_UNITS
+      const double ps = (double)units / (double)PSI_UNITS;  // exact: a power of 2
       const long long n = node_of(X, Y, Z, a.g);
       a.psibox[(long long)pc.x * a.boxmax + pc.y] = ps;
-      atomicAdd(a.psi + n, ps);
+      real_add<FM>(a.psi, n, ps);  // dyadic with 13 fraction bits: exact in float too
       atomicAdd(&P.psisum, ps);
     }
     __syncwarp();
@@ -443,6 +591,7 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
 }
 
 // Psi-smeared particle charge (Eq. 21), or spread over the boundary nodes
+template <class FM>
 __global__ void k_charge_scatter(PartArgs a) {
   const int p = blockIdx.x;
   const DevParticle& P = a.parts[p];
@@ -453,7 +602,7 @@ __global__ void k_charge_scatter(PartArgs a) {
   const long long n = node_of(X, Y, Z, a.g);
   // all Psi_p have been added (k_claim): clamp the sum to 1 once, so readers
   // of psi need no min (idempotent where boxes overlap)
-  if (a.psi[n] > 1.0) a.psi[n] = 1.0;
+  if (real_at<FM>(a.psi, n) > 1.0) real_set<FM>(a.psi, n, 1.0);
   double q = 0.0;
   if (a.ph.pv) {
     const double ps = a.psibox[(long long)p * a.boxmax + c];
@@ -466,7 +615,7 @@ __global__ void k_charge_scatter(PartArgs a) {
     if (a.owner[n] != p || P.nb == 0) return;
     q = P.charge / (double)P.nb;
   }
-  atomicAdd(a.qpart + n, q);
+  real_add<FM>(a.qpart, n, q);
 }
 
 __device__ __forceinline__ bool steady_fluid(const PartArgs& a, long long m) {
@@ -475,8 +624,14 @@ __device__ __forceinline__ bool steady_fluid(const PartArgs& a, long long m) {
 
 // Newly covered / uncovered nodes of particle p (Sec. III.B, III.D.1).  Solute
 // transfers are computed from the values before the transitions and recorded;
-// k_apply_transfers adds them afterwards.
+// k_apply_transfers adds them afterwards.  FP32 form: species are integers and
+// every split is an integer split (the remainder of an expulsion goes one
+// unit each to the first receivers in direction order), so the totals stay
+// exact.
+template <class FM>
 __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
+  using pop_t = typename FM::pop_t;
+  using spc_t = typename FM::spc_t;
   const int p = blockIdx.x;
   DevParticle& P = a.parts[p];
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
@@ -491,6 +646,9 @@ __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
   const bool uncovered = old == p && nw == FLUID;
   if (!covered && !uncovered) return;
   const int K = a.ph.K;
+  const double rho0 = a.ph.rho0;
+  pop_t* f = (pop_t*)a.f;
+  const spc_t* rho = (const spc_t*)a.rho;
   long long rec[Q];
   int nf = 0;
 #pragma unroll
@@ -503,11 +661,11 @@ __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
     double mx = 0.0, my = 0.0, mz = 0.0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const double fi = a.fw[(long long)i * N + n];
+      const double fi = pop_abs<FM>(f, i, N, n, rho0);
       if (dcx(i)) mx += csgn(dcx(i), fi);
       if (dcy(i)) my += csgn(dcy(i), fi);
       if (dcz(i)) mz += csgn(dcz(i), fi);
-      a.fw[(long long)i * N + n] = 0.0;
+      f[(long long)i * N + n] = FM::fp32 ? (pop_t)(-wgt(i) * rho0) : (pop_t)0;
     }
     atomicAdd(&P.ftrans[0], mx);
     atomicAdd(&P.ftrans[1], my);
@@ -524,28 +682,34 @@ __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
     }
     Transfer self;
     self.node = n;
-    double share[EK_MAX_SPECIES];
-    for (int k = 0; k < EK_MAX_SPECIES; ++k) {
-      const double r = k < K ? a.rho[k * N + n] : 0.0;
-      self.amount[k] = -r;
-      share[k] = r / (double)nf;
-    }
+    for (int k = 0; k < EK_MAX_SPECIES; ++k) self.amount[k] = k < K ? -(double)rho[k * N + n] : 0.0;
     a.xfer[slot] = self;
     for (int j = 0; j < nf; ++j) {
       Transfer t;
       t.node = rec[j];
-      for (int k = 0; k < EK_MAX_SPECIES; ++k) t.amount[k] = share[k];
+      for (int k = 0; k < EK_MAX_SPECIES; ++k) {
+        if (k >= K) {
+          t.amount[k] = 0.0;
+        } else if (FM::fp32) {
+          const int r = (int)rho[k * N + n];
+          const int share = r / nf, rem = r - share * nf;  // rem has the sign of r
+          const int extra = (j < (rem < 0 ? -rem : rem)) ? (rem < 0 ? -1 : 1) : 0;
+          t.amount[k] = (double)(share + extra);
+        } else {
+          t.amount[k] = (double)rho[k * N + n] / (double)nf;
+        }
+      }
       a.xfer[slot + 1 + j] = t;
     }
   } else {
     // created fluid: f^eq(mean neighbour density, v_b), momentum taken from the particle
-    double rbar = a.ph.rho0;
+    double rbar = rho0;
     if (nf > 0) {
       double s = 0.0;
       for (int j = 0; j < nf; ++j) {
         double d = 0.0;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) d += a.fw[(long long)i * N + rec[j]];
+        for (int i = 0; i < Q; ++i) d += pop_abs<FM>(f, i, N, rec[j], rho0);
         s += d;
       }
       rbar = s / (double)nf;
@@ -563,8 +727,11 @@ __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double cu = cdot(i, vx, vy, vz);
-      const double fi = wgt(i) * rbar * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-      a.fw[(long long)i * N + n] = fi;
+      const double shape = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
+      const double fi = wgt(i) * rbar * (1.0 + shape);
+      // FP32 form stores the deviation from w_i rho0, formed without cancellation
+      f[(long long)i * N + n] =
+          FM::fp32 ? (pop_t)(wgt(i) * ((rbar - rho0) + rbar * shape)) : (pop_t)fi;
       if (dcx(i)) mx += csgn(dcx(i), fi);
       if (dcy(i)) my += csgn(dcy(i), fi);
       if (dcz(i)) mz += csgn(dcz(i), fi);
@@ -584,7 +751,11 @@ __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
       give.node = rec[j];
       take.node = n;
       for (int k = 0; k < EK_MAX_SPECIES; ++k) {
-        const double sh = k < K ? a.rho[k * N + rec[j]] / (double)(nf + 1) : 0.0;
+        double sh = 0.0;
+        if (k < K) {
+          if (FM::fp32) sh = (double)((int)rho[k * N + rec[j]] / (nf + 1));
+          else sh = (double)rho[k * N + rec[j]] / (double)(nf + 1);
+        }
         give.amount[k] = -sh;
         take.amount[k] = sh;
       }
@@ -594,27 +765,36 @@ __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
   }
 }
 
+template <class FM>
 __global__ void k_apply_transfers(PartArgs a) {
+  using spc_t = typename FM::spc_t;
+  spc_t* rho = (spc_t*)a.rho;
   const int count = min(*a.xfer_count, a.xfer_cap);
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < count; r += gridDim.x * blockDim.x) {
     const Transfer t = a.xfer[r];
-    for (int k = 0; k < a.ph.K; ++k) atomicAdd(a.rho + k * a.g.N + t.node, t.amount[k]);
+    for (int k = 0; k < a.ph.K; ++k) {
+      if (FM::fp32) atomicAdd((int*)rho + k * a.g.N + t.node, (int)t.amount[k]);
+      else atomicAdd((double*)rho + k * a.g.N + t.node, t.amount[k]);
+    }
   }
 }
 
-}  // namespace
-
-cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s) {
-  if (a.P == 0) return cudaSuccess;
-  k_particle_forces<<<dim3(a.P, a.fchunks), FORCE_CHUNK, 0, s>>>(a);
-  k_particle_integrate<<<(a.P + 127) / 128, 128, 0, s>>>(a);
+template <class FM>
+cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s) {
+  const unsigned echunks = (unsigned)((a.emax + PT - 1) / PT);
+  k_force_assign<<<dim3(a.P, echunks), PT, 0, s>>>(a);
+  k_particle_forces<FM><<<dim3(a.P, a.fchunks), FORCE_CHUNK, 0, s>>>(a);
+  k_psum<<<a.P + 1, PSUM_T, 0, s>>>(a);
+  k_particle_integrate<<<1, INTEGRATE_T, 0, s>>>(a);
+  k_key_reset<<<dim3(a.P, echunks), PT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s) {
+template <class FM>
+cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s) {
   const Grid& g = a.g;
   if (!transitions) {
-    k_reset_all<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(a);
+    k_reset_all<FM><<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(a);
   }
   if (a.P == 0) return cudaGetLastError();
   k_box_update<<<(a.P + 127) / 128, 128, 0, s>>>(a, !transitions);
@@ -624,18 +804,29 @@ cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s) {
   const unsigned bchunks = (unsigned)((a.boxmax + PT - 1) / PT);
   if (transitions) {
     k_save_prev<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
-    k_clear<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
+    k_clear<FM><<<dim3(a.P, uchunks), PT, 0, s>>>(a);
   }
   cudaMemsetAsync(a.surf_count, 0, sizeof(int), s);
-  k_claim<<<dim3(a.P, bchunks), PT, 0, s>>>(a);
-  k_psi_surface<<<4 * 152, 32 * PSI_WARPS, 0, s>>>(a);
-  k_charge_scatter<<<dim3(a.P, bchunks), PT, 0, s>>>(a);
+  k_claim<FM><<<dim3(a.P, bchunks), PT, 0, s>>>(a);
+  k_psi_surface<FM><<<4 * 152, 32 * PSI_WARPS, 0, s>>>(a);
+  k_charge_scatter<FM><<<dim3(a.P, bchunks), PT, 0, s>>>(a);
   if (transitions) {
-    k_transitions<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
-    k_apply_transfers<<<152, 256, 0, s>>>(a);
+    k_transitions<FM><<<dim3(a.P, uchunks), PT, 0, s>>>(a);
+    k_apply_transfers<FM><<<152, 256, 0, s>>>(a);
     cudaMemsetAsync(a.xfer_count, 0, sizeof(int), s);
   }
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s) {
+  if (a.P == 0) return cudaSuccess;
+  return a.ph.fp32 ? particle_forces_t<FormF32>(a, s) : particle_forces_t<FormF64>(a, s);
+}
+
+cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s) {
+  return a.ph.fp32 ? reflag_t<FormF32>(a, transitions, s) : reflag_t<FormF64>(a, transitions, s);
 }
 
 }  // namespace ek

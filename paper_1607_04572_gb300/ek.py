@@ -22,6 +22,7 @@ EK_PV = 1
 EK_VACATE_ZERO = 2
 EK_CHARGE_NORM_VP = 4
 EK_NEUTRALIZE = 8
+EK_FP32 = 16
 
 # ek_field
 FIELD_SPECIES = 0

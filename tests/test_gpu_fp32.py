@@ -1,0 +1,106 @@
+"""FP32-storage form (populations as float deviations, int32 fixed-point
+species): exact species conservation, agreement with the FP64 oracle at FP32
+tolerance, and the particle mobility within 1e-3 of the FP64 form."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import ek_oracle as O
+from pairs import make_pair, perm_to_oracle, rel_err
+
+pytestmark = pytest.mark.gpu
+
+FP32 = 16
+TOL32 = 2e-4  # per element, floor 1e-3 of the field's max (FP32 rounding ~6e-8 per op, species units 2^-20 of bulk)
+
+
+def totals(ek, s, K):
+    return np.array([s.get_fields(ek.FIELD_SPECIES, k).sum() for k in range(K)])
+
+
+def test_fp32_fields_match_oracle(gpu_lib):
+    ek = gpu_lib
+    case = workloads.small_case(n=(16, 16, 16), radius=3.0, charge=-20.0)
+    o, s = make_pair(ek, case, flags=O.PV | O.NEUTRALIZE | FP32, vel=[(0.02, -0.01, 0.01)])
+    for _ in range(2):
+        o.step(5)
+        s.step(5)
+        assert np.array_equal(s.get_fields(ek.FIELD_OWNER), o.owner.astype(float))
+        fluid = o.owner == O.FLUID
+        for k in range(o.K):
+            assert rel_err(s.get_fields(ek.FIELD_SPECIES, k), o.rho[k]) < TOL32
+        fg = s.get_fields(ek.FIELD_POPULATIONS)[perm_to_oracle(ek)]
+        assert rel_err(fg[:, fluid], o.f[:, fluid]) < 1e-5
+        assert rel_err(s.get_fields(ek.FIELD_PHI), o.phi) < TOL32
+        assert rel_err(s.get_fields(ek.FIELD_PSI), o.psi) == 0.0
+        u = s.get_fields(ek.FIELD_VELOCITY)
+        assert rel_err(u[:, fluid], o.u[:, fluid], floor=1.0) < 1e-3
+        p = s.get_particles()[0]
+        assert np.max(np.abs(p["pos"] - o.particles[0].pos)) < 1e-6
+        assert np.max(np.abs(p["vel"] - o.particles[0].vel)) < 1e-3 * np.max(np.abs(o.particles[0].vel))
+
+
+def test_fp32_species_conserved_exactly(gpu_lib):
+    """A heavy sphere dragged across cells: every covering, uncovering, flux and
+    advection moves whole units, so the totals never change, bit for bit."""
+    ek = gpu_lib
+    case = workloads.small_case(n=(16, 16, 16), radius=3.0, charge=-10.0)
+    o, s = make_pair(ek, case, flags=O.PV | O.NEUTRALIZE | FP32, vel=[(0.06, 0.025, -0.015)],
+                     rho_p=1e9, perturb=0.0)
+    N0 = totals(ek, s, 2)
+    owner0 = s.get_fields(ek.FIELD_OWNER)
+    flips = 0
+    for _ in range(12):
+        s.step(5)
+        assert np.array_equal(totals(ek, s, 2), N0)
+        ow = s.get_fields(ek.FIELD_OWNER)
+        flips += int((ow != owner0).sum())
+        owner0 = ow
+    assert flips > 20
+
+
+@pytest.mark.parametrize("flags", [O.NEUTRALIZE | FP32, O.PV | O.NEUTRALIZE | O.VACATE_ZERO | FP32])
+def test_fp32_conservation_scheme_variants(gpu_lib, flags):
+    ek = gpu_lib
+    case = workloads.small_case(n=(16, 16, 16), radius=3.0, charge=-10.0)
+    o, s = make_pair(ek, case, flags=flags, vel=[(0.07, 0.0, 0.02)], rho_p=1e9, perturb=0.01)
+    N0 = totals(ek, s, 2)
+    s.step(40)
+    assert np.array_equal(totals(ek, s, 2), N0)
+
+
+def _run_form(ek, w, flags, steps):
+    s = ek.EKSystem(w["shape"], nu=w["nu"], rho0=w["rho0"], bjerrum=w["bjerrum"],
+                    valence=w["valence"], D=w["D"], bulk=w["bulk"], flags=flags)
+    for p in w["particles"]:
+        s.add_particle(p["pos"], radius=p["radius"], charge=p["charge"], rho_p=w["rho_p"])
+    s.set_field(ek.FIELD_E_EXT, np.array(w["E"]))
+    N0 = totals(ek, s, len(w["valence"]))
+    s.step(steps)
+    return s, N0
+
+
+def test_fp32_mobility_matches_fp64_small_workload(gpu_lib):
+    """32^3, R = 4, Z = -50, E = 0.01: the particle velocity (the mobility
+    observable) of the FP32 form within 1e-3 of the FP64 form after 400 steps."""
+    ek = gpu_lib
+    w = workloads.workload("small")
+    s64, _ = _run_form(ek, w, ek.EK_PV | ek.EK_NEUTRALIZE, 400)
+    s32, N0 = _run_form(ek, w, ek.EK_PV | ek.EK_NEUTRALIZE | FP32, 400)
+    v64 = s64.get_particles()[0]["vel"]
+    v32 = s32.get_particles()[0]["vel"]
+    assert abs(v32[0] - v64[0]) <= 1e-3 * abs(v64[0])
+    assert np.linalg.norm(v32 - v64) <= 1e-3 * np.linalg.norm(v64)
+    assert np.array_equal(totals(ek, s32, 2), N0)
+
+
+def test_fp32_single_workload_full_size(gpu_lib):
+    ek = gpu_lib
+    w = workloads.workload("single")
+    s64, _ = _run_form(ek, w, ek.EK_PV | ek.EK_NEUTRALIZE, 100)
+    s32, N0 = _run_form(ek, w, ek.EK_PV | ek.EK_NEUTRALIZE | FP32, 100)
+    v64 = s64.get_particles()[0]["vel"]
+    v32 = s32.get_particles()[0]["vel"]
+    assert np.linalg.norm(v32 - v64) <= 1e-3 * np.linalg.norm(v64)
+    assert np.array_equal(totals(ek, s32, 2), N0)
+    assert v32[0] < 0.0

@@ -50,6 +50,7 @@ def test_stages_one_by_one(gpu_lib):
     # S2 + S3
     J = o.link_fluxes()
     fext = o.coupling_force(J)
+    Fs, Ts = o.solute_forces(fext)
     fnew, u, Fh, Th = o.lb_step(fext)
     adv = o.advection(u)
     o.rho = o.rho - J[:, 1:].sum(axis=1) + adv
@@ -57,7 +58,7 @@ def test_stages_one_by_one(gpu_lib):
     s.run_stage(2)
     compare(ek, o, s, what=("species", "populations", "velocity", "phi", "owner", "psi"))
     # S4
-    o.integrate(Fh, Th)
+    o.integrate(Fh, Th, Fs, Ts)
     s.run_stage(4)
     compare(ek, o, s, what=("particles",))
     # S5
@@ -212,3 +213,20 @@ def test_errors_are_status_codes(gpu_lib):
     assert e.value.code == -5
     with pytest.raises(ek.EKError):
         ek.EKSystem((10, 16, 16))  # 10 = 2 * 5 is not 2^a 3^b
+
+
+def test_particle_crosses_periodic_boundary(gpu_lib):
+    """A heavy sphere pushed across the x = 0 seam (and y): the boxes of the
+    previous and the current position lie in different periodic images."""
+    ek = gpu_lib
+    case = workloads.small_case(n=(16, 16, 16), radius=3.0, charge=-10.0)
+    case["particles"][0]["pos"] = [0.9, 15.6, 7.3]
+    o, s = make_pair(ek, case, vel=[(-0.09, 0.08, 0.01)], rho_p=1e9, perturb=0.0)
+    N0 = o.total_species().copy()
+    for _ in range(6):
+        o.step(5)
+        s.step(5)
+        compare(ek, o, s)
+    assert o.particles[0].pos[0] > 8.0  # wrapped to the far side
+    tot = np.array([s.get_fields(ek.FIELD_SPECIES, k).sum() for k in range(o.K)])
+    assert np.allclose(tot, N0, rtol=1e-12, atol=0)

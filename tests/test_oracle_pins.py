@@ -519,3 +519,60 @@ def test_brute_force_against_naive_loops():
         (f + o.g.reshape(3, 1, 1, 1) * (o.owner == -1)).sum(axis=(1, 2, 3))
     mom_after = np.array([(O.CV[:, a][:, None, None, None] * fnew).sum() for a in range(3)])
     assert np.allclose(mom_before - mom_after, Fh[0], atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# momentum balance with charges: the solute is massless, so the particle's
+# solute force is the reaction of the solute's force on the fluid, and the
+# total momentum of fluid + particles changes only by E times the total charge
+# --------------------------------------------------------------------------
+def test_total_momentum_conserved_with_charges():
+    o = EKOracle(16, 16, 16, bulk=(1e-3, 1e-3))
+    o.E = np.array([0.01, 0.003, -0.002])
+    o.add_particle((8.3, 7.9, 8.1), vel=(0.01, 0.0, 0.0), radius=3.0, charge=-15.0)
+    p = o.particles[0]
+
+    def total():
+        return o.fluid_momentum() + p.mass * p.vel + p.f_trans
+
+    P0 = total()
+    for _ in range(40):
+        o.step()
+        assert np.allclose(total(), P0, rtol=0, atol=1e-12)
+    assert abs(p.vel[0] - 0.01) > 1e-3  # the particle did respond to the field
+
+
+def test_momentum_two_particles_and_remainder():
+    """Two spheres: the per-particle split (nearest surface in the widened
+    boxes plus the evenly shared remainder) keeps the total exact."""
+    o = EKOracle(24, 16, 16, bulk=(1e-3, 1e-3))
+    o.E = np.array([0.01, 0.0, 0.0])
+    o.add_particle((5.3, 7.9, 8.1), radius=2.5, charge=-10.0)
+    o.add_particle((16.7, 8.4, 7.2), radius=2.5, charge=-6.0)
+
+    def total():
+        s = o.fluid_momentum()
+        for p in o.particles:
+            s = s + p.mass * p.vel + p.f_trans
+        return s
+
+    P0 = total()
+    o.step(20)
+    assert np.allclose(total(), P0, rtol=0, atol=1e-12)
+
+
+def test_neutral_box_with_net_charge_gains_QE():
+    """Without neutralisation the box carries charge Q and its momentum grows by
+    exactly Q E per step (the uniform background of the k = 0 mode feels no field)."""
+    o = EKOracle(16, 16, 16, bulk=(1e-3, 1e-3), flags=O.PV)
+    o.E = np.array([0.01, 0.0, 0.0])
+    o.add_particle((8.3, 7.9, 8.1), radius=3.0, charge=-15.0)
+    p = o.particles[0]
+    Q = o.total_charge()
+
+    def total():
+        return o.fluid_momentum() + p.mass * p.vel + p.f_trans
+
+    P0 = total()
+    o.step(10)
+    assert np.allclose(total() - P0, 10 * Q * o.E, rtol=0, atol=1e-12)
