@@ -32,6 +32,7 @@ struct ek_ctx {
   double* ipart = nullptr;             // 3 doubles per lattice block: its sums
   int nipart = 0;
   unsigned long long* fkey = nullptr;  // N: nearest-particle keys of S4
+  unsigned char* vsig = nullptr;       // N: fluid bit and velocity sign codes (S2 -> S3)
   int emax = 0;                        // cells of the widest widened box
   double* tmp = nullptr;  // N doubles of staging for conversions
   size_t rsz = 8;         // bytes of a real (double / float)
@@ -203,6 +204,7 @@ LBArgs lb_args(ek_ctx* ctx) {
   a.u = ctx->u;
   a.ifield = ctx->ifield;
   a.ipart = ctx->ipart;
+  a.vsig = ctx->vsig;
   a.parts = ctx->dparts;
   a.status = ctx->status;
   return a;
@@ -243,7 +245,7 @@ ek_status run_setup(ek_ctx* ctx) {
     const size_t cap = (size_t)ctx->Pcap * boxmax;
     EK_CUDA(cudaMalloc(&ctx->psibox, cap * sizeof(double)));
     EK_CUDA(cudaMalloc(&ctx->fpart, (size_t)ctx->Pcap * fchunks * FPART * sizeof(double)));
-    EK_CUDA(cudaMalloc(&ctx->psum, (size_t)(ctx->Pcap + 1) * FPART * sizeof(double)));
+    EK_CUDA(cudaMalloc(&ctx->psum, (size_t)(ctx->Pcap + 64) * FPART * sizeof(double)));
     EK_CUDA(cudaMalloc(&ctx->surf, cap * sizeof(int2)));
     ctx->psibox_cap = cap;
     ctx->fchunks = fchunks;
@@ -384,6 +386,8 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   if (!p || !out) return EK_ERR_ARG;
   *out = nullptr;
   if (!edge_ok(p->nx) || !edge_ok(p->ny) || !edge_ok(p->nz) || p->nx % 2) return EK_ERR_ARG;
+  // node indices of the FP32 kernels are 32-bit
+  if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return EK_ERR_ARG;
   if (!(p->nu > 0.0) || !(p->rho0 > 0.0) || !(p->bjerrum >= 0.0)) return EK_ERR_ARG;
   if (p->nspecies < 0 || p->nspecies > EK_MAX_SPECIES) return EK_ERR_ARG;
   for (int k = 0; k < p->nspecies; ++k)
@@ -456,6 +460,7 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   }
   alloc((void**)&ctx->ipart, (size_t)ctx->nipart * 3 * sizeof(double));
   alloc((void**)&ctx->fkey, N * sizeof(unsigned long long));
+  alloc((void**)&ctx->vsig, N);
   alloc((void**)&ctx->tmp, N * sizeof(double));
   alloc((void**)&ctx->owner, N * sizeof(int));
   alloc((void**)&ctx->owner_prev, N * sizeof(int));
@@ -503,7 +508,7 @@ ek_status ek_destroy(ek_ctx* ctx) {
                   ctx->qwall, ctx->u, ctx->tmp, ctx->owner, ctx->owner_prev, ctx->wall,
                   ctx->spectrum, ctx->dparts, ctx->psibox, ctx->fpart, ctx->surf, ctx->xfer,
                   ctx->xfer_count, ctx->surf_count, ctx->status, ctx->ifield, ctx->ipart,
-                  ctx->fkey, ctx->psum};
+                  ctx->fkey, ctx->psum, ctx->vsig};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);

@@ -104,6 +104,10 @@ struct Phys {
   double qscale[EK_MAX_SPECIES]; // FP32 form: density of one species unit (a power of 2)
 };
 
+// sign code of a velocity component for the volume-of-fluid shares
+__host__ __device__ __forceinline__ unsigned sign_code(double v) { return v > 0.0 ? 1u : (v < 0.0 ? 2u : 0u); }
+__host__ __device__ __forceinline__ unsigned sign_code(float v) { return v > 0.0f ? 1u : (v < 0.0f ? 2u : 0u); }
+
 // Storage forms.  FP64: every field double.  FP32: populations stored as the
 // deviation f_i - w_i rho0 in float, species as int32 multiples of qscale_k
 // (exact conservation: every transfer is an integer moved from one node to
@@ -215,6 +219,8 @@ struct LBArgs {
   const int* owner;
   void* u;
   void* ifield;    // real_t, 3N: solute force on the fluid minus q_ions E (fluid nodes)
+  unsigned char* vsig;  // N: bit 7 fluid node; bits 0-1, 2-3, 4-5: sign code of u_x, u_y, u_z
+                        // (0 zero, 1 positive, 2 negative), written by S2 for S3
   double* ipart;   // per-block sums of ifield (3 per block of the lattice grid)
   const DevParticle* parts;
   int* status;
@@ -267,7 +273,7 @@ struct PartArgs {
   const double* ipart;       // 3 per lattice block
   int nipart;                // number of lattice blocks
   unsigned long long* fkey;  // N: (surface distance, particle) of the nearest particle
-  double* psum;              // (P + 1) * FPART: per-particle sums, then the lattice total
+  double* psum;              // (P + 64) * FPART: per-particle sums, then 64 lattice slices
   int2* surf;      // (particle, box cell) of the cells cut by a sphere surface
   int* surf_count;
   int surf_cap;

@@ -54,6 +54,7 @@ __device__ __forceinline__ void lb_node(const LBArgs& a, int x, int y, int z, do
   double* ifield = (double*)a.ifield;
   if (a.owner[n] != FLUID) {
     // boundary node: no fluid, no solute transport
+    a.vsig[n] = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) rho_out[k * N + n] = rho_in[k * N + n];
     u[n] = 0.0;
@@ -184,6 +185,7 @@ __device__ __forceinline__ void lb_node(const LBArgs& a, int x, int y, int z, do
   u[n] = ux;
   u[N + n] = uy;
   u[2 * N + n] = uz;
+  a.vsig[n] = (unsigned char)(0x80u | sign_code(ux) | (sign_code(uy) << 2) | (sign_code(uz) << 4));
 
   // ---- push stream with velocity bounce-back (Eq. 12) ----
   f_out[n] = fs[0];
@@ -303,7 +305,11 @@ __global__ void __launch_bounds__(256) k_advect(LBArgs a) {
       for (int qx = -1; qx <= 1; ++qx) {
         if (!qx && !qy && !qz) continue;
         const long long m = node_index(a.g, nb_x(b, x, -qx), nb_y(b, y, -qy), nb_z(b, z, -qz));
-        if (a.owner[m] != FLUID) continue;
+        // the source must be fluid and move towards this node along every nonzero q
+        const unsigned mask = 0x80u | (qx ? 3u : 0u) | (qy ? 12u : 0u) | (qz ? 48u : 0u);
+        const unsigned want = 0x80u | (qx > 0 ? 1u : (qx < 0 ? 2u : 0u)) |
+                              (qy > 0 ? 4u : (qy < 0 ? 8u : 0u)) | (qz > 0 ? 16u : (qz < 0 ? 32u : 0u));
+        if ((a.vsig[m] & mask) != want) continue;
         const double vx = u[m], vy = u[N + m], vz = u[2 * N + m];
         if ((qx && sgn_bits(vx) != qx) || (qy && sgn_bits(vy) != qy) || (qz && sgn_bits(vz) != qz))
           continue;

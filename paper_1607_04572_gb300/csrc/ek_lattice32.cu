@@ -72,32 +72,49 @@ Phys32 make_phys32(const Phys& ph) {
   return p;
 }
 
+__device__ __forceinline__ int nbr32(int d, int x, int y, int z, const Nbr& b, int nx, int ny) {
+  const int X = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
+  const int Y = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
+  const int Z = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
+  return X + nx * (Y + ny * Z);
+}
+
+// One node of S2 (FP32 form).  Node indices are 32-bit (N < 2^31, checked at
+// creation); every field is reached through a per-direction or per-species
+// base pointer.  The 18 neighbour classes are read once into a bit mask that
+// the flux loop and the stream share.
 template <int K, bool PV>
 __device__ __forceinline__ void lb32_node(const LBArgs& a, const Phys32& c, int x, int y, int z,
                                           double (&iv)[3]) {
-  const float* g_in = (const float*)a.f_in;
-  float* g_out = (float*)a.f_out;
-  const int* n_in = (const int*)a.rho_in;
-  int* n_out = (int*)a.rho_out;
-  const float* phi = (const float*)a.phi;
-  const float* psi = (const float*)a.psi;
-  float* u = (float*)a.u;
-  const long long N = a.g.N;
+  const float* __restrict__ g_in = (const float*)a.f_in;
+  float* __restrict__ g_out = (float*)a.f_out;
+  const int* __restrict__ n_in = (const int*)a.rho_in;
+  int* __restrict__ n_out = (int*)a.rho_out;
+  const float* __restrict__ phi = (const float*)a.phi;
+  const float* __restrict__ psi = (const float*)a.psi;
+  const int* __restrict__ owner = a.owner;
+  float* __restrict__ u = (float*)a.u;
+  float* __restrict__ ifield = (float*)a.ifield;
+  const size_t N = (size_t)a.g.N;
   const int nx = a.g.nx, ny = a.g.ny;
-  const long long n = node_index(a.g, x, y, z);
-  float* ifield = (float*)a.ifield;
-  if (a.owner[n] != FLUID) {
+  const int n = x + nx * (y + ny * z);
+  if (owner[n] != FLUID) {
+    a.vsig[n] = 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) n_out[k * N + n] = n_in[k * N + n];
+    for (int k = 0; k < K; ++k) (n_out + k * N)[n] = (n_in + k * N)[n];
     u[n] = 0.0f;
-    u[N + n] = 0.0f;
-    u[2 * N + n] = 0.0f;
+    (u + N)[n] = 0.0f;
+    (u + 2 * N)[n] = 0.0f;
     ifield[n] = 0.0f;
-    ifield[N + n] = 0.0f;
-    ifield[2 * N + n] = 0.0f;
+    (ifield + N)[n] = 0.0f;
+    (ifield + 2 * N)[n] = 0.0f;
     return;
   }
   const Nbr b = make_nbr(x, y, z, a.g);
+  unsigned fluid = 0;  // bit d: neighbour along c_d is a fluid node
+#pragma unroll
+  for (int d = 1; d < Q; ++d)
+    if (owner[nbr32(d, x, y, z, b, nx, ny)] == FLUID) fluid |= 1u << d;
 
   // ---- S2a: quantised link fluxes and coupling force ----
   float gx = 0.0f, gy = 0.0f, gz = 0.0f;
@@ -107,20 +124,20 @@ __device__ __forceinline__ void lb32_node(const LBArgs& a, const Phys32& c, int 
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     S[k] = 0;
-    r0[k] = __fmul_rn((float)n_in[k * N + n], c.qs[k]);
+    r0[k] = __fmul_rn((float)(n_in + k * N)[n], c.qs[k]);
   }
   if (K > 0) {
     const float phi0 = phi[n];
 #pragma unroll
     for (int d = 1; d < Q; ++d) {
-      const long long m = nbr_index(d, x, y, z, b, nx, ny);
-      if (a.owner[m] != FLUID) continue;  // no flux into or out of boundary nodes
+      if (!(fluid & (1u << d))) continue;  // no flux into or out of boundary nodes
+      const int m = nbr32(d, x, y, z, b, nx, ny);
       const float omj = PV ? __fsub_rn(1.0f, psi[m]) : 1.0f;
       const float dphi = __fadd_rn(__fsub_rn(phi0, phi[m]), c.ec[d]);
       float tsum = 0.0f;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float rb = __fmul_rn((float)n_in[k * N + m], c.qs[k]);
+        const float rb = __fmul_rn((float)(n_in + k * N)[m], c.qs[k]);
         const float A = PV ? __fmul_rn(r0[k], omj) : r0[k];
         const float B = PV ? __fmul_rn(rb, om0) : rb;
         float br = fmaf(__fadd_rn(A, B), __fmul_rn(c.hz[k], dphi), __fsub_rn(A, B));
@@ -133,40 +150,40 @@ __device__ __forceinline__ void lb32_node(const LBArgs& a, const Phys32& c, int 
       if (dcz(d)) gz += csgnf(dcz(d), tsum);
     }
   }
+  float qion = 0.0f;
 #pragma unroll
-  for (int k = 0; k < K; ++k) n_out[k * N + n] = n_in[k * N + n] - S[k];
+  for (int k = 0; k < K; ++k) {
+    const int nk = (n_in + k * N)[n];
+    (n_out + k * N)[n] = nk - S[k];
+    qion = fmaf(c.zq[k], (float)nk, qion);
+  }
   // coupling force: sum_k J_k c / (2 D_k) = G / (2 A_0) with the unquantised fluxes
   constexpr float HALF_INV_A0 = 0.13060193748187072f;
-
-  // ---- S2b: TRT collision on the deviations (pair form) ----
-  float g[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) g[i] = g_in[i * N + n];
-  float ps[Q], pd[Q];
-  float drho = g[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
-#pragma unroll
-  for (int i = 1; i < Q; i += 2) {
-    ps[i] = g[i] + g[i + 1];
-    pd[i] = g[i] - g[i + 1];
-    drho += ps[i];
-    if (dcx(i)) jx += csgnf(dcx(i), pd[i]);
-    if (dcy(i)) jy += csgnf(dcy(i), pd[i]);
-    if (dcz(i)) jz += csgnf(dcz(i), pd[i]);
-  }
   {
     // internal solute force: coupling force minus the field's push on the local ion charge
-    float qion = 0.0f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) qion = fmaf(c.zq[k], (float)n_in[k * N + n], qion);
     const float ix = gx * HALF_INV_A0 - qion * c.E[0];
     const float iy = gy * HALF_INV_A0 - qion * c.E[1];
     const float iz = gz * HALF_INV_A0 - qion * c.E[2];
     ifield[n] = ix;
-    ifield[N + n] = iy;
-    ifield[2 * N + n] = iz;
+    (ifield + N)[n] = iy;
+    (ifield + 2 * N)[n] = iz;
     iv[0] = ix;
     iv[1] = iy;
     iv[2] = iz;
+  }
+
+  // ---- S2b: TRT collision on the deviations (pair form) ----
+  float g[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) g[i] = (g_in + i * N)[n];
+  float drho = g[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const float pd = g[i] - g[i + 1];
+    drho += g[i] + g[i + 1];
+    if (dcx(i)) jx += csgnf(dcx(i), pd);
+    if (dcy(i)) jy += csgnf(dcy(i), pd);
+    if (dcz(i)) jz += csgnf(dcz(i), pd);
   }
   const float rho = c.rho0 + drho;
   const float Fx = fmaf(gx, HALF_INV_A0, c.g[0]);
@@ -185,8 +202,14 @@ __device__ __forceinline__ void lb32_node(const LBArgs& a, const Phys32& c, int 
   const float base = fmaf(-1.5f * gg, uF, -le * fmaf(-1.5f * rho, usq, drho));
   const float hle = 0.5f * le, hlo = 0.5f * lo;
   const float k45 = -4.5f * le * rho;
-  float gs[Q];
-  gs[0] = fmaf(1.0f + le, g[0], (float)wgt(0) * base);
+  if (!isfinite(rho) || !isfinite(usq)) atomicOr(a.status, ST_NONFINITE);
+  u[n] = ux;
+  (u + N)[n] = uy;
+  (u + 2 * N)[n] = uz;
+  a.vsig[n] = (unsigned char)(0x80u | sign_code(ux) | (sign_code(uy) << 2) | (sign_code(uz) << 4));
+
+  // ---- collide each pair and push-stream it (velocity bounce-back, Eq. 12) ----
+  g_out[n] = fmaf(1.0f + le, g[0], (float)wgt(0) * base);
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     const float w = (float)wgt(i);
@@ -195,41 +218,33 @@ __device__ __forceinline__ void lb32_node(const LBArgs& a, const Phys32& c, int 
     const float cq = cdotf(i, qx, qy, qz);
     const float Ep = w * fmaf(cu, fmaf(4.5f * gg, cf, k45 * cu), base);
     const float Em = 3.0f * w * cq;
-    const float X = fmaf(hle, ps[i], Ep);
-    const float Y = fmaf(hlo, pd[i], Em);
-    gs[i] = g[i] + (X + Y);
-    gs[i + 1] = g[i + 1] + (X - Y);
-  }
-  if (!isfinite(rho) || !isfinite(usq)) atomicOr(a.status, ST_NONFINITE);
-  u[n] = ux;
-  u[N + n] = uy;
-  u[2 * N + n] = uz;
-
-  // ---- push stream with velocity bounce-back (Eq. 12); the w_i rho0 parts cancel ----
-  g_out[n] = gs[0];
+    const float X = fmaf(hle, g[i] + g[i + 1], Ep);
+    const float Y = fmaf(hlo, g[i] - g[i + 1], Em);
+    const float gsd[2] = {g[i] + (X + Y), g[i + 1] + (X - Y)};
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const long long m = nbr_index(i, x, y, z, b, nx, ny);
-    const int om = a.owner[m];
-    if (om == FLUID) {
-      g_out[i * N + m] = gs[i];
-    } else {
-      float cvb = 0.0f;
-      if (om >= 0) {
-        const DevParticle& P = a.parts[om];
-        const int xb = dcx(i) > 0 ? b.xp : (dcx(i) < 0 ? b.xm : x);
-        const int yb = dcy(i) > 0 ? b.yp : (dcy(i) < 0 ? b.ym : y);
-        const int zb = dcz(i) > 0 ? b.zp : (dcz(i) < 0 ? b.zm : z);
-        const double X = (double)(P.lo[0] + wrapi(xb - P.lo[0], nx));
-        const double Y = (double)(P.lo[1] + wrapi(yb - P.lo[1], ny));
-        const double Z = (double)(P.lo[2] + wrapi(zb - P.lo[2], a.g.nz));
-        const double dx = X - P.pos[0], dy = Y - P.pos[1], dz = Z - P.pos[2];
-        const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
-        const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
-        const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
-        cvb = (float)cdot(i, vx, vy, vz);
+    for (int h = 0; h < 2; ++h) {
+      const int d = i + h;
+      if (fluid & (1u << d)) {
+        (g_out + d * N)[nbr32(d, x, y, z, b, nx, ny)] = gsd[h];
+      } else {
+        float cvb = 0.0f;
+        const int om = owner[nbr32(d, x, y, z, b, nx, ny)];
+        if (om >= 0) {
+          const DevParticle& P = a.parts[om];
+          const int xb = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
+          const int yb = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
+          const int zb = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
+          const double Xb = (double)(P.lo[0] + wrapi(xb - P.lo[0], nx));
+          const double Yb = (double)(P.lo[1] + wrapi(yb - P.lo[1], ny));
+          const double Zb = (double)(P.lo[2] + wrapi(zb - P.lo[2], a.g.nz));
+          const double dx = Xb - P.pos[0], dy = Yb - P.pos[1], dz = Zb - P.pos[2];
+          const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
+          const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
+          const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
+          cvb = (float)cdot(d, vx, vy, vz);
+        }
+        (g_out + opp(d) * N)[n] = gsd[h] - 6.0f * (float)wgt(d) * c.rho0 * cvb;
       }
-      g_out[opp(i) * N + n] = gs[i] - 6.0f * (float)wgt(i) * c.rho0 * cvb;
     }
   }
 }
@@ -257,7 +272,7 @@ __device__ __forceinline__ void block_sum3(double (&v)[3], double* ipart) {
 }
 
 template <int K, bool PV>
-__global__ void __launch_bounds__(256) k_lb32(LBArgs a, Phys32 c) {
+__global__ void __launch_bounds__(256, 3) k_lb32(LBArgs a, Phys32 c) {
   const int x = blockIdx.x * TILE_X + threadIdx.x;
   const int y = blockIdx.y * TILE_Y + threadIdx.y;
   const int z = blockIdx.z;
@@ -278,35 +293,39 @@ __device__ __forceinline__ float vof_share(float vx, float vy, float vz, int ox,
 
 __device__ __forceinline__ int sgnf(float v) { return v > 0.0f ? 1 : (v < 0.0f ? -1 : 0); }
 
+// S3 (FP32 form): the node pulls the shares its 26 neighbours send it and
+// gives away its own; the per-node sign byte of S2 decides which neighbours
+// send anything before any of their data is loaded.
 template <int K>
 __global__ void __launch_bounds__(256) k_advect32(LBArgs a, Phys32 c) {
-  const int* n_in = (const int*)a.rho_in;
-  int* n_out = (int*)a.rho_out;
-  const float* u = (const float*)a.u;
-  const long long N = a.g.N;
+  const int* __restrict__ n_in = (const int*)a.rho_in;
+  int* __restrict__ n_out = (int*)a.rho_out;
+  const float* __restrict__ u = (const float*)a.u;
+  const unsigned char* __restrict__ vs = a.vsig;
+  const size_t N = (size_t)a.g.N;
+  const int nx = a.g.nx, ny = a.g.ny;
   const int x = blockIdx.x * TILE_X + threadIdx.x;
   const int y = blockIdx.y * TILE_Y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x >= a.g.nx || y >= a.g.ny) return;
-  const long long n = node_index(a.g, x, y, z);
-  if (a.owner[n] != FLUID) return;
+  if (x >= nx || y >= ny) return;
+  const int n = x + nx * (y + ny * z);
+  if (!(vs[n] & 0x80u)) return;
   const Nbr b = make_nbr(x, y, z, a.g);
   int acc[K];
   float rs[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    acc[k] = n_out[k * N + n];
-    rs[k] = (float)n_in[k * N + n];
+    acc[k] = (n_out + k * N)[n];
+    rs[k] = (float)(n_in + k * N)[n];
   }
-  const float ux = u[n], uy = u[N + n], uz = u[2 * N + n];
+  const float ux = u[n], uy = (u + N)[n], uz = (u + 2 * N)[n];
   const int sx = sgnf(ux), sy = sgnf(uy), sz = sgnf(uz);
   for (int oz = 0; oz <= (sz != 0); ++oz) {
     for (int oy = 0; oy <= (sy != 0); ++oy) {
       for (int ox = 0; ox <= (sx != 0); ++ox) {
         if (!ox && !oy && !oz) continue;
-        const long long m = node_index(a.g, nb_x(b, x, ox ? sx : 0), nb_y(b, y, oy ? sy : 0),
-                                       nb_z(b, z, oz ? sz : 0));
-        if (a.owner[m] != FLUID) continue;
+        const int m = nb_x(b, x, ox ? sx : 0) + nx * (nb_y(b, y, oy ? sy : 0) + ny * nb_z(b, z, oz ? sz : 0));
+        if (!(vs[m] & 0x80u)) continue;  // share aimed at a boundary stays here
         const float frac = vof_share(ux, uy, uz, ox, oy, oz);
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] -= __float2int_rn(__fmul_rn(rs[k], frac));
@@ -317,19 +336,22 @@ __global__ void __launch_bounds__(256) k_advect32(LBArgs a, Phys32 c) {
     for (int qy = -1; qy <= 1; ++qy) {
       for (int qx = -1; qx <= 1; ++qx) {
         if (!qx && !qy && !qz) continue;
-        const long long m = node_index(a.g, nb_x(b, x, -qx), nb_y(b, y, -qy), nb_z(b, z, -qz));
-        if (a.owner[m] != FLUID) continue;
-        const float vx = u[m], vy = u[N + m], vz = u[2 * N + m];
-        if ((qx && sgnf(vx) != qx) || (qy && sgnf(vy) != qy) || (qz && sgnf(vz) != qz)) continue;
+        // the source must be fluid and move towards this node along every nonzero q
+        const unsigned mask = 0x80u | (qx ? 3u : 0u) | (qy ? 12u : 0u) | (qz ? 48u : 0u);
+        const unsigned want = 0x80u | (qx > 0 ? 1u : (qx < 0 ? 2u : 0u)) |
+                              (qy > 0 ? 4u : (qy < 0 ? 8u : 0u)) | (qz > 0 ? 16u : (qz < 0 ? 32u : 0u));
+        const int m = nb_x(b, x, -qx) + nx * (nb_y(b, y, -qy) + ny * nb_z(b, z, -qz));
+        if ((vs[m] & mask) != want) continue;
+        const float vx = u[m], vy = (u + N)[m], vz = (u + 2 * N)[m];
         const float frac = vof_share(vx, vy, vz, qx != 0, qy != 0, qz != 0);
 #pragma unroll
         for (int k = 0; k < K; ++k)
-          acc[k] += __float2int_rn(__fmul_rn((float)n_in[k * N + m], frac));
+          acc[k] += __float2int_rn(__fmul_rn((float)(n_in + k * N)[m], frac));
       }
     }
   }
 #pragma unroll
-  for (int k = 0; k < K; ++k) n_out[k * N + n] = acc[k];
+  for (int k = 0; k < K; ++k) (n_out + k * N)[n] = acc[k];
 }
 
 __global__ void k_fill32(Grid g, const int* owner, float* f, int* rho, int K, float rho0, int n0,

@@ -206,10 +206,16 @@ __device__ __forceinline__ double min_image(double d, int n) {
 // centre.  Returns true for the first copy of a node (a widened box can be
 // wider than the lattice), so per-node sums count every node once.
 __device__ __forceinline__ bool ext_cell(const DevParticle& P, int c, const Grid& g, int& X, int& Y,
-                                        int& Z, long long& n, double& dx, double& dy, double& dz) {
+                                        int& Z, long long& n, double& dx, double& dy, double& dz,
+                                        int* wrapped = nullptr) {
   box_coord(c, P.elo, P.ehi, X, Y, Z);
   const bool first = X - P.elo[0] < g.nx && Y - P.elo[1] < g.ny && Z - P.elo[2] < g.nz;
   const int x = wrapi(X, g.nx), y = wrapi(Y, g.ny), z = wrapi(Z, g.nz);
+  if (wrapped) {
+    wrapped[0] = x;
+    wrapped[1] = y;
+    wrapped[2] = z;
+  }
   n = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
   dx = min_image(__dsub_rn((double)x, P.pos[0]), g.nx);
   dy = min_image(__dsub_rn((double)y, P.pos[1]), g.ny);
@@ -270,15 +276,18 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
   long long n;
   double mx, my, mz;
   if (c < ncell) {
-    const bool first = ext_cell(P, c, g, X, Y, Z, n, mx, my, mz);
+    int w3[3];
+    const bool first = ext_cell(P, c, g, X, Y, Z, n, mx, my, mz, w3);
     const int own = a.owner[n];
     const bool in_box = X >= P.lo[0] && X < P.hi[0] && Y >= P.lo[1] && Y < P.hi[1] &&
                         Z >= P.lo[2] && Z < P.hi[2];
     if (own == FLUID && in_box) {
       // momentum exchange on every link from this fluid node into the particle (Eq. 11)
+      const Nbr b = make_nbr(w3[0], w3[1], w3[2], g);
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
-        const long long m = node_of(X + dcx(i), Y + dcy(i), Z + dcz(i), g);
+        const long long m = node_index(g, nb_x(b, w3[0], dcx(i)), nb_y(b, w3[1], dcy(i)),
+                                       nb_z(b, w3[2], dcz(i)));
         if (a.owner[m] != p) continue;
         const double dx = (double)(X + dcx(i)) - P.pos[0];
         const double dy = (double)(Y + dcy(i)) - P.pos[1];
@@ -345,21 +354,30 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
 
 constexpr int INTEGRATE_T = 512;
 constexpr int PSUM_T = 256;
+constexpr int PSUM_LAT = 64;  // blocks that sum the lattice-block partials
 
 // Block p < P: the chunk partials of particle p, summed in a fixed order into
-// psum[p]; block P: the lattice-block sums of the internal solute force into
-// psum[P].  Thread t takes the items t, t + PSUM_T, ...; then a fixed tree.
+// psum[p]; blocks P + l, l < PSUM_LAT: slice l of the lattice-block sums of the
+// internal solute force into psum[P + l].  Thread t takes the items t,
+// t + PSUM_T, ... of its range; then a fixed tree.
 __global__ void __launch_bounds__(PSUM_T) k_psum(PartArgs a) {
   __shared__ double red[PSUM_T];
   const int p = blockIdx.x;
-  const bool lattice = p == a.P;
-  const int nitem = lattice ? a.nipart
-                            : (box_cells(a.parts[p].elo, a.parts[p].ehi) + FORCE_CHUNK - 1) / FORCE_CHUNK;
+  const bool lattice = p >= a.P;
+  int first = 0, nitem;
+  if (lattice) {
+    const int l = p - a.P;
+    const int per = (a.nipart + PSUM_LAT - 1) / PSUM_LAT;
+    first = l * per;
+    nitem = max(0, min(per, a.nipart - first));
+  } else {
+    nitem = (box_cells(a.parts[p].elo, a.parts[p].ehi) + FORCE_CHUNK - 1) / FORCE_CHUNK;
+  }
   const int ncomp = lattice ? 3 : FPART;
   for (int j = 0; j < ncomp; ++j) {
     double v = 0.0;
     for (int it = threadIdx.x; it < nitem; it += PSUM_T)
-      v += lattice ? a.ipart[3 * it + j] : a.fpart[((long long)p * a.fchunks + it) * FPART + j];
+      v += lattice ? a.ipart[3 * (first + it) + j] : a.fpart[((long long)p * a.fchunks + it) * FPART + j];
     red[threadIdx.x] = v;
     __syncthreads();
     for (int w = PSUM_T / 2; w > 0; w >>= 1) {
@@ -390,8 +408,11 @@ __global__ void __launch_bounds__(INTEGRATE_T) k_particle_integrate(PartArgs a) 
   for (int p = threadIdx.x; p < a.P; p += blockDim.x)
     for (int d = 0; d < 3; ++d) claimed[d] -= a.psum[(long long)p * FPART + 6 + d];
   double rem[3];
-  for (int d = 0; d < 3; ++d)
-    rem[d] = (a.psum[(long long)a.P * FPART + d] - block_sum_one(claimed[d], red)) / (double)a.P;
+  for (int d = 0; d < 3; ++d) {
+    double tot = 0.0;
+    for (int l = 0; l < PSUM_LAT; ++l) tot += a.psum[(long long)(a.P + l) * FPART + d];
+    rem[d] = (tot - block_sum_one(claimed[d], red)) / (double)a.P;
+  }
   for (int p = threadIdx.x; p < a.P; p += blockDim.x) {
     DevParticle& P = a.parts[p];
     const double* acc = a.psum + (long long)p * FPART;
@@ -784,7 +805,7 @@ cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s) {
   const unsigned echunks = (unsigned)((a.emax + PT - 1) / PT);
   k_force_assign<<<dim3(a.P, echunks), PT, 0, s>>>(a);
   k_particle_forces<FM><<<dim3(a.P, a.fchunks), FORCE_CHUNK, 0, s>>>(a);
-  k_psum<<<a.P + 1, PSUM_T, 0, s>>>(a);
+  k_psum<<<a.P + PSUM_LAT, PSUM_T, 0, s>>>(a);
   k_particle_integrate<<<1, INTEGRATE_T, 0, s>>>(a);
   k_key_reset<<<dim3(a.P, echunks), PT, 0, s>>>(a);
   return cudaGetLastError();
