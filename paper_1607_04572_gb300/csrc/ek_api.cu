@@ -18,6 +18,9 @@ struct ek_ctx {
   Grid g;
   Phys ph;
   cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;        // particle work of S4/S5 runs here, beside S3
+  cudaEvent_t ev_lb = nullptr;       // S2 done
+  cudaEvent_t ev_part = nullptr;     // S4 + re-flag done
   int device = 0;
   int fp32 = 0;  // storage form (EK_FP32)
   // field storage: double (FP64 form) or float / int32 species (FP32 form)
@@ -360,6 +363,35 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
   }
 }
 
+// One full step with the particle work overlapped: after S2, S4 and the
+// re-flag part of S5 (which touch neither the species nor u) run on the
+// auxiliary stream while S3 runs on the context's stream; the transitions
+// (which need S3's species) follow on the context's stream.
+ek_status enqueue_step(ek_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  ek_status st = enqueue_stage(ctx, 1);
+  if (st != EK_OK) return st;
+  const LBArgs la = lb_args(ctx);
+  EK_CUDA(ctx->fp32 ? launch_lb32(la, s) : launch_lb_fused(la, s));
+  ctx->cur = 1 - ctx->cur;
+  const PartArgs pa = part_args(ctx);
+  if (ctx->P) {
+    EK_CUDA(cudaEventRecord(ctx->ev_lb, s));
+    EK_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_lb, 0));
+    EK_CUDA(launch_particle_forces(pa, ctx->aux));
+    EK_CUDA(launch_reflag(pa, true, ctx->aux, 1));
+    EK_CUDA(cudaEventRecord(ctx->ev_part, ctx->aux));
+  }
+  EK_CUDA(ctx->fp32 ? launch_advection32(la, s) : launch_advection(la, s));
+  ctx->launches += ctx->p.nspecies > 0 ? 2 : 1;
+  if (ctx->P) {
+    EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_part, 0));
+    EK_CUDA(launch_reflag(pa, true, s, 2));
+    ctx->launches += 15;
+  }
+  return EK_OK;
+}
+
 ek_status ready(ek_ctx* ctx) {
   if (!ctx) return EK_ERR_ARG;
   if (ctx->broken) return fail(ctx, EK_ERR_STATE, "context is in an error state: " + ctx->err);
@@ -455,7 +487,8 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   alloc(&ctx->u, 3 * N * rsz);
   alloc(&ctx->ifield, 3 * N * rsz);
   {
-    const dim3 lg = lattice_grid(g);
+    // lattice-block partial sums of S2: one per block of its grid
+    const dim3 lg = ctx->fp32 ? lattice_grid32(g) : lattice_grid(g);
     ctx->nipart = (int)(lg.x * lg.y * lg.z);
   }
   alloc((void**)&ctx->ipart, (size_t)ctx->nipart * 3 * sizeof(double));
@@ -487,7 +520,10 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
     cudaMemset(ctx->f[b], 0, 19 * N * rsz);
     cudaMemset(ctx->rho[b], 0, K * N * ssz);
   }
-  if (cudaDeviceSynchronize() != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_lb, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_part, cudaEventDisableTiming) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
     ek_destroy(ctx);
     return EK_ERR_CUDA;
   }
@@ -512,6 +548,12 @@ ek_status ek_destroy(ek_ctx* ctx) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->aux);
+    cudaStreamDestroy(ctx->aux);
+  }
+  if (ctx->ev_lb) cudaEventDestroy(ctx->ev_lb);
+  if (ctx->ev_part) cudaEventDestroy(ctx->ev_part);
   delete ctx;
   return EK_OK;
 }
@@ -749,10 +791,8 @@ ek_status ek_step_async(ek_ctx* ctx, int nsteps) {
   if (st != EK_OK) return st;
   if (nsteps < 0) return fail(ctx, EK_ERR_ARG, "nsteps < 0");
   for (int t = 0; t < nsteps; ++t) {
-    for (int stage : {1, 2, 4, 5}) {
-      st = enqueue_stage(ctx, stage);
-      if (st != EK_OK) return st;
-    }
+    st = enqueue_step(ctx);
+    if (st != EK_OK) return st;
   }
   return EK_OK;
 }

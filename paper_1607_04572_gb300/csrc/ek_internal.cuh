@@ -162,6 +162,12 @@ inline dim3 lattice_grid(const Grid& g) {
               (unsigned)g.nz);
 }
 inline dim3 lattice_block() { return dim3(TILE_X, TILE_Y, 1); }
+// the FP32 form's S2 kernel marches through 8 planes per block
+constexpr int TILE_Z32 = 8;
+inline dim3 lattice_grid32(const Grid& g) {
+  return dim3((unsigned)((g.nx + TILE_X - 1) / TILE_X), (unsigned)((g.ny + TILE_Y - 1) / TILE_Y),
+              (unsigned)((g.nz + TILE_Z32 - 1) / TILE_Z32));
+}
 
 // wrapped neighbour coordinates of (x, y, z)
 struct Nbr {
@@ -283,7 +289,9 @@ struct PartArgs {
 constexpr int FORCE_CHUNK = 128;
 constexpr int FPART = 18;  // Fh Th (momentum exchange) Fs Ts (solute) Fq Tq (field on charge)
 cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s);  // S4
-cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s);  // S5
+// S5; parts: 1 = re-flag, Psi and charge (no species access), 2 = transitions
+// (species after S3), 3 = both
+cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s, int parts = 3);
 cudaError_t launch_fill(const Grid& g, const Phys& ph, const int* owner, double* f, double* rho,
                         const double* bulk_k, cudaStream_t s);
 

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256) k_advect(LBArgs a) {
   const int z = blockIdx.z;
   if (x >= a.g.nx || y >= a.g.ny) return;
   const long long n = node_index(a.g, x, y, z);
-  if (a.owner[n] != FLUID) return;
+  if (!(a.vsig[n] & 0x80u)) return;  // fluid bit of S2 (the flags may change meanwhile)
   const Nbr b = make_nbr(x, y, z, a.g);
   double acc[K];
   double rs[K];
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256) k_advect(LBArgs a) {
         if (!ox && !oy && !oz) continue;
         const long long m = node_index(a.g, nb_x(b, x, ox ? sx : 0), nb_y(b, y, oy ? sy : 0),
                                        nb_z(b, z, oz ? sz : 0));
-        if (a.owner[m] != FLUID) continue;  // share aimed at a boundary stays here
+        if (!(a.vsig[m] & 0x80u)) continue;  // share aimed at a boundary stays here
         const double frac = (ox ? ax : bx) * (oy ? ay : by) * (oz ? az : bz);
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] -= rs[k] * frac;

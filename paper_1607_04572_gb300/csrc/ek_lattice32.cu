@@ -79,176 +79,6 @@ __device__ __forceinline__ int nbr32(int d, int x, int y, int z, const Nbr& b, i
   return X + nx * (Y + ny * Z);
 }
 
-// One node of S2 (FP32 form).  Node indices are 32-bit (N < 2^31, checked at
-// creation); every field is reached through a per-direction or per-species
-// base pointer.  The 18 neighbour classes are read once into a bit mask that
-// the flux loop and the stream share.
-template <int K, bool PV>
-__device__ __forceinline__ void lb32_node(const LBArgs& a, const Phys32& c, int x, int y, int z,
-                                          double (&iv)[3]) {
-  const float* __restrict__ g_in = (const float*)a.f_in;
-  float* __restrict__ g_out = (float*)a.f_out;
-  const int* __restrict__ n_in = (const int*)a.rho_in;
-  int* __restrict__ n_out = (int*)a.rho_out;
-  const float* __restrict__ phi = (const float*)a.phi;
-  const float* __restrict__ psi = (const float*)a.psi;
-  const int* __restrict__ owner = a.owner;
-  float* __restrict__ u = (float*)a.u;
-  float* __restrict__ ifield = (float*)a.ifield;
-  const size_t N = (size_t)a.g.N;
-  const int nx = a.g.nx, ny = a.g.ny;
-  const int n = x + nx * (y + ny * z);
-  if (owner[n] != FLUID) {
-    a.vsig[n] = 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) (n_out + k * N)[n] = (n_in + k * N)[n];
-    u[n] = 0.0f;
-    (u + N)[n] = 0.0f;
-    (u + 2 * N)[n] = 0.0f;
-    ifield[n] = 0.0f;
-    (ifield + N)[n] = 0.0f;
-    (ifield + 2 * N)[n] = 0.0f;
-    return;
-  }
-  const Nbr b = make_nbr(x, y, z, a.g);
-  unsigned fluid = 0;  // bit d: neighbour along c_d is a fluid node
-#pragma unroll
-  for (int d = 1; d < Q; ++d)
-    if (owner[nbr32(d, x, y, z, b, nx, ny)] == FLUID) fluid |= 1u << d;
-
-  // ---- S2a: quantised link fluxes and coupling force ----
-  float gx = 0.0f, gy = 0.0f, gz = 0.0f;
-  int S[K > 0 ? K : 1];
-  float r0[K > 0 ? K : 1];
-  const float om0 = PV ? __fsub_rn(1.0f, psi[n]) : 1.0f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    S[k] = 0;
-    r0[k] = __fmul_rn((float)(n_in + k * N)[n], c.qs[k]);
-  }
-  if (K > 0) {
-    const float phi0 = phi[n];
-#pragma unroll
-    for (int d = 1; d < Q; ++d) {
-      if (!(fluid & (1u << d))) continue;  // no flux into or out of boundary nodes
-      const int m = nbr32(d, x, y, z, b, nx, ny);
-      const float omj = PV ? __fsub_rn(1.0f, psi[m]) : 1.0f;
-      const float dphi = __fadd_rn(__fsub_rn(phi0, phi[m]), c.ec[d]);
-      float tsum = 0.0f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const float rb = __fmul_rn((float)(n_in + k * N)[m], c.qs[k]);
-        const float A = PV ? __fmul_rn(r0[k], omj) : r0[k];
-        const float B = PV ? __fmul_rn(rb, om0) : rb;
-        float br = fmaf(__fadd_rn(A, B), __fmul_rn(c.hz[k], dphi), __fsub_rn(A, B));
-        if (d >= 7) br = __fmul_rn(br, 0.70710678f);
-        S[k] += __float2int_rn(__fmul_rn(br, c.cq[k]));
-        tsum += br;
-      }
-      if (dcx(d)) gx += csgnf(dcx(d), tsum);
-      if (dcy(d)) gy += csgnf(dcy(d), tsum);
-      if (dcz(d)) gz += csgnf(dcz(d), tsum);
-    }
-  }
-  float qion = 0.0f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int nk = (n_in + k * N)[n];
-    (n_out + k * N)[n] = nk - S[k];
-    qion = fmaf(c.zq[k], (float)nk, qion);
-  }
-  // coupling force: sum_k J_k c / (2 D_k) = G / (2 A_0) with the unquantised fluxes
-  constexpr float HALF_INV_A0 = 0.13060193748187072f;
-  {
-    // internal solute force: coupling force minus the field's push on the local ion charge
-    const float ix = gx * HALF_INV_A0 - qion * c.E[0];
-    const float iy = gy * HALF_INV_A0 - qion * c.E[1];
-    const float iz = gz * HALF_INV_A0 - qion * c.E[2];
-    ifield[n] = ix;
-    (ifield + N)[n] = iy;
-    (ifield + 2 * N)[n] = iz;
-    iv[0] = ix;
-    iv[1] = iy;
-    iv[2] = iz;
-  }
-
-  // ---- S2b: TRT collision on the deviations (pair form) ----
-  float g[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) g[i] = (g_in + i * N)[n];
-  float drho = g[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
-#pragma unroll
-  for (int i = 1; i < Q; i += 2) {
-    const float pd = g[i] - g[i + 1];
-    drho += g[i] + g[i + 1];
-    if (dcx(i)) jx += csgnf(dcx(i), pd);
-    if (dcy(i)) jy += csgnf(dcy(i), pd);
-    if (dcz(i)) jz += csgnf(dcz(i), pd);
-  }
-  const float rho = c.rho0 + drho;
-  const float Fx = fmaf(gx, HALF_INV_A0, c.g[0]);
-  const float Fy = fmaf(gy, HALF_INV_A0, c.g[1]);
-  const float Fz = fmaf(gz, HALF_INV_A0, c.g[2]);
-  const float irho = 1.0f / rho;
-  const float ux = (jx + 0.5f * Fx) * irho;
-  const float uy = (jy + 0.5f * Fy) * irho;
-  const float uz = (jz + 0.5f * Fz) * irho;
-  const float usq = ux * ux + uy * uy + uz * uz;
-  const float uF = ux * Fx + uy * Fy + uz * Fz;
-  const float le = c.lam_e, lo = c.lam_o;
-  const float gg = 2.0f + le;
-  const float qx = fmaf(-lo, jx, Fx), qy = fmaf(-lo, jy, Fy), qz = fmaf(-lo, jz, Fz);
-  // even part relative to w_i rho0: base = -1.5 gg u.F - lambda_e (drho - 1.5 rho u^2)
-  const float base = fmaf(-1.5f * gg, uF, -le * fmaf(-1.5f * rho, usq, drho));
-  const float hle = 0.5f * le, hlo = 0.5f * lo;
-  const float k45 = -4.5f * le * rho;
-  if (!isfinite(rho) || !isfinite(usq)) atomicOr(a.status, ST_NONFINITE);
-  u[n] = ux;
-  (u + N)[n] = uy;
-  (u + 2 * N)[n] = uz;
-  a.vsig[n] = (unsigned char)(0x80u | sign_code(ux) | (sign_code(uy) << 2) | (sign_code(uz) << 4));
-
-  // ---- collide each pair and push-stream it (velocity bounce-back, Eq. 12) ----
-  g_out[n] = fmaf(1.0f + le, g[0], (float)wgt(0) * base);
-#pragma unroll
-  for (int i = 1; i < Q; i += 2) {
-    const float w = (float)wgt(i);
-    const float cu = cdotf(i, ux, uy, uz);
-    const float cf = cdotf(i, Fx, Fy, Fz);
-    const float cq = cdotf(i, qx, qy, qz);
-    const float Ep = w * fmaf(cu, fmaf(4.5f * gg, cf, k45 * cu), base);
-    const float Em = 3.0f * w * cq;
-    const float X = fmaf(hle, g[i] + g[i + 1], Ep);
-    const float Y = fmaf(hlo, g[i] - g[i + 1], Em);
-    const float gsd[2] = {g[i] + (X + Y), g[i + 1] + (X - Y)};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int d = i + h;
-      if (fluid & (1u << d)) {
-        (g_out + d * N)[nbr32(d, x, y, z, b, nx, ny)] = gsd[h];
-      } else {
-        float cvb = 0.0f;
-        const int om = owner[nbr32(d, x, y, z, b, nx, ny)];
-        if (om >= 0) {
-          const DevParticle& P = a.parts[om];
-          const int xb = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
-          const int yb = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
-          const int zb = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
-          const double Xb = (double)(P.lo[0] + wrapi(xb - P.lo[0], nx));
-          const double Yb = (double)(P.lo[1] + wrapi(yb - P.lo[1], ny));
-          const double Zb = (double)(P.lo[2] + wrapi(zb - P.lo[2], a.g.nz));
-          const double dx = Xb - P.pos[0], dy = Yb - P.pos[1], dz = Zb - P.pos[2];
-          const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
-          const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
-          const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
-          cvb = (float)cdot(d, vx, vy, vz);
-        }
-        (g_out + opp(d) * N)[n] = gsd[h] - 6.0f * (float)wgt(d) * c.rho0 * cvb;
-      }
-    }
-  }
-}
-
 __device__ __forceinline__ void block_sum3(double (&v)[3], double* ipart) {
   __shared__ double red[TILE_X * TILE_Y / 32][3];
   const int t = threadIdx.x + TILE_X * threadIdx.y;
@@ -271,13 +101,216 @@ __device__ __forceinline__ void block_sum3(double (&v)[3], double* ipart) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// 2.5D-tiled S2 (FP32 form).  A 32 x 8 thread block owns a (32 x 8) column of
+// TZ planes.  The stencil fields of three consecutive planes -- rho_k as
+// float, 1 - Psi, Phi and the node class -- sit in a shared-memory ring with a
+// one-node halo; each plane is read from global memory (and its species
+// converted to float) once per block instead of once per neighbour.
+// ---------------------------------------------------------------------------
+constexpr int TZ = TILE_Z32;                   // planes per block
+constexpr int HX = TILE_X + 2, HY = TILE_Y + 2;  // tile with halo
+constexpr int HP = HX * HY;                    // nodes of one halo plane
+
+template <int K>
+struct LBTile {
+  float rho[K > 0 ? K : 1][3][HP];
+  float om[3][HP];
+  float phi[3][HP];
+  int own[3][HP];
+};
+
 template <int K, bool PV>
-__global__ void __launch_bounds__(256, 3) k_lb32(LBArgs a, Phys32 c) {
-  const int x = blockIdx.x * TILE_X + threadIdx.x;
-  const int y = blockIdx.y * TILE_Y + threadIdx.y;
-  const int z = blockIdx.z;
+__device__ __forceinline__ void load_plane(LBTile<K>& t, int slot, int zz, int x0, int y0,
+                                           const LBArgs& a, const Phys32& c) {
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const size_t N = (size_t)a.g.N;
+  const int z = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+  const int tid = threadIdx.x + TILE_X * threadIdx.y;
+  for (int e = tid; e < HP; e += TILE_X * TILE_Y) {
+    const int ey = e / HX, ex = e - ey * HX;
+    int x = x0 - 1 + ex, y = y0 - 1 + ey;
+    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    const int m = x + nx * (y + ny * z);
+    t.own[slot][e] = a.owner[m];
+    t.phi[slot][e] = ((const float*)a.phi)[m];
+    t.om[slot][e] = PV ? __fsub_rn(1.0f, ((const float*)a.psi)[m]) : 1.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      t.rho[k][slot][e] = __fmul_rn((float)(((const int*)a.rho_in) + k * N)[m], c.qs[k]);
+  }
+}
+
+template <int K, bool PV>
+__global__ void __launch_bounds__(256, 3) k_lb32_tiled(LBArgs a, Phys32 c) {
+  __shared__ LBTile<K> t;
+  const float* __restrict__ g_in = (const float*)a.f_in;
+  float* __restrict__ g_out = (float*)a.f_out;
+  const int* __restrict__ n_in = (const int*)a.rho_in;
+  int* __restrict__ n_out = (int*)a.rho_out;
+  float* __restrict__ u = (float*)a.u;
+  float* __restrict__ ifield = (float*)a.ifield;
+  const size_t N = (size_t)a.g.N;
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y, z0 = blockIdx.z * TZ;
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  const bool in_xy = x < nx && y < ny;
+  const int ex = threadIdx.x + 1, ey = threadIdx.y + 1;
   double iv[3] = {0.0, 0.0, 0.0};
-  if (x < a.g.nx && y < a.g.ny) lb32_node<K, PV>(a, c, x, y, z, iv);
+  load_plane<K, PV>(t, (z0 + 2) % 3, z0 - 1, x0, y0, a, c);  // slot of plane z0 - 1
+  load_plane<K, PV>(t, z0 % 3, z0, x0, y0, a, c);
+  for (int z = z0; z < z0 + TZ; ++z) {
+    load_plane<K, PV>(t, (z + 1) % 3, z + 1, x0, y0, a, c);
+    __syncthreads();
+    if (in_xy && z < nz) {
+      const int sl[3] = {(z + 2) % 3, z % 3, (z + 1) % 3};  // planes z - 1, z, z + 1
+      const int e0 = ex + HX * ey;
+      const int n = x + nx * (y + ny * z);
+      const Nbr b = make_nbr(x, y, z, a.g);
+      if (t.own[sl[1]][e0] != FLUID) {
+        a.vsig[n] = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) (n_out + k * N)[n] = (n_in + k * N)[n];
+        u[n] = 0.0f;
+        (u + N)[n] = 0.0f;
+        (u + 2 * N)[n] = 0.0f;
+        ifield[n] = 0.0f;
+        (ifield + N)[n] = 0.0f;
+        (ifield + 2 * N)[n] = 0.0f;
+      } else {
+        unsigned fluid = 0;
+#pragma unroll
+        for (int d = 1; d < Q; ++d)
+          if (t.own[sl[1 + dcz(d)]][e0 + dcx(d) + HX * dcy(d)] == FLUID) fluid |= 1u << d;
+        // ---- S2a: quantised link fluxes (symmetric operands) and coupling force ----
+        float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+        int S[K > 0 ? K : 1];
+        float r0[K > 0 ? K : 1];
+        const float om0 = t.om[sl[1]][e0];
+        const float phi0 = t.phi[sl[1]][e0];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          S[k] = 0;
+          r0[k] = t.rho[k][sl[1]][e0];
+        }
+#pragma unroll
+        for (int d = 1; d < Q; ++d) {
+          if (K == 0 || !(fluid & (1u << d))) continue;
+          const int sd = sl[1 + dcz(d)], ed = e0 + dcx(d) + HX * dcy(d);
+          const float omj = t.om[sd][ed];
+          const float dphi = __fadd_rn(__fsub_rn(phi0, t.phi[sd][ed]), c.ec[d]);
+          float tsum = 0.0f;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const float rb = t.rho[k][sd][ed];
+            const float A = PV ? __fmul_rn(r0[k], omj) : r0[k];
+            const float B = PV ? __fmul_rn(rb, om0) : rb;
+            float br = fmaf(__fadd_rn(A, B), __fmul_rn(c.hz[k], dphi), __fsub_rn(A, B));
+            if (d >= 7) br = __fmul_rn(br, 0.70710678f);
+            S[k] += __float2int_rn(__fmul_rn(br, c.cq[k]));
+            tsum += br;
+          }
+          if (dcx(d)) gx += csgnf(dcx(d), tsum);
+          if (dcy(d)) gy += csgnf(dcy(d), tsum);
+          if (dcz(d)) gz += csgnf(dcz(d), tsum);
+        }
+        float qion = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int nk = (n_in + k * N)[n];
+          (n_out + k * N)[n] = nk - S[k];
+          qion = fmaf(c.zq[k], (float)nk, qion);
+        }
+        constexpr float HALF_INV_A0 = 0.13060193748187072f;
+        {
+          const float ix = gx * HALF_INV_A0 - qion * c.E[0];
+          const float iy = gy * HALF_INV_A0 - qion * c.E[1];
+          const float iz = gz * HALF_INV_A0 - qion * c.E[2];
+          ifield[n] = ix;
+          (ifield + N)[n] = iy;
+          (ifield + 2 * N)[n] = iz;
+          iv[0] += ix;
+          iv[1] += iy;
+          iv[2] += iz;
+        }
+        // ---- S2b: TRT collision on the deviations (pair form) ----
+        float g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = (g_in + i * N)[n];
+        float drho = g[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+          const float pd = g[i] - g[i + 1];
+          drho += g[i] + g[i + 1];
+          if (dcx(i)) jx += csgnf(dcx(i), pd);
+          if (dcy(i)) jy += csgnf(dcy(i), pd);
+          if (dcz(i)) jz += csgnf(dcz(i), pd);
+        }
+        const float rho = c.rho0 + drho;
+        const float Fx = fmaf(gx, HALF_INV_A0, c.g[0]);
+        const float Fy = fmaf(gy, HALF_INV_A0, c.g[1]);
+        const float Fz = fmaf(gz, HALF_INV_A0, c.g[2]);
+        const float irho = 1.0f / rho;
+        const float ux = (jx + 0.5f * Fx) * irho;
+        const float uy = (jy + 0.5f * Fy) * irho;
+        const float uz = (jz + 0.5f * Fz) * irho;
+        const float usq = ux * ux + uy * uy + uz * uz;
+        const float uF = ux * Fx + uy * Fy + uz * Fz;
+        const float le = c.lam_e, lo = c.lam_o;
+        const float gg = 2.0f + le;
+        const float qx = fmaf(-lo, jx, Fx), qy = fmaf(-lo, jy, Fy), qz = fmaf(-lo, jz, Fz);
+        const float base = fmaf(-1.5f * gg, uF, -le * fmaf(-1.5f * rho, usq, drho));
+        const float hle = 0.5f * le, hlo = 0.5f * lo;
+        const float k45 = -4.5f * le * rho;
+        if (!isfinite(rho) || !isfinite(usq)) atomicOr(a.status, ST_NONFINITE);
+        u[n] = ux;
+        (u + N)[n] = uy;
+        (u + 2 * N)[n] = uz;
+        a.vsig[n] = (unsigned char)(0x80u | sign_code(ux) | (sign_code(uy) << 2) | (sign_code(uz) << 4));
+        // ---- collide each pair and push-stream it (velocity bounce-back, Eq. 12) ----
+        g_out[n] = fmaf(1.0f + le, g[0], (float)wgt(0) * base);
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+          const float w = (float)wgt(i);
+          const float cu = cdotf(i, ux, uy, uz);
+          const float cf = cdotf(i, Fx, Fy, Fz);
+          const float cqv = cdotf(i, qx, qy, qz);
+          const float Ep = w * fmaf(cu, fmaf(4.5f * gg, cf, k45 * cu), base);
+          const float Em = 3.0f * w * cqv;
+          const float X = fmaf(hle, g[i] + g[i + 1], Ep);
+          const float Y = fmaf(hlo, g[i] - g[i + 1], Em);
+          const float gsd[2] = {g[i] + (X + Y), g[i + 1] + (X - Y)};
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int d = i + h;
+            if (fluid & (1u << d)) {
+              (g_out + d * N)[nbr32(d, x, y, z, b, nx, ny)] = gsd[h];
+            } else {
+              float cvb = 0.0f;
+              const int om = t.own[sl[1 + dcz(d)]][e0 + dcx(d) + HX * dcy(d)];
+              if (om >= 0) {
+                const DevParticle& P = a.parts[om];
+                const int xb = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
+                const int yb = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
+                const int zb = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
+                const double Xb = (double)(P.lo[0] + wrapi(xb - P.lo[0], nx));
+                const double Yb = (double)(P.lo[1] + wrapi(yb - P.lo[1], ny));
+                const double Zb = (double)(P.lo[2] + wrapi(zb - P.lo[2], nz));
+                const double dx = Xb - P.pos[0], dy = Yb - P.pos[1], dz = Zb - P.pos[2];
+                const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
+                const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
+                const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
+                cvb = (float)cdot(d, vx, vy, vz);
+              }
+              (g_out + opp(d) * N)[n] = gsd[h] - 6.0f * (float)wgt(d) * c.rho0 * cvb;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();  // the next load overwrites the slot of plane z - 1
+  }
   block_sum3(iv, a.ipart);
 }
 
@@ -430,10 +463,10 @@ cudaError_t launch_lb32(const LBArgs& a, cudaStream_t s) {
   const Phys32 c = make_phys32(a.ph);
   const bool pv = a.ph.pv != 0;
   switch (a.ph.K) {
-#define EK_CASE(KK)                                           \
-  case KK:                                                    \
-    if (pv) k_lb32<KK, true><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c);        \
-    else k_lb32<KK, false><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c);          \
+#define EK_CASE(KK)                                                            \
+  case KK:                                                                     \
+    if (pv) k_lb32_tiled<KK, true><<<lattice_grid32(a.g), lattice_block(), 0, s>>>(a, c);  \
+    else k_lb32_tiled<KK, false><<<lattice_grid32(a.g), lattice_block(), 0, s>>>(a, c);    \
     break;
     EK_CASE(0)
     EK_CASE(1)

@@ -811,17 +811,26 @@ cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// parts: 1 = everything up to the charge scatter (reads no species), 2 = the
+// transitions (read and write the species after S3); 3 = both
 template <class FM>
-cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s) {
+cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s, int parts = 3) {
   const Grid& g = a.g;
+  const int edge = (int)round(cbrt((double)a.boxmax)) + 1;
+  const unsigned uchunks = (unsigned)((edge * edge * edge + PT - 1) / PT);
+  if (!(parts & 1)) {
+    if (a.P == 0 || !transitions) return cudaSuccess;
+    k_transitions<FM><<<dim3(a.P, uchunks), PT, 0, s>>>(a);
+    k_apply_transfers<FM><<<152, 256, 0, s>>>(a);
+    cudaMemsetAsync(a.xfer_count, 0, sizeof(int), s);
+    return cudaGetLastError();
+  }
   if (!transitions) {
     k_reset_all<FM><<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(a);
   }
   if (a.P == 0) return cudaGetLastError();
   k_box_update<<<(a.P + 127) / 128, 128, 0, s>>>(a, !transitions);
   // union boxes are at most one cell wider than a box per axis
-  const int edge = (int)round(cbrt((double)a.boxmax)) + 1;
-  const unsigned uchunks = (unsigned)((edge * edge * edge + PT - 1) / PT);
   const unsigned bchunks = (unsigned)((a.boxmax + PT - 1) / PT);
   if (transitions) {
     k_save_prev<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
@@ -831,7 +840,7 @@ cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s) {
   k_claim<FM><<<dim3(a.P, bchunks), PT, 0, s>>>(a);
   k_psi_surface<FM><<<4 * 152, 32 * PSI_WARPS, 0, s>>>(a);
   k_charge_scatter<FM><<<dim3(a.P, bchunks), PT, 0, s>>>(a);
-  if (transitions) {
+  if (transitions && (parts & 2)) {
     k_transitions<FM><<<dim3(a.P, uchunks), PT, 0, s>>>(a);
     k_apply_transfers<FM><<<152, 256, 0, s>>>(a);
     cudaMemsetAsync(a.xfer_count, 0, sizeof(int), s);
@@ -846,8 +855,9 @@ cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s) {
   return a.ph.fp32 ? particle_forces_t<FormF32>(a, s) : particle_forces_t<FormF64>(a, s);
 }
 
-cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s) {
-  return a.ph.fp32 ? reflag_t<FormF32>(a, transitions, s) : reflag_t<FormF64>(a, transitions, s);
+cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s, int parts) {
+  return a.ph.fp32 ? reflag_t<FormF32>(a, transitions, s, parts)
+                   : reflag_t<FormF64>(a, transitions, s, parts);
 }
 
 }  // namespace ek
