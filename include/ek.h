@@ -185,7 +185,12 @@ ek_status ek_step_timed(ek_ctx* ctx, int nsteps, double stage_ms[6]);
  * context since it was created. */
 long long ek_kernel_launches(const ek_ctx* ctx);
 
-/* Use the CUDA stream `stream` (a cudaStream_t) for all later work. */
+/* Use the CUDA stream `stream` (a cudaStream_t) for all later work; waits for
+ * the work already enqueued on the previous stream first.  On a stream other
+ * than the legacy default one, ek_step / ek_step_async capture one step as a
+ * CUDA graph (one per parity of the double-buffered populations) and replay
+ * it; the graphs are rebuilt after a change of set-up, E, body force or
+ * stream.  Results are the same as with separate launches. */
 ek_status ek_set_stream(ek_ctx* ctx, void* stream);
 /* Wait for all enqueued work and check the device status word. */
 ek_status ek_sync(ek_ctx* ctx);

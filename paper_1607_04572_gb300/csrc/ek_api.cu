@@ -21,6 +21,9 @@ struct ek_ctx {
   cudaStream_t aux = nullptr;        // particle work of S4/S5 runs here, beside S3
   cudaEvent_t ev_lb = nullptr;       // S2 done
   cudaEvent_t ev_part = nullptr;     // S4 + re-flag done
+  // one captured step per parity of `cur` (the ping-pong buffers alternate)
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+  long long graph_launches = 0;      // kernels and memsets in one captured step
   int device = 0;
   int fp32 = 0;  // storage form (EK_FP32)
   // field storage: double (FP64 form) or float / int32 species (FP32 form)
@@ -214,6 +217,13 @@ LBArgs lb_args(ek_ctx* ctx) {
 }
 
 // pull the device particle records into the host copy
+void drop_graphs(ek_ctx* ctx) {
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->step_graph[i]) cudaGraphExecDestroy(ctx->step_graph[i]);
+    ctx->step_graph[i] = nullptr;
+  }
+}
+
 ek_status download_particles(ek_ctx* ctx) {
   if (ctx->P == 0) return EK_OK;
   ctx->hparts.resize(ctx->P);
@@ -228,6 +238,7 @@ ek_status download_particles(ek_ctx* ctx) {
 // step after particles or walls changed.
 ek_status run_setup(ek_ctx* ctx) {
   if (!ctx->setup_pending) return EK_OK;
+  drop_graphs(ctx);
   double rmax = 0.0;
   for (const DevParticle& q : ctx->hparts) rmax = std::max(rmax, q.radius);
   const int edge = (int)floor(2.0 * rmax) + 4;
@@ -392,6 +403,36 @@ ek_status enqueue_step(ek_ctx* ctx) {
   return EK_OK;
 }
 
+// A full step as a CUDA graph, replayed instead of ~30 separate launches.
+// Only on a caller-provided stream (the legacy default stream cannot be
+// captured); the graphs are dropped whenever a kernel argument changes (set-up,
+// E or body force, stream).
+ek_status step_graphed(ek_ctx* ctx) {
+  const int parity = ctx->cur;
+  if (!ctx->step_graph[parity]) {
+    const long long l0 = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    EK_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ek_status st = enqueue_step(ctx);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    ctx->cur = parity;  // nothing ran yet
+    if (st != EK_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(ctx, EK_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->step_graph[parity], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, EK_ERR_CUDA, std::string("step graph: ") + cudaGetErrorString(e));
+    ctx->graph_launches = ctx->launches - l0;
+    ctx->launches = l0;
+  }
+  EK_CUDA(cudaGraphLaunch(ctx->step_graph[parity], ctx->stream));
+  ctx->cur = 1 - parity;
+  ctx->launches += ctx->graph_launches;
+  return EK_OK;
+}
+
 ek_status ready(ek_ctx* ctx) {
   if (!ctx) return EK_ERR_ARG;
   if (ctx->broken) return fail(ctx, EK_ERR_STATE, "context is in an error state: " + ctx->err);
@@ -548,6 +589,7 @@ ek_status ek_destroy(ek_ctx* ctx) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);
+  drop_graphs(ctx);
   if (ctx->aux) {
     cudaStreamSynchronize(ctx->aux);
     cudaStreamDestroy(ctx->aux);
@@ -657,12 +699,17 @@ ek_status ek_set_field(ek_ctx* ctx, ek_field which, int component, const double*
       EK_CUDA(cudaMemcpyAsync(v, src, 3 * sizeof(double),
                               src_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
       EK_CUDA(cudaStreamSynchronize(s));
+      bool changed = false;
       for (int d = 0; d < 3; ++d) {
         if (!isfinite(v[d])) return fail(ctx, EK_ERR_ARG, "non-finite vector");
-        if (which == EK_FIELD_E_EXT) ctx->ph.E[d] = v[d];
-        else ctx->ph.g[d] = v[d];
+        double& dst = which == EK_FIELD_E_EXT ? ctx->ph.E[d] : ctx->ph.g[d];
+        changed |= dst != v[d];
+        dst = v[d];
       }
       update_derived(ctx->ph);
+      // the vectors reach the kernels as launch arguments, so captured steps
+      // hold the old value
+      if (changed) drop_graphs(ctx);
       break;
     }
     case EK_FIELD_WALL:
@@ -791,7 +838,7 @@ ek_status ek_step_async(ek_ctx* ctx, int nsteps) {
   if (st != EK_OK) return st;
   if (nsteps < 0) return fail(ctx, EK_ERR_ARG, "nsteps < 0");
   for (int t = 0; t < nsteps; ++t) {
-    st = enqueue_step(ctx);
+    st = ctx->stream ? step_graphed(ctx) : enqueue_step(ctx);
     if (st != EK_OK) return st;
   }
   return EK_OK;
@@ -880,6 +927,10 @@ int ek_num_particles(const ek_ctx* ctx) { return ctx ? ctx->P : 0; }
 
 ek_status ek_set_stream(ek_ctx* ctx, void* stream) {
   if (!ctx) return EK_ERR_ARG;
+  if ((cudaStream_t)stream != ctx->stream) {
+    EK_CUDA(cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);
+  }
   ctx->stream = (cudaStream_t)stream;
   return EK_OK;
 }
