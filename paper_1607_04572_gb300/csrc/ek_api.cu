@@ -61,6 +61,7 @@ struct ek_ctx {
   int* surf_count = nullptr;
   Transfer* xfer = nullptr;
   int* xfer_count = nullptr;
+  int* ticket = nullptr;
   int xfer_cap = 0;
   int* status = nullptr;
   int cur = 0;
@@ -186,6 +187,7 @@ PartArgs part_args(ek_ctx* ctx) {
   a.psum = ctx->psum;
   a.surf = ctx->surf;
   a.surf_count = ctx->surf_count;
+  a.ticket = ctx->ticket;
   a.surf_cap = (int)std::min<size_t>(ctx->psibox_cap, (size_t)1 << 30);
   a.status = ctx->status;
   return a;
@@ -358,7 +360,7 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
     case 4: {
       PartArgs a = part_args(ctx);
       EK_CUDA(launch_particle_forces(a, s));
-      ctx->launches += ctx->P > 0 ? 5 : 0;
+      ctx->launches += ctx->P > 0 ? 4 : 0;
       return EK_OK;
     }
     case 5: {
@@ -398,7 +400,7 @@ ek_status enqueue_step(ek_ctx* ctx) {
   if (ctx->P) {
     EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_part, 0));
     EK_CUDA(launch_reflag(pa, true, s, 2));
-    ctx->launches += 15;
+    ctx->launches += 14;
   }
   return EK_OK;
 }
@@ -545,6 +547,7 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   alloc((void**)&ctx->xfer_count, sizeof(int));
   alloc((void**)&ctx->surf_count, sizeof(int));
   alloc((void**)&ctx->status, sizeof(int));
+  alloc((void**)&ctx->ticket, sizeof(int));
   if (!ok) {
     ek_destroy(ctx);
     return EK_ERR_NOMEM;
@@ -557,6 +560,7 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   cudaMemset(ctx->fkey, 0xFF, N * sizeof(unsigned long long));
   cudaMemset(ctx->xfer_count, 0, sizeof(int));
   cudaMemset(ctx->status, 0, sizeof(int));
+  cudaMemset(ctx->ticket, 0, sizeof(int));
   for (int b = 0; b < 2; ++b) {
     cudaMemset(ctx->f[b], 0, 19 * N * rsz);
     cudaMemset(ctx->rho[b], 0, K * N * ssz);
@@ -585,7 +589,7 @@ ek_status ek_destroy(ek_ctx* ctx) {
                   ctx->qwall, ctx->u, ctx->tmp, ctx->owner, ctx->owner_prev, ctx->wall,
                   ctx->spectrum, ctx->dparts, ctx->psibox, ctx->fpart, ctx->surf, ctx->xfer,
                   ctx->xfer_count, ctx->surf_count, ctx->status, ctx->ifield, ctx->ipart,
-                  ctx->fkey, ctx->psum, ctx->vsig};
+                  ctx->fkey, ctx->psum, ctx->vsig, ctx->ticket};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);

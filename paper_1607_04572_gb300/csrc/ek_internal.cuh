@@ -283,10 +283,13 @@ struct PartArgs {
   int2* surf;      // (particle, box cell) of the cells cut by a sphere surface
   int* surf_count;
   int surf_cap;
+  int* ticket;     // blocks of the S4 sum kernel done (reset by the last one)
   int* status;
 };
-// cells per CTA of the S4 force kernel; fpart holds P * fchunks * FPART doubles
-constexpr int FORCE_CHUNK = 128;
+// cells per CTA of the S4 force kernel (FORCE_T threads, FORCE_CHUNK / FORCE_T
+// cells each); fpart holds P * fchunks * FPART doubles
+constexpr int FORCE_T = 128;
+constexpr int FORCE_CHUNK = 512;
 constexpr int FPART = 18;  // Fh Th (momentum exchange) Fs Ts (solute) Fq Tq (field on charge)
 cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s);  // S4
 // S5; parts: 1 = re-flag, Psi and charge (no species access), 2 = transitions

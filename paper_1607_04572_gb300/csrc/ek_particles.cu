@@ -191,8 +191,9 @@ __device__ void block_sum(double (&v)[NV]) {
 //                    momentum exchange (Eq. 11), the solute force on the
 //                    particle (reaction of the internal solute force on the
 //                    fluid of its nodes) and the field on its own charge
-//   k_particle_integrate  one block: remainder of the solute force on nodes
-//                    no particle claims, split evenly; symplectic Euler
+//   k_psum_integrate  per-particle and lattice sums; the last block takes the
+//                    remainder of the solute force on nodes no particle
+//                    claims, split evenly, and integrates (symplectic Euler)
 //   k_key_reset      clears the keys of the widened boxes
 // All sums run in a fixed order, so the result is deterministic.
 // ---------------------------------------------------------------------------
@@ -250,14 +251,39 @@ __global__ void k_key_reset(PartArgs a) {
   a.fkey[n] = ~0ULL;
 }
 
+// Sum of FORCE_T values per component, fixed order: the block's values are
+// transposed through shared memory and each of 4 threads per component adds a
+// strided quarter, then one thread adds the quarters.  Components of a group
+// no thread touched are skipped (they stay 0).  Result in out[j] for
+// threadIdx.x == j < NV.  Few FP64 instructions: a warp-shuffle tree would
+// spend 5 * NV double adds per thread.
+template <int NV>
+__device__ void block_sum_t(const double (&v)[NV], const bool (&group_on)[NV / 6], double* out) {
+  __shared__ double tr[NV][FORCE_T + 1];
+  __shared__ double quarter[NV][4];
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < NV; ++j)
+    if (group_on[j / 6]) tr[j][t] = v[j];
+  __syncthreads();
+  if (t < 4 * NV) {
+    const int j = t >> 2, w = t & 3;
+    double s = 0.0;
+    if (group_on[j / 6])
+      for (int i = w; i < FORCE_T; i += 4) s += tr[j][i];
+    quarter[j][w] = s;
+  }
+  __syncthreads();
+  if (t < NV) out[t] = ((quarter[t][0] + quarter[t][1]) + quarter[t][2]) + quarter[t][3];
+}
+
 template <class FM>
-__global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
+__global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   const int p = blockIdx.x;
   const DevParticle& P = a.parts[p];
   const Grid g = a.g;
   const long long N = g.N;
   const int ncell = box_cells(P.elo, P.ehi);
-  const int c = blockIdx.y * FORCE_CHUNK + threadIdx.x;
   if (blockIdx.y * FORCE_CHUNK >= ncell) return;  // whole CTA beyond the widened box
   const bool pv = a.ph.pv != 0;
   double qnorm = 0.0;
@@ -272,10 +298,13 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
   double acc[FPART];
 #pragma unroll
   for (int j = 0; j < FPART; ++j) acc[j] = 0.0;
-  int X, Y, Z;
-  long long n;
-  double mx, my, mz;
-  if (c < ncell) {
+  bool touched[3] = {false, false, false};
+  for (int k = 0; k < FORCE_CHUNK / FORCE_T; ++k) {
+    const int c = blockIdx.y * FORCE_CHUNK + k * FORCE_T + threadIdx.x;
+    if (c >= ncell) break;
+    int X, Y, Z;
+    long long n;
+    double mx, my, mz;
     int w3[3];
     const bool first = ext_cell(P, c, g, X, Y, Z, n, mx, my, mz, w3);
     const int own = a.owner[n];
@@ -289,6 +318,7 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
         const long long m = node_index(g, nb_x(b, w3[0], dcx(i)), nb_y(b, w3[1], dcy(i)),
                                        nb_z(b, w3[2], dcz(i)));
         if (a.owner[m] != p) continue;
+        touched[0] = true;
         const double dx = (double)(X + dcx(i)) - P.pos[0];
         const double dy = (double)(Y + dcy(i)) - P.pos[1];
         const double dz = (double)(Z + dcz(i)) - P.pos[2];
@@ -312,6 +342,7 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
     }
     // reaction of the internal solute force on the fluid nodes this particle claims
     if (first && own == FLUID && (int)(a.fkey[n] & 0xFFFFFull) == p) {
+      touched[1] = true;
       const double ix = real_at<FM>(a.ifield, n);
       const double iy = real_at<FM>(a.ifield, N + n);
       const double iz = real_at<FM>(a.ifield, 2 * N + n);
@@ -333,6 +364,7 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
         qq = qnorm;
       }
       if (qq != 0.0) {
+        touched[2] = true;
         const double fx = qq * a.ph.E[0], fy = qq * a.ph.E[1], fz = qq * a.ph.E[2];
         const double dx = (double)X - P.pos[0], dy = (double)Y - P.pos[1], dz = (double)Z - P.pos[2];
         acc[12] += fx;
@@ -344,97 +376,117 @@ __global__ void __launch_bounds__(FORCE_CHUNK) k_particle_forces(PartArgs a) {
       }
     }
   }
-  block_sum<FPART>(acc);
-  if (threadIdx.x == 0) {
-    double* out = a.fpart + ((long long)p * a.fchunks + blockIdx.y) * FPART;
-#pragma unroll
-    for (int j = 0; j < FPART; ++j) out[j] = acc[j];
-  }
+  bool on[3];
+  on[0] = __syncthreads_or(touched[0]);
+  on[1] = __syncthreads_or(touched[1]);
+  on[2] = __syncthreads_or(touched[2]);
+  double* out = a.fpart + ((long long)p * a.fchunks + blockIdx.y) * FPART;
+  block_sum_t<FPART>(acc, on, out);
 }
 
-constexpr int INTEGRATE_T = 512;
 constexpr int PSUM_T = 256;
 constexpr int PSUM_LAT = 64;  // blocks that sum the lattice-block partials
 
-// Block p < P: the chunk partials of particle p, summed in a fixed order into
-// psum[p]; blocks P + l, l < PSUM_LAT: slice l of the lattice-block sums of the
-// internal solute force into psum[P + l].  Thread t takes the items t,
-// t + PSUM_T, ... of its range; then a fixed tree.
-__global__ void __launch_bounds__(PSUM_T) k_psum(PartArgs a) {
-  __shared__ double red[PSUM_T];
-  const int p = blockIdx.x;
-  const bool lattice = p >= a.P;
-  int first = 0, nitem;
-  if (lattice) {
-    const int l = p - a.P;
+// Column sums of a row-major table (nrow rows of `stride` doubles; columns
+// col0 .. col0 + NC - 1), fixed order: thread t < G * NC takes column t % NC
+// of rows t / NC, t / NC + G, ... (consecutive threads read consecutive
+// addresses), then thread j < NC adds the G partials in order.  Result in
+// out[j] for threadIdx.x == j.
+template <int NC>
+__device__ void column_sums(const double* tab, int nrow, int stride, int col0, double* out) {
+  constexpr int G = PSUM_T / NC;
+  __shared__ double part[G * NC];
+  const int t = threadIdx.x;
+  if (t < G * NC) {
+    const int j = t % NC, r0 = t / NC;
+    double s = 0.0;
+    for (int r = r0; r < nrow; r += G) s += __ldcg(tab + (long long)r * stride + col0 + j);
+    part[t] = s;
+  }
+  __syncthreads();
+  if (t < NC) {
+    double s = 0.0;
+    for (int r = 0; r < G; ++r) s += part[r * NC + t];
+    out[t] = s;
+  }
+  __syncthreads();
+}
+
+// Blocks p < P: the chunk partials of particle p summed into psum[p]; blocks
+// P + l, l < PSUM_LAT: slice l of the lattice-block sums of the internal
+// solute force into psum[P + l].  The last block to finish (ticket) then
+// takes the remainder of the solute force on nodes no particle claims
+// (lattice total minus the claimed sums), splits it evenly, and moves every
+// particle by symplectic Euler (Sec. III.B).  Every sum runs in a fixed order,
+// whichever block comes last.
+__global__ void __launch_bounds__(PSUM_T) k_psum_integrate(PartArgs a) {
+  __shared__ double res[FPART];
+  __shared__ bool last;
+  const int b = blockIdx.x;
+  if (b >= a.P) {
+    const int l = b - a.P;
     const int per = (a.nipart + PSUM_LAT - 1) / PSUM_LAT;
-    first = l * per;
-    nitem = max(0, min(per, a.nipart - first));
+    const int first = l * per;
+    const int nrow = max(0, min(per, a.nipart - first));
+    column_sums<3>(a.ipart + 3LL * first, nrow, 3, 0, res);
+    if (threadIdx.x < 3) a.psum[(long long)b * FPART + threadIdx.x] = res[threadIdx.x];
   } else {
-    nitem = (box_cells(a.parts[p].elo, a.parts[p].ehi) + FORCE_CHUNK - 1) / FORCE_CHUNK;
+    const int nrow = (box_cells(a.parts[b].elo, a.parts[b].ehi) + FORCE_CHUNK - 1) / FORCE_CHUNK;
+    column_sums<FPART>(a.fpart + (long long)b * a.fchunks * FPART, nrow, FPART, 0, res);
+    if (threadIdx.x < FPART) a.psum[(long long)b * FPART + threadIdx.x] = res[threadIdx.x];
   }
-  const int ncomp = lattice ? 3 : FPART;
-  for (int j = 0; j < ncomp; ++j) {
-    double v = 0.0;
-    for (int it = threadIdx.x; it < nitem; it += PSUM_T)
-      v += lattice ? a.ipart[3 * (first + it) + j] : a.fpart[((long long)p * a.fchunks + it) * FPART + j];
-    red[threadIdx.x] = v;
-    __syncthreads();
-    for (int w = PSUM_T / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) a.psum[(long long)p * FPART + j] = red[0];
-    __syncthreads();
-  }
-}
-
-__device__ __forceinline__ double block_sum_one(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __threadfence();
   __syncthreads();
-  if (lane == 0) red[warp] = v;
+  if (threadIdx.x == 0) last = atomicAdd(a.ticket, 1) == (int)gridDim.x - 1;
   __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-  return s;
-}
-
-// remainder of the solute force (lattice total minus what the particles
-// claimed), split evenly; then symplectic Euler, one thread per particle
-__global__ void __launch_bounds__(INTEGRATE_T) k_particle_integrate(PartArgs a) {
-  __shared__ double red[INTEGRATE_T / 32];
-  double claimed[3] = {0.0, 0.0, 0.0};
-  for (int p = threadIdx.x; p < a.P; p += blockDim.x)
-    for (int d = 0; d < 3; ++d) claimed[d] -= a.psum[(long long)p * FPART + 6 + d];
+  if (!last) return;
+  __threadfence();
+  // claimed solute force (psum columns 6..8 of the particles) and lattice total
+  __shared__ double claimed[3], total[3];
+  column_sums<3>(a.psum, a.P, FPART, 6, claimed);
+  column_sums<3>(a.psum + (long long)a.P * FPART, PSUM_LAT, FPART, 0, total);
   double rem[3];
-  for (int d = 0; d < 3; ++d) {
-    double tot = 0.0;
-    for (int l = 0; l < PSUM_LAT; ++l) tot += a.psum[(long long)(a.P + l) * FPART + d];
-    rem[d] = (tot - block_sum_one(claimed[d], red)) / (double)a.P;
-  }
+  for (int d = 0; d < 3; ++d) rem[d] = (total[d] + claimed[d]) / (double)a.P;  // claimed holds -sum i
   for (int p = threadIdx.x; p < a.P; p += blockDim.x) {
-    DevParticle& P = a.parts[p];
-    const double* acc = a.psum + (long long)p * FPART;
+    DevParticle* Pp = a.parts + p;
+    double acc[FPART];
+#pragma unroll
+    for (int j = 0; j < FPART; ++j) acc[j] = __ldcg(a.psum + (long long)p * FPART + j);
+    double pos[3], vel[3], omega[3], ftrans[3];
+    for (int d = 0; d < 3; ++d) {
+      pos[d] = Pp->pos[d];
+      vel[d] = Pp->vel[d];
+      omega[d] = Pp->omega[d];
+      ftrans[d] = Pp->ftrans[d];
+    }
+    const double mass = Pp->mass, inertia = Pp->inertia;
+    const bool fixed = Pp->fixed;
     double F[3], T[3];
     for (int d = 0; d < 3; ++d) {
-      F[d] = acc[d] + acc[6 + d] + acc[12 + d] - rem[d] + P.ftrans[d];
+      F[d] = acc[d] + acc[6 + d] + acc[12 + d] - rem[d] + ftrans[d];
       T[d] = acc[3 + d] + acc[9 + d] + acc[15 + d];
-      P.force[d] = F[d];
-      P.torque[d] = T[d];
-      P.ftrans[d] = 0.0;
     }
-    if (P.fixed) continue;
-    const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
+    if (!fixed) {
+      const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
+      for (int d = 0; d < 3; ++d) {
+        vel[d] = vel[d] + F[d] / mass;
+        omega[d] = omega[d] + T[d] / inertia;
+        pos[d] = pos[d] + vel[d];
+        if (pos[d] >= (double)nn[d]) pos[d] -= (double)nn[d];
+        else if (pos[d] < 0.0) pos[d] += (double)nn[d];
+      }
+      if (!isfinite(pos[0] + pos[1] + pos[2])) atomicOr(a.status, ST_NONFINITE);
+    }
     for (int d = 0; d < 3; ++d) {
-      P.vel[d] = P.vel[d] + F[d] / P.mass;
-      P.omega[d] = P.omega[d] + T[d] / P.inertia;
-      P.pos[d] = P.pos[d] + P.vel[d];
-      if (P.pos[d] >= (double)nn[d]) P.pos[d] -= (double)nn[d];
-      else if (P.pos[d] < 0.0) P.pos[d] += (double)nn[d];
+      Pp->force[d] = F[d];
+      Pp->torque[d] = T[d];
+      Pp->ftrans[d] = 0.0;
+      Pp->pos[d] = pos[d];
+      Pp->vel[d] = vel[d];
+      Pp->omega[d] = omega[d];
     }
-    if (!isfinite(P.pos[0] + P.pos[1] + P.pos[2])) atomicOr(a.status, ST_NONFINITE);
   }
+  if (threadIdx.x == 0) *a.ticket = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -544,10 +596,16 @@ __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
 
 constexpr int PSI_WARPS = 4;  // warps per CTA of k_psi_surface
 
+// Sub-cubes whose float pre-test is inconclusive (a corner within the margin
+// of the surface: common when the centre sits on a dyadic position) are queued
+// per warp and given the FP64 test 32 at a time, so a warp never runs the
+// double-precision path for a single lane.
 template <class FM>
 __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
   __shared__ unsigned short queue[PSI_WARPS][2][512];
+  __shared__ unsigned short fbq[PSI_WARPS][64];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   const int count = min(*a.surf_count, a.surf_cap);
   for (int e = blockIdx.x * PSI_WARPS + wid; e < count; e += gridDim.x * PSI_WARPS) {
     const int2 pc = a.surf[e];
@@ -561,6 +619,7 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
     const float oz = (float)((double)Z - P.pos[2]);
     unsigned short* cur = queue[wid][0];
     unsigned short* nxt = queue[wid][1];
+    unsigned short* fb = fbq[wid];
     if (lane == 0) cur[0] = 0;
     __syncwarp();
     int qlen = 1;
@@ -568,30 +627,53 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
     for (int l = 1; l <= PSI_DEPTH && qlen > 0; ++l) {
       const int ntask = qlen * 8;
       const float h = ldexpf(1.0f, -(l + 1));
-      int newlen = 0;
+      const int in_units = 2 << (3 * (PSI_DEPTH - l));
+      int newlen = 0, nfb = 0;
       for (int t0 = 0; t0 < ntask; t0 += 32) {
         const int t = t0 + lane;
-        bool und = false;
+        bool und = false, exact = false;
         int path = 0;
         if (t < ntask) {
           path = ((int)cur[t >> 3] << 3) | (t & 7);
           float cx, cy, cz;
           subcube_centre_f(path, l, ox, oy, oz, cx, cy, cz);
-          int st = classify_f32(cx, cy, cz, h, R2f, margin);
-          if (st < 0) {
-            double ex, ey, ez;
-            subcube_centre_d(path, l, (double)X, (double)Y, (double)Z, ex, ey, ez);
-            st = classify(ex, ey, ez, ldexp(1.0, -(l + 1)), P.pos, R2);
-          }
-          if (st == CUBE_IN) units += 2 << (3 * (PSI_DEPTH - l));
+          const int st = classify_f32(cx, cy, cz, h, R2f, margin);
+          if (st < 0) exact = true;
+          else if (st == CUBE_IN) units += in_units;
           else if (st == CUBE_UNDECIDED) {
             if (l == PSI_DEPTH) units += 1;
             else und = true;
           }
         }
-        const unsigned mask = __ballot_sync(0xffffffffu, und);
-        if (und) nxt[newlen + __popc(mask & ((1u << lane) - 1u))] = (unsigned short)path;
+        unsigned mask = __ballot_sync(0xffffffffu, und);
+        if (und) nxt[newlen + __popc(mask & lt)] = (unsigned short)path;
         newlen += __popc(mask);
+        mask = __ballot_sync(0xffffffffu, exact);
+        if (exact) fb[nfb + __popc(mask & lt)] = (unsigned short)path;
+        nfb += __popc(mask);
+        const bool level_end = t0 + 32 >= ntask;
+        while (nfb >= 32 || (level_end && nfb > 0)) {
+          __syncwarp();
+          const int take = min(nfb, 32);
+          bool und2 = false;
+          int path2 = 0;
+          if (lane < take) {
+            path2 = fb[nfb - take + lane];
+            double ex, ey, ez;
+            subcube_centre_d(path2, l, (double)X, (double)Y, (double)Z, ex, ey, ez);
+            const int st = classify(ex, ey, ez, ldexp(1.0, -(l + 1)), P.pos, R2);
+            if (st == CUBE_IN) units += in_units;
+            else if (st == CUBE_UNDECIDED) {
+              if (l == PSI_DEPTH) units += 1;
+              else und2 = true;
+            }
+          }
+          const unsigned m2 = __ballot_sync(0xffffffffu, und2);
+          if (und2) nxt[newlen + __popc(m2 & lt)] = (unsigned short)path2;
+          newlen += __popc(m2);
+          nfb -= take;
+          __syncwarp();
+        }
       }
       __syncwarp();
       unsigned short* tmp = cur;
@@ -804,9 +886,8 @@ template <class FM>
 cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s) {
   const unsigned echunks = (unsigned)((a.emax + PT - 1) / PT);
   k_force_assign<<<dim3(a.P, echunks), PT, 0, s>>>(a);
-  k_particle_forces<FM><<<dim3(a.P, a.fchunks), FORCE_CHUNK, 0, s>>>(a);
-  k_psum<<<a.P + PSUM_LAT, PSUM_T, 0, s>>>(a);
-  k_particle_integrate<<<1, INTEGRATE_T, 0, s>>>(a);
+  k_particle_forces<FM><<<dim3(a.P, a.fchunks), FORCE_T, 0, s>>>(a);
+  k_psum_integrate<<<a.P + PSUM_LAT, PSUM_T, 0, s>>>(a);
   k_key_reset<<<dim3(a.P, echunks), PT, 0, s>>>(a);
   return cudaGetLastError();
 }
