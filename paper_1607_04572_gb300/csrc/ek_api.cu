@@ -367,7 +367,7 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
       PartArgs a = part_args(ctx);
       if (ctx->P) {
         EK_CUDA(launch_reflag(a, true, s));
-        ctx->launches += 10;
+        ctx->launches += 9;
       }
       return EK_OK;
     }
@@ -400,7 +400,7 @@ ek_status enqueue_step(ek_ctx* ctx) {
   if (ctx->P) {
     EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_part, 0));
     EK_CUDA(launch_reflag(pa, true, s, 2));
-    ctx->launches += 14;
+    ctx->launches += 13;
   }
   return EK_OK;
 }

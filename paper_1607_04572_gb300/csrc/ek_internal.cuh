@@ -287,10 +287,14 @@ struct PartArgs {
   int* status;
 };
 // cells per CTA of the S4 force kernel (FORCE_T threads, FORCE_CHUNK / FORCE_T
-// cells each); fpart holds P * fchunks * FPART doubles
+// rows of FORCE_T cells each); fpart holds P * fchunks * FPART doubles
 constexpr int FORCE_T = 128;
 constexpr int FORCE_CHUNK = 512;
-constexpr int FPART = 18;  // Fh Th (momentum exchange) Fs Ts (solute) Fq Tq (field on charge)
+// per particle: [0..5] Fh Th (momentum exchange), [6..11] Fs Ts (reaction of
+// the solute force), [12] sum q and [13..15] sum q (r - r_p) of the particle's
+// own charge (the field's force and torque are E and M x E times these),
+// [16..17] unused
+constexpr int FPART = 18;
 cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s);  // S4
 // S5; parts: 1 = re-flag, Psi and charge (no species access), 2 = transitions
 // (species after S3), 3 = both

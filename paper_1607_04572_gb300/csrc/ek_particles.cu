@@ -277,6 +277,16 @@ __device__ void block_sum_t(const double (&v)[NV], const bool (&group_on)[NV / 6
   if (t < NV) out[t] = ((quarter[t][0] + quarter[t][1]) + quarter[t][2]) + quarter[t][3];
 }
 
+// Per fluid node x next to particle p, with d0 = x - r_p and
+// w = V + Omega x d0: the boundary velocity of a link c_i (at x + c_i or its
+// midpoint) has c_i . v_b = c_i . w, since c_i . (Omega x c_i) = 0, and the
+// link torque (x + c_i - r_p) x F_i sums to d0 x sum_i F_i, since
+// c_i x c_i = 0.  So the per-link work is one dot product and one add.
+// The field on the particle's own charge is kept as sum q and sum q (r - r_p)
+// (force E sum q, torque (sum q (r - r_p)) x E).
+// Block (p, b) takes the rows b, b + nb, b + 2 nb, ... of FORCE_T cells of the
+// widened box (nb blocks for this particle), so the cells next to the sphere
+// are spread over all blocks.
 template <class FM>
 __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   const int p = blockIdx.x;
@@ -284,7 +294,8 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   const Grid g = a.g;
   const long long N = g.N;
   const int ncell = box_cells(P.elo, P.ehi);
-  if (blockIdx.y * FORCE_CHUNK >= ncell) return;  // whole CTA beyond the widened box
+  const int nb = (ncell + FORCE_CHUNK - 1) / FORCE_CHUNK;
+  if ((int)blockIdx.y >= nb) return;  // whole CTA beyond this particle's widened box
   const bool pv = a.ph.pv != 0;
   double qnorm = 0.0;
   if (pv) {
@@ -294,13 +305,13 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   } else {
     qnorm = P.nb > 0 ? P.charge / (double)P.nb : 0.0;
   }
-  // Fh Th | Fs Ts | Fq Tq
+  const double rho0 = a.ph.rho0;
   double acc[FPART];
 #pragma unroll
   for (int j = 0; j < FPART; ++j) acc[j] = 0.0;
   bool touched[3] = {false, false, false};
   for (int k = 0; k < FORCE_CHUNK / FORCE_T; ++k) {
-    const int c = blockIdx.y * FORCE_CHUNK + k * FORCE_T + threadIdx.x;
+    const int c = ((int)blockIdx.y + k * nb) * FORCE_T + threadIdx.x;
     if (c >= ncell) break;
     int X, Y, Z;
     long long n;
@@ -312,32 +323,34 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
                         Z >= P.lo[2] && Z < P.hi[2];
     if (own == FLUID && in_box) {
       // momentum exchange on every link from this fluid node into the particle (Eq. 11)
+      const double d0x = (double)X - P.pos[0], d0y = (double)Y - P.pos[1], d0z = (double)Z - P.pos[2];
+      const double wx = P.vel[0] + (P.omega[1] * d0z - P.omega[2] * d0y);
+      const double wy = P.vel[1] + (P.omega[2] * d0x - P.omega[0] * d0z);
+      const double wz = P.vel[2] + (P.omega[0] * d0y - P.omega[1] * d0x);
       const Nbr b = make_nbr(w3[0], w3[1], w3[2], g);
+      double fx = 0.0, fy = 0.0, fz = 0.0;
+      bool link = false;
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         const long long m = node_index(g, nb_x(b, w3[0], dcx(i)), nb_y(b, w3[1], dcy(i)),
                                        nb_z(b, w3[2], dcz(i)));
         if (a.owner[m] != p) continue;
-        touched[0] = true;
-        const double dx = (double)(X + dcx(i)) - P.pos[0];
-        const double dy = (double)(Y + dcy(i)) - P.pos[1];
-        const double dz = (double)(Z + dcz(i)) - P.pos[2];
-        const double vbx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
-        const double vby = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
-        const double vbz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
-        const double cvb = cdot(i, vbx, vby, vbz);
-        const double refl = pop_abs<FM>(a.f, opp(i), N, n, a.ph.rho0);
-        const double fs = refl + 6.0 * wgt(i) * a.ph.rho0 * cvb;  // the population that hit the wall
+        link = true;
+        const double refl = pop_abs<FM>(a.f, opp(i), N, n, rho0);
+        const double fs = refl + 6.0 * wgt(i) * rho0 * cdot(i, wx, wy, wz);  // the population that hit the wall
         const double mom = fs + refl;
-        const double px = dcx(i) ? csgn(dcx(i), mom) : 0.0;
-        const double py = dcy(i) ? csgn(dcy(i), mom) : 0.0;
-        const double pz = dcz(i) ? csgn(dcz(i), mom) : 0.0;
-        acc[0] += px;
-        acc[1] += py;
-        acc[2] += pz;
-        acc[3] += dy * pz - dz * py;
-        acc[4] += dz * px - dx * pz;
-        acc[5] += dx * py - dy * px;
+        if (dcx(i)) fx = dcx(i) > 0 ? fx + mom : fx - mom;
+        if (dcy(i)) fy = dcy(i) > 0 ? fy + mom : fy - mom;
+        if (dcz(i)) fz = dcz(i) > 0 ? fz + mom : fz - mom;
+      }
+      if (link) {
+        touched[0] = true;
+        acc[0] += fx;
+        acc[1] += fy;
+        acc[2] += fz;
+        acc[3] += d0y * fz - d0z * fy;
+        acc[4] += d0z * fx - d0x * fz;
+        acc[5] += d0x * fy - d0y * fx;
       }
     }
     // reaction of the internal solute force on the fluid nodes this particle claims
@@ -353,7 +366,7 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
       acc[10] -= mz * ix - mx * iz;
       acc[11] -= mx * iy - my * ix;
     }
-    // the external field on the particle's own charge in this cell
+    // the particle's own charge in this cell
     if (in_box) {
       double qq = 0.0;
       if (pv) {
@@ -365,14 +378,10 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
       }
       if (qq != 0.0) {
         touched[2] = true;
-        const double fx = qq * a.ph.E[0], fy = qq * a.ph.E[1], fz = qq * a.ph.E[2];
-        const double dx = (double)X - P.pos[0], dy = (double)Y - P.pos[1], dz = (double)Z - P.pos[2];
-        acc[12] += fx;
-        acc[13] += fy;
-        acc[14] += fz;
-        acc[15] += dy * fz - dz * fy;
-        acc[16] += dz * fx - dx * fz;
-        acc[17] += dx * fy - dy * fx;
+        acc[12] += qq;
+        acc[13] += qq * ((double)X - P.pos[0]);
+        acc[14] += qq * ((double)Y - P.pos[1]);
+        acc[15] += qq * ((double)Z - P.pos[2]);
       }
     }
   }
@@ -382,6 +391,28 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   on[2] = __syncthreads_or(touched[2]);
   double* out = a.fpart + ((long long)p * a.fchunks + blockIdx.y) * FPART;
   block_sum_t<FPART>(acc, on, out);
+}
+
+// New box of a particle at `pos`: the cells within R (+1 below, +2 above),
+// the union with the previous box (moved into the periodic image of the new
+// one, as the position wraps when the particle crosses the boundary), and the
+// box widened by ceil(R) + FORCE_MARGIN for the solute-force assignment.
+__device__ void box_update_one(DevParticle& P, const double pos[3], const int nn[3], bool setup) {
+  for (int d = 0; d < 3; ++d) {
+    const int lo = (int)floor(pos[d] - P.radius) - 1;
+    const int hi = (int)floor(pos[d] + P.radius) + 2;
+    int olo = P.lo[d], ohi = P.hi[d];
+    const int shift = (int)rint((double)(lo - olo) / (double)nn[d]) * nn[d];
+    olo += shift;
+    ohi += shift;
+    P.ulo[d] = setup ? lo : min(lo, olo);
+    P.uhi[d] = setup ? hi : max(hi, ohi);
+    P.lo[d] = lo;
+    P.hi[d] = hi;
+    const int m = (int)ceil(P.radius) + FORCE_MARGIN;
+    P.elo[d] = lo - m;
+    P.ehi[d] = hi + m;
+  }
 }
 
 constexpr int PSUM_T = 256;
@@ -447,6 +478,8 @@ __global__ void __launch_bounds__(PSUM_T) k_psum_integrate(PartArgs a) {
   column_sums<3>(a.psum + (long long)a.P * FPART, PSUM_LAT, FPART, 0, total);
   double rem[3];
   for (int d = 0; d < 3; ++d) rem[d] = (total[d] + claimed[d]) / (double)a.P;  // claimed holds -sum i
+  const double E[3] = {a.ph.E[0], a.ph.E[1], a.ph.E[2]};
+  const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
   for (int p = threadIdx.x; p < a.P; p += blockDim.x) {
     DevParticle* Pp = a.parts + p;
     double acc[FPART];
@@ -461,13 +494,15 @@ __global__ void __launch_bounds__(PSUM_T) k_psum_integrate(PartArgs a) {
     }
     const double mass = Pp->mass, inertia = Pp->inertia;
     const bool fixed = Pp->fixed;
+    // field on the own charge: E sum q, (sum q (r - r_p)) x E
+    const double Tq[3] = {acc[14] * E[2] - acc[15] * E[1], acc[15] * E[0] - acc[13] * E[2],
+                          acc[13] * E[1] - acc[14] * E[0]};
     double F[3], T[3];
     for (int d = 0; d < 3; ++d) {
-      F[d] = acc[d] + acc[6 + d] + acc[12 + d] - rem[d] + ftrans[d];
-      T[d] = acc[3 + d] + acc[9 + d] + acc[15 + d];
+      F[d] = acc[d] + acc[6 + d] + acc[12] * E[d] - rem[d] + ftrans[d];
+      T[d] = acc[3 + d] + acc[9 + d] + Tq[d];
     }
     if (!fixed) {
-      const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
       for (int d = 0; d < 3; ++d) {
         vel[d] = vel[d] + F[d] / mass;
         omega[d] = omega[d] + T[d] / inertia;
@@ -485,6 +520,8 @@ __global__ void __launch_bounds__(PSUM_T) k_psum_integrate(PartArgs a) {
       Pp->vel[d] = vel[d];
       Pp->omega[d] = omega[d];
     }
+    // S5 starts here: the boxes follow the new position
+    if (isfinite(pos[0] + pos[1] + pos[2])) box_update_one(*Pp, pos, nn, false);
   }
   if (threadIdx.x == 0) *a.ticket = 0;
 }
@@ -492,34 +529,24 @@ __global__ void __launch_bounds__(PSUM_T) k_psum_integrate(PartArgs a) {
 // ---------------------------------------------------------------------------
 // S5 and set-up
 // ---------------------------------------------------------------------------
-__global__ void k_box_update(PartArgs a, bool setup) {
+// set-up only (in a step the box follows the position in k_psum_integrate)
+__global__ void k_box_update(PartArgs a) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.P) return;
   DevParticle& P = a.parts[p];
   const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
-  for (int d = 0; d < 3; ++d) {
-    const int lo = (int)floor(P.pos[d] - P.radius) - 1;
-    const int hi = (int)floor(P.pos[d] + P.radius) + 2;
-    // the previous box, moved into the periodic image of the new one (the
-    // position wraps when the particle crosses the boundary)
-    int olo = P.lo[d], ohi = P.hi[d];
-    const int shift = (int)rint((double)(lo - olo) / (double)nn[d]) * nn[d];
-    olo += shift;
-    ohi += shift;
-    P.ulo[d] = setup ? lo : min(lo, olo);
-    P.uhi[d] = setup ? hi : max(hi, ohi);
-    P.lo[d] = lo;
-    P.hi[d] = hi;
-    const int m = (int)ceil(P.radius) + FORCE_MARGIN;
-    P.elo[d] = lo - m;
-    P.ehi[d] = hi + m;
-  }
+  const double pos[3] = {P.pos[0], P.pos[1], P.pos[2]};
+  box_update_one(P, pos, nn, true);
   P.psisum = 0.0;
   P.nb = 0;
 }
 
 __global__ void k_save_prev(PartArgs a) {
-  const DevParticle& P = a.parts[blockIdx.x];
+  DevParticle& P = a.parts[blockIdx.x];
+  if (blockIdx.y == 0 && threadIdx.x == 0) {  // k_claim and k_psi_surface sum these afresh
+    P.psisum = 0.0;
+    P.nb = 0;
+  }
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
   if (c >= box_cells(P.ulo, P.uhi)) return;
   int X, Y, Z;
@@ -887,8 +914,9 @@ cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s) {
   const unsigned echunks = (unsigned)((a.emax + PT - 1) / PT);
   k_force_assign<<<dim3(a.P, echunks), PT, 0, s>>>(a);
   k_particle_forces<FM><<<dim3(a.P, a.fchunks), FORCE_T, 0, s>>>(a);
-  k_psum_integrate<<<a.P + PSUM_LAT, PSUM_T, 0, s>>>(a);
+  // before the integration moves the widened boxes
   k_key_reset<<<dim3(a.P, echunks), PT, 0, s>>>(a);
+  k_psum_integrate<<<a.P + PSUM_LAT, PSUM_T, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -910,7 +938,7 @@ cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s, int pa
     k_reset_all<FM><<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(a);
   }
   if (a.P == 0) return cudaGetLastError();
-  k_box_update<<<(a.P + 127) / 128, 128, 0, s>>>(a, !transitions);
+  if (!transitions) k_box_update<<<(a.P + 127) / 128, 128, 0, s>>>(a);
   // union boxes are at most one cell wider than a box per axis
   const unsigned bchunks = (unsigned)((a.boxmax + PT - 1) / PT);
   if (transitions) {
