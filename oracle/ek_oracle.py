@@ -617,7 +617,8 @@ class EKOracle:
         charge), particle p receives
             F_p = Z_p E - sum_{r in V_p} i(r) - (unassigned remainder) / P,
         where V_p are the fluid nodes of p's box widened by ceil(R) + 4 cells
-        for which p is the particle with the nearest surface (minimum image),
+        for which p is the particle with the nearest surface (minimum image;
+        distances compared in single precision, ties to the lower index),
         and the remainder is the sum of i over fluid nodes in no V_p.  Total
         momentum then changes only by E times the total charge (zero in a
         neutral box).  Torque: that of Z_p E on q_p(r) minus sum (r - r_p) x i.
@@ -645,9 +646,16 @@ class EKOracle:
             dx = self.min_image(Xc.astype(np.float64), p.pos[0], nx)
             dy = self.min_image(Yc.astype(np.float64), p.pos[1], ny)
             dz = self.min_image(Zc.astype(np.float64), p.pos[2], nz)
-            dsurf = np.sqrt(dx * dx + dy * dy + dz * dz) - p.radius
-            kq = np.floor((dsurf + 1024.0) * 1048576.0).astype(np.int64)
-            k = (kq << 20) | pid
+            # the nearest-surface decision is taken in IEEE single precision
+            # (squares summed left to right, correctly rounded sqrt); ties go
+            # to the lower index.  The key orders the float distances by
+            # their bit patterns (sign bit flipped, negatives complemented).
+            dxf, dyf, dzf = dx.astype(np.float32), dy.astype(np.float32), dz.astype(np.float32)
+            d2 = dxf * dxf + dyf * dyf + dzf * dzf
+            dsurf = np.sqrt(d2) - np.float32(p.radius)
+            bits = dsurf.view(np.uint32).astype(np.int64)
+            okey = np.where(bits >= 0x80000000, 0xFFFFFFFF - bits, bits + 0x80000000)
+            k = (okey << 20) | pid
             flat = (Xc + nx * (Yc + ny * Zc)).ravel()
             np.minimum.at(key.ravel(), flat, k.ravel())
             regions.append((flat, dx.ravel(), dy.ravel(), dz.ravel()))

@@ -62,6 +62,7 @@ struct ek_ctx {
   Transfer* xfer = nullptr;
   int* xfer_count = nullptr;
   int* ticket = nullptr;
+  int* pticket = nullptr;   // Pcap: force blocks done per particle
   int xfer_cap = 0;
   int* status = nullptr;
   int cur = 0;
@@ -188,6 +189,7 @@ PartArgs part_args(ek_ctx* ctx) {
   a.surf = ctx->surf;
   a.surf_count = ctx->surf_count;
   a.ticket = ctx->ticket;
+  a.pticket = ctx->pticket;
   a.surf_cap = (int)std::min<size_t>(ctx->psibox_cap, (size_t)1 << 30);
   a.status = ctx->status;
   return a;
@@ -253,7 +255,9 @@ ek_status run_setup(ek_ctx* ctx) {
     if (ctx->fpart) cudaFree(ctx->fpart);
     if (ctx->surf) cudaFree(ctx->surf);
     if (ctx->psum) cudaFree(ctx->psum);
+    if (ctx->pticket) cudaFree(ctx->pticket);
     ctx->psum = nullptr;
+    ctx->pticket = nullptr;
     ctx->psibox = nullptr;
     ctx->fpart = nullptr;
     ctx->surf = nullptr;
@@ -261,7 +265,9 @@ ek_status run_setup(ek_ctx* ctx) {
     const size_t cap = (size_t)ctx->Pcap * boxmax;
     EK_CUDA(cudaMalloc(&ctx->psibox, cap * sizeof(double)));
     EK_CUDA(cudaMalloc(&ctx->fpart, (size_t)ctx->Pcap * fchunks * FPART * sizeof(double)));
-    EK_CUDA(cudaMalloc(&ctx->psum, (size_t)(ctx->Pcap + 64) * FPART * sizeof(double)));
+    EK_CUDA(cudaMalloc(&ctx->psum, (size_t)ctx->Pcap * FPART * sizeof(double)));
+    EK_CUDA(cudaMalloc(&ctx->pticket, (size_t)ctx->Pcap * sizeof(int)));
+    EK_CUDA(cudaMemsetAsync(ctx->pticket, 0, (size_t)ctx->Pcap * sizeof(int), ctx->stream));
     EK_CUDA(cudaMalloc(&ctx->surf, cap * sizeof(int2)));
     ctx->psibox_cap = cap;
     ctx->fchunks = fchunks;
@@ -360,7 +366,7 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
     case 4: {
       PartArgs a = part_args(ctx);
       EK_CUDA(launch_particle_forces(a, s));
-      ctx->launches += ctx->P > 0 ? 4 : 0;
+      ctx->launches += ctx->P > 0 ? 3 : 0;
       return EK_OK;
     }
     case 5: {
@@ -400,7 +406,7 @@ ek_status enqueue_step(ek_ctx* ctx) {
   if (ctx->P) {
     EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_part, 0));
     EK_CUDA(launch_reflag(pa, true, s, 2));
-    ctx->launches += 13;
+    ctx->launches += 12;
   }
   return EK_OK;
 }
@@ -589,7 +595,7 @@ ek_status ek_destroy(ek_ctx* ctx) {
                   ctx->qwall, ctx->u, ctx->tmp, ctx->owner, ctx->owner_prev, ctx->wall,
                   ctx->spectrum, ctx->dparts, ctx->psibox, ctx->fpart, ctx->surf, ctx->xfer,
                   ctx->xfer_count, ctx->surf_count, ctx->status, ctx->ifield, ctx->ipart,
-                  ctx->fkey, ctx->psum, ctx->vsig, ctx->ticket};
+                  ctx->fkey, ctx->psum, ctx->vsig, ctx->ticket, ctx->pticket};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);

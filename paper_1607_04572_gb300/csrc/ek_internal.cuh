@@ -76,6 +76,7 @@ struct DevParticle {
   int lo[3], hi[3];  // box [lo, hi) in unwrapped coordinates, current position
   int ulo[3], uhi[3];  // union of the previous and current boxes (transitions)
   int elo[3], ehi[3];  // box widened by ceil(R) + FORCE_MARGIN (solute force region)
+  int kelo[3], kehi[3];  // the widened box whose assignment keys S4 set (cleared after)
 };
 
 // cells added to ceil(R) around a particle's box for the region whose solute
@@ -279,11 +280,12 @@ struct PartArgs {
   const double* ipart;       // 3 per lattice block
   int nipart;                // number of lattice blocks
   unsigned long long* fkey;  // N: (surface distance, particle) of the nearest particle
-  double* psum;              // (P + 64) * FPART: per-particle sums, then 64 lattice slices
+  double* psum;              // P * FPART: per-particle sums of S4
   int2* surf;      // (particle, box cell) of the cells cut by a sphere surface
   int* surf_count;
   int surf_cap;
-  int* ticket;     // blocks of the S4 sum kernel done (reset by the last one)
+  int* ticket;     // particles whose S4 sums are done (reset by the last)
+  int* pticket;    // P: S4 force blocks of the particle done (reset by the last)
   int* status;
 };
 // cells per CTA of the S4 force kernel (FORCE_T threads, FORCE_CHUNK / FORCE_T

@@ -191,9 +191,10 @@ __device__ void block_sum(double (&v)[NV]) {
 //                    momentum exchange (Eq. 11), the solute force on the
 //                    particle (reaction of the internal solute force on the
 //                    fluid of its nodes) and the field on its own charge
-//   k_psum_integrate  per-particle and lattice sums; the last block takes the
-//                    remainder of the solute force on nodes no particle
-//                    claims, split evenly, and integrates (symplectic Euler)
+//                    The last block of a particle sums its rows; the last
+//                    particle takes the remainder of the solute force on
+//                    nodes no particle claims, split evenly, and integrates
+//                    (symplectic Euler)
 //   k_key_reset      clears the keys of the widened boxes
 // All sums run in a fixed order, so the result is deterministic.
 // ---------------------------------------------------------------------------
@@ -233,9 +234,14 @@ __global__ void k_force_assign(PartArgs a) {
   long long n;
   double dx, dy, dz;
   ext_cell(P, c, a.g, X, Y, Z, n, dx, dy, dz);  // a repeated node gets the same key
-  const double dsurf = __dsub_rn(__dsqrt_rn(dist2(dx, dy, dz)), P.radius);
-  const long long kq = (long long)floor(__dmul_rn(__dadd_rn(dsurf, 1024.0), 1048576.0));
-  const unsigned long long key = ((unsigned long long)kq << 20) | (unsigned long long)p;
+  // surface distance in IEEE single precision (the decision's precision),
+  // ordered by its bit pattern; ties go to the lower particle index
+  const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+  const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)), __fmul_rn(fz, fz));
+  const float dsurf = __fsub_rn(__fsqrt_rn(d2), (float)P.radius);
+  unsigned bits = __float_as_uint(dsurf);
+  bits = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+  const unsigned long long key = ((unsigned long long)bits << 20) | (unsigned long long)p;
   atomicMin(a.fkey + n, key);
 }
 
@@ -243,12 +249,10 @@ __global__ void k_key_reset(PartArgs a) {
   const int p = blockIdx.x;
   const DevParticle& P = a.parts[p];
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= box_cells(P.elo, P.ehi)) return;
+  if (c >= box_cells(P.kelo, P.kehi)) return;
   int X, Y, Z;
-  long long n;
-  double dx, dy, dz;
-  ext_cell(P, c, a.g, X, Y, Z, n, dx, dy, dz);
-  a.fkey[n] = ~0ULL;
+  box_coord(c, P.kelo, P.kehi, X, Y, Z);
+  a.fkey[node_of(X, Y, Z, a.g)] = ~0ULL;
 }
 
 // Sum of FORCE_T values per component, fixed order: the block's values are
@@ -257,6 +261,10 @@ __global__ void k_key_reset(PartArgs a) {
 // no thread touched are skipped (they stay 0).  Result in out[j] for
 // threadIdx.x == j < NV.  Few FP64 instructions: a warp-shuffle tree would
 // spend 5 * NV double adds per thread.
+template <int NC>
+__device__ void column_sums(const double* tab, int nrow, int stride, int col0, double* out);
+__device__ void integrate_all(const PartArgs& a);
+
 template <int NV>
 __device__ void block_sum_t(const double (&v)[NV], const bool (&group_on)[NV / 6], double* out) {
   __shared__ double tr[NV][FORCE_T + 1];
@@ -391,6 +399,27 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   on[2] = __syncthreads_or(touched[2]);
   double* out = a.fpart + ((long long)p * a.fchunks + blockIdx.y) * FPART;
   block_sum_t<FPART>(acc, on, out);
+  // the particle's last block sums its rows; the last particle integrates
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(a.pticket + p, 1) == nb - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  column_sums<FPART>(a.fpart + (long long)p * a.fchunks * FPART, nb, FPART, 0,
+                     a.psum + (long long)p * FPART);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.pticket[p] = 0;
+    last = atomicAdd(a.ticket, 1) == a.P - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  integrate_all(a);
+  if (threadIdx.x == 0) *a.ticket = 0;
 }
 
 // New box of a particle at `pos`: the cells within R (+1 below, +2 above),
@@ -415,23 +444,28 @@ __device__ void box_update_one(DevParticle& P, const double pos[3], const int nn
   }
 }
 
-constexpr int PSUM_T = 256;
-constexpr int PSUM_LAT = 64;  // blocks that sum the lattice-block partials
-
 // Column sums of a row-major table (nrow rows of `stride` doubles; columns
-// col0 .. col0 + NC - 1), fixed order: thread t < G * NC takes column t % NC
-// of rows t / NC, t / NC + G, ... (consecutive threads read consecutive
-// addresses), then thread j < NC adds the G partials in order.  Result in
-// out[j] for threadIdx.x == j.
+// col0 .. col0 + NC - 1) by a block of FORCE_T threads, fixed order: thread
+// t < G * NC takes column t % NC of rows t / NC, t / NC + G, ... (eight loads
+// in flight at a time), then thread j < NC adds the G partials in order.
+// Result in out[j] (shared or global) for threadIdx.x == j.
 template <int NC>
 __device__ void column_sums(const double* tab, int nrow, int stride, int col0, double* out) {
-  constexpr int G = PSUM_T / NC;
+  constexpr int G = FORCE_T / NC;
   __shared__ double part[G * NC];
   const int t = threadIdx.x;
   if (t < G * NC) {
-    const int j = t % NC, r0 = t / NC;
+    const int j = t % NC;
     double s = 0.0;
-    for (int r = r0; r < nrow; r += G) s += __ldcg(tab + (long long)r * stride + col0 + j);
+    int r = t / NC;
+    for (; r + 7 * G < nrow; r += 8 * G) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(tab + (long long)(r + u * G) * stride + col0 + j);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; r < nrow; r += G) s += __ldcg(tab + (long long)r * stride + col0 + j);
     part[t] = s;
   }
   __syncthreads();
@@ -443,39 +477,14 @@ __device__ void column_sums(const double* tab, int nrow, int stride, int col0, d
   __syncthreads();
 }
 
-// Blocks p < P: the chunk partials of particle p summed into psum[p]; blocks
-// P + l, l < PSUM_LAT: slice l of the lattice-block sums of the internal
-// solute force into psum[P + l].  The last block to finish (ticket) then
-// takes the remainder of the solute force on nodes no particle claims
-// (lattice total minus the claimed sums), splits it evenly, and moves every
-// particle by symplectic Euler (Sec. III.B).  Every sum runs in a fixed order,
-// whichever block comes last.
-__global__ void __launch_bounds__(PSUM_T) k_psum_integrate(PartArgs a) {
-  __shared__ double res[FPART];
-  __shared__ bool last;
-  const int b = blockIdx.x;
-  if (b >= a.P) {
-    const int l = b - a.P;
-    const int per = (a.nipart + PSUM_LAT - 1) / PSUM_LAT;
-    const int first = l * per;
-    const int nrow = max(0, min(per, a.nipart - first));
-    column_sums<3>(a.ipart + 3LL * first, nrow, 3, 0, res);
-    if (threadIdx.x < 3) a.psum[(long long)b * FPART + threadIdx.x] = res[threadIdx.x];
-  } else {
-    const int nrow = (box_cells(a.parts[b].elo, a.parts[b].ehi) + FORCE_CHUNK - 1) / FORCE_CHUNK;
-    column_sums<FPART>(a.fpart + (long long)b * a.fchunks * FPART, nrow, FPART, 0, res);
-    if (threadIdx.x < FPART) a.psum[(long long)b * FPART + threadIdx.x] = res[threadIdx.x];
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(a.ticket, 1) == (int)gridDim.x - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  // claimed solute force (psum columns 6..8 of the particles) and lattice total
+// Run by the block that finishes S4 last: the remainder of the solute force
+// on nodes no particle claims (lattice total of the internal force minus the
+// claimed sums) is split evenly; every particle then moves by symplectic
+// Euler (Sec. III.B), and its boxes follow the new position (start of S5).
+__device__ void integrate_all(const PartArgs& a) {
   __shared__ double claimed[3], total[3];
+  column_sums<3>(a.ipart, a.nipart, 3, 0, total);
   column_sums<3>(a.psum, a.P, FPART, 6, claimed);
-  column_sums<3>(a.psum + (long long)a.P * FPART, PSUM_LAT, FPART, 0, total);
   double rem[3];
   for (int d = 0; d < 3; ++d) rem[d] = (total[d] + claimed[d]) / (double)a.P;  // claimed holds -sum i
   const double E[3] = {a.ph.E[0], a.ph.E[1], a.ph.E[2]};
@@ -521,15 +530,15 @@ __global__ void __launch_bounds__(PSUM_T) k_psum_integrate(PartArgs a) {
       Pp->omega[d] = omega[d];
     }
     // S5 starts here: the boxes follow the new position
+    for (int d = 0; d < 3; ++d) {
+      Pp->kelo[d] = Pp->elo[d];
+      Pp->kehi[d] = Pp->ehi[d];
+    }
     if (isfinite(pos[0] + pos[1] + pos[2])) box_update_one(*Pp, pos, nn, false);
   }
-  if (threadIdx.x == 0) *a.ticket = 0;
 }
 
-// ---------------------------------------------------------------------------
-// S5 and set-up
-// ---------------------------------------------------------------------------
-// set-up only (in a step the box follows the position in k_psum_integrate)
+// set-up only (in a step the box follows the position in integrate_all)
 __global__ void k_box_update(PartArgs a) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.P) return;
@@ -914,9 +923,9 @@ cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s) {
   const unsigned echunks = (unsigned)((a.emax + PT - 1) / PT);
   k_force_assign<<<dim3(a.P, echunks), PT, 0, s>>>(a);
   k_particle_forces<FM><<<dim3(a.P, a.fchunks), FORCE_T, 0, s>>>(a);
-  // before the integration moves the widened boxes
+  // the widened boxes have moved with the integration: clear the keys of the
+  // old ones, which k_force_assign kept in elo_prev / ehi_prev
   k_key_reset<<<dim3(a.P, echunks), PT, 0, s>>>(a);
-  k_psum_integrate<<<a.P + PSUM_LAT, PSUM_T, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,8 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
+#include <algorithm>
 
 #include "ek_internal.cuh"
 
@@ -278,6 +280,285 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_inv(PassArgs<R> a, int pa
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fast path of the FP32 form for power-of-two edges 32 .. 512: the same five
+// passes, with each line transform specialised at compile time.  A stage of
+// radix R (16, 8 or 4) loads R elements into registers, applies the stage
+// twiddles from a shared-memory table, does the length-R DFT in registers
+// (even/odd splits down to radix 4, constant twiddles) and stores in
+// Stockham order; a length-128 line takes two stages (16 x 8).  Shared-memory
+// rows are padded by one element every 16, which keeps the strided stores of
+// the first stage free of bank conflicts.
+// ---------------------------------------------------------------------------
+constexpr int FAST_T = 128;           // threads per CTA
+constexpr int FAST_ELEMS = 2048;      // complex elements per CTA and buffer (before padding)
+__host__ __device__ constexpr int fpad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int fast_radix(int n, int s) {
+  // radices of the stages: 32 = 8 4, 64 = 8 8, 128 = 16 8, 256 = 16 16, 512 = 8 8 8
+  return n == 32 ? (s == 0 ? 8 : s == 1 ? 4 : 0)
+       : n == 64 ? (s < 2 ? 8 : 0)
+       : n == 128 ? (s == 0 ? 16 : s == 1 ? 8 : 0)
+       : n == 256 ? (s < 2 ? 16 : 0)
+       : n == 512 ? (s < 3 ? 8 : 0)
+       : 0;
+}
+inline bool fast_edge(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+
+// multiply by exp(-+2 pi i k / R) (forward: minus), k < R / 2, R = 8 or 16
+template <int R, bool INV>
+__device__ __forceinline__ float2 wconst(int k, float2 z) {
+  // cos and sin of 2 pi m / 16, m = 0..7
+  constexpr float C16[8] = {1.0f, 0.92387953251128675613f, 0.70710678118654752440f,
+                            0.38268343236508977173f, 0.0f, -0.38268343236508977173f,
+                            -0.70710678118654752440f, -0.92387953251128675613f};
+  constexpr float S16[8] = {0.0f, 0.38268343236508977173f, 0.70710678118654752440f,
+                            0.92387953251128675613f, 1.0f, 0.92387953251128675613f,
+                            0.70710678118654752440f, 0.38268343236508977173f};
+  const int m = k * (16 / R);
+  if (m == 0) return z;
+  if (m == 4) return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+  const float c = C16[m], sn = INV ? S16[m] : -S16[m];
+  return make_float2(z.x * c - z.y * sn, z.x * sn + z.y * c);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+  if constexpr (R == 2) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const float2 s13 = cadd(v[1], v[3]), d13 = rot(csub(v[1], v[3]), INV);
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+  } else {
+    float2 e[R / 2], o[R / 2];
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) {
+      e[r] = v[2 * r];
+      o[r] = v[2 * r + 1];
+    }
+    dft_reg<R / 2, INV>(e);
+    dft_reg<R / 2, INV>(o);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      const float2 t = wconst<R, INV>(k, o[k]);
+      v[k] = cadd(e[k], t);
+      v[k + R / 2] = csub(e[k], t);
+    }
+  }
+}
+
+// one Stockham stage of radix R after stages of total radix NS, on nl lines
+// of length N (padded rows of LS elements)
+template <int N, int NS, int R, bool INV>
+__device__ __forceinline__ void fast_stage(const float2* in, float2* out, int nl, const float2* tw) {
+  constexpr int M = N / R;
+  constexpr int LS = fpad(N);
+  for (int t = threadIdx.x; t < nl * M; t += FAST_T) {
+    const int line = t / M, j = t % M;
+    const float2* src = in + line * LS;
+    float2* dst = out + line * LS;
+    const int k = j % NS;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[fpad(j + r * M)];
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = tw[r * k * (N / (NS * R))];
+        v[r] = INV ? cmulconj(v[r], w) : cmul(v[r], w);
+      }
+    }
+    dft_reg<R, INV>(v);
+    const int base = (j / NS) * NS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[fpad(base + r * NS)] = v[r];
+  }
+  __syncthreads();
+}
+
+// transform nl lines held in a (b is scratch); returns the buffer with the result
+template <int N, bool INV>
+__device__ float2* fast_fft(float2* a, float2* b, int nl, const float2* tw) {
+  constexpr int R0 = fast_radix(N, 0), R1 = fast_radix(N, 1), R2 = fast_radix(N, 2);
+  fast_stage<N, 1, R0, INV>(a, b, nl, tw);
+  if constexpr (R1 == 0) {
+    return b;
+  } else {
+    fast_stage<N, R0, R1, INV>(b, a, nl, tw);
+    if constexpr (R2 == 0) {
+      return a;
+    } else {
+      fast_stage<N, R0 * R1, R2, INV>(a, b, nl, tw);
+      return b;
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void load_twiddles(float2* tw, const AxisPlan& P) {
+  for (int k = threadIdx.x; k < N; k += FAST_T) tw[k] = P.tw32[k];
+}
+
+// X pass, forward, rows r0 = 2p, r1 = 2p + 1 packed as a + i b (as k_fft_x_fwd)
+template <int NX>
+__global__ void __launch_bounds__(FAST_T) k_fast_x_fwd(PassArgs<float> a) {
+  constexpr int PPC = FAST_ELEMS / NX;  // row pairs per CTA
+  constexpr int LS = fpad(NX);
+  __shared__ __align__(16) float2 buf[2][PPC * LS];
+  __shared__ float2 tw[NX];
+  load_twiddles<NX>(tw, a.ax);
+  const int nrows = a.ny * a.nz;
+  const long long N = (long long)NX * a.ny * a.nz;
+  const int p0 = blockIdx.x * PPC;
+  for (int t = threadIdx.x; t < PPC * NX; t += FAST_T) {
+    const int l = t / NX, x = t % NX;
+    const int r0 = 2 * (p0 + l), r1 = r0 + 1;
+    float re = 0.0f, im = 0.0f;
+    if (r0 < nrows) re = charge_at(a, (long long)r0 * NX + x, N);
+    if (r1 < nrows) im = charge_at(a, (long long)r1 * NX + x, N);
+    buf[0][l * LS + fpad(x)] = make_float2(re, im);
+  }
+  __syncthreads();
+  const float2* res = fast_fft<NX, false>(buf[0], buf[1], PPC, tw);
+  constexpr int NXH = NX / 2 + 1;
+  for (int t = threadIdx.x; t < PPC * NXH; t += FAST_T) {
+    const int l = t / NXH, k = t % NXH;
+    const int r0 = 2 * (p0 + l), r1 = r0 + 1;
+    if (r0 >= nrows) continue;
+    const float2 Zk = res[l * LS + fpad(k)];
+    const float2 Zm = res[l * LS + fpad(k == 0 ? 0 : NX - k)];
+    const float2 A = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+    const float2 B = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+    a.S[(long long)r0 * NXH + k] = A;
+    if (r1 < nrows) a.S[(long long)r1 * NXH + k] = B;
+  }
+}
+
+// Y (AXIS 1, forward or inverse) or Z (AXIS 2: forward, Green multiply,
+// inverse) pass on tiles of tx consecutive kx (as k_fft_yz)
+template <int NL, int AXIS, bool INV>
+__global__ void __launch_bounds__(FAST_T) k_fast_yz(PassArgs<float> a, int tx) {
+  constexpr int LS = fpad(NL);
+  __shared__ __align__(16) float2 buf[2][(FAST_ELEMS / NL) * LS];
+  __shared__ float2 tw[NL];
+  const AxisPlan& P = AXIS == 1 ? a.ay : a.az;
+  load_twiddles<NL>(tw, P);
+  const int nxh = a.nxh;
+  const int ntile = (nxh + tx - 1) / tx;
+  const int tile = blockIdx.x % ntile;
+  const int other = blockIdx.x / ntile;  // z (axis 1) or ky (axis 2)
+  const int kx0 = tile * tx;
+  const int nc = min(tx, nxh - kx0);
+  const long long stride = AXIS == 1 ? (long long)nxh : (long long)nxh * a.ny;
+  const long long base = AXIS == 1 ? (long long)other * a.ny * nxh : (long long)other * nxh;
+  for (int t = threadIdx.x; t < nc * NL; t += FAST_T) {
+    const int j = t / nc, c = t - j * nc;
+    buf[0][c * LS + fpad(j)] = a.S[base + j * stride + kx0 + c];
+  }
+  __syncthreads();
+  float2* res;
+  if constexpr (AXIS == 1) {
+    res = fast_fft<NL, INV>(buf[0], buf[1], nc, tw);
+  } else {
+    res = fast_fft<NL, false>(buf[0], buf[1], nc, tw);
+    const float ly = lambda_of(a.ay, other, 0.0f);
+    for (int t = threadIdx.x; t < nc * NL; t += FAST_T) {
+      const int c = t / NL, j = t % NL;
+      const int kx = kx0 + c;
+      const float lam = lambda_of(a.ax, kx, 0.0f) + ly + lambda_of(a.az, j, 0.0f);
+      const float g = (kx == 0 && other == 0 && j == 0) ? 0.0f : a.green_scale / lam;
+      float2& v = res[c * LS + fpad(j)];
+      v = make_float2(v.x * g, v.y * g);
+    }
+    __syncthreads();
+    res = fast_fft<NL, true>(res, res == buf[0] ? buf[1] : buf[0], nc, tw);
+  }
+  for (int t = threadIdx.x; t < nc * NL; t += FAST_T) {
+    const int j = t / nc, c = t - j * nc;
+    a.S[base + j * stride + kx0 + c] = res[c * LS + fpad(j)];
+  }
+}
+
+// X pass, inverse (complex-to-real), two rows per complex transform (as k_fft_x_inv)
+template <int NX>
+__global__ void __launch_bounds__(FAST_T) k_fast_x_inv(PassArgs<float> a) {
+  constexpr int PPC = FAST_ELEMS / NX;
+  constexpr int LS = fpad(NX);
+  constexpr int NXH = NX / 2 + 1;
+  __shared__ __align__(16) float2 buf[2][PPC * LS];
+  __shared__ float2 tw[NX];
+  load_twiddles<NX>(tw, a.ax);
+  const int nrows = a.ny * a.nz;
+  const int p0 = blockIdx.x * PPC;
+  for (int t = threadIdx.x; t < PPC * NX; t += FAST_T) {
+    const int l = t / NX, k = t % NX;
+    const int r0 = 2 * (p0 + l), r1 = r0 + 1;
+    float2 A = make_float2(0.0f, 0.0f), B = make_float2(0.0f, 0.0f);
+    const bool upper = k > NX / 2;
+    const int kk = upper ? NX - k : k;
+    if (r0 < nrows) A = a.S[(long long)r0 * NXH + kk];
+    if (r1 < nrows) B = a.S[(long long)r1 * NXH + kk];
+    if (upper) {
+      A.y = -A.y;
+      B.y = -B.y;
+    }
+    buf[0][l * LS + fpad(k)] = make_float2(A.x - B.y, A.y + B.x);
+  }
+  __syncthreads();
+  const float2* res = fast_fft<NX, true>(buf[0], buf[1], PPC, tw);
+  for (int t = threadIdx.x; t < PPC * NX; t += FAST_T) {
+    const int l = t / NX, x = t % NX;
+    const int r0 = 2 * (p0 + l), r1 = r0 + 1;
+    const float2 v = res[l * LS + fpad(x)];
+    if (r0 < nrows) a.phi[(long long)r0 * NX + x] = v.x;
+    if (r1 < nrows) a.phi[(long long)r1 * NX + x] = v.y;
+  }
+}
+
+template <int NX>
+void launch_fast_x(PassArgs<float>& a, bool inverse, cudaStream_t s) {
+  const int npairs = (a.ny * a.nz + 1) / 2;
+  const unsigned g = (unsigned)((npairs + FAST_ELEMS / NX - 1) / (FAST_ELEMS / NX));
+  if (inverse) k_fast_x_inv<NX><<<g, FAST_T, 0, s>>>(a);
+  else k_fast_x_fwd<NX><<<g, FAST_T, 0, s>>>(a);
+}
+
+template <int NL, int AXIS, bool INV>
+void launch_fast_yz_n(PassArgs<float>& a, cudaStream_t s) {
+  // tiles of at most FAST_ELEMS / NL (<= 16) columns, balanced over nxh
+  const int txmax = std::min(16, FAST_ELEMS / NL);
+  const int ntile = (a.nxh + txmax - 1) / txmax;
+  const int tx = (a.nxh + ntile - 1) / ntile;
+  const int nother = AXIS == 1 ? a.nz : a.ny;
+  k_fast_yz<NL, AXIS, INV><<<(unsigned)(ntile * nother), FAST_T, 0, s>>>(a, tx);
+}
+
+template <int AXIS, bool INV>
+void launch_fast_yz(PassArgs<float>& a, int n, cudaStream_t s) {
+  switch (n) {
+    case 32: launch_fast_yz_n<32, AXIS, INV>(a, s); break;
+    case 64: launch_fast_yz_n<64, AXIS, INV>(a, s); break;
+    case 128: launch_fast_yz_n<128, AXIS, INV>(a, s); break;
+    case 256: launch_fast_yz_n<256, AXIS, INV>(a, s); break;
+    default: launch_fast_yz_n<512, AXIS, INV>(a, s); break;
+  }
+}
+
+void launch_fast_x_any(PassArgs<float>& a, bool inverse, cudaStream_t s) {
+  switch (a.nx) {
+    case 32: launch_fast_x<32>(a, inverse, s); break;
+    case 64: launch_fast_x<64>(a, inverse, s); break;
+    case 128: launch_fast_x<128>(a, inverse, s); break;
+    case 256: launch_fast_x<256>(a, inverse, s); break;
+    default: launch_fast_x<512>(a, inverse, s); break;
+  }
+}
+
 template <class FM>
 __global__ void k_charge(Grid g, Phys ph, const void* rho, const void* qwall, const void* qpart,
                          double* q) {
@@ -386,6 +667,16 @@ cudaError_t run_passes(const PoissonPlan& p, PassArgs<R>& a, double bjerrum, cud
   a.az = p.az;
   const double N = (double)p.nx * p.ny * p.nz;
   a.green_scale = (R)(4.0 * M_PI * bjerrum / N);
+  if constexpr (std::is_same<R, float>::value) {
+    if (fast_edge(p.nx) && fast_edge(p.ny) && fast_edge(p.nz)) {
+      launch_fast_x_any(a, false, s);
+      launch_fast_yz<1, false>(a, p.ny, s);
+      launch_fast_yz<2, false>(a, p.nz, s);
+      launch_fast_yz<1, true>(a, p.ny, s);
+      launch_fast_x_any(a, true, s);
+      return cudaGetLastError();
+    }
+  }
   const int nrows = p.ny * p.nz;
   const int npairs = (nrows + 1) / 2;
   const int ppc = LINE_ELEMS / p.nx > 0 ? LINE_ELEMS / p.nx : 1;
