@@ -79,15 +79,18 @@ __device__ __forceinline__ int nbr32(int d, int x, int y, int z, const Nbr& b, i
   return X + nx * (Y + ny * Z);
 }
 
-__device__ __forceinline__ void block_sum3(double (&v)[3], double* ipart) {
+// block total of the per-thread sums: warps in float (32 threads of at most
+// TZ nodes each), the warp sums in FP64; the GPU's FP64 rate is a small
+// fraction of its FP32 rate, so the per-node accumulation stays in float
+__device__ __forceinline__ void block_sum3(float (&v)[3], double* ipart) {
   __shared__ double red[TILE_X * TILE_Y / 32][3];
   const int t = threadIdx.x + TILE_X * threadIdx.y;
   const int lane = t & 31, warp = t >> 5;
 #pragma unroll
   for (int cc = 0; cc < 3; ++cc) {
-    double s = v[cc];
+    float s = v[cc];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) red[warp][cc] = s;
+    if (lane == 0) red[warp][cc] = (double)s;
   }
   __syncthreads();
   if (t == 0) {
@@ -143,7 +146,7 @@ __device__ __forceinline__ void load_plane(LBTile<K>& t, int slot, int zz, int x
 }
 
 template <int K, bool PV>
-__global__ void __launch_bounds__(256, 3) k_lb32_tiled(LBArgs a, Phys32 c) {
+__global__ void __launch_bounds__(256, 4) k_lb32_tiled(LBArgs a, Phys32 c) {
   __shared__ LBTile<K> t;
   const float* __restrict__ g_in = (const float*)a.f_in;
   float* __restrict__ g_out = (float*)a.f_out;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(256, 3) k_lb32_tiled(LBArgs a, Phys32 c) {
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   const bool in_xy = x < nx && y < ny;
   const int ex = threadIdx.x + 1, ey = threadIdx.y + 1;
-  double iv[3] = {0.0, 0.0, 0.0};
+  float iv[3] = {0.0f, 0.0f, 0.0f};
   load_plane<K, PV>(t, (z0 + 2) % 3, z0 - 1, x0, y0, a, c);  // slot of plane z0 - 1
   load_plane<K, PV>(t, z0 % 3, z0, x0, y0, a, c);
   for (int z = z0; z < z0 + TZ; ++z) {

@@ -142,9 +142,13 @@ __device__ __forceinline__ R charge_at(const PassArgs<R>& a, long long i, long l
   if (a.rho == nullptr) return a.q[i];
   R q = R(0);
   if (a.int_species) {
-    for (int k = 0; k < a.K; ++k) q += a.z[k] * (R)((const int*)a.rho)[k * N + i];
+#pragma unroll
+    for (int k = 0; k < EK_MAX_SPECIES; ++k)
+      if (k < a.K) q += a.z[k] * (R)((const int*)a.rho)[k * N + i];
   } else {
-    for (int k = 0; k < a.K; ++k) q += a.z[k] * ((const R*)a.rho)[k * N + i];
+#pragma unroll
+    for (int k = 0; k < EK_MAX_SPECIES; ++k)
+      if (k < a.K) q += a.z[k] * ((const R*)a.rho)[k * N + i];
   }
   if (a.qwall) q += a.qwall[i];
   if (a.qpart) q += a.qpart[i];
@@ -415,6 +419,9 @@ __global__ void __launch_bounds__(FAST_T) k_fast_x_fwd(PassArgs<float> a) {
   const int nrows = a.ny * a.nz;
   const long long N = (long long)NX * a.ny * a.nz;
   const int p0 = blockIdx.x * PPC;
+  // PPC * NX / FAST_T = 16 elements per thread: unrolled, so the loads of
+  // several elements are in flight together
+#pragma unroll 8
   for (int t = threadIdx.x; t < PPC * NX; t += FAST_T) {
     const int l = t / NX, x = t % NX;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
@@ -456,6 +463,7 @@ __global__ void __launch_bounds__(FAST_T) k_fast_yz(PassArgs<float> a, int tx) {
   const int nc = min(tx, nxh - kx0);
   const long long stride = AXIS == 1 ? (long long)nxh : (long long)nxh * a.ny;
   const long long base = AXIS == 1 ? (long long)other * a.ny * nxh : (long long)other * nxh;
+#pragma unroll 8
   for (int t = threadIdx.x; t < nc * NL; t += FAST_T) {
     const int j = t / nc, c = t - j * nc;
     buf[0][c * LS + fpad(j)] = a.S[base + j * stride + kx0 + c];
@@ -495,6 +503,7 @@ __global__ void __launch_bounds__(FAST_T) k_fast_x_inv(PassArgs<float> a) {
   load_twiddles<NX>(tw, a.ax);
   const int nrows = a.ny * a.nz;
   const int p0 = blockIdx.x * PPC;
+#pragma unroll 8
   for (int t = threadIdx.x; t < PPC * NX; t += FAST_T) {
     const int l = t / NX, k = t % NX;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
