@@ -37,6 +37,7 @@ struct ek_ctx {
   void* ifield = nullptr;              // 3N reals: internal solute force on the fluid (S2)
   double* ipart = nullptr;             // 3 doubles per lattice block: its sums
   int nipart = 0;
+  int nzb = 1;       // FP32 S2: z segments per tile column
   unsigned long long* fkey = nullptr;  // N: nearest-particle keys of S4
   unsigned char* vsig = nullptr;       // N: fluid bit and velocity sign codes (S2 -> S3)
   int emax = 0;                        // cells of the widest widened box
@@ -217,6 +218,7 @@ LBArgs lb_args(ek_ctx* ctx) {
   a.vsig = ctx->vsig;
   a.parts = ctx->dparts;
   a.status = ctx->status;
+  a.nzb = ctx->nzb;
   return a;
 }
 
@@ -519,6 +521,10 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   }
   const size_t N = (size_t)g.N;
   const int K = std::max(p->nspecies, 1);
+  if (ctx->fp32 && lb32_prepare() != cudaSuccess) {
+    delete ctx;
+    return EK_ERR_CUDA;
+  }
   bool ok = true;
   auto alloc = [&](void** ptr, size_t bytes) {
     if (ok && cudaMalloc(ptr, bytes) != cudaSuccess) ok = false;
@@ -537,7 +543,8 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   alloc(&ctx->ifield, 3 * N * rsz);
   {
     // lattice-block partial sums of S2: one per block of its grid
-    const dim3 lg = ctx->fp32 ? lattice_grid32(g) : lattice_grid(g);
+    if (ctx->fp32) ctx->nzb = lb32_segments(g, p->nspecies, (p->flags & EK_PV) != 0);
+    const dim3 lg = ctx->fp32 ? lattice_grid32(g, ctx->nzb) : lattice_grid(g);
     ctx->nipart = (int)(lg.x * lg.y * lg.z);
   }
   alloc((void**)&ctx->ipart, (size_t)ctx->nipart * 3 * sizeof(double));

@@ -163,11 +163,11 @@ inline dim3 lattice_grid(const Grid& g) {
               (unsigned)g.nz);
 }
 inline dim3 lattice_block() { return dim3(TILE_X, TILE_Y, 1); }
-// the FP32 form's S2 kernel marches through 8 planes per block
-constexpr int TILE_Z32 = 8;
-inline dim3 lattice_grid32(const Grid& g) {
+// the FP32 form's S2 kernel marches each (x, y) tile column through nzb
+// segments of consecutive planes
+inline dim3 lattice_grid32(const Grid& g, int nzb) {
   return dim3((unsigned)((g.nx + TILE_X - 1) / TILE_X), (unsigned)((g.ny + TILE_Y - 1) / TILE_Y),
-              (unsigned)((g.nz + TILE_Z32 - 1) / TILE_Z32));
+              (unsigned)nzb);
 }
 
 // wrapped neighbour coordinates of (x, y, z)
@@ -231,10 +231,14 @@ struct LBArgs {
   double* ipart;   // per-block sums of ifield (3 per block of the lattice grid)
   const DevParticle* parts;
   int* status;
+  int nzb;         // FP32 S2: z segments per (x, y) tile column (lb32_segments)
 };
 cudaError_t launch_lb_fused(const LBArgs& a, cudaStream_t s);
 cudaError_t launch_advection(const LBArgs& a, cudaStream_t s);
 // FP32-storage form
+cudaError_t lb32_prepare();  // once per process, before the first launch_lb32
+// z segments per tile column of the FP32 S2 grid, chosen from the occupancy
+int lb32_segments(const Grid& g, int K, bool pv);
 cudaError_t launch_lb32(const LBArgs& a, cudaStream_t s);
 cudaError_t launch_advection32(const LBArgs& a, cudaStream_t s);
 cudaError_t launch_fill32(const Grid& g, const Phys& ph, const int* owner, float* f, int* rho,

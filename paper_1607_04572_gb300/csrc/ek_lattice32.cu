@@ -15,19 +15,13 @@
 // which is antisymmetric by construction.
 #include <math.h>
 
+#include <algorithm>
+
 #include "ek_internal.cuh"
 
 namespace ek {
 
 namespace {
-
-__device__ __forceinline__ long long nbr_index(int d, int x, int y, int z, const Nbr& b, int nx,
-                                               int ny) {
-  const int X = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
-  const int Y = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
-  const int Z = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
-  return (long long)X + (long long)nx * ((long long)Y + (long long)ny * Z);
-}
 
 __device__ __forceinline__ float csgnf(int c, float v) { return c > 0 ? v : -v; }
 __device__ __forceinline__ float cdotf(int i, float x, float y, float z) {
@@ -79,8 +73,8 @@ __device__ __forceinline__ int nbr32(int d, int x, int y, int z, const Nbr& b, i
   return X + nx * (Y + ny * Z);
 }
 
-// block total of the per-thread sums: warps in float (32 threads of at most
-// TZ nodes each), the warp sums in FP64; the GPU's FP64 rate is a small
+// block total of the per-thread sums: warps in float (32 threads, each over
+// its segment's nodes), the warp sums in FP64; the GPU's FP64 rate is a small
 // fraction of its FP32 rate, so the per-node accumulation stays in float
 __device__ __forceinline__ void block_sum3(float (&v)[3], double* ipart) {
   __shared__ double red[TILE_X * TILE_Y / 32][3];
@@ -105,50 +99,107 @@ __device__ __forceinline__ void block_sum3(float (&v)[3], double* ipart) {
 }
 
 // ---------------------------------------------------------------------------
-// 2.5D-tiled S2 (FP32 form).  A 32 x 8 thread block owns a (32 x 8) column of
-// TZ planes.  The stencil fields of three consecutive planes -- rho_k as
-// float, 1 - Psi, Phi and the node class -- sit in a shared-memory ring with a
-// one-node halo; each plane is read from global memory (and its species
-// converted to float) once per block instead of once per neighbour.
+// 2.5D-tiled S2 (FP32 form) with asynchronous staging.  A 32 x 8 thread block
+// owns a (32 x 8) column of consecutive planes (the grid's z dimension splits
+// each column into nzb segments of about 8 planes).  The stencil fields of the planes
+// z - 1, z, z + 1 -- species (raw int units), Psi, Phi and the node class --
+// sit in a 4-slot shared-memory ring with a one-node halo, and the
+// populations of plane z in one of two shared buffers.  While plane z is
+// computed, cp.async copies plane z + 2's stencil fields and plane z + 1's
+// populations in, so the global-memory latency of the loads overlaps the
+// arithmetic instead of stalling it; every value is read from global memory
+// once per block.
 // ---------------------------------------------------------------------------
-constexpr int TZ = TILE_Z32;                   // planes per block
 constexpr int HX = TILE_X + 2, HY = TILE_Y + 2;  // tile with halo
 constexpr int HP = HX * HY;                    // nodes of one halo plane
+constexpr int TN = TILE_X * TILE_Y;            // nodes of one tile plane
+constexpr int RING = 4;
 
 template <int K>
-struct LBTile {
-  float rho[K > 0 ? K : 1][3][HP];
-  float om[3][HP];
-  float phi[3][HP];
-  int own[3][HP];
+struct LBRing {
+  int own[RING][HP];
+  float phi[RING][HP];
+  float psi[RING][HP];
+  int rho[K > 0 ? K : 1][RING][HP];
+  float pop[2][Q][TN];
 };
 
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all groups but the newest `n` are complete (for this thread's copies)
+template <int n>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+}
+
+// stencil fields of plane zz (periodic) into ring slot `slot`
 template <int K, bool PV>
-__device__ __forceinline__ void load_plane(LBTile<K>& t, int slot, int zz, int x0, int y0,
-                                           const LBArgs& a, const Phys32& c) {
+__device__ __forceinline__ void stage_plane(LBRing<K>& t, int slot, int zz, int x0, int y0,
+                                            const LBArgs& a) {
   const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
   const size_t N = (size_t)a.g.N;
   const int z = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
   const int tid = threadIdx.x + TILE_X * threadIdx.y;
-  for (int e = tid; e < HP; e += TILE_X * TILE_Y) {
+  for (int e = tid; e < HP; e += TN) {
     const int ey = e / HX, ex = e - ey * HX;
     int x = x0 - 1 + ex, y = y0 - 1 + ey;
     x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
     y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-    const int m = x + nx * (y + ny * z);
-    t.own[slot][e] = a.owner[m];
-    t.phi[slot][e] = ((const float*)a.phi)[m];
-    t.om[slot][e] = PV ? __fsub_rn(1.0f, ((const float*)a.psi)[m]) : 1.0f;
+    const size_t m = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
+    cp_async4(&t.own[slot][e], a.owner + m);
+    cp_async4(&t.phi[slot][e], (const float*)a.phi + m);
+    if (PV) cp_async4(&t.psi[slot][e], (const float*)a.psi + m);
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-      t.rho[k][slot][e] = __fmul_rn((float)(((const int*)a.rho_in) + k * N)[m], c.qs[k]);
+    for (int k = 0; k < K; ++k) cp_async4(&t.rho[k][slot][e], (const int*)a.rho_in + k * N + m);
   }
 }
 
-template <int K, bool PV>
-__global__ void __launch_bounds__(256, 4) k_lb32_tiled(LBArgs a, Phys32 c) {
-  __shared__ LBTile<K> t;
-  const float* __restrict__ g_in = (const float*)a.f_in;
+// populations of plane z (z < nz) into buffer `buf`: 16-byte copies of four
+// consecutive nodes when rows are 16-byte aligned (nx % 4 == 0), else 4 bytes
+template <int K>
+__device__ __forceinline__ void stage_pops(LBRing<K>& t, int buf, int z, int x0, int y0,
+                                           const LBArgs& a) {
+  const int nx = a.g.nx, ny = a.g.ny;
+  const size_t N = (size_t)a.g.N;
+  const float* f = (const float*)a.f_in;
+  const int tid = threadIdx.x + TILE_X * threadIdx.y;
+  const size_t zoff = (size_t)nx * ny * z;
+  if ((nx & 3) == 0) {
+    // chunk c: population i = c / 64, row r = (c / 8) % 8, four nodes at 4 (c % 8)
+    for (int c = tid; c < Q * TILE_Y * (TILE_X / 4); c += TN) {
+      const int i = c >> 6, r = (c >> 3) & 7, q = (c & 7) * 4;
+      const int y = y0 + r, x = x0 + q;
+      if (y < ny && x < nx)
+        cp_async16(&t.pop[buf][i][r * TILE_X + q], f + i * N + zoff + (size_t)y * nx + x);
+    }
+  } else {
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x < nx && y < ny) {
+      const size_t n = zoff + (size_t)y * nx + x;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) cp_async4(&t.pop[buf][i][tid], f + i * N + n);
+    }
+  }
+}
+
+template <int K>
+constexpr size_t lb32_smem() { return sizeof(LBRing<K>); }
+
+// One node of plane z.  SIMPLE: the block's stencil planes hold fluid nodes
+// only and Psi = 0 (no particle or wall near), so every link is a fluid link,
+// the partial-volume factors are 1 and nothing bounces back; the arithmetic is
+// the same as in the general path with those values.
+template <int K, bool PV, bool SIMPLE>
+__device__ __forceinline__ void lb32_node(const LBRing<K>& t, const LBArgs& a, const Phys32& c,
+                                          int x, int y, int z, int tid, int ex, int ey,
+                                          float (&iv)[3]) {
   float* __restrict__ g_out = (float*)a.f_out;
   const int* __restrict__ n_in = (const int*)a.rho_in;
   int* __restrict__ n_out = (int*)a.rho_out;
@@ -156,164 +207,203 @@ __global__ void __launch_bounds__(256, 4) k_lb32_tiled(LBArgs a, Phys32 c) {
   float* __restrict__ ifield = (float*)a.ifield;
   const size_t N = (size_t)a.g.N;
   const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y, z0 = blockIdx.z * TZ;
-  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  const bool in_xy = x < nx && y < ny;
-  const int ex = threadIdx.x + 1, ey = threadIdx.y + 1;
-  float iv[3] = {0.0f, 0.0f, 0.0f};
-  load_plane<K, PV>(t, (z0 + 2) % 3, z0 - 1, x0, y0, a, c);  // slot of plane z0 - 1
-  load_plane<K, PV>(t, z0 % 3, z0, x0, y0, a, c);
-  for (int z = z0; z < z0 + TZ; ++z) {
-    load_plane<K, PV>(t, (z + 1) % 3, z + 1, x0, y0, a, c);
-    __syncthreads();
-    if (in_xy && z < nz) {
-      const int sl[3] = {(z + 2) % 3, z % 3, (z + 1) % 3};  // planes z - 1, z, z + 1
-      const int e0 = ex + HX * ey;
-      const int n = x + nx * (y + ny * z);
-      const Nbr b = make_nbr(x, y, z, a.g);
-      if (t.own[sl[1]][e0] != FLUID) {
-        a.vsig[n] = 0;
+  const int sl[3] = {(z + 3) & 3, z & 3, (z + 1) & 3};  // planes z - 1, z, z + 1
+  const int e0 = ex + HX * ey;
+  const int n = x + nx * (y + ny * z);
+  const Nbr b = make_nbr(x, y, z, a.g);
+  if (!SIMPLE && t.own[sl[1]][e0] != FLUID) {
+    a.vsig[n] = 0;
 #pragma unroll
-        for (int k = 0; k < K; ++k) (n_out + k * N)[n] = (n_in + k * N)[n];
-        u[n] = 0.0f;
-        (u + N)[n] = 0.0f;
-        (u + 2 * N)[n] = 0.0f;
-        ifield[n] = 0.0f;
-        (ifield + N)[n] = 0.0f;
-        (ifield + 2 * N)[n] = 0.0f;
-      } else {
-        unsigned fluid = 0;
+    for (int k = 0; k < K; ++k) (n_out + k * N)[n] = (n_in + k * N)[n];
+    u[n] = 0.0f;
+    (u + N)[n] = 0.0f;
+    (u + 2 * N)[n] = 0.0f;
+    ifield[n] = 0.0f;
+    (ifield + N)[n] = 0.0f;
+    (ifield + 2 * N)[n] = 0.0f;
+  } else {
+    unsigned fluid = SIMPLE ? 0xFFFFFFFEu : 0u;
+    if (!SIMPLE) {
 #pragma unroll
-        for (int d = 1; d < Q; ++d)
-          if (t.own[sl[1 + dcz(d)]][e0 + dcx(d) + HX * dcy(d)] == FLUID) fluid |= 1u << d;
-        // ---- S2a: quantised link fluxes (symmetric operands) and coupling force ----
-        float gx = 0.0f, gy = 0.0f, gz = 0.0f;
-        int S[K > 0 ? K : 1];
-        float r0[K > 0 ? K : 1];
-        const float om0 = t.om[sl[1]][e0];
-        const float phi0 = t.phi[sl[1]][e0];
+      for (int d = 1; d < Q; ++d)
+        if (t.own[sl[1 + dcz(d)]][e0 + dcx(d) + HX * dcy(d)] == FLUID) fluid |= 1u << d;
+    }
+    // ---- S2a: quantised link fluxes (symmetric operands) and coupling force ----
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+    int S[K > 0 ? K : 1];
+    float r0[K > 0 ? K : 1];
+    const float om0 = PV ? __fsub_rn(1.0f, t.psi[sl[1]][e0]) : 1.0f;
+    const float phi0 = t.phi[sl[1]][e0];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          S[k] = 0;
-          r0[k] = t.rho[k][sl[1]][e0];
-        }
+    for (int k = 0; k < K; ++k) {
+      S[k] = 0;
+      r0[k] = __fmul_rn((float)t.rho[k][sl[1]][e0], c.qs[k]);
+    }
 #pragma unroll
-        for (int d = 1; d < Q; ++d) {
-          if (K == 0 || !(fluid & (1u << d))) continue;
-          const int sd = sl[1 + dcz(d)], ed = e0 + dcx(d) + HX * dcy(d);
-          const float omj = t.om[sd][ed];
-          const float dphi = __fadd_rn(__fsub_rn(phi0, t.phi[sd][ed]), c.ec[d]);
-          float tsum = 0.0f;
+    for (int d = 1; d < Q; ++d) {
+      if (K == 0 || !(fluid & (1u << d))) continue;
+      const int sd = sl[1 + dcz(d)], ed = e0 + dcx(d) + HX * dcy(d);
+      const float omj = PV ? __fsub_rn(1.0f, t.psi[sd][ed]) : 1.0f;
+      const float dphi = __fadd_rn(__fsub_rn(phi0, t.phi[sd][ed]), c.ec[d]);
+      float tsum = 0.0f;
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const float rb = t.rho[k][sd][ed];
-            const float A = PV ? __fmul_rn(r0[k], omj) : r0[k];
-            const float B = PV ? __fmul_rn(rb, om0) : rb;
-            float br = fmaf(__fadd_rn(A, B), __fmul_rn(c.hz[k], dphi), __fsub_rn(A, B));
-            if (d >= 7) br = __fmul_rn(br, 0.70710678f);
-            S[k] += __float2int_rn(__fmul_rn(br, c.cq[k]));
-            tsum += br;
+      for (int k = 0; k < K; ++k) {
+        const float rb = __fmul_rn((float)t.rho[k][sd][ed], c.qs[k]);
+        const float A = PV ? __fmul_rn(r0[k], omj) : r0[k];
+        const float B = PV ? __fmul_rn(rb, om0) : rb;
+        float br = fmaf(__fadd_rn(A, B), __fmul_rn(c.hz[k], dphi), __fsub_rn(A, B));
+        if (d >= 7) br = __fmul_rn(br, 0.70710678f);
+        S[k] += __float2int_rn(__fmul_rn(br, c.cq[k]));
+        tsum += br;
+      }
+      if (dcx(d)) gx += csgnf(dcx(d), tsum);
+      if (dcy(d)) gy += csgnf(dcy(d), tsum);
+      if (dcz(d)) gz += csgnf(dcz(d), tsum);
+    }
+    float qion = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int nk = (n_in + k * N)[n];
+      (n_out + k * N)[n] = nk - S[k];
+      qion = fmaf(c.zq[k], (float)nk, qion);
+    }
+    constexpr float HALF_INV_A0 = 0.13060193748187072f;
+    {
+      const float ix = gx * HALF_INV_A0 - qion * c.E[0];
+      const float iy = gy * HALF_INV_A0 - qion * c.E[1];
+      const float iz = gz * HALF_INV_A0 - qion * c.E[2];
+      ifield[n] = ix;
+      (ifield + N)[n] = iy;
+      (ifield + 2 * N)[n] = iz;
+      iv[0] += ix;
+      iv[1] += iy;
+      iv[2] += iz;
+    }
+    // ---- S2b: TRT collision on the deviations (pair form) ----
+    float g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = t.pop[z & 1][i][tid];
+    float drho = g[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const float pd = g[i] - g[i + 1];
+      drho += g[i] + g[i + 1];
+      if (dcx(i)) jx += csgnf(dcx(i), pd);
+      if (dcy(i)) jy += csgnf(dcy(i), pd);
+      if (dcz(i)) jz += csgnf(dcz(i), pd);
+    }
+    const float rho = c.rho0 + drho;
+    const float Fx = fmaf(gx, HALF_INV_A0, c.g[0]);
+    const float Fy = fmaf(gy, HALF_INV_A0, c.g[1]);
+    const float Fz = fmaf(gz, HALF_INV_A0, c.g[2]);
+    const float irho = 1.0f / rho;
+    const float ux = (jx + 0.5f * Fx) * irho;
+    const float uy = (jy + 0.5f * Fy) * irho;
+    const float uz = (jz + 0.5f * Fz) * irho;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float uF = ux * Fx + uy * Fy + uz * Fz;
+    const float le = c.lam_e, lo = c.lam_o;
+    const float gg = 2.0f + le;
+    const float qx = fmaf(-lo, jx, Fx), qy = fmaf(-lo, jy, Fy), qz = fmaf(-lo, jz, Fz);
+    const float base = fmaf(-1.5f * gg, uF, -le * fmaf(-1.5f * rho, usq, drho));
+    const float hle = 0.5f * le, hlo = 0.5f * lo;
+    const float k45 = -4.5f * le * rho;
+    if (!isfinite(rho) || !isfinite(usq)) atomicOr(a.status, ST_NONFINITE);
+    u[n] = ux;
+    (u + N)[n] = uy;
+    (u + 2 * N)[n] = uz;
+    a.vsig[n] = (unsigned char)(0x80u | sign_code(ux) | (sign_code(uy) << 2) | (sign_code(uz) << 4));
+    // ---- collide each pair and push-stream it (velocity bounce-back, Eq. 12) ----
+    g_out[n] = fmaf(1.0f + le, g[0], (float)wgt(0) * base);
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const float w = (float)wgt(i);
+      const float cu = cdotf(i, ux, uy, uz);
+      const float cf = cdotf(i, Fx, Fy, Fz);
+      const float cqv = cdotf(i, qx, qy, qz);
+      const float Ep = w * fmaf(cu, fmaf(4.5f * gg, cf, k45 * cu), base);
+      const float Em = 3.0f * w * cqv;
+      const float X = fmaf(hle, g[i] + g[i + 1], Ep);
+      const float Y = fmaf(hlo, g[i] - g[i + 1], Em);
+      const float gsd[2] = {g[i] + (X + Y), g[i + 1] + (X - Y)};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int d = i + h;
+        if (fluid & (1u << d)) {
+          (g_out + d * N)[nbr32(d, x, y, z, b, nx, ny)] = gsd[h];
+        } else {
+          float cvb = 0.0f;
+          const int om = t.own[sl[1 + dcz(d)]][e0 + dcx(d) + HX * dcy(d)];
+          if (om >= 0) {
+            const DevParticle& P = a.parts[om];
+            const int xb = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
+            const int yb = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
+            const int zb = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
+            const double Xb = (double)(P.lo[0] + wrapi(xb - P.lo[0], nx));
+            const double Yb = (double)(P.lo[1] + wrapi(yb - P.lo[1], ny));
+            const double Zb = (double)(P.lo[2] + wrapi(zb - P.lo[2], nz));
+            const double dx = Xb - P.pos[0], dy = Yb - P.pos[1], dz = Zb - P.pos[2];
+            const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
+            const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
+            const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
+            cvb = (float)cdot(d, vx, vy, vz);
           }
-          if (dcx(d)) gx += csgnf(dcx(d), tsum);
-          if (dcy(d)) gy += csgnf(dcy(d), tsum);
-          if (dcz(d)) gz += csgnf(dcz(d), tsum);
-        }
-        float qion = 0.0f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const int nk = (n_in + k * N)[n];
-          (n_out + k * N)[n] = nk - S[k];
-          qion = fmaf(c.zq[k], (float)nk, qion);
-        }
-        constexpr float HALF_INV_A0 = 0.13060193748187072f;
-        {
-          const float ix = gx * HALF_INV_A0 - qion * c.E[0];
-          const float iy = gy * HALF_INV_A0 - qion * c.E[1];
-          const float iz = gz * HALF_INV_A0 - qion * c.E[2];
-          ifield[n] = ix;
-          (ifield + N)[n] = iy;
-          (ifield + 2 * N)[n] = iz;
-          iv[0] += ix;
-          iv[1] += iy;
-          iv[2] += iz;
-        }
-        // ---- S2b: TRT collision on the deviations (pair form) ----
-        float g[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = (g_in + i * N)[n];
-        float drho = g[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
-#pragma unroll
-        for (int i = 1; i < Q; i += 2) {
-          const float pd = g[i] - g[i + 1];
-          drho += g[i] + g[i + 1];
-          if (dcx(i)) jx += csgnf(dcx(i), pd);
-          if (dcy(i)) jy += csgnf(dcy(i), pd);
-          if (dcz(i)) jz += csgnf(dcz(i), pd);
-        }
-        const float rho = c.rho0 + drho;
-        const float Fx = fmaf(gx, HALF_INV_A0, c.g[0]);
-        const float Fy = fmaf(gy, HALF_INV_A0, c.g[1]);
-        const float Fz = fmaf(gz, HALF_INV_A0, c.g[2]);
-        const float irho = 1.0f / rho;
-        const float ux = (jx + 0.5f * Fx) * irho;
-        const float uy = (jy + 0.5f * Fy) * irho;
-        const float uz = (jz + 0.5f * Fz) * irho;
-        const float usq = ux * ux + uy * uy + uz * uz;
-        const float uF = ux * Fx + uy * Fy + uz * Fz;
-        const float le = c.lam_e, lo = c.lam_o;
-        const float gg = 2.0f + le;
-        const float qx = fmaf(-lo, jx, Fx), qy = fmaf(-lo, jy, Fy), qz = fmaf(-lo, jz, Fz);
-        const float base = fmaf(-1.5f * gg, uF, -le * fmaf(-1.5f * rho, usq, drho));
-        const float hle = 0.5f * le, hlo = 0.5f * lo;
-        const float k45 = -4.5f * le * rho;
-        if (!isfinite(rho) || !isfinite(usq)) atomicOr(a.status, ST_NONFINITE);
-        u[n] = ux;
-        (u + N)[n] = uy;
-        (u + 2 * N)[n] = uz;
-        a.vsig[n] = (unsigned char)(0x80u | sign_code(ux) | (sign_code(uy) << 2) | (sign_code(uz) << 4));
-        // ---- collide each pair and push-stream it (velocity bounce-back, Eq. 12) ----
-        g_out[n] = fmaf(1.0f + le, g[0], (float)wgt(0) * base);
-#pragma unroll
-        for (int i = 1; i < Q; i += 2) {
-          const float w = (float)wgt(i);
-          const float cu = cdotf(i, ux, uy, uz);
-          const float cf = cdotf(i, Fx, Fy, Fz);
-          const float cqv = cdotf(i, qx, qy, qz);
-          const float Ep = w * fmaf(cu, fmaf(4.5f * gg, cf, k45 * cu), base);
-          const float Em = 3.0f * w * cqv;
-          const float X = fmaf(hle, g[i] + g[i + 1], Ep);
-          const float Y = fmaf(hlo, g[i] - g[i + 1], Em);
-          const float gsd[2] = {g[i] + (X + Y), g[i + 1] + (X - Y)};
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int d = i + h;
-            if (fluid & (1u << d)) {
-              (g_out + d * N)[nbr32(d, x, y, z, b, nx, ny)] = gsd[h];
-            } else {
-              float cvb = 0.0f;
-              const int om = t.own[sl[1 + dcz(d)]][e0 + dcx(d) + HX * dcy(d)];
-              if (om >= 0) {
-                const DevParticle& P = a.parts[om];
-                const int xb = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
-                const int yb = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
-                const int zb = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
-                const double Xb = (double)(P.lo[0] + wrapi(xb - P.lo[0], nx));
-                const double Yb = (double)(P.lo[1] + wrapi(yb - P.lo[1], ny));
-                const double Zb = (double)(P.lo[2] + wrapi(zb - P.lo[2], nz));
-                const double dx = Xb - P.pos[0], dy = Yb - P.pos[1], dz = Zb - P.pos[2];
-                const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
-                const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
-                const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
-                cvb = (float)cdot(d, vx, vy, vz);
-              }
-              (g_out + opp(d) * N)[n] = gsd[h] - 6.0f * (float)wgt(d) * c.rho0 * cvb;
-            }
-          }
+          (g_out + opp(d) * N)[n] = gsd[h] - 6.0f * (float)wgt(d) * c.rho0 * cvb;
         }
       }
     }
-    __syncthreads();  // the next load overwrites the slot of plane z - 1
   }
+}
+
+template <int K, bool PV>
+__global__ void __launch_bounds__(256, 2) k_lb32_tiled(LBArgs a, Phys32 c) {
+  extern __shared__ __align__(16) unsigned char lb_smem[];
+  LBRing<K>& t = *reinterpret_cast<LBRing<K>*>(lb_smem);
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y;
+  const int z0 = (int)((long long)blockIdx.z * nz / a.nzb);
+  const int zend = (int)((long long)(blockIdx.z + 1) * nz / a.nzb);
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  const int tid = threadIdx.x + TILE_X * threadIdx.y;
+  const bool in_xy = x < nx && y < ny;
+  const int ex = threadIdx.x + 1, ey = threadIdx.y + 1;
+  float iv[3] = {0.0f, 0.0f, 0.0f};
+  // ring slot of plane zz: zz mod 4 (zz >= -1)
+  stage_plane<K, PV>(t, (z0 + 3) & 3, z0 - 1, x0, y0, a);
+  stage_plane<K, PV>(t, z0 & 3, z0, x0, y0, a);
+  stage_plane<K, PV>(t, (z0 + 1) & 3, z0 + 1, x0, y0, a);
+  stage_pops<K>(t, z0 & 1, z0, x0, y0, a);
+  cp_async_commit();
+  // does a landed halo plane hold a non-fluid node or Psi > 0?  Each thread
+  // looks at the elements it copied itself (complete after its own wait).
+  auto plane_flag = [&](int slot) -> int {
+    bool f = false;
+    for (int e = tid; e < HP; e += TN) f |= t.own[slot][e] != FLUID || (PV && t.psi[slot][e] != 0.0f);
+    return f ? 1 : 0;
+  };
+  int fm1 = 0, f0 = 0;  // flags of planes z - 1 and z
+  for (int z = z0; z < zend; ++z) {
+    // plane z + 2 and the populations of z + 1 (empty group at the end)
+    if (z + 1 < zend) {
+      stage_plane<K, PV>(t, (z + 2) & 3, z + 2, x0, y0, a);
+      stage_pops<K>(t, (z + 1) & 1, z + 1, x0, y0, a);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    if (z == z0) {
+      fm1 = __syncthreads_or(plane_flag((z0 + 3) & 3));
+      f0 = __syncthreads_or(plane_flag(z0 & 3));
+    }
+    const int fp1 = __syncthreads_or(plane_flag((z + 1) & 3));  // also publishes all copies
+    if (in_xy) {
+      if (!(fm1 | f0 | fp1)) lb32_node<K, false, true>(t, a, c, x, y, z, tid, ex, ey, iv);
+      else lb32_node<K, PV, false>(t, a, c, x, y, z, tid, ex, ey, iv);
+    }
+    fm1 = f0;
+    f0 = fp1;
+    __syncthreads();  // the next copies overwrite the slots of plane z - 1 and populations z
+  }
+  cp_async_wait<0>();
   block_sum3(iv, a.ipart);
 }
 
@@ -462,14 +552,46 @@ unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads -
 
 }  // namespace
 
+// shared memory above the 48 KB default, set once per kernel before any launch
+// (in particular before a step is captured into a graph)
+cudaError_t lb32_prepare() {
+  cudaError_t e = cudaSuccess;
+#define EK_ATTR(KK)                                                                          \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_lb32_tiled<KK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)lb32_smem<KK>());                                          \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_lb32_tiled<KK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)lb32_smem<KK>());
+  EK_ATTR(0)
+  EK_ATTR(1)
+  EK_ATTR(2)
+  EK_ATTR(3)
+  EK_ATTR(4)
+#undef EK_ATTR
+  return e;
+}
+
+// Segments per tile column: about 4 planes each, with two blocks of 256
+// threads per SM (up to 128 registers, no spills).  Measured on GB300 at 128^3
+// (ms per launch): 4-plane segments 0.123, 3 planes 0.127, 2 planes 0.136,
+// 1 plane 0.173; with three blocks per SM (80 registers, spills) 8-plane
+// segments 0.185 and 16-plane 0.200.  Short segments let the block scheduler
+// balance the SMs; one-plane segments pay three halo planes per plane.
+int lb32_segments(const Grid& g, int K, bool pv) {
+  (void)K;
+  (void)pv;
+  return std::max(1, (g.nz + 3) / 4);
+}
+
 cudaError_t launch_lb32(const LBArgs& a, cudaStream_t s) {
   const Phys32 c = make_phys32(a.ph);
   const bool pv = a.ph.pv != 0;
   switch (a.ph.K) {
-#define EK_CASE(KK)                                                            \
-  case KK:                                                                     \
-    if (pv) k_lb32_tiled<KK, true><<<lattice_grid32(a.g), lattice_block(), 0, s>>>(a, c);  \
-    else k_lb32_tiled<KK, false><<<lattice_grid32(a.g), lattice_block(), 0, s>>>(a, c);    \
+#define EK_CASE(KK)                                                                        \
+  case KK:                                                                                 \
+    if (pv) k_lb32_tiled<KK, true><<<lattice_grid32(a.g, a.nzb), lattice_block(), lb32_smem<KK>(), s>>>(a, c); \
+    else k_lb32_tiled<KK, false><<<lattice_grid32(a.g, a.nzb), lattice_block(), lb32_smem<KK>(), s>>>(a, c);   \
     break;
     EK_CASE(0)
     EK_CASE(1)
