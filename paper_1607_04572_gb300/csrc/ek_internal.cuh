@@ -299,8 +299,9 @@ constexpr int FORCE_CHUNK = 512;
 // per particle: [0..5] Fh Th (momentum exchange), [6..11] Fs Ts (reaction of
 // the solute force), [12] sum q and [13..15] sum q (r - r_p) of the particle's
 // own charge (the field's force and torque are E and M x E times these),
-// [16..17] unused
-constexpr int FPART = 18;
+// [18..20] a slice of the lattice total of the internal force (first particle
+// only), [16..17] and [21..23] unused
+constexpr int FPART = 24;
 cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s);  // S4
 // S5; parts: 1 = re-flag, Psi and charge (no species access), 2 = transitions
 // (species after S3), 3 = both

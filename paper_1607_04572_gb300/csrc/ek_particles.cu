@@ -317,15 +317,31 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   double acc[FPART];
 #pragma unroll
   for (int j = 0; j < FPART; ++j) acc[j] = 0.0;
-  bool touched[3] = {false, false, false};
+  // FP32 form: the reaction sums run in float per thread (the ifield is float;
+  // the GPU's FP64 rate is a small fraction of its FP32 rate), with offsets
+  // from the centre split into an integer part and the centre's fraction
+  float racc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  const int cxi = (int)floor(P.pos[0]), cyi = (int)floor(P.pos[1]), czi = (int)floor(P.pos[2]);
+  const float frx = (float)(P.pos[0] - cxi), fry = (float)(P.pos[1] - cyi), frz = (float)(P.pos[2] - czi);
+  bool touched[4] = {false, false, false, false};
   for (int k = 0; k < FORCE_CHUNK / FORCE_T; ++k) {
     const int c = ((int)blockIdx.y + k * nb) * FORCE_T + threadIdx.x;
     if (c >= ncell) break;
     int X, Y, Z;
     long long n;
-    double mx, my, mz;
+    double mx = 0.0, my = 0.0, mz = 0.0;
     int w3[3];
-    const bool first = ext_cell(P, c, g, X, Y, Z, n, mx, my, mz, w3);
+    bool first;
+    if (FM::fp32) {
+      box_coord(c, P.elo, P.ehi, X, Y, Z);
+      first = X - P.elo[0] < g.nx && Y - P.elo[1] < g.ny && Z - P.elo[2] < g.nz;
+      w3[0] = wrapi(X, g.nx);
+      w3[1] = wrapi(Y, g.ny);
+      w3[2] = wrapi(Z, g.nz);
+      n = (long long)w3[0] + (long long)g.nx * ((long long)w3[1] + (long long)g.ny * w3[2]);
+    } else {
+      first = ext_cell(P, c, g, X, Y, Z, n, mx, my, mz, w3);
+    }
     const int own = a.owner[n];
     const bool in_box = X >= P.lo[0] && X < P.hi[0] && Y >= P.lo[1] && Y < P.hi[1] &&
                         Z >= P.lo[2] && Z < P.hi[2];
@@ -364,15 +380,33 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
     // reaction of the internal solute force on the fluid nodes this particle claims
     if (first && own == FLUID && (int)(a.fkey[n] & 0xFFFFFull) == p) {
       touched[1] = true;
-      const double ix = real_at<FM>(a.ifield, n);
-      const double iy = real_at<FM>(a.ifield, N + n);
-      const double iz = real_at<FM>(a.ifield, 2 * N + n);
-      acc[6] -= ix;
-      acc[7] -= iy;
-      acc[8] -= iz;
-      acc[9] -= my * iz - mz * iy;
-      acc[10] -= mz * ix - mx * iz;
-      acc[11] -= mx * iy - my * ix;
+      if (FM::fp32) {
+        const float ix = ((const float*)a.ifield)[n];
+        const float iy = ((const float*)a.ifield)[N + n];
+        const float iz = ((const float*)a.ifield)[2 * N + n];
+        // minimum-image offset of the wrapped node from the centre
+        const float hx = 0.5f * (float)g.nx, hy = 0.5f * (float)g.ny, hz = 0.5f * (float)g.nz;
+        float ox = (float)(w3[0] - cxi) - frx, oy = (float)(w3[1] - cyi) - fry, oz = (float)(w3[2] - czi) - frz;
+        ox = ox > hx ? ox - (float)g.nx : (ox < -hx ? ox + (float)g.nx : ox);
+        oy = oy > hy ? oy - (float)g.ny : (oy < -hy ? oy + (float)g.ny : oy);
+        oz = oz > hz ? oz - (float)g.nz : (oz < -hz ? oz + (float)g.nz : oz);
+        racc[0] -= ix;
+        racc[1] -= iy;
+        racc[2] -= iz;
+        racc[3] -= oy * iz - oz * iy;
+        racc[4] -= oz * ix - ox * iz;
+        racc[5] -= ox * iy - oy * ix;
+      } else {
+        const double ix = real_at<FM>(a.ifield, n);
+        const double iy = real_at<FM>(a.ifield, N + n);
+        const double iz = real_at<FM>(a.ifield, 2 * N + n);
+        acc[6] -= ix;
+        acc[7] -= iy;
+        acc[8] -= iz;
+        acc[9] -= my * iz - mz * iy;
+        acc[10] -= mz * ix - mx * iz;
+        acc[11] -= mx * iy - my * ix;
+      }
     }
     // the particle's own charge in this cell
     if (in_box) {
@@ -393,10 +427,31 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
       }
     }
   }
-  bool on[3];
+  if (FM::fp32) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc[6 + j] = (double)racc[j];
+  }
+  // a slice of the lattice-block sums of the internal force (S2), carried by
+  // the first particle's blocks, so that the lattice total is ready when the
+  // per-particle rows are summed
+  if (p == 0) {
+    const int per = (a.nipart + nb - 1) / nb;
+    const int r0 = (int)blockIdx.y * per, r1 = min(r0 + per, a.nipart);
+    double lat = 0.0;  // component threadIdx.x % 3 (the stride 126 keeps it)
+    for (int q = threadIdx.x; q < 3 * (r1 - r0) && threadIdx.x < 126; q += 126) {
+      lat += __ldcg(a.ipart + 3LL * r0 + q);
+      touched[3] = true;
+    }
+    const int j = threadIdx.x % 3;
+    if (j == 0) acc[18] = lat;
+    else if (j == 1) acc[19] = lat;
+    else acc[20] = lat;
+  }
+  bool on[4];
   on[0] = __syncthreads_or(touched[0]);
   on[1] = __syncthreads_or(touched[1]);
   on[2] = __syncthreads_or(touched[2]);
+  on[3] = __syncthreads_or(touched[3]);
   double* out = a.fpart + ((long long)p * a.fchunks + blockIdx.y) * FPART;
   block_sum_t<FPART>(acc, on, out);
   // the particle's last block sums its rows; the last particle integrates
@@ -483,7 +538,7 @@ __device__ void column_sums(const double* tab, int nrow, int stride, int col0, d
 // Euler (Sec. III.B), and its boxes follow the new position (start of S5).
 __device__ void integrate_all(const PartArgs& a) {
   __shared__ double claimed[3], total[3];
-  column_sums<3>(a.ipart, a.nipart, 3, 0, total);
+  column_sums<3>(a.psum, a.P, FPART, 18, total);
   column_sums<3>(a.psum, a.P, FPART, 6, claimed);
   double rem[3];
   for (int d = 0; d < 3; ++d) rem[d] = (total[d] + claimed[d]) / (double)a.P;  // claimed holds -sum i
