@@ -21,6 +21,8 @@ struct ek_ctx {
   cudaStream_t aux = nullptr;        // particle work of S4/S5 runs here, beside S3
   cudaEvent_t ev_lb = nullptr;       // S2 done
   cudaEvent_t ev_part = nullptr;     // S4 + re-flag done
+  cudaEvent_t ev_start = nullptr;    // step begins (the assignment may start)
+  cudaEvent_t ev_join = nullptr;     // all auxiliary work of the step done
   // one captured step per parity of `cur` (the ping-pong buffers alternate)
   cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
   long long graph_launches = 0;      // kernels and memsets in one captured step
@@ -390,6 +392,13 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
 // (which need S3's species) follow on the context's stream.
 ek_status enqueue_step(ek_ctx* ctx) {
   cudaStream_t s = ctx->stream;
+  if (ctx->P) {
+    // the nearest-surface assignment reads only the particle records, which
+    // S1 and S2 do not write: it runs beside them
+    EK_CUDA(cudaEventRecord(ctx->ev_start, s));
+    EK_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_start, 0));
+    EK_CUDA(launch_particle_forces(part_args(ctx), ctx->aux, S4_ASSIGN));
+  }
   ek_status st = enqueue_stage(ctx, 1);
   if (st != EK_OK) return st;
   const LBArgs la = lb_args(ctx);
@@ -399,15 +408,19 @@ ek_status enqueue_step(ek_ctx* ctx) {
   if (ctx->P) {
     EK_CUDA(cudaEventRecord(ctx->ev_lb, s));
     EK_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_lb, 0));
-    EK_CUDA(launch_particle_forces(pa, ctx->aux));
+    EK_CUDA(launch_particle_forces(pa, ctx->aux, S4_FORCES));
     EK_CUDA(launch_reflag(pa, true, ctx->aux, 1));
     EK_CUDA(cudaEventRecord(ctx->ev_part, ctx->aux));
+    // clearing the keys overlaps the transitions
+    EK_CUDA(launch_particle_forces(pa, ctx->aux, S4_KEY_RESET));
+    EK_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
   }
   EK_CUDA(ctx->fp32 ? launch_advection32(la, s) : launch_advection(la, s));
   ctx->launches += ctx->p.nspecies > 0 ? 2 : 1;
   if (ctx->P) {
     EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_part, 0));
     EK_CUDA(launch_reflag(pa, true, s, 2));
+    EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     ctx->launches += 12;
   }
   return EK_OK;
@@ -431,7 +444,8 @@ ek_status step_graphed(ek_ctx* ctx) {
       return st;
     }
     if (e != cudaSuccess) return fail(ctx, EK_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&ctx->step_graph[parity], graph, 0);
+    // keep the priority of the auxiliary stream on its captured kernels
+    e = cudaGraphInstantiate(&ctx->step_graph[parity], graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(ctx, EK_ERR_CUDA, std::string("step graph: ") + cudaGetErrorString(e));
     ctx->graph_launches = ctx->launches - l0;
@@ -578,9 +592,15 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
     cudaMemset(ctx->f[b], 0, 19 * N * rsz);
     cudaMemset(ctx->rho[b], 0, K * N * ssz);
   }
-  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+  // the particle chain on the auxiliary stream is latency-bound and shares the
+  // SMs with the advection: its blocks go first
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_lb, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_part, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     ek_destroy(ctx);
     return EK_ERR_CUDA;
@@ -613,6 +633,8 @@ ek_status ek_destroy(ek_ctx* ctx) {
   }
   if (ctx->ev_lb) cudaEventDestroy(ctx->ev_lb);
   if (ctx->ev_part) cudaEventDestroy(ctx->ev_part);
+  if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   delete ctx;
   return EK_OK;
 }

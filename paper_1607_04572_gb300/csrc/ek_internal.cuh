@@ -302,7 +302,11 @@ constexpr int FORCE_CHUNK = 512;
 // [18..20] a slice of the lattice total of the internal force (first particle
 // only), [16..17] and [21..23] unused
 constexpr int FPART = 24;
-cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s);  // S4
+// S4 in three launches: the nearest-surface assignment (needs only the
+// particle positions, so it may run beside S1/S2), the forces with the
+// integration (after S2), and the clearing of the assignment keys
+constexpr int S4_ASSIGN = 1, S4_FORCES = 2, S4_KEY_RESET = 4, S4_ALL = 7;
+cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s, int parts = S4_ALL);
 // S5; parts: 1 = re-flag, Psi and charge (no species access), 2 = transitions
 // (species after S3), 3 = both
 cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s, int parts = 3);

@@ -71,7 +71,7 @@ constexpr int PSI_DEPTH = 4;
 // 4 levels of dyadic offsets (absolute error per component below
 // 6 * 2^-24 (R + 2)); the float squared distances of the farthest corner and
 // of the closest point are then within 3e-6 (R + 2)^2 of the exact ones, so
-// whenever they are more than `margin` = 4e-5 (R + 2)^2 away from R^2 the FP64
+// whenever they are more than `margin` = 6e-6 (R + 2)^2 away from R^2 the FP64
 // decision is already known.  Returns -1 when the exact test is needed.
 __device__ __forceinline__ int classify_f32(float ox, float oy, float oz, float h, float R2,
                                             float margin) {
@@ -132,7 +132,7 @@ __device__ __forceinline__ void subcube_centre_d(int path, int l, double X, doub
 
 __device__ __forceinline__ float psi_margin(double R2) {
   const float Rp2 = sqrtf((float)R2) + 2.0f;
-  return 4e-5f * Rp2 * Rp2;
+  return 6e-6f * Rp2 * Rp2;
 }
 
 __device__ __forceinline__ bool node_inside(int X, int Y, int Z, const DevParticle& P) {
@@ -346,28 +346,33 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
     const bool in_box = X >= P.lo[0] && X < P.hi[0] && Y >= P.lo[1] && Y < P.hi[1] &&
                         Z >= P.lo[2] && Z < P.hi[2];
     if (own == FLUID && in_box) {
-      // momentum exchange on every link from this fluid node into the particle (Eq. 11)
-      const double d0x = (double)X - P.pos[0], d0y = (double)Y - P.pos[1], d0z = (double)Z - P.pos[2];
-      const double wx = P.vel[0] + (P.omega[1] * d0z - P.omega[2] * d0y);
-      const double wy = P.vel[1] + (P.omega[2] * d0x - P.omega[0] * d0z);
-      const double wz = P.vel[2] + (P.omega[0] * d0y - P.omega[1] * d0x);
+      // momentum exchange on every link from this fluid node into the particle
+      // (Eq. 11): the links first (all 18 owner loads in flight together), the
+      // FP64 arithmetic only at nodes next to the surface
       const Nbr b = make_nbr(w3[0], w3[1], w3[2], g);
-      double fx = 0.0, fy = 0.0, fz = 0.0;
-      bool link = false;
+      unsigned links = 0;
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         const long long m = node_index(g, nb_x(b, w3[0], dcx(i)), nb_y(b, w3[1], dcy(i)),
                                        nb_z(b, w3[2], dcz(i)));
-        if (a.owner[m] != p) continue;
-        link = true;
-        const double refl = pop_abs<FM>(a.f, opp(i), N, n, rho0);
-        const double fs = refl + 6.0 * wgt(i) * rho0 * cdot(i, wx, wy, wz);  // the population that hit the wall
-        const double mom = fs + refl;
-        if (dcx(i)) fx = dcx(i) > 0 ? fx + mom : fx - mom;
-        if (dcy(i)) fy = dcy(i) > 0 ? fy + mom : fy - mom;
-        if (dcz(i)) fz = dcz(i) > 0 ? fz + mom : fz - mom;
+        if (a.owner[m] == p) links |= 1u << i;
       }
-      if (link) {
+      if (links) {
+        const double d0x = (double)X - P.pos[0], d0y = (double)Y - P.pos[1], d0z = (double)Z - P.pos[2];
+        const double wx = P.vel[0] + (P.omega[1] * d0z - P.omega[2] * d0y);
+        const double wy = P.vel[1] + (P.omega[2] * d0x - P.omega[0] * d0z);
+        const double wz = P.vel[2] + (P.omega[0] * d0y - P.omega[1] * d0x);
+        double fx = 0.0, fy = 0.0, fz = 0.0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          if (!(links & (1u << i))) continue;
+          const double refl = pop_abs<FM>(a.f, opp(i), N, n, rho0);
+          const double fs = refl + 6.0 * wgt(i) * rho0 * cdot(i, wx, wy, wz);  // the population that hit the wall
+          const double mom = fs + refl;
+          if (dcx(i)) fx = dcx(i) > 0 ? fx + mom : fx - mom;
+          if (dcy(i)) fy = dcy(i) > 0 ? fy + mom : fy - mom;
+          if (dcz(i)) fz = dcz(i) > 0 ? fz + mom : fz - mom;
+        }
         touched[0] = true;
         acc[0] += fx;
         acc[1] += fy;
@@ -974,13 +979,13 @@ __global__ void k_apply_transfers(PartArgs a) {
 }
 
 template <class FM>
-cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s) {
+cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s, int parts) {
   const unsigned echunks = (unsigned)((a.emax + PT - 1) / PT);
-  k_force_assign<<<dim3(a.P, echunks), PT, 0, s>>>(a);
-  k_particle_forces<FM><<<dim3(a.P, a.fchunks), FORCE_T, 0, s>>>(a);
+  if (parts & S4_ASSIGN) k_force_assign<<<dim3(a.P, echunks), PT, 0, s>>>(a);
+  if (parts & S4_FORCES) k_particle_forces<FM><<<dim3(a.P, a.fchunks), FORCE_T, 0, s>>>(a);
   // the widened boxes have moved with the integration: clear the keys of the
-  // old ones, which k_force_assign kept in elo_prev / ehi_prev
-  k_key_reset<<<dim3(a.P, echunks), PT, 0, s>>>(a);
+  // old ones, which the integration kept in kelo / kehi
+  if (parts & S4_KEY_RESET) k_key_reset<<<dim3(a.P, echunks), PT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1023,9 +1028,9 @@ cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s, int pa
 
 }  // namespace
 
-cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s) {
+cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s, int parts) {
   if (a.P == 0) return cudaSuccess;
-  return a.ph.fp32 ? particle_forces_t<FormF32>(a, s) : particle_forces_t<FormF64>(a, s);
+  return a.ph.fp32 ? particle_forces_t<FormF32>(a, s, parts) : particle_forces_t<FormF64>(a, s, parts);
 }
 
 cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s, int parts) {
