@@ -294,8 +294,14 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_inv(PassArgs<R> a, int pa
 // rows are padded by one element every 16, which keeps the strided stores of
 // the first stage free of bank conflicts.
 // ---------------------------------------------------------------------------
-constexpr int FAST_T = 128;           // threads per CTA
+constexpr int FAST_T = 256;           // threads per CTA of the y / z passes
 constexpr int FAST_ELEMS = 2048;      // complex elements per CTA and buffer (before padding)
+// the x passes gather the charge (or scatter Phi) straight from the lattice:
+// more, smaller CTAs keep more loads in flight
+constexpr int FAST_XT = 256;
+constexpr int FAST_XELEMS = 1024;
+constexpr int FAST_IT = 128;      // inverse x pass
+constexpr int FAST_IELEMS = 2048;
 __host__ __device__ constexpr int fpad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int fast_radix(int n, int s) {
   // radices of the stages: 32 = 8 4, 64 = 8 8, 128 = 16 8, 256 = 16 16, 512 = 8 8 8
@@ -362,7 +368,7 @@ template <int N, int NS, int R, bool INV>
 __device__ __forceinline__ void fast_stage(const float2* in, float2* out, int nl, const float2* tw) {
   constexpr int M = N / R;
   constexpr int LS = fpad(N);
-  for (int t = threadIdx.x; t < nl * M; t += FAST_T) {
+  for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
     const int line = t / M, j = t % M;
     const float2* src = in + line * LS;
     float2* dst = out + line * LS;
@@ -405,13 +411,13 @@ __device__ float2* fast_fft(float2* a, float2* b, int nl, const float2* tw) {
 
 template <int N>
 __device__ __forceinline__ void load_twiddles(float2* tw, const AxisPlan& P) {
-  for (int k = threadIdx.x; k < N; k += FAST_T) tw[k] = P.tw32[k];
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = P.tw32[k];
 }
 
 // X pass, forward, rows r0 = 2p, r1 = 2p + 1 packed as a + i b (as k_fft_x_fwd)
 template <int NX>
-__global__ void __launch_bounds__(FAST_T) k_fast_x_fwd(PassArgs<float> a) {
-  constexpr int PPC = FAST_ELEMS / NX;  // row pairs per CTA
+__global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
+  constexpr int PPC = FAST_XELEMS / NX > 0 ? FAST_XELEMS / NX : 1;  // row pairs per CTA
   constexpr int LS = fpad(NX);
   __shared__ __align__(16) float2 buf[2][PPC * LS];
   __shared__ float2 tw[NX];
@@ -419,10 +425,10 @@ __global__ void __launch_bounds__(FAST_T) k_fast_x_fwd(PassArgs<float> a) {
   const int nrows = a.ny * a.nz;
   const long long N = (long long)NX * a.ny * a.nz;
   const int p0 = blockIdx.x * PPC;
-  // PPC * NX / FAST_T = 16 elements per thread: unrolled, so the loads of
-  // several elements are in flight together
+  // PPC * NX / FAST_XT = 4 elements per thread: unrolled, so the loads of
+  // all of them are in flight together
 #pragma unroll 8
-  for (int t = threadIdx.x; t < PPC * NX; t += FAST_T) {
+  for (int t = threadIdx.x; t < PPC * NX; t += FAST_XT) {
     const int l = t / NX, x = t % NX;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
     float re = 0.0f, im = 0.0f;
@@ -433,7 +439,7 @@ __global__ void __launch_bounds__(FAST_T) k_fast_x_fwd(PassArgs<float> a) {
   __syncthreads();
   const float2* res = fast_fft<NX, false>(buf[0], buf[1], PPC, tw);
   constexpr int NXH = NX / 2 + 1;
-  for (int t = threadIdx.x; t < PPC * NXH; t += FAST_T) {
+  for (int t = threadIdx.x; t < PPC * NXH; t += FAST_XT) {
     const int l = t / NXH, k = t % NXH;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
     if (r0 >= nrows) continue;
@@ -494,8 +500,8 @@ __global__ void __launch_bounds__(FAST_T) k_fast_yz(PassArgs<float> a, int tx) {
 
 // X pass, inverse (complex-to-real), two rows per complex transform (as k_fft_x_inv)
 template <int NX>
-__global__ void __launch_bounds__(FAST_T) k_fast_x_inv(PassArgs<float> a) {
-  constexpr int PPC = FAST_ELEMS / NX;
+__global__ void __launch_bounds__(FAST_IT) k_fast_x_inv(PassArgs<float> a) {
+  constexpr int PPC = FAST_IELEMS / NX > 0 ? FAST_IELEMS / NX : 1;
   constexpr int LS = fpad(NX);
   constexpr int NXH = NX / 2 + 1;
   __shared__ __align__(16) float2 buf[2][PPC * LS];
@@ -504,7 +510,7 @@ __global__ void __launch_bounds__(FAST_T) k_fast_x_inv(PassArgs<float> a) {
   const int nrows = a.ny * a.nz;
   const int p0 = blockIdx.x * PPC;
 #pragma unroll 8
-  for (int t = threadIdx.x; t < PPC * NX; t += FAST_T) {
+  for (int t = threadIdx.x; t < PPC * NX; t += FAST_IT) {
     const int l = t / NX, k = t % NX;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
     float2 A = make_float2(0.0f, 0.0f), B = make_float2(0.0f, 0.0f);
@@ -520,7 +526,7 @@ __global__ void __launch_bounds__(FAST_T) k_fast_x_inv(PassArgs<float> a) {
   }
   __syncthreads();
   const float2* res = fast_fft<NX, true>(buf[0], buf[1], PPC, tw);
-  for (int t = threadIdx.x; t < PPC * NX; t += FAST_T) {
+  for (int t = threadIdx.x; t < PPC * NX; t += FAST_IT) {
     const int l = t / NX, x = t % NX;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
     const float2 v = res[l * LS + fpad(x)];
@@ -532,9 +538,13 @@ __global__ void __launch_bounds__(FAST_T) k_fast_x_inv(PassArgs<float> a) {
 template <int NX>
 void launch_fast_x(PassArgs<float>& a, bool inverse, cudaStream_t s) {
   const int npairs = (a.ny * a.nz + 1) / 2;
-  const unsigned g = (unsigned)((npairs + FAST_ELEMS / NX - 1) / (FAST_ELEMS / NX));
-  if (inverse) k_fast_x_inv<NX><<<g, FAST_T, 0, s>>>(a);
-  else k_fast_x_fwd<NX><<<g, FAST_T, 0, s>>>(a);
+  if (inverse) {
+    constexpr int ppc = FAST_IELEMS / NX > 0 ? FAST_IELEMS / NX : 1;
+    k_fast_x_inv<NX><<<(unsigned)((npairs + ppc - 1) / ppc), FAST_IT, 0, s>>>(a);
+  } else {
+    constexpr int ppc = FAST_XELEMS / NX > 0 ? FAST_XELEMS / NX : 1;
+    k_fast_x_fwd<NX><<<(unsigned)((npairs + ppc - 1) / ppc), FAST_XT, 0, s>>>(a);
+  }
 }
 
 template <int NL, int AXIS, bool INV>
