@@ -36,22 +36,28 @@ METRIC = "MLUPS per full EK step and % of HBM roofline, FP32/batched vs plain FP
 FLUSH_NOTE = ("state > L2 (populations 2 x 19 x 4 B x N = 319 MB in the FP32 form, 637 MB in "
               "FP64, at 128^3; L2 129 MB), no flush needed")
 
-# Algorithmic work of the fused flux + LB kernel (k_lb_fused), per fluid node,
-# two species, partial volumes on, bulk node (all 18 links fluid): bytes that
-# must cross HBM once per step and FP64 operations of the formulas.
-LB_BYTES_PER_NODE = 2 * 19 * 8 + 2 * 2 * 8 + 8 + 8 + 4 + 3 * 8   # f r/w, rho r/w, psi, phi, owner, u
+# Algorithmic work of the fused flux + LB kernel, per fluid node, two species,
+# partial volumes on, bulk node (all 18 links fluid): bytes that must cross
+# HBM once per step (populations read + written, species read + written after
+# the flux divergence, Psi, Phi and the node class read, u and the internal
+# solute force written for S3 / S4, one sign byte) and FP64 operations of the
+# formulas.
+LB_BYTES_PER_NODE = 2 * 19 * 8 + 2 * 2 * 8 + 8 + 8 + 4 + 3 * 8 + 3 * 8 + 1   # 405 (k_lb_fused)
 LB_FP64_FLOP_PER_NODE = 950
-# the same for the FP32-storage kernel (k_lb32): float populations, int32 species
-LB32_BYTES_PER_NODE = 2 * 19 * 4 + 2 * 2 * 4 + 4 + 4 + 4 + 3 * 4
+# the same for the FP32-storage kernel (k_lb32_tiled): float populations,
+# int32 species, float Psi / Phi / u / internal force
+LB32_BYTES_PER_NODE = 2 * 19 * 4 + 2 * 2 * 4 + 4 + 4 + 4 + 3 * 4 + 3 * 4 + 1  # 205
 # FP64 peak derived from the unit counts: 152 SMs x 2.07 GHz x 4 flop/clk/SM
 # (2 DFMA per clock per SM); a DFMA probe on this pool measured 1.19 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 
-# DRAM traffic of one k_lb_fused launch from an ncu capture (profiles/), valid
-# only for the kernel source it was taken on.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+# from an ncu capture of the 128^3 workload (profiles/), valid only for the
+# kernel source it was taken on.
 TRAFFIC = {"k_lb_fused": {"bytes_per_launch": 755997696,  # profiles/fp64_k_lb_fused_k_advect_single128.md
                            "source_sha": "85d705496daa5794", "file": "ek_lattice.cu"},
-           "k_lb32": {"bytes_per_launch": None, "source_sha": None, "file": "ek_lattice32.cu"}}
+           "k_lb32": {"bytes_per_launch": 202542336 + 180089856,  # profiles/fp32_kernels_single128.md
+                      "source_sha": "e5cb5d9164bc29f8", "file": "ek_lattice32.cu"}}
 
 
 def src_sha(name: str) -> str:
