@@ -80,8 +80,10 @@ enum {
                             opposite valence so the box is neutral                 */
   EK_FP32 = 16           /* FP32-storage form: populations stored as f_i - w_i rho0
                             in float, species as int32 multiples of a per-species
-                            unit 2^-e (e = ceil(20 - log2 bulk_k): at least 2^20
-                            units per bulk density), Phi, Psi, u, charges and the
+                            unit 2^-e (e = ceil(20 - log2 rho_k), rho_k the larger
+                            of bulk_k and the initial density after
+                            neutralisation: at least 2^20 units per initial
+                            density), Phi, Psi, u, charges and the
                             FFT in float, arithmetic in float; particle forces,
                             torques and the integrator stay FP64.  Every species
                             transfer moves whole units between nodes, so the
@@ -232,6 +234,59 @@ ek_status ek_poisson_solve(const double* q, double* phi, int nx, int ny, int nz,
 #define EK_POISSON_STATIC_MAX (1u << 19)
 ek_status ek_poisson_solve_static(const double* q, double* phi, int nx, int ny, int nz,
                                   double bjerrum, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched ensemble: many independent systems (box sizes, salts, fields and
+ * particles of their own, e.g. a mobility sweep) advanced together.  The
+ * paper runs one system at a time; batching is a service of this library.
+ *
+ * The systems are ordinary contexts, created and set up by the caller
+ * (ek_create, ek_add_particle, ek_set_field); the batch borrows them (they
+ * must outlive it and are not destroyed by it).  One batch step advances
+ * every system by one time step, exactly as ek_step would, with all systems'
+ * kernels in one CUDA graph launch: the systems are independent branches of
+ * the graph, so their kernels run side by side on the GPU.  The graph is
+ * captured on the first step (one per ping-pong parity) and again whenever a
+ * system's set-up, field E / body force or tuning changes.
+ *
+ * Work of a batch step is ordered on the batch stream only: call
+ * ek_batch_sync before reading a system (ek_get_fields, ek_get_particles) or
+ * stepping it alone, and do not step a system alone while batch steps are in
+ * flight. */
+typedef struct ek_batch ek_batch;
+
+/* Batch over systems[0..nsys-1] (distinct contexts on the same GPU, each set
+ * up; copies the pointer list).  Waits for the systems' pending work.  Errors:
+ * EK_ERR_ARG (null, repeated or cross-device contexts), EK_ERR_STATE (a
+ * context in an error state), EK_ERR_CUDA. */
+ek_status ek_batch_create(ek_ctx* const* systems, int nsys, ek_batch** out);
+/* Waits for the batch stream and frees the batch (not its systems). */
+ek_status ek_batch_destroy(ek_batch* b);
+/* Launch later batch steps on `stream` (a cudaStream_t other than the legacy
+ * default stream); waits for the batch's earlier work. */
+ek_status ek_batch_set_stream(ek_batch* b, void* stream);
+/* Enqueue nsteps batch steps; returns without waiting. */
+ek_status ek_batch_step_async(ek_batch* b, int nsteps);
+/* ek_batch_step_async, then ek_batch_sync. */
+ek_status ek_batch_step(ek_batch* b, int nsteps);
+/* Wait for the batch stream and read every system's device status word; the
+ * first failing system's status is returned (ek_batch_last_error names it). */
+ek_status ek_batch_sync(ek_batch* b);
+/* Autotuner: times every candidate configuration -- branch streams at capture
+ * (8, 16, 32, 64 or one per system, at most 64), FP32 S2 segment length (2, 4
+ * or 8 planes per block) and whether each system's particle chain runs beside
+ * its advection or in line -- over 2 + trial_steps real batch steps each (the
+ * systems advance by those steps), keeps the fastest and stores its time per
+ * batch step in *best_ms (may be null).  Results do not depend on the choice
+ * except for the summation order of the lattice-block force sums. */
+ek_status ek_batch_tune(ek_batch* b, int trial_steps, double* best_ms);
+/* Current configuration: cfg[0] branch streams, cfg[1] planes per S2 block,
+ * cfg[2] particle chain beside the advection (1) or in line (0). */
+ek_status ek_batch_config(const ek_batch* b, int cfg[3]);
+/* Number of systems; 0 for a null batch. */
+int ek_batch_size(const ek_batch* b);
+/* Reason for the last failure of a batch call. */
+const char* ek_batch_last_error(const ek_batch* b);
 
 #ifdef __cplusplus
 }

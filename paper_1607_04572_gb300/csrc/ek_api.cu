@@ -8,6 +8,8 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <vector>
+#include <string>
 
 #include "ek_internal.cuh"
 
@@ -39,7 +41,10 @@ struct ek_ctx {
   void* ifield = nullptr;              // 3N reals: internal solute force on the fluid (S2)
   double* ipart = nullptr;             // 3 doubles per lattice block: its sums
   int nipart = 0;
+  int nipart_cap = 0;  // rows allocated for ipart (FP32: enough for 2-plane segments)
   int nzb = 1;       // FP32 S2: z segments per tile column
+  int overlap = 1;   // particle chain on the auxiliary stream (1) or in line (0)
+  unsigned long long version = 0;  // bumped whenever captured steps go stale
   unsigned long long* fkey = nullptr;  // N: nearest-particle keys of S4
   unsigned char* vsig = nullptr;       // N: fluid bit and velocity sign codes (S2 -> S3)
   int emax = 0;                        // cells of the widest widened box
@@ -226,6 +231,7 @@ LBArgs lb_args(ek_ctx* ctx) {
 
 // pull the device particle records into the host copy
 void drop_graphs(ek_ctx* ctx) {
+  ++ctx->version;
   for (int i = 0; i < 2; ++i) {
     if (ctx->step_graph[i]) cudaGraphExecDestroy(ctx->step_graph[i]);
     ctx->step_graph[i] = nullptr;
@@ -321,6 +327,15 @@ ek_status run_setup(ek_ctx* ctx) {
     }
   }
   if (ctx->fp32) {
+    // one species unit is 2^-e with at least 2^20 units per initial density
+    // (after neutralisation: counter-ions of a highly charged particle in a
+    // dilute salt can outnumber the bulk many times), so densities up to
+    // 2048 times the initial one fit int32
+    for (int k = 0; k < EK_MAX_SPECIES; ++k) {
+      const double ref = k < ctx->p.nspecies ? std::max(bulk[k], ctx->p.bulk[k]) : 0.0;
+      const int e = ref > 0.0 ? (int)ceil(20.0 - log2(ref)) : 30;
+      ctx->ph.qscale[k] = ldexp(1.0, -e);
+    }
     int units[EK_MAX_SPECIES] = {0, 0, 0, 0};
     for (int k = 0; k < ctx->p.nspecies; ++k) {
       const double v = rint(bulk[k] / ctx->ph.qscale[k]);
@@ -392,6 +407,23 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
 // (which need S3's species) follow on the context's stream.
 ek_status enqueue_step(ek_ctx* ctx) {
   cudaStream_t s = ctx->stream;
+  if (ctx->P && !ctx->overlap) {
+    // everything in line on the context's stream (the batch tuner's other choice)
+    EK_CUDA(launch_particle_forces(part_args(ctx), s, S4_ASSIGN));
+    ek_status st = enqueue_stage(ctx, 1);
+    if (st != EK_OK) return st;
+    const LBArgs la = lb_args(ctx);
+    EK_CUDA(ctx->fp32 ? launch_lb32(la, s) : launch_lb_fused(la, s));
+    ctx->cur = 1 - ctx->cur;
+    const PartArgs pa = part_args(ctx);
+    EK_CUDA(launch_particle_forces(pa, s, S4_FORCES));
+    EK_CUDA(launch_reflag(pa, true, s, 1));
+    EK_CUDA(ctx->fp32 ? launch_advection32(la, s) : launch_advection(la, s));
+    EK_CUDA(launch_reflag(pa, true, s, 2));
+    EK_CUDA(launch_particle_forces(pa, s, S4_KEY_RESET));
+    ctx->launches += (ctx->p.nspecies > 0 ? 2 : 1) + 12;
+    return EK_OK;
+  }
   if (ctx->P) {
     // the nearest-surface assignment reads only the particle records, which
     // S1 and S2 do not write: it runs beside them
@@ -560,8 +592,11 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
     if (ctx->fp32) ctx->nzb = lb32_segments(g, p->nspecies, (p->flags & EK_PV) != 0);
     const dim3 lg = ctx->fp32 ? lattice_grid32(g, ctx->nzb) : lattice_grid(g);
     ctx->nipart = (int)(lg.x * lg.y * lg.z);
+    // the FP32 segment length may be retuned down to 2 planes (ek_batch_tune)
+    ctx->nipart_cap = ctx->fp32 ? (int)(lg.x * lg.y) * std::max(1, (g.nz + 1) / 2) : ctx->nipart;
+    ctx->nipart_cap = std::max(ctx->nipart_cap, ctx->nipart);
   }
-  alloc((void**)&ctx->ipart, (size_t)ctx->nipart * 3 * sizeof(double));
+  alloc((void**)&ctx->ipart, (size_t)ctx->nipart_cap * 3 * sizeof(double));
   alloc((void**)&ctx->fkey, N * sizeof(unsigned long long));
   alloc((void**)&ctx->vsig, N);
   alloc((void**)&ctx->tmp, N * sizeof(double));
@@ -1021,5 +1056,328 @@ ek_status ek_poisson_solve(const double* q, double* phi, int nx, int ny, int nz,
     return EK_ERR_CUDA;
   return EK_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched ensemble: many independent systems (each an ek_ctx of its own box
+// size, salt, field and particles) advanced together.  One step of all of
+// them is one CUDA graph: the systems are branches of the graph (spread over
+// `width` branch streams at capture), so the GPU runs their kernels side by
+// side and one graph launch replaces a few dozen launches per system.
+// ---------------------------------------------------------------------------
+struct ek_batch {
+  std::vector<ek_ctx*> sys;
+  cudaStream_t stream = nullptr;  // where the step graphs are launched
+  bool own_stream = false;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // keyed by the first system's ping-pong parity
+  std::vector<int> cur_at[2];                      // every system's parity at capture
+  std::vector<unsigned long long> version_at[2];
+  std::vector<long long> dlaunch[2];               // each system's launches per replay
+  int width = 16;   // branch streams used at capture
+  int planes = 4;   // FP32 S2 segment length (planes per block)
+  int overlap = 1;  // particle chain beside S3 in each system
+  int device = 0;
+  std::string err;
+};
+
+namespace {
+
+ek_status bfail(ek_batch* b, ek_status st, const std::string& msg) {
+  b->err = msg;
+  return st;
+}
+
+void batch_drop(ek_batch* b) {
+  for (int i = 0; i < 2; ++i) {
+    if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+    b->graph[i] = nullptr;
+    b->cur_at[i].clear();
+    b->version_at[i].clear();
+    b->dlaunch[i].clear();
+  }
+}
+
+// apply the batch's segment length and overlap choice to every system
+void batch_apply(ek_batch* b) {
+  for (ek_ctx* c : b->sys) {
+    int nzb = c->nzb;
+    if (c->fp32) nzb = std::max(1, (c->g.nz + b->planes - 1) / b->planes);
+    const int xt = (c->g.nx + TILE_X - 1) / TILE_X, yt = (c->g.ny + TILE_Y - 1) / TILE_Y;
+    if (c->fp32 && xt * yt * nzb > c->nipart_cap) nzb = c->nipart_cap / (xt * yt);
+    if (nzb != c->nzb || c->overlap != b->overlap) {
+      c->nzb = nzb;
+      if (c->fp32) c->nipart = xt * yt * nzb;
+      c->overlap = b->overlap;
+      drop_graphs(c);
+    }
+  }
+}
+
+ek_status batch_capture(ek_batch* b, int key) {
+  const int width = std::max(1, std::min<int>(b->width, (int)b->branch.size()));
+  std::vector<int> cur0(b->sys.size());
+  std::vector<cudaStream_t> saved(b->sys.size());
+  std::vector<long long> l0v(b->sys.size());
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    cur0[i] = b->sys[i]->cur;
+    saved[i] = b->sys[i]->stream;
+    l0v[i] = b->sys[i]->launches;
+  }
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return bfail(b, EK_ERR_CUDA, "batch capture could not start");
+  ek_status st = EK_OK;
+  if (cudaEventRecord(b->ev_fork, b->stream) != cudaSuccess) st = EK_ERR_CUDA;
+  for (int w = 0; w < width && st == EK_OK; ++w)
+    if (cudaStreamWaitEvent(b->branch[w], b->ev_fork, 0) != cudaSuccess) st = EK_ERR_CUDA;
+  for (size_t i = 0; i < b->sys.size() && st == EK_OK; ++i) {
+    ek_ctx* c = b->sys[i];
+    c->stream = b->branch[i % width];
+    st = enqueue_step(c);
+    c->stream = saved[i];
+  }
+  for (int w = 0; w < width && st == EK_OK; ++w) {
+    if (cudaEventRecord(b->ev_join[w], b->branch[w]) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->ev_join[w], 0) != cudaSuccess)
+      st = EK_ERR_CUDA;
+  }
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+  for (size_t i = 0; i < b->sys.size(); ++i) b->sys[i]->cur = cur0[i];  // nothing ran yet
+  if (st != EK_OK || e != cudaSuccess) {
+    for (size_t i = 0; i < b->sys.size(); ++i) b->sys[i]->launches = l0v[i];
+    if (graph) cudaGraphDestroy(graph);
+    return bfail(b, st != EK_OK ? st : EK_ERR_CUDA, "batch capture failed");
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&b->graph[key], graph, cudaGraphInstantiateFlagUseNodePriority);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return bfail(b, EK_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(ei));
+  // the capture counted its launches on the systems: take them back and add
+  // them per replay
+  b->dlaunch[key].resize(b->sys.size());
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    b->dlaunch[key][i] = b->sys[i]->launches - l0v[i];
+    b->sys[i]->launches = l0v[i];
+  }
+  b->cur_at[key] = cur0;
+  b->version_at[key].resize(b->sys.size());
+  for (size_t i = 0; i < b->sys.size(); ++i) b->version_at[key][i] = b->sys[i]->version;
+  return EK_OK;
+}
+
+bool batch_graph_valid(const ek_batch* b, int key) {
+  if (!b->graph[key] || b->cur_at[key].size() != b->sys.size()) return false;
+  for (size_t i = 0; i < b->sys.size(); ++i)
+    if (b->sys[i]->cur != b->cur_at[key][i] || b->sys[i]->version != b->version_at[key][i]) return false;
+  return true;
+}
+
+ek_status batch_step_once(ek_batch* b) {
+  const int key = b->sys[0]->cur;
+  if (!batch_graph_valid(b, key)) {
+    if (b->graph[key]) {
+      cudaGraphExecDestroy(b->graph[key]);
+      b->graph[key] = nullptr;
+    }
+    ek_status st = batch_capture(b, key);
+    if (st != EK_OK) return st;
+  }
+  if (cudaGraphLaunch(b->graph[key], b->stream) != cudaSuccess)
+    return bfail(b, EK_ERR_CUDA, "batch graph launch failed");
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    b->sys[i]->cur = 1 - b->sys[i]->cur;
+    b->sys[i]->launches += b->dlaunch[key][i];
+  }
+  return EK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ek_status ek_batch_create(ek_ctx* const* systems, int nsys, ek_batch** out) {
+  if (!systems || nsys <= 0 || !out) return EK_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < nsys; ++i) {
+    if (!systems[i]) return EK_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (systems[j] == systems[i]) return EK_ERR_ARG;
+  }
+  ek_batch* b = new (std::nothrow) ek_batch();
+  if (!b) return EK_ERR_NOMEM;
+  b->sys.assign(systems, systems + nsys);
+  b->device = systems[0]->device;
+  for (ek_ctx* c : b->sys) {
+    if (c->device != b->device) {
+      delete b;
+      return EK_ERR_ARG;
+    }
+    if (ready(c) != EK_OK || c->broken) {
+      delete b;
+      return EK_ERR_STATE;
+    }
+  }
+  cudaSetDevice(b->device);
+  const int nbranch = std::min(nsys, 64);
+  bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  b->own_stream = true;
+  b->branch.assign(nbranch, nullptr);
+  b->ev_join.assign(nbranch, nullptr);
+  for (int w = 0; w < nbranch && ok; ++w) {
+    ok = cudaStreamCreateWithFlags(&b->branch[w], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_join[w], cudaEventDisableTiming) == cudaSuccess;
+  }
+  // the systems' earlier work (set-up, fields) is on their own streams
+  for (ek_ctx* c : b->sys) ok = ok && cudaStreamSynchronize(c->stream) == cudaSuccess;
+  b->width = std::min(nbranch, 16);
+  if (!ok) {
+    ek_batch_destroy(b);
+    return EK_ERR_CUDA;
+  }
+  batch_apply(b);
+  *out = b;
+  return EK_OK;
+}
+
+ek_status ek_batch_destroy(ek_batch* b) {
+  if (!b) return EK_ERR_ARG;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop(b);
+  for (size_t w = 0; w < b->branch.size(); ++w) {
+    if (b->branch[w]) cudaStreamDestroy(b->branch[w]);
+    if (b->ev_join[w]) cudaEventDestroy(b->ev_join[w]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return EK_OK;
+}
+
+ek_status ek_batch_set_stream(ek_batch* b, void* stream) {
+  if (!b || !stream) return EK_ERR_ARG;
+  cudaSetDevice(b->device);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, EK_ERR_CUDA, "sync failed");
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  b->own_stream = false;
+  b->stream = (cudaStream_t)stream;
+  batch_drop(b);
+  return EK_OK;
+}
+
+ek_status ek_batch_step_async(ek_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return EK_ERR_ARG;
+  cudaSetDevice(b->device);
+  for (ek_ctx* c : b->sys) {
+    if (c->broken) return bfail(b, EK_ERR_STATE, "a system is in an error state: " + c->err);
+    if (c->setup_pending) {
+      // set-up runs on the system's own stream; order it before the batch
+      if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, EK_ERR_CUDA, "sync failed");
+      const ek_status st = ready(c);
+      if (st != EK_OK) return bfail(b, st, "set-up of a system failed: " + c->err);
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bfail(b, EK_ERR_CUDA, "sync failed");
+    }
+  }
+  for (int t = 0; t < nsteps; ++t) {
+    const ek_status st = batch_step_once(b);
+    if (st != EK_OK) return st;
+  }
+  return EK_OK;
+}
+
+ek_status ek_batch_sync(ek_batch* b) {
+  if (!b) return EK_ERR_ARG;
+  cudaSetDevice(b->device);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, EK_ERR_CUDA, "batch stream failed");
+  ek_status worst = EK_OK;
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    const ek_status st = check_status(b->sys[i]);
+    if (st != EK_OK && worst == EK_OK) {
+      worst = st;
+      b->err = "system " + std::to_string(i) + ": " + b->sys[i]->err;
+    }
+  }
+  return worst;
+}
+
+ek_status ek_batch_step(ek_batch* b, int nsteps) {
+  const ek_status st = ek_batch_step_async(b, nsteps);
+  if (st != EK_OK) return st;
+  return ek_batch_sync(b);
+}
+
+ek_status ek_batch_config(const ek_batch* b, int cfg[3]) {
+  if (!b || !cfg) return EK_ERR_ARG;
+  cfg[0] = b->width;
+  cfg[1] = b->planes;
+  cfg[2] = b->overlap;
+  return EK_OK;
+}
+
+// Autotuner: every candidate (branch width x S2 segment length x overlap of
+// the particle chain) is captured and timed over `trial_steps` real steps of
+// the whole batch (CUDA events on the batch stream, after one untimed step
+// that uploads the graph); the fastest is kept.
+ek_status ek_batch_tune(ek_batch* b, int trial_steps, double* best_ms) {
+  if (!b || trial_steps <= 0) return EK_ERR_ARG;
+  cudaSetDevice(b->device);
+  const int nbranch = (int)b->branch.size();
+  std::vector<int> widths;
+  for (int w : {8, 16, 32, 64})
+    if (w < nbranch) widths.push_back(w);
+  widths.push_back(nbranch);
+  const int planes_set[3] = {2, 4, 8};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return bfail(b, EK_ERR_CUDA, "event creation failed");
+  double best = 1e300;
+  int bw = b->width, bp = b->planes, bo = b->overlap;
+  ek_status st = EK_OK;
+  for (int w : widths) {
+    for (int pl : planes_set) {
+      for (int ov = 0; ov <= 1 && st == EK_OK; ++ov) {
+        b->width = w;
+        b->planes = pl;
+        b->overlap = ov;
+        batch_apply(b);
+        batch_drop(b);
+        st = ek_batch_step_async(b, 2);  // captures both parities and uploads them
+        if (st != EK_OK) break;
+        if (cudaEventRecord(e0, b->stream) != cudaSuccess) st = EK_ERR_CUDA;
+        if (st == EK_OK) st = ek_batch_step_async(b, trial_steps);
+        if (st == EK_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess ||
+                            cudaEventSynchronize(e1) != cudaSuccess))
+          st = EK_ERR_CUDA;
+        float ms = 0.0f;
+        if (st == EK_OK) cudaEventElapsedTime(&ms, e0, e1);
+        const double per = (double)ms / trial_steps;
+        if (st == EK_OK && per < best) {
+          best = per;
+          bw = w;
+          bp = pl;
+          bo = ov;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != EK_OK) return st;
+  b->width = bw;
+  b->planes = bp;
+  b->overlap = bo;
+  batch_apply(b);
+  batch_drop(b);
+  if (best_ms) *best_ms = best;
+  return ek_batch_sync(b);
+}
+
+int ek_batch_size(const ek_batch* b) { return b ? (int)b->sys.size() : 0; }
+
+const char* ek_batch_last_error(const ek_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
 }  // extern "C"

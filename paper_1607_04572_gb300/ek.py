@@ -46,7 +46,10 @@ EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get
            "ek_step", "ek_step_async", "ek_run_stage", "ek_get_particles", "ek_num_particles",
            "ek_set_stream", "ek_sync", "ek_last_error", "ek_lattice_dirs",
            "ek_poisson_scratch_bytes", "ek_poisson_solve", "ek_step_timed",
-           "ek_kernel_launches", "ek_poisson_solve_static"]
+           "ek_kernel_launches", "ek_poisson_solve_static",
+           "ek_batch_create", "ek_batch_destroy", "ek_batch_set_stream", "ek_batch_step_async",
+           "ek_batch_step", "ek_batch_sync", "ek_batch_tune", "ek_batch_config", "ek_batch_size",
+           "ek_batch_last_error"]
 
 
 class EKError(RuntimeError):
@@ -111,9 +114,22 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ek_poisson_solve_static.argtypes = [vp, vp, ip, ip, ip, dp, vp]
     lib.ek_kernel_launches.argtypes = [vp]
     lib.ek_kernel_launches.restype = ctypes.c_longlong
+    lib.ek_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
+    lib.ek_batch_destroy.argtypes = [vp]
+    lib.ek_batch_set_stream.argtypes = [vp, vp]
+    lib.ek_batch_step_async.argtypes = [vp, ip]
+    lib.ek_batch_step.argtypes = [vp, ip]
+    lib.ek_batch_sync.argtypes = [vp]
+    lib.ek_batch_tune.argtypes = [vp, ip, ctypes.POINTER(dp)]
+    lib.ek_batch_config.argtypes = [vp, ctypes.POINTER(ip)]
+    lib.ek_batch_size.argtypes = [vp]
+    lib.ek_batch_size.restype = ip
+    lib.ek_batch_last_error.argtypes = [vp]
+    lib.ek_batch_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("ek_num_particles", "ek_last_error", "ek_lattice_dirs",
-                        "ek_poisson_scratch_bytes", "ek_kernel_launches"):
+                        "ek_poisson_scratch_bytes", "ek_kernel_launches", "ek_batch_size",
+                        "ek_batch_last_error"):
             getattr(lib, name).restype = ip
     _lib = lib
     return lib
@@ -302,3 +318,60 @@ def poisson_solve_static(q, phi, shape, bjerrum, stream=None):
                                      nx, ny, nz, float(bjerrum), ctypes.c_void_p(int(h)))
     if st != 0:
         raise EKError(st, "ek_poisson_solve_static failed (box too large for the fixed scratch?)")
+
+
+class EKBatch:
+    """Many EKSystem objects advanced together, one CUDA graph launch per step
+    of all of them (see ek_batch_* in include/ek.h).  The systems must outlive
+    the batch; call sync() before reading a system or stepping it alone."""
+
+    def __init__(self, systems):
+        self.lib = load_library()
+        self.systems = list(systems)
+        arr = (ctypes.c_void_p * len(self.systems))(*[s.ctx.value for s in self.systems])
+        self.ptr = ctypes.c_void_p()
+        st = self.lib.ek_batch_create(arr, len(self.systems), ctypes.byref(self.ptr))
+        if st != 0:
+            raise EKError(st, "ek_batch_create failed")
+
+    def _check(self, st):
+        if st != 0:
+            raise EKError(st, self.lib.ek_batch_last_error(self.ptr).decode())
+
+    def step(self, n=1):
+        self._check(self.lib.ek_batch_step(self.ptr, int(n)))
+
+    def step_async(self, n=1):
+        self._check(self.lib.ek_batch_step_async(self.ptr, int(n)))
+
+    def sync(self):
+        self._check(self.lib.ek_batch_sync(self.ptr))
+
+    def set_stream(self, stream):
+        h = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.ek_batch_set_stream(self.ptr, ctypes.c_void_p(int(h))))
+
+    def tune(self, trial_steps=2):
+        """Run the autotuner; returns (config dict, ms per batch step)."""
+        best = ctypes.c_double(0.0)
+        self._check(self.lib.ek_batch_tune(self.ptr, int(trial_steps), ctypes.byref(best)))
+        return self.config(), best.value
+
+    def config(self):
+        cfg = (ctypes.c_int * 3)()
+        self._check(self.lib.ek_batch_config(self.ptr, cfg))
+        return {"branches": cfg[0], "planes_per_block": cfg[1], "particle_chain_beside_s3": bool(cfg[2])}
+
+    def __len__(self):
+        return self.lib.ek_batch_size(self.ptr)
+
+    def close(self):
+        if self.ptr:
+            self.lib.ek_batch_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

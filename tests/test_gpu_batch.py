@@ -1,0 +1,82 @@
+"""Batched ensemble: systems of different box sizes, salts, fields and
+particles advanced together by one graph launch per step must end where the
+same systems stepped one by one end, and the autotuner's trials are real,
+conserving steps."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+FP32 = 16
+
+
+def make(ek, w, flags):
+    s = ek.EKSystem(w["shape"], nu=w["nu"], rho0=w["rho0"], bjerrum=w["bjerrum"],
+                    valence=w["valence"], D=w["D"], bulk=w["bulk"], flags=flags)
+    for p in w["particles"]:
+        s.add_particle(p["pos"], radius=p["radius"], charge=p["charge"], rho_p=w["rho_p"])
+    s.set_field(ek.FIELD_E_EXT, np.array(w["E"], dtype=np.float64))
+    return s
+
+
+def ensemble():
+    # small boxes (edges 16..32) so that the spheres of R <= 4 fit (2R + 6 <= edge)
+    return workloads.batch_ensemble(6, seed=77, edges=(16, 24, 32), radius=(2.5, 4.0),
+                                    charge=(-30.0, -10.0), bulk=(1e-3, 1e-2))
+
+
+def state(ek, s):
+    out = {k: s.get_fields(ek.FIELD_SPECIES, k) for k in range(2)}
+    out["f"] = s.get_fields(ek.FIELD_POPULATIONS)
+    out["phi"] = s.get_fields(ek.FIELD_PHI)
+    out["owner"] = s.get_fields(ek.FIELD_OWNER)
+    p = s.get_particles()[0]
+    out["pos"] = np.array(p["pos"])
+    out["vel"] = np.array(p["vel"])
+    return out
+
+
+def test_batch_matches_systems_stepped_alone(gpu_lib):
+    ek = gpu_lib
+    ws = ensemble()
+    # five FP32-form systems and one FP64-form system in the same batch
+    flags = [ek.EK_PV | ek.EK_NEUTRALIZE | (FP32 if i < 5 else 0) for i in range(len(ws))]
+    batched = [make(ek, w, f) for w, f in zip(ws, flags)]
+    alone = [make(ek, w, f) for w, f in zip(ws, flags)]
+    b = ek.EKBatch(batched)
+    assert len(b) == len(ws)
+    b.step(3)
+    b.step(4)  # odd total: both ping-pong parities captured and replayed
+    for s in alone:
+        s.step(7)
+    for i, (sb, sa) in enumerate(zip(batched, alone)):
+        x, y = state(ek, sb), state(ek, sa)
+        assert np.array_equal(x["owner"], y["owner"]), i
+        for key in x:
+            scale = max(np.max(np.abs(y[key])), 1e-300)
+            assert np.max(np.abs(x[key] - y[key])) <= 1e-12 * scale, (i, key)
+        if flags[i] & FP32:
+            for k in range(2):  # int units: the same arithmetic gives the same integers
+                assert np.array_equal(x[k], y[k]), (i, k)
+    assert sum(s.kernel_launches() for s in batched) == sum(s.kernel_launches() for s in alone)
+    b.close()
+
+
+def test_batch_tuner_steps_conserve_and_choose_a_candidate(gpu_lib):
+    ek = gpu_lib
+    ws = ensemble()
+    systems = [make(ek, w, ek.EK_PV | ek.EK_NEUTRALIZE | FP32) for w in ws]
+    totals = [[s.get_fields(ek.FIELD_SPECIES, k).sum() for k in range(2)] for s in systems]
+    b = ek.EKBatch(systems)
+    cfg, ms = b.tune(1)
+    assert cfg["branches"] in (len(ws), 8, 16, 32, 64) and cfg["planes_per_block"] in (2, 4, 8)
+    assert ms > 0.0
+    b.step(5)
+    for s, t in zip(systems, totals):
+        for k in range(2):
+            assert s.get_fields(ek.FIELD_SPECIES, k).sum() == t[k]
+        p = s.get_particles()[0]
+        assert np.all(np.isfinite(p["pos"])) and np.all(np.isfinite(p["vel"]))
+    b.close()

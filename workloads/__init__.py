@@ -12,8 +12,13 @@ Workloads (lattice units, k_B T = e = 1):
   many    256^3, 64 spheres R=5 at seeded non-overlapping positions, Z in
           U[-150,-50], 3 species (z=+1,-1,+2; D=0.2,0.3,0.15), E=0.005.
   large   512^3, 1000 spheres R=6, Z=-200, 2 species bulk 5e-4, E=0.002.
+  batch_ensemble  256 independent boxes, edges from {32, 48, 64} per axis, one
+          sphere R in U[3, 6], Z in U[-100, -20], salt log-uniform 1e-4..1e-2,
+          E log-uniform 1e-3..1e-2 (a mobility sweep).
 """
 from __future__ import annotations
+
+import math
 
 MASK64 = (1 << 64) - 1
 SEED = 1607
@@ -105,6 +110,27 @@ def workload(name: str, seed: int = SEED):
     return dict(name=name, shape=(n, n, n), nu=1.0 / 6.0, rho0=1.0, bjerrum=0.7,
                 valence=val, D=D, bulk=bulk, E=(E, 0.0, 0.0), particles=parts,
                 rho_p=2.0)
+
+
+def batch_ensemble(nsys: int = 256, seed: int = SEED, edges=(32, 48, 64), radius=(3.0, 6.0),
+                   charge=(-100.0, -20.0), bulk=(1e-4, 1e-2), field=(1e-3, 1e-2)):
+    """Independent systems of a mobility sweep: box edges drawn per axis from
+    `edges`, one sphere of radius U(radius) and charge U(charge) at a uniform
+    position, salt (both species) log-uniform in `bulk`, field along x
+    log-uniform in `field`; two species z = +-1, D = 0.3, l_B = 0.7."""
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(nsys):
+        shape = tuple(edges[min(int(rng.uniform() * len(edges)), len(edges) - 1)] for _ in range(3))
+        R = rng.uniform_range(radius[0], radius[1])
+        Z = rng.uniform_range(charge[0], charge[1])
+        b = math.exp(rng.uniform_range(math.log(bulk[0]), math.log(bulk[1])))
+        E = math.exp(rng.uniform_range(math.log(field[0]), math.log(field[1])))
+        pos = [rng.uniform_range(0.0, float(n)) for n in shape]
+        out.append(dict(name="batch", shape=shape, nu=1.0 / 6.0, rho0=1.0, bjerrum=0.7,
+                        valence=(1, -1), D=(0.3, 0.3), bulk=(b, b), E=(E, 0.0, 0.0),
+                        particles=[dict(pos=pos, radius=R, charge=Z)], rho_p=2.0))
+    return out
 
 
 def small_case(n=(16, 16, 16), radius=3.0, charge=-20.0, nparticles=1, seed=SEED,
