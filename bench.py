@@ -206,6 +206,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble measurement")
     args = ap.parse_args()
     import workloads
     w = workloads.workload("single")
@@ -272,6 +273,7 @@ def main():
     r32 = measure(True)
     r64 = measure(False)
     s = r32["system"]
+    rb = None if args.no_batch else measure_batch(ek, torch, args, barrier, max_over_ranks)
 
     # ---- end to end through the public API with host buffers (FP32 form) ----
     # every step: the field E goes host -> device from pinned memory, the step
@@ -334,6 +336,8 @@ def main():
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
     }
+    if rb is not None:
+        line["batched_form"] = rb
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, done, dt = time_oracle(w, 3, budget_s=20.0, warmup=0)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
@@ -344,6 +348,55 @@ def main():
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def measure_batch(ek, torch, args, barrier, max_over_ranks):
+    """The batched ensemble (256 boxes with edges from {32, 48, 64}, one sphere
+    each, FP32 form): autotuned, then timed with CUDA events on the batch
+    stream; beside it the same systems stepped one after another."""
+    import workloads
+    ws_ = workloads.batch_ensemble(256)
+    nodes = sum(w["shape"][0] * w["shape"][1] * w["shape"][2] for w in ws_)
+    systems = [build_system(ek, w, True) for w in ws_]
+    stream = torch.cuda.Stream()
+    b = ek.EKBatch(systems)
+    b.set_stream(stream)
+    cfg, tuned_ms = b.tune(2)
+    b.step(2)
+    steps = max(3, min(args.steps, 20))
+    barrier()
+    launches0 = sum(s.kernel_launches() for s in systems)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.step_async(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    b.sync()
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    launches = sum(s.kernel_launches() for s in systems) - launches0
+    # the same systems, one ek_step after another on one stream (no batching)
+    for sy in systems:
+        sy.set_stream(stream)
+    seq_steps = 3
+    ev0.record(stream)
+    for _ in range(seq_steps):
+        for sy in systems:
+            sy.step_async(1)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_seq = max_over_ranks(ev0.elapsed_time(ev1))
+    b.close()
+    for sy in systems:
+        sy.close()
+    return {"value": round(nodes * steps / (ms / 1e3) / 1e6, 3), "unit": "MLUPS",
+            "ms_per_step": round(ms / steps, 4), "steps": steps, "systems": len(ws_),
+            "nodes": nodes, "gpu_launches": launches, "tuned": cfg,
+            "tuner_ms_per_step": round(tuned_ms, 4),
+            "one_by_one": {"value": round(nodes * seq_steps / (ms_seq / 1e3) / 1e6, 3),
+                           "ms_per_step": round(ms_seq / seq_steps, 4)},
+            "config": "256 boxes, edges {32,48,64} per axis, one sphere R U[3,6], Z U[-min(100,12R),-20], "
+                      "salt log-U[1e-4,1e-2], E log-U[1e-3,1e-2], FP32 form, one graph launch per step"}
 
 
 def ctypes_sizeof_particle(ek):
