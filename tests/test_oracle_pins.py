@@ -576,3 +576,38 @@ def test_neutral_box_with_net_charge_gains_QE():
     P0 = total()
     o.step(10)
     assert np.allclose(total() - P0, 10 * Q * o.E, rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Poisson-Boltzmann slit: counter-ions only between two charged walls
+# --------------------------------------------------------------------------
+def test_poisson_boltzmann_slit_counterions_only():
+    """Equilibrium of the full step (fluxes of Eqs. 13/15, Poisson Eq. 3 with
+    4 pi l_B, wall charge, zero flux at the walls) against the closed-form
+    solution of the Poisson-Boltzmann equation for counter-ions alone between
+    two planes of charge density -sigma (k_B T = e = 1, z = +1):
+        rho(z) = rho_m / cos^2(alpha (z - z_c)),  alpha^2 = 2 pi l_B rho_m,
+        sigma = (rho_m / alpha) tan(alpha d)     (neutrality),
+    with the fluid cells filling [z_c - d, z_c + d].  A wrong migration sign
+    pushes the ions to the midplane, a wrong 4 pi l_B or z/2 changes alpha or
+    the exponent of the Boltzmann factor; the discretisation error is ~0.2%."""
+    nx = ny = 4
+    nz = 34                     # walls at z = 0 and 33, fluid cells 1..32: d = 16
+    lB, d = 0.7, 16.0
+    alpha = 1.0 / 16.0
+    rho_m = alpha ** 2 / (2.0 * math.pi * lB)
+    sigma = rho_m * math.tan(alpha * d) / alpha
+    o = EKOracle(nx, ny, nz, bjerrum=lB, valence=(1,), D=(0.3,), bulk=(0.0,), flags=O.NEUTRALIZE)
+    walls = np.zeros((nz, ny, nx), bool)
+    walls[0] = walls[nz - 1] = True
+    q = np.where(walls, -sigma, 0.0)
+    o.set_wall_charge(q)
+    o.set_walls(walls)          # fills the counter-ions uniformly (neutral box)
+    o.step(1200)
+    z = np.arange(1, nz - 1) - 0.5 * (nz - 1)
+    expect = rho_m / np.cos(alpha * z) ** 2
+    prof = o.rho[0][1:nz - 1]
+    assert np.allclose(prof, prof[:, :1, :1], rtol=0, atol=1e-15)  # laterally uniform
+    assert np.max(np.abs(prof[:, 0, 0] / expect - 1.0)) < 0.01
+    # the walls attract the counter-ions: 3.1x the midplane density next to them
+    assert prof[0, 0, 0] / prof[16, 0, 0] > 3.0
