@@ -77,6 +77,11 @@ struct DevParticle {
   int ulo[3], uhi[3];  // union of the previous and current boxes (transitions)
   int elo[3], ehi[3];  // box widened by ceil(R) + FORCE_MARGIN (solute force region)
   int kelo[3], kehi[3];  // the widened box whose assignment keys S4 set (cleared after)
+  // float forms for the octree pre-test, set with the box: integer part and
+  // fraction of the centre, R^2 and the pre-test margin
+  int ipos[3];
+  float fpos[3];
+  float r2f, psimargin;
 };
 
 // cells added to ceil(R) around a particle's box for the region whose solute

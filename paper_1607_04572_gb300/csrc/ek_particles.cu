@@ -67,10 +67,12 @@ __device__ __forceinline__ int classify(double cx, double cy, double cz, double 
 constexpr int PSI_DEPTH = 4;
 
 // Single-precision pre-test of classify().  (ox, oy, oz) is the cube centre
-// relative to the sphere centre, rounded to float and accumulated over at most
-// 4 levels of dyadic offsets (absolute error per component below
-// 6 * 2^-24 (R + 2)); the float squared distances of the farthest corner and
-// of the closest point are then within 3e-6 (R + 2)^2 of the exact ones, so
+// relative to the sphere centre in float: the node's integer offset from the
+// centre's integer part minus the float fraction of the centre (two roundings),
+// then accumulated over at most 4 levels of dyadic offsets (absolute error per
+// component below 7 * 2^-24 (R + 2)); the float squared distances of the
+// farthest corner and of the closest point are then within 3.5e-6 (R + 2)^2 of
+// the exact ones, so
 // whenever they are more than `margin` = 6e-6 (R + 2)^2 away from R^2 the FP64
 // decision is already known.  Returns -1 when the exact test is needed.
 __device__ __forceinline__ int classify_f32(float ox, float oy, float oz, float h, float R2,
@@ -93,11 +95,12 @@ __device__ __forceinline__ int classify_f32(float ox, float oy, float oz, float 
 // into 8 sub-cells, each classified as completely inside or completely
 // outside; undecided ones are split again, down to depth 4 (edge 1/16), where
 // an undecided cube counts half.  Level 0 (the cell itself) is decided by
-// k_claim; cells still undecided there go to k_psi_surface, where one warp
-// walks the levels breadth first: the 8^l sub-cubes of a level are spread over
-// the lanes, and the undecided ones are compacted (ballot) into the next
-// level's list.  Volumes are counted in units of 1/8192 (half a level-4
-// cube), so the sum is an exact integer in any order.
+// k_claim; cells still undecided there go to k_psi_surface, where eight warps
+// share a cell, one per level-1 octant: a warp walks its octant's levels
+// breadth first, the sub-cubes of a level spread over the lanes and the
+// undecided ones compacted (ballot) into the next level's list.  Volumes are
+// counted in units of 1/8192 (half a level-4 cube), so the sums are exact in
+// any order.
 constexpr int PSI_UNITS = 8192;
 
 // relative (float) and exact (double) centre of sub-cube `path` at level l of
@@ -501,7 +504,12 @@ __device__ void box_update_one(DevParticle& P, const double pos[3], const int nn
     const int m = (int)ceil(P.radius) + FORCE_MARGIN;
     P.elo[d] = lo - m;
     P.ehi[d] = hi + m;
+    P.ipos[d] = (int)floor(pos[d]);
+    P.fpos[d] = (float)(pos[d] - (double)P.ipos[d]);
   }
+  const double R2 = __dmul_rn(P.radius, P.radius);
+  P.r2f = (float)R2;
+  P.psimargin = psi_margin(R2);
 }
 
 // Column sums of a row-major table (nrow rows of `stride` doubles; columns
@@ -667,10 +675,10 @@ __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
       const int old = atomicCAS(a.owner + n, FLUID, p);
       if (old != FLUID) atomicOr(a.status, ST_OVERLAP);
     }
-    const float ox = (float)((double)X - P.pos[0]);
-    const float oy = (float)((double)Y - P.pos[1]);
-    const float oz = (float)((double)Z - P.pos[2]);
-    int s0 = classify_f32(ox, oy, oz, 0.5f, (float)R2, psi_margin(R2));
+    const float ox = __fsub_rn((float)(X - P.ipos[0]), P.fpos[0]);
+    const float oy = __fsub_rn((float)(Y - P.ipos[1]), P.fpos[1]);
+    const float oz = __fsub_rn((float)(Z - P.ipos[2]), P.fpos[2]);
+    int s0 = classify_f32(ox, oy, oz, 0.5f, P.r2f, P.psimargin);
     if (s0 < 0) s0 = classify((double)X, (double)Y, (double)Z, 0.5, P.pos, R2);
     if (s0 == CUBE_IN) {
       ps = 1.0;
@@ -703,24 +711,41 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int count = min(*a.surf_count, a.surf_cap);
-  for (int e = blockIdx.x * PSI_WARPS + wid; e < count; e += gridDim.x * PSI_WARPS) {
-    const int2 pc = a.surf[e];
+  // one warp per (surface cell, level-1 octant): eight warps share a cell
+  for (int e = blockIdx.x * PSI_WARPS + wid; e < 8 * count; e += gridDim.x * PSI_WARPS) {
+    const int2 pc = a.surf[e >> 3];
+    const int oct = e & 7;
     DevParticle& P = a.parts[pc.x];
     int X, Y, Z;
     box_coord(pc.y, P.lo, P.hi, X, Y, Z);
-    const double R2 = __dmul_rn(P.radius, P.radius);
-    const float R2f = (float)R2, margin = psi_margin(R2);
-    const float ox = (float)((double)X - P.pos[0]);
-    const float oy = (float)((double)Y - P.pos[1]);
-    const float oz = (float)((double)Z - P.pos[2]);
+    const float R2f = P.r2f, margin = P.psimargin;
+    const float ox = __fsub_rn((float)(X - P.ipos[0]), P.fpos[0]);
+    const float oy = __fsub_rn((float)(Y - P.ipos[1]), P.fpos[1]);
+    const float oz = __fsub_rn((float)(Z - P.ipos[2]), P.fpos[2]);
     unsigned short* cur = queue[wid][0];
     unsigned short* nxt = queue[wid][1];
     unsigned short* fb = fbq[wid];
-    if (lane == 0) cur[0] = 0;
-    __syncwarp();
-    int qlen = 1;
+    int qlen = 0;
     int units = 0;
-    for (int l = 1; l <= PSI_DEPTH && qlen > 0; ++l) {
+    {
+      // level 1: this warp's octant (every lane takes the same decision)
+      float cx, cy, cz;
+      subcube_centre_f(oct, 1, ox, oy, oz, cx, cy, cz);
+      int st = classify_f32(cx, cy, cz, 0.25f, R2f, margin);
+      if (st < 0) {
+        double ex, ey, ez;
+        subcube_centre_d(oct, 1, (double)X, (double)Y, (double)Z, ex, ey, ez);
+        st = classify(ex, ey, ez, 0.25, P.pos, __dmul_rn(P.radius, P.radius));
+      }
+      if (st == CUBE_IN) {
+        if (lane == 0) units = 2 << (3 * (PSI_DEPTH - 1));
+      } else if (st == CUBE_UNDECIDED) {
+        if (lane == 0) cur[0] = (unsigned short)oct;
+        qlen = 1;
+      }
+    }
+    __syncwarp();
+    for (int l = 2; l <= PSI_DEPTH && qlen > 0; ++l) {
       const int ntask = qlen * 8;
       const float h = ldexpf(1.0f, -(l + 1));
       const int in_units = 2 << (3 * (PSI_DEPTH - l));
@@ -757,7 +782,7 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
             path2 = fb[nfb - take + lane];
             double ex, ey, ez;
             subcube_centre_d(path2, l, (double)X, (double)Y, (double)Z, ex, ey, ez);
-            const int st = classify(ex, ey, ez, ldexp(1.0, -(l + 1)), P.pos, R2);
+            const int st = classify(ex, ey, ez, ldexp(1.0, -(l + 1)), P.pos, __dmul_rn(P.radius, P.radius));
             if (st == CUBE_IN) units += in_units;
             else if (st == CUBE_UNDECIDED) {
               if (l == PSI_DEPTH) units += 1;
@@ -779,10 +804,11 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
     }
     for (int o = 16; o > 0; o >>= 1) units += __shfl_xor_sync(0xffffffffu, units, o);
     if (lane == 0 && units > 0) {
-      const double ps = (double)units / (double)PSI_UNITS;  // exact: a power of 2
+      // dyadic with 13 fraction bits: every sum below is exact, in any order
+      const double ps = (double)units / (double)PSI_UNITS;
       const long long n = node_of(X, Y, Z, a.g);
-      a.psibox[(long long)pc.x * a.boxmax + pc.y] = ps;
-      real_add<FM>(a.psi, n, ps);  // dyadic with 13 fraction bits: exact in float too
+      atomicAdd(a.psibox + (long long)pc.x * a.boxmax + pc.y, ps);
+      real_add<FM>(a.psi, n, ps);
       atomicAdd(&P.psisum, ps);
     }
     __syncwarp();
@@ -1016,7 +1042,7 @@ cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s, int pa
   }
   cudaMemsetAsync(a.surf_count, 0, sizeof(int), s);
   k_claim<FM><<<dim3(a.P, bchunks), PT, 0, s>>>(a);
-  k_psi_surface<FM><<<4 * 152, 32 * PSI_WARPS, 0, s>>>(a);
+  k_psi_surface<FM><<<16 * 152, 32 * PSI_WARPS, 0, s>>>(a);
   k_charge_scatter<FM><<<dim3(a.P, bchunks), PT, 0, s>>>(a);
   if (transitions && (parts & 2)) {
     k_transitions<FM><<<dim3(a.P, uchunks), PT, 0, s>>>(a);

@@ -414,8 +414,10 @@ __device__ __forceinline__ void load_twiddles(float2* tw, const AxisPlan& P) {
   for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = P.tw32[k];
 }
 
-// X pass, forward, rows r0 = 2p, r1 = 2p + 1 packed as a + i b (as k_fft_x_fwd)
-template <int NX>
+// X pass, forward, rows r0 = 2p, r1 = 2p + 1 packed as a + i b (as k_fft_x_fwd).
+// KMAJOR: the half spectrum is stored kx-major, S[kx][z][y], so that each
+// (y, z) plane is contiguous for k_fast_yzplane; else S[z][y][kx].
+template <int NX, bool KMAJOR>
 __global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
   constexpr int PPC = FAST_XELEMS / NX > 0 ? FAST_XELEMS / NX : 1;  // row pairs per CTA
   constexpr int LS = fpad(NX);
@@ -440,15 +442,21 @@ __global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
   const float2* res = fast_fft<NX, false>(buf[0], buf[1], PPC, tw);
   constexpr int NXH = NX / 2 + 1;
   for (int t = threadIdx.x; t < PPC * NXH; t += FAST_XT) {
-    const int l = t / NXH, k = t % NXH;
+    // kx-major: consecutive threads take consecutive rows of one kx
+    const int l = KMAJOR ? t % PPC : t / NXH, k = KMAJOR ? t / PPC : t % NXH;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
     if (r0 >= nrows) continue;
     const float2 Zk = res[l * LS + fpad(k)];
     const float2 Zm = res[l * LS + fpad(k == 0 ? 0 : NX - k)];
     const float2 A = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
     const float2 B = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
-    a.S[(long long)r0 * NXH + k] = A;
-    if (r1 < nrows) a.S[(long long)r1 * NXH + k] = B;
+    if (KMAJOR) {
+      a.S[(long long)k * nrows + r0] = A;
+      if (r1 < nrows) a.S[(long long)k * nrows + r1] = B;
+    } else {
+      a.S[(long long)r0 * NXH + k] = A;
+      if (r1 < nrows) a.S[(long long)r1 * NXH + k] = B;
+    }
   }
 }
 
@@ -499,7 +507,7 @@ __global__ void __launch_bounds__(FAST_T) k_fast_yz(PassArgs<float> a, int tx) {
 }
 
 // X pass, inverse (complex-to-real), two rows per complex transform (as k_fft_x_inv)
-template <int NX>
+template <int NX, bool KMAJOR>
 __global__ void __launch_bounds__(FAST_IT) k_fast_x_inv(PassArgs<float> a) {
   constexpr int PPC = FAST_IELEMS / NX > 0 ? FAST_IELEMS / NX : 1;
   constexpr int LS = fpad(NX);
@@ -511,13 +519,18 @@ __global__ void __launch_bounds__(FAST_IT) k_fast_x_inv(PassArgs<float> a) {
   const int p0 = blockIdx.x * PPC;
 #pragma unroll 8
   for (int t = threadIdx.x; t < PPC * NX; t += FAST_IT) {
-    const int l = t / NX, k = t % NX;
+    const int l = KMAJOR ? t % PPC : t / NX, k = KMAJOR ? t / PPC : t % NX;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
     float2 A = make_float2(0.0f, 0.0f), B = make_float2(0.0f, 0.0f);
     const bool upper = k > NX / 2;
     const int kk = upper ? NX - k : k;
-    if (r0 < nrows) A = a.S[(long long)r0 * NXH + kk];
-    if (r1 < nrows) B = a.S[(long long)r1 * NXH + kk];
+    if (KMAJOR) {
+      if (r0 < nrows) A = a.S[(long long)kk * nrows + r0];
+      if (r1 < nrows) B = a.S[(long long)kk * nrows + r1];
+    } else {
+      if (r0 < nrows) A = a.S[(long long)r0 * NXH + kk];
+      if (r1 < nrows) B = a.S[(long long)r1 * NXH + kk];
+    }
     if (upper) {
       A.y = -A.y;
       B.y = -B.y;
@@ -536,14 +549,18 @@ __global__ void __launch_bounds__(FAST_IT) k_fast_x_inv(PassArgs<float> a) {
 }
 
 template <int NX>
-void launch_fast_x(PassArgs<float>& a, bool inverse, cudaStream_t s) {
+void launch_fast_x(PassArgs<float>& a, bool inverse, bool kmajor, cudaStream_t s) {
   const int npairs = (a.ny * a.nz + 1) / 2;
   if (inverse) {
     constexpr int ppc = FAST_IELEMS / NX > 0 ? FAST_IELEMS / NX : 1;
-    k_fast_x_inv<NX><<<(unsigned)((npairs + ppc - 1) / ppc), FAST_IT, 0, s>>>(a);
+    const unsigned g = (unsigned)((npairs + ppc - 1) / ppc);
+    if (kmajor) k_fast_x_inv<NX, true><<<g, FAST_IT, 0, s>>>(a);
+    else k_fast_x_inv<NX, false><<<g, FAST_IT, 0, s>>>(a);
   } else {
     constexpr int ppc = FAST_XELEMS / NX > 0 ? FAST_XELEMS / NX : 1;
-    k_fast_x_fwd<NX><<<(unsigned)((npairs + ppc - 1) / ppc), FAST_XT, 0, s>>>(a);
+    const unsigned g = (unsigned)((npairs + ppc - 1) / ppc);
+    if (kmajor) k_fast_x_fwd<NX, true><<<g, FAST_XT, 0, s>>>(a);
+    else k_fast_x_fwd<NX, false><<<g, FAST_XT, 0, s>>>(a);
   }
 }
 
@@ -568,14 +585,159 @@ void launch_fast_yz(PassArgs<float>& a, int n, cudaStream_t s) {
   }
 }
 
-void launch_fast_x_any(PassArgs<float>& a, bool inverse, cudaStream_t s) {
+void launch_fast_x_any(PassArgs<float>& a, bool inverse, bool kmajor, cudaStream_t s) {
   switch (a.nx) {
-    case 32: launch_fast_x<32>(a, inverse, s); break;
-    case 64: launch_fast_x<64>(a, inverse, s); break;
-    case 128: launch_fast_x<128>(a, inverse, s); break;
-    case 256: launch_fast_x<256>(a, inverse, s); break;
-    default: launch_fast_x<512>(a, inverse, s); break;
+    case 32: launch_fast_x<32>(a, inverse, kmajor, s); break;
+    case 64: launch_fast_x<64>(a, inverse, kmajor, s); break;
+    case 128: launch_fast_x<128>(a, inverse, kmajor, s); break;
+    case 256: launch_fast_x<256>(a, inverse, kmajor, s); break;
+    default: launch_fast_x<512>(a, inverse, kmajor, s); break;
   }
+}
+
+// ---------------------------------------------------------------------------
+// The y and z passes of one kx plane in one CTA: when a (y, z) plane of the
+// kx-major half spectrum fits in shared memory (edges 32..128), one CTA of
+// 1024 threads loads it (contiguous), transforms along y and z, multiplies by
+// the Green function, transforms back and stores it: three kernels and four
+// round trips through L2 become one.  Each stage runs in place: every thread
+// reads its sub-transforms' elements into registers, the block synchronises,
+// then every thread writes its results.
+// ---------------------------------------------------------------------------
+constexpr int PLANE_T = 1024;
+
+// one in-place Stockham stage of radix R over the lines of the plane.  Along
+// y (ALONG_Y): NLINES = NZ lines of length N = NY, element (line, i) at
+// line * LSY + fpad(i); along z: NY lines of length NZ, element (line, i) at
+// i * LSY + fpad(line), consecutive threads on consecutive lines.
+template <int N, int NLINES, int NS, int R, bool INV, bool ALONG_Y, int LSY>
+__device__ __forceinline__ void plane_stage(float2* pl, const float2* tw) {
+  constexpr int M = N / R;
+  constexpr int ITEMS = NLINES * M;
+  constexpr int PER = (ITEMS + PLANE_T - 1) / PLANE_T;
+  float2 v[PER][R];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int t = threadIdx.x + q * PLANE_T;
+    if (t < ITEMS) {
+      const int line = ALONG_Y ? t / M : t % NLINES, j = ALONG_Y ? t % M : t / NLINES;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = j + r * M;
+        v[q][r] = ALONG_Y ? pl[line * LSY + fpad(i)] : pl[i * LSY + fpad(line)];
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int t = threadIdx.x + q * PLANE_T;
+    if (t < ITEMS) {
+      const int line = ALONG_Y ? t / M : t % NLINES, j = ALONG_Y ? t % M : t / NLINES;
+      const int k = j % NS;
+      if constexpr (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const float2 w = tw[r * k * (N / (NS * R))];
+          v[q][r] = INV ? cmulconj(v[q][r], w) : cmul(v[q][r], w);
+        }
+      }
+      dft_reg<R, INV>(v[q]);
+      const int base = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = base + r * NS;
+        if (ALONG_Y) pl[line * LSY + fpad(i)] = v[q][r];
+        else pl[i * LSY + fpad(line)] = v[q][r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int N, int NLINES, bool INV, bool ALONG_Y, int LSY>
+__device__ __forceinline__ void plane_fft(float2* pl, const float2* tw) {
+  constexpr int R0 = fast_radix(N, 0), R1 = fast_radix(N, 1), R2 = fast_radix(N, 2);
+  plane_stage<N, NLINES, 1, R0, INV, ALONG_Y, LSY>(pl, tw);
+  if constexpr (R1 != 0) plane_stage<N, NLINES, R0, R1, INV, ALONG_Y, LSY>(pl, tw);
+  if constexpr (R2 != 0) plane_stage<N, NLINES, R0 * R1, R2, INV, ALONG_Y, LSY>(pl, tw);
+}
+
+template <int NY, int NZ>
+__global__ void __launch_bounds__(PLANE_T, 1) k_fast_yzplane(PassArgs<float> a) {
+  constexpr int LSY = fpad(NY);
+  extern __shared__ __align__(16) unsigned char plane_smem[];
+  float2* pl = reinterpret_cast<float2*>(plane_smem);  // [z][y], rows padded
+  float2* twy = pl + NZ * LSY;
+  float2* twz = twy + NY;
+  const int kx = blockIdx.x;
+  for (int k = threadIdx.x; k < NY; k += PLANE_T) twy[k] = a.ay.tw32[k];
+  for (int k = threadIdx.x; k < NZ; k += PLANE_T) twz[k] = a.az.tw32[k];
+  const float2* src = a.S + (long long)kx * NY * NZ;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < NY * NZ; e += PLANE_T) pl[(e / NY) * LSY + fpad(e % NY)] = src[e];
+  __syncthreads();
+  plane_fft<NY, NZ, false, true, LSY>(pl, twy);
+  plane_fft<NZ, NY, false, false, LSY>(pl, twz);
+  // Green function of the 7-point Laplacian
+  const float lx = lambda_of(a.ax, kx, 0.0f);
+  for (int e = threadIdx.x; e < NY * NZ; e += PLANE_T) {
+    const int z = e / NY, y = e % NY;
+    const float lam = lx + lambda_of(a.ay, y, 0.0f) + lambda_of(a.az, z, 0.0f);
+    const float g = (kx == 0 && y == 0 && z == 0) ? 0.0f : a.green_scale / lam;
+    float2& v = pl[z * LSY + fpad(y)];
+    v = make_float2(v.x * g, v.y * g);
+  }
+  __syncthreads();
+  plane_fft<NZ, NY, true, false, LSY>(pl, twz);
+  plane_fft<NY, NZ, true, true, LSY>(pl, twy);
+  float2* dst = a.S + (long long)kx * NY * NZ;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < NY * NZ; e += PLANE_T) dst[e] = pl[(e / NY) * LSY + fpad(e % NY)];
+}
+
+template <int NY, int NZ>
+constexpr size_t plane_smem_bytes() {
+  return ((size_t)NZ * fpad(NY) + NY + NZ) * sizeof(float2);
+}
+
+// the plane kernels that exist: NY, NZ in {32, 64, 128}
+inline bool plane_edge(int n) { return n == 32 || n == 64 || n == 128; }
+
+template <int NY, int NZ>
+cudaError_t launch_plane_nn(PassArgs<float>& a, cudaStream_t s) {
+  k_fast_yzplane<NY, NZ><<<(unsigned)a.nxh, PLANE_T, plane_smem_bytes<NY, NZ>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NY>
+cudaError_t launch_plane_n(PassArgs<float>& a, cudaStream_t s) {
+  switch (a.nz) {
+    case 32: return launch_plane_nn<NY, 32>(a, s);
+    case 64: return launch_plane_nn<NY, 64>(a, s);
+    default: return launch_plane_nn<NY, 128>(a, s);
+  }
+}
+
+cudaError_t launch_plane(PassArgs<float>& a, cudaStream_t s) {
+  switch (a.ny) {
+    case 32: return launch_plane_n<32>(a, s);
+    case 64: return launch_plane_n<64>(a, s);
+    default: return launch_plane_n<128>(a, s);
+  }
+}
+
+template <int NY, int NZ>
+cudaError_t plane_attr_nn() {
+  return cudaFuncSetAttribute(k_fast_yzplane<NY, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)plane_smem_bytes<NY, NZ>());
+}
+template <int NY>
+cudaError_t plane_attr_n() {
+  cudaError_t e = plane_attr_nn<NY, 32>();
+  if (e == cudaSuccess) e = plane_attr_nn<NY, 64>();
+  if (e == cudaSuccess) e = plane_attr_nn<NY, 128>();
+  return e;
 }
 
 template <class FM>
@@ -638,6 +800,17 @@ size_t poisson_spectrum_bytes(int nx, int ny, int nz) {
 
 cudaError_t poisson_plan_create(PoissonPlan& p, int nx, int ny, int nz, std::string& err) {
   p = PoissonPlan();
+  // the y-z plane kernels keep a whole plane in shared memory (up to 141 KB);
+  // set once per plan, before any launch or stream capture
+  {
+    cudaError_t e = plane_attr_n<32>();
+    if (e == cudaSuccess) e = plane_attr_n<64>();
+    if (e == cudaSuccess) e = plane_attr_n<128>();
+    if (e != cudaSuccess) {
+      err = "shared-memory size of the plane FFT kernels could not be set";
+      return e;
+    }
+  }
   p.nx = nx;
   p.ny = ny;
   p.nz = nz;
@@ -688,11 +861,17 @@ cudaError_t run_passes(const PoissonPlan& p, PassArgs<R>& a, double bjerrum, cud
   a.green_scale = (R)(4.0 * M_PI * bjerrum / N);
   if constexpr (std::is_same<R, float>::value) {
     if (fast_edge(p.nx) && fast_edge(p.ny) && fast_edge(p.nz)) {
-      launch_fast_x_any(a, false, s);
+      if (plane_edge(p.ny) && plane_edge(p.nz)) {
+        launch_fast_x_any(a, false, true, s);
+        launch_plane(a, s);
+        launch_fast_x_any(a, true, true, s);
+        return cudaGetLastError();
+      }
+      launch_fast_x_any(a, false, false, s);
       launch_fast_yz<1, false>(a, p.ny, s);
       launch_fast_yz<2, false>(a, p.nz, s);
       launch_fast_yz<1, true>(a, p.ny, s);
-      launch_fast_x_any(a, true, s);
+      launch_fast_x_any(a, true, false, s);
       return cudaGetLastError();
     }
   }
