@@ -605,6 +605,18 @@ class EKOracle:
         d = np.where(d < -0.5 * n, d + n, d)
         return d
 
+    @staticmethod
+    def min_image_f32(coord, r, n):
+        """Single-precision offset of integer node coordinates from r, wrapped
+        to the nearest periodic image, in the operations the nearest-surface
+        decision is defined by (see solute_forces)."""
+        ipos = math.floor(r)
+        frac = np.float32(r - ipos)
+        d = (np.asarray(coord) - ipos).astype(np.float32) - frac
+        half, nf = np.float32(0.5 * n), np.float32(n)
+        d = np.where(d > half, d - nf, d)
+        return np.where(d < -half, d + nf, d).astype(np.float32)
+
     def solute_forces(self, fext):
         """Force and torque of the solute on every particle.
 
@@ -646,11 +658,15 @@ class EKOracle:
             dx = self.min_image(Xc.astype(np.float64), p.pos[0], nx)
             dy = self.min_image(Yc.astype(np.float64), p.pos[1], ny)
             dz = self.min_image(Zc.astype(np.float64), p.pos[2], nz)
-            # the nearest-surface decision is taken in IEEE single precision
-            # (squares summed left to right, correctly rounded sqrt); ties go
-            # to the lower index.  The key orders the float distances by
-            # their bit patterns (sign bit flipped, negatives complemented).
-            dxf, dyf, dzf = dx.astype(np.float32), dy.astype(np.float32), dz.astype(np.float32)
+            # the nearest-surface decision is taken in IEEE single precision:
+            # offset = float(node - floor(r_p)) - float(r_p - floor(r_p)),
+            # wrapped to the nearest image in float, squares summed left to
+            # right, correctly rounded sqrt; ties go to the lower index.  The
+            # key orders the float distances by their bit patterns (sign bit
+            # flipped, negatives complemented).
+            dxf = self.min_image_f32(Xc, p.pos[0], nx)
+            dyf = self.min_image_f32(Yc, p.pos[1], ny)
+            dzf = self.min_image_f32(Zc, p.pos[2], nz)
             d2 = dxf * dxf + dyf * dyf + dzf * dzf
             dsurf = np.sqrt(d2) - np.float32(p.radius)
             bits = dsurf.view(np.uint32).astype(np.int64)

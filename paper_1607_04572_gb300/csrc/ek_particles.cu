@@ -234,12 +234,22 @@ __global__ void k_force_assign(PartArgs a) {
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
   if (c >= box_cells(P.elo, P.ehi)) return;
   int X, Y, Z;
-  long long n;
-  double dx, dy, dz;
-  ext_cell(P, c, a.g, X, Y, Z, n, dx, dy, dz);  // a repeated node gets the same key
-  // surface distance in IEEE single precision (the decision's precision),
-  // ordered by its bit pattern; ties go to the lower particle index
-  const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+  box_coord(c, P.elo, P.ehi, X, Y, Z);  // a repeated node gets the same key
+  const int x = wrapi(X, a.g.nx), y = wrapi(Y, a.g.ny), z = wrapi(Z, a.g.nz);
+  const long long n = (long long)x + (long long)a.g.nx * ((long long)y + (long long)a.g.ny * z);
+  // surface distance in IEEE single precision (the decision's precision):
+  // offset = float(node - floor(r_p)) - float fraction of r_p, wrapped to the
+  // nearest image; ordered by its bit pattern, ties to the lower index
+  auto off = [](int v, int ip, float fr, int nn) {
+    const float hn = 0.5f * (float)nn;
+    float d = __fsub_rn((float)(v - ip), fr);
+    if (d > hn) d = __fsub_rn(d, (float)nn);
+    else if (d < -hn) d = __fadd_rn(d, (float)nn);
+    return d;
+  };
+  const float fx = off(x, P.ipos[0], P.fpos[0], a.g.nx);
+  const float fy = off(y, P.ipos[1], P.fpos[1], a.g.ny);
+  const float fz = off(z, P.ipos[2], P.fpos[2], a.g.nz);
   const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)), __fmul_rn(fz, fz));
   const float dsurf = __fsub_rn(__fsqrt_rn(d2), (float)P.radius);
   unsigned bits = __float_as_uint(dsurf);
@@ -706,7 +716,11 @@ constexpr int PSI_WARPS = 4;  // warps per CTA of k_psi_surface
 // double-precision path for a single lane.
 template <class FM>
 __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
-  __shared__ unsigned short queue[PSI_WARPS][2][512];
+  // per warp: the undecided cubes of the current and the next level (paths
+  // and float centres; within one octant a level holds at most 64) and the
+  // paths queued for the exact test
+  __shared__ unsigned short qpath[PSI_WARPS][2][64];
+  __shared__ float3 qcen[PSI_WARPS][2][64];
   __shared__ unsigned short fbq[PSI_WARPS][64];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -722,8 +736,7 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
     const float ox = __fsub_rn((float)(X - P.ipos[0]), P.fpos[0]);
     const float oy = __fsub_rn((float)(Y - P.ipos[1]), P.fpos[1]);
     const float oz = __fsub_rn((float)(Z - P.ipos[2]), P.fpos[2]);
-    unsigned short* cur = queue[wid][0];
-    unsigned short* nxt = queue[wid][1];
+    int cur = 0;
     unsigned short* fb = fbq[wid];
     int qlen = 0;
     int units = 0;
@@ -740,7 +753,10 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
       if (st == CUBE_IN) {
         if (lane == 0) units = 2 << (3 * (PSI_DEPTH - 1));
       } else if (st == CUBE_UNDECIDED) {
-        if (lane == 0) cur[0] = (unsigned short)oct;
+        if (lane == 0) {
+          qpath[wid][0][0] = (unsigned short)oct;
+          qcen[wid][0][0] = make_float3(cx, cy, cz);
+        }
         qlen = 1;
       }
     }
@@ -749,15 +765,22 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
       const int ntask = qlen * 8;
       const float h = ldexpf(1.0f, -(l + 1));
       const int in_units = 2 << (3 * (PSI_DEPTH - l));
+      const int nx = 1 - cur;
       int newlen = 0, nfb = 0;
       for (int t0 = 0; t0 < ntask; t0 += 32) {
         const int t = t0 + lane;
         bool und = false, exact = false;
         int path = 0;
+        float cx = 0.0f, cy = 0.0f, cz = 0.0f;
         if (t < ntask) {
-          path = ((int)cur[t >> 3] << 3) | (t & 7);
-          float cx, cy, cz;
-          subcube_centre_f(path, l, ox, oy, oz, cx, cy, cz);
+          const int bits = t & 7;
+          path = ((int)qpath[wid][cur][t >> 3] << 3) | bits;
+          // the child's centre: the parent's plus or minus h per axis (the same
+          // additions, in the same order, as subcube_centre_f)
+          const float3 c = qcen[wid][cur][t >> 3];
+          cx = __fadd_rn(c.x, (bits & 1) ? h : -h);
+          cy = __fadd_rn(c.y, (bits & 2) ? h : -h);
+          cz = __fadd_rn(c.z, (bits & 4) ? h : -h);
           const int st = classify_f32(cx, cy, cz, h, R2f, margin);
           if (st < 0) exact = true;
           else if (st == CUBE_IN) units += in_units;
@@ -767,7 +790,11 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
           }
         }
         unsigned mask = __ballot_sync(0xffffffffu, und);
-        if (und) nxt[newlen + __popc(mask & lt)] = (unsigned short)path;
+        if (und) {
+          const int slot = newlen + __popc(mask & lt);
+          qpath[wid][nx][slot] = (unsigned short)path;
+          qcen[wid][nx][slot] = make_float3(cx, cy, cz);
+        }
         newlen += __popc(mask);
         mask = __ballot_sync(0xffffffffu, exact);
         if (exact) fb[nfb + __popc(mask & lt)] = (unsigned short)path;
@@ -790,16 +817,20 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
             }
           }
           const unsigned m2 = __ballot_sync(0xffffffffu, und2);
-          if (und2) nxt[newlen + __popc(m2 & lt)] = (unsigned short)path2;
+          if (und2) {
+            const int slot = newlen + __popc(m2 & lt);
+            float fx, fy, fz;
+            subcube_centre_f(path2, l, ox, oy, oz, fx, fy, fz);
+            qpath[wid][nx][slot] = (unsigned short)path2;
+            qcen[wid][nx][slot] = make_float3(fx, fy, fz);
+          }
           newlen += __popc(m2);
           nfb -= take;
           __syncwarp();
         }
       }
       __syncwarp();
-      unsigned short* tmp = cur;
-      cur = nxt;
-      nxt = tmp;
+      cur = nx;
       qlen = newlen;
     }
     for (int o = 16; o > 0; o >>= 1) units += __shfl_xor_sync(0xffffffffu, units, o);
