@@ -80,8 +80,8 @@ struct DevParticle {
   // float forms for the octree pre-test, set with the box: integer part and
   // fraction of the centre, R^2 and the pre-test margin
   int ipos[3];
-  float fpos[3];
-  float r2f, psimargin;
+  float fpos[3], fposlo[3];  // fraction of the centre as a float pair (hi + lo)
+  float r2f, r2lo, psimargin;  // R^2 (the FP64 product) as a float pair
 };
 
 // cells added to ceil(R) around a particle's box for the region whose solute

@@ -67,12 +67,12 @@ __device__ __forceinline__ int classify(double cx, double cy, double cz, double 
 constexpr int PSI_DEPTH = 4;
 
 // Single-precision pre-test of classify().  (ox, oy, oz) is the cube centre
-// relative to the sphere centre in float: the node's integer offset from the
-// centre's integer part minus the float fraction of the centre (two roundings),
-// then accumulated over at most 4 levels of dyadic offsets (absolute error per
-// component below 7 * 2^-24 (R + 2)); the float squared distances of the
-// farthest corner and of the closest point are then within 3.5e-6 (R + 2)^2 of
-// the exact ones, so
+// relative to the sphere centre in float: the centre relative to the sphere
+// centre's integer part (exact: an integer plus dyadic offsets) minus the
+// float fraction of the sphere centre, one rounding each (absolute error per
+// component below 2 * 2^-24 (R + 2)); the float squared distances of the
+// farthest corner and of the closest point are then well within
+// 3.5e-6 (R + 2)^2 of the exact ones, so
 // whenever they are more than `margin` = 6e-6 (R + 2)^2 away from R^2 the FP64
 // decision is already known.  Returns -1 when the exact test is needed.
 __device__ __forceinline__ int classify_f32(float ox, float oy, float oz, float h, float R2,
@@ -88,6 +88,67 @@ __device__ __forceinline__ int classify_f32(float ox, float oy, float oz, float 
     if (dnear > R2 + margin) return CUBE_OUT;
     if (dnear < R2 - margin) return CUBE_UNDECIDED;
   }
+  return -1;
+}
+
+// Second-tier test in float pairs (hi + lo, about 44 significant bits), for
+// the sub-cubes the float pre-test cannot decide: the GPU's FP64 rate is a
+// small fraction of its FP32 rate, so FP64 is left to true near-ties.  (ax,
+// ay, az) is the sub-cube centre minus the centre's integer part, exact in
+// float (an integer plus dyadic offsets); the centre's fraction and R^2 come as
+// float pairs.  The pair arithmetic approximates the exact corner distances to
+// ~1e-12 (R + 2)^2, and the FP64 test's own rounding is below 1e-13 (R + 2)^2,
+// so a distance more than 1e-10 (R + 2)^2 from R^2 gives the FP64 decision.
+struct f2 {
+  float hi, lo;
+};
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ f2 quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  const f2 s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ f2 f2_sqr(f2 a) {
+  const float p = __fmul_rn(a.hi, a.hi);
+  float e = __fmaf_rn(a.hi, a.hi, -p);
+  e = __fmaf_rn(__fmul_rn(2.0f, a.hi), a.lo, e);
+  return quick_two_sum(p, e);
+}
+// |o| + h (far) or max(|o| - h, 0) (near) for o = a - (fhi + flo)
+__device__ __forceinline__ void f2_axis(float a, float fhi, float flo, float h, f2& far, f2& near) {
+  const f2 s = two_sum(a, -fhi);
+  f2 o = quick_two_sum(s.hi, __fsub_rn(s.lo, flo));
+  if (o.hi < 0.0f) o = {-o.hi, -o.lo};
+  const f2 fa = two_sum(o.hi, h);
+  far = quick_two_sum(fa.hi, __fadd_rn(fa.lo, o.lo));
+  const f2 na = two_sum(o.hi, -h);
+  near = quick_two_sum(na.hi, __fadd_rn(na.lo, o.lo));
+  if (near.hi <= 0.0f) near = {0.0f, 0.0f};
+}
+__device__ __forceinline__ int classify_f2(float ax, float ay, float az, float h, const DevParticle& P) {
+  f2 fx, fy, fz, nx, ny, nz;
+  f2_axis(ax, P.fpos[0], P.fposlo[0], h, fx, nx);
+  f2_axis(ay, P.fpos[1], P.fposlo[1], h, fy, ny);
+  f2_axis(az, P.fpos[2], P.fposlo[2], h, fz, nz);
+  const f2 mr2 = {-P.r2f, -P.r2lo};
+  const float Rp = sqrtf(P.r2f) + 2.0f;
+  const float tol = 1e-10f * Rp * Rp;
+  const f2 df = f2_add(f2_add(f2_add(f2_sqr(fx), f2_sqr(fy)), f2_sqr(fz)), mr2);
+  const float Df = __fadd_rn(df.hi, df.lo);
+  if (Df < -tol) return CUBE_IN;
+  if (Df <= tol) return -1;
+  const f2 dn = f2_add(f2_add(f2_add(f2_sqr(nx), f2_sqr(ny)), f2_sqr(nz)), mr2);
+  const float Dn = __fadd_rn(dn.hi, dn.lo);
+  if (Dn > tol) return CUBE_OUT;
+  if (Dn < -tol) return CUBE_UNDECIDED;
   return -1;
 }
 
@@ -138,10 +199,42 @@ __device__ __forceinline__ float psi_margin(double R2) {
   return 6e-6f * Rp2 * Rp2;
 }
 
-__device__ __forceinline__ bool node_inside(int X, int Y, int Z, const DevParticle& P) {
-  const double dx = (double)X - P.pos[0], dy = (double)Y - P.pos[1], dz = (double)Z - P.pos[2];
-  return dist2(dx, dy, dz) < __dmul_rn(P.radius, P.radius);
+// the sub-cube test in three tiers: float, float pair, FP64 (see above)
+// the FP64 tier as a real call: inlined, its FP64 instructions would be
+// issued (predicated off) on every pass through the caller
+__device__ __noinline__ int classify_exact(int path, int l, int X, int Y, int Z, const DevParticle* P) {
+  double ex, ey, ez;
+  subcube_centre_d(path, l, (double)X, (double)Y, (double)Z, ex, ey, ez);
+  return classify(ex, ey, ez, ldexp(1.0, -(l + 1)), P->pos, __dmul_rn(P->radius, P->radius));
 }
+
+__device__ __forceinline__ int classify_tiers(float ax, float ay, float az, int path, int l,
+                                              int X, int Y, int Z, const DevParticle& P) {
+  const float h = ldexpf(1.0f, -(l + 1));
+  const float cx = __fsub_rn(ax, P.fpos[0]), cy = __fsub_rn(ay, P.fpos[1]), cz = __fsub_rn(az, P.fpos[2]);
+  int st = classify_f32(cx, cy, cz, h, P.r2f, P.psimargin);
+  if (st >= 0) return st;
+  st = classify_f2(ax, ay, az, h, P);
+  if (st >= 0) return st;
+  return classify_exact(path, l, X, Y, Z, &P);
+}
+
+__device__ __noinline__ bool node_inside_exact(int X, int Y, int Z, const DevParticle* P) {
+  const double dx = (double)X - P->pos[0], dy = (double)Y - P->pos[1], dz = (double)Z - P->pos[2];
+  return dist2(dx, dy, dz) < __dmul_rn(P->radius, P->radius);
+}
+
+// node centre strictly inside the sphere: float test, FP64 within its margin
+__device__ __forceinline__ bool node_inside_tiers(int X, int Y, int Z, const DevParticle& P) {
+  const float dx = __fsub_rn((float)(X - P.ipos[0]), P.fpos[0]);
+  const float dy = __fsub_rn((float)(Y - P.ipos[1]), P.fpos[1]);
+  const float dz = __fsub_rn((float)(Z - P.ipos[2]), P.fpos[2]);
+  const float d2 = dx * dx + dy * dy + dz * dz;
+  if (d2 < P.r2f - P.psimargin) return true;
+  if (d2 > P.r2f + P.psimargin) return false;
+  return node_inside_exact(X, Y, Z, &P);
+}
+
 
 // typed access to the fields of the two storage forms
 template <class FM>
@@ -308,6 +401,32 @@ __device__ void block_sum_t(const double (&v)[NV], const bool (&group_on)[NV / 6
 // Block (p, b) takes the rows b, b + nb, b + 2 nb, ... of FORCE_T cells of the
 // widened box (nb blocks for this particle), so the cells next to the sphere
 // are spread over all blocks.
+// FP32 form: the per-thread float sums are added within each warp in float
+// (fixed shuffle tree), the FORCE_T / 32 warp sums in FP64 in order.  Result
+// in out[j] for threadIdx.x == j < NV.
+template <int NV>
+__device__ void block_sum_f(const float (&v)[NV], const bool (&group_on)[NV / 6], double* out) {
+  __shared__ double wsum[FORCE_T / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    if (!group_on[j / 6]) continue;
+    float x = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) wsum[warp][j] = (double)x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int j = threadIdx.x;
+    double t = 0.0;
+    if (group_on[j / 6])
+      for (int w = 0; w < FORCE_T / 32; ++w) t += wsum[w][j];
+    out[j] = t;
+  }
+  __syncthreads();
+}
+
 template <class FM>
 __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   const int p = blockIdx.x;
@@ -327,6 +446,11 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
     qnorm = P.nb > 0 ? P.charge / (double)P.nb : 0.0;
   }
   const double rho0 = a.ph.rho0;
+  const float qnormf = (float)qnorm;
+  // the particle's velocities and rho0 in float, once (FP32 form)
+  const float vxf = (float)P.vel[0], vyf = (float)P.vel[1], vzf = (float)P.vel[2];
+  const float qxf = (float)P.omega[0], qyf = (float)P.omega[1], qzf = (float)P.omega[2];
+  const float rho0f = (float)rho0;
   double acc[FPART];
 #pragma unroll
   for (int j = 0; j < FPART; ++j) acc[j] = 0.0;
@@ -334,6 +458,8 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   // the GPU's FP64 rate is a small fraction of its FP32 rate), with offsets
   // from the centre split into an integer part and the centre's fraction
   float racc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  // FP32 form: momentum exchange [0..5] and own charge [6..9] in float
+  float macc[10] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   const int cxi = (int)floor(P.pos[0]), cyi = (int)floor(P.pos[1]), czi = (int)floor(P.pos[2]);
   const float frx = (float)(P.pos[0] - cxi), fry = (float)(P.pos[1] - cyi), frz = (float)(P.pos[2] - czi);
   bool touched[4] = {false, false, false, false};
@@ -370,7 +496,46 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
                                        nb_z(b, w3[2], dcz(i)));
         if (a.owner[m] == p) links |= 1u << i;
       }
-      if (links) {
+      if (links && FM::fp32) {
+        // FP32 form, in float: the populations are stored as deviations
+        // g = f - w rho0, so f*_i + f_ibar = 2 g_ibar + 2 w rho0 + 6 w rho0 c.w;
+        // the deviation terms are small, and the rest-density term is summed
+        // as an exact integer count of 36 w_i c_i
+        const float d0x = __fsub_rn((float)(X - P.ipos[0]), P.fpos[0]);
+        const float d0y = __fsub_rn((float)(Y - P.ipos[1]), P.fpos[1]);
+        const float d0z = __fsub_rn((float)(Z - P.ipos[2]), P.fpos[2]);
+        const float wx = vxf + (qyf * d0z - qzf * d0y);
+        const float wy = vyf + (qzf * d0x - qxf * d0z);
+        const float wz = vzf + (qxf * d0y - qyf * d0x);
+        const float r0 = rho0f;
+        float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+        int kx = 0, ky = 0, kz = 0;  // sum of 36 w_i c_i over the links
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          if (!(links & (1u << i))) continue;
+          const float gdev = ((const float*)a.f)[(long long)opp(i) * N + n];
+          float cw = 0.0f;
+          if (dcx(i)) cw = dcx(i) > 0 ? cw + wx : cw - wx;
+          if (dcy(i)) cw = dcy(i) > 0 ? cw + wy : cw - wy;
+          if (dcz(i)) cw = dcz(i) > 0 ? cw + wz : cw - wz;
+          const float mom = 2.0f * gdev + 6.0f * (float)wgt(i) * r0 * cw;
+          const int k36 = i < 7 ? 2 : 1;
+          if (dcx(i)) { fx = dcx(i) > 0 ? fx + mom : fx - mom; kx += dcx(i) * k36; }
+          if (dcy(i)) { fy = dcy(i) > 0 ? fy + mom : fy - mom; ky += dcy(i) * k36; }
+          if (dcz(i)) { fz = dcz(i) > 0 ? fz + mom : fz - mom; kz += dcz(i) * k36; }
+        }
+        const float cst = 2.0f * r0 / 36.0f;
+        fx += cst * (float)kx;
+        fy += cst * (float)ky;
+        fz += cst * (float)kz;
+        touched[0] = true;
+        macc[0] += fx;
+        macc[1] += fy;
+        macc[2] += fz;
+        macc[3] += d0y * fz - d0z * fy;
+        macc[4] += d0z * fx - d0x * fz;
+        macc[5] += d0x * fy - d0y * fx;
+      } else if (links) {
         const double d0x = (double)X - P.pos[0], d0y = (double)Y - P.pos[1], d0z = (double)Z - P.pos[2];
         const double wx = P.vel[0] + (P.omega[1] * d0z - P.omega[2] * d0y);
         const double wy = P.vel[1] + (P.omega[2] * d0x - P.omega[0] * d0z);
@@ -429,25 +594,46 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
     // the particle's own charge in this cell
     if (in_box) {
       double qq = 0.0;
+      float psf = 0.0f;
       if (pv) {
         const int bx = P.hi[0] - P.lo[0], by = P.hi[1] - P.lo[1];
         const int cb = (X - P.lo[0]) + bx * ((Y - P.lo[1]) + by * (Z - P.lo[2]));
-        qq = qnorm * a.psibox[(long long)p * a.boxmax + cb];
+        const double ps = a.psibox[(long long)p * a.boxmax + cb];
+        if (FM::fp32) qq = ps != 0.0 ? 1.0 : 0.0;  // the weight itself is applied in float below
+        else qq = qnorm * ps;
+        if (FM::fp32 && ps != 0.0) psf = (float)ps;
       } else if (own == p) {
         qq = qnorm;
+        psf = 1.0f;
       }
       if (qq != 0.0) {
         touched[2] = true;
-        acc[12] += qq;
-        acc[13] += qq * ((double)X - P.pos[0]);
-        acc[14] += qq * ((double)Y - P.pos[1]);
-        acc[15] += qq * ((double)Z - P.pos[2]);
+        if (FM::fp32) {
+          const float qf = qnormf * psf;
+          macc[6] += qf;
+          macc[7] += qf * __fsub_rn((float)(X - P.ipos[0]), P.fpos[0]);
+          macc[8] += qf * __fsub_rn((float)(Y - P.ipos[1]), P.fpos[1]);
+          macc[9] += qf * __fsub_rn((float)(Z - P.ipos[2]), P.fpos[2]);
+        } else {
+          acc[12] += qq;
+          acc[13] += qq * ((double)X - P.pos[0]);
+          acc[14] += qq * ((double)Y - P.pos[1]);
+          acc[15] += qq * ((double)Z - P.pos[2]);
+        }
       }
     }
   }
+  float facc[FPART];
   if (FM::fp32) {
 #pragma unroll
-    for (int j = 0; j < 6; ++j) acc[6 + j] = (double)racc[j];
+    for (int j = 0; j < FPART; ++j) facc[j] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      facc[j] = macc[j];
+      facc[6 + j] = racc[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) facc[12 + j] = macc[6 + j];
   }
   // a slice of the lattice-block sums of the internal force (S2), carried by
   // the first particle's blocks, so that the lattice total is ready when the
@@ -471,7 +657,13 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   on[2] = __syncthreads_or(touched[2]);
   on[3] = __syncthreads_or(touched[3]);
   double* out = a.fpart + ((long long)p * a.fchunks + blockIdx.y) * FPART;
-  block_sum_t<FPART>(acc, on, out);
+  if (FM::fp32) {
+#pragma unroll
+    for (int j = 18; j < 21; ++j) facc[j] = (float)acc[j];  // the lattice slice
+    block_sum_f<FPART>(facc, on, out);
+  } else {
+    block_sum_t<FPART>(acc, on, out);
+  }
   // the particle's last block sums its rows; the last particle integrates
   __shared__ bool last;
   __threadfence();
@@ -515,10 +707,13 @@ __device__ void box_update_one(DevParticle& P, const double pos[3], const int nn
     P.elo[d] = lo - m;
     P.ehi[d] = hi + m;
     P.ipos[d] = (int)floor(pos[d]);
-    P.fpos[d] = (float)(pos[d] - (double)P.ipos[d]);
+    const double frac = pos[d] - (double)P.ipos[d];  // exact
+    P.fpos[d] = (float)frac;
+    P.fposlo[d] = (float)(frac - (double)P.fpos[d]);
   }
   const double R2 = __dmul_rn(P.radius, P.radius);
   P.r2f = (float)R2;
+  P.r2lo = (float)(R2 - (double)P.r2f);
   P.psimargin = psi_margin(R2);
 }
 
@@ -680,16 +875,13 @@ __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
     box_coord(c, P.lo, P.hi, X, Y, Z);
     const long long n = node_of(X, Y, Z, a.g);
     const double R2 = __dmul_rn(P.radius, P.radius);
-    if (node_inside(X, Y, Z, P)) {
+    if (node_inside_tiers(X, Y, Z, P)) {
       inside = 1;
       const int old = atomicCAS(a.owner + n, FLUID, p);
       if (old != FLUID) atomicOr(a.status, ST_OVERLAP);
     }
-    const float ox = __fsub_rn((float)(X - P.ipos[0]), P.fpos[0]);
-    const float oy = __fsub_rn((float)(Y - P.ipos[1]), P.fpos[1]);
-    const float oz = __fsub_rn((float)(Z - P.ipos[2]), P.fpos[2]);
-    int s0 = classify_f32(ox, oy, oz, 0.5f, P.r2f, P.psimargin);
-    if (s0 < 0) s0 = classify((double)X, (double)Y, (double)Z, 0.5, P.pos, R2);
+    const int s0 = classify_tiers((float)(X - P.ipos[0]), (float)(Y - P.ipos[1]),
+                                  (float)(Z - P.ipos[2]), 0, 0, X, Y, Z, P);
     if (s0 == CUBE_IN) {
       ps = 1.0;
       real_add<FM>(a.psi, n, 1.0);
@@ -700,25 +892,26 @@ __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
     }
     a.psibox[(long long)p * a.boxmax + c] = ps;
   }
-  double v[2] = {ps, (double)inside};
-  block_sum<2>(v);
+  // level 0 decides whole cells: Psi_p is 0 or 1 here, so both sums are counts
+  const int nin = __syncthreads_count(ps != 0.0);
+  const int nbd = __syncthreads_count(inside);
   if (threadIdx.x == 0) {
-    if (v[0] != 0.0) atomicAdd(&P.psisum, v[0]);  // dyadic: exact in any order
-    if (v[1] != 0.0) atomicAdd(&P.nb, (int)v[1]);
+    if (nin) atomicAdd(&P.psisum, (double)nin);  // integers: exact in any order
+    if (nbd) atomicAdd(&P.nb, nbd);
   }
 }
 
 constexpr int PSI_WARPS = 4;  // warps per CTA of k_psi_surface
 
 // Sub-cubes whose float pre-test is inconclusive (a corner within the margin
-// of the surface: common when the centre sits on a dyadic position) are queued
-// per warp and given the FP64 test 32 at a time, so a warp never runs the
-// double-precision path for a single lane.
+// of the surface) are queued per warp and given the float-pair test 32 at a
+// time; only near-ties that test cannot decide take the FP64 one.
 template <class FM>
 __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
   // per warp: the undecided cubes of the current and the next level (paths
-  // and float centres; within one octant a level holds at most 64) and the
-  // paths queued for the exact test
+  // and centres relative to the centre's integer part, exact in float; within
+  // one octant a level holds at most 64) and the paths the float pre-test
+  // could not decide
   __shared__ unsigned short qpath[PSI_WARPS][2][64];
   __shared__ float3 qcen[PSI_WARPS][2][64];
   __shared__ unsigned short fbq[PSI_WARPS][64];
@@ -733,29 +926,23 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
     int X, Y, Z;
     box_coord(pc.y, P.lo, P.hi, X, Y, Z);
     const float R2f = P.r2f, margin = P.psimargin;
-    const float ox = __fsub_rn((float)(X - P.ipos[0]), P.fpos[0]);
-    const float oy = __fsub_rn((float)(Y - P.ipos[1]), P.fpos[1]);
-    const float oz = __fsub_rn((float)(Z - P.ipos[2]), P.fpos[2]);
+    // the cell centre minus the particle centre's integer part (exact)
+    const float bx = (float)(X - P.ipos[0]), by = (float)(Y - P.ipos[1]), bz = (float)(Z - P.ipos[2]);
     int cur = 0;
     unsigned short* fb = fbq[wid];
     int qlen = 0;
     int units = 0;
     {
       // level 1: this warp's octant (every lane takes the same decision)
-      float cx, cy, cz;
-      subcube_centre_f(oct, 1, ox, oy, oz, cx, cy, cz);
-      int st = classify_f32(cx, cy, cz, 0.25f, R2f, margin);
-      if (st < 0) {
-        double ex, ey, ez;
-        subcube_centre_d(oct, 1, (double)X, (double)Y, (double)Z, ex, ey, ez);
-        st = classify(ex, ey, ez, 0.25, P.pos, __dmul_rn(P.radius, P.radius));
-      }
+      float ax, ay, az;
+      subcube_centre_f(oct, 1, bx, by, bz, ax, ay, az);
+      const int st = classify_tiers(ax, ay, az, oct, 1, X, Y, Z, P);
       if (st == CUBE_IN) {
         if (lane == 0) units = 2 << (3 * (PSI_DEPTH - 1));
       } else if (st == CUBE_UNDECIDED) {
         if (lane == 0) {
           qpath[wid][0][0] = (unsigned short)oct;
-          qcen[wid][0][0] = make_float3(cx, cy, cz);
+          qcen[wid][0][0] = make_float3(ax, ay, az);
         }
         qlen = 1;
       }
@@ -771,17 +958,17 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
         const int t = t0 + lane;
         bool und = false, exact = false;
         int path = 0;
-        float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
         if (t < ntask) {
           const int bits = t & 7;
           path = ((int)qpath[wid][cur][t >> 3] << 3) | bits;
-          // the child's centre: the parent's plus or minus h per axis (the same
-          // additions, in the same order, as subcube_centre_f)
+          // the child's centre: the parent's plus or minus h per axis (exact)
           const float3 c = qcen[wid][cur][t >> 3];
-          cx = __fadd_rn(c.x, (bits & 1) ? h : -h);
-          cy = __fadd_rn(c.y, (bits & 2) ? h : -h);
-          cz = __fadd_rn(c.z, (bits & 4) ? h : -h);
-          const int st = classify_f32(cx, cy, cz, h, R2f, margin);
+          ax = __fadd_rn(c.x, (bits & 1) ? h : -h);
+          ay = __fadd_rn(c.y, (bits & 2) ? h : -h);
+          az = __fadd_rn(c.z, (bits & 4) ? h : -h);
+          const int st = classify_f32(__fsub_rn(ax, P.fpos[0]), __fsub_rn(ay, P.fpos[1]),
+                                      __fsub_rn(az, P.fpos[2]), h, R2f, margin);
           if (st < 0) exact = true;
           else if (st == CUBE_IN) units += in_units;
           else if (st == CUBE_UNDECIDED) {
@@ -793,7 +980,7 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
         if (und) {
           const int slot = newlen + __popc(mask & lt);
           qpath[wid][nx][slot] = (unsigned short)path;
-          qcen[wid][nx][slot] = make_float3(cx, cy, cz);
+          qcen[wid][nx][slot] = make_float3(ax, ay, az);
         }
         newlen += __popc(mask);
         mask = __ballot_sync(0xffffffffu, exact);
@@ -805,11 +992,11 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
           const int take = min(nfb, 32);
           bool und2 = false;
           int path2 = 0;
+          float fx = 0.0f, fy = 0.0f, fz = 0.0f;
           if (lane < take) {
             path2 = fb[nfb - take + lane];
-            double ex, ey, ez;
-            subcube_centre_d(path2, l, (double)X, (double)Y, (double)Z, ex, ey, ez);
-            const int st = classify(ex, ey, ez, ldexp(1.0, -(l + 1)), P.pos, __dmul_rn(P.radius, P.radius));
+            subcube_centre_f(path2, l, bx, by, bz, fx, fy, fz);
+            const int st = classify_tiers(fx, fy, fz, path2, l, X, Y, Z, P);
             if (st == CUBE_IN) units += in_units;
             else if (st == CUBE_UNDECIDED) {
               if (l == PSI_DEPTH) units += 1;
@@ -819,8 +1006,6 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
           const unsigned m2 = __ballot_sync(0xffffffffu, und2);
           if (und2) {
             const int slot = newlen + __popc(m2 & lt);
-            float fx, fy, fz;
-            subcube_centre_f(path2, l, ox, oy, oz, fx, fy, fz);
             qpath[wid][nx][slot] = (unsigned short)path2;
             qcen[wid][nx][slot] = make_float3(fx, fy, fz);
           }
