@@ -175,6 +175,15 @@ ek_status ek_run_stage(ek_ctx* ctx, int stage);
 
 /* Copy up to count particle records to host memory dst (synchronises). */
 ek_status ek_get_particles(ek_ctx* ctx, ek_particle* dst, int count);
+
+/* The same records, enqueued on the context's stream without waiting (for a
+ * caller that reads every step's particle state while the next steps run):
+ * the first min(count, P) records are packed on the device and copied to dst,
+ * which must be page-locked host memory (cudaHostAlloc, or a pinned torch
+ * tensor) or device memory; they are valid once the stream has passed this
+ * call (an event recorded after it, or ek_sync).  The device status word is not
+ * read (ek_sync reads it).  Errors: EK_ERR_ARG, EK_ERR_CUDA. */
+ek_status ek_get_particles_async(ek_ctx* ctx, ek_particle* dst, int count);
 int ek_num_particles(const ek_ctx* ctx);
 
 /* Run nsteps steps like ek_step, recording CUDA events on the context's stream

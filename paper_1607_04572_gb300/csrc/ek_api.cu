@@ -71,6 +71,7 @@ struct ek_ctx {
   int* xfer_count = nullptr;
   int* ticket = nullptr;
   int* pticket = nullptr;   // Pcap: force blocks done per particle
+  ek_particle* pstage = nullptr;  // Pcap records for ek_get_particles_async
   int xfer_cap = 0;
   int* status = nullptr;
   int cur = 0;
@@ -134,6 +135,27 @@ __global__ void k_double_to_u8(Grid g, const double* in, unsigned char* out) {
 __global__ void k_psi_clamped(Grid g, const double* psi, double* out) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n < g.N) out[n] = fmin(psi[n], 1.0);
+}
+
+// the particle records in the exchange layout (ek_particle), for an
+// asynchronous copy to the host
+__global__ void k_pack_particles(const DevParticle* parts, int P, ek_particle* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const DevParticle& q = parts[i];
+  ek_particle o;
+  for (int d = 0; d < 3; ++d) {
+    o.pos[d] = q.pos[d];
+    o.vel[d] = q.vel[d];
+    o.omega[d] = q.omega[d];
+    o.force[d] = q.force[d];
+    o.torque[d] = q.torque[d];
+  }
+  o.radius = q.radius;
+  o.charge = q.charge;
+  o.rho_p = q.mass / (4.0 / 3.0 * M_PI * q.radius * q.radius * q.radius);
+  o.fixed = q.fixed;
+  out[i] = o;
 }
 
 __global__ void k_count_fluid(Grid g, const int* owner, unsigned long long* count) {
@@ -266,8 +288,10 @@ ek_status run_setup(ek_ctx* ctx) {
     if (ctx->surf) cudaFree(ctx->surf);
     if (ctx->psum) cudaFree(ctx->psum);
     if (ctx->pticket) cudaFree(ctx->pticket);
+    if (ctx->pstage) cudaFree(ctx->pstage);
     ctx->psum = nullptr;
     ctx->pticket = nullptr;
+    ctx->pstage = nullptr;
     ctx->psibox = nullptr;
     ctx->fpart = nullptr;
     ctx->surf = nullptr;
@@ -277,6 +301,7 @@ ek_status run_setup(ek_ctx* ctx) {
     EK_CUDA(cudaMalloc(&ctx->fpart, (size_t)ctx->Pcap * fchunks * FPART * sizeof(double)));
     EK_CUDA(cudaMalloc(&ctx->psum, (size_t)ctx->Pcap * FPART * sizeof(double)));
     EK_CUDA(cudaMalloc(&ctx->pticket, (size_t)ctx->Pcap * sizeof(int)));
+    EK_CUDA(cudaMalloc(&ctx->pstage, (size_t)ctx->Pcap * sizeof(ek_particle)));
     EK_CUDA(cudaMemsetAsync(ctx->pticket, 0, (size_t)ctx->Pcap * sizeof(int), ctx->stream));
     EK_CUDA(cudaMalloc(&ctx->surf, cap * sizeof(int2)));
     ctx->psibox_cap = cap;
@@ -657,7 +682,7 @@ ek_status ek_destroy(ek_ctx* ctx) {
                   ctx->qwall, ctx->u, ctx->tmp, ctx->owner, ctx->owner_prev, ctx->wall,
                   ctx->spectrum, ctx->dparts, ctx->psibox, ctx->fpart, ctx->surf, ctx->xfer,
                   ctx->xfer_count, ctx->surf_count, ctx->status, ctx->ifield, ctx->ipart,
-                  ctx->fkey, ctx->psum, ctx->vsig, ctx->ticket, ctx->pticket};
+                  ctx->fkey, ctx->psum, ctx->vsig, ctx->ticket, ctx->pticket, ctx->pstage};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);
@@ -770,9 +795,12 @@ ek_status ek_set_field(ek_ctx* ctx, ek_field which, int component, const double*
     case EK_FIELD_E_EXT:
     case EK_FIELD_BODY_FORCE: {
       double v[3];
-      EK_CUDA(cudaMemcpyAsync(v, src, 3 * sizeof(double),
-                              src_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
-      EK_CUDA(cudaStreamSynchronize(s));
+      if (src_on_device) {
+        EK_CUDA(cudaMemcpyAsync(v, src, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        EK_CUDA(cudaStreamSynchronize(s));
+      } else {
+        memcpy(v, src, 3 * sizeof(double));  // read on the host: no wait for the stream
+      }
       bool changed = false;
       for (int d = 0; d < 3; ++d) {
         if (!isfinite(v[d])) return fail(ctx, EK_ERR_ARG, "non-finite vector");
@@ -994,6 +1022,21 @@ ek_status ek_get_particles(ek_ctx* ctx, ek_particle* dst, int count) {
     o.rho_p = q.mass / (4.0 / 3.0 * M_PI * pow(q.radius, 3.0));
     o.fixed = q.fixed;
   }
+  return EK_OK;
+}
+
+ek_status ek_get_particles_async(ek_ctx* ctx, ek_particle* dst, int count) {
+  if (!ctx || (!dst && count > 0) || count < 0) return EK_ERR_ARG;
+  if (!ctx->broken) {
+    ek_status st = ready(ctx);
+    if (st != EK_OK) return st;
+  }
+  const int n = std::min(count, ctx->P);
+  if (n == 0) return EK_OK;
+  k_pack_particles<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx->dparts, n, ctx->pstage);
+  EK_CUDA(cudaGetLastError());
+  EK_CUDA(cudaMemcpyAsync(dst, ctx->pstage, (size_t)n * sizeof(ek_particle), cudaMemcpyDefault,
+                          ctx->stream));
   return EK_OK;
 }
 

@@ -43,7 +43,8 @@ STATUS = {0: "EK_OK", -1: "EK_ERR_ARG", -2: "EK_ERR_NOMEM", -3: "EK_ERR_CUDA",
 
 # entry points declared in include/ek.h
 EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get_fields",
-           "ek_step", "ek_step_async", "ek_run_stage", "ek_get_particles", "ek_num_particles",
+           "ek_step", "ek_step_async", "ek_run_stage", "ek_get_particles", "ek_get_particles_async",
+           "ek_num_particles",
            "ek_set_stream", "ek_sync", "ek_last_error", "ek_lattice_dirs",
            "ek_poisson_scratch_bytes", "ek_poisson_solve", "ek_step_timed",
            "ek_kernel_launches", "ek_poisson_solve_static",
@@ -99,6 +100,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ek_step_async.argtypes = [vp, ip]
     lib.ek_run_stage.argtypes = [vp, ip]
     lib.ek_get_particles.argtypes = [vp, ctypes.POINTER(ParticleRec), ip]
+    lib.ek_get_particles_async.argtypes = [vp, vp, ip]
     lib.ek_num_particles.argtypes = [vp]
     lib.ek_num_particles.restype = ip
     lib.ek_set_stream.argtypes = [vp, vp]
@@ -275,6 +277,15 @@ class EKSystem:
     def num_particles(self):
         return self.lib.ek_num_particles(self.ctx)
 
+    def get_particles_async(self, buf):
+        """Enqueue a copy of the particle records into `buf`, a page-locked
+        host (or device) buffer of at least num_particles() records, e.g.
+        torch.empty(n * ctypes.sizeof(ParticleRec), dtype=torch.uint8).pin_memory();
+        decode with particles_from_buffer once the stream has passed the call."""
+        ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else int(buf)
+        self._check(self.lib.ek_get_particles_async(self.ctx, ctypes.c_void_p(ptr),
+                                                     self.num_particles()))
+
     def get_particles(self):
         P = self.num_particles()
         recs = (ParticleRec * max(P, 1))()
@@ -286,6 +297,18 @@ class EKSystem:
                             torque=np.array(r.torque[:]), radius=r.radius, charge=r.charge,
                             rho_p=r.rho_p, fixed=bool(r.fixed)))
         return out
+
+
+def particles_from_buffer(buf, count):
+    """Decode `count` ek_particle records from a host buffer (bytes-like, or a
+    pinned torch uint8 tensor filled by EKSystem.get_particles_async)."""
+    if count <= 0:
+        return []
+    raw = bytes(buf.numpy()) if hasattr(buf, "numpy") else bytes(buf)
+    recs = (ParticleRec * count).from_buffer_copy(raw[:count * ctypes.sizeof(ParticleRec)])
+    return [dict(pos=np.array(r.pos[:]), vel=np.array(r.vel[:]), omega=np.array(r.omega[:]),
+                 force=np.array(r.force[:]), torque=np.array(r.torque[:]), radius=r.radius,
+                 charge=r.charge, rho_p=r.rho_p, fixed=bool(r.fixed)) for r in recs[:count]]
 
 
 def poisson_scratch_bytes(nx, ny, nz):

@@ -60,3 +60,28 @@ def test_graph_replay_matches_direct_launches(gpu_lib, flags):
     b = snapshot(ek, direct, len(case["valence"]))
     assert np.array_equal(a["owner"], b["owner"])
     same(a, b, 1e-12)
+
+
+def test_async_particle_records_match(gpu_lib):
+    """ek_get_particles_async (packed on the device, copied into pinned host
+    memory on the stream) gives the records ek_get_particles gives."""
+    import ctypes
+    import torch
+    ek = gpu_lib
+    case = workloads.small_case(n=(24, 18, 16), radius=3.0, charge=-20.0, nparticles=2)
+    _, s = make_pair(ek, case, flags=O.PV | O.NEUTRALIZE | FP32, vel=[(0.03, 0.0, 0.0), (0.0, -0.02, 0.0)])
+    stream = torch.cuda.Stream()
+    s.set_stream(stream)
+    n = s.num_particles()
+    buf = torch.zeros(n * ctypes.sizeof(ek.ParticleRec), dtype=torch.uint8).pin_memory()
+    for _ in range(2):
+        s.step_async(3)
+        s.get_particles_async(buf)
+        stream.synchronize()
+        got = ek.particles_from_buffer(buf, n)
+        want = s.get_particles()
+        for g, w in zip(got, want):
+            for key in ("pos", "vel", "omega", "force", "torque"):
+                assert np.array_equal(g[key], w[key]), key
+            assert g["radius"] == w["radius"] and g["charge"] == w["charge"] and g["fixed"] == w["fixed"]
+
