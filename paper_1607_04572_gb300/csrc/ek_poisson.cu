@@ -285,9 +285,9 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_inv(PassArgs<R> a, int pa
 }
 
 // ---------------------------------------------------------------------------
-// Fast path of the FP32 form for power-of-two edges 32 .. 512: the same five
-// passes, with each line transform specialised at compile time.  A stage of
-// radix R (16, 8 or 4) loads R elements into registers, applies the stage
+// Fast path of the FP32 form for edges 2^k and 3 2^k from 24 to 512: the same
+// five passes, with each line transform specialised at compile time.  A stage
+// of radix R (16, 8, 4 or 3) loads R elements into registers, applies the stage
 // twiddles from a shared-memory table, does the length-R DFT in registers
 // (even/odd splits down to radix 4, constant twiddles) and stores in
 // Stockham order; a length-128 line takes two stages (16 x 8).  Shared-memory
@@ -304,15 +304,24 @@ constexpr int FAST_IT = 128;      // inverse x pass
 constexpr int FAST_IELEMS = 2048;
 __host__ __device__ constexpr int fpad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int fast_radix(int n, int s) {
-  // radices of the stages: 32 = 8 4, 64 = 8 8, 128 = 16 8, 256 = 16 16, 512 = 8 8 8
+  // radices of the stages: 32 = 8 4, 64 = 8 8, 128 = 16 8, 256 = 16 16, 512 = 8 8 8,
+  // 24 = 8 3, 48 = 16 3, 96 = 8 4 3, 192 = 16 4 3, 384 = 16 8 3
   return n == 32 ? (s == 0 ? 8 : s == 1 ? 4 : 0)
        : n == 64 ? (s < 2 ? 8 : 0)
        : n == 128 ? (s == 0 ? 16 : s == 1 ? 8 : 0)
        : n == 256 ? (s < 2 ? 16 : 0)
        : n == 512 ? (s < 3 ? 8 : 0)
+       : n == 24 ? (s == 0 ? 8 : s == 1 ? 3 : 0)
+       : n == 48 ? (s == 0 ? 16 : s == 1 ? 3 : 0)
+       : n == 96 ? (s == 0 ? 8 : s == 1 ? 4 : s == 2 ? 3 : 0)
+       : n == 192 ? (s == 0 ? 16 : s == 1 ? 4 : s == 2 ? 3 : 0)
+       : n == 384 ? (s == 0 ? 16 : s == 1 ? 8 : s == 2 ? 3 : 0)
        : 0;
 }
-inline bool fast_edge(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+inline bool fast_edge(int n) {
+  return n == 24 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256 ||
+         n == 384 || n == 512;
+}
 
 // multiply by exp(-+2 pi i k / R) (forward: minus), k < R / 2, R = 8 or 16
 template <int R, bool INV>
@@ -337,6 +346,15 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
     const float2 a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
+  } else if constexpr (R == 3) {
+    // X1,2 = v0 - (v1 + v2)/2 -+ i (sqrt 3 / 2)(v1 - v2) (forward; inverse conjugate)
+    const float2 sm = cadd(v[1], v[2]), df = csub(v[1], v[2]);
+    const float2 t = make_float2(v[0].x - 0.5f * sm.x, v[0].y - 0.5f * sm.y);
+    const float c = 0.86602540378443865f;
+    const float2 r = rot(make_float2(c * df.x, c * df.y), INV);
+    v[0] = cadd(v[0], sm);
+    v[1] = cadd(t, r);
+    v[2] = csub(t, r);
   } else if constexpr (R == 4) {
     const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
     const float2 s13 = cadd(v[1], v[3]), d13 = rot(csub(v[1], v[3]), INV);
@@ -577,20 +595,30 @@ void launch_fast_yz_n(PassArgs<float>& a, cudaStream_t s) {
 template <int AXIS, bool INV>
 void launch_fast_yz(PassArgs<float>& a, int n, cudaStream_t s) {
   switch (n) {
+    case 24: launch_fast_yz_n<24, AXIS, INV>(a, s); break;
     case 32: launch_fast_yz_n<32, AXIS, INV>(a, s); break;
+    case 48: launch_fast_yz_n<48, AXIS, INV>(a, s); break;
     case 64: launch_fast_yz_n<64, AXIS, INV>(a, s); break;
+    case 96: launch_fast_yz_n<96, AXIS, INV>(a, s); break;
     case 128: launch_fast_yz_n<128, AXIS, INV>(a, s); break;
+    case 192: launch_fast_yz_n<192, AXIS, INV>(a, s); break;
     case 256: launch_fast_yz_n<256, AXIS, INV>(a, s); break;
+    case 384: launch_fast_yz_n<384, AXIS, INV>(a, s); break;
     default: launch_fast_yz_n<512, AXIS, INV>(a, s); break;
   }
 }
 
 void launch_fast_x_any(PassArgs<float>& a, bool inverse, bool kmajor, cudaStream_t s) {
   switch (a.nx) {
+    case 24: launch_fast_x<24>(a, inverse, kmajor, s); break;
     case 32: launch_fast_x<32>(a, inverse, kmajor, s); break;
+    case 48: launch_fast_x<48>(a, inverse, kmajor, s); break;
     case 64: launch_fast_x<64>(a, inverse, kmajor, s); break;
+    case 96: launch_fast_x<96>(a, inverse, kmajor, s); break;
     case 128: launch_fast_x<128>(a, inverse, kmajor, s); break;
+    case 192: launch_fast_x<192>(a, inverse, kmajor, s); break;
     case 256: launch_fast_x<256>(a, inverse, kmajor, s); break;
+    case 384: launch_fast_x<384>(a, inverse, kmajor, s); break;
     default: launch_fast_x<512>(a, inverse, kmajor, s); break;
   }
 }
@@ -701,8 +729,8 @@ constexpr size_t plane_smem_bytes() {
   return ((size_t)NZ * fpad(NY) + NY + NZ) * sizeof(float2);
 }
 
-// the plane kernels that exist: NY, NZ in {32, 64, 128}
-inline bool plane_edge(int n) { return n == 32 || n == 64 || n == 128; }
+// the plane kernels that exist: NY, NZ in {32, 48, 64, 128}
+inline bool plane_edge(int n) { return n == 32 || n == 48 || n == 64 || n == 128; }
 
 template <int NY, int NZ>
 cudaError_t launch_plane_nn(PassArgs<float>& a, cudaStream_t s) {
@@ -714,6 +742,7 @@ template <int NY>
 cudaError_t launch_plane_n(PassArgs<float>& a, cudaStream_t s) {
   switch (a.nz) {
     case 32: return launch_plane_nn<NY, 32>(a, s);
+    case 48: return launch_plane_nn<NY, 48>(a, s);
     case 64: return launch_plane_nn<NY, 64>(a, s);
     default: return launch_plane_nn<NY, 128>(a, s);
   }
@@ -722,6 +751,7 @@ cudaError_t launch_plane_n(PassArgs<float>& a, cudaStream_t s) {
 cudaError_t launch_plane(PassArgs<float>& a, cudaStream_t s) {
   switch (a.ny) {
     case 32: return launch_plane_n<32>(a, s);
+    case 48: return launch_plane_n<48>(a, s);
     case 64: return launch_plane_n<64>(a, s);
     default: return launch_plane_n<128>(a, s);
   }
@@ -735,6 +765,7 @@ cudaError_t plane_attr_nn() {
 template <int NY>
 cudaError_t plane_attr_n() {
   cudaError_t e = plane_attr_nn<NY, 32>();
+  if (e == cudaSuccess) e = plane_attr_nn<NY, 48>();
   if (e == cudaSuccess) e = plane_attr_nn<NY, 64>();
   if (e == cudaSuccess) e = plane_attr_nn<NY, 128>();
   return e;
@@ -804,6 +835,7 @@ cudaError_t poisson_plan_create(PoissonPlan& p, int nx, int ny, int nz, std::str
   // set once per plan, before any launch or stream capture
   {
     cudaError_t e = plane_attr_n<32>();
+    if (e == cudaSuccess) e = plane_attr_n<48>();
     if (e == cudaSuccess) e = plane_attr_n<64>();
     if (e == cudaSuccess) e = plane_attr_n<128>();
     if (e != cudaSuccess) {

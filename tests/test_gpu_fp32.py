@@ -135,12 +135,14 @@ def test_fp32_single_workload_full_size(gpu_lib):
 
 @pytest.mark.parametrize("shape", [(32, 32, 32), (64, 32, 128), (128, 64, 32), (256, 32, 64),
                                    (512, 32, 32), (128, 128, 128), (32, 256, 32), (64, 32, 256),
-                                   (48, 32, 32), (32, 48, 64)])
+                                   (48, 32, 32), (32, 48, 64), (96, 24, 48), (192, 48, 96),
+                                   (36, 32, 32)])
 def test_fp32_poisson_shapes(gpu_lib, shape):
     """S1 of the FP32 form against the oracle's Poisson solve of the same
-    charge, within FP32 rounding of the spectrum: power-of-two edges 32..512
-    take the specialised line transforms (with n_y, n_z <= 128 the y and z
-    passes of a kx plane run in one CTA), other edges the generic ones."""
+    charge, within FP32 rounding of the spectrum: edges 2^k and 3 2^k from 24
+    to 512 take the specialised line transforms (with n_y, n_z in {32, 48, 64,
+    128} the y and z passes of a kx plane run in one CTA), other edges (36)
+    the generic ones."""
     ek = gpu_lib
     nx, ny, nz = shape
     s = ek.EKSystem(shape, nu=1.0 / 6.0, rho0=1.0, bjerrum=0.7, valence=(1, -1), D=(0.3, 0.3),
