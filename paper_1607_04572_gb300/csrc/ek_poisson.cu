@@ -19,6 +19,7 @@
 // (Govindaraju et al., SC 2008 formulation), ping-ponging between two shared
 // memory buffers, so no bit reversal pass is needed.
 #include <math.h>
+#include <cstdint>
 
 #include <map>
 #include <mutex>
@@ -26,9 +27,13 @@
 #include <type_traits>
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "ek_internal.cuh"
 
 namespace ek {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -152,6 +157,49 @@ __device__ __forceinline__ R charge_at(const PassArgs<R>& a, long long i, long l
   }
   if (a.qwall) q += a.qwall[i];
   if (a.qpart) q += a.qpart[i];
+  return q;
+}
+
+// the charge of four consecutive nodes i..i+3 (i % 4 == 0, every array 16-byte
+// aligned): the operations of charge_at, lane by lane, on 16-byte loads
+__device__ __forceinline__ float4 charge_at4(const PassArgs<float>& a, long long i, long long N) {
+  if (a.rho == nullptr) return *reinterpret_cast<const float4*>(a.q + i);
+  float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (a.int_species) {
+#pragma unroll
+    for (int k = 0; k < EK_MAX_SPECIES; ++k)
+      if (k < a.K) {
+        const int4 v = *reinterpret_cast<const int4*>((const int*)a.rho + k * N + i);
+        q.x += a.z[k] * (float)v.x;
+        q.y += a.z[k] * (float)v.y;
+        q.z += a.z[k] * (float)v.z;
+        q.w += a.z[k] * (float)v.w;
+      }
+  } else {
+#pragma unroll
+    for (int k = 0; k < EK_MAX_SPECIES; ++k)
+      if (k < a.K) {
+        const float4 v = *reinterpret_cast<const float4*>((const float*)a.rho + k * N + i);
+        q.x += a.z[k] * v.x;
+        q.y += a.z[k] * v.y;
+        q.z += a.z[k] * v.z;
+        q.w += a.z[k] * v.w;
+      }
+  }
+  if (a.qwall) {
+    const float4 v = *reinterpret_cast<const float4*>(a.qwall + i);
+    q.x += v.x;
+    q.y += v.y;
+    q.z += v.z;
+    q.w += v.w;
+  }
+  if (a.qpart) {
+    const float4 v = *reinterpret_cast<const float4*>(a.qpart + i);
+    q.x += v.x;
+    q.y += v.y;
+    q.z += v.z;
+    q.w += v.w;
+  }
   return q;
 }
 
@@ -435,7 +483,7 @@ __device__ __forceinline__ void load_twiddles(float2* tw, const AxisPlan& P) {
 // X pass, forward, rows r0 = 2p, r1 = 2p + 1 packed as a + i b (as k_fft_x_fwd).
 // KMAJOR: the half spectrum is stored kx-major, S[kx][z][y], so that each
 // (y, z) plane is contiguous for k_fast_yzplane; else S[z][y][kx].
-template <int NX, bool KMAJOR>
+template <int NX, bool KMAJOR, bool VEC>
 __global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
   constexpr int PPC = FAST_XELEMS / NX > 0 ? FAST_XELEMS / NX : 1;  // row pairs per CTA
   constexpr int LS = fpad(NX);
@@ -445,16 +493,43 @@ __global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
   const int nrows = a.ny * a.nz;
   const long long N = (long long)NX * a.ny * a.nz;
   const int p0 = blockIdx.x * PPC;
-  // PPC * NX / FAST_XT = 4 elements per thread: unrolled, so the loads of
-  // all of them are in flight together
-#pragma unroll 8
-  for (int t = threadIdx.x; t < PPC * NX; t += FAST_XT) {
-    const int l = t / NX, x = t % NX;
-    const int r0 = 2 * (p0 + l), r1 = r0 + 1;
-    float re = 0.0f, im = 0.0f;
-    if (r0 < nrows) re = charge_at(a, (long long)r0 * NX + x, N);
-    if (r1 < nrows) im = charge_at(a, (long long)r1 * NX + x, N);
-    buf[0][l * LS + fpad(x)] = make_float2(re, im);
+  // every load of the thread is issued before the first shared-memory store:
+  // the stores go through no pointer the loads could alias, so the latencies
+  // overlap instead of adding up
+  if constexpr (VEC) {
+    // four consecutive x of one row pair per item (PPC * NX / 4 <= FAST_XT items)
+    static_assert(NX % 4 == 0 && PPC * NX / 4 <= FAST_XT, "one vector item per thread");
+    const int t = threadIdx.x;
+    if (t < PPC * NX / 4) {
+      const int l = t / (NX / 4), x = 4 * (t - l * (NX / 4));
+      const int r0 = 2 * (p0 + l), r1 = r0 + 1;
+      float4 re = make_float4(0.0f, 0.0f, 0.0f, 0.0f), im = re;
+      if (r0 < nrows) re = charge_at4(a, (long long)r0 * NX + x, N);
+      if (r1 < nrows) im = charge_at4(a, (long long)r1 * NX + x, N);
+      float2* d = &buf[0][l * LS + fpad(x)];  // x .. x + 3 lie in one padding group of 16
+      d[0] = make_float2(re.x, im.x);
+      d[1] = make_float2(re.y, im.y);
+      d[2] = make_float2(re.z, im.z);
+      d[3] = make_float2(re.w, im.w);
+    }
+  } else {
+    constexpr int PER = (PPC * NX + FAST_XT - 1) / FAST_XT;
+    float re[PER], im[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int t = threadIdx.x + q * FAST_XT;
+      const int l = t / NX, x = t % NX;
+      const int r0 = 2 * (p0 + l), r1 = r0 + 1;
+      re[q] = 0.0f;
+      im[q] = 0.0f;
+      if (t < PPC * NX && r0 < nrows) re[q] = charge_at(a, (long long)r0 * NX + x, N);
+      if (t < PPC * NX && r1 < nrows) im[q] = charge_at(a, (long long)r1 * NX + x, N);
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int t = threadIdx.x + q * FAST_XT;
+      if (t < PPC * NX) buf[0][(t / NX) * LS + fpad(t % NX)] = make_float2(re[q], im[q]);
+    }
   }
   __syncthreads();
   const float2* res = fast_fft<NX, false>(buf[0], buf[1], PPC, tw);
@@ -524,36 +599,50 @@ __global__ void __launch_bounds__(FAST_T) k_fast_yz(PassArgs<float> a, int tx) {
   }
 }
 
-// X pass, inverse (complex-to-real), two rows per complex transform (as k_fft_x_inv)
+// X pass, inverse (complex-to-real), two rows per complex transform (as k_fft_x_inv).
+// Each stored coefficient kk <= NX / 2 is loaded once and gives the inputs k = kk
+// and, conjugated, k = NX - kk; the thread's loads are all issued before its
+// first shared-memory store.
 template <int NX, bool KMAJOR>
 __global__ void __launch_bounds__(FAST_IT) k_fast_x_inv(PassArgs<float> a) {
   constexpr int PPC = FAST_IELEMS / NX > 0 ? FAST_IELEMS / NX : 1;
   constexpr int LS = fpad(NX);
   constexpr int NXH = NX / 2 + 1;
+  constexpr int PER = (PPC * NXH + FAST_IT - 1) / FAST_IT;
   __shared__ __align__(16) float2 buf[2][PPC * LS];
   __shared__ float2 tw[NX];
   load_twiddles<NX>(tw, a.ax);
   const int nrows = a.ny * a.nz;
   const int p0 = blockIdx.x * PPC;
-#pragma unroll 8
-  for (int t = threadIdx.x; t < PPC * NX; t += FAST_IT) {
-    const int l = KMAJOR ? t % PPC : t / NX, k = KMAJOR ? t / PPC : t % NX;
+  float2 A[PER], B[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int t = threadIdx.x + q * FAST_IT;
+    const int l = KMAJOR ? t % PPC : t / NXH, kk = KMAJOR ? t / PPC : t % NXH;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
-    float2 A = make_float2(0.0f, 0.0f), B = make_float2(0.0f, 0.0f);
-    const bool upper = k > NX / 2;
-    const int kk = upper ? NX - k : k;
-    if (KMAJOR) {
-      if (r0 < nrows) A = a.S[(long long)kk * nrows + r0];
-      if (r1 < nrows) B = a.S[(long long)kk * nrows + r1];
-    } else {
-      if (r0 < nrows) A = a.S[(long long)r0 * NXH + kk];
-      if (r1 < nrows) B = a.S[(long long)r1 * NXH + kk];
+    A[q] = make_float2(0.0f, 0.0f);
+    B[q] = A[q];
+    if (t < PPC * NXH) {
+      if (KMAJOR) {
+        if (r0 < nrows) A[q] = a.S[(long long)kk * nrows + r0];
+        if (r1 < nrows) B[q] = a.S[(long long)kk * nrows + r1];
+      } else {
+        if (r0 < nrows) A[q] = a.S[(long long)r0 * NXH + kk];
+        if (r1 < nrows) B[q] = a.S[(long long)r1 * NXH + kk];
+      }
     }
-    if (upper) {
-      A.y = -A.y;
-      B.y = -B.y;
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int t = threadIdx.x + q * FAST_IT;
+    if (t < PPC * NXH) {
+      const int l = KMAJOR ? t % PPC : t / NXH, kk = KMAJOR ? t / PPC : t % NXH;
+      buf[0][l * LS + fpad(kk)] = make_float2(A[q].x - B[q].y, A[q].y + B[q].x);
+      if (kk > 0 && kk < NX - NXH + 1) {  // 0 < kk < NX / 2: the upper half, conjugated
+        const float2 Ac = make_float2(A[q].x, -A[q].y), Bc = make_float2(B[q].x, -B[q].y);
+        buf[0][l * LS + fpad(NX - kk)] = make_float2(Ac.x - Bc.y, Ac.y + Bc.x);
+      }
     }
-    buf[0][l * LS + fpad(k)] = make_float2(A.x - B.y, A.y + B.x);
   }
   __syncthreads();
   const float2* res = fast_fft<NX, true>(buf[0], buf[1], PPC, tw);
@@ -577,8 +666,16 @@ void launch_fast_x(PassArgs<float>& a, bool inverse, bool kmajor, cudaStream_t s
   } else {
     constexpr int ppc = FAST_XELEMS / NX > 0 ? FAST_XELEMS / NX : 1;
     const unsigned g = (unsigned)((npairs + ppc - 1) / ppc);
-    if (kmajor) k_fast_x_fwd<NX, true><<<g, FAST_XT, 0, s>>>(a);
-    else k_fast_x_fwd<NX, false><<<g, FAST_XT, 0, s>>>(a);
+    // 16-byte loads when every charge array is 16-byte aligned (N % 4 == 0: NX % 4 == 0)
+    const auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    const bool vec = al(a.q) && al(a.rho) && al(a.qwall) && al(a.qpart);
+    if (vec) {
+      if (kmajor) k_fast_x_fwd<NX, true, true><<<g, FAST_XT, 0, s>>>(a);
+      else k_fast_x_fwd<NX, false, true><<<g, FAST_XT, 0, s>>>(a);
+    } else {
+      if (kmajor) k_fast_x_fwd<NX, true, false><<<g, FAST_XT, 0, s>>>(a);
+      else k_fast_x_fwd<NX, false, false><<<g, FAST_XT, 0, s>>>(a);
+    }
   }
 }
 
@@ -634,19 +731,59 @@ void launch_fast_x_any(PassArgs<float>& a, bool inverse, bool kmajor, cudaStream
 // ---------------------------------------------------------------------------
 constexpr int PLANE_T = 1024;
 
+// E contiguous elements of the spectrum (rows of NY) to and from the padded
+// shared-memory layout, in batches of up to 8 per thread whose global loads
+// (or shared-memory loads) are all issued before the first store
+template <int E, int NY, int LS, int T>
+__device__ __forceinline__ void plane_load(const float2* __restrict__ src, float2* pl) {
+  constexpr int PER = (E + T - 1) / T, B = PER < 8 ? PER : 8;
+#pragma unroll
+  for (int q0 = 0; q0 < PER; q0 += B) {
+    float2 v[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int e = threadIdx.x + (q0 + q) * T;
+      if (q0 + q < PER && e < E) v[q] = src[e];
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int e = threadIdx.x + (q0 + q) * T;
+      if (q0 + q < PER && e < E) pl[(e / NY) * LS + fpad(e % NY)] = v[q];
+    }
+  }
+}
+template <int E, int NY, int LS, int T>
+__device__ __forceinline__ void plane_store(const float2* pl, float2* __restrict__ dst) {
+  constexpr int PER = (E + T - 1) / T, B = PER < 8 ? PER : 8;
+#pragma unroll
+  for (int q0 = 0; q0 < PER; q0 += B) {
+    float2 v[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int e = threadIdx.x + (q0 + q) * T;
+      if (q0 + q < PER && e < E) v[q] = pl[(e / NY) * LS + fpad(e % NY)];
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int e = threadIdx.x + (q0 + q) * T;
+      if (q0 + q < PER && e < E) dst[e] = v[q];
+    }
+  }
+}
+
 // one in-place Stockham stage of radix R over the lines of the plane.  Along
 // y (ALONG_Y): NLINES = NZ lines of length N = NY, element (line, i) at
 // line * LSY + fpad(i); along z: NY lines of length NZ, element (line, i) at
 // i * LSY + fpad(line), consecutive threads on consecutive lines.
-template <int N, int NLINES, int NS, int R, bool INV, bool ALONG_Y, int LSY>
+template <int N, int NLINES, int NS, int R, bool INV, bool ALONG_Y, int LSY, int T>
 __device__ __forceinline__ void plane_stage(float2* pl, const float2* tw) {
   constexpr int M = N / R;
   constexpr int ITEMS = NLINES * M;
-  constexpr int PER = (ITEMS + PLANE_T - 1) / PLANE_T;
+  constexpr int PER = (ITEMS + T - 1) / T;
   float2 v[PER][R];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const int t = threadIdx.x + q * PLANE_T;
+    const int t = threadIdx.x + q * T;
     if (t < ITEMS) {
       const int line = ALONG_Y ? t / M : t % NLINES, j = ALONG_Y ? t % M : t / NLINES;
 #pragma unroll
@@ -659,7 +796,7 @@ __device__ __forceinline__ void plane_stage(float2* pl, const float2* tw) {
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const int t = threadIdx.x + q * PLANE_T;
+    const int t = threadIdx.x + q * T;
     if (t < ITEMS) {
       const int line = ALONG_Y ? t / M : t % NLINES, j = ALONG_Y ? t % M : t / NLINES;
       const int k = j % NS;
@@ -683,12 +820,12 @@ __device__ __forceinline__ void plane_stage(float2* pl, const float2* tw) {
   __syncthreads();
 }
 
-template <int N, int NLINES, bool INV, bool ALONG_Y, int LSY>
+template <int N, int NLINES, bool INV, bool ALONG_Y, int LSY, int T = PLANE_T>
 __device__ __forceinline__ void plane_fft(float2* pl, const float2* tw) {
   constexpr int R0 = fast_radix(N, 0), R1 = fast_radix(N, 1), R2 = fast_radix(N, 2);
-  plane_stage<N, NLINES, 1, R0, INV, ALONG_Y, LSY>(pl, tw);
-  if constexpr (R1 != 0) plane_stage<N, NLINES, R0, R1, INV, ALONG_Y, LSY>(pl, tw);
-  if constexpr (R2 != 0) plane_stage<N, NLINES, R0 * R1, R2, INV, ALONG_Y, LSY>(pl, tw);
+  plane_stage<N, NLINES, 1, R0, INV, ALONG_Y, LSY, T>(pl, tw);
+  if constexpr (R1 != 0) plane_stage<N, NLINES, R0, R1, INV, ALONG_Y, LSY, T>(pl, tw);
+  if constexpr (R2 != 0) plane_stage<N, NLINES, R0 * R1, R2, INV, ALONG_Y, LSY, T>(pl, tw);
 }
 
 template <int NY, int NZ>
@@ -702,8 +839,7 @@ __global__ void __launch_bounds__(PLANE_T, 1) k_fast_yzplane(PassArgs<float> a) 
   for (int k = threadIdx.x; k < NY; k += PLANE_T) twy[k] = a.ay.tw32[k];
   for (int k = threadIdx.x; k < NZ; k += PLANE_T) twz[k] = a.az.tw32[k];
   const float2* src = a.S + (long long)kx * NY * NZ;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < NY * NZ; e += PLANE_T) pl[(e / NY) * LSY + fpad(e % NY)] = src[e];
+  plane_load<NY * NZ, NY, LSY, PLANE_T>(src, pl);
   __syncthreads();
   plane_fft<NY, NZ, false, true, LSY>(pl, twy);
   plane_fft<NZ, NY, false, false, LSY>(pl, twz);
@@ -719,9 +855,7 @@ __global__ void __launch_bounds__(PLANE_T, 1) k_fast_yzplane(PassArgs<float> a) 
   __syncthreads();
   plane_fft<NZ, NY, true, false, LSY>(pl, twz);
   plane_fft<NY, NZ, true, true, LSY>(pl, twy);
-  float2* dst = a.S + (long long)kx * NY * NZ;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < NY * NZ; e += PLANE_T) dst[e] = pl[(e / NY) * LSY + fpad(e % NY)];
+  plane_store<NY * NZ, NY, LSY, PLANE_T>(pl, a.S + (long long)kx * NY * NZ);
 }
 
 template <int NY, int NZ>
@@ -729,12 +863,82 @@ constexpr size_t plane_smem_bytes() {
   return ((size_t)NZ * fpad(NY) + NY + NZ) * sizeof(float2);
 }
 
+// The same plane transform on a cluster of two CTAs, twice as many SMs as the
+// one-CTA kernel (whose nx / 2 + 1 CTAs leave most SMs idle at edges <= 128).
+// CTA r loads z lines [r NZ/2, (r+1) NZ/2) and transforms them along y into
+// `pa` ([z][y]); each CTA then writes every element to the CTA that owns its
+// y half (distributed shared memory), into `pb` ([z][y - r NY/2], all z), so
+// that CTA r transforms y lines [r NY/2, (r+1) NY/2) along z, multiplies by the
+// Green function and transforms back; a second exchange returns the z halves
+// for the inverse y transform.  The stages are those of the one-CTA kernel,
+// line by line, so the results are identical.  A cluster barrier separates
+// each exchange from the reads that follow it; no CTA touches the peer's
+// shared memory after the last one, so either may exit first.
+constexpr int PLANE2_T = 512;
+
+template <int NY, int NZ>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PLANE2_T, 1)
+    k_fast_yzplane2(PassArgs<float> a) {
+  constexpr int HZ = NZ / 2, HY = NY / 2;
+  constexpr int LSA = fpad(NY), LSB = fpad(HY);
+  extern __shared__ __align__(16) unsigned char plane_smem[];
+  float2* pa = reinterpret_cast<float2*>(plane_smem);  // [z - r HZ][y], HZ rows
+  float2* pb = pa + HZ * LSA;                          // [z][y - r HY], NZ rows
+  float2* twy = pb + NZ * LSB;
+  float2* twz = twy + NY;
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  cl.barrier_arrive();  // the peer has started before its shared memory is written
+  const int kx = blockIdx.x >> 1;
+  for (int k = threadIdx.x; k < NY; k += PLANE2_T) twy[k] = a.ay.tw32[k];
+  for (int k = threadIdx.x; k < NZ; k += PLANE2_T) twz[k] = a.az.tw32[k];
+  const float2* src = a.S + (long long)kx * NY * NZ + (long long)r * HZ * NY;
+  plane_load<HZ * NY, NY, LSA, PLANE2_T>(src, pa);
+  __syncthreads();
+  plane_fft<NY, HZ, false, true, LSA, PLANE2_T>(pa, twy);
+  float2* const pb0 = cl.map_shared_rank(pb, 0);
+  float2* const pb1 = cl.map_shared_rank(pb, 1);
+  cl.barrier_wait();
+#pragma unroll 4
+  for (int e = threadIdx.x; e < HZ * NY; e += PLANE2_T) {
+    const int zl = e / NY, y = e % NY, o = y / HY;
+    (o ? pb1 : pb0)[(r * HZ + zl) * LSB + fpad(y - o * HY)] = pa[zl * LSA + fpad(y)];
+  }
+  cl.sync();
+  plane_fft<NZ, HY, false, false, LSB, PLANE2_T>(pb, twz);
+  const float lx = lambda_of(a.ax, kx, 0.0f);
+  for (int e = threadIdx.x; e < NZ * HY; e += PLANE2_T) {
+    const int z = e / HY, yl = e % HY, y = r * HY + yl;
+    const float lam = lx + lambda_of(a.ay, y, 0.0f) + lambda_of(a.az, z, 0.0f);
+    const float g = (kx == 0 && y == 0 && z == 0) ? 0.0f : a.green_scale / lam;
+    float2& v = pb[z * LSB + fpad(yl)];
+    v = make_float2(v.x * g, v.y * g);
+  }
+  __syncthreads();
+  plane_fft<NZ, HY, true, false, LSB, PLANE2_T>(pb, twz);
+  float2* const pa0 = cl.map_shared_rank(pa, 0);
+  float2* const pa1 = cl.map_shared_rank(pa, 1);
+#pragma unroll 4
+  for (int e = threadIdx.x; e < NZ * HY; e += PLANE2_T) {
+    const int z = e / HY, yl = e % HY, o = z / HZ;
+    (o ? pa1 : pa0)[(z - o * HZ) * LSA + fpad(r * HY + yl)] = pb[z * LSB + fpad(yl)];
+  }
+  cl.sync();
+  plane_fft<NY, HZ, true, true, LSA, PLANE2_T>(pa, twy);
+  plane_store<HZ * NY, NY, LSA, PLANE2_T>(pa, a.S + (long long)kx * NY * NZ + (long long)r * HZ * NY);
+}
+
+template <int NY, int NZ>
+constexpr size_t plane2_smem_bytes() {
+  return ((size_t)(NZ / 2) * fpad(NY) + (size_t)NZ * fpad(NY / 2) + NY + NZ) * sizeof(float2);
+}
+
 // the plane kernels that exist: NY, NZ in {32, 48, 64, 128}
 inline bool plane_edge(int n) { return n == 32 || n == 48 || n == 64 || n == 128; }
 
 template <int NY, int NZ>
 cudaError_t launch_plane_nn(PassArgs<float>& a, cudaStream_t s) {
-  k_fast_yzplane<NY, NZ><<<(unsigned)a.nxh, PLANE_T, plane_smem_bytes<NY, NZ>(), s>>>(a);
+  k_fast_yzplane2<NY, NZ><<<2 * (unsigned)a.nxh, PLANE2_T, plane2_smem_bytes<NY, NZ>(), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -759,8 +963,12 @@ cudaError_t launch_plane(PassArgs<float>& a, cudaStream_t s) {
 
 template <int NY, int NZ>
 cudaError_t plane_attr_nn() {
-  return cudaFuncSetAttribute(k_fast_yzplane<NY, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)plane_smem_bytes<NY, NZ>());
+  cudaError_t e = cudaFuncSetAttribute(k_fast_yzplane<NY, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)plane_smem_bytes<NY, NZ>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fast_yzplane2<NY, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)plane2_smem_bytes<NY, NZ>());
+  return e;
 }
 template <int NY>
 cudaError_t plane_attr_n() {

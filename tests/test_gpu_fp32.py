@@ -141,8 +141,9 @@ def test_fp32_poisson_shapes(gpu_lib, shape):
     """S1 of the FP32 form against the oracle's Poisson solve of the same
     charge, within FP32 rounding of the spectrum: edges 2^k and 3 2^k from 24
     to 512 take the specialised line transforms (with n_y, n_z in {32, 48, 64,
-    128} the y and z passes of a kx plane run in one CTA), other edges (36)
-    the generic ones."""
+    128} the y and z passes of a kx plane run on a cluster of two CTAs that
+    exchange halves through distributed shared memory), other edges (36) the
+    generic ones."""
     ek = gpu_lib
     nx, ny, nz = shape
     s = ek.EKSystem(shape, nu=1.0 / 6.0, rho0=1.0, bjerrum=0.7, valence=(1, -1), D=(0.3, 0.3),
