@@ -119,8 +119,8 @@ template <int K>
 struct LBRing {
   int own[RING][HP];
   float phi[RING][HP];
-  float psi[RING][HP];
-  int rho[K > 0 ? K : 1][RING][HP];
+  float psi[RING][HP];                // Psi as copied; 1 - Psi once landed
+  int rho[K > 0 ? K : 1][RING][HP];   // int units as copied; rho qscale (float bits) once landed
   float pop[2][Q][TN];
 };
 
@@ -232,23 +232,23 @@ __device__ __forceinline__ void lb32_node(const LBRing<K>& t, const LBArgs& a, c
     float gx = 0.0f, gy = 0.0f, gz = 0.0f;
     int S[K > 0 ? K : 1];
     float r0[K > 0 ? K : 1];
-    const float om0 = PV ? __fsub_rn(1.0f, t.psi[sl[1]][e0]) : 1.0f;
+    const float om0 = PV ? t.psi[sl[1]][e0] : 1.0f;
     const float phi0 = t.phi[sl[1]][e0];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       S[k] = 0;
-      r0[k] = __fmul_rn((float)t.rho[k][sl[1]][e0], c.qs[k]);
+      r0[k] = __int_as_float(t.rho[k][sl[1]][e0]);
     }
 #pragma unroll
     for (int d = 1; d < Q; ++d) {
       if (K == 0 || !(fluid & (1u << d))) continue;
       const int sd = sl[1 + dcz(d)], ed = e0 + dcx(d) + HX * dcy(d);
-      const float omj = PV ? __fsub_rn(1.0f, t.psi[sd][ed]) : 1.0f;
+      const float omj = PV ? t.psi[sd][ed] : 1.0f;
       const float dphi = __fadd_rn(__fsub_rn(phi0, t.phi[sd][ed]), c.ec[d]);
       float tsum = 0.0f;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float rb = __fmul_rn((float)t.rho[k][sd][ed], c.qs[k]);
+        const float rb = __int_as_float(t.rho[k][sd][ed]);
         const float A = PV ? __fmul_rn(r0[k], omj) : r0[k];
         const float B = PV ? __fmul_rn(rb, om0) : rb;
         float br = fmaf(__fadd_rn(A, B), __fmul_rn(c.hz[k], dphi), __fsub_rn(A, B));
@@ -374,11 +374,20 @@ __global__ void __launch_bounds__(256, 2) k_lb32_tiled(LBArgs a, Phys32 c) {
   stage_plane<K, PV>(t, (z0 + 1) & 3, z0 + 1, x0, y0, a);
   stage_pops<K>(t, z0 & 1, z0, x0, y0, a);
   cp_async_commit();
-  // does a landed halo plane hold a non-fluid node or Psi > 0?  Each thread
-  // looks at the elements it copied itself (complete after its own wait).
+  // A landed halo plane: does it hold a non-fluid node or Psi > 0?  And its
+  // species and Psi are converted once, in place, to the operands of the link
+  // fluxes (rho qscale and 1 - Psi, the same operations each of the 19 uses
+  // would repeat).  Each thread handles the elements it copied itself
+  // (complete after its own wait); the barrier that follows publishes them.
   auto plane_flag = [&](int slot) -> int {
     bool f = false;
-    for (int e = tid; e < HP; e += TN) f |= t.own[slot][e] != FLUID || (PV && t.psi[slot][e] != 0.0f);
+    for (int e = tid; e < HP; e += TN) {
+      f |= t.own[slot][e] != FLUID || (PV && t.psi[slot][e] != 0.0f);
+      if (PV) t.psi[slot][e] = __fsub_rn(1.0f, t.psi[slot][e]);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        t.rho[k][slot][e] = __float_as_int(__fmul_rn((float)t.rho[k][slot][e], c.qs[k]));
+    }
     return f ? 1 : 0;
   };
   int fm1 = 0, f0 = 0;  // flags of planes z - 1 and z

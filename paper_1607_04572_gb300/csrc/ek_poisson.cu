@@ -482,7 +482,7 @@ __device__ __forceinline__ void load_twiddles(float2* tw, const AxisPlan& P) {
 
 // X pass, forward, rows r0 = 2p, r1 = 2p + 1 packed as a + i b (as k_fft_x_fwd).
 // KMAJOR: the half spectrum is stored kx-major, S[kx][z][y], so that each
-// (y, z) plane is contiguous for k_fast_yzplane; else S[z][y][kx].
+// (y, z) plane is contiguous for k_fast_yzplane2; else S[z][y][kx].
 template <int NX, bool KMAJOR, bool VEC>
 __global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
   constexpr int PPC = FAST_XELEMS / NX > 0 ? FAST_XELEMS / NX : 1;  // row pairs per CTA
@@ -570,10 +570,23 @@ __global__ void __launch_bounds__(FAST_T) k_fast_yz(PassArgs<float> a, int tx) {
   const int nc = min(tx, nxh - kx0);
   const long long stride = AXIS == 1 ? (long long)nxh : (long long)nxh * a.ny;
   const long long base = AXIS == 1 ? (long long)other * a.ny * nxh : (long long)other * nxh;
-#pragma unroll 8
-  for (int t = threadIdx.x; t < nc * NL; t += FAST_T) {
-    const int j = t / nc, c = t - j * nc;
-    buf[0][c * LS + fpad(j)] = a.S[base + j * stride + kx0 + c];
+  {
+    // all of the thread's loads before its first shared-memory store
+    constexpr int TXMAX = FAST_ELEMS / NL < 16 ? FAST_ELEMS / NL : 16;  // nc <= TXMAX
+    constexpr int PER = (TXMAX * NL + FAST_T - 1) / FAST_T;
+    float2 v[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int t = threadIdx.x + q * FAST_T;
+      const int j = t / nc, c = t - j * nc;
+      if (t < nc * NL) v[q] = a.S[base + j * stride + kx0 + c];
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int t = threadIdx.x + q * FAST_T;
+      const int j = t / nc, c = t - j * nc;
+      if (t < nc * NL) buf[0][c * LS + fpad(j)] = v[q];
+    }
   }
   __syncthreads();
   float2* res;
@@ -721,15 +734,14 @@ void launch_fast_x_any(PassArgs<float>& a, bool inverse, bool kmajor, cudaStream
 }
 
 // ---------------------------------------------------------------------------
-// The y and z passes of one kx plane in one CTA: when a (y, z) plane of the
-// kx-major half spectrum fits in shared memory (edges 32..128), one CTA of
-// 1024 threads loads it (contiguous), transforms along y and z, multiplies by
-// the Green function, transforms back and stores it: three kernels and four
-// round trips through L2 become one.  Each stage runs in place: every thread
-// reads its sub-transforms' elements into registers, the block synchronises,
-// then every thread writes its results.
+// The y and z passes of one kx plane in one kernel: when a (y, z) plane of the
+// kx-major half spectrum fits in the shared memory of two CTAs (edges
+// 32..128), a cluster of two loads it (contiguous), transforms along y and z,
+// multiplies by the Green function, transforms back and stores it: three
+// kernels and four round trips through L2 become one.  Each stage runs in
+// place: every thread reads its sub-transforms' elements into registers, the
+// block synchronises, then every thread writes its results.
 // ---------------------------------------------------------------------------
-constexpr int PLANE_T = 1024;
 
 // E contiguous elements of the spectrum (rows of NY) to and from the padded
 // shared-memory layout, in batches of up to 8 per thread whose global loads
@@ -820,7 +832,7 @@ __device__ __forceinline__ void plane_stage(float2* pl, const float2* tw) {
   __syncthreads();
 }
 
-template <int N, int NLINES, bool INV, bool ALONG_Y, int LSY, int T = PLANE_T>
+template <int N, int NLINES, bool INV, bool ALONG_Y, int LSY, int T>
 __device__ __forceinline__ void plane_fft(float2* pl, const float2* tw) {
   constexpr int R0 = fast_radix(N, 0), R1 = fast_radix(N, 1), R2 = fast_radix(N, 2);
   plane_stage<N, NLINES, 1, R0, INV, ALONG_Y, LSY, T>(pl, tw);
@@ -828,50 +840,14 @@ __device__ __forceinline__ void plane_fft(float2* pl, const float2* tw) {
   if constexpr (R2 != 0) plane_stage<N, NLINES, R0 * R1, R2, INV, ALONG_Y, LSY, T>(pl, tw);
 }
 
-template <int NY, int NZ>
-__global__ void __launch_bounds__(PLANE_T, 1) k_fast_yzplane(PassArgs<float> a) {
-  constexpr int LSY = fpad(NY);
-  extern __shared__ __align__(16) unsigned char plane_smem[];
-  float2* pl = reinterpret_cast<float2*>(plane_smem);  // [z][y], rows padded
-  float2* twy = pl + NZ * LSY;
-  float2* twz = twy + NY;
-  const int kx = blockIdx.x;
-  for (int k = threadIdx.x; k < NY; k += PLANE_T) twy[k] = a.ay.tw32[k];
-  for (int k = threadIdx.x; k < NZ; k += PLANE_T) twz[k] = a.az.tw32[k];
-  const float2* src = a.S + (long long)kx * NY * NZ;
-  plane_load<NY * NZ, NY, LSY, PLANE_T>(src, pl);
-  __syncthreads();
-  plane_fft<NY, NZ, false, true, LSY>(pl, twy);
-  plane_fft<NZ, NY, false, false, LSY>(pl, twz);
-  // Green function of the 7-point Laplacian
-  const float lx = lambda_of(a.ax, kx, 0.0f);
-  for (int e = threadIdx.x; e < NY * NZ; e += PLANE_T) {
-    const int z = e / NY, y = e % NY;
-    const float lam = lx + lambda_of(a.ay, y, 0.0f) + lambda_of(a.az, z, 0.0f);
-    const float g = (kx == 0 && y == 0 && z == 0) ? 0.0f : a.green_scale / lam;
-    float2& v = pl[z * LSY + fpad(y)];
-    v = make_float2(v.x * g, v.y * g);
-  }
-  __syncthreads();
-  plane_fft<NZ, NY, true, false, LSY>(pl, twz);
-  plane_fft<NY, NZ, true, true, LSY>(pl, twy);
-  plane_store<NY * NZ, NY, LSY, PLANE_T>(pl, a.S + (long long)kx * NY * NZ);
-}
-
-template <int NY, int NZ>
-constexpr size_t plane_smem_bytes() {
-  return ((size_t)NZ * fpad(NY) + NY + NZ) * sizeof(float2);
-}
-
-// The same plane transform on a cluster of two CTAs, twice as many SMs as the
-// one-CTA kernel (whose nx / 2 + 1 CTAs leave most SMs idle at edges <= 128).
-// CTA r loads z lines [r NZ/2, (r+1) NZ/2) and transforms them along y into
+// Two CTAs per plane use twice the SMs of one (nx / 2 + 1 CTAs would leave
+// most SMs idle at edges <= 128).  CTA r loads z lines [r NZ/2, (r+1) NZ/2) and transforms them along y into
 // `pa` ([z][y]); each CTA then writes every element to the CTA that owns its
 // y half (distributed shared memory), into `pb` ([z][y - r NY/2], all z), so
 // that CTA r transforms y lines [r NY/2, (r+1) NY/2) along z, multiplies by the
 // Green function and transforms back; a second exchange returns the z halves
-// for the inverse y transform.  The stages are those of the one-CTA kernel,
-// line by line, so the results are identical.  A cluster barrier separates
+// for the inverse y transform.  Every line goes through the same stages as
+// in a one-CTA transform of the plane.  A cluster barrier separates
 // each exchange from the reads that follow it; no CTA touches the peer's
 // shared memory after the last one, so either may exit first.
 constexpr int PLANE2_T = 512;
@@ -963,12 +939,8 @@ cudaError_t launch_plane(PassArgs<float>& a, cudaStream_t s) {
 
 template <int NY, int NZ>
 cudaError_t plane_attr_nn() {
-  cudaError_t e = cudaFuncSetAttribute(k_fast_yzplane<NY, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)plane_smem_bytes<NY, NZ>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fast_yzplane2<NY, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)plane2_smem_bytes<NY, NZ>());
-  return e;
+  return cudaFuncSetAttribute(k_fast_yzplane2<NY, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)plane2_smem_bytes<NY, NZ>());
 }
 template <int NY>
 cudaError_t plane_attr_n() {
