@@ -192,8 +192,9 @@ int ek_num_particles(const ek_ctx* ctx);
  * advection, [3] S4, [4] S5, [5] the whole nsteps steps.  Waits for the work. */
 ek_status ek_step_timed(ek_ctx* ctx, int nsteps, double stage_ms[6]);
 
-/* Number of kernels (and device memsets) the library has enqueued on this
- * context since it was created. */
+/* Number of kernels the step and stage calls (ek_step, ek_step_async,
+ * ek_run_stage, ek_step_timed and batch steps) have enqueued on this context
+ * since it was created; device memsets and set-up work are not counted. */
 long long ek_kernel_launches(const ek_ctx* ctx);
 
 /* Use the CUDA stream `stream` (a cudaStream_t) for all later work; waits for

@@ -27,7 +27,7 @@ struct ek_ctx {
   cudaEvent_t ev_join = nullptr;     // all auxiliary work of the step done
   // one captured step per parity of `cur` (the ping-pong buffers alternate)
   cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
-  long long graph_launches = 0;      // kernels and memsets in one captured step
+  long long graph_launches = 0;      // kernels in one captured step
   int device = 0;
   int fp32 = 0;  // storage form (EK_FP32)
   // field storage: double (FP64 form) or float / int32 species (FP32 form)
@@ -75,7 +75,7 @@ struct ek_ctx {
   int xfer_cap = 0;
   int* status = nullptr;
   int cur = 0;
-  long long launches = 0;  // kernels and memsets enqueued so far
+  long long launches = 0;  // kernels enqueued by the step and stage calls so far
   bool setup_pending = true;
   bool has_qwall = false;
   bool broken = false;
@@ -396,7 +396,7 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
                               (const double*)ctx->qpart, ctx->ph, (double*)ctx->phi,
                               (double2*)ctx->spectrum, s));
       }
-      ctx->launches += 5;
+      ctx->launches += poisson_kernel_count(ctx->plan, ctx->fp32);
       return EK_OK;
     case 2: {
       LBArgs a = lb_args(ctx);
@@ -417,7 +417,7 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
       PartArgs a = part_args(ctx);
       if (ctx->P) {
         EK_CUDA(launch_reflag(a, true, s));
-        ctx->launches += 9;
+        ctx->launches += 7;
       }
       return EK_OK;
     }
@@ -446,7 +446,7 @@ ek_status enqueue_step(ek_ctx* ctx) {
     EK_CUDA(ctx->fp32 ? launch_advection32(la, s) : launch_advection(la, s));
     EK_CUDA(launch_reflag(pa, true, s, 2));
     EK_CUDA(launch_particle_forces(pa, s, S4_KEY_RESET));
-    ctx->launches += (ctx->p.nspecies > 0 ? 2 : 1) + 12;
+    ctx->launches += (ctx->p.nspecies > 0 ? 2 : 1) + 10;
     return EK_OK;
   }
   if (ctx->P) {
@@ -478,7 +478,7 @@ ek_status enqueue_step(ek_ctx* ctx) {
     EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_part, 0));
     EK_CUDA(launch_reflag(pa, true, s, 2));
     EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
-    ctx->launches += 12;
+    ctx->launches += 10;
   }
   return EK_OK;
 }

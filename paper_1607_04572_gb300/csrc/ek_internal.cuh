@@ -204,6 +204,8 @@ __device__ __forceinline__ long long node_index(const Grid& g, int x, int y, int
 cudaError_t poisson_plan_create(PoissonPlan& p, int nx, int ny, int nz, std::string& err);
 void poisson_plan_destroy(PoissonPlan& p);
 size_t poisson_spectrum_bytes(int nx, int ny, int nz);
+// kernels one solve of this plan launches (the FP32 or the FP64 passes)
+int poisson_kernel_count(const PoissonPlan& p, bool fp32);
 // radix plan of one axis (n = 2^a 3^b); false if n has another factor
 bool poisson_factor(int n, AxisPlan& P);
 // charge assembly fused into the first FFT pass when rho != nullptr; else q is read.

@@ -691,36 +691,45 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
 // the union with the previous box (moved into the periodic image of the new
 // one, as the position wraps when the particle crosses the boundary), and the
 // box widened by ceil(R) + FORCE_MARGIN for the solute-force assignment.
-__device__ void box_update_one(DevParticle& P, const double pos[3], const int nn[3], bool setup) {
-  for (int d = 0; d < 3; ++d) {
-    const int lo = (int)floor(pos[d] - P.radius) - 1;
-    const int hi = (int)floor(pos[d] + P.radius) + 2;
-    int olo = P.lo[d], ohi = P.hi[d];
-    const int shift = (int)rint((double)(lo - olo) / (double)nn[d]) * nn[d];
-    olo += shift;
-    ohi += shift;
-    P.ulo[d] = setup ? lo : min(lo, olo);
-    P.uhi[d] = setup ? hi : max(hi, ohi);
-    P.lo[d] = lo;
-    P.hi[d] = hi;
-    const int m = (int)ceil(P.radius) + FORCE_MARGIN;
-    P.elo[d] = lo - m;
-    P.ehi[d] = hi + m;
-    P.ipos[d] = (int)floor(pos[d]);
-    const double frac = pos[d] - (double)P.ipos[d];  // exact
-    P.fpos[d] = (float)frac;
-    P.fposlo[d] = (float)(frac - (double)P.fpos[d]);
-  }
+// Axis d alone (the integration runs one thread per axis).
+__device__ void box_update_axis(DevParticle& P, int d, double pos, int nn, bool setup) {
+  const int lo = (int)floor(pos - P.radius) - 1;
+  const int hi = (int)floor(pos + P.radius) + 2;
+  int olo = P.lo[d], ohi = P.hi[d];
+  const int shift = (int)rint((double)(lo - olo) / (double)nn) * nn;
+  olo += shift;
+  ohi += shift;
+  P.ulo[d] = setup ? lo : min(lo, olo);
+  P.uhi[d] = setup ? hi : max(hi, ohi);
+  P.lo[d] = lo;
+  P.hi[d] = hi;
+  const int m = (int)ceil(P.radius) + FORCE_MARGIN;
+  P.elo[d] = lo - m;
+  P.ehi[d] = hi + m;
+  P.ipos[d] = (int)floor(pos);
+  const double frac = pos - (double)P.ipos[d];  // exact
+  P.fpos[d] = (float)frac;
+  P.fposlo[d] = (float)(frac - (double)P.fpos[d]);
+}
+
+// the radius in the forms the inside tests use
+__device__ void radius_forms(DevParticle& P) {
   const double R2 = __dmul_rn(P.radius, P.radius);
   P.r2f = (float)R2;
   P.r2lo = (float)(R2 - (double)P.r2f);
   P.psimargin = psi_margin(R2);
 }
 
+__device__ void box_update_one(DevParticle& P, const double pos[3], const int nn[3], bool setup) {
+  for (int d = 0; d < 3; ++d) box_update_axis(P, d, pos[d], nn[d], setup);
+  radius_forms(P);
+}
+
 // Column sums of a row-major table (nrow rows of `stride` doubles; columns
 // col0 .. col0 + NC - 1) by a block of FORCE_T threads, fixed order: thread
 // t < G * NC takes column t % NC of rows t / NC, t / NC + G, ... (eight loads
-// in flight at a time), then thread j < NC adds the G partials in order.
+// in flight at a time), then thread j < NC adds the partials of the groups
+// that hold rows (min(G, nrow); the others would add zeros) in order.
 // Result in out[j] (shared or global) for threadIdx.x == j.
 template <int NC>
 __device__ void column_sums(const double* tab, int nrow, int stride, int col0, double* out) {
@@ -743,8 +752,9 @@ __device__ void column_sums(const double* tab, int nrow, int stride, int col0, d
   }
   __syncthreads();
   if (t < NC) {
+    const int gu = min(G, nrow);
     double s = 0.0;
-    for (int r = 0; r < G; ++r) s += part[r * NC + t];
+    for (int r = 0; r < gu; ++r) s += part[r * NC + t];
     out[t] = s;
   }
   __syncthreads();
@@ -754,60 +764,71 @@ __device__ void column_sums(const double* tab, int nrow, int stride, int col0, d
 // on nodes no particle claims (lattice total of the internal force minus the
 // claimed sums) is split evenly; every particle then moves by symplectic
 // Euler (Sec. III.B), and its boxes follow the new position (start of S5).
+// Up to FORCE_T / 4 particles take four lanes each, lane d < 3 doing axis d,
+// so that the FP64 divisions of the three axes (by the mass, the moment of
+// inertia, the box edge) run side by side instead of one after another in
+// one thread; more particles take one thread each (all three axes).
 __device__ void integrate_all(const PartArgs& a) {
-  __shared__ double claimed[3], total[3];
+  __shared__ double claimed[3], total[3], rem[3];
+  __shared__ unsigned char fin[3 * FORCE_T];
   column_sums<3>(a.psum, a.P, FPART, 18, total);
   column_sums<3>(a.psum, a.P, FPART, 6, claimed);
-  double rem[3];
-  for (int d = 0; d < 3; ++d) rem[d] = (total[d] + claimed[d]) / (double)a.P;  // claimed holds -sum i
-  const double E[3] = {a.ph.E[0], a.ph.E[1], a.ph.E[2]};
-  const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
-  for (int p = threadIdx.x; p < a.P; p += blockDim.x) {
-    DevParticle* Pp = a.parts + p;
-    double acc[FPART];
-#pragma unroll
-    for (int j = 0; j < FPART; ++j) acc[j] = __ldcg(a.psum + (long long)p * FPART + j);
-    double pos[3], vel[3], omega[3], ftrans[3];
-    for (int d = 0; d < 3; ++d) {
-      pos[d] = Pp->pos[d];
-      vel[d] = Pp->vel[d];
-      omega[d] = Pp->omega[d];
-      ftrans[d] = Pp->ftrans[d];
-    }
-    const double mass = Pp->mass, inertia = Pp->inertia;
-    const bool fixed = Pp->fixed;
-    // field on the own charge: E sum q, (sum q (r - r_p)) x E
-    const double Tq[3] = {acc[14] * E[2] - acc[15] * E[1], acc[15] * E[0] - acc[13] * E[2],
-                          acc[13] * E[1] - acc[14] * E[0]};
-    double F[3], T[3];
-    for (int d = 0; d < 3; ++d) {
-      F[d] = acc[d] + acc[6 + d] + acc[12] * E[d] - rem[d] + ftrans[d];
-      T[d] = acc[3 + d] + acc[9 + d] + Tq[d];
-    }
-    if (!fixed) {
-      for (int d = 0; d < 3; ++d) {
-        vel[d] = vel[d] + F[d] / mass;
-        omega[d] = omega[d] + T[d] / inertia;
-        pos[d] = pos[d] + vel[d];
-        if (pos[d] >= (double)nn[d]) pos[d] -= (double)nn[d];
-        else if (pos[d] < 0.0) pos[d] += (double)nn[d];
+  if (threadIdx.x < 3)
+    rem[threadIdx.x] = (total[threadIdx.x] + claimed[threadIdx.x]) / (double)a.P;  // claimed holds -sum i
+  __syncthreads();
+  const bool quad = a.P <= FORCE_T / 4;
+  const int per_pass = quad ? FORCE_T / 4 : FORCE_T;
+  const int pl = quad ? (int)threadIdx.x >> 2 : (int)threadIdx.x;
+  const int d0 = quad ? (int)(threadIdx.x & 3) : 0, dstep = quad ? 3 : 1;
+  const double* E = a.ph.E;
+  for (int base = 0; base < a.P; base += per_pass) {
+    const int p = base + pl;
+    const bool on = p < a.P;
+    double posd[3] = {0.0, 0.0, 0.0};
+    if (on) {
+      DevParticle* Pp = a.parts + p;
+      const double* acc = a.psum + (long long)p * FPART;
+      for (int d = d0; d < 3; d += dstep) {
+        const int d1 = d == 2 ? 0 : d + 1, d2 = d == 0 ? 2 : d - 1;  // (d, d1, d2) cyclic
+        const int nn = d == 0 ? a.g.nx : (d == 1 ? a.g.ny : a.g.nz);
+        // field on the own charge: E sum q, (sum q (r - r_p)) x E
+        const double Tq = __ldcg(acc + 13 + d1) * E[d2] - __ldcg(acc + 13 + d2) * E[d1];
+        const double F = __ldcg(acc + d) + __ldcg(acc + 6 + d) + __ldcg(acc + 12) * E[d] - rem[d] +
+                         Pp->ftrans[d];
+        const double T = __ldcg(acc + 3 + d) + __ldcg(acc + 9 + d) + Tq;
+        double pos = Pp->pos[d], vel = Pp->vel[d], omega = Pp->omega[d];
+        if (!Pp->fixed) {
+          vel = vel + F / Pp->mass;
+          omega = omega + T / Pp->inertia;
+          pos = pos + vel;
+          if (pos >= (double)nn) pos -= (double)nn;
+          else if (pos < 0.0) pos += (double)nn;
+          if (!isfinite(pos)) atomicOr(a.status, ST_NONFINITE);
+        }
+        Pp->force[d] = F;
+        Pp->torque[d] = T;
+        Pp->ftrans[d] = 0.0;
+        Pp->pos[d] = pos;
+        Pp->vel[d] = vel;
+        Pp->omega[d] = omega;
+        // S5 starts here: the boxes follow the new position
+        Pp->kelo[d] = Pp->elo[d];
+        Pp->kehi[d] = Pp->ehi[d];
+        fin[3 * pl + d] = isfinite(pos) ? 1 : 0;
+        if (d == 0) posd[0] = pos;
+        else if (d == 1) posd[1] = pos;
+        else posd[2] = pos;
       }
-      if (!isfinite(pos[0] + pos[1] + pos[2])) atomicOr(a.status, ST_NONFINITE);
     }
-    for (int d = 0; d < 3; ++d) {
-      Pp->force[d] = F[d];
-      Pp->torque[d] = T[d];
-      Pp->ftrans[d] = 0.0;
-      Pp->pos[d] = pos[d];
-      Pp->vel[d] = vel[d];
-      Pp->omega[d] = omega[d];
+    __syncthreads();
+    if (on && d0 < 3 && fin[3 * pl] && fin[3 * pl + 1] && fin[3 * pl + 2]) {
+      DevParticle& P = a.parts[p];
+      for (int d = d0; d < 3; d += dstep)
+        box_update_axis(P, d, d == 0 ? posd[0] : (d == 1 ? posd[1] : posd[2]),
+                        d == 0 ? a.g.nx : (d == 1 ? a.g.ny : a.g.nz), false);
+      if (d0 == 0) radius_forms(P);
     }
-    // S5 starts here: the boxes follow the new position
-    for (int d = 0; d < 3; ++d) {
-      Pp->kelo[d] = Pp->elo[d];
-      Pp->kehi[d] = Pp->ehi[d];
-    }
-    if (isfinite(pos[0] + pos[1] + pos[2])) box_update_one(*Pp, pos, nn, false);
+    __syncthreads();
   }
 }
 

@@ -1110,6 +1110,13 @@ cudaError_t run_passes(const PoissonPlan& p, PassArgs<R>& a, double bjerrum, cud
 
 }  // namespace
 
+int poisson_kernel_count(const PoissonPlan& p, bool fp32) {
+  if (fp32 && fast_edge(p.nx) && fast_edge(p.ny) && fast_edge(p.nz) && plane_edge(p.ny) &&
+      plane_edge(p.nz))
+    return 3;  // x, the y-z plane kernel, inverse x
+  return 5;    // x, y, z (with the Green multiply and the inverse z), inverse y, inverse x
+}
+
 cudaError_t poisson_solve(const PoissonPlan& p, const double* q, const double* rho,
                           const double* qwall, const double* qpart, const Phys& ph,
                           double* phi, double2* spectrum, cudaStream_t s) {
