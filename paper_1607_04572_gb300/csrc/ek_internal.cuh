@@ -82,6 +82,7 @@ struct DevParticle {
   int ipos[3];
   float fpos[3], fposlo[3];  // fraction of the centre as a float pair (hi + lo)
   float r2f, r2lo, psimargin;  // R^2 (the FP64 product) as a float pair
+  float velf[3], omegaf[3];    // vel and omega rounded to float (FP32-form wall velocity)
 };
 
 // cells added to ceil(R) around a particle's box for the region whose solute

@@ -339,14 +339,16 @@ __device__ __forceinline__ void lb32_node(const LBRing<K>& t, const LBArgs& a, c
             const int xb = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
             const int yb = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
             const int zb = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
-            const double Xb = (double)(P.lo[0] + wrapi(xb - P.lo[0], nx));
-            const double Yb = (double)(P.lo[1] + wrapi(yb - P.lo[1], ny));
-            const double Zb = (double)(P.lo[2] + wrapi(zb - P.lo[2], nz));
-            const double dx = Xb - P.pos[0], dy = Yb - P.pos[1], dz = Zb - P.pos[2];
-            const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
-            const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
-            const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
-            cvb = (float)cdot(d, vx, vy, vz);
+            // wall velocity at the boundary node in float (it enters the
+            // float population): the offset from the centre as integer part
+            // minus the centre's fraction, the velocities as float copies
+            const float dx = __fsub_rn((float)(P.lo[0] + wrapi(xb - P.lo[0], nx) - P.ipos[0]), P.fpos[0]);
+            const float dy = __fsub_rn((float)(P.lo[1] + wrapi(yb - P.lo[1], ny) - P.ipos[1]), P.fpos[1]);
+            const float dz = __fsub_rn((float)(P.lo[2] + wrapi(zb - P.lo[2], nz) - P.ipos[2]), P.fpos[2]);
+            const float vx = P.velf[0] + (P.omegaf[1] * dz - P.omegaf[2] * dy);
+            const float vy = P.velf[1] + (P.omegaf[2] * dx - P.omegaf[0] * dz);
+            const float vz = P.velf[2] + (P.omegaf[0] * dy - P.omegaf[1] * dx);
+            cvb = cdotf(d, vx, vy, vz);
           }
           (g_out + opp(d) * N)[n] = gsd[h] - 6.0f * (float)wgt(d) * c.rho0 * cvb;
         }

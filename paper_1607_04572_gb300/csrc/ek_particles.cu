@@ -721,7 +721,11 @@ __device__ void radius_forms(DevParticle& P) {
 }
 
 __device__ void box_update_one(DevParticle& P, const double pos[3], const int nn[3], bool setup) {
-  for (int d = 0; d < 3; ++d) box_update_axis(P, d, pos[d], nn[d], setup);
+  for (int d = 0; d < 3; ++d) {
+    box_update_axis(P, d, pos[d], nn[d], setup);
+    P.velf[d] = (float)P.vel[d];
+    P.omegaf[d] = (float)P.omega[d];
+  }
   radius_forms(P);
 }
 
@@ -811,6 +815,8 @@ __device__ void integrate_all(const PartArgs& a) {
         Pp->pos[d] = pos;
         Pp->vel[d] = vel;
         Pp->omega[d] = omega;
+        Pp->velf[d] = (float)vel;
+        Pp->omegaf[d] = (float)omega;
         // S5 starts here: the boxes follow the new position
         Pp->kelo[d] = Pp->elo[d];
         Pp->kehi[d] = Pp->ehi[d];
