@@ -696,7 +696,14 @@ __device__ void box_update_axis(DevParticle& P, int d, double pos, int nn, bool 
   const int lo = (int)floor(pos - P.radius) - 1;
   const int hi = (int)floor(pos + P.radius) + 2;
   int olo = P.lo[d], ohi = P.hi[d];
-  const int shift = (int)rint((double)(lo - olo) / (double)nn) * nn;
+  // shift = rint((lo - olo) / nn) nn, in integers (ties to even): the
+  // quotient of two integers with nn <= 1024 lies at least 1 / 2048 from any
+  // half-integer it is not, so rounding it first would change nothing
+  const int k = lo - olo;
+  int q = k >= 0 ? k / nn : -((nn - 1 - k) / nn);  // floor(k / nn)
+  const int r = k - q * nn;                         // in [0, nn)
+  if (2 * r > nn || (2 * r == nn && (q & 1))) ++q;
+  const int shift = q * nn;
   olo += shift;
   ohi += shift;
   P.ulo[d] = setup ? lo : min(lo, olo);

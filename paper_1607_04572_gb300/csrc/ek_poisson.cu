@@ -497,20 +497,31 @@ __global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
   // the stores go through no pointer the loads could alias, so the latencies
   // overlap instead of adding up
   if constexpr (VEC) {
-    // four consecutive x of one row pair per item (PPC * NX / 4 <= FAST_XT items)
-    static_assert(NX % 4 == 0 && PPC * NX / 4 <= FAST_XT, "one vector item per thread");
-    const int t = threadIdx.x;
-    if (t < PPC * NX / 4) {
+    // four consecutive x of one row pair per item
+    static_assert(NX % 4 == 0, "16-byte items");
+    constexpr int NV = PPC * NX / 4, PER = (NV + FAST_XT - 1) / FAST_XT;
+    float4 re[PER], im[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int t = threadIdx.x + q * FAST_XT;
       const int l = t / (NX / 4), x = 4 * (t - l * (NX / 4));
       const int r0 = 2 * (p0 + l), r1 = r0 + 1;
-      float4 re = make_float4(0.0f, 0.0f, 0.0f, 0.0f), im = re;
-      if (r0 < nrows) re = charge_at4(a, (long long)r0 * NX + x, N);
-      if (r1 < nrows) im = charge_at4(a, (long long)r1 * NX + x, N);
-      float2* d = &buf[0][l * LS + fpad(x)];  // x .. x + 3 lie in one padding group of 16
-      d[0] = make_float2(re.x, im.x);
-      d[1] = make_float2(re.y, im.y);
-      d[2] = make_float2(re.z, im.z);
-      d[3] = make_float2(re.w, im.w);
+      re[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      im[q] = re[q];
+      if (t < NV && r0 < nrows) re[q] = charge_at4(a, (long long)r0 * NX + x, N);
+      if (t < NV && r1 < nrows) im[q] = charge_at4(a, (long long)r1 * NX + x, N);
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int t = threadIdx.x + q * FAST_XT;
+      if (t < NV) {
+        const int l = t / (NX / 4), x = 4 * (t - l * (NX / 4));
+        float2* d = &buf[0][l * LS + fpad(x)];  // x .. x + 3 lie in one padding group of 16
+        d[0] = make_float2(re[q].x, im[q].x);
+        d[1] = make_float2(re[q].y, im[q].y);
+        d[2] = make_float2(re[q].z, im[q].z);
+        d[3] = make_float2(re[q].w, im[q].w);
+      }
     }
   } else {
     constexpr int PER = (PPC * NX + FAST_XT - 1) / FAST_XT;
