@@ -186,6 +186,27 @@ ek_status ek_get_particles(ek_ctx* ctx, ek_particle* dst, int count);
 ek_status ek_get_particles_async(ek_ctx* ctx, ek_particle* dst, int count);
 int ek_num_particles(const ek_ctx* ctx);
 
+/* Checkpoint and resume (the paper has no counterpart; the state is what a
+ * time step of Sec. III reads).  ek_get_state: with buf == NULL, *bytes
+ * receives the size of a checkpoint; otherwise buf (host memory of *bytes
+ * bytes, caller owned) receives the checkpoint and *bytes its size.  The
+ * checkpoint holds a header (shape, species, storage form, flags, particle
+ * count and box size, species units, E, body force) and, as stored on the
+ * device, both population buffers, the species, Psi, particle
+ * and wall charge, Phi, u, node owners, the wall mask and the particles'
+ * records and Psi_p boxes.  Waits for the context's work.  Errors: EK_ERR_ARG
+ * (null bytes; buffer smaller than the checkpoint, *bytes then holds the size
+ * needed), EK_ERR_CUDA, and the device status of ek_sync. */
+ek_status ek_get_state(ek_ctx* ctx, void* buf, size_t* bytes);
+/* Restore a checkpoint into a context created with the same parameters and
+ * particles (any number of steps later, or a fresh context): the steps that
+ * follow give bit for bit what the checkpointed context's next steps give.
+ * buf is host memory of `bytes` bytes, read only during the call.  Errors:
+ * EK_ERR_ARG (null, too short, not a checkpoint of this library version),
+ * EK_ERR_STATE (a checkpoint of a different system: shape, species, storage
+ * form, flags, particle count or box size, species units), EK_ERR_CUDA. */
+ek_status ek_set_state(ek_ctx* ctx, const void* buf, size_t bytes);
+
 /* Run nsteps steps like ek_step, recording CUDA events on the context's stream
  * between the stages, and add the device time of each to stage_ms (caller
  * owned, 6 doubles): [0] S1 Poisson, [1] S2 fused flux/LB kernel, [2] S3

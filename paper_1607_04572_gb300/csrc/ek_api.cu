@@ -532,6 +532,69 @@ size_t field_size(const ek_ctx* ctx, ek_field w) {
   }
 }
 
+// Checkpoint layout: a header, then the device arrays a step reads, each as
+// stored (both population buffers, the species of the current one, Psi,
+// particle and wall charge, Phi, u, node owners, wall mask, the particles'
+// Psi_p boxes and records).  Scratch that every step rewrites before reading
+// it (spectrum, internal force, sign bytes, assignment keys, S4 partial sums,
+// transfer lists) is not part of it.
+constexpr unsigned long long STATE_MAGIC = 0x3130545341454b45ull;
+constexpr int STATE_VERSION = 1;
+
+struct StateHeader {
+  unsigned long long magic;
+  int version;
+  int nx, ny, nz, nspecies, fp32, P, boxmax;
+  unsigned flags;
+  double E[3], g[3];
+  double qscale[EK_MAX_SPECIES];
+};
+
+struct StateArray {
+  void* dev;
+  size_t bytes;
+};
+
+std::vector<StateArray> state_arrays(ek_ctx* ctx) {
+  const size_t N = (size_t)ctx->g.N, rs = ctx->rsz, K = (size_t)ctx->p.nspecies;
+  const size_t ss = ctx->fp32 ? sizeof(int) : sizeof(double);
+  // both population buffers: push streaming never writes the populations of
+  // boundary nodes, so the other buffer keeps values of two steps back there
+  return {{ctx->f[ctx->cur], 19 * N * rs},
+          {ctx->f[1 - ctx->cur], 19 * N * rs},
+          {ctx->rho[ctx->cur], K * N * ss},
+          {ctx->psi, N * rs},
+          {ctx->qpart, N * rs},
+          {ctx->qwall, N * rs},
+          {ctx->phi, N * rs},
+          {ctx->u, 3 * N * rs},
+          {ctx->owner, N * sizeof(int)},
+          {ctx->wall, N},
+          {ctx->psibox, (size_t)ctx->P * (size_t)ctx->boxmax * sizeof(double)},
+          {ctx->dparts, (size_t)ctx->P * sizeof(DevParticle)}};
+}
+
+StateHeader state_header(const ek_ctx* ctx) {
+  StateHeader h;
+  memset(&h, 0, sizeof(h));
+  h.magic = STATE_MAGIC;
+  h.version = STATE_VERSION;
+  h.nx = ctx->g.nx;
+  h.ny = ctx->g.ny;
+  h.nz = ctx->g.nz;
+  h.nspecies = ctx->p.nspecies;
+  h.fp32 = ctx->fp32;
+  h.P = ctx->P;
+  h.boxmax = ctx->boxmax;
+  h.flags = ctx->p.flags;
+  for (int d = 0; d < 3; ++d) {
+    h.E[d] = ctx->ph.E[d];
+    h.g[d] = ctx->ph.g[d];
+  }
+  for (int k = 0; k < EK_MAX_SPECIES; ++k) h.qscale[k] = ctx->ph.qscale[k];
+  return h;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1037,6 +1100,77 @@ ek_status ek_get_particles_async(ek_ctx* ctx, ek_particle* dst, int count) {
   EK_CUDA(cudaGetLastError());
   EK_CUDA(cudaMemcpyAsync(dst, ctx->pstage, (size_t)n * sizeof(ek_particle), cudaMemcpyDefault,
                           ctx->stream));
+  return EK_OK;
+}
+
+ek_status ek_get_state(ek_ctx* ctx, void* buf, size_t* bytes) {
+  if (!ctx || !bytes) return EK_ERR_ARG;
+  ek_status st = ready(ctx);
+  if (st != EK_OK) return st;
+  const std::vector<StateArray> arrays = state_arrays(ctx);
+  size_t total = sizeof(StateHeader);
+  for (const StateArray& a : arrays) total += a.bytes;
+  if (!buf) {
+    *bytes = total;
+    return EK_OK;
+  }
+  if (*bytes < total) {
+    *bytes = total;
+    return fail(ctx, EK_ERR_ARG, "checkpoint buffer too small");
+  }
+  const StateHeader h = state_header(ctx);
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  memcpy(out, &h, sizeof(h));
+  size_t off = sizeof(h);
+  for (const StateArray& a : arrays) {
+    if (a.bytes) EK_CUDA(cudaMemcpyAsync(out + off, a.dev, a.bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    off += a.bytes;
+  }
+  EK_CUDA(cudaStreamSynchronize(ctx->stream));
+  *bytes = total;
+  return check_status(ctx);
+}
+
+ek_status ek_set_state(ek_ctx* ctx, const void* buf, size_t bytes) {
+  if (!ctx || !buf) return EK_ERR_ARG;
+  ek_status st = ready(ctx);  // a pending set-up must not overwrite the restored state later
+  if (st != EK_OK) return st;
+  StateHeader h;
+  if (bytes < sizeof(h)) return fail(ctx, EK_ERR_ARG, "not a checkpoint (too short)");
+  memcpy(&h, buf, sizeof(h));
+  if (h.magic != STATE_MAGIC || h.version != STATE_VERSION)
+    return fail(ctx, EK_ERR_ARG, "not a checkpoint of this library version");
+  const StateHeader mine = state_header(ctx);
+  bool same = h.nx == mine.nx && h.ny == mine.ny && h.nz == mine.nz && h.nspecies == mine.nspecies &&
+              h.fp32 == mine.fp32 && h.P == mine.P && h.boxmax == mine.boxmax && h.flags == mine.flags;
+  for (int k = 0; k < EK_MAX_SPECIES; ++k) same = same && h.qscale[k] == mine.qscale[k];
+  if (!same)
+    return fail(ctx, EK_ERR_STATE,
+                "checkpoint of a different system (shape, species, storage form, flags, particle "
+                "count or size, or species units)");
+  const std::vector<StateArray> arrays = state_arrays(ctx);
+  size_t total = sizeof(StateHeader);
+  for (const StateArray& a : arrays) total += a.bytes;
+  if (bytes < total) return fail(ctx, EK_ERR_ARG, "checkpoint truncated");
+  EK_CUDA(cudaStreamSynchronize(ctx->stream));
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  size_t off = sizeof(h);
+  for (const StateArray& a : arrays) {
+    if (a.bytes) EK_CUDA(cudaMemcpyAsync(a.dev, in + off, a.bytes, cudaMemcpyHostToDevice, ctx->stream));
+    off += a.bytes;
+  }
+  EK_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int d = 0; d < 3; ++d) {
+    ctx->ph.E[d] = h.E[d];
+    ctx->ph.g[d] = h.g[d];
+  }
+  if (ctx->P) {
+    // the particle records are the last array
+    ctx->hparts.resize(ctx->P);
+    memcpy(ctx->hparts.data(), in + off - (size_t)ctx->P * sizeof(DevParticle),
+           (size_t)ctx->P * sizeof(DevParticle));
+  }
+  drop_graphs(ctx);  // E and the body force are launch arguments of the captured steps
   return EK_OK;
 }
 

@@ -44,7 +44,7 @@ STATUS = {0: "EK_OK", -1: "EK_ERR_ARG", -2: "EK_ERR_NOMEM", -3: "EK_ERR_CUDA",
 # entry points declared in include/ek.h
 EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get_fields",
            "ek_step", "ek_step_async", "ek_run_stage", "ek_get_particles", "ek_get_particles_async",
-           "ek_num_particles",
+           "ek_num_particles", "ek_get_state", "ek_set_state",
            "ek_set_stream", "ek_sync", "ek_last_error", "ek_lattice_dirs",
            "ek_poisson_scratch_bytes", "ek_poisson_solve", "ek_step_timed",
            "ek_kernel_launches", "ek_poisson_solve_static",
@@ -103,6 +103,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ek_get_particles_async.argtypes = [vp, vp, ip]
     lib.ek_num_particles.argtypes = [vp]
     lib.ek_num_particles.restype = ip
+    lib.ek_get_state.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.ek_set_state.argtypes = [vp, vp, ctypes.c_size_t]
     lib.ek_set_stream.argtypes = [vp, vp]
     lib.ek_sync.argtypes = [vp]
     lib.ek_last_error.argtypes = [vp]
@@ -276,6 +278,19 @@ class EKSystem:
 
     def num_particles(self):
         return self.lib.ek_num_particles(self.ctx)
+
+    def get_state(self) -> np.ndarray:
+        """A checkpoint of the system (ek_get_state) as a uint8 array."""
+        n = ctypes.c_size_t(0)
+        self._check(self.lib.ek_get_state(self.ctx, None, ctypes.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        self._check(self.lib.ek_get_state(self.ctx, ctypes.c_void_p(buf.ctypes.data), ctypes.byref(n)))
+        return buf
+
+    def set_state(self, buf):
+        """Restore a checkpoint from get_state (ek_set_state)."""
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(self.lib.ek_set_state(self.ctx, ctypes.c_void_p(b.ctypes.data), b.nbytes))
 
     def get_particles_async(self, buf):
         """Enqueue a copy of the particle records into `buf`, a page-locked
