@@ -47,6 +47,27 @@ LB_FP64_FLOP_PER_NODE = 950
 # the same for the FP32-storage kernel (k_lb32_tiled): float populations,
 # int32 species, float Psi / Phi / u / internal force
 LB32_BYTES_PER_NODE = 2 * 19 * 4 + 2 * 2 * 4 + 4 + 4 + 4 + 3 * 4 + 3 * 4 + 1  # 205
+# Algorithmic bytes per node of a whole step (S1-S5), the state read once and
+# written once with every intermediate fused: populations read + written,
+# species read + written, Psi and the node class read, Phi written (S1) and read
+# (S2), the charge written and read, one round trip of the half spectrum.  The
+# stored u, the extra FFT passes and the particle boxes count against it.
+def step_bytes_per_node(fp32, K):
+    if fp32:
+        return 2 * 19 * 4 + 2 * K * 4 + 5 + 8 + 8 + 8      # 197 for K = 2
+    return 2 * 19 * 8 + 2 * K * 8 + 9 + 16 + 16 + 16       # 393 for K = 2
+
+
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
+def step_roofline(mlups, bytes_per_node, hbm_peak):
+    gbs = mlups * 1e6 * bytes_per_node / 1e9
+    return {"bytes_per_node": bytes_per_node, "achieved": round(gbs, 1), "unit": "GB/s",
+            "peak": hbm_peak, "frac": round(gbs / hbm_peak, 4), "nominal_peak": NOMINAL_HBM_GBS,
+            "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4)}
+
+
 # FP64 peak derived from the unit counts: 152 SMs x 2.07 GHz x 4 flop/clk/SM
 # (2 DFMA per clock per SM); a DFMA probe on this pool measured 1.19 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
@@ -332,11 +353,15 @@ def main():
                      "peak_kind": peak_kind, "traffic": traffic("k_lb32"),
                      "algorithmic_bytes": LB32_BYTES_PER_NODE * nodes,
                      "kernel_ms": round(r32["lb_ms"], 4)},
+        "step_roofline": step_roofline(r32["value"], step_bytes_per_node(True, len(w["valence"])),
+                                       hbm_peak),
         "stages_ms_per_step": r32["stages"],
         "fp64_form": {
             "value": round(r64["value"], 3), "unit": "MLUPS",
             "ms_per_step": round(r64["ms"] / args.steps, 4), "stages_ms_per_step": r64["stages"],
             "gpu_launches": r64["launches"], "clocks": r64["clocks"],
+            "step_roofline": step_roofline(r64["value"], step_bytes_per_node(False, len(w["valence"])),
+                                           hbm_peak),
             "roofline": {"bound": "alu", "kernel": "k_lb_fused", "achieved": round(tflops64, 4),
                          "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s (FP64)",
                          "frac": round(tflops64 / FP64_PEAK_TFLOPS, 4),
@@ -351,6 +376,7 @@ def main():
         "clocks": r32["clocks"],
     }
     if rb is not None:
+        rb["step_roofline"] = step_roofline(rb["value"], step_bytes_per_node(True, 2), hbm_peak)
         line["batched_form"] = rb
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, done, dt = time_oracle(w, 3, budget_s=20.0, warmup=0)
