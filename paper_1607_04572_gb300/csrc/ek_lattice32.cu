@@ -432,63 +432,83 @@ __device__ __forceinline__ int sgnf(float v) { return v > 0.0f ? 1 : (v < 0.0f ?
 
 // S3 (FP32 form): the node pulls the shares its 26 neighbours send it and
 // gives away its own; the per-node sign byte of S2 decides which neighbours
-// send anything before any of their data is loaded.
+// send anything before any of their data is loaded.  Node indices are 32-bit
+// (N < 2^31) from per-array base pointers and the three x, row and plane
+// offsets of the neighbourhood; every loop is unrolled, so the sign tests use
+// constant masks.  Each share is computed with the same operations as in its
+// source, and integer sums do not depend on their order.
 template <int K>
 __global__ void __launch_bounds__(256) k_advect32(LBArgs a, Phys32 c) {
-  const int* __restrict__ n_in = (const int*)a.rho_in;
-  int* __restrict__ n_out = (int*)a.rho_out;
-  const float* __restrict__ u = (const float*)a.u;
-  const unsigned char* __restrict__ vs = a.vsig;
-  const size_t N = (size_t)a.g.N;
   const int nx = a.g.nx, ny = a.g.ny;
   const int x = blockIdx.x * TILE_X + threadIdx.x;
   const int y = blockIdx.y * TILE_Y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= nx || y >= ny) return;
+  const unsigned char* __restrict__ vs = a.vsig;
   const int n = x + nx * (y + ny * z);
   if (!(vs[n] & 0x80u)) return;
-  const Nbr b = make_nbr(x, y, z, a.g);
-  int acc[K];
-  float rs[K];
+  const int N = (int)a.g.N;
+  const float* __restrict__ ux = (const float*)a.u;
+  const float* __restrict__ uy = ux + N;
+  const float* __restrict__ uz = uy + N;
+  const int* nin[K > 0 ? K : 1];
+  int* nout[K > 0 ? K : 1];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    acc[k] = (n_out + k * N)[n];
-    rs[k] = (float)(n_in + k * N)[n];
+    nin[k] = (const int*)a.rho_in + (size_t)k * N;
+    nout[k] = (int*)a.rho_out + (size_t)k * N;
   }
-  const float ux = u[n], uy = (u + N)[n], uz = (u + 2 * N)[n];
-  const int sx = sgnf(ux), sy = sgnf(uy), sz = sgnf(uz);
-  for (int oz = 0; oz <= (sz != 0); ++oz) {
-    for (int oy = 0; oy <= (sy != 0); ++oy) {
-      for (int ox = 0; ox <= (sx != 0); ++ox) {
-        if (!ox && !oy && !oz) continue;
-        const int m = nb_x(b, x, ox ? sx : 0) + nx * (nb_y(b, y, oy ? sy : 0) + ny * nb_z(b, z, oz ? sz : 0));
-        if (!(vs[m] & 0x80u)) continue;  // share aimed at a boundary stays here
-        const float frac = vof_share(ux, uy, uz, ox, oy, oz);
+  const Nbr b = make_nbr(x, y, z, a.g);
+  const int nxy = nx * ny;
+  const int X0 = b.xm, X1 = x, X2 = b.xp;
+  const int Y0 = nx * b.ym, Y1 = nx * y, Y2 = nx * b.yp;
+  const int Z0 = nxy * b.zm, Z1 = nxy * z, Z2 = nxy * b.zp;
+  int acc[K > 0 ? K : 1];
+  float rs[K > 0 ? K : 1];
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] -= __float2int_rn(__fmul_rn(rs[k], frac));
-      }
-    }
+  for (int k = 0; k < K; ++k) {
+    acc[k] = nout[k][n];
+    rs[k] = (float)nin[k][n];
   }
+  const float vx = ux[n], vy = uy[n], vz = uz[n];
+  const int sx = sgnf(vx), sy = sgnf(vy), sz = sgnf(vz);
+  // the node's own shares to offsets (ox, oy, oz) in {0, sign(v_a)}^3
+  const int xs = sx > 0 ? X2 : (sx < 0 ? X0 : X1);
+  const int ys = sy > 0 ? Y2 : (sy < 0 ? Y0 : Y1);
+  const int zs = sz > 0 ? Z2 : (sz < 0 ? Z0 : Z1);
+#pragma unroll
+  for (int o = 1; o < 8; ++o) {
+    const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+    if ((ox && !sx) || (oy && !sy) || (oz && !sz)) continue;
+    const int m = (ox ? xs : X1) + (oy ? ys : Y1) + (oz ? zs : Z1);
+    if (!(vs[m] & 0x80u)) continue;  // share aimed at a boundary stays here
+    const float frac = vof_share(vx, vy, vz, ox, oy, oz);
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] -= __float2int_rn(__fmul_rn(rs[k], frac));
+  }
+  // shares from the neighbour at -q: fluid and moving towards this node along
+  // every nonzero component of q
+#pragma unroll
   for (int qz = -1; qz <= 1; ++qz) {
+#pragma unroll
     for (int qy = -1; qy <= 1; ++qy) {
+#pragma unroll
       for (int qx = -1; qx <= 1; ++qx) {
         if (!qx && !qy && !qz) continue;
-        // the source must be fluid and move towards this node along every nonzero q
         const unsigned mask = 0x80u | (qx ? 3u : 0u) | (qy ? 12u : 0u) | (qz ? 48u : 0u);
         const unsigned want = 0x80u | (qx > 0 ? 1u : (qx < 0 ? 2u : 0u)) |
                               (qy > 0 ? 4u : (qy < 0 ? 8u : 0u)) | (qz > 0 ? 16u : (qz < 0 ? 32u : 0u));
-        const int m = nb_x(b, x, -qx) + nx * (nb_y(b, y, -qy) + ny * nb_z(b, z, -qz));
+        const int m = (qx > 0 ? X0 : (qx < 0 ? X2 : X1)) + (qy > 0 ? Y0 : (qy < 0 ? Y2 : Y1)) +
+                      (qz > 0 ? Z0 : (qz < 0 ? Z2 : Z1));
         if ((vs[m] & mask) != want) continue;
-        const float vx = u[m], vy = (u + N)[m], vz = (u + 2 * N)[m];
-        const float frac = vof_share(vx, vy, vz, qx != 0, qy != 0, qz != 0);
+        const float frac = vof_share(ux[m], uy[m], uz[m], qx != 0, qy != 0, qz != 0);
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-          acc[k] += __float2int_rn(__fmul_rn((float)(n_in + k * N)[m], frac));
+        for (int k = 0; k < K; ++k) acc[k] += __float2int_rn(__fmul_rn((float)nin[k][m], frac));
       }
     }
   }
 #pragma unroll
-  for (int k = 0; k < K; ++k) (n_out + k * N)[n] = acc[k];
+  for (int k = 0; k < K; ++k) nout[k][n] = acc[k];
 }
 
 __global__ void k_fill32(Grid g, const int* owner, float* f, int* rho, int K, float rho0, int n0,
