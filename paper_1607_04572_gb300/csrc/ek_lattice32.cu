@@ -66,11 +66,20 @@ Phys32 make_phys32(const Phys& ph) {
   return p;
 }
 
-__device__ __forceinline__ int nbr32(int d, int x, int y, int z, const Nbr& b, int nx, int ny) {
-  const int X = dcx(d) > 0 ? b.xp : (dcx(d) < 0 ? b.xm : x);
-  const int Y = dcy(d) > 0 ? b.yp : (dcy(d) < 0 ? b.ym : y);
-  const int Z = dcz(d) > 0 ? b.zp : (dcz(d) < 0 ? b.zm : z);
-  return X + nx * (Y + ny * Z);
+// The neighbourhood of a node as its three x coordinates, row offsets and
+// plane offsets (periodic, 32-bit: N < 2^31): a neighbour's index is one
+// three-operand add.
+struct Off3 {
+  int X0, X1, X2, Y0, Y1, Y2, Z0, Z1, Z2;
+};
+__device__ __forceinline__ Off3 make_off3(const Nbr& b, int x, int y, int z, int nx, int ny) {
+  const int nxy = nx * ny;
+  return {b.xm, x, b.xp, nx * b.ym, nx * y, nx * b.yp, nxy * b.zm, nxy * z, nxy * b.zp};
+}
+__device__ __forceinline__ int nbr32(int d, const Off3& o) {
+  return (dcx(d) > 0 ? o.X2 : (dcx(d) < 0 ? o.X0 : o.X1)) +
+         (dcy(d) > 0 ? o.Y2 : (dcy(d) < 0 ? o.Y0 : o.Y1)) +
+         (dcz(d) > 0 ? o.Z2 : (dcz(d) < 0 ? o.Z0 : o.Z1));
 }
 
 // block total of the per-thread sums: warps in float (32 threads, each over
@@ -211,6 +220,7 @@ __device__ __forceinline__ void lb32_node(const LBRing<K>& t, const LBArgs& a, c
   const int e0 = ex + HX * ey;
   const int n = x + nx * (y + ny * z);
   const Nbr b = make_nbr(x, y, z, a.g);
+  const Off3 nb = make_off3(b, x, y, z, nx, ny);
   if (!SIMPLE && t.own[sl[1]][e0] != FLUID) {
     a.vsig[n] = 0;
 #pragma unroll
@@ -330,7 +340,7 @@ __device__ __forceinline__ void lb32_node(const LBRing<K>& t, const LBArgs& a, c
       for (int h = 0; h < 2; ++h) {
         const int d = i + h;
         if (fluid & (1u << d)) {
-          (g_out + d * N)[nbr32(d, x, y, z, b, nx, ny)] = gsd[h];
+          (g_out + d * N)[nbr32(d, nb)] = gsd[h];
         } else {
           float cvb = 0.0f;
           const int om = t.own[sl[1 + dcz(d)]][e0 + dcx(d) + HX * dcy(d)];
