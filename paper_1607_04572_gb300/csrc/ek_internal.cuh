@@ -70,7 +70,9 @@ struct DevParticle {
   double force[3], torque[3];
   double ftrans[3];  // create/destroy momentum of the last S5, applied at the next S4
   double radius, charge, mass, inertia;
-  double psisum;     // sum of Psi_p over the particle's box
+  // sum of Psi_p over the particle's box in units of 2^-13 (exact), in eight
+  // partial sums (one per octant of the surface cells) that take the atomics
+  unsigned long long psiunits[8];
   int nb;            // number of boundary nodes
   int fixed;
   int lo[3], hi[3];  // box [lo, hi) in unwrapped coordinates, current position

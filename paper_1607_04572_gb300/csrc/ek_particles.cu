@@ -164,6 +164,14 @@ __device__ __forceinline__ int classify_f2(float ax, float ay, float az, float h
 // any order.
 constexpr int PSI_UNITS = 8192;
 
+// sum of Psi_p over the particle's box (counts of 2^-13 units: exact)
+__device__ __forceinline__ double psi_sum(const DevParticle& P) {
+  unsigned long long u = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) u += P.psiunits[j];
+  return (double)u / (double)PSI_UNITS;
+}
+
 // relative (float) and exact (double) centre of sub-cube `path` at level l of
 // the cell centred at (X, Y, Z); path holds 3 bits per level, level 1 highest
 __device__ __forceinline__ void subcube_centre_f(int path, int l, float ox, float oy, float oz,
@@ -441,7 +449,7 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   if (pv) {
     qnorm = (a.ph.flags & EK_CHARGE_NORM_VP)
                 ? P.charge / (4.0 / 3.0 * M_PI * P.radius * P.radius * P.radius)
-                : (P.psisum > 0.0 ? P.charge / P.psisum : 0.0);
+                : (psi_sum(P) > 0.0 ? P.charge / psi_sum(P) : 0.0);
   } else {
     qnorm = P.nb > 0 ? P.charge / (double)P.nb : 0.0;
   }
@@ -853,14 +861,14 @@ __global__ void k_box_update(PartArgs a) {
   const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
   const double pos[3] = {P.pos[0], P.pos[1], P.pos[2]};
   box_update_one(P, pos, nn, true);
-  P.psisum = 0.0;
+  for (int j = 0; j < 8; ++j) P.psiunits[j] = 0;
   P.nb = 0;
 }
 
 __global__ void k_save_prev(PartArgs a) {
   DevParticle& P = a.parts[blockIdx.x];
   if (blockIdx.y == 0 && threadIdx.x == 0) {  // k_claim and k_psi_surface sum these afresh
-    P.psisum = 0.0;
+    for (int j = 0; j < 8; ++j) P.psiunits[j] = 0;
     P.nb = 0;
   }
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
@@ -930,7 +938,7 @@ __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
   const int nin = __syncthreads_count(ps != 0.0);
   const int nbd = __syncthreads_count(inside);
   if (threadIdx.x == 0) {
-    if (nin) atomicAdd(&P.psisum, (double)nin);  // integers: exact in any order
+    if (nin) atomicAdd(&P.psiunits[0], (unsigned long long)nin * PSI_UNITS);
     if (nbd) atomicAdd(&P.nb, nbd);
   }
 }
@@ -1059,7 +1067,9 @@ __global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
       const long long n = node_of(X, Y, Z, a.g);
       atomicAdd(a.psibox + (long long)pc.x * a.boxmax + pc.y, ps);
       real_add<FM>(a.psi, n, ps);
-      atomicAdd(&P.psisum, ps);
+      // integer counts, spread over eight addresses (the total of one
+      // particle would otherwise serialise the atomics of all its cells)
+      atomicAdd(&P.psiunits[oct], (unsigned long long)units);
     }
     __syncwarp();
   }
@@ -1085,7 +1095,7 @@ __global__ void k_charge_scatter(PartArgs a) {
     if (a.ph.flags & EK_CHARGE_NORM_VP)
       q = P.charge * ps / (4.0 / 3.0 * M_PI * P.radius * P.radius * P.radius);
     else
-      q = P.charge * ps / P.psisum;
+      q = P.charge * ps / psi_sum(P);
   } else {
     if (a.owner[n] != p || P.nb == 0) return;
     q = P.charge / (double)P.nb;
