@@ -97,3 +97,45 @@ def test_stokes_drag_hasimoto(gpu_lib, fp32):
     # measured 3.3% (FP64 form); without the periodic correction the two boxes
     # would disagree by 40%
     assert abs(f16 / predicted - 1.0) < 0.05, (f16, predicted, rh)
+
+
+def _channel(ek, fp32, magic, H=14, steps=2000, g=1e-5):
+    """Force-driven flow between bounce-back walls at z = 0 and z = H + 1,
+    started from the exact profile of a wall half-way between the wall node
+    and the first fluid node."""
+    nx, ny, nz = 8, 8, H + 2
+    s = ek.EKSystem((nx, ny, nz), valence=(), D=(), bulk=(), magic=magic, flags=FP32 if fp32 else 0)
+    walls = np.zeros((nz, ny, nx))
+    walls[0] = walls[nz - 1] = 1.0
+    s.set_field(ek.FIELD_WALL, walls.ravel())
+    s.set_field(ek.FIELD_BODY_FORCE, np.array([g, 0.0, 0.0]))
+    nu = 1.0 / 6.0
+    zs = np.arange(1, H + 1, dtype=float)
+    exact = g / (2.0 * nu) * (zs - 0.5) * (H + 0.5 - zs)
+    u0 = np.zeros((3, nz, ny, nx))
+    u0[0, 1:H + 1] = exact[:, None, None]
+    s.set_field(ek.FIELD_VELOCITY, u0.ravel())
+    s.step(steps)
+    u = s.get_fields(ek.FIELD_VELOCITY).reshape(3, nz, ny, nx)
+    assert np.max(np.abs(u[1:])) <= 1e-12 + (2e-6 if fp32 else 1e-14) * exact.max()
+    return u[0, 1:H + 1], exact
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_poiseuille_trt_magic_wall_halfway(gpu_lib, fp32):
+    """TRT with Ginzburg's magic product Lambda = 3/16 (the paper's collision,
+    Sec. III.A) puts the bounce-back wall exactly half-way: the steady profile
+    is the parabola u = g/(2 nu) (z - 1/2)(H + 1/2 - z) to rounding (FP64 form)
+    and to the float resolution of the stored deviations (FP32 form); BGK at
+    tau = 1 (Lambda = 1/4) leaves a small slip."""
+    ek = gpu_lib
+    u, exact = _channel(ek, fp32, 3.0 / 16.0)
+    # laterally uniform, the profile of every column
+    assert np.max(np.abs(u - u.mean(axis=(1, 2), keepdims=True))) <= (1e-4 if fp32 else 1e-12) * exact.max()
+    err = np.max(np.abs(u.mean(axis=(1, 2)) - exact)) / exact.max()
+    # (the FP64 oracle, started the same way, is at 2.1e-10 after 2000 steps:
+    # the start lacks the non-equilibrium part of the populations)
+    assert err < (1e-4 if fp32 else 1e-9), err
+    ub, _ = _channel(ek, fp32, None)
+    errb = np.max(np.abs(ub.mean(axis=(1, 2)) - exact)) / exact.max()
+    assert 5e-4 < errb < 0.05, errb  # the oracle: 1.7e-3
