@@ -870,6 +870,10 @@ __global__ void k_save_prev(PartArgs a) {
   if (blockIdx.y == 0 && threadIdx.x == 0) {  // k_claim and k_psi_surface sum these afresh
     for (int j = 0; j < 8; ++j) P.psiunits[j] = 0;
     P.nb = 0;
+    // the transfer list of the last step's transitions has been applied;
+    // this step's transitions append to an empty one (a kernel of the chain
+    // instead of a memset node after the transfers)
+    if (blockIdx.x == 0) *a.xfer_count = 0;
   }
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
   if (c >= box_cells(P.ulo, P.uhi)) return;
@@ -882,6 +886,8 @@ __global__ void k_save_prev(PartArgs a) {
 template <class FM>
 __global__ void k_clear(PartArgs a) {
   const DevParticle& P = a.parts[blockIdx.x];
+  // the surface-cell list of the last step has been read; k_claim refills it
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *a.surf_count = 0;
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
   if (c >= box_cells(P.ulo, P.uhi)) return;
   int X, Y, Z;
@@ -1284,9 +1290,9 @@ cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s, int pa
   const unsigned uchunks = (unsigned)((edge * edge * edge + PT - 1) / PT);
   if (!(parts & 1)) {
     if (a.P == 0 || !transitions) return cudaSuccess;
+    // (k_save_prev of this step emptied the transfer list)
     k_transitions<FM><<<dim3(a.P, uchunks), PT, 0, s>>>(a);
     k_apply_transfers<FM><<<152, 256, 0, s>>>(a);
-    cudaMemsetAsync(a.xfer_count, 0, sizeof(int), s);
     return cudaGetLastError();
   }
   if (!transitions) {
@@ -1300,14 +1306,13 @@ cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s, int pa
     k_save_prev<<<dim3(a.P, uchunks), PT, 0, s>>>(a);
     k_clear<FM><<<dim3(a.P, uchunks), PT, 0, s>>>(a);
   }
-  cudaMemsetAsync(a.surf_count, 0, sizeof(int), s);
+  if (!transitions) cudaMemsetAsync(a.surf_count, 0, sizeof(int), s);  // else k_clear resets it
   k_claim<FM><<<dim3(a.P, bchunks), PT, 0, s>>>(a);
   k_psi_surface<FM><<<16 * 152, 32 * PSI_WARPS, 0, s>>>(a);
   k_charge_scatter<FM><<<dim3(a.P, bchunks), PT, 0, s>>>(a);
   if (transitions && (parts & 2)) {
     k_transitions<FM><<<dim3(a.P, uchunks), PT, 0, s>>>(a);
     k_apply_transfers<FM><<<152, 256, 0, s>>>(a);
-    cudaMemsetAsync(a.xfer_count, 0, sizeof(int), s);
   }
   return cudaGetLastError();
 }
