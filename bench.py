@@ -98,16 +98,21 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock samples during the timed region."""
+    """nvidia-smi clock samples around the timed region: started (and waited
+    for) before it, stopped a little after it; the samples whose timestamps
+    fall within MARGIN seconds of the region are kept (a short region can lie
+    between two samples)."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    MARGIN = 0.25
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -115,24 +120,41 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            deadline = time.time() + 5.0
+            while time.time() < deadline and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(self.MARGIN)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        import datetime
         rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) >= 9:
-                rows.append(f)
+            if len(f) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            if self.t0 is None or self.t0 - self.MARGIN <= ts <= self.t1 + self.MARGIN:
+                rows.append(f[1:])
         os.unlink(self.path)
         if not rows:
             return None
@@ -146,7 +168,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows),
+                "window_s": round(self.t1 - self.t0 + 2 * self.MARGIN, 3) if self.t0 else None}
 
 
 def build_system(ek, w, fp32=True):
@@ -273,10 +296,12 @@ def main():
         launches0 = s.kernel_launches()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
+        clk.mark(True)
         ev0.record(stream)
         s.step_async(args.steps)
         ev1.record(stream)
         ev1.synchronize()
+        clk.mark(False)
         barrier()
         clocks = clk.stop()
         launches = s.kernel_launches() - launches0
@@ -375,6 +400,8 @@ def main():
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
     }
+    if rank == 0 and ws == 1 and not args.no_batch:
+        line["poisson_mg"] = measure_poisson_mg(ek, torch)
     if rb is not None:
         rb["step_roofline"] = step_roofline(rb["value"], step_bytes_per_node(True, 2), hbm_peak)
         line["batched_form"] = rb
@@ -388,6 +415,55 @@ def main():
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+# Multigrid V-cycle traffic at the finest level, per node (an estimate of the
+# bytes that must cross HBM, intermediates in L2 not subtracted): 8 red-black
+# half-sweeps (read phi and the colour's b, write the colour's phi: 16 B),
+# residual 24, restriction 8, prolongation 17, the residual and its norm
+# after the cycle 32; the coarser levels add an eighth per level.
+MG_BYTES_PER_NODE_CYCLE = round((8 * 16 + 24 + 8 + 17 + 32) * 8 / 7)   # 239
+
+
+def measure_poisson_mg(ek, torch, shape=(128, 128, 128), reps=3):
+    """The periodic Poisson solve of S1 (FP64) by multigrid V-cycles against
+    the FFT solve, on the same seeded charge: time per solve (CUDA events on
+    the solvers' stream, after a warm-up solve), cycles, residual, and the
+    largest difference between the two solutions."""
+    import numpy as np
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    rng = np.random.default_rng(1607)
+    q = torch.tensor(rng.random(n) - 0.5, device="cuda", dtype=torch.float64)
+    phi_mg = torch.empty_like(q)
+    phi_fft = torch.empty_like(q)
+    scratch = torch.empty(ek.poisson_mg_scratch_bytes(shape), dtype=torch.uint8, device="cuda")
+    spectrum = torch.empty(ek.load_library().ek_poisson_scratch_bytes(nx, ny, nz), dtype=torch.uint8,
+                           device="cuda")
+    st = torch.cuda.Stream()
+    times = {}
+    for name in ("mg", "fft"):
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            if name == "mg":
+                cycles, res = ek.poisson_solve_mg(q, phi_mg, shape, 0.7, scratch, tol=1e-12,
+                                                  max_cycles=50, stream=st)
+            else:
+                ek.poisson_solve(q, phi_fft, shape, 0.7, spectrum, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            if r > 0:
+                times.setdefault(name, []).append(e0.elapsed_time(e1))
+    ms = min(times["mg"])
+    diff = (phi_mg - phi_fft).abs().max().item() / phi_fft.abs().max().item()
+    gbs = MG_BYTES_PER_NODE_CYCLE * n * cycles / (ms / 1e3) / 1e9
+    return {"shape": list(shape), "ms": round(ms, 4), "cycles": cycles, "residual": res,
+            "ms_per_cycle": round(ms / max(cycles, 1), 4), "fft_ms": round(min(times["fft"]), 4),
+            "max_rel_diff_vs_fft": diff,
+            "bytes_per_node_cycle": MG_BYTES_PER_NODE_CYCLE, "achieved_gbs": round(gbs, 1),
+            "note": "FP64; every V-cycle's residual norm is read on the host to test convergence"}
 
 
 def measure_batch(ek, torch, args, barrier, max_over_ranks):

@@ -243,6 +243,28 @@ size_t ek_poisson_scratch_bytes(int nx, int ny, int nz);
 ek_status ek_poisson_solve(const double* q, double* phi, int nx, int ny, int nz,
                            double bjerrum, void* spectrum, void* stream);
 
+/* The same periodic problem of Eq. 3 solved iteratively (the paper names
+ * iterative solvers as the alternative to the FFT, Sec. III.C): geometric
+ * multigrid V-cycles (two red-black Gauss-Seidel sweeps before and after,
+ * full-weighting restriction, trilinear prolongation) on the box and its
+ * coarsenings by 2 (while every coarse edge stays even and >= 8, n_x / 2
+ * even, and the level holds more than 4096 nodes), the coarsest level solved
+ * exactly by the FFT; cycles until max|r| <= tol * max|b|, b = 4 pi l_B
+ * (q - mean q), r = b - (6 phi - sum of the 6 neighbours), at most max_cycles.
+ * A box that cannot be coarsened is solved by the FFT in one cycle.  phi is
+ * returned with mean 0.  q, phi: device arrays of nx*ny*nz doubles (may
+ * alias); scratch: caller-allocated device memory of at least
+ * ek_poisson_mg_scratch_bytes(nx, ny, nz) bytes; stream: a cudaStream_t or
+ * NULL; *cycles and *residual (max|r| / max|b|), when not NULL, receive the
+ * V-cycles run and the final relative residual.  Waits for the work.
+ * Supported edges as for ek_poisson_solve.  Errors: EK_ERR_ARG (null
+ * pointer, unsupported edges, tol <= 0, max_cycles < 1), EK_ERR_CUDA.
+ * ek_poisson_mg_scratch_bytes returns 0 for unsupported edges. */
+size_t ek_poisson_mg_scratch_bytes(int nx, int ny, int nz);
+ek_status ek_poisson_solve_mg(const double* q, double* phi, int nx, int ny, int nz,
+                              double bjerrum, double tol, int max_cycles, void* scratch,
+                              void* stream, int* cycles, double* residual);
+
 /* The same Poisson solve for callers that cannot allocate device memory:
  * code whose device memory is entirely reserved up front by another runtime's
  * pool (so a raw cudaMalloc would fail), latency-critical loops that must not

@@ -595,6 +595,28 @@ StateHeader state_header(const ek_ctx* ctx) {
   return h;
 }
 
+// FFT plans of the standalone solvers, one per device and shape, kept for
+// the life of the process
+cudaError_t cached_plan(int nx, int ny, int nz, PoissonPlan& plan) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, PoissonPlan> plans;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(dev, nx, ny, nz);
+  auto it = plans.find(key);
+  if (it == plans.end()) {
+    std::string err;
+    PoissonPlan p;
+    e = poisson_plan_create(p, nx, ny, nz, err);
+    if (e != cudaSuccess) return e;
+    it = plans.emplace(key, p).first;
+  }
+  plan = it->second;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1208,28 +1230,34 @@ ek_status ek_poisson_solve(const double* q, double* phi, int nx, int ny, int nz,
   if (!q || !phi || !spectrum || !edge_ok(nx) || !edge_ok(ny) || !edge_ok(nz) || nx % 2 ||
       !(bjerrum >= 0.0))
     return EK_ERR_ARG;
-  static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int>, PoissonPlan> plans;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return EK_ERR_CUDA;
   PoissonPlan plan;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    auto key = std::make_tuple(dev, nx, ny, nz);
-    auto it = plans.find(key);
-    if (it == plans.end()) {
-      std::string err;
-      PoissonPlan p;
-      if (poisson_plan_create(p, nx, ny, nz, err) != cudaSuccess) return EK_ERR_CUDA;
-      it = plans.emplace(key, p).first;
-    }
-    plan = it->second;
-  }
+  if (cached_plan(nx, ny, nz, plan) != cudaSuccess) return EK_ERR_CUDA;
   Phys ph;
   memset(&ph, 0, sizeof(ph));
   ph.bjerrum = bjerrum;
   if (poisson_solve(plan, q, nullptr, nullptr, nullptr, ph, phi, (double2*)spectrum,
                     (cudaStream_t)stream) != cudaSuccess)
+    return EK_ERR_CUDA;
+  return EK_OK;
+}
+
+size_t ek_poisson_mg_scratch_bytes(int nx, int ny, int nz) {
+  if (!edge_ok(nx) || !edge_ok(ny) || !edge_ok(nz) || nx % 2) return 0;
+  return poisson_mg_scratch_bytes(nx, ny, nz);
+}
+
+ek_status ek_poisson_solve_mg(const double* q, double* phi, int nx, int ny, int nz, double bjerrum,
+                              double tol, int max_cycles, void* scratch, void* stream, int* cycles,
+                              double* residual) {
+  if (!q || !phi || !scratch || !edge_ok(nx) || !edge_ok(ny) || !edge_ok(nz) || nx % 2 ||
+      !(bjerrum >= 0.0) || !(tol > 0.0) || max_cycles < 1)
+    return EK_ERR_ARG;
+  int coarse[3];
+  poisson_mg_levels(nx, ny, nz, coarse);
+  PoissonPlan plan;
+  if (cached_plan(coarse[0], coarse[1], coarse[2], plan) != cudaSuccess) return EK_ERR_CUDA;
+  if (poisson_solve_mg(plan, q, phi, nx, ny, nz, bjerrum, tol, max_cycles, scratch,
+                       (cudaStream_t)stream, cycles, residual) != cudaSuccess)
     return EK_ERR_CUDA;
   return EK_OK;
 }

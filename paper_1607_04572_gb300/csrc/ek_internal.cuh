@@ -213,6 +213,14 @@ int poisson_kernel_count(const PoissonPlan& p, bool fp32);
 bool poisson_factor(int n, AxisPlan& P);
 // charge assembly fused into the first FFT pass when rho != nullptr; else q is read.
 // FP64 form: double fields, double2 spectrum.
+// Multigrid solve of the same periodic problem (ek_multigrid.cu): levels down
+// to a coarse grid (dims in coarse[]) that coarse_plan, an FFT plan of those
+// dims, solves exactly; V-cycles until max|r| <= tol max|b|
+size_t poisson_mg_scratch_bytes(int nx, int ny, int nz);
+int poisson_mg_levels(int nx, int ny, int nz, int coarse[3]);
+cudaError_t poisson_solve_mg(const PoissonPlan& coarse_plan, const double* q, double* phi, int nx,
+                             int ny, int nz, double bjerrum, double tol, int max_cycles,
+                             void* scratch, cudaStream_t s, int* cycles, double* residual);
 cudaError_t poisson_solve(const PoissonPlan& p, const double* q, const double* rho,
                           const double* qwall, const double* qpart, const Phys& ph,
                           double* phi, double2* spectrum, cudaStream_t s);

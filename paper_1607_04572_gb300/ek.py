@@ -47,7 +47,8 @@ EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get
            "ek_num_particles", "ek_get_state", "ek_set_state",
            "ek_set_stream", "ek_sync", "ek_last_error", "ek_lattice_dirs",
            "ek_poisson_scratch_bytes", "ek_poisson_solve", "ek_step_timed",
-           "ek_kernel_launches", "ek_poisson_solve_static",
+           "ek_kernel_launches", "ek_poisson_solve_static", "ek_poisson_mg_scratch_bytes",
+           "ek_poisson_solve_mg",
            "ek_batch_create", "ek_batch_destroy", "ek_batch_set_stream", "ek_batch_step_async",
            "ek_batch_step", "ek_batch_sync", "ek_batch_tune", "ek_batch_config", "ek_batch_size",
            "ek_batch_last_error"]
@@ -116,6 +117,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ek_poisson_solve.argtypes = [vp, vp, ip, ip, ip, dp, vp, vp]
     lib.ek_step_timed.argtypes = [vp, ip, ctypes.POINTER(dp)]
     lib.ek_poisson_solve_static.argtypes = [vp, vp, ip, ip, ip, dp, vp]
+    lib.ek_poisson_mg_scratch_bytes.argtypes = [ip, ip, ip]
+    lib.ek_poisson_mg_scratch_bytes.restype = ctypes.c_size_t
+    lib.ek_poisson_solve_mg.argtypes = [vp, vp, ip, ip, ip, dp, dp, ip, vp, vp,
+                                        ctypes.POINTER(ip), ctypes.POINTER(dp)]
     lib.ek_kernel_launches.argtypes = [vp]
     lib.ek_kernel_launches.restype = ctypes.c_longlong
     lib.ek_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
@@ -133,6 +138,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     for name in EXPORTS:
         if name not in ("ek_num_particles", "ek_last_error", "ek_lattice_dirs",
                         "ek_poisson_scratch_bytes", "ek_kernel_launches", "ek_batch_size",
+                        "ek_poisson_mg_scratch_bytes",
                         "ek_batch_last_error"):
             getattr(lib, name).restype = ip
     _lib = lib
@@ -340,6 +346,28 @@ def poisson_solve(q, phi, shape, bjerrum, spectrum, stream=None):
                               ctypes.c_void_p(int(h)))
     if st != 0:
         raise EKError(st, "ek_poisson_solve failed")
+
+
+def poisson_mg_scratch_bytes(shape):
+    return int(load_library().ek_poisson_mg_scratch_bytes(*(int(v) for v in shape)))
+
+
+def poisson_solve_mg(q, phi, shape, bjerrum, scratch, tol=1e-12, max_cycles=50, stream=None):
+    """Multigrid Poisson solve on device tensors (torch, float64; scratch a
+    device tensor of at least poisson_mg_scratch_bytes(shape) bytes): see
+    ek_poisson_solve_mg in include/ek.h.  Returns (V-cycles, relative residual)."""
+    lib = load_library()
+    nx, ny, nz = shape
+    h = 0 if stream is None else getattr(stream, "cuda_stream", stream)
+    cyc = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    st = lib.ek_poisson_solve_mg(ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                                 nx, ny, nz, float(bjerrum), float(tol), int(max_cycles),
+                                 ctypes.c_void_p(scratch.data_ptr()), ctypes.c_void_p(int(h)),
+                                 ctypes.byref(cyc), ctypes.byref(res))
+    if st != 0:
+        raise EKError(st, "ek_poisson_solve_mg failed")
+    return cyc.value, res.value
 
 
 POISSON_STATIC_MAX = 1 << 19  # complex doubles of the fixed scratch of ek_poisson_solve_static
