@@ -36,11 +36,11 @@ struct Level {
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// b = s (q - qmean), qmean = sums[0] / n (sums written by k_sum_final)
+// b = s (q - qmean), qmean = sums[1] (written by k_sum_final)
 __global__ void k_mg_rhs(const double* q, double* b, long long n, double s, const double* sums) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  b[i] = s * (q[i] - sums[0] / (double)n);
+  b[i] = s * (q[i] - sums[1]);
 }
 
 // block partial sums of x (fixed order: a grid-stride sum per thread, then a
@@ -60,42 +60,52 @@ __global__ void k_sum_partial(const double* x, long long n, double* part) {
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-// out[0] = sum of the nblk partial sums, in order (one thread)
-__global__ void k_sum_final(const double* part, int nblk, double* out) {
+// out[0] = sum of the nblk partial sums, in order (one thread); out[1] = the
+// mean over n values (one division, not one per node)
+__global__ void k_sum_final(const double* part, int nblk, long long n, double* out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double s = 0.0;
   for (int i = 0; i < nblk; ++i) s += part[i];
   out[0] = s;
+  out[1] = s / (double)n;
+}
+
+// sum of the six neighbours of node i = (x, y, z) (32-bit indices: N < 2^31)
+__device__ __forceinline__ double nb_sum(const double* phi, int i, int x, int y, int z, int nx,
+                                         int ny, int nz) {
+  const int sy = nx, sz = nx * ny;
+  return phi[i - x + wrap(x - 1, nx)] + phi[i - x + wrap(x + 1, nx)] +
+         phi[i + (wrap(y - 1, ny) - y) * sy] + phi[i + (wrap(y + 1, ny) - y) * sy] +
+         phi[i + (wrap(z - 1, nz) - z) * sz] + phi[i + (wrap(z + 1, nz) - z) * sz];
 }
 
 // one colour of a red-black Gauss-Seidel sweep: the nodes with
-// (x + y + z) % 2 == colour take phi = (sum nb + b / c) / 6
-__global__ void k_mg_rbgs(double* phi, const double* b, int nx, int ny, int nz, double c,
+// (x + y + z) % 2 == colour take phi = (sum nb + b / c) / 6, as products
+// (inv_c = 1 / c = 4^l exactly; an FP64 division costs a long sequence on the
+// FP64 pipe, and the fixed point is set by the residual, which divides
+// nothing); thread j takes the j-th node of the colour (n_x even: half of
+// every row)
+__global__ void k_mg_rbgs(double* phi, const double* b, int nx, int ny, int nz, double inv_c,
                           int colour) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)nx * ny * nz;
-  if (i >= n) return;
-  const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
-  if (((x + y + z) & 1) != colour) return;
-  const long long sy = nx, sz = (long long)nx * ny;
-  const double nb = phi[i - x + wrap(x - 1, nx)] + phi[i - x + wrap(x + 1, nx)] +
-                    phi[i + (wrap(y - 1, ny) - y) * sy] + phi[i + (wrap(y + 1, ny) - y) * sy] +
-                    phi[i + (wrap(z - 1, nz) - z) * sz] + phi[i + (wrap(z + 1, nz) - z) * sz];
-  phi[i] = (nb + b[i] / c) / 6.0;
+  const unsigned j = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned hx = (unsigned)nx / 2u;
+  if (j >= hx * (unsigned)ny * (unsigned)nz) return;
+  const unsigned row = j / hx;
+  const int y = (int)(row % (unsigned)ny), z = (int)(row / (unsigned)ny);
+  const int x = 2 * (int)(j - row * hx) + ((y + z + colour) & 1);
+  const int i = x + nx * (int)row;
+  constexpr double SIXTH = 1.0 / 6.0;
+  phi[i] = (nb_sum(phi, i, x, y, z, nx, ny, nz) + b[i] * inv_c) * SIXTH;
 }
 
 // r = b - c (6 phi - sum nb)
 __global__ void k_mg_resid(const double* phi, const double* b, double* r, int nx, int ny, int nz,
                            double c) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)nx * ny * nz;
-  if (i >= n) return;
-  const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
-  const long long sy = nx, sz = (long long)nx * ny;
-  const double nb = phi[i - x + wrap(x - 1, nx)] + phi[i - x + wrap(x + 1, nx)] +
-                    phi[i + (wrap(y - 1, ny) - y) * sy] + phi[i + (wrap(y + 1, ny) - y) * sy] +
-                    phi[i + (wrap(z - 1, nz) - z) * sz] + phi[i + (wrap(z + 1, nz) - z) * sz];
-  r[i] = b[i] - c * (6.0 * phi[i] - nb);
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)nx * (unsigned)ny * (unsigned)nz) return;
+  const unsigned row = i / (unsigned)nx;
+  const int x = (int)(i - row * (unsigned)nx), y = (int)(row % (unsigned)ny), z = (int)(row / (unsigned)ny);
+  r[i] = b[i] - c * (6.0 * phi[i] - nb_sum(phi, (int)i, x, y, z, nx, ny, nz));
 }
 
 // full weighting: coarse node (X, Y, Z) sits on fine node (2X, 2Y, 2Z) and
@@ -104,15 +114,16 @@ __global__ void k_mg_resid(const double* phi, const double* b, double* r, int nx
 // total weight of 1, so the mean is kept); phi_c = 0 for the cycle below
 __global__ void k_mg_restrict(const double* rf, int nx, int ny, int nz, double* bc, double* phic) {
   const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)cx * cy * cz) return;
-  const int X = (int)(i % cx), Y = (int)((i / cx) % cy), Z = (int)(i / ((long long)cx * cy));
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)cx * (unsigned)cy * (unsigned)cz) return;
+  const unsigned row = i / (unsigned)cx;
+  const int X = (int)(i - row * (unsigned)cx), Y = (int)(row % (unsigned)cy), Z = (int)(row / (unsigned)cy);
   double s = 0.0;
   for (int dz = -1; dz <= 1; ++dz) {
-    const long long oz = (long long)wrap(2 * Z + dz, nz) * ny;
+    const int oz = wrap(2 * Z + dz, nz) * ny;
     const double wz = dz ? 0.5 : 1.0;
     for (int dy = -1; dy <= 1; ++dy) {
-      const long long oy = (oz + wrap(2 * Y + dy, ny)) * nx;
+      const int oy = (oz + wrap(2 * Y + dy, ny)) * nx;
       const double wy = wz * (dy ? 0.5 : 1.0);
       for (int dx = -1; dx <= 1; ++dx) s += wy * (dx ? 0.5 : 1.0) * rf[oy + wrap(2 * X + dx, nx)];
     }
@@ -124,22 +135,21 @@ __global__ void k_mg_restrict(const double* rf, int nx, int ny, int nz, double* 
 // trilinear prolongation of the coarse correction, added to the fine phi
 __global__ void k_mg_prolong_add(const double* phic, int nx, int ny, int nz, double* phif) {
   const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)nx * ny * nz) return;
-  const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)nx * (unsigned)ny * (unsigned)nz) return;
+  const unsigned row = i / (unsigned)nx;
+  const int x = (int)(i - row * (unsigned)nx), y = (int)(row % (unsigned)ny), z = (int)(row / (unsigned)ny);
   // per axis: an even fine index lies on coarse node x / 2, an odd one half
-  // way between (x - 1) / 2 and (x + 1) / 2 (periodic)
+  // way between (x - 1) / 2 and (x + 1) / 2 (periodic); the weight of each
+  // of the (1, 2, 4 or 8) coarse nodes is 1/2 per odd axis
   const int x0 = x >> 1, x1 = (x & 1) ? wrap(x0 + 1, cx) : x0;
-  const int y0 = y >> 1, y1 = (y & 1) ? wrap(y0 + 1, cy) : y0;
-  const int z0 = z >> 1, z1 = (z & 1) ? wrap(z0 + 1, cz) : z0;
-  const double wx = (x & 1) ? 0.5 : 1.0, wy = (y & 1) ? 0.5 : 1.0, wz = (z & 1) ? 0.5 : 1.0;
-  const int xs[2] = {x0, x1}, ys[2] = {y0, y1}, zs[2] = {z0, z1};
-  double s = 0.0;
-  for (int a = 0; a < ((z & 1) ? 2 : 1); ++a)
-    for (int bb = 0; bb < ((y & 1) ? 2 : 1); ++bb)
-      for (int cc = 0; cc < ((x & 1) ? 2 : 1); ++cc)
-        s += phic[((long long)zs[a] * cy + ys[bb]) * cx + xs[cc]];
-  phif[i] += wx * wy * wz * s;
+  const int y0 = (y >> 1) * cx, y1 = (y & 1) ? wrap((y >> 1) + 1, cy) * cx : y0;
+  const int z0 = (z >> 1) * cx * cy, z1 = (z & 1) ? wrap((z >> 1) + 1, cz) * cx * cy : z0;
+  // an even axis counts its one node twice and halves the sum: the same
+  // value as one node at weight 1
+  const double s = ((phic[z0 + y0 + x0] + phic[z0 + y0 + x1]) + (phic[z0 + y1 + x0] + phic[z0 + y1 + x1])) +
+                   ((phic[z1 + y0 + x0] + phic[z1 + y0 + x1]) + (phic[z1 + y1 + x0] + phic[z1 + y1 + x1]));
+  phif[i] += 0.125 * s;
 }
 
 // block maxima of |x| (a maximum does not depend on the order)
@@ -165,11 +175,11 @@ __global__ void k_max_final(const double* part, int nblk, double* out) {
   out[0] = m;
 }
 
-// phi -= mean phi (sums[0] = sum of phi)
+// phi -= mean phi (sums[1])
 __global__ void k_sub_mean(double* phi, long long n, const double* sums) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  phi[i] -= sums[0] / (double)n;
+  phi[i] -= sums[1];
 }
 
 unsigned blocks(long long n) { return (unsigned)((n + MG_T - 1) / MG_T); }
@@ -231,7 +241,7 @@ struct Solver {
 cudaError_t sum_of(const Solver& S, const double* x, long long n) {
   const int nb = (int)std::min<long long>(MG_RED_BLOCKS, (n + MG_T - 1) / MG_T);
   k_sum_partial<<<nb, MG_T, 0, S.s>>>(x, n, S.part);
-  k_sum_final<<<1, 32, 0, S.s>>>(S.part, nb, S.out);
+  k_sum_final<<<1, 32, 0, S.s>>>(S.part, nb, n, S.out);
   return cudaGetLastError();
 }
 
@@ -247,7 +257,7 @@ cudaError_t absmax_of(const Solver& S, const double* x, long long n, double& hos
 cudaError_t smooth(const Solver& S, const Level& l) {
   for (int sweep = 0; sweep < 2; ++sweep)
     for (int colour = 0; colour < 2; ++colour)
-      k_mg_rbgs<<<blocks(l.n), MG_T, 0, S.s>>>(l.phi, l.b, l.nx, l.ny, l.nz, l.c, colour);
+      k_mg_rbgs<<<blocks(l.n / 2), MG_T, 0, S.s>>>(l.phi, l.b, l.nx, l.ny, l.nz, 1.0 / l.c, colour);
   return cudaGetLastError();
 }
 
