@@ -219,6 +219,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks_of(x, ws, device):
+    """The largest of the ranks' values, on every rank (a replica job takes as
+    long as its slowest rank)."""
+    if ws == 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes, steps, ws, ms):
+    """Whole-job MLUPS of ws replicas (weak scaling): every rank advanced its
+    own box of `nodes` nodes `steps` times; ms is the slowest rank's time."""
+    return nodes * steps * ws / (ms / 1e3) / 1e6
+
+
 def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -278,11 +295,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, ws, "cuda")
 
     def measure(fp32):
         """Warm-up, then K steps timed with CUDA events on the context's stream
@@ -309,7 +322,7 @@ def main():
         ms = max_over_ranks(ev0.elapsed_time(ev1))
         kst = max(10, min(args.steps, 50))
         stage = s.step_timed(kst)
-        return dict(system=s, ms=ms, value=nodes * args.steps * ws / (ms / 1e3) / 1e6,
+        return dict(system=s, ms=ms, value=job_mlups(nodes, args.steps, ws, ms),
                     launches=launches, clocks=clocks,
                     stages={k: round(v / kst, 4) for k, v in
                             zip(["S1_poisson", "S2_flux_lb", "S3_advection", "S4_particles",
@@ -348,7 +361,7 @@ def main():
     s.sync()
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = nodes * e2e_steps * ws / e2e_s / 1e6
+    e2e_value = job_mlups(nodes, e2e_steps, ws, e2e_s * 1e3)
     h2d = 3 * 8
     d2h = len(parts) * ctypes_sizeof_particle(ek)
 
