@@ -278,12 +278,14 @@ ek_status ek_poisson_solve_mg(const double* q, double* phi, int nx, int ny, int 
  * The caller passes q and phi (device arrays of nx*ny*nz doubles, may alias).
  * Returns EK_ERR_ARG when (nx/2 + 1)*ny*nz exceeds EK_POISSON_STATIC_MAX or an
  * edge is not 2^a 3^b in [8, 1024] (nx even).  The first call on a device
- * resolves the arrays' device addresses (cudaGetSymbolAddress) and every call
- * with a new box shape reloads the tables with a blocking cudaMemcpy, so make
- * the first call for each device and shape before any stream capture.  All
- * calls share the arrays, which keep the last call's contents (nothing in them
- * needs to start at zero: the first FFT pass writes the whole spectrum); calls
- * that overlap on the GPU, on any streams, race and give wrong results. */
+ * resolves the arrays' device addresses (cudaGetSymbolAddress), so make the
+ * first call on each device before any stream capture.  A call with a box
+ * shape other than the previous call's reloads the tables by copies queued on
+ * `stream`, after the work already queued there: calls issued in order on one
+ * stream may change shape freely.  All calls share the arrays, which keep the
+ * last call's contents (nothing in them needs to start at zero: the first FFT
+ * pass writes the whole spectrum); calls that overlap on the GPU (on different
+ * streams with no ordering between them) race and give wrong results. */
 #define EK_POISSON_STATIC_MAX (1u << 19)
 ek_status ek_poisson_solve_static(const double* q, double* phi, int nx, int ny, int nz,
                                   double bjerrum, void* stream);

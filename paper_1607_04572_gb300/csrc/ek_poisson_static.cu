@@ -84,8 +84,16 @@ extern "C" ek_status ek_poisson_solve_static(const double* q, double* phi, int n
         ax3[a]->tw = t.twiddle + a * STATIC_EDGE;
         ax3[a]->lam = t.lambda + a * STATIC_EDGE;
       }
-      if (cudaMemcpy(t.twiddle, h_twiddle, sizeof(h_twiddle), cudaMemcpyHostToDevice) != cudaSuccess ||
-          cudaMemcpy(t.lambda, h_lambda, sizeof(h_lambda), cudaMemcpyHostToDevice) != cudaSuccess) {
+      // The refill is queued on the caller's stream: an earlier solve still
+      // queued there reads the old tables before they are overwritten, and
+      // the solve below reads the new ones.  A copy from pageable memory
+      // returns once its source has been staged, so the host buffers may be
+      // refilled by the next call.
+      cudaStream_t s = (cudaStream_t)stream;
+      if (cudaMemcpyAsync(t.twiddle, h_twiddle, sizeof(h_twiddle), cudaMemcpyHostToDevice, s) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(t.lambda, h_lambda, sizeof(h_lambda), cudaMemcpyHostToDevice, s) !=
+              cudaSuccess) {
         t.nx = t.ny = t.nz = 0;
         return EK_ERR_CUDA;
       }

@@ -39,6 +39,30 @@ def test_static_poisson_two_calls_match_allocating_entry_point(gpu_lib):
         assert float((out - ref).abs().max()) <= 1e-12 * scale
 
 
+def test_static_poisson_shape_changes_in_order_on_one_stream(gpu_lib):
+    """Calls queued back to back on a non-default stream, changing the box
+    shape between them with no synchronisation: each table reload is ordered
+    after the solves already queued, so every result equals the allocating
+    solve of its own shape."""
+    import torch
+    ek = gpu_lib
+    rng = np.random.default_rng(1608)
+    shapes = [(48, 32, 64), (24, 16, 18), (48, 32, 64), (32, 36, 24), (24, 16, 18)]
+    qs = [torch.from_numpy(rng.standard_normal(s[0] * s[1] * s[2])).cuda() for s in shapes]
+    refs = [_reference(ek, q, s) for q, s in zip(qs, shapes)]
+    torch.cuda.synchronize()
+    outs = [torch.full_like(q, float("nan")) for q in qs]
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        for q, out, s in zip(qs, outs, shapes):
+            ek.poisson_solve_static(q, out, s, 0.7, stream=st)
+    st.synchronize()
+    for out, ref in zip(outs, refs):
+        scale = float(ref.abs().max())
+        assert float((out - ref).abs().max()) <= 1e-12 * scale
+
+
 def test_static_poisson_rejects_too_large_box(gpu_lib):
     import torch
     ek = gpu_lib
