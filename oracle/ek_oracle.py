@@ -605,17 +605,49 @@ class EKOracle:
         d = np.where(d < -0.5 * n, d + n, d)
         return d
 
-    @staticmethod
-    def min_image_f32(coord, r, n):
-        """Single-precision offset of integer node coordinates from r, wrapped
-        to the nearest periodic image, in the operations the nearest-surface
-        decision is defined by (see solute_forces)."""
-        ipos = math.floor(r)
-        frac = np.float32(r - ipos)
-        d = (np.asarray(coord) - ipos).astype(np.float32) - frac
-        half, nf = np.float32(0.5 * n), np.float32(n)
-        d = np.where(d > half, d - nf, d)
-        return np.where(d < -half, d + nf, d).astype(np.float32)
+    def surface_distance(self, pid, X, Y, Z):
+        """Distance from node centres (X, Y, Z) (integer lattice coordinates,
+        0 <= X < nx ...) to the surface of particle pid, in FP64:
+        s = sqrt(dx*dx + dy*dy + dz*dz) - R with d the minimum-image offset
+        node - centre, the squares summed left to right.  Also returns d."""
+        p = self.particles[pid]
+        nx, ny, nz = self.n
+        dx = self.min_image(np.asarray(X, dtype=np.float64), p.pos[0], nx)
+        dy = self.min_image(np.asarray(Y, dtype=np.float64), p.pos[1], ny)
+        dz = self.min_image(np.asarray(Z, dtype=np.float64), p.pos[2], nz)
+        return np.sqrt(dx * dx + dy * dy + dz * dz) - p.radius, dx, dy, dz
+
+    def nearest_particle(self):
+        """Nearest-surface partition of the widened boxes (the regions V_p of
+        solute_forces).  Every node of particle p's box widened by ceil(R) + 4
+        cells is a candidate of p; a node belongs to the candidate with the
+        smallest FP64 surface distance, equal distances to the lower index.
+        Returns (nearest, regions): nearest[n] is the particle of flat node n
+        (-1 outside every widened box); regions[p] = (flat nodes of p's widened
+        box, each once, and their minimum-image offsets dx, dy, dz)."""
+        nx, ny, nz = self.n
+        best = np.full(self.shape, np.inf).ravel()
+        nearest = np.full(self.shape, -1, dtype=np.int64).ravel()
+        regions = []
+        # particles visited in index order; a node changes hands only to a
+        # strictly smaller distance
+        for pid, p in enumerate(self.particles):
+            lo, hi = particle_box(p.pos, p.radius)
+            m = int(math.ceil(p.radius)) + FORCE_MARGIN
+            iz = np.mod(np.arange(lo[2] - m, hi[2] + m), nz)
+            iy = np.mod(np.arange(lo[1] - m, hi[1] + m), ny)
+            ix = np.mod(np.arange(lo[0] - m, hi[0] + m), nx)
+            Zc, Yc, Xc = np.meshgrid(iz, iy, ix, indexing="ij")
+            flat = (Xc + nx * (Yc + ny * Zc)).ravel()
+            # a widened box wider than the lattice lists a node more than once
+            flat, first = np.unique(flat, return_index=True)
+            s, dx, dy, dz = self.surface_distance(pid, Xc.ravel()[first], Yc.ravel()[first],
+                                                  Zc.ravel()[first])
+            closer = s < best[flat]
+            best[flat[closer]] = s[closer]
+            nearest[flat[closer]] = pid
+            regions.append((flat, dx, dy, dz))
+        return nearest, regions
 
     def solute_forces(self, fext):
         """Force and torque of the solute on every particle.
@@ -629,11 +661,12 @@ class EKOracle:
         charge), particle p receives
             F_p = Z_p E - sum_{r in V_p} i(r) - (unassigned remainder) / P,
         where V_p are the fluid nodes of p's box widened by ceil(R) + 4 cells
-        for which p is the particle with the nearest surface (minimum image;
-        distances compared in single precision, ties to the lower index),
-        and the remainder is the sum of i over fluid nodes in no V_p.  Total
-        momentum then changes only by E times the total charge (zero in a
-        neutral box).  Torque: that of Z_p E on q_p(r) minus sum (r - r_p) x i.
+        for which p is the particle with the nearest surface, and the remainder
+        is the sum of i over fluid nodes in no V_p.  "Nearest" compares the FP64
+        surface distances of surface_distance(); equal values go to the lower
+        particle index.  Total momentum then changes only by E times the total
+        charge (zero in a neutral box).  Torque: that of Z_p E on q_p(r) minus
+        sum (r - r_p) x i.
         Returns (F, T) arrays of shape (P, 3).
         """
         P = len(self.particles)
@@ -645,45 +678,14 @@ class EKOracle:
         fluid = self.owner == FLUID
         q_ions = np.tensordot(self.valence, self.rho, axes=(0, 0)) if self.K else np.zeros(self.shape)
         ifield = np.where(fluid[None], fext - q_ions[None] * self.E.reshape(3, 1, 1, 1), 0.0)
-        big = np.iinfo(np.int64).max
-        key = np.full(self.shape, big, dtype=np.int64)
-        regions = []
-        for pid, p in enumerate(self.particles):
-            lo, hi = particle_box(p.pos, p.radius)
-            m = int(math.ceil(p.radius)) + FORCE_MARGIN
-            iz = np.mod(np.arange(lo[2] - m, hi[2] + m), nz)
-            iy = np.mod(np.arange(lo[1] - m, hi[1] + m), ny)
-            ix = np.mod(np.arange(lo[0] - m, hi[0] + m), nx)
-            Zc, Yc, Xc = np.meshgrid(iz, iy, ix, indexing="ij")
-            dx = self.min_image(Xc.astype(np.float64), p.pos[0], nx)
-            dy = self.min_image(Yc.astype(np.float64), p.pos[1], ny)
-            dz = self.min_image(Zc.astype(np.float64), p.pos[2], nz)
-            # the nearest-surface decision is taken in IEEE single precision:
-            # offset = float(node - floor(r_p)) - float(r_p - floor(r_p)),
-            # wrapped to the nearest image in float, squares summed left to
-            # right, correctly rounded sqrt; ties go to the lower index.  The
-            # key orders the float distances by their bit patterns (sign bit
-            # flipped, negatives complemented).
-            dxf = self.min_image_f32(Xc, p.pos[0], nx)
-            dyf = self.min_image_f32(Yc, p.pos[1], ny)
-            dzf = self.min_image_f32(Zc, p.pos[2], nz)
-            d2 = dxf * dxf + dyf * dyf + dzf * dzf
-            dsurf = np.sqrt(d2) - np.float32(p.radius)
-            bits = dsurf.view(np.uint32).astype(np.int64)
-            okey = np.where(bits >= 0x80000000, 0xFFFFFFFF - bits, bits + 0x80000000)
-            k = (okey << 20) | pid
-            flat = (Xc + nx * (Yc + ny * Zc)).ravel()
-            np.minimum.at(key.ravel(), flat, k.ravel())
-            regions.append((flat, dx.ravel(), dy.ravel(), dz.ravel()))
+        nearest, regions = self.nearest_particle()
         assigned = np.zeros(3)
         for pid, p in enumerate(self.particles):
             flat, dx, dy, dz = regions[pid]
-            flat_u, first = np.unique(flat, return_index=True)
-            dx, dy, dz = dx[first], dy[first], dz[first]
-            mine = ((key.ravel()[flat_u] & ((1 << 20) - 1)) == pid) & fluid.ravel()[flat_u]
-            ix_ = ifield[0].ravel()[flat_u][mine]
-            iy_ = ifield[1].ravel()[flat_u][mine]
-            iz_ = ifield[2].ravel()[flat_u][mine]
+            mine = (nearest[flat] == pid) & fluid.ravel()[flat]
+            ix_ = ifield[0].ravel()[flat][mine]
+            iy_ = ifield[1].ravel()[flat][mine]
+            iz_ = ifield[2].ravel()[flat][mine]
             s = np.array([ix_.sum(), iy_.sum(), iz_.sum()])
             assigned += s
             Fq, Tq = self.charge_field_force(pid)

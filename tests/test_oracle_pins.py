@@ -401,6 +401,55 @@ def test_psi_against_fine_sampling():
         assert abs(ps - frac) < 0.02, (cell, ps, frac)
 
 
+def _psi_level4(cell, c, R):
+    """Psi of one cell from its 4096 level-4 cubes alone, each tested on its own
+    (all 8 corners strictly inside: 1; closest point at distance >= R: 0; else
+    1/2), FP64, corners as the cube's exact corner coordinates minus the centre,
+    squares summed x, y, z."""
+    e = np.arange(17) / 16.0 - 0.5
+    d = [cell[a] + e - c[a] for a in range(3)]            # plane offsets per axis
+    lo = [d[a][:-1] for a in range(3)]
+    hi = [d[a][1:] for a in range(3)]
+    far = [np.maximum(np.abs(lo[a]), np.abs(hi[a])) for a in range(3)]
+    near = [np.where((lo[a] <= 0) & (hi[a] >= 0), 0.0, np.minimum(np.abs(lo[a]), np.abs(hi[a])))
+            for a in range(3)]
+    R2 = R * R
+
+    def d2(v):
+        x, y, z = np.meshgrid(v[0], v[1], v[2], indexing="ij")
+        return x * x + y * y + z * z
+
+    inside = d2(far) < R2
+    out = d2(near) >= R2
+    und = ~inside & ~out
+    return (inside.sum() + 0.5 * und.sum()) / 4096.0
+
+
+@pytest.mark.parametrize("c,R", [((0.31, -0.27, 0.44), 4.0), ((0.5, 0.25, 0.125), 2.0),
+                                 ((0.0, 0.0, 0.0), 3.0), ((0.0625, 0.5, -0.1875), 2.5),
+                                 ((0.123456789, 0.987654321, 0.5), 5.3)])
+def test_psi_octree_equals_level4_cubes(c, R):
+    """The octree of Sec. III.D.2 (decided cubes take their whole volume,
+    undecided ones are split, to depth 4) gives every cell exactly the value of
+    its level-4 cubes classified one by one: a cube decided at a coarser level
+    has all its sub-cubes decided alike (a sub-cube's farthest corner is no
+    farther per axis, its closest point no nearer, and rounding is monotone).
+    Dyadic centres put many corners exactly on the sphere."""
+    lo, hi = O.particle_box(c, R)
+    cells = [(x, y, z) for x in range(lo[0], hi[0]) for y in range(lo[1], hi[1])
+             for z in range(lo[2], hi[2])]
+    X = np.array([float(q[0]) for q in cells])
+    Y = np.array([float(q[1]) for q in cells])
+    Z = np.array([float(q[2]) for q in cells])
+    ps = O.psi_cells(X, Y, Z, np.array(c), R)
+    surface = 0
+    for i, cell in enumerate(cells):
+        flat = _psi_level4(cell, c, R)
+        assert ps[i] == flat, (cell, ps[i], flat)
+        surface += 0.0 < flat < 1.0
+    assert surface > 20
+
+
 def test_boundary_nodes_strictly_inside():
     o = quiet_box((16, 16, 16))
     o.add_particle((8.0, 8.0, 8.0), radius=3.0, charge=0.0)
