@@ -66,6 +66,10 @@ struct ek_ctx {
   int fchunks = 0;
   double* psum = nullptr;   // (Pcap + 1) * FPART
   int2* surf = nullptr;     // surface-cell list of S5, P * boxmax entries
+  int* tie_list = nullptr;  // nodes of possible nearest-surface ties (S4)
+  int* tie_count = nullptr;
+  int tie_cap = 1 << 16;
+  float tie_thr = 0.0f;
   int* surf_count = nullptr;
   Transfer* xfer = nullptr;
   int* xfer_count = nullptr;
@@ -221,6 +225,10 @@ PartArgs part_args(ek_ctx* ctx) {
   a.ticket = ctx->ticket;
   a.pticket = ctx->pticket;
   a.surf_cap = (int)std::min<size_t>(ctx->psibox_cap, (size_t)1 << 30);
+  a.tie_list = ctx->tie_list;
+  a.tie_count = ctx->tie_count;
+  a.tie_cap = ctx->tie_cap;
+  a.tie_thr = ctx->tie_thr;
   a.status = ctx->status;
   return a;
 }
@@ -281,6 +289,14 @@ ek_status run_setup(ek_ctx* ctx) {
   const int boxmax = ctx->P ? edge * edge * edge : 0;
   const int eedge = edge + 2 * ((int)ceil(rmax) + FORCE_MARGIN);
   const int emax = ctx->P ? eedge * eedge * eedge : 0;
+  {
+    // window of possible nearest-surface ties (k_force_assign): twice the
+    // float distance error bound 2^-21 (|d| + R + 1), |d| at most the widened
+    // box's half diagonal, plus the rounding of the difference of two float
+    // distances
+    const double dmax = sqrt(3.0) * (rmax + ceil(rmax) + FORCE_MARGIN + 2.0) + 1.0;
+    ctx->tie_thr = (float)(2.0 * ldexp(dmax + rmax + 1.0, -21) + ldexp(dmax + rmax, -22));
+  }
   const int fchunks = (emax + FORCE_CHUNK - 1) / FORCE_CHUNK;
   if (ctx->P && ((size_t)ctx->P * boxmax > ctx->psibox_cap || fchunks > ctx->fchunks)) {
     if (ctx->psibox) cudaFree(ctx->psibox);
@@ -410,7 +426,7 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
     case 4: {
       PartArgs a = part_args(ctx);
       EK_CUDA(launch_particle_forces(a, s));
-      ctx->launches += ctx->P > 0 ? 3 : 0;
+      ctx->launches += ctx->P > 0 ? 4 : 0;
       return EK_OK;
     }
     case 5: {
@@ -446,7 +462,7 @@ ek_status enqueue_step(ek_ctx* ctx) {
     EK_CUDA(ctx->fp32 ? launch_advection32(la, s) : launch_advection(la, s));
     EK_CUDA(launch_reflag(pa, true, s, 2));
     EK_CUDA(launch_particle_forces(pa, s, S4_KEY_RESET));
-    ctx->launches += (ctx->p.nspecies > 0 ? 2 : 1) + 10;
+    ctx->launches += (ctx->p.nspecies > 0 ? 2 : 1) + 11;
     return EK_OK;
   }
   if (ctx->P) {
@@ -478,7 +494,7 @@ ek_status enqueue_step(ek_ctx* ctx) {
     EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_part, 0));
     EK_CUDA(launch_reflag(pa, true, s, 2));
     EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
-    ctx->launches += 10;
+    ctx->launches += 11;
   }
   return EK_OK;
 }
@@ -718,6 +734,8 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   alloc((void**)&ctx->xfer, (size_t)ctx->xfer_cap * sizeof(Transfer));
   alloc((void**)&ctx->xfer_count, sizeof(int));
   alloc((void**)&ctx->surf_count, sizeof(int));
+  alloc((void**)&ctx->tie_list, (size_t)ctx->tie_cap * sizeof(int));
+  alloc((void**)&ctx->tie_count, sizeof(int));
   alloc((void**)&ctx->status, sizeof(int));
   alloc((void**)&ctx->ticket, sizeof(int));
   if (!ok) {
@@ -731,6 +749,7 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   cudaMemset(ctx->ifield, 0, 3 * N * rsz);
   cudaMemset(ctx->fkey, 0xFF, N * sizeof(unsigned long long));
   cudaMemset(ctx->xfer_count, 0, sizeof(int));
+  cudaMemset(ctx->tie_count, 0, sizeof(int));
   cudaMemset(ctx->status, 0, sizeof(int));
   cudaMemset(ctx->ticket, 0, sizeof(int));
   for (int b = 0; b < 2; ++b) {
@@ -767,7 +786,8 @@ ek_status ek_destroy(ek_ctx* ctx) {
                   ctx->qwall, ctx->u, ctx->tmp, ctx->owner, ctx->owner_prev, ctx->wall,
                   ctx->spectrum, ctx->dparts, ctx->psibox, ctx->fpart, ctx->surf, ctx->xfer,
                   ctx->xfer_count, ctx->surf_count, ctx->status, ctx->ifield, ctx->ipart,
-                  ctx->fkey, ctx->psum, ctx->vsig, ctx->ticket, ctx->pticket, ctx->pstage};
+                  ctx->fkey, ctx->psum, ctx->vsig, ctx->ticket, ctx->pticket, ctx->pstage,
+                  ctx->tie_list, ctx->tie_count};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);

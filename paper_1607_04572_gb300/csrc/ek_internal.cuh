@@ -302,6 +302,12 @@ struct PartArgs {
   const double* ipart;       // 3 per lattice block
   int nipart;                // number of lattice blocks
   unsigned long long* fkey;  // N: (surface distance, particle) of the nearest particle
+  // nodes whose nearest particle the float distances cannot decide: the FP64
+  // decision is taken there by a second kernel (cleared by the key reset)
+  int* tie_list;
+  int* tie_count;
+  int tie_cap;
+  float tie_thr;   // float distances closer than this are a possible tie
   double* psum;              // P * FPART: per-particle sums of S4
   int2* surf;      // (particle, box cell) of the cells cut by a sphere surface
   int* surf_count;

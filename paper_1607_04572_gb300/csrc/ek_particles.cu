@@ -329,6 +329,36 @@ __device__ __forceinline__ bool ext_cell(const DevParticle& P, int c, const Grid
   return first;
 }
 
+// FP64 surface distance of node (x, y, z) (wrapped coordinates) from particle
+// P: minimum-image offset, squares summed left to right, correctly rounded
+// square root, minus R; every operation rounded to nearest, no contraction.
+__device__ __forceinline__ double surface_distance64(const DevParticle& P, int x, int y, int z,
+                                                     const Grid& g) {
+  const double dx = min_image(__dsub_rn((double)x, P.pos[0]), g.nx);
+  const double dy = min_image(__dsub_rn((double)y, P.pos[1]), g.ny);
+  const double dz = min_image(__dsub_rn((double)z, P.pos[2]), g.nz);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  return __dsub_rn(__dsqrt_rn(d2), P.radius);
+}
+
+__device__ __forceinline__ float key_distance(unsigned long long key) {
+  unsigned bits = (unsigned)(key >> 20);
+  bits = (bits & 0x80000000u) ? (bits & 0x7FFFFFFFu) : ~bits;
+  return __uint_as_float(bits);
+}
+
+// The nearest particle of a node is the one with the smallest FP64 surface
+// distance (surface_distance64), equal distances to the lower index.  The key
+// holds a float estimate of it: the offset from the centre's integer part and
+// float fraction, wrapped in float, squares summed, sqrt, minus R.  Its error
+// against the FP64 distance is below 2^-24 (5.5 |d| + 2 R + 4.4) <=
+// 2^-21 (|d| + R + 1) (offset 2^-23 (|d| + 1.25) per axis, the square sum,
+// the root, R rounded to float, the difference), so when the float and the
+// FP64 orders disagree the two distances lie within 2 such bounds of each
+// other, and of the final minimum.  Whichever of the two writes its key second
+// then finds the other's (or a smaller, still within the window) in the value
+// atomicMin returns and lists the node; k_tie_resolve decides the listed nodes
+// in FP64.
 __global__ void k_force_assign(PartArgs a) {
   const int p = blockIdx.x;
   const DevParticle& P = a.parts[p];
@@ -338,9 +368,6 @@ __global__ void k_force_assign(PartArgs a) {
   box_coord(c, P.elo, P.ehi, X, Y, Z);  // a repeated node gets the same key
   const int x = wrapi(X, a.g.nx), y = wrapi(Y, a.g.ny), z = wrapi(Z, a.g.nz);
   const long long n = (long long)x + (long long)a.g.nx * ((long long)y + (long long)a.g.ny * z);
-  // surface distance in IEEE single precision (the decision's precision):
-  // offset = float(node - floor(r_p)) - float fraction of r_p, wrapped to the
-  // nearest image; ordered by its bit pattern, ties to the lower index
   auto off = [](int v, int ip, float fr, int nn) {
     const float hn = 0.5f * (float)nn;
     float d = __fsub_rn((float)(v - ip), fr);
@@ -356,13 +383,63 @@ __global__ void k_force_assign(PartArgs a) {
   unsigned bits = __float_as_uint(dsurf);
   bits = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
   const unsigned long long key = ((unsigned long long)bits << 20) | (unsigned long long)p;
-  atomicMin(a.fkey + n, key);
+  const unsigned long long old = atomicMin(a.fkey + n, key);
+  if (old != ~0ULL && (int)(old & 0xFFFFFull) != p) {
+    const float dold = key_distance(old);
+    if (dsurf - dold <= a.tie_thr && dold - dsurf <= a.tie_thr) {
+      const int slot = atomicAdd(a.tie_count, 1);
+      if (slot < a.tie_cap) a.tie_list[slot] = (int)n;
+      else atomicOr(a.status, ST_CAPACITY);
+    }
+  }
+}
+
+// FP64 decision on the listed nodes: one warp per entry, its lanes over the
+// particles whose widened box holds the node; the smallest (distance, index)
+// wins and its index replaces the key's.  A node listed twice gets the same
+// answer twice.
+__global__ void k_tie_resolve(PartArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int count = min(*a.tie_count, a.tie_cap);
+  const Grid g = a.g;
+  for (int e = warp; e < count; e += nwarps) {
+    const long long n = a.tie_list[e];
+    const int x = (int)(n % g.nx), y = (int)((n / g.nx) % g.ny), z = (int)(n / ((long long)g.nx * g.ny));
+    double best = INFINITY;
+    int who = 0x7FFFFFFF;
+    for (int q = lane; q < a.P; q += 32) {
+      const DevParticle& P = a.parts[q];
+      const int ex = P.ehi[0] - P.elo[0], ey = P.ehi[1] - P.elo[1], ez = P.ehi[2] - P.elo[2];
+      const bool in = (ex >= g.nx || wrapi(x - P.elo[0], g.nx) < ex) &&
+                      (ey >= g.ny || wrapi(y - P.elo[1], g.ny) < ey) &&
+                      (ez >= g.nz || wrapi(z - P.elo[2], g.nz) < ez);
+      if (!in) continue;
+      const double s = surface_distance64(P, x, y, z, g);
+      if (s < best) {  // q rises with the loop: an equal distance keeps the lower index
+        best = s;
+        who = q;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double sb = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+      const int wb = __shfl_xor_sync(0xFFFFFFFFu, who, o);
+      if (sb < best || (sb == best && wb < who)) {
+        best = sb;
+        who = wb;
+      }
+    }
+    if (lane == 0 && who != 0x7FFFFFFF) a.fkey[n] = (a.fkey[n] & ~0xFFFFFull) | (unsigned long long)who;
+  }
 }
 
 __global__ void k_key_reset(PartArgs a) {
   const int p = blockIdx.x;
   const DevParticle& P = a.parts[p];
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (p == 0 && c == 0) *a.tie_count = 0;
   if (c >= box_cells(P.kelo, P.kehi)) return;
   int X, Y, Z;
   box_coord(c, P.kelo, P.kehi, X, Y, Z);
@@ -949,135 +1026,173 @@ __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
   }
 }
 
-constexpr int PSI_WARPS = 4;  // warps per CTA of k_psi_surface
+// Psi_p of a surface cell (level 0 undecided) from the finest level alone.
+// In FP64 the octree's decisions are inherited: a cube decided inside at some
+// level has every level-4 sub-cube inside too, since a sub-cube's farthest
+// corner is no farther from the centre, axis by axis, than its parent's, and
+// rounding to nearest is monotone, so the rounded squared distance is no
+// larger; likewise a cube decided outside has every sub-cube outside (its
+// closest point is no closer).  Hence Psi_p = (2 N_in + N_und) / 8192 over the
+// 4096 level-4 cubes, N_in of them with the farthest corner strictly inside,
+// N_und the rest of those with the closest point nearer than R; that is
+// (N_in + N_near) / 8192 with N_near = N_in + N_und, bit for bit the
+// hierarchical result.
+//
+// One warp per cell, the 256 columns of 16 level-4 cubes along the axis u in
+// which the cell lies farthest from the centre spread over the lanes.  When the
+// centre lies beyond the cell's extent along u the distance of a column's
+// planes grows from the near end, so the planes whose far corner is inside
+// form a prefix (T planes: T - 1 inside cubes) and so do the cubes whose near
+// face is nearer than R (T_N cubes).  T and T_N are estimated from a float
+// square root, then settled by testing the planes at the boundary, each in
+// float, with the exact FP64 test of the octree where the float distance lies
+// within the margin of R^2 (see classify_f32).  A centre within the cell's u
+// extent (cells of spheres below R = 2) takes every plane's test.
+constexpr int PSI_CTA = 256;  // threads per CTA of k_psi_surface
 
-// Sub-cubes whose float pre-test is inconclusive (a corner within the margin
-// of the surface) are queued per warp and given the float-pair test 32 at a
-// time; only near-ties that test cannot decide take the FP64 one.
+struct PsiCell {
+  const DevParticle* P;
+  int X[3];     // the cell (unwrapped coordinates)
+  float fb[3];  // X - integer part of the centre (exact in float)
+  float R2f, margin;
+  double R2;
+  int u, v, w;  // column axis and the two across it
+};
+
+// offset of plane m (0..16) of the cell along axis a from the centre, the FP64
+// value of the octree's test: the plane's exact coordinate minus the centre,
+// rounded (the float estimate in the kernel is one rounding of the exact float
+// difference of the plane and the centre's float fraction)
+__device__ __forceinline__ double plane_off_d(const PsiCell& c, int a, int m) {
+  return __dsub_rn((double)c.X[a] + (0.0625 * (double)m - 0.5), c.P->pos[a]);
+}
+// far (largest magnitude) or near (0 when the centre lies within) offset of
+// slab j (planes j, j + 1) along axis a
+__device__ __forceinline__ float slab_f(float a0, float a1, bool far) {
+  if (far) return fmaxf(fabsf(a0), fabsf(a1));
+  return (a0 <= 0.0f && a1 >= 0.0f) ? 0.0f : fminf(fabsf(a0), fabsf(a1));
+}
+__device__ __forceinline__ double slab_d(double a0, double a1, bool far) {
+  if (far) return fmax(fabs(a0), fabs(a1));
+  return (a0 <= 0.0 && a1 >= 0.0) ? 0.0 : fmin(fabs(a0), fabs(a1));
+}
+
+// the FP64 test of the octree for the point whose u offset is the plane mu
+// (or, with mu1 >= 0, the near face of the slab mu..mu1) and whose v and w
+// offsets are the far or near ones of slabs j and l: squared distance summed
+// x, y, z left to right, against R^2.  A real call: inlined, its FP64
+// instructions would be issued (predicated off) on every float test.
+__device__ __noinline__ bool psi_exact(const PsiCell* c, int mu, int mu1, int j, int l, bool far) {
+  double o[3];
+  const double a0 = plane_off_d(*c, c->u, mu);
+  o[c->u] = mu1 >= 0 ? slab_d(a0, plane_off_d(*c, c->u, mu1), far) : fabs(a0);
+  o[c->v] = slab_d(plane_off_d(*c, c->v, j), plane_off_d(*c, c->v, j + 1), far);
+  o[c->w] = slab_d(plane_off_d(*c, c->w, l), plane_off_d(*c, c->w, l + 1), far);
+  return dist2(o[0], o[1], o[2]) < c->R2;
+}
+
+// float test with the FP64 one where the float squared distance is within the
+// margin of R^2
+__device__ __forceinline__ bool psi_test(const PsiCell& c, float gu, float gvw2, int mu, int mu1,
+                                         int j, int l, bool far) {
+  const float d = gu * gu + gvw2;
+  if (d < c.R2f - c.margin) return true;
+  if (d > c.R2f + c.margin) return false;
+  return psi_exact(&c, mu, mu1, j, l, far);
+}
+
 template <class FM>
-__global__ void __launch_bounds__(32 * PSI_WARPS) k_psi_surface(PartArgs a) {
-  // per warp: the undecided cubes of the current and the next level (paths
-  // and centres relative to the centre's integer part, exact in float; within
-  // one octant a level holds at most 64) and the paths the float pre-test
-  // could not decide
-  __shared__ unsigned short qpath[PSI_WARPS][2][64];
-  __shared__ float3 qcen[PSI_WARPS][2][64];
-  __shared__ unsigned short fbq[PSI_WARPS][64];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
+__global__ void __launch_bounds__(PSI_CTA) k_psi_surface(PartArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * PSI_CTA + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * PSI_CTA) >> 5;
   const int count = min(*a.surf_count, a.surf_cap);
-  // one warp per (surface cell, level-1 octant): eight warps share a cell
-  for (int e = blockIdx.x * PSI_WARPS + wid; e < 8 * count; e += gridDim.x * PSI_WARPS) {
-    const int2 pc = a.surf[e >> 3];
-    const int oct = e & 7;
-    DevParticle& P = a.parts[pc.x];
-    int X, Y, Z;
-    box_coord(pc.y, P.lo, P.hi, X, Y, Z);
-    const float R2f = P.r2f, margin = P.psimargin;
-    // the cell centre minus the particle centre's integer part (exact)
-    const float bx = (float)(X - P.ipos[0]), by = (float)(Y - P.ipos[1]), bz = (float)(Z - P.ipos[2]);
-    int cur = 0;
-    unsigned short* fb = fbq[wid];
-    int qlen = 0;
+  for (int e = warp; e < count; e += nwarps) {
+    const int2 pc = a.surf[e];
+    const DevParticle& P = a.parts[pc.x];
+    PsiCell c;
+    c.P = &P;
+    box_coord(pc.y, P.lo, P.hi, c.X[0], c.X[1], c.X[2]);
+    for (int d = 0; d < 3; ++d) c.fb[d] = (float)(c.X[d] - P.ipos[d]);
+    c.R2f = P.r2f;
+    c.margin = P.psimargin;
+    c.R2 = __dmul_rn(P.radius, P.radius);
+    // the column axis: the largest distance of the cell centre from the centre
+    float best = -1.0f;
+    c.u = 0;
+    for (int d = 0; d < 3; ++d) {
+      const float o = fabsf(__fsub_rn(c.fb[d], P.fpos[d]));
+      if (o > best) {
+        best = o;
+        c.u = d;
+      }
+    }
+    c.v = c.u == 0 ? 1 : 0;
+    c.w = c.u == 2 ? 1 : 2;
+    // near end of the columns: the plane nearest the centre, when the centre
+    // lies beyond the cell along u (exact comparisons in FP64)
+    const double lo_u = (double)c.X[c.u] - 0.5, hi_u = (double)c.X[c.u] + 0.5;
+    const int near = P.pos[c.u] <= lo_u ? 0 : (P.pos[c.u] >= hi_u ? 16 : -1);
+    const int step = near == 0 ? 1 : -1;
+    // per-axis constants of the float offsets (registers, not indexed)
+    const float bu = c.fb[c.u], bv = c.fb[c.v], bw = c.fb[c.w];
+    const float fu = P.fpos[c.u], fv_ = P.fpos[c.v], fw_ = P.fpos[c.w];
+    auto off = [](float b, float f, int m) { return __fsub_rn(b + (0.0625f * (float)m - 0.5f), f); };
     int units = 0;
-    {
-      // level 1: this warp's octant (every lane takes the same decision)
-      float ax, ay, az;
-      subcube_centre_f(oct, 1, bx, by, bz, ax, ay, az);
-      const int st = classify_tiers(ax, ay, az, oct, 1, X, Y, Z, P);
-      if (st == CUBE_IN) {
-        if (lane == 0) units = 2 << (3 * (PSI_DEPTH - 1));
-      } else if (st == CUBE_UNDECIDED) {
-        if (lane == 0) {
-          qpath[wid][0][0] = (unsigned short)oct;
-          qcen[wid][0][0] = make_float3(ax, ay, az);
-        }
-        qlen = 1;
-      }
-    }
-    __syncwarp();
-    for (int l = 2; l <= PSI_DEPTH && qlen > 0; ++l) {
-      const int ntask = qlen * 8;
-      const float h = ldexpf(1.0f, -(l + 1));
-      const int in_units = 2 << (3 * (PSI_DEPTH - l));
-      const int nx = 1 - cur;
-      int newlen = 0, nfb = 0;
-      for (int t0 = 0; t0 < ntask; t0 += 32) {
-        const int t = t0 + lane;
-        bool und = false, exact = false;
-        int path = 0;
-        float ax = 0.0f, ay = 0.0f, az = 0.0f;
-        if (t < ntask) {
-          const int bits = t & 7;
-          path = ((int)qpath[wid][cur][t >> 3] << 3) | bits;
-          // the child's centre: the parent's plus or minus h per axis (exact)
-          const float3 c = qcen[wid][cur][t >> 3];
-          ax = __fadd_rn(c.x, (bits & 1) ? h : -h);
-          ay = __fadd_rn(c.y, (bits & 2) ? h : -h);
-          az = __fadd_rn(c.z, (bits & 4) ? h : -h);
-          const int st = classify_f32(__fsub_rn(ax, P.fpos[0]), __fsub_rn(ay, P.fpos[1]),
-                                      __fsub_rn(az, P.fpos[2]), h, R2f, margin);
-          if (st < 0) exact = true;
-          else if (st == CUBE_IN) units += in_units;
-          else if (st == CUBE_UNDECIDED) {
-            if (l == PSI_DEPTH) units += 1;
-            else und = true;
-          }
-        }
-        unsigned mask = __ballot_sync(0xffffffffu, und);
-        if (und) {
-          const int slot = newlen + __popc(mask & lt);
-          qpath[wid][nx][slot] = (unsigned short)path;
-          qcen[wid][nx][slot] = make_float3(ax, ay, az);
-        }
-        newlen += __popc(mask);
-        mask = __ballot_sync(0xffffffffu, exact);
-        if (exact) fb[nfb + __popc(mask & lt)] = (unsigned short)path;
-        nfb += __popc(mask);
-        const bool level_end = t0 + 32 >= ntask;
-        while (nfb >= 32 || (level_end && nfb > 0)) {
-          __syncwarp();
-          const int take = min(nfb, 32);
-          bool und2 = false;
-          int path2 = 0;
-          float fx = 0.0f, fy = 0.0f, fz = 0.0f;
-          if (lane < take) {
-            path2 = fb[nfb - take + lane];
-            subcube_centre_f(path2, l, bx, by, bz, fx, fy, fz);
-            const int st = classify_tiers(fx, fy, fz, path2, l, X, Y, Z, P);
-            if (st == CUBE_IN) units += in_units;
-            else if (st == CUBE_UNDECIDED) {
-              if (l == PSI_DEPTH) units += 1;
-              else und2 = true;
-            }
-          }
-          const unsigned m2 = __ballot_sync(0xffffffffu, und2);
-          if (und2) {
-            const int slot = newlen + __popc(m2 & lt);
-            qpath[wid][nx][slot] = (unsigned short)path2;
-            qcen[wid][nx][slot] = make_float3(fx, fy, fz);
-          }
-          newlen += __popc(m2);
-          nfb -= take;
-          __syncwarp();
+    for (int col = lane; col < 256; col += 32) {
+      const int j = col & 15, l = col >> 4;
+      const float v0 = off(bv, fv_, j), v1 = off(bv, fv_, j + 1);
+      const float w0 = off(bw, fw_, l), w1 = off(bw, fw_, l + 1);
+      const float fv = slab_f(v0, v1, true), fw = slab_f(w0, w1, true);
+      const float nv = slab_f(v0, v1, false), nw = slab_f(w0, w1, false);
+      const float far2 = fv * fv + fw * fw, near2 = nv * nv + nw * nw;
+      if (near >= 0) {
+        const float e0 = fabsf(off(bu, fu, near));
+        // planes t = 0..16 from the near end whose far corner is inside
+        const float A = c.R2f - far2;
+        int T = A > 0.0f ? (int)ceilf((sqrtf(A) - e0) * 16.0f) : 0;
+        T = min(max(T, 0), 17);
+        auto pin = [&](int t) {
+          const int m = near + step * t;
+          return psi_test(c, fabsf(off(bu, fu, m)), far2, m, -1, j, l, true);
+        };
+        while (T > 0 && !pin(T - 1)) --T;
+        while (T < 17 && pin(T)) ++T;
+        // cubes t = 0..15 whose near face (plane t) is nearer than R
+        const float B = c.R2f - near2;
+        int TN = B > 0.0f ? (int)ceilf((sqrtf(B) - e0) * 16.0f) : 0;
+        TN = min(max(TN, 0), 16);
+        auto pnear = [&](int t) {
+          const int m = near + step * t;
+          return psi_test(c, fabsf(off(bu, fu, m)), near2, m, -1, j, l, false);
+        };
+        while (TN > 0 && !pnear(TN - 1)) --TN;
+        while (TN < 16 && pnear(TN)) ++TN;
+        units += max(T - 1, 0) + TN;
+      } else {
+        // the centre within the cell's extent along u: every cube
+        bool prev = psi_test(c, fabsf(off(bu, fu, 0)), far2, 0, -1, j, l, true);
+        for (int k = 0; k < 16; ++k) {
+          const float a0 = off(bu, fu, k), a1 = off(bu, fu, k + 1);
+          const bool in1 = psi_test(c, fabsf(a1), far2, k + 1, -1, j, l, true);
+          if (prev && in1) units += 1;
+          prev = in1;
+          if (psi_test(c, slab_f(a0, a1, false), near2, k, k + 1, j, l, false)) units += 1;
         }
       }
-      __syncwarp();
-      cur = nx;
-      qlen = newlen;
     }
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) units += __shfl_xor_sync(0xffffffffu, units, o);
     if (lane == 0 && units > 0) {
       // dyadic with 13 fraction bits: every sum below is exact, in any order
       const double ps = (double)units / (double)PSI_UNITS;
-      const long long n = node_of(X, Y, Z, a.g);
-      atomicAdd(a.psibox + (long long)pc.x * a.boxmax + pc.y, ps);
+      const long long n = node_of(c.X[0], c.X[1], c.X[2], a.g);
+      a.psibox[(long long)pc.x * a.boxmax + pc.y] = ps;
       real_add<FM>(a.psi, n, ps);
       // integer counts, spread over eight addresses (the total of one
       // particle would otherwise serialise the atomics of all its cells)
-      atomicAdd(&P.psiunits[oct], (unsigned long long)units);
+      atomicAdd(&a.parts[pc.x].psiunits[pc.y & 7], (unsigned long long)units);
     }
-    __syncwarp();
   }
 }
 
@@ -1273,7 +1388,10 @@ __global__ void k_apply_transfers(PartArgs a) {
 template <class FM>
 cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s, int parts) {
   const unsigned echunks = (unsigned)((a.emax + PT - 1) / PT);
-  if (parts & S4_ASSIGN) k_force_assign<<<dim3(a.P, echunks), PT, 0, s>>>(a);
+  if (parts & S4_ASSIGN) {
+    k_force_assign<<<dim3(a.P, echunks), PT, 0, s>>>(a);
+    k_tie_resolve<<<8, 256, 0, s>>>(a);
+  }
   if (parts & S4_FORCES) k_particle_forces<FM><<<dim3(a.P, a.fchunks), FORCE_T, 0, s>>>(a);
   // the widened boxes have moved with the integration: clear the keys of the
   // old ones, which the integration kept in kelo / kehi
@@ -1308,7 +1426,7 @@ cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s, int pa
   }
   if (!transitions) cudaMemsetAsync(a.surf_count, 0, sizeof(int), s);  // else k_clear resets it
   k_claim<FM><<<dim3(a.P, bchunks), PT, 0, s>>>(a);
-  k_psi_surface<FM><<<16 * 152, 32 * PSI_WARPS, 0, s>>>(a);
+  k_psi_surface<FM><<<8 * 152, PSI_CTA, 0, s>>>(a);
   k_charge_scatter<FM><<<dim3(a.P, bchunks), PT, 0, s>>>(a);
   if (transitions && (parts & 2)) {
     k_transitions<FM><<<dim3(a.P, uchunks), PT, 0, s>>>(a);
