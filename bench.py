@@ -1,21 +1,25 @@
 #!/usr/bin/env python
 """Throughput of the full moving-boundary electrokinetics step (S1-S5) on GB300.
 
-Workload (default): the single-sphere electrophoresis box -- 128^3 periodic
-lattice, D3Q19 BGK tau = 1, 2 ion species (z = +1/-1, D = 0.3, bulk 1e-3,
-neutralised), Bjerrum length 0.7, one sphere R = 8, Z = -300 at a seeded
-off-centre position, free to move, E = 0.005 along x.  A step is one full time
-step: Poisson, fused flux + LB, advection, particle forces and integration,
-re-flagging and transitions.  `value` is the FP32-storage form (float
-populations, int32 fixed-point species, FP64 particle sums and integrator);
-the plain FP64 form is measured beside it under "fp64_form".
+Workload (default, the headline): many moving colloids in the large box --
+512^3 periodic lattice, D3Q19 BGK tau = 1, 1000 spheres R = 6, Z = -200 at
+seeded non-overlapping positions, free to move, 2 ion species (z = +1/-1,
+D = 0.3, bulk 5e-4, neutralised), Bjerrum length 0.7, E = 0.002 along x, in
+the FP32-storage form (float populations, int32 fixed-point species, FP64
+particle sums and integrator).  A step is one full time step: Poisson, fused
+flux + LB, advection, particle forces and integration, re-flagging and
+transitions.  Beside it: the single-sphere 128^3 box in both storage forms
+(the plain FP64 form is the parity reference), the 256^3 box with 64 spheres
+and three species, the batched ensemble of 256 small boxes, and the
+multigrid Poisson solve.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line (rank 0).  `value` is MLUPS (million lattice-node updates
 per second, boundary nodes included) over all ranks; with N > 1 every rank
 runs its own replica of the box (weak scaling, no collective on the data path).
-`--impl reference` times the FP64 CPU oracle on the same workload instead.
+`--impl reference` times the FP64 CPU oracle on all host cores instead (a
+bounded sub-box sample of the same workload, one oracle replica per core).
 """
 from __future__ import annotations
 
@@ -33,20 +37,43 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS per full EK step and % of HBM roofline, FP32/batched vs plain FP64 at 1e-3 mobility"
-FLUSH_NOTE = ("state > L2 (populations 2 x 19 x 4 B x N = 319 MB in the FP32 form, 637 MB in "
-              "FP64, at 128^3; L2 129 MB), no flush needed")
+HEADLINE = "large"
+SAMPLE_EDGE = 128  # edge of the sub-box the CPU oracle is timed on
 
-# Algorithmic work of the fused flux + LB kernel, per fluid node, two species,
-# partial volumes on, bulk node (all 18 links fluid): bytes that must cross
-# HBM once per step (populations read + written, species read + written after
-# the flux divergence, Psi, Phi and the node class read, u and the internal
-# solute force written for S3 / S4, one sign byte) and FP64 operations of the
-# formulas.
-LB_BYTES_PER_NODE = 2 * 19 * 8 + 2 * 2 * 8 + 8 + 8 + 4 + 3 * 8 + 3 * 8 + 1   # 405 (k_lb_fused)
+
+def l2_note(w, fp32):
+    n = w["shape"][0] * w["shape"][1] * w["shape"][2]
+    mb = 2 * 19 * (4 if fp32 else 8) * n / 1e6
+    return (f"state > L2 (populations 2 x 19 x {4 if fp32 else 8} B x N = {mb:.0f} MB; "
+            f"L2 129 MB), no flush needed")
+
+
+def describe(w):
+    P = len(w["particles"])
+    R = sorted({p["radius"] for p in w["particles"]})
+    Z = [p["charge"] for p in w["particles"]]
+    zs = f"{Z[0]:g}" if len(set(Z)) == 1 else f"U[{min(Z):.0f},{max(Z):.0f}]"
+    nx, ny, nz = w["shape"]
+    return (f"{w['name']}: {nx}x{ny}x{nz}, {P} sphere(s) R={','.join(f'{r:g}' for r in R)}, "
+            f"Z={zs}, {len(w['valence'])} species z={list(w['valence'])} bulk {w['bulk'][0]:g}, "
+            f"E={w['E'][0]:g} along x, BGK tau=1")
+
+
+# Algorithmic bytes per lattice node of the fused flux + LB kernel: what the
+# stage must read and write once per step by the method's own state (SURVEY's
+# per-node items that S2 touches): populations read + written, species read and
+# written after the flux divergence, Psi and the node class, Phi.  The u,
+# internal-force and sign-byte writes it also makes (for S3 and S4) are
+# implementation overhead and count against the fraction.
+def lb_bytes_per_node(fp32, K):
+    if fp32:
+        return 2 * 19 * 4 + 2 * K * 4 + 5 + 4        # 177 for K = 2
+    return 2 * 19 * 8 + 2 * K * 8 + 9 + 8            # 353 for K = 2
+
+
 LB_FP64_FLOP_PER_NODE = 950
-# the same for the FP32-storage kernel (k_lb32_tiled): float populations,
-# int32 species, float Psi / Phi / u / internal force
-LB32_BYTES_PER_NODE = 2 * 19 * 4 + 2 * 2 * 4 + 4 + 4 + 4 + 3 * 4 + 3 * 4 + 1  # 205
+
+
 # Algorithmic bytes per node of a whole step (S1-S5), the state read once and
 # written once with every intermediate fused: populations read + written,
 # species read + written, Psi and the node class read, Phi written (S1) and read
@@ -72,18 +99,25 @@ def step_roofline(mlups, bytes_per_node, hbm_peak):
 # (2 DFMA per clock per SM); a DFMA probe on this pool measured 1.19 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
-# from an ncu capture of the 128^3 workload (profiles/), valid only for the
-# kernel source it was taken on.
-TRAFFIC = {"k_lb_fused": {"bytes_per_launch": 755997696,  # profiles/fp64_k_lb_fused_k_advect_single128.md
-                           "source_sha": "85d705496daa5794", "file": "ek_lattice.cu"},
-           "k_lb32": {"bytes_per_launch": 202392832 + 179882240,  # profiles/fp32_kernels_single128.md
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per lattice node
+# of one launch of the kernel, from an ncu capture, valid only for the kernel
+# source it was taken on (otherwise the traffic is reported as null).
+TRAFFIC = {"k_lb_fused": {"bytes_per_node": 755997696 / 128 ** 3,
+                          "source_sha": "85d705496daa5794", "file": "ek_lattice.cu"},
+           "k_lb32": {"bytes_per_node": (202392832 + 179882240) / 128 ** 3,
                       "source_sha": "8e4ea3cf1efc08bf", "file": "ek_lattice32.cu"}}
 
 
 def src_sha(name: str) -> str:
     p = os.path.join(ROOT, "paper_1607_04572_gb300", "csrc", name)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def traffic(kernel, nodes):
+    t = TRAFFIC[kernel]
+    if t["source_sha"] != src_sha(t["file"]):
+        return None
+    return int(round(t["bytes_per_node"] * nodes))
 
 
 def measured_peaks():
@@ -183,33 +217,73 @@ def build_system(ek, w, fp32=True):
     return s
 
 
-def build_oracle(w):
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores (the CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_replica(job, start, out):
+    """One oracle replica of the sample in its own process (single-threaded
+    numpy): `warmup` untimed steps, a barrier with the other replicas, then
+    steps until `steps` are done or the budget is spent.  Puts (steps done,
+    wall-clock start and end) on `out`."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    name, edge, steps, warmup, budget_s = job
     import numpy as np
+    import workloads
     from oracle.ek_oracle import EKOracle, NEUTRALIZE, PV
+    w = workloads.sub_box(name, edge)
     o = EKOracle(*w["shape"], nu=w["nu"], rho0=w["rho0"], bjerrum=w["bjerrum"],
                  valence=w["valence"], D=w["D"], bulk=w["bulk"], flags=PV | NEUTRALIZE)
     for p in w["particles"]:
         o.add_particle(p["pos"], radius=p["radius"], charge=p["charge"], rho_p=w["rho_p"])
     o.E = np.array(w["E"], dtype=np.float64)
-    return o
-
-
-def time_oracle(w, max_steps, budget_s, warmup=1):
-    """Oracle MLUPS on the host: `warmup` untimed steps, then up to max_steps
-    timed steps or until budget_s seconds are spent."""
-    o = build_oracle(w)
     for _ in range(warmup):
         o.step()
-    nodes = w["shape"][0] * w["shape"][1] * w["shape"][2]
-    t0 = time.perf_counter()
+    start.wait(timeout=600)  # all replicas start their timed steps together
+    t0 = time.time()
     done = 0
-    while done < max_steps:
+    while done < steps:
         o.step()
         done += 1
-        if time.perf_counter() - t0 > budget_s:
+        if time.time() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    return nodes * done / dt / 1e6, done, dt
+    out.put((done, t0, time.time()))
+
+
+def oracle_procs(edge):
+    """Replicas to run at once: one per host core, as far as the host memory
+    holds them (an oracle of n^3 nodes peaks near 1.8 kB per node)."""
+    cores = os.cpu_count() or 1
+    try:
+        avail = [int(l.split()[1]) * 1024 for l in open("/proc/meminfo") if l.startswith("MemAvailable")][0]
+    except Exception:
+        avail = 8 << 30
+    per = 1800 * edge ** 3
+    return max(1, min(cores, int(0.6 * avail // per)))
+
+
+def time_oracle_all_cores(name, edge, steps, warmup, budget_s):
+    """Oracle MLUPS on the host: one replica of the sub-box sample per core,
+    spawned processes (no fork of a CUDA process), timed steps aligned;
+    throughput = all replicas' node updates over the span of their timed
+    steps."""
+    import multiprocessing as mp
+    procs = oracle_procs(edge)
+    ctx = mp.get_context("spawn")
+    start = ctx.Barrier(procs)
+    out = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_replica, args=((name, edge, steps, warmup, budget_s), start, out))
+          for _ in range(procs)]
+    for p in ps:
+        p.start()
+    res = [out.get(timeout=1200) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+    done = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    nodes = edge ** 3
+    return {"value": nodes * done / span / 1e6, "procs": procs, "steps": min(r[0] for r in res),
+            "span_s": span}
 
 
 def dist_env():
@@ -240,24 +314,118 @@ def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    nodes = w["shape"][0] * w["shape"][1] * w["shape"][2]
-    # each oracle step of the 128^3 box takes seconds: time a bounded sample
-    value, done, dt = time_oracle(w, args.steps, budget_s=120.0, warmup=min(args.warmup, 1))
-    sample = (f"{done} timed of {args.steps} requested steps of the {w['shape'][0]}^3 workload "
-              f"after {min(args.warmup, 1)} warm-up step(s); numpy FP64 oracle, single thread")
-    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
-            "n_gpus": args.gpus, "steps": done, "warmup": min(args.warmup, 1),
-            "ms_per_step": round(dt / done * 1e3, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "single-sphere electrophoresis 128^3, R=8, Z=-300, 2 species, "
-                                   "E=0.005, FP64", "nodes": nodes, "parallelism": "replicas",
-                       "l2": FLUSH_NOTE},
-            "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1,
+    warm = min(args.warmup, 1)
+    r = time_oracle_all_cores(w["name"], SAMPLE_EDGE, args.steps, warm, budget_s=150.0)
+    sample = (f"{SAMPLE_EDGE}^3 periodic sub-box of the {describe(w)} workload "
+              f"({len(__import__('workloads').sub_box(w['name'], SAMPLE_EDGE)['particles'])} "
+              f"sphere(s) wholly inside); {r['procs']} single-threaded numpy FP64 oracle "
+              f"replicas in parallel, {r['steps']} timed of {args.steps} requested steps each "
+              f"after {warm} warm-up step(s)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(r["value"], 4), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": r["steps"], "warmup": warm,
+            "ms_per_step": round(r["span_s"] / max(r["steps"], 1) * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": describe(w), "nodes": SAMPLE_EDGE ** 3,
+                       "parallelism": "replicas", "l2": "host run"},
+            "cpu_baseline": {"value": round(r["value"], 4), "unit": "MLUPS", "cores": r["procs"],
                              "kind": "oracle", "sample": sample},
-            "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+            "e2e": {"value": round(r["value"], 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure(ek, torch, w, fp32, args, stream, barrier, max_over_ranks, ws, stage_steps=None):
+    """Warm-up, then K steps timed with CUDA events on the context's stream
+    (inputs resident in HBM); then a per-stage split of more steps."""
+    s = build_system(ek, w, fp32)
+    s.set_stream(stream)
+    s.step(max(args.warmup, 3))
+    nodes = w["shape"][0] * w["shape"][1] * w["shape"][2]
+    clk = ClockSampler(dist_env()[2])
+    barrier()
+    clk.start()
+    launches0 = s.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clk.mark(True)
+    ev0.record(stream)
+    s.step_async(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    clk.mark(False)
+    barrier()
+    clocks = clk.stop()
+    launches = s.kernel_launches() - launches0
+    s.sync()
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    kst = stage_steps or max(10, min(args.steps, 50))
+    stage = s.step_timed(kst)
+    return dict(system=s, ms=ms, value=job_mlups(nodes, args.steps, ws, ms), nodes=nodes,
+                launches=launches, clocks=clocks,
+                stages={k: round(v / kst, 4) for k, v in
+                        zip(["S1_poisson", "S2_flux_lb", "S3_advection", "S4_particles",
+                             "S5_reflag", "total"], stage)},
+                lb_ms=stage[1] / kst)
+
+
+def end_to_end(ek, torch, w, s, stream, steps, barrier, max_over_ranks, ws):
+    """The same metric through the public API with host buffers: every step the
+    field E is read from pinned host memory into the step's launch, the step
+    runs, and the particle records (the mobility observable) are copied into
+    pinned host memory and decoded on the host; two record buffers let step
+    t + 1 run while step t's records are read."""
+    nodes = w["shape"][0] * w["shape"][1] * w["shape"][2]
+    e_host = torch.tensor(w["E"], dtype=torch.float64).pin_memory()
+    npart = s.num_particles()
+    recbytes = npart * ctypes_sizeof_particle(ek)
+    bufs = [torch.zeros(max(recbytes, 1), dtype=torch.uint8).pin_memory() for _ in range(2)]
+    evs = [torch.cuda.Event() for _ in range(2)]
+    barrier()
+    t0 = time.perf_counter()
+    parts = []
+    for t in range(steps):
+        s.set_field(ek.FIELD_E_EXT, e_host)
+        s.step_async(1)
+        s.get_particles_async(bufs[t % 2])
+        evs[t % 2].record(stream)
+        if t > 0:
+            evs[(t - 1) % 2].synchronize()
+            parts = ek.particles_from_buffer(bufs[(t - 1) % 2], npart)
+    evs[(steps - 1) % 2].synchronize()
+    parts = ek.particles_from_buffer(bufs[(steps - 1) % 2], npart)
+    s.sync()
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    return {"value": round(job_mlups(nodes, steps, ws, e2e_s * 1e3), 3), "unit": "MLUPS",
+            "h2d_bytes_per_step": 3 * 8, "d2h_bytes_per_step": len(parts) * ctypes_sizeof_particle(ek),
+            "steps": steps}
+
+
+def form_line(r, w, fp32, hbm_peak, peak_kind):
+    """Throughput, stages and rooflines of one measured system."""
+    K = len(w["valence"])
+    n = r["nodes"]
+    d = {"value": round(r["value"], 3), "unit": "MLUPS", "ms_per_step": None,
+         "stages_ms_per_step": r["stages"], "gpu_launches": r["launches"], "clocks": r["clocks"],
+         "step_roofline": step_roofline(r["value"], step_bytes_per_node(fp32, K), hbm_peak)}
+    lb_alg = lb_bytes_per_node(fp32, K) * n
+    gbs = lb_alg / (r["lb_ms"] / 1e3) / 1e9
+    if fp32:
+        d["roofline"] = {"bound": "hbm", "kernel": "k_lb32_tiled", "achieved": round(gbs, 1),
+                         "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+                         "peak_kind": peak_kind, "traffic": traffic("k_lb32", n),
+                         "algorithmic_bytes": lb_alg, "kernel_ms": round(r["lb_ms"], 4)}
+    else:
+        tflops = LB_FP64_FLOP_PER_NODE * n / (r["lb_ms"] / 1e3) / 1e12
+        d["roofline"] = {"bound": "alu", "kernel": "k_lb_fused", "achieved": round(tflops, 4),
+                         "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s (FP64)",
+                         "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                         "traffic": traffic("k_lb_fused", n), "algorithmic_bytes": lb_alg,
+                         "hbm": {"achieved": round(gbs, 1), "frac": round(gbs / hbm_peak, 4)},
+                         "kernel_ms": round(r["lb_ms"], 4)}
+    return d
 
 
 def main():
@@ -267,16 +435,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline workload only (no 128^3 / 256^3 / FP64 / batched / multigrid lines)")
     args = ap.parse_args()
     import workloads
-    w = workloads.workload("single")
+    w = workloads.workload(HEADLINE)
     if args.impl == "reference":
         return run_reference(args, w)
 
-    import numpy as np
-    import torch
     ws, rank, local = dist_env()
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the host baseline before any CUDA call: its processes are spawned,
+        # and the GPU is not yet busy
+        cpu = time_oracle_all_cores(HEADLINE, SAMPLE_EDGE, 2, 1, budget_s=30.0)
+    import torch
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
     torch.cuda.set_device(local)
@@ -285,7 +458,6 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1607_04572_gb300 import ek
 
-    nodes = w["shape"][0] * w["shape"][1] * w["shape"][2]
     stream = torch.cuda.Stream()
 
     def barrier():
@@ -297,132 +469,73 @@ def main():
     def max_over_ranks(x):
         return max_over_ranks_of(x, ws, "cuda")
 
-    def measure(fp32):
-        """Warm-up, then K steps timed with CUDA events on the context's stream
-        (inputs resident in HBM); then a per-stage split of more steps."""
-        s = build_system(ek, w, fp32)
-        s.set_stream(stream)
-        s.step(max(args.warmup, 3))
-        clk = ClockSampler(local)
-        barrier()
-        clk.start()
-        launches0 = s.kernel_launches()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        clk.mark(True)
-        ev0.record(stream)
-        s.step_async(args.steps)
-        ev1.record(stream)
-        ev1.synchronize()
-        clk.mark(False)
-        barrier()
-        clocks = clk.stop()
-        launches = s.kernel_launches() - launches0
-        s.sync()
-        ms = max_over_ranks(ev0.elapsed_time(ev1))
-        kst = max(10, min(args.steps, 50))
-        stage = s.step_timed(kst)
-        return dict(system=s, ms=ms, value=job_mlups(nodes, args.steps, ws, ms),
-                    launches=launches, clocks=clocks,
-                    stages={k: round(v / kst, 4) for k, v in
-                            zip(["S1_poisson", "S2_flux_lb", "S3_advection", "S4_particles",
-                                 "S5_reflag", "total"], stage)},
-                    lb_ms=stage[1] / kst)
-
-    r32 = measure(True)
-    r64 = measure(False)
-    s = r32["system"]
-    rb = None if args.no_batch else measure_batch(ek, torch, args, barrier, max_over_ranks)
-
-    # ---- end to end through the public API with host buffers (FP32 form) ----
-    # every step: the field E is read from pinned host memory into the step's
-    # launch, the step runs, and the particle records (the mobility
-    # observable) are copied into pinned host memory and decoded on the host;
-    # two record buffers let step t + 1 run while step t's records are read
-    e_host = torch.tensor(w["E"], dtype=torch.float64).pin_memory()
-    e2e_steps = max(5, min(args.steps, 50))
-    npart = s.num_particles()
-    recbytes = npart * ctypes_sizeof_particle(ek)
-    bufs = [torch.zeros(max(recbytes, 1), dtype=torch.uint8).pin_memory() for _ in range(2)]
-    evs = [torch.cuda.Event() for _ in range(2)]
-    barrier()
-    t0 = time.perf_counter()
-    parts = []
-    for t in range(e2e_steps):
-        s.set_field(ek.FIELD_E_EXT, e_host)
-        s.step_async(1)
-        s.get_particles_async(bufs[t % 2])
-        evs[t % 2].record(stream)
-        if t > 0:
-            evs[(t - 1) % 2].synchronize()
-            parts = ek.particles_from_buffer(bufs[(t - 1) % 2], npart)
-    evs[(e2e_steps - 1) % 2].synchronize()
-    parts = ek.particles_from_buffer(bufs[(e2e_steps - 1) % 2], npart)
-    s.sync()
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = job_mlups(nodes, e2e_steps, ws, e2e_s * 1e3)
-    h2d = 3 * 8
-    d2h = len(parts) * ctypes_sizeof_particle(ek)
-
     peaks, peak_kind = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs"))
 
-    def traffic(kernel):
-        t = TRAFFIC[kernel]
-        return t["bytes_per_launch"] if t["source_sha"] == src_sha(t["file"]) else None
-
-    gbs32 = LB32_BYTES_PER_NODE * nodes / (r32["lb_ms"] / 1e3) / 1e9
-    tflops64 = LB_FP64_FLOP_PER_NODE * nodes / (r64["lb_ms"] / 1e3) / 1e12
-    gbs64 = LB_BYTES_PER_NODE * nodes / (r64["lb_ms"] / 1e3) / 1e9
-
+    # ---- the headline: the large box, FP32-storage form -----------------------
+    r = measure(ek, torch, w, True, args, stream, barrier, max_over_ranks, ws, stage_steps=10)
+    e2e = end_to_end(ek, torch, w, r["system"], stream, max(5, min(args.steps, 20)), barrier,
+                     max_over_ranks, ws)
+    head = form_line(r, w, True, hbm_peak, peak_kind)
+    r["system"].close()
     line = {
-        "metric": METRIC, "value": round(r32["value"], 3), "unit": "MLUPS", "n_gpus": ws,
+        "metric": METRIC, "value": head["value"], "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": max(args.warmup, 3),
-        "ms_per_step": round(r32["ms"] / args.steps, 4),
+        "ms_per_step": round(r["ms"] / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (int32 species, f64 particle sums)", "data": "synthetic",
-        "config": {"workload": "single-sphere electrophoresis 128^3, R=8, Z=-300, 2 species, "
-                               "E=0.005; FP32-storage form (FP64 form beside it)",
-                   "nodes": nodes, "particles": len(w["particles"]),
-                   "parallelism": "replicas" if ws > 1 else "single", "l2": FLUSH_NOTE},
-        "roofline": {"bound": "hbm", "kernel": "k_lb32", "achieved": round(gbs32, 1),
-                     "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs32 / hbm_peak, 4),
-                     "peak_kind": peak_kind, "traffic": traffic("k_lb32"),
-                     "algorithmic_bytes": LB32_BYTES_PER_NODE * nodes,
-                     "kernel_ms": round(r32["lb_ms"], 4)},
-        "step_roofline": step_roofline(r32["value"], step_bytes_per_node(True, len(w["valence"])),
-                                       hbm_peak),
-        "stages_ms_per_step": r32["stages"],
-        "fp64_form": {
-            "value": round(r64["value"], 3), "unit": "MLUPS",
-            "ms_per_step": round(r64["ms"] / args.steps, 4), "stages_ms_per_step": r64["stages"],
-            "gpu_launches": r64["launches"], "clocks": r64["clocks"],
-            "step_roofline": step_roofline(r64["value"], step_bytes_per_node(False, len(w["valence"])),
-                                           hbm_peak),
-            "roofline": {"bound": "alu", "kernel": "k_lb_fused", "achieved": round(tflops64, 4),
-                         "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s (FP64)",
-                         "frac": round(tflops64 / FP64_PEAK_TFLOPS, 4),
-                         "traffic": traffic("k_lb_fused"),
-                         "algorithmic_bytes": LB_BYTES_PER_NODE * nodes,
-                         "hbm": {"achieved": round(gbs64, 1), "frac": round(gbs64 / hbm_peak, 4)},
-                         "kernel_ms": round(r64["lb_ms"], 4)}},
-        "speedup_vs_fp64": round(r32["value"] / r64["value"], 2),
-        "e2e": {"value": round(e2e_value, 3), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-        "gpu_launches": r32["launches"],
-        "clocks": r32["clocks"],
+        "config": {"workload": describe(w) + "; FP32-storage form", "nodes": r["nodes"],
+                   "particles": len(w["particles"]),
+                   "parallelism": "replicas" if ws > 1 else "single", "l2": l2_note(w, True)},
+        "roofline": head["roofline"],
+        "step_roofline": head["step_roofline"],
+        "stages_ms_per_step": head["stages_ms_per_step"],
+        "e2e": e2e,
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
     }
-    if rank == 0 and ws == 1 and not args.no_batch:
-        line["poisson_mg"] = measure_poisson_mg(ek, torch)
-    if rb is not None:
+    if not args.no_extra:
+        extra_args = argparse.Namespace(**vars(args))
+        extra_args.steps = min(args.steps, 50)
+        # the single-sphere box in both storage forms (FP64: the parity form)
+        ws1 = workloads.workload("single")
+        r32 = measure(ek, torch, ws1, True, extra_args, stream, barrier, max_over_ranks, ws)
+        r64 = measure(ek, torch, ws1, False, extra_args, stream, barrier, max_over_ranks, ws)
+        l32 = form_line(r32, ws1, True, hbm_peak, peak_kind)
+        l32["ms_per_step"] = round(r32["ms"] / extra_args.steps, 4)
+        l32["workload"] = describe(ws1)
+        l32["e2e"] = end_to_end(ek, torch, ws1, r32["system"], stream, max(5, min(args.steps, 50)),
+                                barrier, max_over_ranks, ws)
+        l64 = form_line(r64, ws1, False, hbm_peak, peak_kind)
+        l64["ms_per_step"] = round(r64["ms"] / extra_args.steps, 4)
+        l64["workload"] = describe(ws1)
+        r32["system"].close()
+        r64["system"].close()
+        line["single_128"] = l32
+        line["fp64_form"] = l64
+        line["speedup_fp32_vs_fp64_128"] = round(r32["value"] / r64["value"], 2)
+        # the 256^3 box with 64 spheres and three species
+        wm = workloads.workload("many")
+        rm = measure(ek, torch, wm, True, extra_args, stream, barrier, max_over_ranks, ws)
+        lm = form_line(rm, wm, True, hbm_peak, peak_kind)
+        lm["ms_per_step"] = round(rm["ms"] / extra_args.steps, 4)
+        lm["workload"] = describe(wm)
+        rm["system"].close()
+        line["many_256"] = lm
+        if rank == 0 and ws == 1:
+            line["poisson_mg"] = measure_poisson_mg(ek, torch)
+        rb = measure_batch(ek, torch, args, barrier, max_over_ranks)
         rb["step_roofline"] = step_roofline(rb["value"], step_bytes_per_node(True, 2), hbm_peak)
         line["batched_form"] = rb
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, done, dt = time_oracle(w, 3, budget_s=20.0, warmup=0)
-        line["cpu_baseline"] = {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                                "sample": f"{done} steps of the {w['shape'][0]}^3 workload, "
-                                          f"{dt:.1f} s, numpy FP64 oracle, single thread"}
+    if cpu is not None:
+        nsp = len(workloads.sub_box(HEADLINE, SAMPLE_EDGE)["particles"])
+        line["cpu_baseline"] = {
+            "value": round(cpu["value"], 4), "unit": "MLUPS", "cores": cpu["procs"],
+            "kind": "oracle",
+            "sample": (f"{SAMPLE_EDGE}^3 periodic sub-box of the headline workload ({nsp} "
+                       f"sphere(s) wholly inside), {cpu['procs']} single-threaded numpy FP64 "
+                       f"oracle replicas in parallel, {cpu['steps']} timed step(s) each after "
+                       f"1 warm-up, {cpu['span_s']:.1f} s")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -118,6 +118,37 @@ def test_moving_matches_co_moving_fixed_sphere(gpu_lib):
     assert abs(vm - vf) <= 0.03 * abs(vf)
 
 
+def test_fp32_mobility_many_spheres_matches_fp64(gpu_lib):
+    """The many-colloid workload at full size (256^3, 64 spheres R = 5 with
+    charges in [-100, -50], species z = +1, -1, +2, E = 0.005): the mean
+    electrophoretic velocity of the spheres along E, averaged over steps
+    1000-2000 (the double layers have formed after a few hundred steps; the
+    window average takes out their slow drift), of the FP32 form within 1e-3
+    of the FP64 form; the FP32 species totals stay exact."""
+    ek = gpu_lib
+    w = workloads.workload("many")
+    K = len(w["valence"])
+
+    def run(flags):
+        s = _system(ek, w, flags)
+        N0 = totals(ek, s, K)
+        s.step(1000)
+        vs = []
+        for _ in range(10):
+            s.step(100)
+            vs.append(np.mean([p["vel"][0] for p in s.get_particles()]))
+        v = float(np.mean(vs))
+        tot = totals(ek, s, K)
+        s.close()
+        return v, N0, tot
+
+    v64, _, _ = run(ek.EK_PV | ek.EK_NEUTRALIZE)
+    v32, N0, tot = run(ek.EK_PV | ek.EK_NEUTRALIZE | FP32)
+    assert v64 < 0.0
+    assert abs(v32 - v64) <= 1e-3 * abs(v64), (v32, v64)
+    assert np.array_equal(tot, N0)
+
+
 def test_fp32_single_workload_full_size(gpu_lib):
     ek = gpu_lib
     w = workloads.workload("single")
