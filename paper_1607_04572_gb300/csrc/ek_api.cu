@@ -64,6 +64,7 @@ struct ek_ctx {
   size_t psibox_cap = 0;  // doubles allocated for psibox
   double* fpart = nullptr;  // S4 partial sums, P * fchunks * FPART
   int fchunks = 0;
+  int fcells = FORCE_CHUNK;  // widened-box cells per S4 force CTA
   double* psum = nullptr;   // (Pcap + 1) * FPART
   int2* surf = nullptr;     // surface-cell list of S5, P * boxmax entries
   int* tie_list = nullptr;  // nodes of possible nearest-surface ties (S4)
@@ -214,6 +215,7 @@ PartArgs part_args(ek_ctx* ctx) {
   a.xfer_cap = ctx->xfer_cap;
   a.fpart = ctx->fpart;
   a.fchunks = ctx->fchunks;
+  a.fcells = ctx->fcells;
   a.emax = ctx->emax;
   a.ifield = ctx->ifield;
   a.ipart = ctx->ipart;
@@ -297,7 +299,13 @@ ek_status run_setup(ek_ctx* ctx) {
     const double dmax = sqrt(3.0) * (rmax + ceil(rmax) + FORCE_MARGIN + 2.0) + 1.0;
     ctx->tie_thr = (float)(2.0 * ldexp(dmax + rmax + 1.0, -21) + ldexp(dmax + rmax, -22));
   }
-  const int fchunks = (emax + FORCE_CHUNK - 1) / FORCE_CHUNK;
+  // cells per S4 force CTA: FORCE_CHUNK, doubled while the particles still
+  // fill eight waves of 912 CTAs (152 SMs x 6) with the larger chunks
+  int fcells = FORCE_CHUNK;
+  while (fcells < 8 * FORCE_CHUNK &&
+         (long long)ctx->P * ((emax + 2 * fcells - 1) / (2 * fcells)) >= 8LL * 152 * 6)
+    fcells *= 2;
+  const int fchunks = (emax + fcells - 1) / fcells;
   if (ctx->P && ((size_t)ctx->P * boxmax > ctx->psibox_cap || fchunks > ctx->fchunks)) {
     if (ctx->psibox) cudaFree(ctx->psibox);
     if (ctx->fpart) cudaFree(ctx->fpart);
@@ -323,6 +331,7 @@ ek_status run_setup(ek_ctx* ctx) {
     ctx->psibox_cap = cap;
     ctx->fchunks = fchunks;
   }
+  ctx->fcells = fcells;
   ctx->boxmax = boxmax;
   ctx->emax = emax;
   if (ctx->P) {

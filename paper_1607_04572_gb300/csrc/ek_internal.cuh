@@ -297,6 +297,7 @@ struct PartArgs {
   int xfer_cap;
   double* fpart;   // per (particle, chunk) partial force/torque sums of S4
   int fchunks;     // chunks per particle in fpart
+  int fcells;      // widened-box cells per chunk (a multiple of FORCE_CHUNK)
   int emax;        // capacity (cells) of one particle's widened box
   const void* ifield;        // real_t, 3N (written by S2)
   const double* ipart;       // 3 per lattice block
@@ -316,8 +317,10 @@ struct PartArgs {
   int* pticket;    // P: S4 force blocks of the particle done (reset by the last)
   int* status;
 };
-// cells per CTA of the S4 force kernel (FORCE_T threads, FORCE_CHUNK / FORCE_T
-// rows of FORCE_T cells each); fpart holds P * fchunks * FPART doubles
+// cells per CTA of the S4 force kernel: FORCE_T threads, each over `fcells /
+// FORCE_T` rows of FORCE_T cells, fcells a multiple of FORCE_CHUNK chosen at
+// set-up (larger when many particles give enough CTAs anyway, so fewer block
+// sums are made); fpart holds P * fchunks * FPART doubles
 constexpr int FORCE_T = 128;
 constexpr int FORCE_CHUNK = 512;
 // per particle: [0..5] Fh Th (momentum exchange), [6..11] Fs Ts (reaction of

@@ -291,7 +291,7 @@ __device__ void block_sum(double (&v)[NV]) {
 //   k_force_assign   every fluid node of a particle's widened box records the
 //                    particle with the nearest surface (minimum image): an
 //                    atomicMin on the key (quantised surface distance, index)
-//   k_particle_forces  grid (particle, chunk of FORCE_CHUNK widened-box cells):
+//   k_particle_forces  grid (particle, chunk of fcells widened-box cells):
 //                    momentum exchange (Eq. 11), the solute force on the
 //                    particle (reaction of the internal solute force on the
 //                    fluid of its nodes) and the field on its own charge
@@ -513,13 +513,13 @@ __device__ void block_sum_f(const float (&v)[NV], const bool (&group_on)[NV / 6]
 }
 
 template <class FM>
-__global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
+__global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 6 : 4) k_particle_forces(PartArgs a) {
   const int p = blockIdx.x;
   const DevParticle& P = a.parts[p];
   const Grid g = a.g;
   const long long N = g.N;
   const int ncell = box_cells(P.elo, P.ehi);
-  const int nb = (ncell + FORCE_CHUNK - 1) / FORCE_CHUNK;
+  const int nb = (ncell + a.fcells - 1) / a.fcells;
   if ((int)blockIdx.y >= nb) return;  // whole CTA beyond this particle's widened box
   const bool pv = a.ph.pv != 0;
   double qnorm = 0.0;
@@ -548,7 +548,8 @@ __global__ void __launch_bounds__(FORCE_T) k_particle_forces(PartArgs a) {
   const int cxi = (int)floor(P.pos[0]), cyi = (int)floor(P.pos[1]), czi = (int)floor(P.pos[2]);
   const float frx = (float)(P.pos[0] - cxi), fry = (float)(P.pos[1] - cyi), frz = (float)(P.pos[2] - czi);
   bool touched[4] = {false, false, false, false};
-  for (int k = 0; k < FORCE_CHUNK / FORCE_T; ++k) {
+  const int rows = a.fcells / FORCE_T;
+  for (int k = 0; k < rows; ++k) {
     const int c = ((int)blockIdx.y + k * nb) * FORCE_T + threadIdx.x;
     if (c >= ncell) break;
     int X, Y, Z;
