@@ -1139,36 +1139,69 @@ __global__ void __launch_bounds__(PSI_CTA) k_psi_surface(PartArgs a) {
     const float bu = c.fb[c.u], bv = c.fb[c.v], bw = c.fb[c.w];
     const float fu = P.fpos[c.u], fv_ = P.fpos[c.v], fw_ = P.fpos[c.w];
     auto off = [](float b, float f, int m) { return __fsub_rn(b + (0.0625f * (float)m - 0.5f), f); };
+    // the squared far and near offsets across the columns are separable: a
+    // lane's columns share one v slab (j = lane mod 16) and take their w slabs
+    // (l) from the lane that holds slab l
     int units = 0;
-    for (int col = lane; col < 256; col += 32) {
-      const int j = col & 15, l = col >> 4;
-      const float v0 = off(bv, fv_, j), v1 = off(bv, fv_, j + 1);
-      const float w0 = off(bw, fw_, l), w1 = off(bw, fw_, l + 1);
-      const float fv = slab_f(v0, v1, true), fw = slab_f(w0, w1, true);
-      const float nv = slab_f(v0, v1, false), nw = slab_f(w0, w1, false);
-      const float far2 = fv * fv + fw * fw, near2 = nv * nv + nw * nw;
+    const int jl = lane & 15;
+    float FV2, NV2, FW2, NW2;
+    {
+      const float v0 = off(bv, fv_, jl), v1 = off(bv, fv_, jl + 1);
+      const float w0 = off(bw, fw_, jl), w1 = off(bw, fw_, jl + 1);
+      const float fv = slab_f(v0, v1, true), nv = slab_f(v0, v1, false);
+      const float fw = slab_f(w0, w1, true), nw = slab_f(w0, w1, false);
+      FV2 = fv * fv;
+      NV2 = nv * nv;
+      FW2 = fw * fw;
+      NW2 = nw * nw;
+    }
+    const float e0 = near >= 0 ? fabsf(off(bu, fu, near)) : 0.0f;
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      const int j = jl, l = (lane >> 4) + 2 * q;
+      const float far2 = FV2 + __shfl_sync(0xffffffffu, FW2, l);
+      const float near2 = NV2 + __shfl_sync(0xffffffffu, NW2, l);
       if (near >= 0) {
-        const float e0 = fabsf(off(bu, fu, near));
+        // the count of planes t (offset e0 + t/16 from the near end) with
+        // (e0 + t/16)^2 + S < R^2 is ceil(v), v = 16 (sqrt(R^2 - S) - e0),
+        // unless v lies within its error bound of an integer (or R^2 - S is
+        // within the margin of 0): then the planes at the boundary are tested
+        auto estimate = [&](float S, int tmax, bool& sure) {
+          const float A = c.R2f - S;
+          if (A <= 2.0f * c.margin) {
+            sure = false;
+            return A > 0.0f ? min(max((int)ceilf((sqrtf(A) - e0) * 16.0f), 0), tmax) : 0;
+          }
+          const float sa = sqrtf(A);
+          const float v = (sa - e0) * 16.0f;
+          // |A - exact| < margin: sqrt off by < margin / sqrt(A) (rsqrtf within
+          // 1%); the roundings of the root, of e0 and of v below
+          // 2^-22 (sqrt(A) + e0 + 1) each
+          const float err = 32.0f * (1.01f * c.margin * rsqrtf(A) + 2.4e-7f * (sa + e0 + 1.0f));
+          sure = fabsf(v - rintf(v)) > err;
+          return min(max((int)ceilf(v), 0), tmax);
+        };
+        bool sure;
         // planes t = 0..16 from the near end whose far corner is inside
-        const float A = c.R2f - far2;
-        int T = A > 0.0f ? (int)ceilf((sqrtf(A) - e0) * 16.0f) : 0;
-        T = min(max(T, 0), 17);
-        auto pin = [&](int t) {
-          const int m = near + step * t;
-          return psi_test(c, fabsf(off(bu, fu, m)), far2, m, -1, j, l, true);
-        };
-        while (T > 0 && !pin(T - 1)) --T;
-        while (T < 17 && pin(T)) ++T;
+        int T = estimate(far2, 17, sure);
+        if (!sure) {
+          auto pin = [&](int t) {
+            const int m = near + step * t;
+            return psi_test(c, fabsf(off(bu, fu, m)), far2, m, -1, j, l, true);
+          };
+          while (T > 0 && !pin(T - 1)) --T;
+          while (T < 17 && pin(T)) ++T;
+        }
         // cubes t = 0..15 whose near face (plane t) is nearer than R
-        const float B = c.R2f - near2;
-        int TN = B > 0.0f ? (int)ceilf((sqrtf(B) - e0) * 16.0f) : 0;
-        TN = min(max(TN, 0), 16);
-        auto pnear = [&](int t) {
-          const int m = near + step * t;
-          return psi_test(c, fabsf(off(bu, fu, m)), near2, m, -1, j, l, false);
-        };
-        while (TN > 0 && !pnear(TN - 1)) --TN;
-        while (TN < 16 && pnear(TN)) ++TN;
+        int TN = estimate(near2, 16, sure);
+        if (!sure) {
+          auto pnear = [&](int t) {
+            const int m = near + step * t;
+            return psi_test(c, fabsf(off(bu, fu, m)), near2, m, -1, j, l, false);
+          };
+          while (TN > 0 && !pnear(TN - 1)) --TN;
+          while (TN < 16 && pnear(TN)) ++TN;
+        }
         units += max(T - 1, 0) + TN;
       } else {
         // the centre within the cell's extent along u: every cube
