@@ -341,3 +341,60 @@ def test_charge_simple_scheme_even_spread():
     assert np.allclose(q[inside], Z / nb, rtol=1e-15, atol=0)
     assert np.all(q[~inside] == 0.0)
     assert abs(q.sum() - Z) < 1e-12 * abs(Z)
+
+
+# --------------------------------------------------------------------------
+# Stokes drag in a periodic array (Hasimoto), on the oracle itself
+# --------------------------------------------------------------------------
+def _hasimoto_K(phi):
+    """Hasimoto's correction for a simple cubic array of spheres: the drag is
+    6 pi eta a U / K with K = 1 - 1.7601 phi^(1/3) + phi - 1.5593 phi^2."""
+    return 1.0 - 1.7601 * phi ** (1.0 / 3.0) + phi - 1.5593 * phi ** 2
+
+
+def _steady_drag(n, R, g, steps):
+    """A fixed sphere in an n^3 periodic box, fluid driven by the body force g
+    along x (nu = 1, TRT 3/16, no ions): the drag on the sphere and the mean
+    fluid velocity at steady state."""
+    o = EKOracle(n, n, n, nu=1.0, bulk=(0.0, 0.0), magic=3.0 / 16.0)
+    o.add_particle((n / 2 + 0.3, n / 2 - 0.2, n / 2 + 0.1), radius=R, charge=0.0, fixed=True)
+    o.g = np.array([g, 0.0, 0.0])
+    hist = []
+    for _ in range(steps // 50):
+        o.step(50)
+        hist.append(o.particles[0].force[0])
+    fluid = o.owner == O.FLUID
+    U = float(o.u[0][fluid].mean())
+    return hist, U, o
+
+
+@pytest.mark.slow
+def test_stokes_drag_with_hasimoto_correction():
+    """At steady state the momentum exchange carries the whole body force
+    (g times the fluid nodes).  The hydrodynamic radius fitted to the 12^3
+    box's drag through Hasimoto's law predicts the 16^3 box's within 5%."""
+    eta = 1.0
+    R, g = 2.5, 2e-6
+    h12, U12, o12 = _steady_drag(12, R, g, 600)
+    h16, U16, o16 = _steady_drag(16, R, g, 1200)
+    for h, o in ((h12, o12), (h16, o16)):
+        assert abs(h[-1] - h[-2]) < 1e-4 * abs(h[-1])  # steady
+        nf = int((o.owner == O.FLUID).sum())
+        assert abs(h[-1] - g * nf) < 2e-3 * g * nf     # the drag balances the body force
+
+    def drag(a, n, U):
+        phi = 4.0 / 3.0 * math.pi * a ** 3 / n ** 3
+        return 6.0 * math.pi * eta * a * U / _hasimoto_K(phi)
+
+    # fit a on the 12^3 box (bisection: the drag grows with a)
+    lo, hi = 1.5, 3.5
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if drag(mid, 12, U12) < h12[-1]:
+            lo = mid
+        else:
+            hi = mid
+    a = 0.5 * (lo + hi)
+    pred = drag(a, 16, U16)
+    assert 1.8 < a < 2.8
+    assert abs(pred / h16[-1] - 1.0) < 0.05, (a, pred, h16[-1])
