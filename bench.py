@@ -315,9 +315,11 @@ def run_reference(args, w):
     if rank != 0:
         return 0
     warm = min(args.warmup, 1)
-    r = time_oracle_all_cores(w["name"], SAMPLE_EDGE, args.steps, warm, budget_s=150.0)
-    sample = (f"{SAMPLE_EDGE}^3 periodic sub-box of the {describe(w)} workload "
-              f"({len(__import__('workloads').sub_box(w['name'], SAMPLE_EDGE)['particles'])} "
+    import workloads
+    edge = min(SAMPLE_EDGE, w["shape"][0])
+    r = time_oracle_all_cores(w["name"], edge, args.steps, warm, budget_s=150.0)
+    sample = (f"{edge}^3 periodic sub-box of the {describe(w)} workload "
+              f"({len(workloads.sub_box(w['name'], edge)['particles'])} "
               f"sphere(s) wholly inside); {r['procs']} single-threaded numpy FP64 oracle "
               f"replicas in parallel, {r['steps']} timed of {args.steps} requested steps each "
               f"after {warm} warm-up step(s)")
@@ -326,7 +328,7 @@ def run_reference(args, w):
             "ms_per_step": round(r["span_s"] / max(r["steps"], 1) * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": describe(w), "nodes": SAMPLE_EDGE ** 3,
+            "config": {"workload": describe(w), "nodes": edge ** 3,
                        "parallelism": "replicas", "l2": "host run"},
             "cpu_baseline": {"value": round(r["value"], 4), "unit": "MLUPS", "cores": r["procs"],
                              "kind": "oracle", "sample": sample},
@@ -437,9 +439,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="headline workload only (no 128^3 / 256^3 / FP64 / batched / multigrid lines)")
+    ap.add_argument("--workload", default=HEADLINE, choices=["large", "many", "single", "small"],
+                    help="the measured workload (the headline is the large box; the others are "
+                         "for profiling smaller cases)")
     args = ap.parse_args()
     import workloads
-    w = workloads.workload(HEADLINE)
+    w = workloads.workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -448,7 +453,7 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # the host baseline before any CUDA call: its processes are spawned,
         # and the GPU is not yet busy
-        cpu = time_oracle_all_cores(HEADLINE, SAMPLE_EDGE, 2, 1, budget_s=30.0)
+        cpu = time_oracle_all_cores(w["name"], min(SAMPLE_EDGE, w["shape"][0]), 2, 1, budget_s=30.0)
     import torch
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
@@ -528,11 +533,12 @@ def main():
         rb["step_roofline"] = step_roofline(rb["value"], step_bytes_per_node(True, 2), hbm_peak)
         line["batched_form"] = rb
     if cpu is not None:
-        nsp = len(workloads.sub_box(HEADLINE, SAMPLE_EDGE)["particles"])
+        edge = min(SAMPLE_EDGE, w["shape"][0])
+        nsp = len(workloads.sub_box(w["name"], edge)["particles"])
         line["cpu_baseline"] = {
             "value": round(cpu["value"], 4), "unit": "MLUPS", "cores": cpu["procs"],
             "kind": "oracle",
-            "sample": (f"{SAMPLE_EDGE}^3 periodic sub-box of the headline workload ({nsp} "
+            "sample": (f"{edge}^3 periodic sub-box of the measured workload ({nsp} "
                        f"sphere(s) wholly inside), {cpu['procs']} single-threaded numpy FP64 "
                        f"oracle replicas in parallel, {cpu['steps']} timed step(s) each after "
                        f"1 warm-up, {cpu['span_s']:.1f} s")}
