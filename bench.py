@@ -102,9 +102,7 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per lattice node
 # of one launch of the kernel, from an ncu capture, valid only for the kernel
 # source it was taken on (otherwise the traffic is reported as null).
-TRAFFIC = {"k_lb_fused": {"bytes_per_node": 755997696 / 128 ** 3,
-                          "source_sha": "85d705496daa5794", "file": "ek_lattice.cu"},
-           "k_lb32": {"bytes_per_node": (202392832 + 179882240) / 128 ** 3,
+TRAFFIC = {"k_lb32": {"bytes_per_node": (202456832 + 180115200) / 128 ** 3,
                       "source_sha": "8e4ea3cf1efc08bf", "file": "ek_lattice32.cu"}}
 
 
@@ -114,7 +112,9 @@ def src_sha(name: str) -> str:
 
 
 def traffic(kernel, nodes):
-    t = TRAFFIC[kernel]
+    t = TRAFFIC.get(kernel)
+    if t is None:
+        return None
     if t["source_sha"] != src_sha(t["file"]):
         return None
     return int(round(t["bytes_per_node"] * nodes))
