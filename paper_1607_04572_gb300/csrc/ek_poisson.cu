@@ -371,20 +371,28 @@ inline bool fast_edge(int n) {
          n == 384 || n == 512;
 }
 
-// multiply by exp(-+2 pi i k / R) (forward: minus), k < R / 2, R = 8 or 16
+// multiply by exp(-+2 pi i k / R) (forward: minus), k < R / 2, R = 8, 16 or 32
 template <int R, bool INV>
 __device__ __forceinline__ float2 wconst(int k, float2 z) {
-  // cos and sin of 2 pi m / 16, m = 0..7
-  constexpr float C16[8] = {1.0f, 0.92387953251128675613f, 0.70710678118654752440f,
-                            0.38268343236508977173f, 0.0f, -0.38268343236508977173f,
-                            -0.70710678118654752440f, -0.92387953251128675613f};
-  constexpr float S16[8] = {0.0f, 0.38268343236508977173f, 0.70710678118654752440f,
-                            0.92387953251128675613f, 1.0f, 0.92387953251128675613f,
-                            0.70710678118654752440f, 0.38268343236508977173f};
-  const int m = k * (16 / R);
+  // cos and sin of 2 pi m / 32, m = 0..15
+  constexpr float C32[16] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
+                             0.83146961230254523708f, 0.70710678118654752440f,
+                             0.55557023301960222474f, 0.38268343236508977173f,
+                             0.19509032201612826785f, 0.0f, -0.19509032201612826785f,
+                             -0.38268343236508977173f, -0.55557023301960222474f,
+                             -0.70710678118654752440f, -0.83146961230254523708f,
+                             -0.92387953251128675613f, -0.98078528040323044913f};
+  constexpr float S32[16] = {0.0f, 0.19509032201612826785f, 0.38268343236508977173f,
+                             0.55557023301960222474f, 0.70710678118654752440f,
+                             0.83146961230254523708f, 0.92387953251128675613f,
+                             0.98078528040323044913f, 1.0f, 0.98078528040323044913f,
+                             0.92387953251128675613f, 0.83146961230254523708f,
+                             0.70710678118654752440f, 0.55557023301960222474f,
+                             0.38268343236508977173f, 0.19509032201612826785f};
+  const int m = k * (32 / R);
   if (m == 0) return z;
-  if (m == 4) return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
-  const float c = C16[m], sn = INV ? S16[m] : -S16[m];
+  if (m == 8) return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+  const float c = C32[m], sn = INV ? S32[m] : -S32[m];
   return make_float2(z.x * c - z.y * sn, z.x * sn + z.y * c);
 }
 
@@ -623,6 +631,101 @@ __global__ void __launch_bounds__(FAST_T) k_fast_yz(PassArgs<float> a, int tx) {
   }
 }
 
+// Y (AXIS 1, forward or inverse) or Z (AXIS 2: forward, Green multiply,
+// inverse) pass for lines of NL = 16 N2 points (256, 512) as four-step
+// transforms on tiles of TX = 256 / N2 consecutive kx: x[N2 n1 + n2] ->
+// X[k1 + 16 k2].  Thread (c, n2) holds the 16 points n1 of its line in
+// registers, transforms them, multiplies by the twiddle exp(-+2 pi i n2 k1 / NL)
+// and writes them to shared memory; after one barrier thread (c, k1) reads the
+// N2 points n2 and transforms them.  The Z pass keeps the result in
+// registers for the Green multiply and runs the inverse the same way back.
+// The shared layout c + TX (n2 + N2 k1) makes both the writes and the reads
+// of a warp contiguous.
+template <int NL, int AXIS, bool INV>
+__global__ void __launch_bounds__(256) k_line4(PassArgs<float> a) {
+  constexpr int N1 = 16, N2 = NL / 16, TX = 256 / N2;
+  __shared__ __align__(16) float2 T[TX * NL];
+  __shared__ float2 tw[NL];
+  const AxisPlan& P = AXIS == 1 ? a.ay : a.az;
+  load_twiddles<NL>(tw, P);
+  const int nxh = a.nxh;
+  const int ntile = (nxh + TX - 1) / TX;
+  const int tile = blockIdx.x % ntile;
+  const int other = blockIdx.x / ntile;  // z (axis 1) or ky (axis 2)
+  const int kx0 = tile * TX;
+  const long long stride = AXIS == 1 ? (long long)nxh : (long long)nxh * a.ny;
+  const long long base = (AXIS == 1 ? (long long)other * a.ny * nxh : (long long)other * nxh) + kx0;
+  const int t = threadIdx.x;
+  const int c = t % TX;
+  const bool col = kx0 + c < nxh;
+  constexpr bool FINV = AXIS == 1 && INV;  // direction of the first transform
+  {
+    // thread (c, n2): the 16 points x[N2 n1 + n2]
+    const int n2 = t / TX;
+    float2 v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1)
+      v[n1] = col ? a.S[base + (long long)(N2 * n1 + n2) * stride + c] : make_float2(0.0f, 0.0f);
+    __syncthreads();  // the twiddles
+    dft_reg<N1, FINV>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const float2 w = tw[n2 * k1];
+      T[c + TX * (n2 + N2 * k1)] = FINV ? cmulconj(v[k1], w) : cmul(v[k1], w);
+    }
+  }
+  __syncthreads();
+  if (t < TX * N1) {
+    // thread (c, k1): the N2 points n2, giving X[k1 + 16 k2]
+    const int k1 = t / TX;
+    float2 z[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) z[n2] = T[c + TX * (n2 + N2 * k1)];
+    dft_reg<N2, FINV>(z);
+    if constexpr (AXIS == 1) {
+      if (col) {
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) a.S[base + (long long)(k1 + N1 * k2) * stride + c] = z[k2];
+      }
+      return;
+    } else {
+      const int kx = kx0 + c;
+      const float lxy = lambda_of(a.ax, col ? kx : 0, 0.0f) + lambda_of(a.ay, other, 0.0f);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int j = k1 + N1 * k2;
+        const float lam = lxy + lambda_of(a.az, j, 0.0f);
+        const float g = (kx == 0 && other == 0 && j == 0) ? 0.0f : a.green_scale / lam;
+        z[k2] = make_float2(z[k2].x * g, z[k2].y * g);
+      }
+      // back: the N2 points k2 of this k1, then the twiddle
+      dft_reg<N2, true>(z);
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) T[c + TX * (n2 + N2 * k1)] = cmulconj(z[n2], tw[n2 * k1]);
+    }
+  }
+  if constexpr (AXIS == 2) {
+    __syncthreads();
+    const int n2 = t / TX;
+    float2 v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = T[c + TX * (n2 + N2 * k1)];
+    dft_reg<N1, true>(v);
+    if (col) {
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) a.S[base + (long long)(N2 * n1 + n2) * stride + c] = v[n1];
+    }
+  }
+}
+
+template <int NL, int AXIS, bool INV>
+void launch_line4(PassArgs<float>& a, cudaStream_t s) {
+  constexpr int TX = 256 / (NL / 16);
+  const int ntile = (a.nxh + TX - 1) / TX;
+  const int nother = AXIS == 1 ? a.nz : a.ny;
+  k_line4<NL, AXIS, INV><<<(unsigned)(ntile * nother), 256, 0, s>>>(a);
+}
+
 // X pass, inverse (complex-to-real), two rows per complex transform (as k_fft_x_inv).
 // Each stored coefficient kk <= NX / 2 is loaded once and gives the inputs k = kk
 // and, conjugated, k = NX - kk; the thread's loads are all issued before its
@@ -723,9 +826,9 @@ void launch_fast_yz(PassArgs<float>& a, int n, cudaStream_t s) {
     case 96: launch_fast_yz_n<96, AXIS, INV>(a, s); break;
     case 128: launch_fast_yz_n<128, AXIS, INV>(a, s); break;
     case 192: launch_fast_yz_n<192, AXIS, INV>(a, s); break;
-    case 256: launch_fast_yz_n<256, AXIS, INV>(a, s); break;
+    case 256: launch_line4<256, AXIS, INV>(a, s); break;
     case 384: launch_fast_yz_n<384, AXIS, INV>(a, s); break;
-    default: launch_fast_yz_n<512, AXIS, INV>(a, s); break;
+    default: launch_line4<512, AXIS, INV>(a, s); break;
   }
 }
 

@@ -40,6 +40,30 @@ def test_fp32_fields_match_oracle(gpu_lib):
         assert np.max(np.abs(p["vel"] - o.particles[0].vel)) < 1e-3 * np.max(np.abs(o.particles[0].vel))
 
 
+def test_fp32_fields_match_oracle_workload_small_100_steps(gpu_lib):
+    """The 32^3 single-sphere workload (R = 4, Z = -50, E = 0.01) for 100 steps in
+    the FP32-storage form against the FP64 oracle, field by field: species
+    and Phi per element (floor 1e-3 of the field's max), populations of fluid
+    nodes, Psi exactly, the particle's position and velocity."""
+    ek = gpu_lib
+    case = workloads.workload("small")
+    o, s = make_pair(ek, case, flags=O.PV | O.NEUTRALIZE | FP32, perturb=0.0)
+    for _ in range(4):
+        o.step(25)
+        s.step(25)
+        assert np.array_equal(s.get_fields(ek.FIELD_OWNER), o.owner.astype(float))
+        fluid = o.owner == O.FLUID
+        for k in range(o.K):
+            assert rel_err(s.get_fields(ek.FIELD_SPECIES, k), o.rho[k]) < 1e-3
+        fg = s.get_fields(ek.FIELD_POPULATIONS)[perm_to_oracle(ek)]
+        assert rel_err(fg[:, fluid], o.f[:, fluid]) < 1e-5
+        assert rel_err(s.get_fields(ek.FIELD_PHI), o.phi) < 1e-3
+        assert rel_err(s.get_fields(ek.FIELD_PSI), o.psi) == 0.0
+        p = s.get_particles()[0]
+        assert np.max(np.abs(p["pos"] - o.particles[0].pos)) < 1e-5
+        assert np.max(np.abs(p["vel"] - o.particles[0].vel)) < 2e-3 * np.max(np.abs(o.particles[0].vel))
+
+
 def test_fp32_species_conserved_exactly(gpu_lib):
     """A heavy sphere dragged across cells: every covering, uncovering, flux and
     advection moves whole units, so the totals never change, bit for bit."""
@@ -149,6 +173,29 @@ def test_fp32_mobility_many_spheres_matches_fp64(gpu_lib):
     assert np.array_equal(tot, N0)
 
 
+def test_fp32_mobility_single_128_stationary(gpu_lib):
+    """The 128^3 single-sphere workload: the electrophoretic velocity averaged
+    over steps 2000-3000 (past the start-up transient), FP32 form within 1e-3
+    of the FP64 form."""
+    ek = gpu_lib
+    w = workloads.workload("single")
+
+    def run(flags):
+        s = _system(ek, w, flags)
+        s.step(2000)
+        vs = []
+        for _ in range(10):
+            s.step(100)
+            vs.append(s.get_particles()[0]["vel"][0])
+        s.close()
+        return float(np.mean(vs))
+
+    v64 = run(ek.EK_PV | ek.EK_NEUTRALIZE)
+    v32 = run(ek.EK_PV | ek.EK_NEUTRALIZE | FP32)
+    assert v64 < 0.0
+    assert abs(v32 - v64) <= 1e-3 * abs(v64), (v32, v64)
+
+
 def test_fp32_single_workload_full_size(gpu_lib):
     ek = gpu_lib
     w = workloads.workload("single")
@@ -167,14 +214,15 @@ def test_fp32_single_workload_full_size(gpu_lib):
 @pytest.mark.parametrize("shape", [(32, 32, 32), (64, 32, 128), (128, 64, 32), (256, 32, 64),
                                    (512, 32, 32), (128, 128, 128), (32, 256, 32), (64, 32, 256),
                                    (48, 32, 32), (32, 48, 64), (96, 24, 48), (192, 48, 96),
-                                   (36, 32, 32)])
+                                   (36, 32, 32), (32, 512, 32), (32, 32, 512), (48, 256, 512)])
 def test_fp32_poisson_shapes(gpu_lib, shape):
     """S1 of the FP32 form against the oracle's Poisson solve of the same
     charge, within FP32 rounding of the spectrum: edges 2^k and 3 2^k from 24
     to 512 take the specialised line transforms (with n_y, n_z in {32, 48, 64,
     128} the y and z passes of a kx plane run on a cluster of two CTAs that
-    exchange halves through distributed shared memory), other edges (36) the
-    generic ones."""
+    exchange halves through distributed shared memory; 256- and 512-point y
+    and z lines run as four-step 16 x 16 and 16 x 32 transforms), other edges
+    (36) the generic ones."""
     ek = gpu_lib
     nx, ny, nz = shape
     s = ek.EKSystem(shape, nu=1.0 / 6.0, rho0=1.0, bjerrum=0.7, valence=(1, -1), D=(0.3, 0.3),
