@@ -299,7 +299,6 @@ __device__ void block_sum(double (&v)[NV]) {
 //                    particle takes the remainder of the solute force on
 //                    nodes no particle claims, split evenly, and integrates
 //                    (symplectic Euler)
-//   k_key_reset      clears the keys of the widened boxes
 // All sums run in a fixed order, so the result is deterministic.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double min_image(double d, int n) {
@@ -435,17 +434,6 @@ __global__ void k_tie_resolve(PartArgs a) {
   }
 }
 
-__global__ void k_key_reset(PartArgs a) {
-  const int p = blockIdx.x;
-  const DevParticle& P = a.parts[p];
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (p == 0 && c == 0) *a.tie_count = 0;
-  if (c >= box_cells(P.kelo, P.kehi)) return;
-  int X, Y, Z;
-  box_coord(c, P.kelo, P.kehi, X, Y, Z);
-  a.fkey[node_of(X, Y, Z, a.g)] = ~0ULL;
-}
-
 // Sum of FORCE_T values per component, fixed order: the block's values are
 // transposed through shared memory and each of 4 threads per component adds a
 // strided quarter, then one thread adds the quarters.  Components of a group
@@ -513,7 +501,7 @@ __device__ void block_sum_f(const float (&v)[NV], const bool (&group_on)[NV / 6]
 }
 
 template <class FM>
-__global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 6 : 4) k_particle_forces(PartArgs a) {
+__global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 5 : 4) k_particle_forces(PartArgs a) {
   const int p = blockIdx.x;
   const DevParticle& P = a.parts[p];
   const Grid g = a.g;
@@ -549,25 +537,50 @@ __global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 6 : 4) k_particle_forces(P
   const float frx = (float)(P.pos[0] - cxi), fry = (float)(P.pos[1] - cyi), frz = (float)(P.pos[2] - czi);
   bool touched[4] = {false, false, false, false};
   const int rows = a.fcells / FORCE_T;
-  for (int k = 0; k < rows; ++k) {
-    const int c = ((int)blockIdx.y + k * nb) * FORCE_T + threadIdx.x;
-    if (c >= ncell) break;
-    int X, Y, Z;
-    long long n;
-    double mx = 0.0, my = 0.0, mz = 0.0;
-    int w3[3];
-    bool first;
+  // cell c of the widened box: coordinates, node, first copy of the node
+  auto locate = [&](int c, int& X, int& Y, int& Z, long long& n, int (&w3)[3], double& mx, double& my,
+                    double& mz) {
     if (FM::fp32) {
       box_coord(c, P.elo, P.ehi, X, Y, Z);
-      first = X - P.elo[0] < g.nx && Y - P.elo[1] < g.ny && Z - P.elo[2] < g.nz;
       w3[0] = wrapi(X, g.nx);
       w3[1] = wrapi(Y, g.ny);
       w3[2] = wrapi(Z, g.nz);
       n = (long long)w3[0] + (long long)g.nx * ((long long)w3[1] + (long long)g.ny * w3[2]);
-    } else {
-      first = ext_cell(P, c, g, X, Y, Z, n, mx, my, mz, w3);
+      return X - P.elo[0] < g.nx && Y - P.elo[1] < g.ny && Z - P.elo[2] < g.nz;
     }
-    const int own = a.owner[n];
+    return ext_cell(P, c, g, X, Y, Z, n, mx, my, mz, w3);
+  };
+  // the next row's cell is located and its owner and key loaded while this
+  // one is processed (the loads of consecutive rows overlap)
+  int nX, nY, nZ, nw3[3];
+  long long nn = 0;
+  double nmx = 0.0, nmy = 0.0, nmz = 0.0;
+  bool nfirst = false;
+  int nown = FLUID;
+  unsigned long long nkey = ~0ULL;
+  int cnext = (int)blockIdx.y * FORCE_T + threadIdx.x;
+  bool nvalid = cnext < ncell;
+  if (nvalid) {
+    nfirst = locate(cnext, nX, nY, nZ, nn, nw3, nmx, nmy, nmz);
+    nown = a.owner[nn];
+    nkey = a.fkey[nn];
+  }
+  for (int k = 0; k < rows; ++k) {
+    if (!nvalid) break;
+    const int X = nX, Y = nY, Z = nZ;
+    const long long n = nn;
+    const double mx = nmx, my = nmy, mz = nmz;
+    const int w3[3] = {nw3[0], nw3[1], nw3[2]};
+    const bool first = nfirst;
+    const int own = nown;
+    const unsigned long long key = nkey;
+    cnext = ((int)blockIdx.y + (k + 1) * nb) * FORCE_T + threadIdx.x;
+    nvalid = k + 1 < rows && cnext < ncell;
+    if (nvalid) {
+      nfirst = locate(cnext, nX, nY, nZ, nn, nw3, nmx, nmy, nmz);
+      nown = a.owner[nn];
+      nkey = a.fkey[nn];
+    }
     const bool in_box = X >= P.lo[0] && X < P.hi[0] && Y >= P.lo[1] && Y < P.hi[1] &&
                         Z >= P.lo[2] && Z < P.hi[2];
     if (own == FLUID && in_box) {
@@ -647,7 +660,15 @@ __global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 6 : 4) k_particle_forces(P
       }
     }
     // reaction of the internal solute force on the fluid nodes this particle claims
-    if (first && own == FLUID && (int)(a.fkey[n] & 0xFFFFFull) == p) {
+    // the key of a node is cleared by the particle it names, right after
+    // reading it: any other particle reading it meanwhile finds either that
+    // key or an empty one, and neither names it
+    bool mine = false;
+    if (first && (int)(key & 0xFFFFFull) == p) {
+      a.fkey[n] = ~0ULL;
+      mine = true;
+    }
+    if (mine && own == FLUID) {
       touched[1] = true;
       if (FM::fp32) {
         const float ix = ((const float*)a.ifield)[n];
@@ -770,7 +791,10 @@ __global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 6 : 4) k_particle_forces(P
   if (!last) return;
   __threadfence();
   integrate_all(a);
-  if (threadIdx.x == 0) *a.ticket = 0;
+  if (threadIdx.x == 0) {
+    *a.ticket = 0;
+    *a.tie_count = 0;  // the next step's assignment lists its ties afresh
+  }
 }
 
 // New box of a particle at `pos`: the cells within R (+1 below, +2 above),
@@ -911,8 +935,6 @@ __device__ void integrate_all(const PartArgs& a) {
         Pp->velf[d] = (float)vel;
         Pp->omegaf[d] = (float)omega;
         // S5 starts here: the boxes follow the new position
-        Pp->kelo[d] = Pp->elo[d];
-        Pp->kehi[d] = Pp->ehi[d];
         fin[3 * pl + d] = isfinite(pos) ? 1 : 0;
         if (d == 0) posd[0] = pos;
         else if (d == 1) posd[1] = pos;
@@ -1172,12 +1194,13 @@ __global__ void __launch_bounds__(PSI_CTA) k_psi_surface(PartArgs a) {
             sure = false;
             return A > 0.0f ? min(max((int)ceilf((sqrtf(A) - e0) * 16.0f), 0), tmax) : 0;
           }
-          const float sa = sqrtf(A);
+          const float ra = rsqrtf(A);
+          const float sa = A * ra;  // the root within a few ulp
           const float v = (sa - e0) * 16.0f;
-          // |A - exact| < margin: sqrt off by < margin / sqrt(A) (rsqrtf within
-          // 1%); the roundings of the root, of e0 and of v below
-          // 2^-22 (sqrt(A) + e0 + 1) each
-          const float err = 32.0f * (1.01f * c.margin * rsqrtf(A) + 2.4e-7f * (sa + e0 + 1.0f));
+          // |A - exact| < margin: the root off by < margin / sqrt(A) (ra within
+          // 1%); the approximate root, e0 and v off by less than
+          // 2^-21 (sqrt(A) + e0 + 1) together
+          const float err = 32.0f * (1.01f * c.margin * ra + 4.8e-7f * (sa + e0 + 1.0f));
           sure = fabsf(v - rintf(v)) > err;
           return min(max((int)ceilf(v), 0), tmax);
         };
@@ -1427,9 +1450,6 @@ cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s, int parts) {
     k_tie_resolve<<<8, 256, 0, s>>>(a);
   }
   if (parts & S4_FORCES) k_particle_forces<FM><<<dim3(a.P, a.fchunks), FORCE_T, 0, s>>>(a);
-  // the widened boxes have moved with the integration: clear the keys of the
-  // old ones, which the integration kept in kelo / kehi
-  if (parts & S4_KEY_RESET) k_key_reset<<<dim3(a.P, echunks), PT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
