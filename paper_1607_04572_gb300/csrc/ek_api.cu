@@ -435,7 +435,7 @@ ek_status enqueue_stage(ek_ctx* ctx, int stage, cudaEvent_t mid = nullptr) {
     case 4: {
       PartArgs a = part_args(ctx);
       EK_CUDA(launch_particle_forces(a, s));
-      ctx->launches += ctx->P > 0 ? 4 : 0;
+      ctx->launches += ctx->P > 0 ? 3 : 0;
       return EK_OK;
     }
     case 5: {
@@ -470,8 +470,7 @@ ek_status enqueue_step(ek_ctx* ctx) {
     EK_CUDA(launch_reflag(pa, true, s, 1));
     EK_CUDA(ctx->fp32 ? launch_advection32(la, s) : launch_advection(la, s));
     EK_CUDA(launch_reflag(pa, true, s, 2));
-    EK_CUDA(launch_particle_forces(pa, s, S4_KEY_RESET));
-    ctx->launches += (ctx->p.nspecies > 0 ? 2 : 1) + 11;
+    ctx->launches += (ctx->p.nspecies > 0 ? 2 : 1) + 10;
     return EK_OK;
   }
   if (ctx->P) {
@@ -493,8 +492,6 @@ ek_status enqueue_step(ek_ctx* ctx) {
     EK_CUDA(launch_particle_forces(pa, ctx->aux, S4_FORCES));
     EK_CUDA(launch_reflag(pa, true, ctx->aux, 1));
     EK_CUDA(cudaEventRecord(ctx->ev_part, ctx->aux));
-    // clearing the keys overlaps the transitions
-    EK_CUDA(launch_particle_forces(pa, ctx->aux, S4_KEY_RESET));
     EK_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
   }
   EK_CUDA(ctx->fp32 ? launch_advection32(la, s) : launch_advection(la, s));
@@ -503,7 +500,7 @@ ek_status enqueue_step(ek_ctx* ctx) {
     EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_part, 0));
     EK_CUDA(launch_reflag(pa, true, s, 2));
     EK_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
-    ctx->launches += 11;
+    ctx->launches += 10;
   }
   return EK_OK;
 }

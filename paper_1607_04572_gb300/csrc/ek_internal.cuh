@@ -78,7 +78,6 @@ struct DevParticle {
   int lo[3], hi[3];  // box [lo, hi) in unwrapped coordinates, current position
   int ulo[3], uhi[3];  // union of the previous and current boxes (transitions)
   int elo[3], ehi[3];  // box widened by ceil(R) + FORCE_MARGIN (solute force region)
-  int kelo[3], kehi[3];  // the widened box whose assignment keys S4 set (cleared after)
   // float forms for the octree pre-test, set with the box: integer part and
   // fraction of the centre, R^2 and the pre-test margin
   int ipos[3];
@@ -329,10 +328,10 @@ constexpr int FORCE_CHUNK = 512;
 // [18..20] a slice of the lattice total of the internal force (first particle
 // only), [16..17] and [21..23] unused
 constexpr int FPART = 24;
-// S4 in three launches: the nearest-surface assignment (needs only the
-// particle positions, so it may run beside S1/S2), the forces with the
-// integration (after S2), and the clearing of the assignment keys
-constexpr int S4_ASSIGN = 1, S4_FORCES = 2, S4_KEY_RESET = 4, S4_ALL = 7;
+// S4 in two parts: the nearest-surface assignment (needs only the particle
+// positions, so it may run beside S1/S2), and the forces with the
+// integration (after S2), which also clear the assignment keys
+constexpr int S4_ASSIGN = 1, S4_FORCES = 2, S4_ALL = 3;
 cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s, int parts = S4_ALL);
 // S5; parts: 1 = re-flag, Psi and charge (no species access), 2 = transitions
 // (species after S3), 3 = both
