@@ -298,11 +298,19 @@ ek_status ek_poisson_solve_static(const double* q, double* phi, int nx, int ny, 
  * The systems are ordinary contexts, created and set up by the caller
  * (ek_create, ek_add_particle, ek_set_field); the batch borrows them (they
  * must outlive it and are not destroyed by it).  One batch step advances
- * every system by one time step, exactly as ek_step would, with all systems'
- * kernels in one CUDA graph launch: the systems are independent branches of
- * the graph, so their kernels run side by side on the GPU.  The graph is
- * captured on the first step (one per ping-pong parity) and again whenever a
- * system's set-up, field E / body force or tuning changes.
+ * every system by one time step, exactly as ek_step would, in one CUDA graph
+ * launch, in one of two forms:
+ *  - fused (when every system has the FP32 storage form, the same number of
+ *    species and the same partial-volume choice; the default then): each
+ *    kernel of the step runs once for the whole batch over a list of
+ *    (system, block) ranges -- a system's CTAs find its arguments in a device
+ *    table -- so a step is about twenty launches whatever the number of
+ *    systems.  S1 of the systems whose edges are all 32, 48 or 64 shares
+ *    launches by FFT kernel variant; other systems' S1 runs per system.
+ *  - branches: each system's own step is an independent branch of the graph,
+ *    so the systems' kernels run side by side on the GPU.
+ * The graph is captured on the first step (one per ping-pong parity) and
+ * again whenever a system's set-up, field E / body force or tuning changes.
  *
  * Work of a batch step is ordered on the batch stream only: call
  * ek_batch_sync before reading a system (ek_get_fields, ek_get_particles) or
@@ -327,17 +335,24 @@ ek_status ek_batch_step(ek_batch* b, int nsteps);
 /* Wait for the batch stream and read every system's device status word; the
  * first failing system's status is returned (ek_batch_last_error names it). */
 ek_status ek_batch_sync(ek_batch* b);
-/* Autotuner: times every candidate configuration -- branch streams at capture
- * (8, 16, 32, 64 or one per system, at most 64), FP32 S2 segment length (2, 4
- * or 8 planes per block) and whether each system's particle chain runs beside
- * its advection or in line -- over 2 + trial_steps real batch steps each (the
- * systems advance by those steps), keeps the fastest and stores its time per
- * batch step in *best_ms (may be null).  Results do not depend on the choice
- * except for the summation order of the lattice-block force sums. */
+/* Autotuner: times every candidate configuration -- the fused form (where
+ * the batch allows it) or branches with 8, 16, 32, 64 or one branch stream
+ * per system (at most 64), FP32 S2 segment length (2, 4 or 8 planes per
+ * block), and whether the particle chain runs beside the advection or in line
+ * -- over 2 + trial_steps real batch steps each (the systems advance by those
+ * steps), keeps the fastest and stores its time per batch step in *best_ms
+ * (may be null).  Results do not depend on the choice except for the
+ * summation order of the lattice-block force sums. */
 ek_status ek_batch_tune(ek_batch* b, int trial_steps, double* best_ms);
 /* Current configuration: cfg[0] branch streams, cfg[1] planes per S2 block,
- * cfg[2] particle chain beside the advection (1) or in line (0). */
-ek_status ek_batch_config(const ek_batch* b, int cfg[3]);
+ * cfg[2] particle chain beside the advection (1) or in line (0), cfg[3] the
+ * fused form (1) or branches (0). */
+ek_status ek_batch_config(const ek_batch* b, int cfg[4]);
+/* Set the configuration (cfg as ek_batch_config gives it: branch streams 1 ..
+ * min(nsys, 64), planes per S2 block 1 .. 64, overlap 0 or 1, fused 0 or 1);
+ * waits for the batch's earlier work.  EK_ERR_ARG for a value out of range or
+ * the fused form on a batch that does not allow it. */
+ek_status ek_batch_set_config(ek_batch* b, const int cfg[4]);
 /* Number of systems; 0 for a null batch. */
 int ek_batch_size(const ek_batch* b);
 /* Reason for the last failure of a batch call. */

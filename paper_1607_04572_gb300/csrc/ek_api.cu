@@ -1313,6 +1313,28 @@ struct ek_batch {
   int overlap = 1;  // particle chain beside S3 in each system
   int device = 0;
   std::string err;
+  // Stage launches over all systems (FP32 systems with one species count and
+  // one partial-volume choice): each kernel of the step runs once for the
+  // whole batch over a list of (system, block) ranges instead of once per
+  // system.  Per parity key: one device block holding the argument tables and
+  // the ranges, and the launches made from it.
+  bool fusable = false;
+  int fuse = 0;  // 1: stage launches over all systems; 0: a graph branch per system
+  struct Launch {
+    int variant = 0;    // FFT kernel variant
+    size_t slot = 0;    // byte offset of its BatchSlot ranges in the block
+    int nslot = 0, ctas = 0;
+  };
+  struct Fused {
+    char* dev = nullptr;
+    size_t o_pre = 0, o_post = 0, o_lb = 0, o_pa = 0;  // argument tables
+    Launch part[PK_COUNT];
+    Launch lb, adv;
+    std::vector<Launch> fft[3];  // per pass, one per kernel variant
+    std::vector<int> s1_alone;   // systems whose S1 runs by itself (other edges)
+  } fused[2];
+  cudaStream_t aux = nullptr;  // the particle chain beside S3 in the fused step
+  cudaEvent_t ev_lb = nullptr, ev_part = nullptr;
 };
 
 namespace {
@@ -1323,6 +1345,11 @@ ek_status bfail(ek_batch* b, ek_status st, const std::string& msg) {
 }
 
 void batch_drop(ek_batch* b) {
+  if ((b->fused[0].dev || b->fused[1].dev) && b->stream) cudaStreamSynchronize(b->stream);
+  for (int i = 0; i < 2; ++i) {
+    if (b->fused[i].dev) cudaFree(b->fused[i].dev);
+    b->fused[i] = ek_batch::Fused();
+  }
   for (int i = 0; i < 2; ++i) {
     if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
     b->graph[i] = nullptr;
@@ -1399,6 +1426,202 @@ ek_status batch_capture(ek_batch* b, int key) {
   return EK_OK;
 }
 
+// The device block of the fused step for the systems' current parities: the
+// particle arguments before and after S2's buffer swap, the S2/S3 entries,
+// the S1 pass arguments, and per launch the ranges of the systems with work.
+ek_status fused_build(ek_batch* b, int key) {
+  ek_batch::Fused& F = b->fused[key];
+  const size_t n = b->sys.size();
+  const size_t pas = poisson_batch_args_size();
+  std::vector<PartArgs> pre(n), post(n);
+  std::vector<LBBatchEntry> lbt(n);
+  std::vector<char> pargs(n * pas);
+  for (size_t i = 0; i < n; ++i) {
+    ek_ctx* c = b->sys[i];
+    const int cur0 = c->cur;
+    pre[i] = part_args(c);
+    poisson_batch_args(&pargs[i * pas], c->plan, (const int*)c->rho[c->cur],
+                       c->has_qwall ? (const float*)c->qwall : nullptr, (const float*)c->qpart, c->ph,
+                       (float*)c->phi, (float2*)c->spectrum);
+    lbt[i].a = lb_args(c);
+    lbt[i].c = make_phys32(c->ph);
+    c->cur = 1 - c->cur;
+    post[i] = part_args(c);
+    c->cur = cur0;
+  }
+  const auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  size_t off = 0;
+  F.o_pre = off;
+  off = up(off + n * sizeof(PartArgs));
+  F.o_post = off;
+  off = up(off + n * sizeof(PartArgs));
+  F.o_lb = off;
+  off = up(off + n * sizeof(LBBatchEntry));
+  F.o_pa = off;
+  off = up(off + n * pas);
+  std::vector<BatchSlot> slots;  // all launches' ranges, after the tables
+  const size_t o_slots = off;
+  // one launch over the systems' (gx, gy) grids, in system order
+  const auto make = [&](const std::vector<std::tuple<int, int, int>>& items, int variant) {
+    ek_batch::Launch L;
+    L.variant = variant;
+    L.slot = o_slots + slots.size() * sizeof(BatchSlot);
+    for (const auto& it : items) {
+      const int gx = std::get<1>(it), gy = std::get<2>(it);
+      if (gx <= 0 || gy <= 0) continue;
+      slots.push_back(BatchSlot{L.ctas, gx, gy, std::get<0>(it)});
+      L.ctas += gx * gy;
+      ++L.nslot;
+    }
+    return L;
+  };
+  for (int k = 0; k < PK_COUNT; ++k) {
+    std::vector<std::tuple<int, int, int>> items;
+    for (size_t i = 0; i < n; ++i) {
+      int gx, gy;
+      particle_batch_grid(k, k <= PK_TIE ? pre[i] : post[i], gx, gy);
+      items.emplace_back((int)i, gx, gy);
+    }
+    F.part[k] = make(items, 0);
+  }
+  F.s1_alone.clear();
+  for (size_t i = 0; i < n; ++i)
+    if (!poisson_batch_ok(b->sys[i]->plan)) F.s1_alone.push_back((int)i);
+  for (int pass = 0; pass < 3; ++pass) {
+    std::map<int, std::vector<std::tuple<int, int, int>>> groups;  // by kernel variant
+    for (size_t i = 0; i < n; ++i) {
+      if (!poisson_batch_ok(b->sys[i]->plan)) continue;
+      int variant, ctas;
+      poisson_batch_pass(b->sys[i]->plan, pass, &pargs[i * pas], variant, ctas);
+      groups[variant].emplace_back((int)i, ctas, 1);
+    }
+    F.fft[pass].clear();
+    for (const auto& gi : groups) F.fft[pass].push_back(make(gi.second, gi.first));
+  }
+  {
+    std::vector<std::tuple<int, int, int>> il, ia;
+    for (size_t i = 0; i < n; ++i) {
+      int gx, gy;
+      lb32_batch_grid(lbt[i].a, gx, gy);
+      il.emplace_back((int)i, gx, gy);
+      advect32_batch_grid(lbt[i].a, gx, gy);
+      ia.emplace_back((int)i, gx, gy);
+    }
+    F.lb = make(il, 0);
+    F.adv = make(ia, 0);
+  }
+  const size_t total = o_slots + slots.size() * sizeof(BatchSlot);
+  std::vector<char> host(total, 0);
+  memcpy(host.data() + F.o_pre, pre.data(), n * sizeof(PartArgs));
+  memcpy(host.data() + F.o_post, post.data(), n * sizeof(PartArgs));
+  memcpy(host.data() + F.o_lb, lbt.data(), n * sizeof(LBBatchEntry));
+  memcpy(host.data() + F.o_pa, pargs.data(), n * pas);
+  if (!slots.empty()) memcpy(host.data() + o_slots, slots.data(), slots.size() * sizeof(BatchSlot));
+  if (cudaMalloc((void**)&F.dev, total) != cudaSuccess) {
+    F.dev = nullptr;
+    return bfail(b, EK_ERR_NOMEM, "batch tables could not be allocated");
+  }
+  if (cudaMemcpy(F.dev, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
+    return bfail(b, EK_ERR_CUDA, "batch tables could not be copied");
+  return EK_OK;
+}
+
+// The fused step as a graph: every kernel once for all systems, in the order
+// of a single system's step (the assignment beside S1 and S2, the forces and
+// the re-flag beside S3 when overlap is chosen, the transitions after both).
+ek_status batch_capture_fused(ek_batch* b, int key) {
+  ek_batch::Fused& F = b->fused[key];
+  if (F.dev) {
+    cudaStreamSynchronize(b->stream);
+    cudaFree(F.dev);
+    F = ek_batch::Fused();
+  }
+  ek_status st = fused_build(b, key);
+  if (st != EK_OK) return st;
+  const size_t n = b->sys.size();
+  const ek_ctx* c0 = b->sys[0];
+  const int K = c0->ph.K;
+  const bool pv = c0->ph.pv != 0;
+  char* base = F.dev;
+  long long count = 0;
+  std::vector<long long> alone(n, 0);
+  cudaStream_t s = b->stream;
+  cudaStream_t ps = b->overlap ? b->aux : s;  // where the particle chain runs
+  const auto part = [&](int k, cudaStream_t on) {
+    const ek_batch::Launch& L = F.part[k];
+    if (L.ctas == 0) return cudaSuccess;
+    ++count;
+    const PartArgs* tab = (const PartArgs*)(base + (k <= PK_TIE ? F.o_pre : F.o_post));
+    return launch_particle_batch(k, BatchLaunch<PartArgs>{tab, (const BatchSlot*)(base + L.slot), L.nslot, L.ctas}, on);
+  };
+  const auto lbl = [&](const ek_batch::Launch& L) {
+    return BatchLaunch<LBBatchEntry>{(const LBBatchEntry*)(base + F.o_lb), (const BatchSlot*)(base + L.slot),
+                                     L.nslot, L.ctas};
+  };
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return bfail(b, EK_ERR_CUDA, "batch capture could not start");
+  cudaError_t e = cudaSuccess;
+  const auto ok = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  if (b->overlap) {
+    ok(cudaEventRecord(b->ev_fork, s));
+    ok(cudaStreamWaitEvent(b->aux, b->ev_fork, 0));
+  }
+  ok(part(PK_ASSIGN, ps));
+  ok(part(PK_TIE, ps));
+  for (int pass = 0; pass < 3; ++pass) {
+    for (const ek_batch::Launch& L : F.fft[pass]) {
+      ok(launch_poisson_batch(pass, L.variant, base + F.o_pa, (const BatchSlot*)(base + L.slot), L.nslot,
+                              L.ctas, s));
+      ++count;
+    }
+  }
+  for (int i : F.s1_alone) {
+    ek_ctx* c = b->sys[i];
+    ok(poisson_solve_f32(c->plan, (const int*)c->rho[c->cur], c->has_qwall ? (const float*)c->qwall : nullptr,
+                         (const float*)c->qpart, c->ph, (float*)c->phi, (float2*)c->spectrum, s));
+    alone[i] += poisson_kernel_count(c->plan, true);
+  }
+  ok(launch_lb32_batch(lbl(F.lb), K, pv, s));
+  ++count;
+  if (b->overlap) {
+    ok(cudaEventRecord(b->ev_lb, s));
+    ok(cudaStreamWaitEvent(b->aux, b->ev_lb, 0));
+  }
+  for (int k = PK_FORCES; k <= PK_CHARGE; ++k) ok(part(k, ps));
+  if (b->overlap) ok(cudaEventRecord(b->ev_part, b->aux));
+  if (K > 0) {
+    ok(launch_advection32_batch(lbl(F.adv), K, s));
+    ++count;
+  }
+  if (b->overlap) ok(cudaStreamWaitEvent(s, b->ev_part, 0));
+  ok(part(PK_TRANS, s));
+  ok(part(PK_APPLY, s));
+  const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+  if (e != cudaSuccess || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return bfail(b, EK_ERR_CUDA, std::string("fused batch capture failed: ") +
+                                     cudaGetErrorString(e != cudaSuccess ? e : ec));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&b->graph[key], graph, cudaGraphInstantiateFlagUseNodePriority);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return bfail(b, EK_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(ei));
+  // the batch's launches are counted on the first system, S1 run alone on
+  // its own system
+  b->dlaunch[key].assign(n, 0);
+  for (size_t i = 0; i < n; ++i) b->dlaunch[key][i] = alone[i];
+  b->dlaunch[key][0] += count;
+  b->cur_at[key].resize(n);
+  b->version_at[key].resize(n);
+  for (size_t i = 0; i < n; ++i) {
+    b->cur_at[key][i] = b->sys[i]->cur;
+    b->version_at[key][i] = b->sys[i]->version;
+  }
+  return EK_OK;
+}
+
 bool batch_graph_valid(const ek_batch* b, int key) {
   if (!b->graph[key] || b->cur_at[key].size() != b->sys.size()) return false;
   for (size_t i = 0; i < b->sys.size(); ++i)
@@ -1413,7 +1636,7 @@ ek_status batch_step_once(ek_batch* b) {
       cudaGraphExecDestroy(b->graph[key]);
       b->graph[key] = nullptr;
     }
-    ek_status st = batch_capture(b, key);
+    ek_status st = b->fuse && b->fusable ? batch_capture_fused(b, key) : batch_capture(b, key);
     if (st != EK_OK) return st;
   }
   if (cudaGraphLaunch(b->graph[key], b->stream) != cudaSuccess)
@@ -1462,9 +1685,20 @@ ek_status ek_batch_create(ek_ctx* const* systems, int nsys, ek_batch** out) {
     ok = cudaStreamCreateWithFlags(&b->branch[w], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->ev_join[w], cudaEventDisableTiming) == cudaSuccess;
   }
+  // the fused step's particle chain runs on a stream of the greatest
+  // priority, as a single system's does
+  int lo_pri = 0, hi_pri = 0;
+  ok = ok && cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri) == cudaSuccess &&
+       cudaStreamCreateWithPriority(&b->aux, cudaStreamNonBlocking, hi_pri) == cudaSuccess &&
+       cudaEventCreateWithFlags(&b->ev_lb, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&b->ev_part, cudaEventDisableTiming) == cudaSuccess;
   // the systems' earlier work (set-up, fields) is on their own streams
   for (ek_ctx* c : b->sys) ok = ok && cudaStreamSynchronize(c->stream) == cudaSuccess;
   b->width = std::min(nbranch, 16);
+  b->fusable = true;
+  for (ek_ctx* c : b->sys)
+    b->fusable = b->fusable && c->fp32 && c->ph.K == b->sys[0]->ph.K && c->ph.pv == b->sys[0]->ph.pv;
+  b->fuse = b->fusable ? 1 : 0;
   if (!ok) {
     ek_batch_destroy(b);
     return EK_ERR_CUDA;
@@ -1484,6 +1718,9 @@ ek_status ek_batch_destroy(ek_batch* b) {
     if (b->ev_join[w]) cudaEventDestroy(b->ev_join[w]);
   }
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_lb) cudaEventDestroy(b->ev_lb);
+  if (b->ev_part) cudaEventDestroy(b->ev_part);
+  if (b->aux) cudaStreamDestroy(b->aux);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return EK_OK;
@@ -1541,11 +1778,12 @@ ek_status ek_batch_step(ek_batch* b, int nsteps) {
   return ek_batch_sync(b);
 }
 
-ek_status ek_batch_config(const ek_batch* b, int cfg[3]) {
+ek_status ek_batch_config(const ek_batch* b, int cfg[4]) {
   if (!b || !cfg) return EK_ERR_ARG;
   cfg[0] = b->width;
   cfg[1] = b->planes;
   cfg[2] = b->overlap;
+  cfg[3] = b->fuse && b->fusable ? 1 : 0;
   return EK_OK;
 }
 
@@ -1561,43 +1799,44 @@ ek_status ek_batch_tune(ek_batch* b, int trial_steps, double* best_ms) {
   for (int w : {8, 16, 32, 64})
     if (w < nbranch) widths.push_back(w);
   widths.push_back(nbranch);
-  const int planes_set[3] = {2, 4, 8};
+  // candidates (fuse, branch width, planes per S2 block, overlap); the fused
+  // step has no branches
+  std::vector<std::tuple<int, int, int, int>> cands;
+  for (int pl : {2, 4, 8})
+    for (int ov = 0; ov <= 1; ++ov) {
+      if (b->fusable) cands.emplace_back(1, b->width, pl, ov);
+      for (int w : widths) cands.emplace_back(0, w, pl, ov);
+    }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return bfail(b, EK_ERR_CUDA, "event creation failed");
   double best = 1e300;
-  int bw = b->width, bp = b->planes, bo = b->overlap;
+  int bf = b->fuse, bw = b->width, bp = b->planes, bo = b->overlap;
   ek_status st = EK_OK;
-  for (int w : widths) {
-    for (int pl : planes_set) {
-      for (int ov = 0; ov <= 1 && st == EK_OK; ++ov) {
-        b->width = w;
-        b->planes = pl;
-        b->overlap = ov;
-        batch_apply(b);
-        batch_drop(b);
-        st = ek_batch_step_async(b, 2);  // captures both parities and uploads them
-        if (st != EK_OK) break;
-        if (cudaEventRecord(e0, b->stream) != cudaSuccess) st = EK_ERR_CUDA;
-        if (st == EK_OK) st = ek_batch_step_async(b, trial_steps);
-        if (st == EK_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess ||
-                            cudaEventSynchronize(e1) != cudaSuccess))
-          st = EK_ERR_CUDA;
-        float ms = 0.0f;
-        if (st == EK_OK) cudaEventElapsedTime(&ms, e0, e1);
-        const double per = (double)ms / trial_steps;
-        if (st == EK_OK && per < best) {
-          best = per;
-          bw = w;
-          bp = pl;
-          bo = ov;
-        }
-      }
+  for (const auto& cand : cands) {
+    std::tie(b->fuse, b->width, b->planes, b->overlap) = cand;
+    batch_apply(b);
+    batch_drop(b);
+    st = ek_batch_step_async(b, 2);  // captures both parities and uploads them
+    if (st != EK_OK) break;
+    if (cudaEventRecord(e0, b->stream) != cudaSuccess) st = EK_ERR_CUDA;
+    if (st == EK_OK) st = ek_batch_step_async(b, trial_steps);
+    if (st == EK_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess ||
+                        cudaEventSynchronize(e1) != cudaSuccess))
+      st = EK_ERR_CUDA;
+    if (st != EK_OK) break;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = (double)ms / trial_steps;
+    if (per < best) {
+      best = per;
+      std::tie(bf, bw, bp, bo) = cand;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != EK_OK) return st;
+  b->fuse = bf;
   b->width = bw;
   b->planes = bp;
   b->overlap = bo;
@@ -1605,6 +1844,23 @@ ek_status ek_batch_tune(ek_batch* b, int trial_steps, double* best_ms) {
   batch_drop(b);
   if (best_ms) *best_ms = best;
   return ek_batch_sync(b);
+}
+
+ek_status ek_batch_set_config(ek_batch* b, const int cfg[4]) {
+  if (!b || !cfg) return EK_ERR_ARG;
+  if (cfg[0] < 1 || cfg[0] > (int)b->branch.size() || cfg[1] < 1 || cfg[1] > 64 || cfg[2] < 0 ||
+      cfg[2] > 1 || cfg[3] < 0 || cfg[3] > 1)
+    return bfail(b, EK_ERR_ARG, "configuration out of range");
+  if (cfg[3] && !b->fusable)
+    return bfail(b, EK_ERR_ARG, "the fused form needs FP32 systems with one species count and partial-volume choice");
+  cudaSetDevice(b->device);
+  b->width = cfg[0];
+  b->planes = cfg[1];
+  b->overlap = cfg[2];
+  b->fuse = cfg[3];
+  batch_apply(b);
+  batch_drop(b);
+  return EK_OK;
 }
 
 int ek_batch_size(const ek_batch* b) { return b ? (int)b->sys.size() : 0; }

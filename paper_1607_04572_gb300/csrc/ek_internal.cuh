@@ -177,6 +177,48 @@ inline dim3 lattice_grid32(const Grid& g, int nzb) {
               (unsigned)nzb);
 }
 
+// ---------------------------------------------------------------------------
+// Launches over the systems of a batch.  One 1-D launch runs a stage for many
+// systems: system s owns the CTAs [cta0, cta0 + gx * gy) and runs them as its
+// own gx x gy grid (x fastest) with its own arguments, read from a device
+// table.  A kernel body takes its block as a Blk, so that one body serves the
+// launch for one system (the Blk from blockIdx and gridDim) and the batched
+// launch (the Blk of the system's range).
+// ---------------------------------------------------------------------------
+struct Blk {
+  int x, y;  // block coordinates in the system's grid
+  int nx;    // the grid's x extent (the stride of grid-stride loops)
+};
+struct BatchSlot {
+  int cta0, gx, gy;
+  int entry;  // the system's row of the argument table
+};
+__device__ __forceinline__ Blk grid_blk() { return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x}; }
+// the system whose range holds this CTA (binary search over the ascending
+// cta0), and the CTA's block in that system's grid
+__device__ __forceinline__ Blk batch_blk(const BatchSlot* __restrict__ sl, int nsys, int& sys) {
+  const int b = (int)blockIdx.x;
+  int lo = 0, hi = nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sl[mid].cta0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchSlot s = sl[lo];
+  sys = s.entry;
+  const int l = b - s.cta0;
+  return Blk{l % s.gx, l / s.gx, s.gx};
+}
+// a batched launch: per-system argument table and ranges (device memory), the
+// number of systems and the CTA total
+template <class A>
+struct BatchLaunch {
+  const A* tab;
+  const BatchSlot* slot;
+  int nsys;
+  int ctas;
+};
+
 // wrapped neighbour coordinates of (x, y, z)
 struct Nbr {
   int xm, xp, ym, yp, zm, zp;
@@ -229,6 +271,19 @@ cudaError_t poisson_solve_f32(const PoissonPlan& p, const int* rho, const float*
                               cudaStream_t s);
 cudaError_t charge_density(const Grid& g, const Phys& ph, const void* rho, const void* qwall,
                            const void* qpart, double* q, cudaStream_t s);
+// S1 of the FP32 systems of a batch whose edges are all 32, 48 or 64
+// (poisson_batch_ok): pass 0 the x transform, 1 the y-z planes with the Green
+// multiply, 2 the inverse x transform.  A system's entry of the argument
+// table is poisson_batch_args_size() bytes written by poisson_batch_args;
+// poisson_batch_pass gives the kernel variant of a pass (systems of one
+// variant share a launch) and the system's CTAs in it.
+bool poisson_batch_ok(const PoissonPlan& p);
+size_t poisson_batch_args_size();
+void poisson_batch_args(void* out, const PoissonPlan& p, const int* rho, const float* qwall,
+                        const float* qpart, const Phys& ph, float* phi, float2* spectrum);
+void poisson_batch_pass(const PoissonPlan& p, int pass, const void* args, int& variant, int& ctas);
+cudaError_t launch_poisson_batch(int pass, int variant, const void* tab, const BatchSlot* slot, int nsys,
+                                 int ctas, cudaStream_t s);
 
 // S2 + S3
 struct LBArgs {
@@ -250,6 +305,23 @@ struct LBArgs {
   int* status;
   int nzb;         // FP32 S2: z segments per (x, y) tile column (lb32_segments)
 };
+// Constants of the FP32 kernels, rounded once on the host.
+struct Phys32 {
+  float rho0, lam_e, lam_o;
+  float qs[EK_MAX_SPECIES];  // density of one species unit
+  float cq[EK_MAX_SPECIES];  // D_k / (A_0 qs_k): flux in units per bracket value
+  float hz[EK_MAX_SPECIES];  // z_k / 2
+  float ec[19];              // E . c_i
+  float g[3];
+  float E[3];
+  float zq[EK_MAX_SPECIES];  // z_k qs_k: charge of one unit of species k
+};
+Phys32 make_phys32(const Phys& ph);
+// one system's entry of the batched FP32 S2 / S3 launches
+struct LBBatchEntry {
+  LBArgs a;
+  Phys32 c;
+};
 cudaError_t launch_lb_fused(const LBArgs& a, cudaStream_t s);
 cudaError_t launch_advection(const LBArgs& a, cudaStream_t s);
 // FP32-storage form
@@ -258,6 +330,13 @@ cudaError_t lb32_prepare();  // once per process, before the first launch_lb32
 int lb32_segments(const Grid& g, int K, bool pv);
 cudaError_t launch_lb32(const LBArgs& a, cudaStream_t s);
 cudaError_t launch_advection32(const LBArgs& a, cudaStream_t s);
+// the same S2 and S3 for the systems of a batch (all FP32 with the same K and
+// partial-volume choice), one launch each; the per-system grids (gx, gy) that
+// the ranges of L.slot must give
+void lb32_batch_grid(const LBArgs& a, int& gx, int& gy);
+void advect32_batch_grid(const LBArgs& a, int& gx, int& gy);
+cudaError_t launch_lb32_batch(const BatchLaunch<LBBatchEntry>& L, int K, bool pv, cudaStream_t s);
+cudaError_t launch_advection32_batch(const BatchLaunch<LBBatchEntry>& L, int K, cudaStream_t s);
 cudaError_t launch_fill32(const Grid& g, const Phys& ph, const int* owner, float* f, int* rho,
                           const int* units, cudaStream_t s);
 enum {
@@ -303,7 +382,8 @@ struct PartArgs {
   int nipart;                // number of lattice blocks
   unsigned long long* fkey;  // N: (surface distance, particle) of the nearest particle
   // nodes whose nearest particle the float distances cannot decide: the FP64
-  // decision is taken there by a second kernel (cleared by the key reset)
+  // decision is taken there by a second kernel (the count is cleared by the
+  // integration at the end of S4)
   int* tie_list;
   int* tie_count;
   int tie_cap;
@@ -336,6 +416,18 @@ cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s, int parts 
 // S5; parts: 1 = re-flag, Psi and charge (no species access), 2 = transitions
 // (species after S3), 3 = both
 cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s, int parts = 3);
+// The kernels of S4 and of S5's transitions step, each also as one launch
+// over the systems of a batch (FP32 form), in the order a step runs them:
+// assignment and its FP64 tie decision (beside S1/S2); after S2 the forces
+// with the integration, then the re-flag part of S5; after S3 the
+// transitions and the transfers they list.
+enum PartKernel {
+  PK_ASSIGN, PK_TIE, PK_FORCES, PK_SAVE_PREV, PK_CLEAR, PK_CLAIM, PK_PSI, PK_CHARGE, PK_TRANS,
+  PK_APPLY, PK_COUNT
+};
+// the grid (gx, gy) kernel k runs for one system; gx = 0: no launch (P = 0)
+void particle_batch_grid(int k, const PartArgs& a, int& gx, int& gy);
+cudaError_t launch_particle_batch(int k, const BatchLaunch<PartArgs>& L, cudaStream_t s);
 cudaError_t launch_fill(const Grid& g, const Phys& ph, const int* owner, double* f, double* rho,
                         const double* bulk_k, cudaStream_t s);
 

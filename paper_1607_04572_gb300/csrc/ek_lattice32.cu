@@ -35,17 +35,7 @@ __device__ __forceinline__ float cdotf(int i, float x, float y, float z) {
   return 0.0f;
 }
 
-// Constants of the FP32 kernels, rounded once on the host.
-struct Phys32 {
-  float rho0, lam_e, lam_o;
-  float qs[EK_MAX_SPECIES];  // density of one species unit
-  float cq[EK_MAX_SPECIES];  // D_k / (A_0 qs_k): flux in units per bracket value
-  float hz[EK_MAX_SPECIES];  // z_k / 2
-  float ec[19];              // E . c_i
-  float g[3];
-  float E[3];
-  float zq[EK_MAX_SPECIES];  // z_k qs_k: charge of one unit of species k
-};
+}  // namespace
 
 Phys32 make_phys32(const Phys& ph) {
   Phys32 p;
@@ -66,6 +56,8 @@ Phys32 make_phys32(const Phys& ph) {
   return p;
 }
 
+namespace {
+
 // The neighbourhood of a node as its three x coordinates, row offsets and
 // plane offsets (periodic, 32-bit: N < 2^31): a neighbour's index is one
 // three-operand add.
@@ -85,7 +77,7 @@ __device__ __forceinline__ int nbr32(int d, const Off3& o) {
 // block total of the per-thread sums: warps in float (32 threads, each over
 // its segment's nodes), the warp sums in FP64; the GPU's FP64 rate is a small
 // fraction of its FP32 rate, so the per-node accumulation stays in float
-__device__ __forceinline__ void block_sum3(float (&v)[3], double* ipart) {
+__device__ __forceinline__ void block_sum3(float (&v)[3], double* ipart, long long blk) {
   __shared__ double red[TILE_X * TILE_Y / 32][3];
   const int t = threadIdx.x + TILE_X * threadIdx.y;
   const int lane = t & 31, warp = t >> 5;
@@ -97,7 +89,6 @@ __device__ __forceinline__ void block_sum3(float (&v)[3], double* ipart) {
   }
   __syncthreads();
   if (t == 0) {
-    const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
       double s = 0.0;
@@ -367,14 +358,17 @@ __device__ __forceinline__ void lb32_node(const LBRing<K>& t, const LBArgs& a, c
   }
 }
 
+// One block of the S2 grid: tile (bx, by), z segment bz; blk is the block's
+// row of the per-block sums.
 template <int K, bool PV>
-__global__ void __launch_bounds__(256, 2) k_lb32_tiled(LBArgs a, Phys32 c) {
+__device__ __forceinline__ void lb32_block(const LBArgs& a, const Phys32& c, int bx, int by, int bz,
+                                           long long blk) {
   extern __shared__ __align__(16) unsigned char lb_smem[];
   LBRing<K>& t = *reinterpret_cast<LBRing<K>*>(lb_smem);
   const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y;
-  const int z0 = (int)((long long)blockIdx.z * nz / a.nzb);
-  const int zend = (int)((long long)(blockIdx.z + 1) * nz / a.nzb);
+  const int x0 = bx * TILE_X, y0 = by * TILE_Y;
+  const int z0 = (int)((long long)bz * nz / a.nzb);
+  const int zend = (int)((long long)(bz + 1) * nz / a.nzb);
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   const int tid = threadIdx.x + TILE_X * threadIdx.y;
   const bool in_xy = x < nx && y < ny;
@@ -425,7 +419,26 @@ __global__ void __launch_bounds__(256, 2) k_lb32_tiled(LBArgs a, Phys32 c) {
     __syncthreads();  // the next copies overwrite the slots of plane z - 1 and populations z
   }
   cp_async_wait<0>();
-  block_sum3(iv, a.ipart);
+  block_sum3(iv, a.ipart, blk);
+}
+
+template <int K, bool PV>
+__global__ void __launch_bounds__(256, 2) k_lb32_tiled(LBArgs a, Phys32 c) {
+  lb32_block<K, PV>(a, c, blockIdx.x, blockIdx.y, blockIdx.z,
+                    blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z));
+}
+
+// S2 of a batch's systems in one launch: system s runs its xt x (yt nzb) grid
+// (tiles x fastest, then y, then the z segment), the block sums in the same
+// rows as its own launch would
+template <int K, bool PV>
+__global__ void __launch_bounds__(256, 2) k_lb32_batch(const LBBatchEntry* __restrict__ tab,
+                                                       const BatchSlot* __restrict__ slot, int nsys) {
+  int sys;
+  const Blk b = batch_blk(slot, nsys, sys);
+  const LBBatchEntry& e = tab[sys];
+  const int yt = (e.a.g.ny + TILE_Y - 1) / TILE_Y;
+  lb32_block<K, PV>(e.a, e.c, b.x, b.y % yt, b.y / yt, b.x + (long long)b.nx * b.y);
 }
 
 // share of the cell displaced by velocity (vx, vy, vz) that lands at offset
@@ -448,11 +461,11 @@ __device__ __forceinline__ int sgnf(float v) { return v > 0.0f ? 1 : (v < 0.0f ?
 // constant masks.  Each share is computed with the same operations as in its
 // source, and integer sums do not depend on their order.
 template <int K>
-__global__ void __launch_bounds__(256) k_advect32(LBArgs a, Phys32 c) {
+__device__ __forceinline__ void advect32_block(const LBArgs& a, int bx, int by, int bz) {
   const int nx = a.g.nx, ny = a.g.ny;
-  const int x = blockIdx.x * TILE_X + threadIdx.x;
-  const int y = blockIdx.y * TILE_Y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int x = bx * TILE_X + threadIdx.x;
+  const int y = by * TILE_Y + threadIdx.y;
+  const int z = bz;
   if (x >= nx || y >= ny) return;
   const unsigned char* __restrict__ vs = a.vsig;
   const int n = x + nx * (y + ny * z);
@@ -519,6 +532,23 @@ __global__ void __launch_bounds__(256) k_advect32(LBArgs a, Phys32 c) {
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) nout[k][n] = acc[k];
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_advect32(LBArgs a, Phys32 c) {
+  (void)c;
+  advect32_block<K>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// S3 of a batch's systems in one launch (system s: its xt x (yt nz) grid)
+template <int K>
+__global__ void __launch_bounds__(256) k_advect32_batch(const LBBatchEntry* __restrict__ tab,
+                                                        const BatchSlot* __restrict__ slot, int nsys) {
+  int sys;
+  const Blk b = batch_blk(slot, nsys, sys);
+  const LBArgs& a = tab[sys].a;
+  const int yt = (a.g.ny + TILE_Y - 1) / TILE_Y;
+  advect32_block<K>(a, b.x, b.y % yt, b.y / yt);
 }
 
 __global__ void k_fill32(Grid g, const int* owner, float* f, int* rho, int K, float rho0, int n0,
@@ -603,6 +633,12 @@ cudaError_t lb32_prepare() {
                              (int)lb32_smem<KK>());                                          \
   if (e == cudaSuccess)                                                                      \
     e = cudaFuncSetAttribute(k_lb32_tiled<KK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)lb32_smem<KK>());                                          \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_lb32_batch<KK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)lb32_smem<KK>());                                          \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_lb32_batch<KK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)lb32_smem<KK>());
   EK_ATTR(0)
   EK_ATTR(1)
@@ -654,6 +690,51 @@ cudaError_t launch_advection32(const LBArgs& a, cudaStream_t s) {
     case 2: k_advect32<2><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
     case 3: k_advect32<3><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
     case 4: k_advect32<4><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+void lb32_batch_grid(const LBArgs& a, int& gx, int& gy) {
+  const dim3 g = lattice_grid32(a.g, a.nzb);
+  gx = (int)g.x;
+  gy = (int)(g.y * g.z);
+}
+
+void advect32_batch_grid(const LBArgs& a, int& gx, int& gy) {
+  const dim3 g = lattice_grid(a.g);
+  gx = (int)g.x;
+  gy = (int)(g.y * g.z);
+}
+
+cudaError_t launch_lb32_batch(const BatchLaunch<LBBatchEntry>& L, int K, bool pv, cudaStream_t s) {
+  if (L.ctas == 0) return cudaSuccess;
+  switch (K) {
+#define EK_CASE(KK)                                                                            \
+  case KK:                                                                                     \
+    if (pv) k_lb32_batch<KK, true><<<L.ctas, lattice_block(), lb32_smem<KK>(), s>>>(L.tab, L.slot, L.nsys); \
+    else k_lb32_batch<KK, false><<<L.ctas, lattice_block(), lb32_smem<KK>(), s>>>(L.tab, L.slot, L.nsys);   \
+    break;
+    EK_CASE(0)
+    EK_CASE(1)
+    EK_CASE(2)
+    EK_CASE(3)
+    EK_CASE(4)
+#undef EK_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advection32_batch(const BatchLaunch<LBBatchEntry>& L, int K, cudaStream_t s) {
+  if (L.ctas == 0) return cudaSuccess;
+  switch (K) {
+    case 0: return cudaSuccess;
+    case 1: k_advect32_batch<1><<<L.ctas, lattice_block(), 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case 2: k_advect32_batch<2><<<L.ctas, lattice_block(), 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case 3: k_advect32_batch<3><<<L.ctas, lattice_block(), 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case 4: k_advect32_batch<4><<<L.ctas, lattice_block(), 0, s>>>(L.tab, L.slot, L.nsys); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -358,10 +358,10 @@ __device__ __forceinline__ float key_distance(unsigned long long key) {
 // then finds the other's (or a smaller, still within the window) in the value
 // atomicMin returns and lists the node; k_tie_resolve decides the listed nodes
 // in FP64.
-__global__ void k_force_assign(PartArgs a) {
-  const int p = blockIdx.x;
+__device__ __forceinline__ void force_assign_body(const PartArgs& a, const Blk bk) {
+  const int p = bk.x;
   const DevParticle& P = a.parts[p];
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  const int c = bk.y * blockDim.x + threadIdx.x;
   if (c >= box_cells(P.elo, P.ehi)) return;
   int X, Y, Z;
   box_coord(c, P.elo, P.ehi, X, Y, Z);  // a repeated node gets the same key
@@ -393,14 +393,16 @@ __global__ void k_force_assign(PartArgs a) {
   }
 }
 
+__global__ void k_force_assign(PartArgs a) { force_assign_body(a, grid_blk()); }
+
 // FP64 decision on the listed nodes: one warp per entry, its lanes over the
 // particles whose widened box holds the node; the smallest (distance, index)
 // wins and its index replaces the key's.  A node listed twice gets the same
 // answer twice.
-__global__ void k_tie_resolve(PartArgs a) {
+__device__ __forceinline__ void tie_resolve_body(const PartArgs& a, const Blk bk) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int warp = (bk.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (bk.nx * blockDim.x) >> 5;
   const int count = min(*a.tie_count, a.tie_cap);
   const Grid g = a.g;
   for (int e = warp; e < count; e += nwarps) {
@@ -433,6 +435,8 @@ __global__ void k_tie_resolve(PartArgs a) {
     if (lane == 0 && who != 0x7FFFFFFF) a.fkey[n] = (a.fkey[n] & ~0xFFFFFull) | (unsigned long long)who;
   }
 }
+
+__global__ void k_tie_resolve(PartArgs a) { tie_resolve_body(a, grid_blk()); }
 
 // Sum of FORCE_T values per component, fixed order: the block's values are
 // transposed through shared memory and each of 4 threads per component adds a
@@ -501,14 +505,14 @@ __device__ void block_sum_f(const float (&v)[NV], const bool (&group_on)[NV / 6]
 }
 
 template <class FM>
-__global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 5 : 4) k_particle_forces(PartArgs a) {
-  const int p = blockIdx.x;
+__device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Blk bk) {
+  const int p = bk.x;
   const DevParticle& P = a.parts[p];
   const Grid g = a.g;
   const long long N = g.N;
   const int ncell = box_cells(P.elo, P.ehi);
   const int nb = (ncell + a.fcells - 1) / a.fcells;
-  if ((int)blockIdx.y >= nb) return;  // whole CTA beyond this particle's widened box
+  if ((int)bk.y >= nb) return;  // whole CTA beyond this particle's widened box
   const bool pv = a.ph.pv != 0;
   double qnorm = 0.0;
   if (pv) {
@@ -558,7 +562,7 @@ __global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 5 : 4) k_particle_forces(P
   bool nfirst = false;
   int nown = FLUID;
   unsigned long long nkey = ~0ULL;
-  int cnext = (int)blockIdx.y * FORCE_T + threadIdx.x;
+  int cnext = (int)bk.y * FORCE_T + threadIdx.x;
   bool nvalid = cnext < ncell;
   if (nvalid) {
     nfirst = locate(cnext, nX, nY, nZ, nn, nw3, nmx, nmy, nmz);
@@ -574,7 +578,7 @@ __global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 5 : 4) k_particle_forces(P
     const bool first = nfirst;
     const int own = nown;
     const unsigned long long key = nkey;
-    cnext = ((int)blockIdx.y + (k + 1) * nb) * FORCE_T + threadIdx.x;
+    cnext = ((int)bk.y + (k + 1) * nb) * FORCE_T + threadIdx.x;
     nvalid = k + 1 < rows && cnext < ncell;
     if (nvalid) {
       nfirst = locate(cnext, nX, nY, nZ, nn, nw3, nmx, nmy, nmz);
@@ -747,7 +751,7 @@ __global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 5 : 4) k_particle_forces(P
   // per-particle rows are summed
   if (p == 0) {
     const int per = (a.nipart + nb - 1) / nb;
-    const int r0 = (int)blockIdx.y * per, r1 = min(r0 + per, a.nipart);
+    const int r0 = (int)bk.y * per, r1 = min(r0 + per, a.nipart);
     double lat = 0.0;  // component threadIdx.x % 3 (the stride 126 keeps it)
     for (int q = threadIdx.x; q < 3 * (r1 - r0) && threadIdx.x < 126; q += 126) {
       lat += __ldcg(a.ipart + 3LL * r0 + q);
@@ -763,7 +767,7 @@ __global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 5 : 4) k_particle_forces(P
   on[1] = __syncthreads_or(touched[1]);
   on[2] = __syncthreads_or(touched[2]);
   on[3] = __syncthreads_or(touched[3]);
-  double* out = a.fpart + ((long long)p * a.fchunks + blockIdx.y) * FPART;
+  double* out = a.fpart + ((long long)p * a.fchunks + bk.y) * FPART;
   if (FM::fp32) {
 #pragma unroll
     for (int j = 18; j < 21; ++j) facc[j] = (float)acc[j];  // the lattice slice
@@ -795,6 +799,11 @@ __global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 5 : 4) k_particle_forces(P
     *a.ticket = 0;
     *a.tie_count = 0;  // the next step's assignment lists its ties afresh
   }
+}
+
+template <class FM>
+__global__ void __launch_bounds__(FORCE_T, FM::fp32 ? 5 : 4) k_particle_forces(PartArgs a) {
+  particle_forces_body<FM>(a, grid_blk());
 }
 
 // New box of a particle at `pos`: the cells within R (+1 below, +2 above),
@@ -965,17 +974,17 @@ __global__ void k_box_update(PartArgs a) {
   P.nb = 0;
 }
 
-__global__ void k_save_prev(PartArgs a) {
-  DevParticle& P = a.parts[blockIdx.x];
-  if (blockIdx.y == 0 && threadIdx.x == 0) {  // k_claim and k_psi_surface sum these afresh
+__device__ __forceinline__ void save_prev_body(const PartArgs& a, const Blk bk) {
+  DevParticle& P = a.parts[bk.x];
+  if (bk.y == 0 && threadIdx.x == 0) {  // k_claim and k_psi_surface sum these afresh
     for (int j = 0; j < 8; ++j) P.psiunits[j] = 0;
     P.nb = 0;
     // the transfer list of the last step's transitions has been applied;
     // this step's transitions append to an empty one (a kernel of the chain
     // instead of a memset node after the transfers)
-    if (blockIdx.x == 0) *a.xfer_count = 0;
+    if (bk.x == 0) *a.xfer_count = 0;
   }
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  const int c = bk.y * blockDim.x + threadIdx.x;
   if (c >= box_cells(P.ulo, P.uhi)) return;
   int X, Y, Z;
   box_coord(c, P.ulo, P.uhi, X, Y, Z);
@@ -983,12 +992,14 @@ __global__ void k_save_prev(PartArgs a) {
   a.owner_prev[n] = a.owner[n];
 }
 
+__global__ void k_save_prev(PartArgs a) { save_prev_body(a, grid_blk()); }
+
 template <class FM>
-__global__ void k_clear(PartArgs a) {
-  const DevParticle& P = a.parts[blockIdx.x];
+__device__ __forceinline__ void clear_body(const PartArgs& a, const Blk bk) {
+  const DevParticle& P = a.parts[bk.x];
   // the surface-cell list of the last step has been read; k_claim refills it
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *a.surf_count = 0;
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (bk.x == 0 && bk.y == 0 && threadIdx.x == 0) *a.surf_count = 0;
+  const int c = bk.y * blockDim.x + threadIdx.x;
   if (c >= box_cells(P.ulo, P.uhi)) return;
   int X, Y, Z;
   box_coord(c, P.ulo, P.uhi, X, Y, Z);
@@ -997,6 +1008,9 @@ __global__ void k_clear(PartArgs a) {
   real_set<FM>(a.psi, n, 0.0);
   real_set<FM>(a.qpart, n, 0.0);
 }
+
+template <class FM>
+__global__ void k_clear(PartArgs a) { clear_body<FM>(a, grid_blk()); }
 
 template <class FM>
 __global__ void k_reset_all(PartArgs a) {
@@ -1011,10 +1025,10 @@ __global__ void k_reset_all(PartArgs a) {
 // every cell of the current box; cells cut by the surface are queued for
 // k_psi_surface
 template <class FM>
-__global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
-  const int p = blockIdx.x;
+__device__ __forceinline__ void claim_body(const PartArgs& a, const Blk bk) {
+  const int p = bk.x;
   DevParticle& P = a.parts[p];
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  const int c = bk.y * blockDim.x + threadIdx.x;
   const int ncell = box_cells(P.lo, P.hi);
   double ps = 0.0;
   int inside = 0;
@@ -1048,6 +1062,9 @@ __global__ void __launch_bounds__(PT) k_claim(PartArgs a) {
     if (nbd) atomicAdd(&P.nb, nbd);
   }
 }
+
+template <class FM>
+__global__ void __launch_bounds__(PT) k_claim(PartArgs a) { claim_body<FM>(a, grid_blk()); }
 
 // Psi_p of a surface cell (level 0 undecided) from the finest level alone.
 // In FP64 the octree's decisions are inherited: a cube decided inside at some
@@ -1125,10 +1142,10 @@ __device__ __forceinline__ bool psi_test(const PsiCell& c, float gu, float gvw2,
 }
 
 template <class FM>
-__global__ void __launch_bounds__(PSI_CTA) k_psi_surface(PartArgs a) {
+__device__ __forceinline__ void psi_surface_body(const PartArgs& a, const Blk bk) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * PSI_CTA + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * PSI_CTA) >> 5;
+  const int warp = (bk.x * PSI_CTA + threadIdx.x) >> 5;
+  const int nwarps = (bk.nx * PSI_CTA) >> 5;
   const int count = min(*a.surf_count, a.surf_cap);
   for (int e = warp; e < count; e += nwarps) {
     const int2 pc = a.surf[e];
@@ -1253,12 +1270,17 @@ __global__ void __launch_bounds__(PSI_CTA) k_psi_surface(PartArgs a) {
   }
 }
 
+template <class FM>
+__global__ void __launch_bounds__(PSI_CTA) k_psi_surface(PartArgs a) {
+  psi_surface_body<FM>(a, grid_blk());
+}
+
 // Psi-smeared particle charge (Eq. 21), or spread over the boundary nodes
 template <class FM>
-__global__ void k_charge_scatter(PartArgs a) {
-  const int p = blockIdx.x;
+__device__ __forceinline__ void charge_scatter_body(const PartArgs& a, const Blk bk) {
+  const int p = bk.x;
   const DevParticle& P = a.parts[p];
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  const int c = bk.y * blockDim.x + threadIdx.x;
   if (c >= box_cells(P.lo, P.hi)) return;
   int X, Y, Z;
   box_coord(c, P.lo, P.hi, X, Y, Z);
@@ -1281,6 +1303,9 @@ __global__ void k_charge_scatter(PartArgs a) {
   real_add<FM>(a.qpart, n, q);
 }
 
+template <class FM>
+__global__ void k_charge_scatter(PartArgs a) { charge_scatter_body<FM>(a, grid_blk()); }
+
 __device__ __forceinline__ bool steady_fluid(const PartArgs& a, long long m) {
   return a.owner_prev[m] == FLUID && a.owner[m] == FLUID;
 }
@@ -1292,12 +1317,12 @@ __device__ __forceinline__ bool steady_fluid(const PartArgs& a, long long m) {
 // unit each to the first receivers in direction order), so the totals stay
 // exact.
 template <class FM>
-__global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
+__device__ __forceinline__ void transitions_body(const PartArgs& a, const Blk bk) {
   using pop_t = typename FM::pop_t;
   using spc_t = typename FM::spc_t;
-  const int p = blockIdx.x;
+  const int p = bk.x;
   DevParticle& P = a.parts[p];
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  const int c = bk.y * blockDim.x + threadIdx.x;
   if (c >= box_cells(P.ulo, P.uhi)) return;
   int X, Y, Z;
   box_coord(c, P.ulo, P.uhi, X, Y, Z);
@@ -1429,11 +1454,14 @@ __global__ void __launch_bounds__(PT) k_transitions(PartArgs a) {
 }
 
 template <class FM>
-__global__ void k_apply_transfers(PartArgs a) {
+__global__ void __launch_bounds__(PT) k_transitions(PartArgs a) { transitions_body<FM>(a, grid_blk()); }
+
+template <class FM>
+__device__ __forceinline__ void apply_transfers_body(const PartArgs& a, const Blk bk) {
   using spc_t = typename FM::spc_t;
   spc_t* rho = (spc_t*)a.rho;
   const int count = min(*a.xfer_count, a.xfer_cap);
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < count; r += gridDim.x * blockDim.x) {
+  for (int r = bk.x * blockDim.x + threadIdx.x; r < count; r += bk.nx * blockDim.x) {
     const Transfer t = a.xfer[r];
     for (int k = 0; k < a.ph.K; ++k) {
       if (FM::fp32) atomicAdd((int*)rho + k * a.g.N + t.node, (int)t.amount[k]);
@@ -1441,6 +1469,9 @@ __global__ void k_apply_transfers(PartArgs a) {
     }
   }
 }
+
+template <class FM>
+__global__ void k_apply_transfers(PartArgs a) { apply_transfers_body<FM>(a, grid_blk()); }
 
 template <class FM>
 cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s, int parts) {
@@ -1489,7 +1520,72 @@ cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s, int pa
   return cudaGetLastError();
 }
 
+// The same kernels as one launch over the systems of a batch (FP32 form):
+// each CTA finds its system's arguments and its block in that system's grid.
+#define EK_PART_BATCH(NAME, BODY, BOUNDS)                                                    \
+  __global__ void BOUNDS NAME(const PartArgs* __restrict__ tab, const BatchSlot* __restrict__ sl, \
+                              int nsys) {                                                    \
+    int sys;                                                                                 \
+    const Blk bk = batch_blk(sl, nsys, sys);                                                 \
+    BODY(tab[sys], bk);                                                                      \
+  }
+EK_PART_BATCH(k_force_assign_batch, force_assign_body, __launch_bounds__(PT))
+EK_PART_BATCH(k_tie_resolve_batch, tie_resolve_body, __launch_bounds__(256))
+EK_PART_BATCH(k_particle_forces_batch, particle_forces_body<FormF32>, __launch_bounds__(FORCE_T, 4))
+EK_PART_BATCH(k_save_prev_batch, save_prev_body, __launch_bounds__(PT))
+EK_PART_BATCH(k_clear_batch, clear_body<FormF32>, __launch_bounds__(PT))
+EK_PART_BATCH(k_claim_batch, claim_body<FormF32>, __launch_bounds__(PT))
+EK_PART_BATCH(k_psi_surface_batch, psi_surface_body<FormF32>, __launch_bounds__(PSI_CTA))
+EK_PART_BATCH(k_charge_scatter_batch, charge_scatter_body<FormF32>, __launch_bounds__(PT))
+EK_PART_BATCH(k_transitions_batch, transitions_body<FormF32>, __launch_bounds__(PT))
+EK_PART_BATCH(k_apply_transfers_batch, apply_transfers_body<FormF32>, __launch_bounds__(256))
+#undef EK_PART_BATCH
+
 }  // namespace
+
+void particle_batch_grid(int k, const PartArgs& a, int& gx, int& gy) {
+  gx = a.P;
+  gy = 1;
+  if (a.P == 0) return;
+  const int edge = (int)round(cbrt((double)a.boxmax)) + 1;
+  const int uchunks = (edge * edge * edge + PT - 1) / PT;
+  const int bchunks = (a.boxmax + PT - 1) / PT;
+  switch (k) {
+    case PK_ASSIGN: gy = (a.emax + PT - 1) / PT; break;
+    case PK_FORCES: gy = a.fchunks; break;
+    case PK_SAVE_PREV:
+    case PK_CLEAR:
+    case PK_TRANS: gy = uchunks; break;
+    case PK_CLAIM:
+    case PK_CHARGE: gy = bchunks; break;
+    // grid-stride kernels: their lists are short for a few particles (a CTA
+    // per system), Psi's surface cells some hundreds per particle (eight
+    // warps per CTA, eight CTAs per particle)
+    case PK_TIE:
+    case PK_APPLY: gx = 1; break;
+    case PK_PSI: gx = std::min(8 * 152, 8 * a.P); break;
+    default: gx = 0;
+  }
+}
+
+cudaError_t launch_particle_batch(int k, const BatchLaunch<PartArgs>& L, cudaStream_t s) {
+  if (L.ctas == 0) return cudaSuccess;
+  const unsigned n = (unsigned)L.ctas;
+  switch (k) {
+    case PK_ASSIGN: k_force_assign_batch<<<n, PT, 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case PK_TIE: k_tie_resolve_batch<<<n, 256, 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case PK_FORCES: k_particle_forces_batch<<<n, FORCE_T, 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case PK_SAVE_PREV: k_save_prev_batch<<<n, PT, 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case PK_CLEAR: k_clear_batch<<<n, PT, 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case PK_CLAIM: k_claim_batch<<<n, PT, 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case PK_PSI: k_psi_surface_batch<<<n, PSI_CTA, 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case PK_CHARGE: k_charge_scatter_batch<<<n, PT, 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case PK_TRANS: k_transitions_batch<<<n, PT, 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case PK_APPLY: k_apply_transfers_batch<<<n, 256, 0, s>>>(L.tab, L.slot, L.nsys); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s, int parts) {
   if (a.P == 0) return cudaSuccess;

@@ -20,6 +20,7 @@
 // memory buffers, so no bit reversal pass is needed.
 #include <math.h>
 #include <cstdint>
+#include <cstring>
 
 #include <map>
 #include <mutex>
@@ -492,7 +493,7 @@ __device__ __forceinline__ void load_twiddles(float2* tw, const AxisPlan& P) {
 // KMAJOR: the half spectrum is stored kx-major, S[kx][z][y], so that each
 // (y, z) plane is contiguous for k_fast_yzplane2; else S[z][y][kx].
 template <int NX, bool KMAJOR, bool VEC>
-__global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
+__device__ __forceinline__ void fast_x_fwd_body(const PassArgs<float>& a, int bx) {
   constexpr int PPC = FAST_XELEMS / NX > 0 ? FAST_XELEMS / NX : 1;  // row pairs per CTA
   constexpr int LS = fpad(NX);
   __shared__ __align__(16) float2 buf[2][PPC * LS];
@@ -500,7 +501,7 @@ __global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
   load_twiddles<NX>(tw, a.ax);
   const int nrows = a.ny * a.nz;
   const long long N = (long long)NX * a.ny * a.nz;
-  const int p0 = blockIdx.x * PPC;
+  const int p0 = bx * PPC;
   // every load of the thread is issued before the first shared-memory store:
   // the stores go through no pointer the loads could alias, so the latencies
   // overlap instead of adding up
@@ -570,6 +571,11 @@ __global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
       if (r1 < nrows) a.S[(long long)r1 * NXH + k] = B;
     }
   }
+}
+
+template <int NX, bool KMAJOR, bool VEC>
+__global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd(PassArgs<float> a) {
+  fast_x_fwd_body<NX, KMAJOR, VEC>(a, blockIdx.x);
 }
 
 // Y (AXIS 1, forward or inverse) or Z (AXIS 2: forward, Green multiply,
@@ -731,7 +737,7 @@ void launch_line4(PassArgs<float>& a, cudaStream_t s) {
 // and, conjugated, k = NX - kk; the thread's loads are all issued before its
 // first shared-memory store.
 template <int NX, bool KMAJOR>
-__global__ void __launch_bounds__(FAST_IT) k_fast_x_inv(PassArgs<float> a) {
+__device__ __forceinline__ void fast_x_inv_body(const PassArgs<float>& a, int bx) {
   constexpr int PPC = FAST_IELEMS / NX > 0 ? FAST_IELEMS / NX : 1;
   constexpr int LS = fpad(NX);
   constexpr int NXH = NX / 2 + 1;
@@ -740,7 +746,7 @@ __global__ void __launch_bounds__(FAST_IT) k_fast_x_inv(PassArgs<float> a) {
   __shared__ float2 tw[NX];
   load_twiddles<NX>(tw, a.ax);
   const int nrows = a.ny * a.nz;
-  const int p0 = blockIdx.x * PPC;
+  const int p0 = bx * PPC;
   float2 A[PER], B[PER];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
@@ -780,6 +786,11 @@ __global__ void __launch_bounds__(FAST_IT) k_fast_x_inv(PassArgs<float> a) {
     if (r0 < nrows) a.phi[(long long)r0 * NX + x] = v.x;
     if (r1 < nrows) a.phi[(long long)r1 * NX + x] = v.y;
   }
+}
+
+template <int NX, bool KMAJOR>
+__global__ void __launch_bounds__(FAST_IT) k_fast_x_inv(PassArgs<float> a) {
+  fast_x_inv_body<NX, KMAJOR>(a, blockIdx.x);
 }
 
 template <int NX>
@@ -967,8 +978,7 @@ __device__ __forceinline__ void plane_fft(float2* pl, const float2* tw) {
 constexpr int PLANE2_T = 512;
 
 template <int NY, int NZ>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PLANE2_T, 1)
-    k_fast_yzplane2(PassArgs<float> a) {
+__device__ __forceinline__ void fast_yzplane2_body(const PassArgs<float>& a, int bx) {
   constexpr int HZ = NZ / 2, HY = NY / 2;
   constexpr int LSA = fpad(NY), LSB = fpad(HY);
   extern __shared__ __align__(16) unsigned char plane_smem[];
@@ -979,7 +989,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PLANE2_T, 1)
   cg::cluster_group cl = cg::this_cluster();
   const int r = (int)cl.block_rank();
   cl.barrier_arrive();  // the peer has started before its shared memory is written
-  const int kx = blockIdx.x >> 1;
+  const int kx = bx >> 1;
   for (int k = threadIdx.x; k < NY; k += PLANE2_T) twy[k] = a.ay.tw32[k];
   for (int k = threadIdx.x; k < NZ; k += PLANE2_T) twz[k] = a.az.tw32[k];
   const float2* src = a.S + (long long)kx * NY * NZ + (long long)r * HZ * NY;
@@ -1016,6 +1026,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PLANE2_T, 1)
   cl.sync();
   plane_fft<NY, HZ, true, true, LSA, PLANE2_T>(pa, twy);
   plane_store<HZ * NY, NY, LSA, PLANE2_T>(pa, a.S + (long long)kx * NY * NZ + (long long)r * HZ * NY);
+}
+
+template <int NY, int NZ>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PLANE2_T, 1)
+    k_fast_yzplane2(PassArgs<float> a) {
+  fast_yzplane2_body<NY, NZ>(a, blockIdx.x);
 }
 
 template <int NY, int NZ>
@@ -1115,6 +1131,70 @@ cudaError_t axis_create(AxisPlan& P, int n) {
   return e;
 }
 
+
+// ---------------------------------------------------------------------------
+// S1 of the FP32 systems of a batch.  A system whose edges are all 32, 48 or
+// 64 runs its three passes (x forward, the y-z planes, x inverse) in launches
+// shared with the other systems of the same kernel variant; the bodies are
+// those of the single-system kernels, so the results are the same.
+// ---------------------------------------------------------------------------
+template <int NX, bool VEC>
+__global__ void __launch_bounds__(FAST_XT) k_fast_x_fwd_batch(const PassArgs<float>* __restrict__ tab,
+                                                              const BatchSlot* __restrict__ sl, int nsys) {
+  int sys;
+  const Blk bk = batch_blk(sl, nsys, sys);
+  fast_x_fwd_body<NX, true, VEC>(tab[sys], bk.x);
+}
+
+template <int NX>
+__global__ void __launch_bounds__(FAST_IT) k_fast_x_inv_batch(const PassArgs<float>* __restrict__ tab,
+                                                              const BatchSlot* __restrict__ sl, int nsys) {
+  int sys;
+  const Blk bk = batch_blk(sl, nsys, sys);
+  fast_x_inv_body<NX, true>(tab[sys], bk.x);
+}
+
+// every system's range is 2 nxh CTAs and starts at an even CTA, so a cluster
+// (two consecutive CTAs) lies in one system and its rank is the block's parity
+template <int NY, int NZ>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PLANE2_T, 1)
+    k_fast_yzplane2_batch(const PassArgs<float>* __restrict__ tab, const BatchSlot* __restrict__ sl,
+                          int nsys) {
+  int sys;
+  const Blk bk = batch_blk(sl, nsys, sys);
+  fast_yzplane2_body<NY, NZ>(tab[sys], bk.x);
+}
+
+inline bool batch_edge(int n) { return n == 32 || n == 48 || n == 64; }
+
+template <int NX>
+int fast_x_ctas(int ny, int nz, bool inverse) {
+  const int npairs = (ny * nz + 1) / 2;
+  constexpr int pf = FAST_XELEMS / NX > 0 ? FAST_XELEMS / NX : 1;
+  constexpr int pi = FAST_IELEMS / NX > 0 ? FAST_IELEMS / NX : 1;
+  const int ppc = inverse ? pi : pf;
+  return (npairs + ppc - 1) / ppc;
+}
+
+template <int NY, int NZ>
+cudaError_t plane_batch_launch(const PassArgs<float>* tab, const BatchSlot* sl, int nsys, int ctas,
+                               cudaStream_t s) {
+  k_fast_yzplane2_batch<NY, NZ><<<(unsigned)ctas, PLANE2_T, plane2_smem_bytes<NY, NZ>(), s>>>(tab, sl, nsys);
+  return cudaGetLastError();
+}
+
+template <int NY, int NZ>
+cudaError_t plane_batch_attr_nn() {
+  return cudaFuncSetAttribute(k_fast_yzplane2_batch<NY, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)plane2_smem_bytes<NY, NZ>());
+}
+template <int NY>
+cudaError_t plane_batch_attr_n() {
+  cudaError_t e = plane_batch_attr_nn<NY, 32>();
+  if (e == cudaSuccess) e = plane_batch_attr_nn<NY, 48>();
+  if (e == cudaSuccess) e = plane_batch_attr_nn<NY, 64>();
+  return e;
+}
 }  // namespace
 
 bool poisson_factor(int n, AxisPlan& P) { return factor(n, P); }
@@ -1132,6 +1212,9 @@ cudaError_t poisson_plan_create(PoissonPlan& p, int nx, int ny, int nz, std::str
     if (e == cudaSuccess) e = plane_attr_n<48>();
     if (e == cudaSuccess) e = plane_attr_n<64>();
     if (e == cudaSuccess) e = plane_attr_n<128>();
+    if (e == cudaSuccess) e = plane_batch_attr_n<32>();
+    if (e == cudaSuccess) e = plane_batch_attr_n<48>();
+    if (e == cudaSuccess) e = plane_batch_attr_n<64>();
     if (e != cudaSuccess) {
       err = "shared-memory size of the plane FFT kernels could not be set";
       return e;
@@ -1261,6 +1344,90 @@ cudaError_t poisson_solve_f32(const PoissonPlan& p, const int* rho, const float*
   a.S = spectrum;
   a.phi = phi;
   return run_passes<float>(p, a, ph.bjerrum, s);
+}
+
+bool poisson_batch_ok(const PoissonPlan& p) {
+  return batch_edge(p.nx) && batch_edge(p.ny) && batch_edge(p.nz);
+}
+
+size_t poisson_batch_args_size() { return sizeof(PassArgs<float>); }
+
+void poisson_batch_args(void* out, const PoissonPlan& p, const int* rho, const float* qwall,
+                        const float* qpart, const Phys& ph, float* phi, float2* spectrum) {
+  PassArgs<float> a;
+  a.nx = p.nx;
+  a.ny = p.ny;
+  a.nz = p.nz;
+  a.nxh = p.nx / 2 + 1;
+  a.ax = p.ax;
+  a.ay = p.ay;
+  a.az = p.az;
+  a.q = nullptr;
+  a.rho = rho;
+  a.int_species = true;
+  a.qwall = qwall;
+  a.qpart = qpart;
+  a.K = ph.K;
+  for (int k = 0; k < EK_MAX_SPECIES; ++k) a.z[k] = (float)(ph.z[k] * ph.qscale[k]);
+  a.S = spectrum;
+  a.phi = phi;
+  const double N = (double)p.nx * p.ny * p.nz;
+  a.green_scale = (float)(4.0 * M_PI * ph.bjerrum / N);
+  memcpy(out, &a, sizeof(a));
+}
+
+void poisson_batch_pass(const PoissonPlan& p, int pass, const void* args, int& variant, int& ctas) {
+  const PassArgs<float>& a = *(const PassArgs<float>*)args;
+  variant = -1;
+  ctas = 0;
+  if (!poisson_batch_ok(p)) return;
+  if (pass == 1) {
+    variant = p.ny * 256 + p.nz;
+    ctas = 2 * (p.nx / 2 + 1);
+    return;
+  }
+  const bool inverse = pass == 2;
+  ctas = p.nx == 32 ? fast_x_ctas<32>(p.ny, p.nz, inverse)
+                    : (p.nx == 48 ? fast_x_ctas<48>(p.ny, p.nz, inverse) : fast_x_ctas<64>(p.ny, p.nz, inverse));
+  const auto al = [](const void* q) { return ((uintptr_t)q & 15) == 0; };
+  const bool vec = al(a.q) && al(a.rho) && al(a.qwall) && al(a.qpart);
+  variant = inverse ? p.nx : 2 * p.nx + (vec ? 1 : 0);
+}
+
+cudaError_t launch_poisson_batch(int pass, int variant, const void* tab, const BatchSlot* slot, int nsys,
+                                 int ctas, cudaStream_t s) {
+  if (ctas == 0) return cudaSuccess;
+  const PassArgs<float>* t = (const PassArgs<float>*)tab;
+  const unsigned n = (unsigned)ctas;
+  if (pass == 0) {
+    switch (variant) {
+      case 64: k_fast_x_fwd_batch<32, false><<<n, FAST_XT, 0, s>>>(t, slot, nsys); break;
+      case 65: k_fast_x_fwd_batch<32, true><<<n, FAST_XT, 0, s>>>(t, slot, nsys); break;
+      case 96: k_fast_x_fwd_batch<48, false><<<n, FAST_XT, 0, s>>>(t, slot, nsys); break;
+      case 97: k_fast_x_fwd_batch<48, true><<<n, FAST_XT, 0, s>>>(t, slot, nsys); break;
+      case 128: k_fast_x_fwd_batch<64, false><<<n, FAST_XT, 0, s>>>(t, slot, nsys); break;
+      case 129: k_fast_x_fwd_batch<64, true><<<n, FAST_XT, 0, s>>>(t, slot, nsys); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else if (pass == 2) {
+    switch (variant) {
+      case 32: k_fast_x_inv_batch<32><<<n, FAST_IT, 0, s>>>(t, slot, nsys); break;
+      case 48: k_fast_x_inv_batch<48><<<n, FAST_IT, 0, s>>>(t, slot, nsys); break;
+      case 64: k_fast_x_inv_batch<64><<<n, FAST_IT, 0, s>>>(t, slot, nsys); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (variant) {
+#define EK_PLANE(NY, NZ) \
+  case NY * 256 + NZ: return plane_batch_launch<NY, NZ>(t, slot, nsys, ctas, s);
+      EK_PLANE(32, 32) EK_PLANE(32, 48) EK_PLANE(32, 64)
+      EK_PLANE(48, 32) EK_PLANE(48, 48) EK_PLANE(48, 64)
+      EK_PLANE(64, 32) EK_PLANE(64, 48) EK_PLANE(64, 64)
+#undef EK_PLANE
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t charge_density(const Grid& g, const Phys& ph, const void* rho, const void* qwall,

@@ -50,7 +50,8 @@ EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get
            "ek_kernel_launches", "ek_poisson_solve_static", "ek_poisson_mg_scratch_bytes",
            "ek_poisson_solve_mg",
            "ek_batch_create", "ek_batch_destroy", "ek_batch_set_stream", "ek_batch_step_async",
-           "ek_batch_step", "ek_batch_sync", "ek_batch_tune", "ek_batch_config", "ek_batch_size",
+           "ek_batch_step", "ek_batch_sync", "ek_batch_tune", "ek_batch_config", "ek_batch_set_config",
+           "ek_batch_size",
            "ek_batch_last_error"]
 
 
@@ -131,6 +132,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ek_batch_sync.argtypes = [vp]
     lib.ek_batch_tune.argtypes = [vp, ip, ctypes.POINTER(dp)]
     lib.ek_batch_config.argtypes = [vp, ctypes.POINTER(ip)]
+    lib.ek_batch_set_config.argtypes = [vp, ctypes.POINTER(ip)]
     lib.ek_batch_size.argtypes = [vp]
     lib.ek_batch_size.restype = ip
     lib.ek_batch_last_error.argtypes = [vp]
@@ -424,9 +426,20 @@ class EKBatch:
         return self.config(), best.value
 
     def config(self):
-        cfg = (ctypes.c_int * 3)()
+        cfg = (ctypes.c_int * 4)()
         self._check(self.lib.ek_batch_config(self.ptr, cfg))
-        return {"branches": cfg[0], "planes_per_block": cfg[1], "particle_chain_beside_s3": bool(cfg[2])}
+        return {"branches": cfg[0], "planes_per_block": cfg[1], "particle_chain_beside_s3": bool(cfg[2]),
+                "fused": bool(cfg[3])}
+
+    def set_config(self, branches=None, planes_per_block=None, particle_chain_beside_s3=None, fused=None):
+        """Change part of the configuration (the rest stays as it is)."""
+        c = self.config()
+        vals = [c["branches"] if branches is None else branches,
+                c["planes_per_block"] if planes_per_block is None else planes_per_block,
+                int(c["particle_chain_beside_s3"] if particle_chain_beside_s3 is None else particle_chain_beside_s3),
+                int(c["fused"] if fused is None else fused)]
+        cfg = (ctypes.c_int * 4)(*vals)
+        self._check(self.lib.ek_batch_set_config(self.ptr, cfg))
 
     def __len__(self):
         return self.lib.ek_batch_size(self.ptr)

@@ -80,3 +80,72 @@ def test_batch_tuner_steps_conserve_and_choose_a_candidate(gpu_lib):
         p = s.get_particles()[0]
         assert np.all(np.isfinite(p["pos"])) and np.all(np.isfinite(p["vel"]))
     b.close()
+
+
+def compare(ek, batched, alone, fp32):
+    for i, (sb, sa) in enumerate(zip(batched, alone)):
+        x, y = state(ek, sb), state(ek, sa)
+        assert np.array_equal(x["owner"], y["owner"]), i
+        for key in x:
+            scale = max(np.max(np.abs(y[key])), 1e-300)
+            assert np.max(np.abs(x[key] - y[key])) <= 1e-12 * scale, (i, key)
+        if fp32:
+            for k in range(2):  # int units: the same arithmetic gives the same integers
+                assert np.array_equal(x[k], y[k]), (i, k)
+
+
+@pytest.mark.parametrize("edges,overlap", [((16, 24, 32), 1), ((32, 48, 64), 1), ((32, 48, 64), 0)])
+def test_fused_batch_matches_systems_stepped_alone(gpu_lib, edges, overlap):
+    """The fused form (each kernel once over all systems' (system, block)
+    ranges) against the same FP32 systems stepped alone: edges 32, 48 and 64
+    take the batched S1 passes, 16 and 24 their own S1 inside the fused step."""
+    ek = gpu_lib
+    ws = workloads.batch_ensemble(6, seed=78, edges=edges, radius=(2.5, 4.0),
+                                  charge=(-30.0, -10.0), bulk=(1e-3, 1e-2))
+    flags = ek.EK_PV | ek.EK_NEUTRALIZE | FP32
+    batched = [make(ek, w, flags) for w in ws]
+    alone = [make(ek, w, flags) for w in ws]
+    b = ek.EKBatch(batched)
+    assert b.config()["fused"]  # the default where the batch allows it
+    b.set_config(particle_chain_beside_s3=overlap)
+    b.step(3)
+    b.step(4)
+    for s in alone:
+        s.step(7)
+    compare(ek, batched, alone, True)
+    # a step is one set of launches for the whole batch
+    assert sum(s.kernel_launches() for s in batched) < sum(s.kernel_launches() for s in alone)
+    b.close()
+
+
+def test_fused_and_branch_forms_agree_over_a_change_of_form(gpu_lib):
+    """Steps of the fused form, then of the branch form, then fused again end
+    where the systems stepped alone end (the forms share every system's state)."""
+    ek = gpu_lib
+    ws = workloads.batch_ensemble(4, seed=79, edges=(32, 48), radius=(2.5, 4.0),
+                                  charge=(-30.0, -10.0), bulk=(1e-3, 1e-2))
+    flags = ek.EK_PV | ek.EK_NEUTRALIZE | FP32
+    batched = [make(ek, w, flags) for w in ws]
+    alone = [make(ek, w, flags) for w in ws]
+    b = ek.EKBatch(batched)
+    b.step(2)
+    b.set_config(fused=0, branches=2)
+    b.step(3)
+    b.set_config(fused=1)
+    b.step(2)
+    for s in alone:
+        s.step(7)
+    compare(ek, batched, alone, True)
+    b.close()
+
+
+def test_fused_form_refused_for_a_mixed_batch(gpu_lib):
+    ek = gpu_lib
+    ws = ensemble()[:2]
+    systems = [make(ek, ws[0], ek.EK_PV | FP32), make(ek, ws[1], ek.EK_PV)]
+    b = ek.EKBatch(systems)
+    assert not b.config()["fused"]
+    with pytest.raises(ek.EKError):
+        b.set_config(fused=1)
+    b.step(1)
+    b.close()
