@@ -63,6 +63,7 @@ typedef enum {
   EK_ERR_UNSTABLE = -4,  /* a non-finite density or velocity was produced         */
   EK_ERR_OVERLAP = -5,   /* a node lies inside two particles                      */
   EK_ERR_EXPEL = -6,     /* a newly covered node has no fluid neighbour           */
+  EK_ERR_TIMEOUT = -7,   /* a bounded device wait gave up (batch grid barrier)    */
   EK_ERR_STATE = -8      /* call not valid in the context's state, or a capacity  */
 } ek_status;
 
@@ -307,6 +308,10 @@ ek_status ek_poisson_solve_static(const double* q, double* phi, int nx, int ny, 
  *    table -- so a step is about twenty launches whatever the number of
  *    systems.  S1 of the systems whose edges are all 32, 48 or 64 shares
  *    launches by FFT kernel variant; other systems' S1 runs per system.
+ *    A variant of it (form 2) runs the particle kernels between two
+ *    stream-ordered points as phases of one persistent cooperative launch
+ *    whose CTAs meet at a grid barrier between phases; every wait there is
+ *    bounded (EK_ERR_TIMEOUT, ek_batch_wait_test).
  *  - branches: each system's own step is an independent branch of the graph,
  *    so the systems' kernels run side by side on the GPU.
  * The graph is captured on the first step (one per ping-pong parity) and
@@ -335,8 +340,8 @@ ek_status ek_batch_step(ek_batch* b, int nsteps);
 /* Wait for the batch stream and read every system's device status word; the
  * first failing system's status is returned (ek_batch_last_error names it). */
 ek_status ek_batch_sync(ek_batch* b);
-/* Autotuner: times every candidate configuration -- the fused form (where
- * the batch allows it) or branches with 8, 16, 32, 64 or one branch stream
+/* Autotuner: times every candidate configuration -- the fused forms (where
+ * the batch allows them) or branches with 8, 16, 32, 64 or one branch stream
  * per system (at most 64), FP32 S2 segment length (2, 4 or 8 planes per
  * block), and whether the particle chain runs beside the advection or in line
  * -- over 2 + trial_steps real batch steps each (the systems advance by those
@@ -346,13 +351,22 @@ ek_status ek_batch_sync(ek_batch* b);
 ek_status ek_batch_tune(ek_batch* b, int trial_steps, double* best_ms);
 /* Current configuration: cfg[0] branch streams, cfg[1] planes per S2 block,
  * cfg[2] particle chain beside the advection (1) or in line (0), cfg[3] the
- * fused form (1) or branches (0). */
+ * form: 0 branches, 1 fused, 2 fused with the particle kernels other than the
+ * forces as three persistent launches whose phases meet at grid barriers. */
 ek_status ek_batch_config(const ek_batch* b, int cfg[4]);
 /* Set the configuration (cfg as ek_batch_config gives it: branch streams 1 ..
- * min(nsys, 64), planes per S2 block 1 .. 64, overlap 0 or 1, fused 0 or 1);
+ * min(nsys, 64), planes per S2 block 1 .. 64, overlap 0 or 1, form 0, 1 or 2);
  * waits for the batch's earlier work.  EK_ERR_ARG for a value out of range or
- * the fused form on a batch that does not allow it. */
+ * a fused form on a batch that does not allow it. */
 ek_status ek_batch_set_config(ek_batch* b, const int cfg[4]);
+/* Failure-detection test hook for form 2: in the steps captured from now on,
+ * CTA leave_cta of each persistent particle-chain launch returns before the
+ * first grid barrier (-1: none), and a wait at a barrier gives up after
+ * limit_ms (default 1000; at most 60000).  A wait that gives up makes every
+ * CTA of the launch return; ek_batch_sync then returns EK_ERR_TIMEOUT and
+ * puts every system of the batch into the error state (their step stopped
+ * part way).  Waits for the batch's earlier work.  Errors: EK_ERR_ARG. */
+ek_status ek_batch_wait_test(ek_batch* b, int leave_cta, double limit_ms);
 /* Number of systems; 0 for a null batch. */
 int ek_batch_size(const ek_batch* b);
 /* Reason for the last failure of a batch call. */

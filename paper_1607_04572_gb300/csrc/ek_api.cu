@@ -1335,6 +1335,13 @@ struct ek_batch {
   } fused[2];
   cudaStream_t aux = nullptr;  // the particle chain beside S3 in the fused step
   cudaEvent_t ev_lb = nullptr, ev_part = nullptr;
+  // fuse == 2: the particle kernels (but the forces) as three persistent
+  // launches with grid barriers; dstatus[0] is the batch's status word, then
+  // three barrier blocks of four words
+  int* dstatus = nullptr;
+  int chain_ctas = 0;
+  long long limit_ns = 1000000000LL;  // a barrier wait gives up after this
+  int leave_cta = -1;                 // failure-detection test hook
 };
 
 namespace {
@@ -1569,8 +1576,36 @@ ek_status batch_capture_fused(ek_batch* b, int key) {
     ok(cudaEventRecord(b->ev_fork, s));
     ok(cudaStreamWaitEvent(b->aux, b->ev_fork, 0));
   }
-  ok(part(PK_ASSIGN, ps));
-  ok(part(PK_TIE, ps));
+  // fuse == 2: the phases between two stream-ordered points as one persistent
+  // launch (its barrier block zeroed in the graph first)
+  const bool chain = b->fuse == 2;
+  const auto chain_launch = [&](int blk, std::initializer_list<int> kinds, cudaStream_t on) {
+    ChainArgs A;
+    A.tab = (const PartArgs*)(base + (*kinds.begin() <= PK_TIE ? F.o_pre : F.o_post));
+    A.nph = 0;
+    int most = 0;
+    for (int k : kinds) {
+      const ek_batch::Launch& L = F.part[k];
+      if (L.ctas == 0) continue;
+      A.ph[A.nph++] = ChainPhase{k, L.ctas, L.nslot, (const BatchSlot*)(base + L.slot)};
+      most = std::max(most, L.ctas);
+    }
+    if (A.nph == 0) return cudaSuccess;
+    A.bar = (unsigned*)(b->dstatus + 4 * blk);
+    A.status = b->dstatus;
+    A.limit_ns = b->limit_ns;
+    A.leave_cta = b->leave_cta;
+    cudaError_t r = cudaMemsetAsync(A.bar, 0, 4 * sizeof(unsigned), on);
+    if (r != cudaSuccess) return r;
+    ++count;
+    return launch_particle_chain(A, std::min(most, b->chain_ctas), on);
+  };
+  if (chain) {
+    ok(chain_launch(1, {PK_ASSIGN, PK_TIE}, ps));
+  } else {
+    ok(part(PK_ASSIGN, ps));
+    ok(part(PK_TIE, ps));
+  }
   for (int pass = 0; pass < 3; ++pass) {
     for (const ek_batch::Launch& L : F.fft[pass]) {
       ok(launch_poisson_batch(pass, L.variant, base + F.o_pa, (const BatchSlot*)(base + L.slot), L.nslot,
@@ -1590,15 +1625,24 @@ ek_status batch_capture_fused(ek_batch* b, int key) {
     ok(cudaEventRecord(b->ev_lb, s));
     ok(cudaStreamWaitEvent(b->aux, b->ev_lb, 0));
   }
-  for (int k = PK_FORCES; k <= PK_CHARGE; ++k) ok(part(k, ps));
+  if (chain) {
+    ok(part(PK_FORCES, ps));
+    ok(chain_launch(2, {PK_SAVE_PREV, PK_CLEAR, PK_CLAIM, PK_PSI, PK_CHARGE}, ps));
+  } else {
+    for (int k = PK_FORCES; k <= PK_CHARGE; ++k) ok(part(k, ps));
+  }
   if (b->overlap) ok(cudaEventRecord(b->ev_part, b->aux));
   if (K > 0) {
     ok(launch_advection32_batch(lbl(F.adv), K, s));
     ++count;
   }
   if (b->overlap) ok(cudaStreamWaitEvent(s, b->ev_part, 0));
-  ok(part(PK_TRANS, s));
-  ok(part(PK_APPLY, s));
+  if (chain) {
+    ok(chain_launch(3, {PK_TRANS, PK_APPLY}, s));
+  } else {
+    ok(part(PK_TRANS, s));
+    ok(part(PK_APPLY, s));
+  }
   const cudaError_t ec = cudaStreamEndCapture(s, &graph);
   if (e != cudaSuccess || ec != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -1695,6 +1739,9 @@ ek_status ek_batch_create(ek_ctx* const* systems, int nsys, ek_batch** out) {
   // the systems' earlier work (set-up, fields) is on their own streams
   for (ek_ctx* c : b->sys) ok = ok && cudaStreamSynchronize(c->stream) == cudaSuccess;
   b->width = std::min(nbranch, 16);
+  ok = ok && cudaMalloc((void**)&b->dstatus, 16 * sizeof(int)) == cudaSuccess &&
+       cudaMemset(b->dstatus, 0, 16 * sizeof(int)) == cudaSuccess;
+  b->chain_ctas = ok ? particle_chain_ctas() : 0;
   b->fusable = true;
   for (ek_ctx* c : b->sys)
     b->fusable = b->fusable && c->fp32 && c->ph.K == b->sys[0]->ph.K && c->ph.pv == b->sys[0]->ph.pv;
@@ -1721,6 +1768,7 @@ ek_status ek_batch_destroy(ek_batch* b) {
   if (b->ev_lb) cudaEventDestroy(b->ev_lb);
   if (b->ev_part) cudaEventDestroy(b->ev_part);
   if (b->aux) cudaStreamDestroy(b->aux);
+  if (b->dstatus) cudaFree(b->dstatus);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return EK_OK;
@@ -1761,6 +1809,17 @@ ek_status ek_batch_sync(ek_batch* b) {
   if (!b) return EK_ERR_ARG;
   cudaSetDevice(b->device);
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, EK_ERR_CUDA, "batch stream failed");
+  int bst = 0;
+  if (b->dstatus && cudaMemcpy(&bst, b->dstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bfail(b, EK_ERR_CUDA, "batch status could not be read");
+  if (bst & ST_TIMEOUT) {
+    // a step stopped part way: no system's state is a state of the method
+    for (ek_ctx* c : b->sys) {
+      c->broken = true;
+      c->err = "a batch step was cut short by a grid-barrier timeout";
+    }
+    return bfail(b, EK_ERR_TIMEOUT, "a grid barrier of the persistent particle chain timed out");
+  }
   ek_status worst = EK_OK;
   for (size_t i = 0; i < b->sys.size(); ++i) {
     const ek_status st = check_status(b->sys[i]);
@@ -1783,7 +1842,16 @@ ek_status ek_batch_config(const ek_batch* b, int cfg[4]) {
   cfg[0] = b->width;
   cfg[1] = b->planes;
   cfg[2] = b->overlap;
-  cfg[3] = b->fuse && b->fusable ? 1 : 0;
+  cfg[3] = b->fusable ? b->fuse : 0;
+  return EK_OK;
+}
+
+ek_status ek_batch_wait_test(ek_batch* b, int leave_cta, double limit_ms) {
+  if (!b || leave_cta < -1 || !(limit_ms > 0.0) || limit_ms > 60000.0) return EK_ERR_ARG;
+  cudaSetDevice(b->device);
+  b->leave_cta = leave_cta;
+  b->limit_ns = (long long)(limit_ms * 1e6);
+  batch_drop(b);
   return EK_OK;
 }
 
@@ -1804,7 +1872,10 @@ ek_status ek_batch_tune(ek_batch* b, int trial_steps, double* best_ms) {
   std::vector<std::tuple<int, int, int, int>> cands;
   for (int pl : {2, 4, 8})
     for (int ov = 0; ov <= 1; ++ov) {
-      if (b->fusable) cands.emplace_back(1, b->width, pl, ov);
+      if (b->fusable) {
+        cands.emplace_back(1, b->width, pl, ov);
+        if (b->chain_ctas > 0) cands.emplace_back(2, b->width, pl, ov);
+      }
       for (int w : widths) cands.emplace_back(0, w, pl, ov);
     }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1849,7 +1920,7 @@ ek_status ek_batch_tune(ek_batch* b, int trial_steps, double* best_ms) {
 ek_status ek_batch_set_config(ek_batch* b, const int cfg[4]) {
   if (!b || !cfg) return EK_ERR_ARG;
   if (cfg[0] < 1 || cfg[0] > (int)b->branch.size() || cfg[1] < 1 || cfg[1] > 64 || cfg[2] < 0 ||
-      cfg[2] > 1 || cfg[3] < 0 || cfg[3] > 1)
+      cfg[2] > 1 || cfg[3] < 0 || cfg[3] > 2)
     return bfail(b, EK_ERR_ARG, "configuration out of range");
   if (cfg[3] && !b->fusable)
     return bfail(b, EK_ERR_ARG, "the fused form needs FP32 systems with one species count and partial-volume choice");

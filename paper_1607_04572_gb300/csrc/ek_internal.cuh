@@ -62,6 +62,7 @@ enum : int {
   ST_OVERLAP = 2,
   ST_EXPEL = 4,
   ST_CAPACITY = 8,
+  ST_TIMEOUT = 16,  // a bounded device wait gave up (the batch's grid barrier)
 };
 
 // Particle record on the device (all FP64).
@@ -194,10 +195,9 @@ struct BatchSlot {
   int entry;  // the system's row of the argument table
 };
 __device__ __forceinline__ Blk grid_blk() { return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x}; }
-// the system whose range holds this CTA (binary search over the ascending
-// cta0), and the CTA's block in that system's grid
-__device__ __forceinline__ Blk batch_blk(const BatchSlot* __restrict__ sl, int nsys, int& sys) {
-  const int b = (int)blockIdx.x;
+// the system whose range holds CTA (or work item) b (binary search over the
+// ascending cta0), and the block it is in that system's grid
+__device__ __forceinline__ Blk batch_blk_at(const BatchSlot* __restrict__ sl, int nsys, int b, int& sys) {
   int lo = 0, hi = nsys - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -208,6 +208,9 @@ __device__ __forceinline__ Blk batch_blk(const BatchSlot* __restrict__ sl, int n
   sys = s.entry;
   const int l = b - s.cta0;
   return Blk{l % s.gx, l / s.gx, s.gx};
+}
+__device__ __forceinline__ Blk batch_blk(const BatchSlot* __restrict__ sl, int nsys, int& sys) {
+  return batch_blk_at(sl, nsys, (int)blockIdx.x, sys);
 }
 // a batched launch: per-system argument table and ranges (device memory), the
 // number of systems and the CTA total
@@ -428,6 +431,31 @@ enum PartKernel {
 // the grid (gx, gy) kernel k runs for one system; gx = 0: no launch (P = 0)
 void particle_batch_grid(int k, const PartArgs& a, int& gx, int& gy);
 cudaError_t launch_particle_batch(int k, const BatchLaunch<PartArgs>& L, cudaStream_t s);
+// Several of those kernels (all but PK_FORCES) as phases of one persistent
+// launch: the resident CTAs take each phase's (system, block) items in turn
+// and meet at a grid barrier before the next phase.  Each wait at the barrier
+// ends after limit_ns of the global timer at most: the CTA then sets
+// ST_TIMEOUT in *status and the abort word, and every CTA returns.
+constexpr int CHAIN_MAX = 5;
+struct ChainPhase {
+  int kind;  // PartKernel
+  int ctas;  // items: the CTAs the batched launch would have
+  int nslot;
+  const BatchSlot* slot;
+};
+struct ChainArgs {
+  const PartArgs* tab;
+  ChainPhase ph[CHAIN_MAX];
+  int nph;
+  unsigned* bar;      // [0] arrivals, [1] generation, [2] abort; zero before the launch
+  int* status;        // ST_TIMEOUT on a wait that gave up
+  long long limit_ns;
+  int leave_cta;      // failure-detection test: this CTA returns before the first barrier (-1: none)
+};
+// CTAs of the persistent launch that are resident at once (it is a
+// cooperative launch of that many at most)
+int particle_chain_ctas();
+cudaError_t launch_particle_chain(const ChainArgs& A, int ctas, cudaStream_t s);
 cudaError_t launch_fill(const Grid& g, const Phys& ph, const int* owner, double* f, double* rho,
                         const double* bulk_k, cudaStream_t s);
 

@@ -1541,7 +1541,107 @@ EK_PART_BATCH(k_transitions_batch, transitions_body<FormF32>, __launch_bounds__(
 EK_PART_BATCH(k_apply_transfers_batch, apply_transfers_body<FormF32>, __launch_bounds__(256))
 #undef EK_PART_BATCH
 
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier of the persistent chain (all CTAs resident).  Thread 0 reads
+// the generation, arrives, and the last arrival resets the count and
+// advances the generation; the others wait for that, for the abort word, or
+// until limit_ns has passed (then they set the timeout status and the abort
+// word).  Returns false when the kernel must end.
+__device__ bool chain_barrier(const ChainArgs& A) {
+  __shared__ int go;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* bar = A.bar;
+    int ok = bar[2] == 0u;
+    if (ok) {
+      const unsigned gen = bar[1];
+      __threadfence();
+      if (atomicAdd(A.bar, 1u) == gridDim.x - 1) {
+        atomicExch(A.bar, 0u);
+        __threadfence();
+        atomicAdd(A.bar + 1, 1u);
+      } else {
+        const long long t0 = global_ns();
+        while (bar[1] == gen) {
+          if (bar[2] != 0u) {
+            ok = 0;
+            break;
+          }
+          if (global_ns() - t0 > A.limit_ns) {
+            atomicOr(A.status, ST_TIMEOUT);
+            atomicExch(A.bar + 2, 1u);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+    go = ok;
+  }
+  __syncthreads();
+  return go != 0;
+}
+
+// The phases of the chain: a CTA takes items blockIdx.x, + gridDim.x, ... of
+// each phase (each item one block of a system's grid, CTA-uniform, so the
+// bodies' own barriers are met by the whole CTA).
+__global__ void __launch_bounds__(256) k_particle_chain(ChainArgs A) {
+  if ((int)blockIdx.x == A.leave_cta) return;
+  for (int q = 0; q < A.nph; ++q) {
+    if (q > 0 && !chain_barrier(A)) return;
+    const ChainPhase& P = A.ph[q];
+    for (int w = (int)blockIdx.x; w < P.ctas; w += (int)gridDim.x) {
+      int sys;
+      const Blk bk = batch_blk_at(P.slot, P.nslot, w, sys);
+      const PartArgs& a = A.tab[sys];
+      switch (P.kind) {
+        case PK_ASSIGN: force_assign_body(a, bk); break;
+        case PK_TIE: tie_resolve_body(a, bk); break;
+        case PK_SAVE_PREV: save_prev_body(a, bk); break;
+        case PK_CLEAR: clear_body<FormF32>(a, bk); break;
+        case PK_CLAIM: claim_body<FormF32>(a, bk); break;
+        case PK_PSI: psi_surface_body<FormF32>(a, bk); break;
+        case PK_CHARGE: charge_scatter_body<FormF32>(a, bk); break;
+        case PK_TRANS: transitions_body<FormF32>(a, bk); break;
+        case PK_APPLY: apply_transfers_body<FormF32>(a, bk); break;
+        default: break;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+int particle_chain_ctas() {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_particle_chain, 256, 0) != cudaSuccess)
+    return 0;
+  return sms * per;
+}
+
+cudaError_t launch_particle_chain(const ChainArgs& A, int ctas, cudaStream_t s) {
+  if (ctas <= 0 || A.nph <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_particle_chain, A);
+}
 
 void particle_batch_grid(int k, const PartArgs& a, int& gx, int& gy) {
   gx = a.P;

@@ -39,7 +39,8 @@ FIELD_OWNER = 10
 FIELD_CHARGE = 11
 
 STATUS = {0: "EK_OK", -1: "EK_ERR_ARG", -2: "EK_ERR_NOMEM", -3: "EK_ERR_CUDA",
-          -4: "EK_ERR_UNSTABLE", -5: "EK_ERR_OVERLAP", -6: "EK_ERR_EXPEL", -8: "EK_ERR_STATE"}
+          -4: "EK_ERR_UNSTABLE", -5: "EK_ERR_OVERLAP", -6: "EK_ERR_EXPEL", -7: "EK_ERR_TIMEOUT",
+          -8: "EK_ERR_STATE"}
 
 # entry points declared in include/ek.h
 EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get_fields",
@@ -51,7 +52,7 @@ EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get
            "ek_poisson_solve_mg",
            "ek_batch_create", "ek_batch_destroy", "ek_batch_set_stream", "ek_batch_step_async",
            "ek_batch_step", "ek_batch_sync", "ek_batch_tune", "ek_batch_config", "ek_batch_set_config",
-           "ek_batch_size",
+           "ek_batch_wait_test", "ek_batch_size",
            "ek_batch_last_error"]
 
 
@@ -133,6 +134,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ek_batch_tune.argtypes = [vp, ip, ctypes.POINTER(dp)]
     lib.ek_batch_config.argtypes = [vp, ctypes.POINTER(ip)]
     lib.ek_batch_set_config.argtypes = [vp, ctypes.POINTER(ip)]
+    lib.ek_batch_wait_test.argtypes = [vp, ip, dp]
     lib.ek_batch_size.argtypes = [vp]
     lib.ek_batch_size.restype = ip
     lib.ek_batch_last_error.argtypes = [vp]
@@ -429,7 +431,7 @@ class EKBatch:
         cfg = (ctypes.c_int * 4)()
         self._check(self.lib.ek_batch_config(self.ptr, cfg))
         return {"branches": cfg[0], "planes_per_block": cfg[1], "particle_chain_beside_s3": bool(cfg[2]),
-                "fused": bool(cfg[3])}
+                "fused": cfg[3]}
 
     def set_config(self, branches=None, planes_per_block=None, particle_chain_beside_s3=None, fused=None):
         """Change part of the configuration (the rest stays as it is)."""
@@ -440,6 +442,12 @@ class EKBatch:
                 int(c["fused"] if fused is None else fused)]
         cfg = (ctypes.c_int * 4)(*vals)
         self._check(self.lib.ek_batch_set_config(self.ptr, cfg))
+
+    def wait_test(self, leave_cta=-1, limit_ms=1000.0):
+        """Failure-detection hook of the persistent particle chain (form 2):
+        one CTA leaves before the first grid barrier, the waits give up after
+        limit_ms (see ek_batch_wait_test in include/ek.h)."""
+        self._check(self.lib.ek_batch_wait_test(self.ptr, int(leave_cta), float(limit_ms)))
 
     def __len__(self):
         return self.lib.ek_batch_size(self.ptr)

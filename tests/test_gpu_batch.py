@@ -94,11 +94,15 @@ def compare(ek, batched, alone, fp32):
                 assert np.array_equal(x[k], y[k]), (i, k)
 
 
-@pytest.mark.parametrize("edges,overlap", [((16, 24, 32), 1), ((32, 48, 64), 1), ((32, 48, 64), 0)])
-def test_fused_batch_matches_systems_stepped_alone(gpu_lib, edges, overlap):
-    """The fused form (each kernel once over all systems' (system, block)
-    ranges) against the same FP32 systems stepped alone: edges 32, 48 and 64
-    take the batched S1 passes, 16 and 24 their own S1 inside the fused step."""
+@pytest.mark.parametrize("edges,overlap,form", [((16, 24, 32), 1, 1), ((32, 48, 64), 1, 1),
+                                               ((32, 48, 64), 0, 1), ((16, 24, 32), 1, 2),
+                                               ((32, 48, 64), 0, 2)])
+def test_fused_batch_matches_systems_stepped_alone(gpu_lib, edges, overlap, form):
+    """The fused forms (each kernel once over all systems' (system, block)
+    ranges; form 2 with the particle kernels as persistent launches whose
+    phases meet at grid barriers) against the same FP32 systems stepped
+    alone: edges 32, 48 and 64 take the batched S1 passes, 16 and 24 their own
+    S1 inside the fused step."""
     ek = gpu_lib
     ws = workloads.batch_ensemble(6, seed=78, edges=edges, radius=(2.5, 4.0),
                                   charge=(-30.0, -10.0), bulk=(1e-3, 1e-2))
@@ -106,8 +110,9 @@ def test_fused_batch_matches_systems_stepped_alone(gpu_lib, edges, overlap):
     batched = [make(ek, w, flags) for w in ws]
     alone = [make(ek, w, flags) for w in ws]
     b = ek.EKBatch(batched)
-    assert b.config()["fused"]  # the default where the batch allows it
-    b.set_config(particle_chain_beside_s3=overlap)
+    assert b.config()["fused"] == 1  # the default where the batch allows it
+    b.set_config(particle_chain_beside_s3=overlap, fused=form)
+    assert b.config()["fused"] == form
     b.step(3)
     b.step(4)
     for s in alone:
@@ -149,3 +154,30 @@ def test_fused_form_refused_for_a_mixed_batch(gpu_lib):
         b.set_config(fused=1)
     b.step(1)
     b.close()
+
+
+def test_grid_barrier_wait_is_bounded_and_reported(gpu_lib):
+    """Failure detection of the persistent particle chain without a fault: one
+    CTA of each persistent launch leaves before the first grid barrier, so the
+    others' waits run out (after 20 ms); the kernel ends, the batch reports
+    EK_ERR_TIMEOUT and its systems refuse further work, and the device stays
+    usable (a new system steps normally)."""
+    ek = gpu_lib
+    ws = workloads.batch_ensemble(4, seed=80, edges=(32, 48), radius=(2.5, 4.0),
+                                  charge=(-30.0, -10.0), bulk=(1e-3, 1e-2))
+    flags = ek.EK_PV | ek.EK_NEUTRALIZE | FP32
+    systems = [make(ek, w, flags) for w in ws]
+    b = ek.EKBatch(systems)
+    b.set_config(fused=2)
+    b.step(2)  # the barriers pass when every CTA arrives
+    b.wait_test(leave_cta=0, limit_ms=20.0)
+    with pytest.raises(ek.EKError) as e:
+        b.step(1)
+    assert e.value.code == -7  # EK_ERR_TIMEOUT
+    with pytest.raises(ek.EKError):
+        b.step(1)  # the systems stopped part way through a step
+    b.close()
+    s = make(ek, ws[0], flags)
+    s.step(3)
+    p = s.get_particles()[0]
+    assert np.all(np.isfinite(p["pos"]))
