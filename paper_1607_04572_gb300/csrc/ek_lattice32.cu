@@ -139,6 +139,15 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
 }
 
+// periodic coordinate of a tile-halo position v in [-1, n + 33).  One wrap
+// is exact for every position a node of the box reads (at most n); the
+// positions past it, which exist only for edges below the tile width and are
+// never read, are clamped into the box so that their loads stay in bounds.
+__device__ __forceinline__ int halo_wrap(int v, int n) {
+  v = v < 0 ? v + n : (v >= n ? v - n : v);
+  return min(v, n - 1);
+}
+
 // stencil fields of plane zz (periodic) into ring slot `slot`
 template <int K, bool PV>
 __device__ __forceinline__ void stage_plane(LBRing<K>& t, int slot, int zz, int x0, int y0,
@@ -149,9 +158,7 @@ __device__ __forceinline__ void stage_plane(LBRing<K>& t, int slot, int zz, int 
   const int tid = threadIdx.x + TILE_X * threadIdx.y;
   for (int e = tid; e < HP; e += TN) {
     const int ey = e / HX, ex = e - ey * HX;
-    int x = x0 - 1 + ex, y = y0 - 1 + ey;
-    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    const int x = halo_wrap(x0 - 1 + ex, nx), y = halo_wrap(y0 - 1 + ey, ny);
     const size_t m = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
     cp_async4(&t.own[slot][e], a.owner + m);
     cp_async4(&t.phi[slot][e], (const float*)a.phi + m);
@@ -453,94 +460,192 @@ __device__ __forceinline__ float vof_share(float vx, float vy, float vz, int ox,
 
 __device__ __forceinline__ int sgnf(float v) { return v > 0.0f ? 1 : (v < 0.0f ? -1 : 0); }
 
-// S3 (FP32 form): the node pulls the shares its 26 neighbours send it and
-// gives away its own; the per-node sign byte of S2 decides which neighbours
-// send anything before any of their data is loaded.  Node indices are 32-bit
-// (N < 2^31) from per-array base pointers and the three x, row and plane
-// offsets of the neighbourhood; every loop is unrolled, so the sign tests use
-// constant masks.  Each share is computed with the same operations as in its
-// source, and integer sums do not depend on their order.
+// ---------------------------------------------------------------------------
+// S3 (FP32 form), tiled.  A 32 x 8 block marches through a segment of planes
+// of its (x, y) tile column.  For every source plane it first computes, for
+// each node of the tile and its one-node halo, the integer shares of each
+// species that the node's volume-of-fluid displacement sends to the seven
+// offsets {0, sign(v_a)}^3 \ 0 (a shared-memory ring of three planes, with
+// the nodes' sign bytes from S2); then every fluid node of the middle plane
+// subtracts its own shares aimed at fluid nodes and adds the shares its 26
+// neighbours aim at it.  A share is computed by the same operations in every
+// block that holds its source, so a source's loss and its destination's gain
+// are the same integers and the species totals do not change.
+// ---------------------------------------------------------------------------
 template <int K>
-__device__ __forceinline__ void advect32_block(const LBArgs& a, int bx, int by, int bz) {
-  const int nx = a.g.nx, ny = a.g.ny;
-  const int x = bx * TILE_X + threadIdx.x;
-  const int y = by * TILE_Y + threadIdx.y;
-  const int z = bz;
-  if (x >= nx || y >= ny) return;
-  const unsigned char* __restrict__ vs = a.vsig;
-  const int n = x + nx * (y + ny * z);
-  if (!(vs[n] & 0x80u)) return;
+struct AdvRing {
+  int sh[3][7][K][HP];       // shares by class (ox | oy << 1 | oz << 2) - 1
+  unsigned char sg[3][HP];   // sign byte of S2: bit 7 fluid, sign codes of u
+};
+
+template <int K>
+constexpr size_t adv32_smem() { return sizeof(AdvRing<K>); }
+
+// planes per z segment of the tiled S3 grid
+constexpr int ADV_PLANES = 8;
+__host__ __device__ inline int adv32_segments(const Grid& g) {
+  const int s = (g.nz + ADV_PLANES - 1) / ADV_PLANES;
+  return s > 1 ? s : 1;
+}
+
+// the sign bytes, velocities and species of a source plane's halo-tile
+// nodes held by one thread (up to two nodes), loaded one plane ahead of use
+template <int K>
+struct AdvSrc {
+  static constexpr int PER = (HP + TN - 1) / TN;
+  unsigned sgn[PER];
+  float v[PER][3];
+  int r[PER][K];
+};
+
+// in-plane offsets of the thread's halo-tile nodes (-1: none)
+template <int K>
+__device__ __forceinline__ void adv_offsets(int (&hoff)[AdvSrc<K>::PER], int x0, int y0, const LBArgs& a) {
+  const int tid = threadIdx.x + TILE_X * threadIdx.y;
+#pragma unroll
+  for (int q = 0; q < AdvSrc<K>::PER; ++q) {
+    const int e = tid + q * TN;
+    const int ey = e / HX, ex = e - ey * HX;
+    hoff[q] = e < HP ? halo_wrap(x0 - 1 + ex, a.g.nx) + a.g.nx * halo_wrap(y0 - 1 + ey, a.g.ny) : -1;
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void adv_load(AdvSrc<K>& R, const int (&hoff)[AdvSrc<K>::PER], int zz,
+                                         const LBArgs& a) {
+  const int nz = a.g.nz;
   const int N = (int)a.g.N;
+  const int z = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+  const int pz = a.g.nx * a.g.ny * z;
   const float* __restrict__ ux = (const float*)a.u;
   const float* __restrict__ uy = ux + N;
   const float* __restrict__ uz = uy + N;
-  const int* nin[K > 0 ? K : 1];
-  int* nout[K > 0 ? K : 1];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    nin[k] = (const int*)a.rho_in + (size_t)k * N;
-    nout[k] = (int*)a.rho_out + (size_t)k * N;
-  }
-  const Nbr b = make_nbr(x, y, z, a.g);
-  const int nxy = nx * ny;
-  const int X0 = b.xm, X1 = x, X2 = b.xp;
-  const int Y0 = nx * b.ym, Y1 = nx * y, Y2 = nx * b.yp;
-  const int Z0 = nxy * b.zm, Z1 = nxy * z, Z2 = nxy * b.zp;
-  int acc[K > 0 ? K : 1];
-  float rs[K > 0 ? K : 1];
+  for (int q = 0; q < AdvSrc<K>::PER; ++q) {
+    R.sgn[q] = 0u;
+    if (hoff[q] >= 0) {
+      const int m = hoff[q] + pz;
+      R.sgn[q] = a.vsig[m];
+      R.v[q][0] = ux[m];
+      R.v[q][1] = uy[m];
+      R.v[q][2] = uz[m];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    acc[k] = nout[k][n];
-    rs[k] = (float)nin[k][n];
-  }
-  const float vx = ux[n], vy = uy[n], vz = uz[n];
-  const int sx = sgnf(vx), sy = sgnf(vy), sz = sgnf(vz);
-  // the node's own shares to offsets (ox, oy, oz) in {0, sign(v_a)}^3
-  const int xs = sx > 0 ? X2 : (sx < 0 ? X0 : X1);
-  const int ys = sy > 0 ? Y2 : (sy < 0 ? Y0 : Y1);
-  const int zs = sz > 0 ? Z2 : (sz < 0 ? Z0 : Z1);
-#pragma unroll
-  for (int o = 1; o < 8; ++o) {
-    const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-    if ((ox && !sx) || (oy && !sy) || (oz && !sz)) continue;
-    const int m = (ox ? xs : X1) + (oy ? ys : Y1) + (oz ? zs : Z1);
-    if (!(vs[m] & 0x80u)) continue;  // share aimed at a boundary stays here
-    const float frac = vof_share(vx, vy, vz, ox, oy, oz);
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] -= __float2int_rn(__fmul_rn(rs[k], frac));
-  }
-  // shares from the neighbour at -q: fluid and moving towards this node along
-  // every nonzero component of q
-#pragma unroll
-  for (int qz = -1; qz <= 1; ++qz) {
-#pragma unroll
-    for (int qy = -1; qy <= 1; ++qy) {
-#pragma unroll
-      for (int qx = -1; qx <= 1; ++qx) {
-        if (!qx && !qy && !qz) continue;
-        const unsigned mask = 0x80u | (qx ? 3u : 0u) | (qy ? 12u : 0u) | (qz ? 48u : 0u);
-        const unsigned want = 0x80u | (qx > 0 ? 1u : (qx < 0 ? 2u : 0u)) |
-                              (qy > 0 ? 4u : (qy < 0 ? 8u : 0u)) | (qz > 0 ? 16u : (qz < 0 ? 32u : 0u));
-        const int m = (qx > 0 ? X0 : (qx < 0 ? X2 : X1)) + (qy > 0 ? Y0 : (qy < 0 ? Y2 : Y1)) +
-                      (qz > 0 ? Z0 : (qz < 0 ? Z2 : Z1));
-        if ((vs[m] & mask) != want) continue;
-        const float frac = vof_share(ux[m], uy[m], uz[m], qx != 0, qy != 0, qz != 0);
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += __float2int_rn(__fmul_rn((float)nin[k][m], frac));
-      }
+      for (int k = 0; k < K; ++k) R.r[q][k] = ((const int*)a.rho_in + (size_t)k * N)[m];
     }
   }
+}
+
+// the loaded plane's shares into ring slot `slot`
+template <int K>
+__device__ __forceinline__ void adv_store(AdvRing<K>& t, int slot, const AdvSrc<K>& R) {
+  const int tid = threadIdx.x + TILE_X * threadIdx.y;
 #pragma unroll
-  for (int k = 0; k < K; ++k) nout[k][n] = acc[k];
+  for (int q = 0; q < AdvSrc<K>::PER; ++q) {
+    const int e = tid + q * TN;
+    if (e >= HP) continue;
+    t.sg[slot][e] = (unsigned char)R.sgn[q];
+    if (!(R.sgn[q] & 0x80u)) continue;  // never a source: nothing reads its shares
+#pragma unroll
+    for (int o = 1; o < 8; ++o) {
+      const float frac = vof_share(R.v[q][0], R.v[q][1], R.v[q][2], o & 1, (o >> 1) & 1, o >> 2);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        t.sh[slot][o - 1][k][e] = __float2int_rn(__fmul_rn((float)R.r[q][k], frac));
+    }
+  }
+}
+
+// sign code (bits 0-1 of c >> shift) as -1, 0, +1
+__device__ __forceinline__ int sign_of(unsigned c, int shift) {
+  const unsigned v = (c >> shift) & 3u;
+  return v == 1u ? 1 : (v == 2u ? -1 : 0);
+}
+
+template <int K>
+__device__ __forceinline__ void advect32_block(const LBArgs& a, int bx, int by, int bz, int nseg) {
+  extern __shared__ __align__(16) unsigned char adv_smem[];
+  AdvRing<K>& t = *reinterpret_cast<AdvRing<K>*>(adv_smem);
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const int N = (int)a.g.N;
+  const int x0 = bx * TILE_X, y0 = by * TILE_Y;
+  const int z0 = (int)((long long)bz * nz / nseg);
+  const int zend = (int)((long long)(bz + 1) * nz / nseg);
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  const bool in_xy = x < nx && y < ny;
+  const int c = (threadIdx.y + 1) * HX + threadIdx.x + 1;  // the node's halo-tile index
+  int* nout[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) nout[k] = (int*)a.rho_out + (size_t)k * N;
+  // ring slot of plane zz: (zz - z0 + 1) mod 3; the sources of plane z + 2
+  // are loaded while plane z is summed
+  AdvSrc<K> R;
+  int hoff[AdvSrc<K>::PER];
+  adv_offsets<K>(hoff, x0, y0, a);
+  adv_load<K>(R, hoff, z0 - 1, a);
+  adv_store<K>(t, 0, R);
+  adv_load<K>(R, hoff, z0, a);
+  adv_store<K>(t, 1, R);
+  adv_load<K>(R, hoff, z0 + 1, a);
+  for (int z = z0; z < zend; ++z) {
+    const int s0 = (z - z0) % 3, s1 = (z - z0 + 1) % 3, s2 = (z - z0 + 2) % 3;
+    const int n = x + nx * (y + ny * z);
+    int acc[K];
+    if (in_xy) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = nout[k][n];  // S2's result, issued early
+    }
+    adv_store<K>(t, s2, R);
+    if (z + 2 <= zend) adv_load<K>(R, hoff, z + 2, a);
+    __syncthreads();
+    const unsigned own = in_xy ? t.sg[s1][c] : 0u;
+    if (own & 0x80u) {
+      // own shares to the offsets {0, sign(v_a)}^3 \ 0 whose node is fluid
+      const int sx = sign_of(own, 0), sy = sign_of(own, 2), sz = sign_of(own, 4);
+      const int ts = sz > 0 ? s2 : (sz < 0 ? s0 : s1);
+#pragma unroll
+      for (int o = 1; o < 8; ++o) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+        if ((ox && !sx) || (oy && !sy) || (oz && !sz)) continue;
+        const int tc = c + (oy ? sy * HX : 0) + (ox ? sx : 0);
+        if (!(t.sg[oz ? ts : s1][tc] & 0x80u)) continue;  // aimed at a boundary: stays here
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] -= t.sh[s1][o - 1][k][c];
+      }
+      // shares of the neighbour at -q: fluid and moving towards this node
+      // along every nonzero component of q
+#pragma unroll
+      for (int qz = -1; qz <= 1; ++qz) {
+        const int ss = qz > 0 ? s0 : (qz < 0 ? s2 : s1);
+#pragma unroll
+        for (int qy = -1; qy <= 1; ++qy) {
+#pragma unroll
+          for (int qx = -1; qx <= 1; ++qx) {
+            if (!qx && !qy && !qz) continue;
+            const unsigned mask = 0x80u | (qx ? 3u : 0u) | (qy ? 12u : 0u) | (qz ? 48u : 0u);
+            const unsigned want = 0x80u | (qx > 0 ? 1u : (qx < 0 ? 2u : 0u)) |
+                                  (qy > 0 ? 4u : (qy < 0 ? 8u : 0u)) | (qz > 0 ? 16u : (qz < 0 ? 32u : 0u));
+            const int sc = c - qy * HX - qx;
+            if ((t.sg[ss][sc] & mask) != want) continue;
+            const int cls = (qx ? 1 : 0) | (qy ? 2 : 0) | (qz ? 4 : 0);
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] += t.sh[ss][cls - 1][k][sc];
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) nout[k][n] = acc[k];
+    }
+    __syncthreads();  // the next plane's shares overwrite slot s0
+  }
 }
 
 template <int K>
 __global__ void __launch_bounds__(256) k_advect32(LBArgs a, Phys32 c) {
   (void)c;
-  advect32_block<K>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+  advect32_block<K>(a, blockIdx.x, blockIdx.y, blockIdx.z, (int)gridDim.z);
 }
 
-// S3 of a batch's systems in one launch (system s: its xt x (yt nz) grid)
+// S3 of a batch's systems in one launch (system s: its xt x (yt nseg) grid)
 template <int K>
 __global__ void __launch_bounds__(256) k_advect32_batch(const LBBatchEntry* __restrict__ tab,
                                                         const BatchSlot* __restrict__ slot, int nsys) {
@@ -548,7 +653,7 @@ __global__ void __launch_bounds__(256) k_advect32_batch(const LBBatchEntry* __re
   const Blk b = batch_blk(slot, nsys, sys);
   const LBArgs& a = tab[sys].a;
   const int yt = (a.g.ny + TILE_Y - 1) / TILE_Y;
-  advect32_block<K>(a, b.x, b.y % yt, b.y / yt);
+  advect32_block<K>(a, b.x, b.y % yt, b.y / yt, adv32_segments(a.g));
 }
 
 __global__ void k_fill32(Grid g, const int* owner, float* f, int* rho, int K, float rho0, int n0,
@@ -646,6 +751,18 @@ cudaError_t lb32_prepare() {
   EK_ATTR(3)
   EK_ATTR(4)
 #undef EK_ATTR
+#define EK_ADV_ATTR(KK)                                                                   \
+  if (e == cudaSuccess)                                                                    \
+    e = cudaFuncSetAttribute(k_advect32<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                             (int)adv32_smem<KK>());                                       \
+  if (e == cudaSuccess)                                                                    \
+    e = cudaFuncSetAttribute(k_advect32_batch<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)adv32_smem<KK>());
+  EK_ADV_ATTR(1)
+  EK_ADV_ATTR(2)
+  EK_ADV_ATTR(3)
+  EK_ADV_ATTR(4)
+#undef EK_ADV_ATTR
   return e;
 }
 
@@ -686,10 +803,10 @@ cudaError_t launch_advection32(const LBArgs& a, cudaStream_t s) {
   const Phys32 c = make_phys32(a.ph);
   switch (a.ph.K) {
     case 0: return cudaSuccess;
-    case 1: k_advect32<1><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
-    case 2: k_advect32<2><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
-    case 3: k_advect32<3><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
-    case 4: k_advect32<4><<<lattice_grid(a.g), lattice_block(), 0, s>>>(a, c); break;
+    case 1: k_advect32<1><<<lattice_grid32(a.g, adv32_segments(a.g)), lattice_block(), adv32_smem<1>(), s>>>(a, c); break;
+    case 2: k_advect32<2><<<lattice_grid32(a.g, adv32_segments(a.g)), lattice_block(), adv32_smem<2>(), s>>>(a, c); break;
+    case 3: k_advect32<3><<<lattice_grid32(a.g, adv32_segments(a.g)), lattice_block(), adv32_smem<3>(), s>>>(a, c); break;
+    case 4: k_advect32<4><<<lattice_grid32(a.g, adv32_segments(a.g)), lattice_block(), adv32_smem<4>(), s>>>(a, c); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -702,7 +819,7 @@ void lb32_batch_grid(const LBArgs& a, int& gx, int& gy) {
 }
 
 void advect32_batch_grid(const LBArgs& a, int& gx, int& gy) {
-  const dim3 g = lattice_grid(a.g);
+  const dim3 g = lattice_grid32(a.g, adv32_segments(a.g));
   gx = (int)g.x;
   gy = (int)(g.y * g.z);
 }
@@ -731,10 +848,10 @@ cudaError_t launch_advection32_batch(const BatchLaunch<LBBatchEntry>& L, int K, 
   if (L.ctas == 0) return cudaSuccess;
   switch (K) {
     case 0: return cudaSuccess;
-    case 1: k_advect32_batch<1><<<L.ctas, lattice_block(), 0, s>>>(L.tab, L.slot, L.nsys); break;
-    case 2: k_advect32_batch<2><<<L.ctas, lattice_block(), 0, s>>>(L.tab, L.slot, L.nsys); break;
-    case 3: k_advect32_batch<3><<<L.ctas, lattice_block(), 0, s>>>(L.tab, L.slot, L.nsys); break;
-    case 4: k_advect32_batch<4><<<L.ctas, lattice_block(), 0, s>>>(L.tab, L.slot, L.nsys); break;
+    case 1: k_advect32_batch<1><<<L.ctas, lattice_block(), adv32_smem<1>(), s>>>(L.tab, L.slot, L.nsys); break;
+    case 2: k_advect32_batch<2><<<L.ctas, lattice_block(), adv32_smem<2>(), s>>>(L.tab, L.slot, L.nsys); break;
+    case 3: k_advect32_batch<3><<<L.ctas, lattice_block(), adv32_smem<3>(), s>>>(L.tab, L.slot, L.nsys); break;
+    case 4: k_advect32_batch<4><<<L.ctas, lattice_block(), adv32_smem<4>(), s>>>(L.tab, L.slot, L.nsys); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
