@@ -75,7 +75,10 @@ struct ek_ctx {
   Transfer* xfer = nullptr;
   int* xfer_count = nullptr;
   int* ticket = nullptr;
-  int* pticket = nullptr;   // Pcap: force blocks done per particle
+  int* pticket = nullptr;   // Pcap: force (or transition) blocks done per particle
+  double* tpart = nullptr;  // S5 transition momentum per CTA, 3 * tcap
+  size_t tcap = 0;          // (particle, CTA) rows allocated in tpart
+  int uchunks = 0;          // CTAs per particle over the union box (in use)
   ek_particle* pstage = nullptr;  // Pcap records for ek_get_particles_async
   int xfer_cap = 0;
   int* status = nullptr;
@@ -226,6 +229,8 @@ PartArgs part_args(ek_ctx* ctx) {
   a.surf_count = ctx->surf_count;
   a.ticket = ctx->ticket;
   a.pticket = ctx->pticket;
+  a.tpart = ctx->tpart;
+  a.uchunks = ctx->uchunks;
   a.surf_cap = (int)std::min<size_t>(ctx->psibox_cap, (size_t)1 << 30);
   a.tie_list = ctx->tie_list;
   a.tie_count = ctx->tie_count;
@@ -331,6 +336,15 @@ ek_status run_setup(ek_ctx* ctx) {
     ctx->psibox_cap = cap;
     ctx->fchunks = fchunks;
   }
+  const int uchunks = ctx->P ? union_chunks(boxmax) : 0;
+  if (ctx->P && (size_t)ctx->Pcap * uchunks > ctx->tcap) {
+    if (ctx->tpart) cudaFree(ctx->tpart);
+    ctx->tpart = nullptr;
+    ctx->tcap = 0;
+    EK_CUDA(cudaMalloc(&ctx->tpart, (size_t)ctx->Pcap * uchunks * 3 * sizeof(double)));
+    ctx->tcap = (size_t)ctx->Pcap * uchunks;
+  }
+  ctx->uchunks = uchunks;
   ctx->fcells = fcells;
   ctx->boxmax = boxmax;
   ctx->emax = emax;
@@ -793,7 +807,7 @@ ek_status ek_destroy(ek_ctx* ctx) {
                   ctx->spectrum, ctx->dparts, ctx->psibox, ctx->fpart, ctx->surf, ctx->xfer,
                   ctx->xfer_count, ctx->surf_count, ctx->status, ctx->ifield, ctx->ipart,
                   ctx->fkey, ctx->psum, ctx->vsig, ctx->ticket, ctx->pticket, ctx->pstage,
-                  ctx->tie_list, ctx->tie_count};
+                  ctx->tie_list, ctx->tie_count, ctx->tpart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   poisson_plan_destroy(ctx->plan);

@@ -396,7 +396,9 @@ struct PartArgs {
   int* surf_count;
   int surf_cap;
   int* ticket;     // particles whose S4 sums are done (reset by the last)
-  int* pticket;    // P: S4 force blocks of the particle done (reset by the last)
+  int* pticket;    // P: S4 force (or S5 transition) blocks of the particle done (reset by the last)
+  int uchunks;     // CTAs per particle over its union box (S5 clear and transitions)
+  double* tpart;   // P * uchunks * 3: per-CTA sums of the transitions' momentum
   int* status;
 };
 // cells per CTA of the S4 force kernel: FORCE_T threads, each over `fcells /
@@ -416,6 +418,8 @@ constexpr int FPART = 24;
 // integration (after S2), which also clear the assignment keys
 constexpr int S4_ASSIGN = 1, S4_FORCES = 2, S4_ALL = 3;
 cudaError_t launch_particle_forces(const PartArgs& a, cudaStream_t s, int parts = S4_ALL);
+// CTAs per particle that cover its union box (previous and current box)
+int union_chunks(int boxmax);
 // S5; parts: 1 = re-flag, Psi and charge (no species access), 2 = transitions
 // (species after S3), 3 = both
 cudaError_t launch_reflag(const PartArgs& a, bool transitions, cudaStream_t s, int parts = 3);

@@ -1323,73 +1323,43 @@ __device__ __forceinline__ void transitions_body(const PartArgs& a, const Blk bk
   const int p = bk.x;
   DevParticle& P = a.parts[p];
   const int c = bk.y * blockDim.x + threadIdx.x;
-  if (c >= box_cells(P.ulo, P.uhi)) return;
-  int X, Y, Z;
-  box_coord(c, P.ulo, P.uhi, X, Y, Z);
   const Grid g = a.g;
   const long long N = g.N;
-  const long long n = node_of(X, Y, Z, g);
-  const int old = a.owner_prev[n], nw = a.owner[n];
-  const bool covered = old == FLUID && nw == p;
-  const bool uncovered = old == p && nw == FLUID;
-  if (!covered && !uncovered) return;
-  const int K = a.ph.K;
   const double rho0 = a.ph.rho0;
   pop_t* f = (pop_t*)a.f;
-  const spc_t* rho = (const spc_t*)a.rho;
+  int X = 0, Y = 0, Z = 0;
+  long long n = 0;
+  bool covered = false, uncovered = false;
+  if (c < box_cells(P.ulo, P.uhi)) {
+    box_coord(c, P.ulo, P.uhi, X, Y, Z);
+    n = node_of(X, Y, Z, g);
+    const int old = a.owner_prev[n], nw = a.owner[n];
+    covered = old == FLUID && nw == p;
+    uncovered = old == p && nw == FLUID;
+  }
   long long rec[Q];
   int nf = 0;
+  // momentum the particle receives from this node: that of the destroyed
+  // fluid, or minus that of the created fluid
+  double mom[3] = {0.0, 0.0, 0.0};
+  if (covered || uncovered) {
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const long long m = node_of(X + dcx(i), Y + dcy(i), Z + dcz(i), g);
-    if (steady_fluid(a, m)) rec[nf++] = m;
+    for (int i = 1; i < Q; ++i) {
+      const long long m = node_of(X + dcx(i), Y + dcy(i), Z + dcz(i), g);
+      if (steady_fluid(a, m)) rec[nf++] = m;
+    }
   }
   if (covered) {
     // destroyed fluid: its momentum goes to the particle
-    double mx = 0.0, my = 0.0, mz = 0.0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double fi = pop_abs<FM>(f, i, N, n, rho0);
-      if (dcx(i)) mx += csgn(dcx(i), fi);
-      if (dcy(i)) my += csgn(dcy(i), fi);
-      if (dcz(i)) mz += csgn(dcz(i), fi);
+      if (dcx(i)) mom[0] += csgn(dcx(i), fi);
+      if (dcy(i)) mom[1] += csgn(dcy(i), fi);
+      if (dcz(i)) mom[2] += csgn(dcz(i), fi);
       f[(long long)i * N + n] = FM::fp32 ? (pop_t)(-wgt(i) * rho0) : (pop_t)0;
     }
-    atomicAdd(&P.ftrans[0], mx);
-    atomicAdd(&P.ftrans[1], my);
-    atomicAdd(&P.ftrans[2], mz);
-    if (nf == 0) {
-      atomicOr(a.status, ST_EXPEL);
-      return;
-    }
-    if (K == 0) return;
-    const int slot = atomicAdd(a.xfer_count, 1 + nf);
-    if (slot + 1 + nf > a.xfer_cap) {
-      atomicOr(a.status, ST_CAPACITY);
-      return;
-    }
-    Transfer self;
-    self.node = n;
-    for (int k = 0; k < EK_MAX_SPECIES; ++k) self.amount[k] = k < K ? -(double)rho[k * N + n] : 0.0;
-    a.xfer[slot] = self;
-    for (int j = 0; j < nf; ++j) {
-      Transfer t;
-      t.node = rec[j];
-      for (int k = 0; k < EK_MAX_SPECIES; ++k) {
-        if (k >= K) {
-          t.amount[k] = 0.0;
-        } else if (FM::fp32) {
-          const int r = (int)rho[k * N + n];
-          const int share = r / nf, rem = r - share * nf;  // rem has the sign of r
-          const int extra = (j < (rem < 0 ? -rem : rem)) ? (rem < 0 ? -1 : 1) : 0;
-          t.amount[k] = (double)(share + extra);
-        } else {
-          t.amount[k] = (double)rho[k * N + n] / (double)nf;
-        }
-      }
-      a.xfer[slot + 1 + j] = t;
-    }
-  } else {
+  } else if (uncovered) {
     // created fluid: f^eq(mean neighbour density, v_b), momentum taken from the particle
     double rbar = rho0;
     if (nf > 0) {
@@ -1424,32 +1394,105 @@ __device__ __forceinline__ void transitions_body(const PartArgs& a, const Blk bk
       if (dcy(i)) my += csgn(dcy(i), fi);
       if (dcz(i)) mz += csgn(dcz(i), fi);
     }
-    atomicAdd(&P.ftrans[0], -mx);
-    atomicAdd(&P.ftrans[1], -my);
-    atomicAdd(&P.ftrans[2], -mz);
-    if ((a.ph.flags & EK_VACATE_ZERO) || nf == 0 || K == 0) return;
-    // refill, Eqs. 17-18: each neighbour gives rho/(N_f + 1)
-    const int slot = atomicAdd(a.xfer_count, 2 * nf);
-    if (slot + 2 * nf > a.xfer_cap) {
+    mom[0] = -mx;
+    mom[1] = -my;
+    mom[2] = -mz;
+  }
+  // the particle's transition momentum, summed in a fixed order: the CTA's
+  // nodes in a fixed tree, then the CTAs' sums in chunk order by the
+  // particle's last CTA, added to the momentum the next integration applies
+  {
+    __shared__ double tr[3][PT];
+    __shared__ double quarter[3][4];
+    __shared__ bool last;
+    const int t = threadIdx.x;
+    tr[0][t] = mom[0];
+    tr[1][t] = mom[1];
+    tr[2][t] = mom[2];
+    __syncthreads();
+    if (t < 12) {
+      const int d = t >> 2, w = t & 3;
+      double sq = 0.0;
+      for (int i = w; i < PT; i += 4) sq += tr[d][i];
+      quarter[d][w] = sq;
+    }
+    __syncthreads();
+    if (t < 3)
+      a.tpart[((long long)p * a.uchunks + bk.y) * 3 + t] =
+          ((quarter[t][0] + quarter[t][1]) + quarter[t][2]) + quarter[t][3];
+    __threadfence();
+    __syncthreads();
+    if (t == 0) last = atomicAdd(a.pticket + p, 1) == a.uchunks - 1;
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      if (t < 3) {
+        double sum = 0.0;
+        for (int j = 0; j < a.uchunks; ++j) sum += __ldcg(a.tpart + ((long long)p * a.uchunks + j) * 3 + t);
+        P.ftrans[t] += sum;
+      }
+      if (t == 0) a.pticket[p] = 0;
+    }
+  }
+  if (!covered && !uncovered) return;
+  const int K = a.ph.K;
+  const spc_t* rho = (const spc_t*)a.rho;
+  if (covered) {
+    if (nf == 0) {
+      atomicOr(a.status, ST_EXPEL);
+      return;
+    }
+    if (K == 0) return;
+    const int slot = atomicAdd(a.xfer_count, 1 + nf);
+    if (slot + 1 + nf > a.xfer_cap) {
       atomicOr(a.status, ST_CAPACITY);
       return;
     }
+    Transfer self;
+    self.node = n;
+    for (int k = 0; k < EK_MAX_SPECIES; ++k) self.amount[k] = k < K ? -(double)rho[k * N + n] : 0.0;
+    a.xfer[slot] = self;
     for (int j = 0; j < nf; ++j) {
-      Transfer give, take;
-      give.node = rec[j];
-      take.node = n;
+      Transfer tr;
+      tr.node = rec[j];
       for (int k = 0; k < EK_MAX_SPECIES; ++k) {
-        double sh = 0.0;
-        if (k < K) {
-          if (FM::fp32) sh = (double)((int)rho[k * N + rec[j]] / (nf + 1));
-          else sh = (double)rho[k * N + rec[j]] / (double)(nf + 1);
+        if (k >= K) {
+          tr.amount[k] = 0.0;
+        } else if (FM::fp32) {
+          const int r = (int)rho[k * N + n];
+          const int share = r / nf, rem = r - share * nf;  // rem has the sign of r
+          const int extra = (j < (rem < 0 ? -rem : rem)) ? (rem < 0 ? -1 : 1) : 0;
+          tr.amount[k] = (double)(share + extra);
+        } else {
+          tr.amount[k] = (double)rho[k * N + n] / (double)nf;
         }
-        give.amount[k] = -sh;
-        take.amount[k] = sh;
       }
-      a.xfer[slot + 2 * j] = give;
-      a.xfer[slot + 2 * j + 1] = take;
+      a.xfer[slot + 1 + j] = tr;
     }
+    return;
+  }
+  if ((a.ph.flags & EK_VACATE_ZERO) || nf == 0 || K == 0) return;
+  // refill, Eqs. 17-18: each neighbour gives rho/(N_f + 1)
+  const int slot = atomicAdd(a.xfer_count, 2 * nf);
+  if (slot + 2 * nf > a.xfer_cap) {
+    atomicOr(a.status, ST_CAPACITY);
+    return;
+  }
+  for (int j = 0; j < nf; ++j) {
+    Transfer give, take;
+    give.node = rec[j];
+    take.node = n;
+    for (int k = 0; k < EK_MAX_SPECIES; ++k) {
+      double sh = 0.0;
+      if (k < K) {
+        if (FM::fp32) sh = (double)((int)rho[k * N + rec[j]] / (nf + 1));
+        else sh = (double)rho[k * N + rec[j]] / (double)(nf + 1);
+      }
+      give.amount[k] = -sh;
+      take.amount[k] = sh;
+    }
+    a.xfer[slot + 2 * j] = give;
+    a.xfer[slot + 2 * j + 1] = take;
   }
 }
 
@@ -1489,8 +1532,7 @@ cudaError_t particle_forces_t(const PartArgs& a, cudaStream_t s, int parts) {
 template <class FM>
 cudaError_t reflag_t(const PartArgs& a, bool transitions, cudaStream_t s, int parts = 3) {
   const Grid& g = a.g;
-  const int edge = (int)round(cbrt((double)a.boxmax)) + 1;
-  const unsigned uchunks = (unsigned)((edge * edge * edge + PT - 1) / PT);
+  const unsigned uchunks = (unsigned)union_chunks(a.boxmax);
   if (!(parts & 1)) {
     if (a.P == 0 || !transitions) return cudaSuccess;
     // (k_save_prev of this step emptied the transfer list)
@@ -1643,12 +1685,17 @@ cudaError_t launch_particle_chain(const ChainArgs& A, int ctas, cudaStream_t s) 
   return cudaLaunchKernelEx(&cfg, k_particle_chain, A);
 }
 
+// union boxes are at most one cell wider per axis than a box of boxmax cells
+int union_chunks(int boxmax) {
+  const int edge = (int)round(cbrt((double)boxmax)) + 1;
+  return (edge * edge * edge + PT - 1) / PT;
+}
+
 void particle_batch_grid(int k, const PartArgs& a, int& gx, int& gy) {
   gx = a.P;
   gy = 1;
   if (a.P == 0) return;
-  const int edge = (int)round(cbrt((double)a.boxmax)) + 1;
-  const int uchunks = (edge * edge * edge + PT - 1) / PT;
+  const int uchunks = union_chunks(a.boxmax);
   const int bchunks = (a.boxmax + PT - 1) / PT;
   switch (k) {
     case PK_ASSIGN: gy = (a.emax + PT - 1) / PT; break;
