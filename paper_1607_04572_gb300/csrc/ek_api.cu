@@ -43,6 +43,7 @@ struct ek_ctx {
   int nipart = 0;
   int nipart_cap = 0;  // rows allocated for ipart (FP32: enough for 2-plane segments)
   int nzb = 1;       // FP32 S2: z segments per tile column
+  int advseg = 1;    // FP32 S3: z segments per tile column
   int overlap = 1;   // particle chain on the auxiliary stream (1) or in line (0)
   unsigned long long version = 0;  // bumped whenever captured steps go stale
   unsigned long long* fkey = nullptr;  // N: nearest-particle keys of S4
@@ -263,6 +264,7 @@ LBArgs lb_args(ek_ctx* ctx) {
   a.parts = ctx->dparts;
   a.status = ctx->status;
   a.nzb = ctx->nzb;
+  a.advseg = ctx->advseg;
   return a;
 }
 
@@ -736,6 +738,7 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   {
     // lattice-block partial sums of S2: one per block of its grid
     if (ctx->fp32) ctx->nzb = lb32_segments(g, p->nspecies, (p->flags & EK_PV) != 0);
+    if (ctx->fp32) ctx->advseg = adv32_segments(g, false);
     const dim3 lg = ctx->fp32 ? lattice_grid32(g, ctx->nzb) : lattice_grid(g);
     ctx->nipart = (int)(lg.x * lg.y * lg.z);
     // the FP32 segment length may be retuned down to 2 planes (ek_batch_tune)
@@ -1465,6 +1468,7 @@ ek_status fused_build(ek_batch* b, int key) {
                        c->has_qwall ? (const float*)c->qwall : nullptr, (const float*)c->qpart, c->ph,
                        (float*)c->phi, (float2*)c->spectrum);
     lbt[i].a = lb_args(c);
+    lbt[i].a.advseg = adv32_segments(c->g, true);  // one launch for all systems: wide
     lbt[i].c = make_phys32(c->ph);
     c->cur = 1 - c->cur;
     post[i] = part_args(c);

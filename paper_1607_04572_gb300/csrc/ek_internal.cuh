@@ -307,6 +307,7 @@ struct LBArgs {
   const DevParticle* parts;
   int* status;
   int nzb;         // FP32 S2: z segments per (x, y) tile column (lb32_segments)
+  int advseg;      // FP32 S3: z segments per tile column (adv32_segments)
 };
 // Constants of the FP32 kernels, rounded once on the host.
 struct Phys32 {
@@ -333,6 +334,10 @@ cudaError_t lb32_prepare();  // once per process, before the first launch_lb32
 int lb32_segments(const Grid& g, int K, bool pv);
 cudaError_t launch_lb32(const LBArgs& a, cudaStream_t s);
 cudaError_t launch_advection32(const LBArgs& a, cudaStream_t s);
+// z segments per tile column of the FP32 S3 grid: 16-plane segments where
+// the grid still has two waves of blocks (`wide`: the launch is shared with
+// other systems, so its size does not depend on this machine), else 8, else 4
+int adv32_segments(const Grid& g, bool wide);
 // the same S2 and S3 for the systems of a batch (all FP32 with the same K and
 // partial-volume choice), one launch each; the per-system grids (gx, gy) that
 // the ranges of L.slot must give

@@ -474,19 +474,45 @@ __device__ __forceinline__ int sgnf(float v) { return v > 0.0f ? 1 : (v < 0.0f ?
 // ---------------------------------------------------------------------------
 template <int K>
 struct AdvRing {
-  int sh[3][7][K][HP];       // shares by class (ox | oy << 1 | oz << 2) - 1
+  // shares by class (ox | oy << 1 | oz << 2) - 1; per class row the nodes'
+  // species 0 and 1 as pairs, then species 2 and 3 as pairs (K = 4) or
+  // single values (K = 3), so that a node's shares are one or two vector
+  // accesses
+  int sh[3][7][HP * K];
   unsigned char sg[3][HP];   // sign byte of S2: bit 7 fluid, sign codes of u
 };
+
+// the K shares of node e in a class row
+template <int K>
+__device__ __forceinline__ void share_get(const int* row, int e, int (&v)[K]) {
+  if constexpr (K == 1) {
+    v[0] = row[e];
+  } else {
+    const int2 w = reinterpret_cast<const int2*>(row)[e];
+    v[0] = w.x;
+    v[1] = w.y;
+    if constexpr (K == 3) v[2] = row[2 * HP + e];
+    if constexpr (K == 4) {
+      const int2 w2 = reinterpret_cast<const int2*>(row + 2 * HP)[e];
+      v[2] = w2.x;
+      v[3] = w2.y;
+    }
+  }
+}
+template <int K>
+__device__ __forceinline__ void share_put(int* row, int e, const int (&v)[K]) {
+  if constexpr (K == 1) {
+    row[e] = v[0];
+  } else {
+    reinterpret_cast<int2*>(row)[e] = make_int2(v[0], v[1]);
+    if constexpr (K == 3) row[2 * HP + e] = v[2];
+    if constexpr (K == 4) reinterpret_cast<int2*>(row + 2 * HP)[e] = make_int2(v[2], v[3]);
+  }
+}
 
 template <int K>
 constexpr size_t adv32_smem() { return sizeof(AdvRing<K>); }
 
-// planes per z segment of the tiled S3 grid
-constexpr int ADV_PLANES = 8;
-__host__ __device__ inline int adv32_segments(const Grid& g) {
-  const int s = (g.nz + ADV_PLANES - 1) / ADV_PLANES;
-  return s > 1 ? s : 1;
-}
 
 // the sign bytes, velocities and species of a source plane's halo-tile
 // nodes held by one thread (up to two nodes), loaded one plane ahead of use
@@ -548,9 +574,10 @@ __device__ __forceinline__ void adv_store(AdvRing<K>& t, int slot, const AdvSrc<
 #pragma unroll
     for (int o = 1; o < 8; ++o) {
       const float frac = vof_share(R.v[q][0], R.v[q][1], R.v[q][2], o & 1, (o >> 1) & 1, o >> 2);
+      int v[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k)
-        t.sh[slot][o - 1][k][e] = __float2int_rn(__fmul_rn((float)R.r[q][k], frac));
+      for (int k = 0; k < K; ++k) v[k] = __float2int_rn(__fmul_rn((float)R.r[q][k], frac));
+      share_put<K>(t.sh[slot][o - 1], e, v);
     }
   }
 }
@@ -608,8 +635,10 @@ __device__ __forceinline__ void advect32_block(const LBArgs& a, int bx, int by, 
         if ((ox && !sx) || (oy && !sy) || (oz && !sz)) continue;
         const int tc = c + (oy ? sy * HX : 0) + (ox ? sx : 0);
         if (!(t.sg[oz ? ts : s1][tc] & 0x80u)) continue;  // aimed at a boundary: stays here
+        int v[K];
+        share_get<K>(t.sh[s1][o - 1], c, v);
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] -= t.sh[s1][o - 1][k][c];
+        for (int k = 0; k < K; ++k) acc[k] -= v[k];
       }
       // shares of the neighbour at -q: fluid and moving towards this node
       // along every nonzero component of q
@@ -627,8 +656,10 @@ __device__ __forceinline__ void advect32_block(const LBArgs& a, int bx, int by, 
             const int sc = c - qy * HX - qx;
             if ((t.sg[ss][sc] & mask) != want) continue;
             const int cls = (qx ? 1 : 0) | (qy ? 2 : 0) | (qz ? 4 : 0);
+            int v[K];
+            share_get<K>(t.sh[ss][cls - 1], sc, v);
 #pragma unroll
-            for (int k = 0; k < K; ++k) acc[k] += t.sh[ss][cls - 1][k][sc];
+            for (int k = 0; k < K; ++k) acc[k] += v[k];
           }
         }
       }
@@ -642,7 +673,7 @@ __device__ __forceinline__ void advect32_block(const LBArgs& a, int bx, int by, 
 template <int K>
 __global__ void __launch_bounds__(256) k_advect32(LBArgs a, Phys32 c) {
   (void)c;
-  advect32_block<K>(a, blockIdx.x, blockIdx.y, blockIdx.z, (int)gridDim.z);
+  advect32_block<K>(a, blockIdx.x, blockIdx.y, blockIdx.z, a.advseg);
 }
 
 // S3 of a batch's systems in one launch (system s: its xt x (yt nseg) grid)
@@ -653,7 +684,7 @@ __global__ void __launch_bounds__(256) k_advect32_batch(const LBBatchEntry* __re
   const Blk b = batch_blk(slot, nsys, sys);
   const LBArgs& a = tab[sys].a;
   const int yt = (a.g.ny + TILE_Y - 1) / TILE_Y;
-  advect32_block<K>(a, b.x, b.y % yt, b.y / yt, adv32_segments(a.g));
+  advect32_block<K>(a, b.x, b.y % yt, b.y / yt, a.advseg);
 }
 
 __global__ void k_fill32(Grid g, const int* owner, float* f, int* rho, int K, float rho0, int n0,
@@ -803,10 +834,10 @@ cudaError_t launch_advection32(const LBArgs& a, cudaStream_t s) {
   const Phys32 c = make_phys32(a.ph);
   switch (a.ph.K) {
     case 0: return cudaSuccess;
-    case 1: k_advect32<1><<<lattice_grid32(a.g, adv32_segments(a.g)), lattice_block(), adv32_smem<1>(), s>>>(a, c); break;
-    case 2: k_advect32<2><<<lattice_grid32(a.g, adv32_segments(a.g)), lattice_block(), adv32_smem<2>(), s>>>(a, c); break;
-    case 3: k_advect32<3><<<lattice_grid32(a.g, adv32_segments(a.g)), lattice_block(), adv32_smem<3>(), s>>>(a, c); break;
-    case 4: k_advect32<4><<<lattice_grid32(a.g, adv32_segments(a.g)), lattice_block(), adv32_smem<4>(), s>>>(a, c); break;
+    case 1: k_advect32<1><<<lattice_grid32(a.g, a.advseg), lattice_block(), adv32_smem<1>(), s>>>(a, c); break;
+    case 2: k_advect32<2><<<lattice_grid32(a.g, a.advseg), lattice_block(), adv32_smem<2>(), s>>>(a, c); break;
+    case 3: k_advect32<3><<<lattice_grid32(a.g, a.advseg), lattice_block(), adv32_smem<3>(), s>>>(a, c); break;
+    case 4: k_advect32<4><<<lattice_grid32(a.g, a.advseg), lattice_block(), adv32_smem<4>(), s>>>(a, c); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -818,8 +849,20 @@ void lb32_batch_grid(const LBArgs& a, int& gx, int& gy) {
   gy = (int)(g.y * g.z);
 }
 
+int adv32_segments(const Grid& g, bool wide) {
+  const long long cols = (long long)((g.nx + TILE_X - 1) / TILE_X) * ((g.ny + TILE_Y - 1) / TILE_Y);
+  int planes = 4;
+  for (int p : {16, 8}) {
+    if (wide || cols * ((g.nz + p - 1) / p) >= 2 * 152 * 3) {
+      planes = p;
+      break;
+    }
+  }
+  return std::max(1, (g.nz + planes - 1) / planes);
+}
+
 void advect32_batch_grid(const LBArgs& a, int& gx, int& gy) {
-  const dim3 g = lattice_grid32(a.g, adv32_segments(a.g));
+  const dim3 g = lattice_grid32(a.g, a.advseg);
   gx = (int)g.x;
   gy = (int)(g.y * g.z);
 }

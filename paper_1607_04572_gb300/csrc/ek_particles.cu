@@ -1406,20 +1406,24 @@ __device__ __forceinline__ void transitions_body(const PartArgs& a, const Blk bk
     __shared__ double quarter[3][4];
     __shared__ bool last;
     const int t = threadIdx.x;
-    tr[0][t] = mom[0];
-    tr[1][t] = mom[1];
-    tr[2][t] = mom[2];
-    __syncthreads();
-    if (t < 12) {
-      const int d = t >> 2, w = t & 3;
-      double sq = 0.0;
-      for (int i = w; i < PT; i += 4) sq += tr[d][i];
-      quarter[d][w] = sq;
+    if (__syncthreads_or(covered || uncovered)) {
+      tr[0][t] = mom[0];
+      tr[1][t] = mom[1];
+      tr[2][t] = mom[2];
+      __syncthreads();
+      if (t < 12) {
+        const int d = t >> 2, w = t & 3;
+        double sq = 0.0;
+        for (int i = w; i < PT; i += 4) sq += tr[d][i];
+        quarter[d][w] = sq;
+      }
+      __syncthreads();
+      if (t < 3)
+        a.tpart[((long long)p * a.uchunks + bk.y) * 3 + t] =
+            ((quarter[t][0] + quarter[t][1]) + quarter[t][2]) + quarter[t][3];
+    } else if (t < 3) {
+      a.tpart[((long long)p * a.uchunks + bk.y) * 3 + t] = 0.0;  // no transition in this CTA
     }
-    __syncthreads();
-    if (t < 3)
-      a.tpart[((long long)p * a.uchunks + bk.y) * 3 + t] =
-          ((quarter[t][0] + quarter[t][1]) + quarter[t][2]) + quarter[t][3];
     __threadfence();
     __syncthreads();
     if (t == 0) last = atomicAdd(a.pticket + p, 1) == a.uchunks - 1;
