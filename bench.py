@@ -442,6 +442,11 @@ def main():
     ap.add_argument("--workload", default=HEADLINE, choices=["large", "many", "single", "small"],
                     help="the measured workload (the headline is the large box; the others are "
                          "for profiling smaller cases)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only the batched ensemble (its line; for profiling the batched step)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batched ensemble: the fused form with 8-plane S2 segments and the "
+                         "particle chain beside S3 instead of the autotuner's choice")
     args = ap.parse_args()
     import workloads
     w = workloads.workload(args.workload)
@@ -476,6 +481,12 @@ def main():
 
     peaks, peak_kind = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs"))
+    if args.batch_only:
+        rb = measure_batch(ek, torch, args, barrier, max_over_ranks)
+        rb["step_roofline"] = step_roofline(rb["value"], step_bytes_per_node(True, 2), hbm_peak)
+        if rank == 0:
+            print(json.dumps({"metric": "MLUPS of the batched ensemble", **rb}), flush=True)
+        return 0
 
     # ---- the headline: the large box, FP32-storage form -----------------------
     r = measure(ek, torch, w, True, args, stream, barrier, max_over_ranks, ws, stage_steps=10)
@@ -609,7 +620,11 @@ def measure_batch(ek, torch, args, barrier, max_over_ranks):
     stream = torch.cuda.Stream()
     b = ek.EKBatch(systems)
     b.set_stream(stream)
-    cfg, tuned_ms = b.tune(2)
+    if getattr(args, "no_tune", False):
+        b.set_config(fused=1, planes_per_block=8, particle_chain_beside_s3=1)
+        cfg, tuned_ms = b.config(), 0.0
+    else:
+        cfg, tuned_ms = b.tune(2)
     b.step(2)
     steps = max(3, min(args.steps, 20))
     barrier()
