@@ -359,6 +359,11 @@ ek_status ek_batch_config(const ek_batch* b, int cfg[4]);
  * waits for the batch's earlier work.  EK_ERR_ARG for a value out of range or
  * a fused form on a batch that does not allow it. */
 ek_status ek_batch_set_config(ek_batch* b, const int cfg[4]);
+/* Failure-detection test hook: the n-th device allocation of a field that
+ * ek_create makes from now on (counting across calls) fails as if the device
+ * were out of memory, so that ek_create frees what it allocated and returns
+ * EK_ERR_NOMEM; n <= 0 clears the hook.  Process-wide; for tests. */
+void ek_debug_fail_alloc(int n);
 /* Failure-detection test hook for form 2: in the steps captured from now on,
  * CTA leave_cta of each persistent particle-chain launch returns before the
  * first grid barrier (-1: none), and a wait at a barrier gives up after

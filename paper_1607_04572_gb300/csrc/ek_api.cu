@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <new>
@@ -14,6 +15,19 @@
 #include "ek_internal.cuh"
 
 using namespace ek;
+
+namespace {
+// ek_debug_fail_alloc: the n-th field allocation of ek_create from now on
+// fails (0: none)
+std::atomic<int> g_alloc_fault{0};
+bool alloc_fault_due() {
+  int n = g_alloc_fault.load();
+  while (n > 0) {
+    if (g_alloc_fault.compare_exchange_weak(n, n - 1)) return n == 1;
+  }
+  return false;
+}
+}  // namespace
 
 struct ek_ctx {
   ek_params p;
@@ -721,6 +735,7 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   }
   bool ok = true;
   auto alloc = [&](void** ptr, size_t bytes) {
+    if (ok && alloc_fault_due()) ok = false;  // the test hook's injected failure
     if (ok && cudaMalloc(ptr, bytes) != cudaSuccess) ok = false;
   };
   const size_t rsz = ctx->rsz;  // populations, Phi, Psi, charges and u share the real size
@@ -800,6 +815,8 @@ ek_status ek_create(const ek_params* p, ek_ctx** out) {
   *out = ctx;
   return EK_OK;
 }
+
+void ek_debug_fail_alloc(int n) { g_alloc_fault.store(n > 0 ? n : 0); }
 
 ek_status ek_destroy(ek_ctx* ctx) {
   if (!ctx) return EK_ERR_ARG;

@@ -478,9 +478,9 @@ __device__ void block_sum_t(const double (&v)[NV], const bool (&group_on)[NV / 6
 // Block (p, b) takes the rows b, b + nb, b + 2 nb, ... of FORCE_T cells of the
 // widened box (nb blocks for this particle), so the cells next to the sphere
 // are spread over all blocks.
-// FP32 form: the per-thread float sums are added within each warp in float
-// (fixed shuffle tree), the FORCE_T / 32 warp sums in FP64 in order.  Result
-// in out[j] for threadIdx.x == j < NV.
+// FP32 form: each thread's float sums over its own few cells are widened to
+// FP64 and added within the warp by a fixed shuffle tree, then the FORCE_T / 32
+// warp sums in FP64 in order.  Result in out[j] for threadIdx.x == j < NV.
 template <int NV>
 __device__ void block_sum_f(const float (&v)[NV], const bool (&group_on)[NV / 6], double* out) {
   __shared__ double wsum[FORCE_T / 32][NV];
@@ -488,10 +488,10 @@ __device__ void block_sum_f(const float (&v)[NV], const bool (&group_on)[NV / 6]
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     if (!group_on[j / 6]) continue;
-    float x = v[j];
+    double x = (double)v[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) wsum[warp][j] = (double)x;
+    if (lane == 0) wsum[warp][j] = x;
   }
   __syncthreads();
   if (threadIdx.x < NV) {

@@ -52,7 +52,7 @@ EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get
            "ek_poisson_solve_mg",
            "ek_batch_create", "ek_batch_destroy", "ek_batch_set_stream", "ek_batch_step_async",
            "ek_batch_step", "ek_batch_sync", "ek_batch_tune", "ek_batch_config", "ek_batch_set_config",
-           "ek_batch_wait_test", "ek_batch_size",
+           "ek_batch_wait_test", "ek_batch_size", "ek_debug_fail_alloc",
            "ek_batch_last_error"]
 
 
@@ -135,6 +135,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ek_batch_config.argtypes = [vp, ctypes.POINTER(ip)]
     lib.ek_batch_set_config.argtypes = [vp, ctypes.POINTER(ip)]
     lib.ek_batch_wait_test.argtypes = [vp, ip, dp]
+    lib.ek_debug_fail_alloc.argtypes = [ip]
+    lib.ek_debug_fail_alloc.restype = None
     lib.ek_batch_size.argtypes = [vp]
     lib.ek_batch_size.restype = ip
     lib.ek_batch_last_error.argtypes = [vp]
@@ -142,11 +144,17 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     for name in EXPORTS:
         if name not in ("ek_num_particles", "ek_last_error", "ek_lattice_dirs",
                         "ek_poisson_scratch_bytes", "ek_kernel_launches", "ek_batch_size",
-                        "ek_poisson_mg_scratch_bytes",
+                        "ek_poisson_mg_scratch_bytes", "ek_debug_fail_alloc",
                         "ek_batch_last_error"):
             getattr(lib, name).restype = ip
     _lib = lib
     return lib
+
+
+def debug_fail_alloc(n: int) -> None:
+    """Test hook: the n-th field allocation of ek_create from now on fails (see
+    ek_debug_fail_alloc in include/ek.h); n <= 0 clears it."""
+    load_library().ek_debug_fail_alloc(int(n))
 
 
 def lattice_dirs() -> np.ndarray:

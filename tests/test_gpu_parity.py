@@ -232,3 +232,38 @@ def test_particle_crosses_periodic_boundary(gpu_lib):
     assert o.particles[0].pos[0] > 8.0  # wrapped to the far side
     tot = np.array([s.get_fields(ek.FIELD_SPECIES, k).sum() for k in range(o.K)])
     assert np.allclose(tot, N0, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("flags", [0, 16])
+def test_nonfinite_state_is_reported_not_propagated_silently(gpu_lib, flags):
+    """A NaN written into the populations of one node (host fault injection)
+    makes the next step return EK_ERR_UNSTABLE; the context then refuses
+    further steps instead of running on."""
+    ek = gpu_lib
+    s = ek.EKSystem((16, 16, 16), flags=flags)
+    s.step(2)
+    f = s.get_fields(ek.FIELD_POPULATIONS)
+    f = np.array(f, dtype=np.float64)
+    f.reshape(19, -1)[3, 1234] = np.nan
+    s.set_field(ek.FIELD_POPULATIONS, f.ravel())
+    with pytest.raises(ek.EKError) as e:
+        s.step(1)
+    assert e.value.code == -4  # EK_ERR_UNSTABLE
+    with pytest.raises(ek.EKError):
+        s.step(1)
+    s.close()
+
+
+def test_allocation_failure_is_reported_and_cleaned_up(gpu_lib):
+    """The allocation-failure hook: the fifth field allocation of the next
+    ek_create fails; ek_create returns EK_ERR_NOMEM after freeing the rest,
+    and the next ek_create succeeds."""
+    ek = gpu_lib
+    ek.debug_fail_alloc(5)
+    with pytest.raises(ek.EKError) as e:
+        ek.EKSystem((32, 32, 32), flags=16)
+    assert e.value.code == -2  # EK_ERR_NOMEM
+    s = ek.EKSystem((32, 32, 32), flags=16)
+    s.step(2)
+    s.close()
+    ek.debug_fail_alloc(0)
