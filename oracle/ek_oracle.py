@@ -184,6 +184,62 @@ def poisson(q, bjerrum):
     return np.fft.ifftn(ph).real
 
 
+def poisson_dielectric(q, bjerrum, eps=None, fixed=None, phi_fixed=None):
+    """Eq. (3) with an inhomogeneous permittivity and fixed-potential nodes,
+    the problem the paper leaves to iterative solvers (Sec. III.C, the
+    paragraph after Eq. 16): div(eps grad Phi) = -4 pi l_B q, eps the
+    permittivity relative to the solvent's (whose Bjerrum length is l_B).
+
+    Reading: the 7-point discretisation of the periodic solve with face
+    permittivities, the harmonic mean 2 eps_i eps_j / (eps_i + eps_j) of the
+    two nodes of a face (it keeps the flux eps grad Phi continuous across a
+    jump).  A free node i satisfies sum_f eps_f (Phi_i - Phi_j) = 4 pi l_B q_i
+    over its six faces; a node with fixed[i] holds Phi = phi_fixed[i]
+    (Dirichlet).  Without fixed nodes the charge's mean is removed and Phi has
+    mean 0, as in ``poisson``.  Arrays [z, y, x]; eps, fixed, phi_fixed may be
+    None (eps = 1, no fixed node).  scipy's sparse direct solver is the
+    library primitive.
+    """
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    shape = q.shape
+    n = q.size
+    e = np.ones(shape) if eps is None else np.asarray(eps, dtype=np.float64)
+    fx = np.zeros(shape, dtype=bool) if fixed is None else np.asarray(fixed, dtype=bool)
+    pf = np.zeros(shape) if phi_fixed is None else np.asarray(phi_fixed, dtype=np.float64)
+    idx = np.arange(n).reshape(shape)
+    rows, cols, vals = [], [], []
+    diag = np.zeros(n)
+    for axis in range(3):
+        j = np.roll(idx, -1, axis=axis)            # the node across the face on the + side
+        ej = np.roll(e, -1, axis=axis)
+        ef = (2.0 * e * ej / (e + ej)).ravel()     # face permittivity
+        i_, j_ = idx.ravel(), j.ravel()
+        diag[i_] += ef
+        diag[j_] += ef
+        rows += [i_, j_]
+        cols += [j_, i_]
+        vals += [-ef, -ef]
+    A = sp.csr_matrix((np.concatenate(vals + [diag]),
+                       (np.concatenate(rows + [np.arange(n)]), np.concatenate(cols + [np.arange(n)]))),
+                      shape=(n, n))
+    b = 4.0 * np.pi * bjerrum * q.ravel().astype(np.float64)
+    free = ~fx.ravel()
+    phi = np.where(fx.ravel(), pf.ravel(), 0.0)
+    if not fx.any():
+        # singular (constants): remove the mean charge, hold node 0 at 0,
+        # then shift to mean 0
+        b = b - b.mean()
+        keep = np.arange(1, n)
+        sol = spl.spsolve(A[keep][:, keep].tocsc(), b[keep])
+        phi = np.concatenate([[0.0], sol])
+        return (phi - phi.mean()).reshape(shape)
+    Aff = A[free][:, free].tocsc()
+    rhs = b[free] - A[free][:, ~free] @ phi[~free]
+    phi[free] = spl.spsolve(Aff, rhs)
+    return phi.reshape(shape)
+
+
 # ---------------------------------------------------------------------------
 # Partial volumes Psi by octree subdivision (Sec. III.D.2)
 # ---------------------------------------------------------------------------
