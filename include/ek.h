@@ -266,6 +266,40 @@ ek_status ek_poisson_solve_mg(const double* q, double* phi, int nx, int ny, int 
                               double bjerrum, double tol, int max_cycles, void* scratch,
                               void* stream, int* cycles, double* residual);
 
+/* Poisson solve with an inhomogeneous permittivity and fixed-potential nodes:
+ * the problem the paper leaves to iterative solvers such as Krylov subspace
+ * methods, which also handle inhomogeneous dielectric coefficients (Sec.
+ * III.C, the paragraph after Eq. 16).  Solves div(eps grad Phi) = -4 pi l_B q
+ * on the periodic nx x ny x nz box, eps the permittivity relative to the
+ * solvent whose Bjerrum length is l_B: the 7-point operator of
+ * ek_poisson_solve with face permittivities, the harmonic mean
+ * 2 eps_i eps_j / (eps_i + eps_j) of the face's two nodes; a free node
+ * satisfies sum_f eps_f (Phi_i - Phi_j) = 4 pi l_B q_i over its six faces, a
+ * node with fixed[i] != 0 holds Phi = phi_fixed[i] (walls, electrodes).
+ * Without fixed nodes the mean charge is removed and phi is returned with
+ * mean 0 (then with eps = 1 the result is ek_poisson_solve's).  Method:
+ * Jacobi-preconditioned conjugate gradients in FP64 from Phi = 0 on the free
+ * nodes, until ||r||_2 <= tol ||b||_2 over the free nodes (checked every 10
+ * iterations) or max_iter iterations; every inner product is a fixed-order
+ * sum, so a solve is bit-reproducible.
+ *
+ * All arrays are device arrays of nx*ny*nz values, index x + nx*(y + ny*z):
+ * q, phi (double; may alias), eps (double, positive and finite; NULL: 1
+ * everywhere), fixed (unsigned char; NULL: none), phi_fixed (double; NULL:
+ * 0; may alias phi).  scratch: caller-allocated device memory of at least
+ * ek_poisson_cg_scratch_bytes(nx, ny, nz) bytes.  stream: a cudaStream_t or
+ * NULL.  *iters and *residual (||r|| / ||b||), when not NULL, receive the
+ * iterations run and the final relative residual (a residual above tol means
+ * max_iter ran out).  Waits for the work.  Any edge >= 1 (nx*ny*nz < 2^31).
+ * Errors: EK_ERR_ARG (null q, phi or scratch, bad sizes, tol <= 0,
+ * max_iter < 1, a permittivity that is not positive and finite), EK_ERR_CUDA.
+ * ek_poisson_cg_scratch_bytes returns 0 for bad sizes. */
+size_t ek_poisson_cg_scratch_bytes(int nx, int ny, int nz);
+ek_status ek_poisson_solve_cg(const double* q, const double* eps, const unsigned char* fixed,
+                              const double* phi_fixed, double* phi, int nx, int ny, int nz,
+                              double bjerrum, double tol, int max_iter, void* scratch, void* stream,
+                              int* iters, double* residual);
+
 /* The same Poisson solve for callers that cannot allocate device memory:
  * code whose device memory is entirely reserved up front by another runtime's
  * pool (so a raw cudaMalloc would fail), latency-critical loops that must not

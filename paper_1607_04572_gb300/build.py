@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libek.so")
 SOURCES = ["ek_api.cu", "ek_lattice.cu", "ek_lattice32.cu", "ek_poisson.cu", "ek_particles.cu",
-           "ek_poisson_static.cu", "ek_multigrid.cu"]
+           "ek_poisson_static.cu", "ek_multigrid.cu", "ek_krylov.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

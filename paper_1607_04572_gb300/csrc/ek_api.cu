@@ -1322,6 +1322,25 @@ ek_status ek_poisson_solve_mg(const double* q, double* phi, int nx, int ny, int 
   return EK_OK;
 }
 
+size_t ek_poisson_cg_scratch_bytes(int nx, int ny, int nz) {
+  if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz >= (1LL << 31)) return 0;
+  return poisson_cg_scratch_bytes(nx, ny, nz);
+}
+
+ek_status ek_poisson_solve_cg(const double* q, const double* eps, const unsigned char* fixed,
+                              const double* phi_fixed, double* phi, int nx, int ny, int nz,
+                              double bjerrum, double tol, int max_iter, void* scratch, void* stream,
+                              int* iters, double* residual) {
+  if (!q || !phi || !scratch || nx < 1 || ny < 1 || nz < 1 ||
+      (long long)nx * ny * nz >= (1LL << 31) || !(bjerrum >= 0.0) || !(tol > 0.0) || max_iter < 1)
+    return EK_ERR_ARG;
+  bool bad = false;
+  if (poisson_solve_cg(q, eps, fixed, phi_fixed, phi, nx, ny, nz, bjerrum, tol, max_iter, scratch,
+                       (cudaStream_t)stream, iters, residual, &bad) != cudaSuccess)
+    return EK_ERR_CUDA;
+  return bad ? EK_ERR_ARG : EK_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -274,6 +274,14 @@ cudaError_t poisson_solve_f32(const PoissonPlan& p, const int* rho, const float*
                               cudaStream_t s);
 cudaError_t charge_density(const Grid& g, const Phys& ph, const void* rho, const void* qwall,
                            const void* qpart, double* q, cudaStream_t s);
+// Poisson solve with an inhomogeneous permittivity and fixed-potential nodes
+// by Jacobi-preconditioned conjugate gradients (ek_krylov.cu); *bad_eps is set
+// (and nothing solved) when a permittivity is not positive and finite
+size_t poisson_cg_scratch_bytes(int nx, int ny, int nz);
+cudaError_t poisson_solve_cg(const double* q, const double* eps, const unsigned char* fixed,
+                             const double* phi_fixed, double* phi, int nx, int ny, int nz, double bjerrum,
+                             double tol, int max_iter, void* scratch, cudaStream_t s, int* iters,
+                             double* residual, bool* bad_eps);
 // S1 of the FP32 systems of a batch whose edges are all 32, 48 or 64
 // (poisson_batch_ok): pass 0 the x transform, 1 the y-z planes with the Green
 // multiply, 2 the inverse x transform.  A system's entry of the argument

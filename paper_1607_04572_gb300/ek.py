@@ -49,7 +49,7 @@ EXPORTS = ["ek_create", "ek_destroy", "ek_add_particle", "ek_set_field", "ek_get
            "ek_set_stream", "ek_sync", "ek_last_error", "ek_lattice_dirs",
            "ek_poisson_scratch_bytes", "ek_poisson_solve", "ek_step_timed",
            "ek_kernel_launches", "ek_poisson_solve_static", "ek_poisson_mg_scratch_bytes",
-           "ek_poisson_solve_mg",
+           "ek_poisson_solve_mg", "ek_poisson_cg_scratch_bytes", "ek_poisson_solve_cg",
            "ek_batch_create", "ek_batch_destroy", "ek_batch_set_stream", "ek_batch_step_async",
            "ek_batch_step", "ek_batch_sync", "ek_batch_tune", "ek_batch_config", "ek_batch_set_config",
            "ek_batch_wait_test", "ek_batch_size", "ek_debug_fail_alloc",
@@ -123,6 +123,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ek_poisson_mg_scratch_bytes.restype = ctypes.c_size_t
     lib.ek_poisson_solve_mg.argtypes = [vp, vp, ip, ip, ip, dp, dp, ip, vp, vp,
                                         ctypes.POINTER(ip), ctypes.POINTER(dp)]
+    lib.ek_poisson_cg_scratch_bytes.argtypes = [ip, ip, ip]
+    lib.ek_poisson_cg_scratch_bytes.restype = ctypes.c_size_t
+    lib.ek_poisson_solve_cg.argtypes = [vp, vp, vp, vp, vp, ip, ip, ip, dp, dp, ip, vp, vp,
+                                        ctypes.POINTER(ip), ctypes.POINTER(dp)]
     lib.ek_kernel_launches.argtypes = [vp]
     lib.ek_kernel_launches.restype = ctypes.c_longlong
     lib.ek_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
@@ -145,6 +149,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         if name not in ("ek_num_particles", "ek_last_error", "ek_lattice_dirs",
                         "ek_poisson_scratch_bytes", "ek_kernel_launches", "ek_batch_size",
                         "ek_poisson_mg_scratch_bytes", "ek_debug_fail_alloc",
+                        "ek_poisson_cg_scratch_bytes",
                         "ek_batch_last_error"):
             getattr(lib, name).restype = ip
     _lib = lib
@@ -380,6 +385,31 @@ def poisson_solve_mg(q, phi, shape, bjerrum, scratch, tol=1e-12, max_cycles=50, 
     if st != 0:
         raise EKError(st, "ek_poisson_solve_mg failed")
     return cyc.value, res.value
+
+
+def poisson_cg_scratch_bytes(shape):
+    return int(load_library().ek_poisson_cg_scratch_bytes(*(int(v) for v in shape)))
+
+
+def poisson_solve_cg(q, phi, shape, bjerrum, scratch, eps=None, fixed=None, phi_fixed=None,
+                     tol=1e-12, max_iter=20000, stream=None):
+    """Poisson solve with an inhomogeneous permittivity and fixed-potential
+    nodes by conjugate gradients (see ek_poisson_solve_cg in include/ek.h).
+    q, phi, eps, phi_fixed: float64 device tensors; fixed: uint8 device
+    tensor; scratch: a device tensor of at least poisson_cg_scratch_bytes(shape)
+    bytes.  Returns (iterations, relative residual)."""
+    lib = load_library()
+    nx, ny, nz = shape
+    h = 0 if stream is None else getattr(stream, "cuda_stream", stream)
+    ptr = (lambda t: ctypes.c_void_p(None) if t is None else ctypes.c_void_p(t.data_ptr()))
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    st = lib.ek_poisson_solve_cg(ptr(q), ptr(eps), ptr(fixed), ptr(phi_fixed), ptr(phi), nx, ny, nz,
+                                 float(bjerrum), float(tol), int(max_iter), ptr(scratch),
+                                 ctypes.c_void_p(int(h)), ctypes.byref(it), ctypes.byref(res))
+    if st != 0:
+        raise EKError(st, "ek_poisson_solve_cg failed")
+    return it.value, res.value
 
 
 POISSON_STATIC_MAX = 1 << 19  # complex doubles of the fixed scratch of ek_poisson_solve_static
