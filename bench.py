@@ -438,7 +438,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="headline workload only (no 128^3 / 256^3 / FP64 / batched / multigrid lines)")
+                    help="headline workload only (no 128^3 / 256^3 / FP64 / batched / multigrid / CG lines)")
     ap.add_argument("--workload", default=HEADLINE, choices=["large", "many", "single", "small"],
                     help="the measured workload (the headline is the large box; the others are "
                          "for profiling smaller cases)")
@@ -540,6 +540,7 @@ def main():
         line["many_256"] = lm
         if rank == 0 and ws == 1:
             line["poisson_mg"] = measure_poisson_mg(ek, torch)
+            line["poisson_cg"] = measure_poisson_cg(ek, torch)
         rb = measure_batch(ek, torch, args, barrier, max_over_ranks)
         rb["step_roofline"] = step_roofline(rb["value"], step_bytes_per_node(True, 2), hbm_peak)
         line["batched_form"] = rb
@@ -607,6 +608,51 @@ def measure_poisson_mg(ek, torch, shape=(128, 128, 128), reps=3):
             "max_rel_diff_vs_fft": diff,
             "bytes_per_node_cycle": MG_BYTES_PER_NODE_CYCLE, "achieved_gbs": round(gbs, 1),
             "note": "FP64; every V-cycle's residual norm is read on the host to test convergence"}
+
+
+# Conjugate-gradient traffic per node and iteration (FP64): the operator
+# reads p, D^-1 and the node's three face permittivities and writes Ap (48);
+# the update reads D^-1, p, Ap and reads and writes x and r (56); the new
+# direction reads D^-1 and reads and writes r and p (40).
+CG_BYTES_PER_NODE_ITER = 48 + 56 + 40   # 144
+
+
+def measure_poisson_cg(ek, torch, shape=(128, 128, 128), tol=1e-10):
+    """The Poisson solve with an inhomogeneous permittivity and fixed
+    potentials (FP64 conjugate gradients): a low-permittivity sphere (eps 2,
+    R = 20) in water (eps 80) with a charged shell, between planes held at
+    +-1: time per solve (CUDA events, after a warm-up solve), iterations and
+    achieved bandwidth on the CG's bytes per node and iteration."""
+    import numpy as np
+    nx, ny, nz = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r = np.sqrt((x - nx / 2 + 0.3) ** 2 + (y - ny / 2 - 0.2) ** 2 + (z - nz / 2 + 0.1) ** 2)
+    dev = "cuda"
+    eps = torch.tensor(np.where(r < 20.0, 2.0, 80.0), device=dev, dtype=torch.float64)
+    q = torch.tensor(np.where((r >= 20.0) & (r < 22.0), -0.01, 0.0), device=dev, dtype=torch.float64)
+    fixed = torch.tensor(((z == 0) | (z == nz - 1)).astype(np.uint8), device=dev)
+    pf = torch.tensor(np.where(z == 0, 1.0, -1.0), device=dev, dtype=torch.float64)
+    phi = torch.empty_like(q)
+    scratch = torch.empty(ek.poisson_cg_scratch_bytes(shape), dtype=torch.uint8, device=dev)
+    st = torch.cuda.Stream()
+    best = None
+    for rep in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        it, res = ek.poisson_solve_cg(q, phi, shape, 0.7, scratch, eps=eps, fixed=fixed, phi_fixed=pf,
+                                      tol=tol, max_iter=20000, stream=st)
+        e1.record(st)
+        e1.synchronize()
+        if rep > 0:
+            best = e0.elapsed_time(e1)
+    n = nx * ny * nz
+    gbs = CG_BYTES_PER_NODE_ITER * n * it / (best / 1e3) / 1e9
+    return {"shape": list(shape), "ms": round(best, 3), "iterations": it, "residual": res,
+            "ms_per_iteration": round(best / max(it, 1), 4),
+            "bytes_per_node_iteration": CG_BYTES_PER_NODE_ITER, "achieved_gbs": round(gbs, 1),
+            "note": "FP64 Jacobi-preconditioned CG, tol 1e-10; eps 2 sphere R=20 in eps 80 with a "
+                    "charged shell, planes z=0 and z=nz-1 held at +1 and -1"}
 
 
 def measure_batch(ek, torch, args, barrier, max_over_ranks):

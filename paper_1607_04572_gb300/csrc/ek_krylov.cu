@@ -91,6 +91,14 @@ __device__ __forceinline__ double block_total(double v) {
   return t;
 }
 
+// the sum of part[row * CG_BLOCKS + 0 .. nb) by one block: each thread adds
+// its strided entries in order, then the fixed tree; valid in thread 0
+__device__ __forceinline__ double row_total(const double* part, int row, int nb) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < nb; i += CG_T) t += part[row * CG_BLOCKS + i];
+  return block_total(t);
+}
+
 // sum of q, the number of fixed nodes and of permittivities that are not
 // positive and finite (block sums)
 __global__ void __launch_bounds__(CG_T) k_cg_stats(Box b, const double* q, const double* eps,
@@ -113,14 +121,12 @@ __global__ void __launch_bounds__(CG_T) k_cg_stats(Box b, const double* q, const
 
 // the block sums of part's rows 0, 1, 2 (CG_BLOCKS apart), each added in
 // order, into sc[i0], sc[i1], sc[i2] (a negative index: that row is skipped)
-__global__ void k_cg_total(const double* part, int nb, double* sc, int i0, int i1, int i2) {
+__global__ void __launch_bounds__(CG_T) k_cg_total(const double* part, int nb, double* sc, int i0, int i1,
+                                                   int i2) {
+  const double a = row_total(part, 0, nb);
+  const double c = i1 >= 0 ? row_total(part, 1, nb) : 0.0;
+  const double d = i2 >= 0 ? row_total(part, 2, nb) : 0.0;
   if (threadIdx.x == 0) {
-    double a = 0.0, c = 0.0, d = 0.0;
-    for (int i = 0; i < nb; ++i) {
-      a += part[i];
-      if (i1 >= 0) c += part[CG_BLOCKS + i];
-      if (i2 >= 0) d += part[2 * CG_BLOCKS + i];
-    }
     sc[i0] = a;
     if (i1 >= 0) sc[i1] = c;
     if (i2 >= 0) sc[i2] = d;
@@ -190,20 +196,33 @@ __global__ void __launch_bounds__(CG_T) k_cg_prep(Box b, CGView v, const double*
   }
 }
 
-// Ap on the free nodes (p is 0 on fixed nodes); block sums of p.Ap
-__global__ void __launch_bounds__(CG_T) k_cg_apply(Box b, CGView v) {
+// Ap on the free nodes (p is 0 on fixed nodes); block sums of p.Ap.  The
+// work items are the 32 x 8 tiles of every plane (tx x ty tiles per plane);
+// block b takes items b, b + gridDim.x, ...: node coordinates come from the
+// item, with no division per node.
+__global__ void __launch_bounds__(CG_T) k_cg_apply(Box b, CGView v, int tx, int ty) {
+  const int N = (int)b.N, sy = b.nx, sz = b.nx * b.ny;
+  const int items = tx * ty * b.nz;
+  const double* __restrict__ cx = v.cf;
+  const double* __restrict__ cy = v.cf + N;
+  const double* __restrict__ cz = v.cf + 2 * (size_t)N;
   double pap = 0.0;
-  for (long long n = blockIdx.x * (long long)CG_T + threadIdx.x; n < b.N; n += (long long)gridDim.x * CG_T) {
+  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+    const int bx = w % tx, by = (w / tx) % ty, z = w / (tx * ty);
+    const int x = bx * 32 + (threadIdx.x & 31), y = by * 8 + (threadIdx.x >> 5);
+    if (x >= b.nx || y >= b.ny) continue;
+    const int n = x + sy * y + sz * z;
     if (v.dinv[n] == 0.0) {
       v.ap[n] = 0.0;
       continue;
     }
-    long long m[6];
-    neighbours(b, n, m);
+    const int dxp = x + 1 < b.nx ? 1 : 1 - b.nx, dxm = x > 0 ? -1 : b.nx - 1;
+    const int dyp = y + 1 < b.ny ? sy : sy - sz, dym = y > 0 ? -sy : sz - sy;
+    const int dzp = z + 1 < b.nz ? sz : sz - N, dzm = z > 0 ? -sz : N - sz;
     const double pn = v.p[n];
-    const double a = v.cf[n] * (pn - v.p[m[0]]) + v.cf[m[1]] * (pn - v.p[m[1]]) +
-                     v.cf[b.N + n] * (pn - v.p[m[2]]) + v.cf[b.N + m[3]] * (pn - v.p[m[3]]) +
-                     v.cf[2 * b.N + n] * (pn - v.p[m[4]]) + v.cf[2 * b.N + m[5]] * (pn - v.p[m[5]]);
+    const double a = cx[n] * (pn - v.p[n + dxp]) + cx[n + dxm] * (pn - v.p[n + dxm]) +
+                     cy[n] * (pn - v.p[n + dyp]) + cy[n + dym] * (pn - v.p[n + dym]) +
+                     cz[n] * (pn - v.p[n + dzp]) + cz[n + dzm] * (pn - v.p[n + dzm]);
     v.ap[n] = a;
     pap += pn * a;
   }
@@ -211,11 +230,10 @@ __global__ void __launch_bounds__(CG_T) k_cg_apply(Box b, CGView v) {
   if (threadIdx.x == 0) v.part[blockIdx.x] = pap;
 }
 
-// alpha = r.z / p.Ap (the block sums added in order)
-__global__ void k_cg_alpha(CGView v, int nb) {
+// alpha = r.z / p.Ap
+__global__ void __launch_bounds__(CG_T) k_cg_alpha(CGView v, int nb) {
+  const double pap = row_total(v.part, 0, nb);
   if (threadIdx.x == 0) {
-    double pap = 0.0;
-    for (int i = 0; i < nb; ++i) pap += v.part[i];
     v.sc[1] = pap;
     v.sc[2] = pap > 0.0 ? v.sc[0] / pap : 0.0;
   }
@@ -255,17 +273,15 @@ __global__ void __launch_bounds__(CG_T) k_cg_update(Box b, CGView v, double* x, 
 
 // beta = r.z(new) / r.z(old); r.r for the convergence test; with the
 // projection (every node free): m = mean r, and r.z, r.r of r - m
-__global__ void k_cg_beta(CGView v, int nb, long long N, int neutral) {
+__global__ void __launch_bounds__(CG_T) k_cg_beta(CGView v, int nb, long long N, int neutral) {
+  double rz = row_total(v.part, 0, nb);
+  double rr = row_total(v.part, 1, nb);
+  double s1 = 0.0, s2 = 0.0;
+  if (neutral) {
+    s1 = row_total(v.part, 2, nb);
+    s2 = row_total(v.part, 3, nb);
+  }
   if (threadIdx.x == 0) {
-    double rz = 0.0, rr = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int i = 0; i < nb; ++i) {
-      rz += v.part[i];
-      rr += v.part[CG_BLOCKS + i];
-      if (neutral) {
-        s1 += v.part[2 * CG_BLOCKS + i];
-        s2 += v.part[3 * CG_BLOCKS + i];
-      }
-    }
     double m = 0.0;
     if (neutral) {
       m = s1 / (double)N;
@@ -322,11 +338,13 @@ cudaError_t poisson_solve_cg(const double* q, const double* eps, const unsigned 
   CGView v;
   cg_layout(b.N, &v, scratch);
   const int nb = (int)std::min<long long>(CG_BLOCKS, (b.N + CG_T - 1) / CG_T);
+  const int tx = (nx + 31) / 32, ty = (ny + 7) / 8;
+  const int na = (int)std::min<long long>(CG_BLOCKS, (long long)tx * ty * nz);  // operator blocks
   double h[12];
   *bad_eps = false;
   // the charge's sum, the fixed-node count and the invalid permittivities
   k_cg_stats<<<nb, CG_T, 0, s>>>(b, q, eps, fixed, v.part);
-  k_cg_total<<<1, 32, 0, s>>>(v.part, nb, v.sc, 6, 7, 8);
+  k_cg_total<<<1, CG_T, 0, s>>>(v.part, nb, v.sc, 6, 7, 8);
   cudaError_t e = cudaMemcpyAsync(h, v.sc, 12 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
@@ -336,35 +354,57 @@ cudaError_t poisson_solve_cg(const double* q, const double* eps, const unsigned 
   }
   const int neutral = h[7] == 0.0 ? 1 : 0;  // no fixed node: remove the mean charge
   k_cg_prep<<<nb, CG_T, 0, s>>>(b, v, q, eps, fixed, phi_fixed, phi, 4.0 * M_PI * bjerrum, v.sc, neutral);
-  k_cg_total<<<1, 32, 0, s>>>(v.part, nb, v.sc, 0, 5, 9);
+  k_cg_total<<<1, CG_T, 0, s>>>(v.part, nb, v.sc, 0, 5, 9);
   e = cudaMemcpyAsync(h, v.sc, 12 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
   const double bnorm = sqrt(h[5]);
   int it = 0;
   double rel = 0.0;
+  auto iterate = [&]() {
+    k_cg_apply<<<na, CG_T, 0, s>>>(b, v, tx, ty);
+    k_cg_alpha<<<1, CG_T, 0, s>>>(v, na);
+    k_cg_update<<<nb, CG_T, 0, s>>>(b, v, phi, neutral);
+    k_cg_beta<<<1, CG_T, 0, s>>>(v, nb, b.N, neutral);
+    k_cg_direction<<<nb, CG_T, 0, s>>>(b, v);
+  };
+  // CG_CHECK iterations as one graph (a caller stream other than the legacy
+  // default stream can be captured); else the launches one by one
+  cudaGraphExec_t graph = nullptr;
+  if (s != nullptr && bnorm > 0.0 && max_iter >= CG_CHECK) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      for (int k = 0; k < CG_CHECK; ++k) iterate();
+      if (cudaStreamEndCapture(s, &g) == cudaSuccess && g) {
+        if (cudaGraphInstantiate(&graph, g, 0) != cudaSuccess) graph = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();  // a failed capture leaves the launches one by one
+  }
   if (bnorm > 0.0) {
     rel = 1.0;
     while (it < max_iter && rel > tol) {
       const int batch = std::min(CG_CHECK, max_iter - it);
-      for (int k = 0; k < batch; ++k) {
-        k_cg_apply<<<nb, CG_T, 0, s>>>(b, v);
-        k_cg_alpha<<<1, 32, 0, s>>>(v, nb);
-        k_cg_update<<<nb, CG_T, 0, s>>>(b, v, phi, neutral);
-        k_cg_beta<<<1, 32, 0, s>>>(v, nb, b.N, neutral);
-        k_cg_direction<<<nb, CG_T, 0, s>>>(b, v);
+      if (batch == CG_CHECK && graph) {
+        e = cudaGraphLaunch(graph, s);
+        if (e != cudaSuccess) break;
+      } else {
+        for (int k = 0; k < batch; ++k) iterate();
       }
       it += batch;
       e = cudaMemcpyAsync(h, v.sc, 12 * sizeof(double), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) return e;
+      if (e != cudaSuccess) break;
       rel = sqrt(h[4]) / bnorm;
       if (!(rel == rel)) break;  // not a number: reported to the caller
     }
   }
+  if (graph) cudaGraphExecDestroy(graph);
+  if (e != cudaSuccess) return e;
   if (neutral) {
     k_cg_sum<<<nb, CG_T, 0, s>>>(b, phi, v.part);
-    k_cg_total<<<1, 32, 0, s>>>(v.part, nb, v.sc, 5, -1, -1);
+    k_cg_total<<<1, CG_T, 0, s>>>(v.part, nb, v.sc, 5, -1, -1);
     k_cg_shift<<<nb, CG_T, 0, s>>>(b, phi, v.sc);
   }
   e = cudaStreamSynchronize(s);
