@@ -448,14 +448,14 @@ template <int NC>
 __device__ void column_sums(const double* tab, int nrow, int stride, int col0, double* out);
 __device__ void integrate_all(const PartArgs& a);
 
-template <int NV>
-__device__ void block_sum_t(const double (&v)[NV], const bool (&group_on)[NV / 6], double* out) {
+template <int NV, class Get>
+__device__ void block_sum_t(Get v, const bool (&group_on)[NV / 6], double* out) {
   __shared__ double tr[NV][FORCE_T + 1];
   __shared__ double quarter[NV][4];
   const int t = threadIdx.x;
 #pragma unroll
   for (int j = 0; j < NV; ++j)
-    if (group_on[j / 6]) tr[j][t] = v[j];
+    if (group_on[j / 6]) tr[j][t] = v(j);
   __syncthreads();
   if (t < 4 * NV) {
     const int j = t >> 2, w = t & 3;
@@ -478,32 +478,6 @@ __device__ void block_sum_t(const double (&v)[NV], const bool (&group_on)[NV / 6
 // Block (p, b) takes the rows b, b + nb, b + 2 nb, ... of FORCE_T cells of the
 // widened box (nb blocks for this particle), so the cells next to the sphere
 // are spread over all blocks.
-// FP32 form: each thread's float sums over its own few cells are widened to
-// FP64 and added within the warp by a fixed shuffle tree, then the FORCE_T / 32
-// warp sums in FP64 in order.  Result in out[j] for threadIdx.x == j < NV.
-template <int NV>
-__device__ void block_sum_f(const float (&v)[NV], const bool (&group_on)[NV / 6], double* out) {
-  __shared__ double wsum[FORCE_T / 32][NV];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    if (!group_on[j / 6]) continue;
-    double x = (double)v[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) wsum[warp][j] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    const int j = threadIdx.x;
-    double t = 0.0;
-    if (group_on[j / 6])
-      for (int w = 0; w < FORCE_T / 32; ++w) t += wsum[w][j];
-    out[j] = t;
-  }
-  __syncthreads();
-}
-
 template <class FM>
 __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Blk bk) {
   const int p = bk.x;
@@ -769,11 +743,11 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
   on[3] = __syncthreads_or(touched[3]);
   double* out = a.fpart + ((long long)p * a.fchunks + bk.y) * FPART;
   if (FM::fp32) {
-#pragma unroll
-    for (int j = 18; j < 21; ++j) facc[j] = (float)acc[j];  // the lattice slice
-    block_sum_f<FPART>(facc, on, out);
+    // each thread's float sums over its own few cells, widened to FP64 (the
+    // lattice slice is FP64 already); everything above them in FP64
+    block_sum_t<FPART>([&](int j) { return (j >= 18 && j < 21) ? acc[j] : (double)facc[j]; }, on, out);
   } else {
-    block_sum_t<FPART>(acc, on, out);
+    block_sum_t<FPART>([&](int j) { return acc[j]; }, on, out);
   }
   // the particle's last block sums its rows; the last particle integrates
   __shared__ bool last;
@@ -1320,83 +1294,169 @@ template <class FM>
 __device__ __forceinline__ void transitions_body(const PartArgs& a, const Blk bk) {
   using pop_t = typename FM::pop_t;
   using spc_t = typename FM::spc_t;
+  constexpr unsigned FULL = 0xffffffffu;
   const int p = bk.x;
   DevParticle& P = a.parts[p];
   const int c = bk.y * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const Grid g = a.g;
   const long long N = g.N;
   const double rho0 = a.ph.rho0;
+  const int K = a.ph.K;
   pop_t* f = (pop_t*)a.f;
+  const spc_t* rho = (const spc_t*)a.rho;
   int X = 0, Y = 0, Z = 0;
-  long long n = 0;
   bool covered = false, uncovered = false;
   if (c < box_cells(P.ulo, P.uhi)) {
     box_coord(c, P.ulo, P.uhi, X, Y, Z);
-    n = node_of(X, Y, Z, g);
+    const long long n = node_of(X, Y, Z, g);
     const int old = a.owner_prev[n], nw = a.owner[n];
     covered = old == FLUID && nw == p;
     uncovered = old == p && nw == FLUID;
   }
-  long long rec[Q];
-  int nf = 0;
-  // momentum the particle receives from this node: that of the destroyed
-  // fluid, or minus that of the created fluid
+  // momentum the particle receives from this thread's node: that of the
+  // destroyed fluid, or minus that of the created fluid
   double mom[3] = {0.0, 0.0, 0.0};
-  if (covered || uncovered) {
+  // The warp takes its transition nodes one after another, all 32 lanes on
+  // each: lane k (1 <= k < Q) looks at the neighbour in direction k, lane
+  // i < Q at population i, so the loads of a node are issued together.  Sums
+  // over lanes go through a fixed shuffle tree.
+  auto warp_sum = [&](double v) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const long long m = node_of(X + dcx(i), Y + dcy(i), Z + dcz(i), g);
-      if (steady_fluid(a, m)) rec[nf++] = m;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+  };
+  unsigned todo = __ballot_sync(FULL, covered || uncovered);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int Xs = __shfl_sync(FULL, X, src), Ys = __shfl_sync(FULL, Y, src), Zs = __shfl_sync(FULL, Z, src);
+    const bool cov = __shfl_sync(FULL, covered ? 1 : 0, src) != 0;
+    const long long ns = node_of(Xs, Ys, Zs, g);
+    // the neighbours that are fluid before and after the re-flag
+    long long mk = ns;
+    bool sf = false;
+    if (lane >= 1 && lane < Q) {
+      mk = node_of(Xs + dcx(lane), Ys + dcy(lane), Zs + dcz(lane), g);
+      sf = steady_fluid(a, mk);
     }
-  }
-  if (covered) {
-    // destroyed fluid: its momentum goes to the particle
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const double fi = pop_abs<FM>(f, i, N, n, rho0);
-      if (dcx(i)) mom[0] += csgn(dcx(i), fi);
-      if (dcy(i)) mom[1] += csgn(dcy(i), fi);
-      if (dcz(i)) mom[2] += csgn(dcz(i), fi);
-      f[(long long)i * N + n] = FM::fp32 ? (pop_t)(-wgt(i) * rho0) : (pop_t)0;
-    }
-  } else if (uncovered) {
-    // created fluid: f^eq(mean neighbour density, v_b), momentum taken from the particle
-    double rbar = rho0;
-    if (nf > 0) {
-      double s = 0.0;
-      for (int j = 0; j < nf; ++j) {
-        double d = 0.0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) d += pop_abs<FM>(f, i, N, rec[j], rho0);
-        s += d;
-      }
-      rbar = s / (double)nf;
-    }
-    // v_b at this node, unwrapped into the particle's current box
-    const double Xu = (double)(P.lo[0] + wrapi(wrapi(X, g.nx) - P.lo[0], g.nx));
-    const double Yu = (double)(P.lo[1] + wrapi(wrapi(Y, g.ny) - P.lo[1], g.ny));
-    const double Zu = (double)(P.lo[2] + wrapi(wrapi(Z, g.nz) - P.lo[2], g.nz));
-    const double dx = Xu - P.pos[0], dy = Yu - P.pos[1], dz = Zu - P.pos[2];
-    const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
-    const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
-    const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
-    const double usq = vx * vx + vy * vy + vz * vz;
+    const unsigned fm = __ballot_sync(FULL, sf);
+    const int nf = __popc(fm);
+    const int rank = __popc(fm & ((1u << lane) - 1u));  // place in the list, direction order
     double mx = 0.0, my = 0.0, mz = 0.0;
+    if (cov) {
+      // destroyed fluid: its momentum goes to the particle
+      if (lane < Q) {
+        const double fi = pop_abs<FM>(f, lane, N, ns, rho0);
+        if (dcx(lane)) mx = csgn(dcx(lane), fi);
+        if (dcy(lane)) my = csgn(dcy(lane), fi);
+        if (dcz(lane)) mz = csgn(dcz(lane), fi);
+        f[(long long)lane * N + ns] = FM::fp32 ? (pop_t)(-wgt(lane) * rho0) : (pop_t)0;
+      }
+    } else {
+      // created fluid: f^eq(mean neighbour density, v_b), momentum taken from
+      // the particle
+      double d = 0.0;
+      if (sf) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const double cu = cdot(i, vx, vy, vz);
-      const double shape = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
-      const double fi = wgt(i) * rbar * (1.0 + shape);
-      // FP32 form stores the deviation from w_i rho0, formed without cancellation
-      f[(long long)i * N + n] =
-          FM::fp32 ? (pop_t)(wgt(i) * ((rbar - rho0) + rbar * shape)) : (pop_t)fi;
-      if (dcx(i)) mx += csgn(dcx(i), fi);
-      if (dcy(i)) my += csgn(dcy(i), fi);
-      if (dcz(i)) mz += csgn(dcz(i), fi);
+        for (int i = 0; i < Q; ++i) d += pop_abs<FM>(f, i, N, mk, rho0);
+      }
+      const double sum = warp_sum(d);
+      const double rbar = nf > 0 ? sum / (double)nf : rho0;
+      // v_b at this node, unwrapped into the particle's current box
+      const double Xu = (double)(P.lo[0] + wrapi(wrapi(Xs, g.nx) - P.lo[0], g.nx));
+      const double Yu = (double)(P.lo[1] + wrapi(wrapi(Ys, g.ny) - P.lo[1], g.ny));
+      const double Zu = (double)(P.lo[2] + wrapi(wrapi(Zs, g.nz) - P.lo[2], g.nz));
+      const double dx = Xu - P.pos[0], dy = Yu - P.pos[1], dz = Zu - P.pos[2];
+      const double vx = P.vel[0] + (P.omega[1] * dz - P.omega[2] * dy);
+      const double vy = P.vel[1] + (P.omega[2] * dx - P.omega[0] * dz);
+      const double vz = P.vel[2] + (P.omega[0] * dy - P.omega[1] * dx);
+      const double usq = vx * vx + vy * vy + vz * vz;
+      if (lane < Q) {
+        const double cu = dcx(lane) * vx + dcy(lane) * vy + dcz(lane) * vz;
+        const double shape = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
+        const double fi = wgt(lane) * rbar * (1.0 + shape);
+        // FP32 form stores the deviation from w_i rho0, formed without cancellation
+        f[(long long)lane * N + ns] =
+            FM::fp32 ? (pop_t)(wgt(lane) * ((rbar - rho0) + rbar * shape)) : (pop_t)fi;
+        if (dcx(lane)) mx = -csgn(dcx(lane), fi);
+        if (dcy(lane)) my = -csgn(dcy(lane), fi);
+        if (dcz(lane)) mz = -csgn(dcz(lane), fi);
+      }
     }
-    mom[0] = -mx;
-    mom[1] = -my;
-    mom[2] = -mz;
+    mx = warp_sum(mx);
+    my = warp_sum(my);
+    mz = warp_sum(mz);
+    if (lane == src) {
+      mom[0] = mx;
+      mom[1] = my;
+      mom[2] = mz;
+    }
+    // solute: expelled to the neighbours (covered) or refilled from them,
+    // Eqs. 17-18 (uncovered); records applied after every transition is known
+    if (cov) {
+      if (nf == 0) {
+        if (lane == 0) atomicOr(a.status, ST_EXPEL);
+        continue;
+      }
+      if (K == 0) continue;
+      int slot = 0;
+      if (lane == 0) slot = atomicAdd(a.xfer_count, 1 + nf);
+      slot = __shfl_sync(FULL, slot, 0);
+      if (slot + 1 + nf > a.xfer_cap) {
+        if (lane == 0) atomicOr(a.status, ST_CAPACITY);
+        continue;
+      }
+      if (lane == 0) {
+        Transfer self;
+        self.node = ns;
+        for (int k = 0; k < EK_MAX_SPECIES; ++k) self.amount[k] = k < K ? -(double)rho[k * N + ns] : 0.0;
+        a.xfer[slot] = self;
+      }
+      if (sf) {
+        Transfer tr;
+        tr.node = mk;
+        for (int k = 0; k < EK_MAX_SPECIES; ++k) {
+          if (k >= K) {
+            tr.amount[k] = 0.0;
+          } else if (FM::fp32) {
+            const int r = (int)rho[k * N + ns];
+            const int share = r / nf, rem = r - share * nf;  // rem has the sign of r
+            const int extra = (rank < (rem < 0 ? -rem : rem)) ? (rem < 0 ? -1 : 1) : 0;
+            tr.amount[k] = (double)(share + extra);
+          } else {
+            tr.amount[k] = (double)rho[k * N + ns] / (double)nf;
+          }
+        }
+        a.xfer[slot + 1 + rank] = tr;
+      }
+    } else {
+      if ((a.ph.flags & EK_VACATE_ZERO) || nf == 0 || K == 0) continue;
+      // refill, Eqs. 17-18: each neighbour gives rho/(N_f + 1)
+      int slot = 0;
+      if (lane == 0) slot = atomicAdd(a.xfer_count, 2 * nf);
+      slot = __shfl_sync(FULL, slot, 0);
+      if (slot + 2 * nf > a.xfer_cap) {
+        if (lane == 0) atomicOr(a.status, ST_CAPACITY);
+        continue;
+      }
+      if (sf) {
+        Transfer give, take;
+        give.node = mk;
+        take.node = ns;
+        for (int k = 0; k < EK_MAX_SPECIES; ++k) {
+          double sh = 0.0;
+          if (k < K) {
+            if (FM::fp32) sh = (double)((int)rho[k * N + mk] / (nf + 1));
+            else sh = (double)rho[k * N + mk] / (double)(nf + 1);
+          }
+          give.amount[k] = -sh;
+          take.amount[k] = sh;
+        }
+        a.xfer[slot + 2 * rank] = give;
+        a.xfer[slot + 2 * rank + 1] = take;
+      }
+    }
   }
   // the particle's transition momentum, summed in a fixed order: the CTA's
   // nodes in a fixed tree, then the CTAs' sums in chunk order by the
@@ -1418,13 +1478,15 @@ __device__ __forceinline__ void transitions_body(const PartArgs& a, const Blk bk
         quarter[d][w] = sq;
       }
       __syncthreads();
-      if (t < 3)
+      if (t < 3) {
         a.tpart[((long long)p * a.uchunks + bk.y) * 3 + t] =
             ((quarter[t][0] + quarter[t][1]) + quarter[t][2]) + quarter[t][3];
+        __threadfence();
+      }
     } else if (t < 3) {
       a.tpart[((long long)p * a.uchunks + bk.y) * 3 + t] = 0.0;  // no transition in this CTA
+      __threadfence();
     }
-    __threadfence();
     __syncthreads();
     if (t == 0) last = atomicAdd(a.pticket + p, 1) == a.uchunks - 1;
     __syncthreads();
@@ -1437,66 +1499,6 @@ __device__ __forceinline__ void transitions_body(const PartArgs& a, const Blk bk
       }
       if (t == 0) a.pticket[p] = 0;
     }
-  }
-  if (!covered && !uncovered) return;
-  const int K = a.ph.K;
-  const spc_t* rho = (const spc_t*)a.rho;
-  if (covered) {
-    if (nf == 0) {
-      atomicOr(a.status, ST_EXPEL);
-      return;
-    }
-    if (K == 0) return;
-    const int slot = atomicAdd(a.xfer_count, 1 + nf);
-    if (slot + 1 + nf > a.xfer_cap) {
-      atomicOr(a.status, ST_CAPACITY);
-      return;
-    }
-    Transfer self;
-    self.node = n;
-    for (int k = 0; k < EK_MAX_SPECIES; ++k) self.amount[k] = k < K ? -(double)rho[k * N + n] : 0.0;
-    a.xfer[slot] = self;
-    for (int j = 0; j < nf; ++j) {
-      Transfer tr;
-      tr.node = rec[j];
-      for (int k = 0; k < EK_MAX_SPECIES; ++k) {
-        if (k >= K) {
-          tr.amount[k] = 0.0;
-        } else if (FM::fp32) {
-          const int r = (int)rho[k * N + n];
-          const int share = r / nf, rem = r - share * nf;  // rem has the sign of r
-          const int extra = (j < (rem < 0 ? -rem : rem)) ? (rem < 0 ? -1 : 1) : 0;
-          tr.amount[k] = (double)(share + extra);
-        } else {
-          tr.amount[k] = (double)rho[k * N + n] / (double)nf;
-        }
-      }
-      a.xfer[slot + 1 + j] = tr;
-    }
-    return;
-  }
-  if ((a.ph.flags & EK_VACATE_ZERO) || nf == 0 || K == 0) return;
-  // refill, Eqs. 17-18: each neighbour gives rho/(N_f + 1)
-  const int slot = atomicAdd(a.xfer_count, 2 * nf);
-  if (slot + 2 * nf > a.xfer_cap) {
-    atomicOr(a.status, ST_CAPACITY);
-    return;
-  }
-  for (int j = 0; j < nf; ++j) {
-    Transfer give, take;
-    give.node = rec[j];
-    take.node = n;
-    for (int k = 0; k < EK_MAX_SPECIES; ++k) {
-      double sh = 0.0;
-      if (k < K) {
-        if (FM::fp32) sh = (double)((int)rho[k * N + rec[j]] / (nf + 1));
-        else sh = (double)rho[k * N + rec[j]] / (double)(nf + 1);
-      }
-      give.amount[k] = -sh;
-      take.amount[k] = sh;
-    }
-    a.xfer[slot + 2 * j] = give;
-    a.xfer[slot + 2 * j + 1] = take;
   }
 }
 
