@@ -619,7 +619,7 @@ CG_BYTES_PER_NODE_ITER = 48 + 56 + 40   # 144
 
 def measure_poisson_cg(ek, torch, shape=(128, 128, 128), tol=1e-10):
     """The Poisson solve with an inhomogeneous permittivity and fixed
-    potentials (FP64 conjugate gradients): a low-permittivity sphere (eps 2,
+    potentials (FP64 preconditioned conjugate gradients): a low-permittivity sphere (eps 2,
     R = 20) in water (eps 80) with a charged shell, between planes held at
     +-1: time per solve (CUDA events, after a warm-up solve), iterations and
     achieved bandwidth on the CG's bytes per node and iteration."""
@@ -651,8 +651,9 @@ def measure_poisson_cg(ek, torch, shape=(128, 128, 128), tol=1e-10):
     return {"shape": list(shape), "ms": round(best, 3), "iterations": it, "residual": res,
             "ms_per_iteration": round(best / max(it, 1), 4),
             "bytes_per_node_iteration": CG_BYTES_PER_NODE_ITER, "achieved_gbs": round(gbs, 1),
-            "note": "FP64 Jacobi-preconditioned CG, tol 1e-10; eps 2 sphere R=20 in eps 80 with a "
-                    "charged shell, planes z=0 and z=nz-1 held at +1 and -1"}
+            "note": "FP64 CG preconditioned by a multigrid V-cycle, tol 1e-10; eps 2 sphere R=20 "
+                    "in eps 80 with a charged shell, planes z=0 and z=nz-1 held at +1 and -1; the "
+                    "bytes are the CG's own (the V-cycle's are not counted)"}
 
 
 def measure_batch(ek, torch, args, barrier, max_over_ranks):

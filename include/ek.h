@@ -278,10 +278,15 @@ ek_status ek_poisson_solve_mg(const double* q, double* phi, int nx, int ny, int 
  * node with fixed[i] != 0 holds Phi = phi_fixed[i] (walls, electrodes).
  * Without fixed nodes the mean charge is removed and phi is returned with
  * mean 0 (then with eps = 1 the result is ek_poisson_solve's).  Method:
- * Jacobi-preconditioned conjugate gradients in FP64 from Phi = 0 on the free
- * nodes, until ||r||_2 <= tol ||b||_2 over the free nodes (checked every 10
- * iterations) or max_iter iterations; every inner product is a fixed-order
- * sum, so a solve is bit-reproducible.
+ * preconditioned conjugate gradients in FP64 from Phi = 0 on the free nodes,
+ * until ||r||_2 <= tol ||b||_2 over the free nodes or max_iter iterations.
+ * The preconditioner is one multigrid V-cycle of the same operator (levels
+ * halved while every edge is even and stays >= 4, coarse face permittivity
+ * the halved sum of the 4 fine faces it covers, damped Jacobi smoothing,
+ * the coarsest level of at most 8192 nodes by 40 sweeps) when the box has
+ * at least two levels, else the diagonal (Jacobi); the residual is checked
+ * every 2 (multigrid) or 10 (Jacobi) iterations.  Every inner product is a
+ * fixed-order sum, so a solve is bit-reproducible.
  *
  * All arrays are device arrays of nx*ny*nz values, index x + nx*(y + ny*z):
  * q, phi (double; may alias), eps (double, positive and finite; NULL: 1
