@@ -148,18 +148,32 @@ __device__ __forceinline__ int halo_wrap(int v, int n) {
   return min(v, n - 1);
 }
 
+// in-plane offsets (x + nx y) of the thread's halo-tile nodes e = tid and
+// tid + TN (-1: none); the same in every plane
+__device__ __forceinline__ void halo_offsets(int (&hoff)[2], int x0, int y0, const LBArgs& a) {
+  const int tid = threadIdx.x + TILE_X * threadIdx.y;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int e = tid + q * TN;
+    const int ey = e / HX, ex = e - ey * HX;
+    hoff[q] = e < HP ? halo_wrap(x0 - 1 + ex, a.g.nx) + a.g.nx * halo_wrap(y0 - 1 + ey, a.g.ny) : -1;
+  }
+}
+
 // stencil fields of plane zz (periodic) into ring slot `slot`
 template <int K, bool PV>
-__device__ __forceinline__ void stage_plane(LBRing<K>& t, int slot, int zz, int x0, int y0,
+__device__ __forceinline__ void stage_plane(LBRing<K>& t, int slot, int zz, const int (&hoff)[2],
                                             const LBArgs& a) {
   const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
   const size_t N = (size_t)a.g.N;
   const int z = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
   const int tid = threadIdx.x + TILE_X * threadIdx.y;
-  for (int e = tid; e < HP; e += TN) {
-    const int ey = e / HX, ex = e - ey * HX;
-    const int x = halo_wrap(x0 - 1 + ex, nx), y = halo_wrap(y0 - 1 + ey, ny);
-    const size_t m = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
+  const size_t pz = (size_t)nx * ny * z;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (hoff[q] < 0) continue;
+    const int e = tid + q * TN;
+    const size_t m = (size_t)hoff[q] + pz;
     cp_async4(&t.own[slot][e], a.owner + m);
     cp_async4(&t.phi[slot][e], (const float*)a.phi + m);
     if (PV) cp_async4(&t.psi[slot][e], (const float*)a.psi + m);
@@ -179,12 +193,17 @@ __device__ __forceinline__ void stage_pops(LBRing<K>& t, int buf, int z, int x0,
   const int tid = threadIdx.x + TILE_X * threadIdx.y;
   const size_t zoff = (size_t)nx * ny * z;
   if ((nx & 3) == 0) {
-    // chunk c: population i = c / 64, row r = (c / 8) % 8, four nodes at 4 (c % 8)
-    for (int c = tid; c < Q * TILE_Y * (TILE_X / 4); c += TN) {
-      const int i = c >> 6, r = (c >> 3) & 7, q = (c & 7) * 4;
-      const int y = y0 + r, x = x0 + q;
-      if (y < ny && x < nx)
-        cp_async16(&t.pop[buf][i][r * TILE_X + q], f + i * N + zoff + (size_t)y * nx + x);
+    // chunk tid + 256 j: population (tid >> 6) + 4 j, row (tid >> 3) % 8, four
+    // nodes at 4 (tid % 8): the row and nodes are the thread's own in every
+    // chunk, so only the population advances
+    const int r = (tid >> 3) & 7, q = (tid & 7) * 4, i0 = tid >> 6;
+    const int y = y0 + r, x = x0 + q;
+    if (y < ny && x < nx) {
+      const float* src = f + i0 * N + zoff + (size_t)y * nx + x;
+      float* dst = &t.pop[buf][i0][r * TILE_X + q];
+#pragma unroll
+      for (int j = 0; j < (Q + 3) / 4; ++j)
+        if (i0 + 4 * j < Q) cp_async16(dst + j * 4 * TN, src + (size_t)(4 * j) * N);
     }
   } else {
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
@@ -381,10 +400,12 @@ __device__ __forceinline__ void lb32_block(const LBArgs& a, const Phys32& c, int
   const bool in_xy = x < nx && y < ny;
   const int ex = threadIdx.x + 1, ey = threadIdx.y + 1;
   float iv[3] = {0.0f, 0.0f, 0.0f};
+  int hoff[2];
+  halo_offsets(hoff, x0, y0, a);
   // ring slot of plane zz: zz mod 4 (zz >= -1)
-  stage_plane<K, PV>(t, (z0 + 3) & 3, z0 - 1, x0, y0, a);
-  stage_plane<K, PV>(t, z0 & 3, z0, x0, y0, a);
-  stage_plane<K, PV>(t, (z0 + 1) & 3, z0 + 1, x0, y0, a);
+  stage_plane<K, PV>(t, (z0 + 3) & 3, z0 - 1, hoff, a);
+  stage_plane<K, PV>(t, z0 & 3, z0, hoff, a);
+  stage_plane<K, PV>(t, (z0 + 1) & 3, z0 + 1, hoff, a);
   stage_pops<K>(t, z0 & 1, z0, x0, y0, a);
   cp_async_commit();
   // A landed halo plane: does it hold a non-fluid node or Psi > 0?  And its
@@ -407,7 +428,7 @@ __device__ __forceinline__ void lb32_block(const LBArgs& a, const Phys32& c, int
   for (int z = z0; z < zend; ++z) {
     // plane z + 2 and the populations of z + 1 (empty group at the end)
     if (z + 1 < zend) {
-      stage_plane<K, PV>(t, (z + 2) & 3, z + 2, x0, y0, a);
+      stage_plane<K, PV>(t, (z + 2) & 3, z + 2, hoff, a);
       stage_pops<K>(t, (z + 1) & 1, z + 1, x0, y0, a);
     }
     cp_async_commit();
