@@ -503,23 +503,40 @@ struct AdvRing {
   unsigned char sg[3][HP];   // sign byte of S2: bit 7 fluid, sign codes of u
 };
 
-// the K shares of node e in a class row
+// a slot's shares as seen from node c: row 0 at node c (the pair of species
+// 0 and 1, or the single species) and at its species 2 (and 3); the shares of
+// class cls of the node at offset d from c are then at compile-time offsets
 template <int K>
-__device__ __forceinline__ void share_get(const int* row, int e, int (&v)[K]) {
+struct ShareRef {
+  const int* lo;
+  const int* hi;
+};
+template <int K>
+__device__ __forceinline__ ShareRef<K> share_ref(const int* row0, int c) {
+  ShareRef<K> r;
+  r.lo = K == 1 ? row0 + c : row0 + 2 * c;
+  r.hi = K == 3 ? row0 + 2 * HP + c : (K == 4 ? row0 + 2 * HP + 2 * c : row0);
+  return r;
+}
+template <int K>
+__device__ __forceinline__ void share_at(const ShareRef<K>& r, int cls, int d, int (&v)[K]) {
+  constexpr int ROW = HP * K;
   if constexpr (K == 1) {
-    v[0] = row[e];
+    v[0] = r.lo[(cls - 1) * ROW + d];
   } else {
-    const int2 w = reinterpret_cast<const int2*>(row)[e];
+    const int2 w = *reinterpret_cast<const int2*>(r.lo + (cls - 1) * ROW + 2 * d);
     v[0] = w.x;
     v[1] = w.y;
-    if constexpr (K == 3) v[2] = row[2 * HP + e];
+    if constexpr (K == 3) v[2] = r.hi[(cls - 1) * ROW + d];
     if constexpr (K == 4) {
-      const int2 w2 = reinterpret_cast<const int2*>(row + 2 * HP)[e];
+      const int2 w2 = *reinterpret_cast<const int2*>(r.hi + (cls - 1) * ROW + 2 * d);
       v[2] = w2.x;
       v[3] = w2.y;
     }
   }
 }
+
+// the K shares of node e into a class row
 template <int K>
 __device__ __forceinline__ void share_put(int* row, int e, const int (&v)[K]) {
   if constexpr (K == 1) {
@@ -647,17 +664,25 @@ __device__ __forceinline__ void advect32_block(const LBArgs& a, int bx, int by, 
     __syncthreads();
     const unsigned own = in_xy ? t.sg[s1][c] : 0u;
     if (own & 0x80u) {
+      // the three planes' sign bytes and shares as seen from this node, so
+      // that every access below is a base plus a compile-time offset
+      const unsigned char* g0 = &t.sg[s0][c];
+      const unsigned char* g1 = &t.sg[s1][c];
+      const unsigned char* g2 = &t.sg[s2][c];
+      const ShareRef<K> r0 = share_ref<K>(t.sh[s0][0], c);
+      const ShareRef<K> r1 = share_ref<K>(t.sh[s1][0], c);
+      const ShareRef<K> r2 = share_ref<K>(t.sh[s2][0], c);
       // own shares to the offsets {0, sign(v_a)}^3 \ 0 whose node is fluid
       const int sx = sign_of(own, 0), sy = sign_of(own, 2), sz = sign_of(own, 4);
-      const int ts = sz > 0 ? s2 : (sz < 0 ? s0 : s1);
+      const unsigned char* gt = sz > 0 ? g2 : (sz < 0 ? g0 : g1);
 #pragma unroll
       for (int o = 1; o < 8; ++o) {
         const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
         if ((ox && !sx) || (oy && !sy) || (oz && !sz)) continue;
-        const int tc = c + (oy ? sy * HX : 0) + (ox ? sx : 0);
-        if (!(t.sg[oz ? ts : s1][tc] & 0x80u)) continue;  // aimed at a boundary: stays here
+        const int td = (oy ? sy * HX : 0) + (ox ? sx : 0);
+        if (!((oz ? gt : g1)[td] & 0x80u)) continue;  // aimed at a boundary: stays here
         int v[K];
-        share_get<K>(t.sh[s1][o - 1], c, v);
+        share_at<K>(r1, o, 0, v);
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] -= v[k];
       }
@@ -665,7 +690,8 @@ __device__ __forceinline__ void advect32_block(const LBArgs& a, int bx, int by, 
       // along every nonzero component of q
 #pragma unroll
       for (int qz = -1; qz <= 1; ++qz) {
-        const int ss = qz > 0 ? s0 : (qz < 0 ? s2 : s1);
+        const unsigned char* gs = qz > 0 ? g0 : (qz < 0 ? g2 : g1);
+        const ShareRef<K>& rs = qz > 0 ? r0 : (qz < 0 ? r2 : r1);
 #pragma unroll
         for (int qy = -1; qy <= 1; ++qy) {
 #pragma unroll
@@ -674,11 +700,11 @@ __device__ __forceinline__ void advect32_block(const LBArgs& a, int bx, int by, 
             const unsigned mask = 0x80u | (qx ? 3u : 0u) | (qy ? 12u : 0u) | (qz ? 48u : 0u);
             const unsigned want = 0x80u | (qx > 0 ? 1u : (qx < 0 ? 2u : 0u)) |
                                   (qy > 0 ? 4u : (qy < 0 ? 8u : 0u)) | (qz > 0 ? 16u : (qz < 0 ? 32u : 0u));
-            const int sc = c - qy * HX - qx;
-            if ((t.sg[ss][sc] & mask) != want) continue;
+            const int d = -qy * HX - qx;
+            if ((gs[d] & mask) != want) continue;
             const int cls = (qx ? 1 : 0) | (qy ? 2 : 0) | (qz ? 4 : 0);
             int v[K];
-            share_get<K>(t.sh[ss][cls - 1], sc, v);
+            share_at<K>(rs, cls, d, v);
 #pragma unroll
             for (int k = 0; k < K; ++k) acc[k] += v[k];
           }
