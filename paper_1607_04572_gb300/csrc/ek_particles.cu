@@ -515,16 +515,32 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
   const float frx = (float)(P.pos[0] - cxi), fry = (float)(P.pos[1] - cyi), frz = (float)(P.pos[2] - czi);
   bool touched[4] = {false, false, false, false};
   const int rows = a.fcells / FORCE_T;
-  // cell c of the widened box: coordinates, node, first copy of the node
+  // FP32 form: a thread's cells are rows of FORCE_T apart in the widened
+  // box's x-fastest order, nb rows per step, so their box-local coordinates
+  // advance by a fixed step with carries (no division per cell); the box lies
+  // within one period on either side of the lattice (2R + 6 <= edge), so two
+  // conditional wraps give the node
+  const int ebx = P.ehi[0] - P.elo[0], eby = P.ehi[1] - P.elo[1];
+  const int rstep = nb * FORCE_T;
+  const int sX = rstep % ebx, sY = (rstep / ebx) % eby, sZ = rstep / (ebx * eby);
+  int lX = 0, lY = 0, lZ = 0;  // box-local coordinates of the next cell
+  auto wrap_near = [](int v, int nn) {
+    v = v < 0 ? v + nn : (v >= nn ? v - nn : v);
+    return v < 0 ? v + nn : (v >= nn ? v - nn : v);
+  };
+  // cell c of the widened box (FP32 form: the cell at lX, lY, lZ):
+  // coordinates, node, first copy of the node
   auto locate = [&](int c, int& X, int& Y, int& Z, long long& n, int (&w3)[3], double& mx, double& my,
                     double& mz) {
     if (FM::fp32) {
-      box_coord(c, P.elo, P.ehi, X, Y, Z);
-      w3[0] = wrapi(X, g.nx);
-      w3[1] = wrapi(Y, g.ny);
-      w3[2] = wrapi(Z, g.nz);
-      n = (long long)w3[0] + (long long)g.nx * ((long long)w3[1] + (long long)g.ny * w3[2]);
-      return X - P.elo[0] < g.nx && Y - P.elo[1] < g.ny && Z - P.elo[2] < g.nz;
+      X = P.elo[0] + lX;
+      Y = P.elo[1] + lY;
+      Z = P.elo[2] + lZ;
+      w3[0] = wrap_near(X, g.nx);
+      w3[1] = wrap_near(Y, g.ny);
+      w3[2] = wrap_near(Z, g.nz);
+      n = (long long)(w3[0] + g.nx * (w3[1] + g.ny * w3[2]));
+      return lX < g.nx && lY < g.ny && lZ < g.nz;
     }
     return ext_cell(P, c, g, X, Y, Z, n, mx, my, mz, w3);
   };
@@ -538,6 +554,11 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
   unsigned long long nkey = ~0ULL;
   int cnext = (int)bk.y * FORCE_T + threadIdx.x;
   bool nvalid = cnext < ncell;
+  if (FM::fp32) {
+    lX = cnext % ebx;
+    lY = (cnext / ebx) % eby;
+    lZ = cnext / (ebx * eby);
+  }
   if (nvalid) {
     nfirst = locate(cnext, nX, nY, nZ, nn, nw3, nmx, nmy, nmz);
     nown = a.owner[nn];
@@ -554,6 +575,19 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
     const unsigned long long key = nkey;
     cnext = ((int)bk.y + (k + 1) * nb) * FORCE_T + threadIdx.x;
     nvalid = k + 1 < rows && cnext < ncell;
+    if (FM::fp32) {
+      lX += sX;
+      lY += sY;
+      lZ += sZ;
+      if (lX >= ebx) {
+        lX -= ebx;
+        ++lY;
+      }
+      if (lY >= eby) {
+        lY -= eby;
+        ++lZ;
+      }
+    }
     if (nvalid) {
       nfirst = locate(cnext, nX, nY, nZ, nn, nw3, nmx, nmy, nmz);
       nown = a.owner[nn];
