@@ -31,6 +31,14 @@ __device__ __forceinline__ void box_coord(int c, const int lo[3], const int hi[3
   Z = lo[2] + c / (bx * by);
 }
 
+// periodic coordinate of a widened-box coordinate: the box lies within one
+// period on either side of the lattice (2R + 6 <= edge, margin ceil(R) + 4),
+// so v is in [-2n, 3n) and two conditional wraps replace a modulo
+__device__ __forceinline__ int wrap_box(int v, int n) {
+  v = v < 0 ? v + n : (v >= n ? v - n : v);
+  return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
 __device__ __forceinline__ long long node_of(int X, int Y, int Z, const Grid& g) {
   return (long long)wrapi(X, g.nx) +
          (long long)g.nx * ((long long)wrapi(Y, g.ny) + (long long)g.ny * wrapi(Z, g.nz));
@@ -365,7 +373,7 @@ __device__ __forceinline__ void force_assign_body(const PartArgs& a, const Blk b
   if (c >= box_cells(P.elo, P.ehi)) return;
   int X, Y, Z;
   box_coord(c, P.elo, P.ehi, X, Y, Z);  // a repeated node gets the same key
-  const int x = wrapi(X, a.g.nx), y = wrapi(Y, a.g.ny), z = wrapi(Z, a.g.nz);
+  const int x = wrap_box(X, a.g.nx), y = wrap_box(Y, a.g.ny), z = wrap_box(Z, a.g.nz);
   const long long n = (long long)x + (long long)a.g.nx * ((long long)y + (long long)a.g.ny * z);
   auto off = [](int v, int ip, float fr, int nn) {
     const float hn = 0.5f * (float)nn;
@@ -517,17 +525,12 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
   const int rows = a.fcells / FORCE_T;
   // FP32 form: a thread's cells are rows of FORCE_T apart in the widened
   // box's x-fastest order, nb rows per step, so their box-local coordinates
-  // advance by a fixed step with carries (no division per cell); the box lies
-  // within one period on either side of the lattice (2R + 6 <= edge), so two
-  // conditional wraps give the node
+  // advance by a fixed step with carries (no division per cell); wrap_box
+  // gives the node
   const int ebx = P.ehi[0] - P.elo[0], eby = P.ehi[1] - P.elo[1];
   const int rstep = nb * FORCE_T;
   const int sX = rstep % ebx, sY = (rstep / ebx) % eby, sZ = rstep / (ebx * eby);
   int lX = 0, lY = 0, lZ = 0;  // box-local coordinates of the next cell
-  auto wrap_near = [](int v, int nn) {
-    v = v < 0 ? v + nn : (v >= nn ? v - nn : v);
-    return v < 0 ? v + nn : (v >= nn ? v - nn : v);
-  };
   // cell c of the widened box (FP32 form: the cell at lX, lY, lZ):
   // coordinates, node, first copy of the node
   auto locate = [&](int c, int& X, int& Y, int& Z, long long& n, int (&w3)[3], double& mx, double& my,
@@ -536,9 +539,9 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
       X = P.elo[0] + lX;
       Y = P.elo[1] + lY;
       Z = P.elo[2] + lZ;
-      w3[0] = wrap_near(X, g.nx);
-      w3[1] = wrap_near(Y, g.ny);
-      w3[2] = wrap_near(Z, g.nz);
+      w3[0] = wrap_box(X, g.nx);
+      w3[1] = wrap_box(Y, g.ny);
+      w3[2] = wrap_box(Z, g.nz);
       n = (long long)(w3[0] + g.nx * (w3[1] + g.ny * w3[2]));
       return lX < g.nx && lY < g.ny && lZ < g.nz;
     }
@@ -939,8 +942,14 @@ __device__ void integrate_all(const PartArgs& a) {
           vel = vel + F / Pp->mass;
           omega = omega + T / Pp->inertia;
           pos = pos + vel;
-          if (pos >= (double)nn) pos -= (double)nn;
-          else if (pos < 0.0) pos += (double)nn;
+          // into [0, n): one period at any sane speed; a step longer than a
+          // period is wrapped all the same, so that every box stays within one
+          // period of the lattice (the cell kernels rely on it)
+          if (pos >= (double)nn || pos < 0.0) {
+            pos -= floor(pos / (double)nn) * (double)nn;
+            if (pos < 0.0) pos += (double)nn;  // the quotient rounded up
+            if (pos >= (double)nn) pos -= (double)nn;
+          }
           if (!isfinite(pos)) atomicOr(a.status, ST_NONFINITE);
         }
         Pp->force[d] = F;
