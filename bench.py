@@ -60,9 +60,10 @@ def describe(w):
 
 
 # Algorithmic bytes per lattice node of the fused flux + LB kernel: what the
-# stage must read and write once per step by the method's own state (SURVEY's
-# per-node items that S2 touches): populations read + written, species read and
-# written after the flux divergence, Psi and the node class, Phi.  The u,
+# stage must read and write once per step by the method's own state (the items
+# of the step's per-node byte budget that S2 touches): populations read +
+# written, species read and written after the flux divergence, Psi and the
+# node class, Phi.  The u,
 # internal-force and sign-byte writes it also makes (for S3 and S4) are
 # implementation overhead and count against the fraction.
 def lb_bytes_per_node(fp32, K):
