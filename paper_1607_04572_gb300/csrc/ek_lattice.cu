@@ -235,7 +235,7 @@ __device__ __forceinline__ void block_sum3(double (&v)[3], double* ipart) {
 }
 
 template <int K, bool PV>
-__global__ void __launch_bounds__(256) k_lb_fused(LBArgs a) {
+__global__ void __launch_bounds__(256, 2) k_lb_fused(LBArgs a) {
   const int x = blockIdx.x * TILE_X + threadIdx.x;
   const int y = blockIdx.y * TILE_Y + threadIdx.y;
   const int z = blockIdx.z;

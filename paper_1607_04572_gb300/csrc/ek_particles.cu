@@ -72,8 +72,6 @@ __device__ __forceinline__ int classify(double cx, double cy, double cz, double 
   return CUBE_UNDECIDED;
 }
 
-constexpr int PSI_DEPTH = 4;
-
 // Single-precision pre-test of classify().  (ox, oy, oz) is the cube centre
 // relative to the sphere centre in float: the centre relative to the sphere
 // centre's integer part (exact: an integer plus dyadic offsets) minus the
