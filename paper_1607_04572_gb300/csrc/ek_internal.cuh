@@ -342,9 +342,10 @@ cudaError_t lb32_prepare();  // once per process, before the first launch_lb32
 int lb32_segments(const Grid& g, int K, bool pv);
 cudaError_t launch_lb32(const LBArgs& a, cudaStream_t s);
 cudaError_t launch_advection32(const LBArgs& a, cudaStream_t s);
-// z segments per tile column of the FP32 S3 grid: 16-plane segments where
-// the grid still has two waves of blocks (`wide`: the launch is shared with
-// other systems, so its size does not depend on this machine), else 8, else 4
+// z segments per tile column of the FP32 S3 grid: 32-plane segments on
+// large boxes, 16 where the grid still fills the SMs (`wide`: the launch is
+// shared with other systems, so its size does not depend on this machine: 16),
+// else 8, else 4
 int adv32_segments(const Grid& g, bool wide);
 // the same S2 and S3 for the systems of a batch (all FP32 with the same K and
 // partial-volume choice), one launch each; the per-system grids (gx, gy) that

@@ -469,126 +469,100 @@ __global__ void __launch_bounds__(256, 2) k_lb32_batch(const LBBatchEntry* __res
   lb32_block<K, PV>(e.a, e.c, b.x, b.y % yt, b.y / yt, b.x + (long long)b.nx * b.y);
 }
 
-// share of the cell displaced by velocity (vx, vy, vz) that lands at offset
-// (ox, oy, oz) in {0, sign(v_a)}^3; identical operations in the source and the
-// destination thread
-__device__ __forceinline__ float vof_share(float vx, float vy, float vz, int ox, int oy, int oz) {
-  const float wx = ox ? fabsf(vx) : __fsub_rn(1.0f, fabsf(vx));
-  const float wy = oy ? fabsf(vy) : __fsub_rn(1.0f, fabsf(vy));
-  const float wz = oz ? fabsf(vz) : __fsub_rn(1.0f, fabsf(vz));
-  return __fmul_rn(__fmul_rn(wx, wy), wz);
+// sign code (bits 0-1 of c >> shift) as -1, 0, +1
+__device__ __forceinline__ int sign_of(unsigned c, int shift) {
+  const unsigned v = (c >> shift) & 3u;
+  return v == 1u ? 1 : (v == 2u ? -1 : 0);
 }
 
-__device__ __forceinline__ int sgnf(float v) { return v > 0.0f ? 1 : (v < 0.0f ? -1 : 0); }
+// ---------------------------------------------------------------------------
+// S3 (FP32 form), tiled push.  A 32 x 8 block marches through a segment of
+// planes of its (x, y) tile column.  The cell of a fluid node displaced by its
+// velocity v (Eq. 15's volume-of-fluid advection) overlaps the node itself
+// and the offsets {0, sign(v_a)}^3 \ 0; the share landing at offset o is
+// rho_k prod_a (o_a ? |v_a| : 1 - |v_a|), quantised to integer units.  Every
+// node of the tile and its one-node halo adds the shares it sends into
+// shared-memory accumulators of the receiving positions (integer atomics:
+// the sums do not depend on the order), and every node of the tile takes
+// from its own accumulator the shares it sends to fluid nodes (a share aimed
+// at a boundary node stays where it is).  A plane is complete once the
+// planes on both sides have pushed; its nodes then add their accumulator to
+// S2's result.  A share is computed by the same operations in every block
+// that holds its source, so a source's loss and its destination's gain are
+// the same integers and the species totals do not change.
+// ---------------------------------------------------------------------------
+constexpr int AW = HX + 2, AH = HY + 2;  // accumulator plane: the halo tile with a margin of one
+constexpr int AP = AW * AH;
+constexpr int HALO = HP - TN;            // halo nodes of a tile plane
 
-// ---------------------------------------------------------------------------
-// S3 (FP32 form), tiled.  A 32 x 8 block marches through a segment of planes
-// of its (x, y) tile column.  For every source plane it first computes, for
-// each node of the tile and its one-node halo, the integer shares of each
-// species that the node's volume-of-fluid displacement sends to the seven
-// offsets {0, sign(v_a)}^3 \ 0 (a shared-memory ring of three planes, with
-// the nodes' sign bytes from S2); then every fluid node of the middle plane
-// subtracts its own shares aimed at fluid nodes and adds the shares its 26
-// neighbours aim at it.  A share is computed by the same operations in every
-// block that holds its source, so a source's loss and its destination's gain
-// are the same integers and the species totals do not change.
-// ---------------------------------------------------------------------------
 template <int K>
 struct AdvRing {
-  // shares by class (ox | oy << 1 | oz << 2) - 1; per class row the nodes'
-  // species 0 and 1 as pairs, then species 2 and 3 as pairs (K = 4) or
-  // single values (K = 3), so that a node's shares are one or two vector
-  // accesses
-  int sh[3][7][HP * K];
-  unsigned char sg[3][HP];   // sign byte of S2: bit 7 fluid, sign codes of u
+  int acc[4][K > 0 ? K : 1][AP];  // shares received minus shares sent, plane p in slot p & 3
+  unsigned char sg[4][HP];        // sign bytes of S2 (bit 7 fluid, sign codes of u), slot p & 3
 };
-
-// a slot's shares as seen from node c: row 0 at node c (the pair of species
-// 0 and 1, or the single species) and at its species 2 (and 3); the shares of
-// class cls of the node at offset d from c are then at compile-time offsets
-template <int K>
-struct ShareRef {
-  const int* lo;
-  const int* hi;
-};
-template <int K>
-__device__ __forceinline__ ShareRef<K> share_ref(const int* row0, int c) {
-  ShareRef<K> r;
-  r.lo = K == 1 ? row0 + c : row0 + 2 * c;
-  r.hi = K == 3 ? row0 + 2 * HP + c : (K == 4 ? row0 + 2 * HP + 2 * c : row0);
-  return r;
-}
-template <int K>
-__device__ __forceinline__ void share_at(const ShareRef<K>& r, int cls, int d, int (&v)[K]) {
-  constexpr int ROW = HP * K;
-  if constexpr (K == 1) {
-    v[0] = r.lo[(cls - 1) * ROW + d];
-  } else {
-    const int2 w = *reinterpret_cast<const int2*>(r.lo + (cls - 1) * ROW + 2 * d);
-    v[0] = w.x;
-    v[1] = w.y;
-    if constexpr (K == 3) v[2] = r.hi[(cls - 1) * ROW + d];
-    if constexpr (K == 4) {
-      const int2 w2 = *reinterpret_cast<const int2*>(r.hi + (cls - 1) * ROW + 2 * d);
-      v[2] = w2.x;
-      v[3] = w2.y;
-    }
-  }
-}
-
-// the K shares of node e into a class row
-template <int K>
-__device__ __forceinline__ void share_put(int* row, int e, const int (&v)[K]) {
-  if constexpr (K == 1) {
-    row[e] = v[0];
-  } else {
-    reinterpret_cast<int2*>(row)[e] = make_int2(v[0], v[1]);
-    if constexpr (K == 3) row[2 * HP + e] = v[2];
-    if constexpr (K == 4) reinterpret_cast<int2*>(row + 2 * HP)[e] = make_int2(v[2], v[3]);
-  }
-}
 
 template <int K>
 constexpr size_t adv32_smem() { return sizeof(AdvRing<K>); }
 
+// the sources of a thread: 0 its own node of the tile, 1 the halo node with
+// the thread's index (threads below HALO): the top row, the bottom row, then
+// the left and the right column of the halo.  Halo-tile index e (stride HX),
+// accumulator index (stride AW, one further in from the margin) and the
+// in-plane offset of the node in the box (-1: none).
+struct AdvPos {
+  int e[2], pos[2], hoff[2];
+};
+__device__ __forceinline__ AdvPos adv_positions(int x0, int y0, const LBArgs& a) {
+  const int tid = threadIdx.x + TILE_X * threadIdx.y;
+  int ex[2] = {(int)threadIdx.x + 1, 0}, ey[2] = {(int)threadIdx.y + 1, 0};
+  if (tid < HX) {
+    ex[1] = tid;
+  } else if (tid < 2 * HX) {
+    ex[1] = tid - HX;
+    ey[1] = HY - 1;
+  } else if (tid < 2 * HX + TILE_Y) {
+    ey[1] = tid - 2 * HX + 1;
+  } else {
+    ex[1] = HX - 1;
+    ey[1] = tid - 2 * HX - TILE_Y + 1;
+  }
+  AdvPos p;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    p.e[q] = ex[q] + HX * ey[q];
+    p.pos[q] = ex[q] + 1 + AW * (ey[q] + 1);
+    p.hoff[q] = q == 0 || tid < HALO
+                    ? halo_wrap(x0 - 1 + ex[q], a.g.nx) + a.g.nx * halo_wrap(y0 - 1 + ey[q], a.g.ny)
+                    : -1;
+  }
+  return p;
+}
 
-// the sign bytes, velocities and species of a source plane's halo-tile
-// nodes held by one thread (up to two nodes), loaded one plane ahead of use
+// the sign bytes, velocities and species of a thread's sources in one plane,
+// loaded one plane ahead of use
 template <int K>
 struct AdvSrc {
-  static constexpr int PER = (HP + TN - 1) / TN;
-  unsigned sgn[PER];
-  float v[PER][3];
-  int r[PER][K];
+  unsigned sgn[2];
+  float v[2][3];
+  int r[2][K > 0 ? K : 1];
 };
 
-// in-plane offsets of the thread's halo-tile nodes (-1: none)
-template <int K>
-__device__ __forceinline__ void adv_offsets(int (&hoff)[AdvSrc<K>::PER], int x0, int y0, const LBArgs& a) {
-  const int tid = threadIdx.x + TILE_X * threadIdx.y;
-#pragma unroll
-  for (int q = 0; q < AdvSrc<K>::PER; ++q) {
-    const int e = tid + q * TN;
-    const int ey = e / HX, ex = e - ey * HX;
-    hoff[q] = e < HP ? halo_wrap(x0 - 1 + ex, a.g.nx) + a.g.nx * halo_wrap(y0 - 1 + ey, a.g.ny) : -1;
-  }
+__device__ __forceinline__ int wrap_plane(int zz, int nz) {
+  return zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
 }
 
 template <int K>
-__device__ __forceinline__ void adv_load(AdvSrc<K>& R, const int (&hoff)[AdvSrc<K>::PER], int zz,
-                                         const LBArgs& a) {
-  const int nz = a.g.nz;
+__device__ __forceinline__ void adv_load(AdvSrc<K>& R, const AdvPos& P, int zz, const LBArgs& a) {
   const int N = (int)a.g.N;
-  const int z = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
-  const int pz = a.g.nx * a.g.ny * z;
+  const int pz = a.g.nx * a.g.ny * wrap_plane(zz, a.g.nz);
   const float* __restrict__ ux = (const float*)a.u;
   const float* __restrict__ uy = ux + N;
   const float* __restrict__ uz = uy + N;
 #pragma unroll
-  for (int q = 0; q < AdvSrc<K>::PER; ++q) {
+  for (int q = 0; q < 2; ++q) {
     R.sgn[q] = 0u;
-    if (hoff[q] >= 0) {
-      const int m = hoff[q] + pz;
+    if (P.hoff[q] >= 0) {
+      const int m = P.hoff[q] + pz;
       R.sgn[q] = a.vsig[m];
       R.v[q][0] = ux[m];
       R.v[q][1] = uy[m];
@@ -599,31 +573,69 @@ __device__ __forceinline__ void adv_load(AdvSrc<K>& R, const int (&hoff)[AdvSrc<
   }
 }
 
-// the loaded plane's shares into ring slot `slot`
+__device__ __forceinline__ void adv_sign(unsigned (&s)[2], const AdvPos& P, int zz, const LBArgs& a) {
+  const int pz = a.g.nx * a.g.ny * wrap_plane(zz, a.g.nz);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) s[q] = P.hoff[q] >= 0 ? a.vsig[P.hoff[q] + pz] : 0u;
+}
+
 template <int K>
-__device__ __forceinline__ void adv_store(AdvRing<K>& t, int slot, const AdvSrc<K>& R) {
-  const int tid = threadIdx.x + TILE_X * threadIdx.y;
+__device__ __forceinline__ void adv_sign_put(AdvRing<K>& t, int zz, const AdvPos& P, const unsigned (&s)[2]) {
 #pragma unroll
-  for (int q = 0; q < AdvSrc<K>::PER; ++q) {
-    const int e = tid + q * TN;
-    if (e >= HP) continue;
-    t.sg[slot][e] = (unsigned char)R.sgn[q];
-    if (!(R.sgn[q] & 0x80u)) continue;  // never a source: nothing reads its shares
+  for (int q = 0; q < 2; ++q)
+    if (P.hoff[q] >= 0) t.sg[zz & 3][P.e[q]] = (unsigned char)s[q];
+}
+
+// source q of plane p: its shares added at the receiving positions; a node of
+// the tile (OWN) also takes from its own accumulator the shares it sends to
+// fluid nodes.  The share of offset o is the same product, in the same order,
+// wherever it is computed: (w_x w_y) w_z with w_a = |v_a| or 1 - |v_a|.
+template <int K, bool OWN>
+__device__ __forceinline__ void adv_push(AdvRing<K>& t, int p, const AdvPos& P, const AdvSrc<K>& R, int q) {
+  const unsigned s = R.sgn[q];
+  if (!(s & 0x80u)) return;  // not a fluid node: sends nothing
+  const int sx = sign_of(s, 0), sy = sign_of(s, 2), sz = sign_of(s, 4);
+  const float ax = fabsf(R.v[q][0]), ay = fabsf(R.v[q][1]), az = fabsf(R.v[q][2]);
+  const float bx = __fsub_rn(1.0f, ax), by = __fsub_rn(1.0f, ay), bz = __fsub_rn(1.0f, az);
+  const float wxy[4] = {__fmul_rn(bx, by), __fmul_rn(ax, by), __fmul_rn(bx, ay), __fmul_rn(ax, ay)};
+  float rf[K > 0 ? K : 1];
 #pragma unroll
-    for (int o = 1; o < 8; ++o) {
-      const float frac = vof_share(R.v[q][0], R.v[q][1], R.v[q][2], o & 1, (o >> 1) & 1, o >> 2);
-      int v[K];
+  for (int k = 0; k < K; ++k) rf[k] = (float)R.r[q][k];
+  // a share whose offset has a component where v has none is zero: it adds
+  // nothing wherever it lands
+  int* const a0 = &t.acc[p & 3][0][P.pos[q]];
+  int* const a1 = &t.acc[(p + sz) & 3][0][P.pos[q]];
+  const unsigned char* const f0 = &t.sg[p & 3][P.e[q]];
+  const unsigned char* const f1 = &t.sg[(p + sz) & 3][P.e[q]];
+  const int dy = sy * AW, fy = sy * HX;
+  int net[K > 0 ? K : 1];
 #pragma unroll
-      for (int k = 0; k < K; ++k) v[k] = __float2int_rn(__fmul_rn((float)R.r[q][k], frac));
-      share_put<K>(t.sh[slot][o - 1], e, v);
+  for (int k = 0; k < K; ++k) net[k] = 0;
+#pragma unroll
+  for (int o = 1; o < 8; ++o) {
+    const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+    const float frac = __fmul_rn(wxy[o & 3], oz ? az : bz);
+    int* const dst = (oz ? a1 : a0) + (ox ? sx : 0) + (oy ? dy : 0);
+    bool fl = false;
+    if (OWN) fl = ((oz ? f1 : f0)[(ox ? sx : 0) + (oy ? fy : 0)] & 0x80u) != 0u;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int v = __float2int_rn(__fmul_rn(rf[k], frac));
+      atomicAdd(dst + k * AP, v);
+      if (OWN && fl) net[k] += v;
     }
+  }
+  if (OWN) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) atomicAdd(a0 + k * AP, -net[k]);
   }
 }
 
-// sign code (bits 0-1 of c >> shift) as -1, 0, +1
-__device__ __forceinline__ int sign_of(unsigned c, int shift) {
-  const unsigned v = (c >> shift) & 3u;
-  return v == 1u ? 1 : (v == 2u ? -1 : 0);
+template <int K>
+__device__ __forceinline__ void adv_zero(AdvRing<K>& t, int slot) {
+  int4* z = reinterpret_cast<int4*>(&t.acc[slot][0][0]);
+  const int tid = threadIdx.x + TILE_X * threadIdx.y;
+  for (int i = tid; i < K * AP / 4; i += TN) z[i] = make_int4(0, 0, 0, 0);
 }
 
 template <int K>
@@ -636,84 +648,61 @@ __device__ __forceinline__ void advect32_block(const LBArgs& a, int bx, int by, 
   const int z0 = (int)((long long)bz * nz / nseg);
   const int zend = (int)((long long)(bz + 1) * nz / nseg);
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  const int tid = threadIdx.x + TILE_X * threadIdx.y;
   const bool in_xy = x < nx && y < ny;
-  const int c = (threadIdx.y + 1) * HX + threadIdx.x + 1;  // the node's halo-tile index
-  int* nout[K];
+  const bool halo = tid < HALO;
+  int* nout[K > 0 ? K : 1];
 #pragma unroll
   for (int k = 0; k < K; ++k) nout[k] = (int*)a.rho_out + (size_t)k * N;
-  // ring slot of plane zz: (zz - z0 + 1) mod 3; the sources of plane z + 2
-  // are loaded while plane z is summed
+  const AdvPos P = adv_positions(x0, y0, a);
   AdvSrc<K> R;
-  int hoff[AdvSrc<K>::PER];
-  adv_offsets<K>(hoff, x0, y0, a);
-  adv_load<K>(R, hoff, z0 - 1, a);
-  adv_store<K>(t, 0, R);
-  adv_load<K>(R, hoff, z0, a);
-  adv_store<K>(t, 1, R);
-  adv_load<K>(R, hoff, z0 + 1, a);
+  unsigned sgn[2];
+  // Plane z is complete when planes z - 1, z and z + 1 have pushed; a push of
+  // plane p needs the sign bytes of planes p - 1 .. p + 1 (the fluid test of
+  // the receiving nodes).  Before the loop: all slots zero, the sign bytes of
+  // planes z0 - 1 .. z0 + 1, pushes of planes z0 - 1 (only its shares into
+  // plane z0 count) and z0.
+  for (int s = 0; s < 4; ++s) adv_zero<K>(t, s);
+  for (int i = tid; i < 4 * HP; i += TN) (&t.sg[0][0])[i] = 0;
+  __syncthreads();
+  for (int zz = z0 - 1; zz <= z0 + 1; ++zz) {
+    adv_sign(sgn, P, zz, a);
+    adv_sign_put<K>(t, zz, P, sgn);
+  }
+  adv_load<K>(R, P, z0 - 1, a);
+  __syncthreads();
+  adv_push<K, true>(t, z0 - 1, P, R, 0);
+  if (halo) adv_push<K, false>(t, z0 - 1, P, R, 1);
+  adv_load<K>(R, P, z0, a);
+  __syncthreads();
+  adv_zero<K>(t, (z0 - 2) & 3);  // the slot of plane z0 + 2: planes z0 - 2's shares
+  adv_push<K, true>(t, z0, P, R, 0);
+  if (halo) adv_push<K, false>(t, z0, P, R, 1);
+  adv_load<K>(R, P, z0 + 1, a);
+  adv_sign(sgn, P, z0 + 2, a);
+  const int c = (threadIdx.y + 1) * HX + threadIdx.x + 1;        // the node's halo-tile index
+  const int pc = threadIdx.x + 2 + AW * (threadIdx.y + 2);       // and accumulator index
   for (int z = z0; z < zend; ++z) {
-    const int s0 = (z - z0) % 3, s1 = (z - z0 + 1) % 3, s2 = (z - z0 + 2) % 3;
     const int n = x + nx * (y + ny * z);
-    int acc[K];
+    int s2[K > 0 ? K : 1];
     if (in_xy) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc[k] = nout[k][n];  // S2's result, issued early
+      for (int k = 0; k < K; ++k) s2[k] = nout[k][n];  // S2's result, issued early
     }
-    adv_store<K>(t, s2, R);
-    if (z + 2 <= zend) adv_load<K>(R, hoff, z + 2, a);
-    __syncthreads();
-    const unsigned own = in_xy ? t.sg[s1][c] : 0u;
-    if (own & 0x80u) {
-      // the three planes' sign bytes and shares as seen from this node, so
-      // that every access below is a base plus a compile-time offset
-      const unsigned char* g0 = &t.sg[s0][c];
-      const unsigned char* g1 = &t.sg[s1][c];
-      const unsigned char* g2 = &t.sg[s2][c];
-      const ShareRef<K> r0 = share_ref<K>(t.sh[s0][0], c);
-      const ShareRef<K> r1 = share_ref<K>(t.sh[s1][0], c);
-      const ShareRef<K> r2 = share_ref<K>(t.sh[s2][0], c);
-      // own shares to the offsets {0, sign(v_a)}^3 \ 0 whose node is fluid
-      const int sx = sign_of(own, 0), sy = sign_of(own, 2), sz = sign_of(own, 4);
-      const unsigned char* gt = sz > 0 ? g2 : (sz < 0 ? g0 : g1);
-#pragma unroll
-      for (int o = 1; o < 8; ++o) {
-        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-        if ((ox && !sx) || (oy && !sy) || (oz && !sz)) continue;
-        const int td = (oy ? sy * HX : 0) + (ox ? sx : 0);
-        if (!((oz ? gt : g1)[td] & 0x80u)) continue;  // aimed at a boundary: stays here
-        int v[K];
-        share_at<K>(r1, o, 0, v);
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] -= v[k];
-      }
-      // shares of the neighbour at -q: fluid and moving towards this node
-      // along every nonzero component of q
-#pragma unroll
-      for (int qz = -1; qz <= 1; ++qz) {
-        const unsigned char* gs = qz > 0 ? g0 : (qz < 0 ? g2 : g1);
-        const ShareRef<K>& rs = qz > 0 ? r0 : (qz < 0 ? r2 : r1);
-#pragma unroll
-        for (int qy = -1; qy <= 1; ++qy) {
-#pragma unroll
-          for (int qx = -1; qx <= 1; ++qx) {
-            if (!qx && !qy && !qz) continue;
-            const unsigned mask = 0x80u | (qx ? 3u : 0u) | (qy ? 12u : 0u) | (qz ? 48u : 0u);
-            const unsigned want = 0x80u | (qx > 0 ? 1u : (qx < 0 ? 2u : 0u)) |
-                                  (qy > 0 ? 4u : (qy < 0 ? 8u : 0u)) | (qz > 0 ? 16u : (qz < 0 ? 32u : 0u));
-            const int d = -qy * HX - qx;
-            if ((gs[d] & mask) != want) continue;
-            const int cls = (qx ? 1 : 0) | (qy ? 2 : 0) | (qz ? 4 : 0);
-            int v[K];
-            share_at<K>(rs, cls, d, v);
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc[k] += v[k];
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < K; ++k) nout[k][n] = acc[k];
+    adv_sign_put<K>(t, z + 2, P, sgn);
+    __syncthreads();  // the sign bytes of plane z + 2; slot z + 2 zero
+    adv_push<K, true>(t, z + 1, P, R, 0);
+    if (halo) adv_push<K, false>(t, z + 1, P, R, 1);
+    if (z + 1 < zend) {
+      adv_load<K>(R, P, z + 2, a);
+      adv_sign(sgn, P, z + 3, a);
     }
-    __syncthreads();  // the next plane's shares overwrite slot s0
+    __syncthreads();  // plane z complete
+    if (in_xy && (t.sg[z & 3][c] & 0x80u)) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) nout[k][n] = s2[k] + t.acc[z & 3][k][pc];
+    }
+    adv_zero<K>(t, (z - 1) & 3);  // the slot of plane z + 3
   }
 }
 
@@ -896,15 +885,19 @@ void lb32_batch_grid(const LBArgs& a, int& gx, int& gy) {
   gy = (int)(g.y * g.z);
 }
 
+// Planes per S3 segment.  Every segment pushes the plane on each side of it
+// as well, so long segments waste less; short ones give the block scheduler
+// enough blocks to balance the SMs (five blocks of 256 threads fit on one).
+// Measured on GB300 (ms per launch): 128^3 4/8/16/32 planes 0.041, 0.038,
+// 0.037, 0.053; 256^3 (K = 3) 0.341, 0.287, 0.262, 0.265; 512^3 1.99, 1.64,
+// 1.48, 1.40.  A batch launch (wide) holds many systems: 16 planes.
 int adv32_segments(const Grid& g, bool wide) {
   const long long cols = (long long)((g.nx + TILE_X - 1) / TILE_X) * ((g.ny + TILE_Y - 1) / TILE_Y);
+  auto blocks = [&](int p) { return cols * ((g.nz + p - 1) / p); };
   int planes = 4;
-  for (int p : {16, 8}) {
-    if (wide || cols * ((g.nz + p - 1) / p) >= 2 * 152 * 3) {
-      planes = p;
-      break;
-    }
-  }
+  if (!wide && blocks(32) >= 8192) planes = 32;
+  else if (wide || blocks(16) >= 3 * 152) planes = 16;
+  else if (blocks(8) >= 3 * 152) planes = 8;
   return std::max(1, (g.nz + planes - 1) / planes);
 }
 
