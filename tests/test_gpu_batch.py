@@ -181,3 +181,65 @@ def test_grid_barrier_wait_is_bounded_and_reported(gpu_lib):
     s.step(3)
     p = s.get_particles()[0]
     assert np.all(np.isfinite(p["pos"]))
+
+
+def _oracle_members(ek, ws, flags):
+    from oracle import ek_oracle as O  # noqa: F401  (the pairs helper builds both sides)
+    from pairs import make_pair
+    return [make_pair(ek, w, flags=flags, perturb=0.0) for w in ws]
+
+
+def test_batch_members_match_oracle_fp64(gpu_lib):
+    """Three ensemble members (ragged boxes of edges 16..32, one sphere each,
+    their own salt, charge and field) in the FP64 form, advanced by the batch,
+    against the FP64 oracle stepped member by member: every field at the
+    parity tolerance of the single-system path (1e-11)."""
+    from pairs import compare as oracle_compare
+    ek = gpu_lib
+    ws = workloads.batch_ensemble(3, seed=81, edges=(16, 24, 32), radius=(2.5, 4.0),
+                                  charge=(-30.0, -10.0), bulk=(1e-3, 1e-2))
+    pairs = _oracle_members(ek, ws, ek.EK_PV | ek.EK_NEUTRALIZE)
+    b = ek.EKBatch([s for _, s in pairs])
+    b.step(3)
+    b.step(4)
+    for o, s in pairs:
+        o.step(7)
+        oracle_compare(ek, o, s)
+    b.close()
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_batch_members_match_oracle_fp32_fused(gpu_lib, form):
+    """Three FP32-form members on the fused batch path (edges 32 and 48 take
+    the batched S1 passes; form 2 runs the particle kernels as persistent
+    launches with grid barriers) against the FP64 oracle: boundary flags and
+    Psi exactly, species and Phi per element within 2e-4 (floor 1e-3 of the
+    field's max), fluid populations within 1e-5, the particle within 1e-6 in
+    position and 2e-3 of its speed in velocity."""
+    from pairs import perm_to_oracle, rel_err
+    from oracle import ek_oracle as O
+    ek = gpu_lib
+    ws = workloads.batch_ensemble(3, seed=82, edges=(32, 48), radius=(2.5, 4.0),
+                                  charge=(-30.0, -10.0), bulk=(1e-3, 1e-2))
+    pairs = _oracle_members(ek, ws, ek.EK_PV | ek.EK_NEUTRALIZE | FP32)
+    b = ek.EKBatch([s for _, s in pairs])
+    b.set_config(fused=form)
+    assert b.config()["fused"] == form
+    b.step(3)
+    b.step(4)
+    perm = perm_to_oracle(ek)
+    for i, (o, s) in enumerate(pairs):
+        o.step(7)
+        assert np.array_equal(s.get_fields(ek.FIELD_OWNER), o.owner.astype(float)), i
+        fluid = o.owner == O.FLUID
+        for k in range(o.K):
+            assert rel_err(s.get_fields(ek.FIELD_SPECIES, k), o.rho[k]) < 2e-4, (i, k)
+        fg = s.get_fields(ek.FIELD_POPULATIONS)[perm]
+        assert rel_err(fg[:, fluid], o.f[:, fluid]) < 1e-5, i
+        assert rel_err(s.get_fields(ek.FIELD_PHI), o.phi) < 2e-4, i
+        assert rel_err(s.get_fields(ek.FIELD_PSI), o.psi) == 0.0, i
+        p = s.get_particles()[0]
+        assert np.max(np.abs(p["pos"] - o.particles[0].pos)) < 1e-6, i
+        vmax = np.max(np.abs(o.particles[0].vel))
+        assert np.max(np.abs(p["vel"] - o.particles[0].vel)) < 2e-3 * vmax, i
+    b.close()
