@@ -103,8 +103,8 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per lattice node
 # of one launch of the kernel, from an ncu capture, valid only for the kernel
 # source it was taken on (otherwise the traffic is reported as null).
-TRAFFIC = {"k_lb32": {"bytes_per_node": (202443520 + 178695680) / 128 ** 3,
-                      "source_sha": "3969c454e9dca646", "file": "ek_lattice32.cu"}}
+TRAFFIC = {"k_lb32": {"bytes_per_node": (202409472 + 178517504) / 128 ** 3,
+                      "source_sha": "b124e8565c46b3fd", "file": "ek_lattice32.cu"}}
 
 
 def src_sha(name: str) -> str:

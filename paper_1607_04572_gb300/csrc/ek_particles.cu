@@ -178,22 +178,8 @@ __device__ __forceinline__ double psi_sum(const DevParticle& P) {
   return (double)u / (double)PSI_UNITS;
 }
 
-// relative (float) and exact (double) centre of sub-cube `path` at level l of
-// the cell centred at (X, Y, Z); path holds 3 bits per level, level 1 highest
-__device__ __forceinline__ void subcube_centre_f(int path, int l, float ox, float oy, float oz,
-                                                 float& cx, float& cy, float& cz) {
-  cx = ox;
-  cy = oy;
-  cz = oz;
-  for (int m = 1; m <= l; ++m) {
-    const int bits = (path >> (3 * (l - m))) & 7;
-    const float hm = ldexpf(1.0f, -(m + 1));
-    cx += (bits & 1) ? hm : -hm;
-    cy += (bits & 2) ? hm : -hm;
-    cz += (bits & 4) ? hm : -hm;
-  }
-}
-
+// exact (double) centre of sub-cube `path` at level l of the cell centred
+// at (X, Y, Z); path holds 3 bits per level, level 1 highest
 __device__ __forceinline__ void subcube_centre_d(int path, int l, double X, double Y, double Z,
                                                  double& cx, double& cy, double& cz) {
   cx = X;
@@ -553,6 +539,19 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
   bool nfirst = false;
   int nown = FLUID;
   unsigned long long nkey = ~0ULL;
+  // FP32 form: the internal force of the next cell too (most cells of a
+  // widened box are the particle's own), so no load waits on the key
+  float nif[3] = {0.0f, 0.0f, 0.0f};
+  const float* const ifl = (const float*)a.ifield;
+  auto fetch = [&]() {
+    nown = a.owner[nn];
+    nkey = a.fkey[nn];
+    if (FM::fp32) {
+      nif[0] = ifl[nn];
+      nif[1] = ifl[N + nn];
+      nif[2] = ifl[2 * N + nn];
+    }
+  };
   int cnext = (int)bk.y * FORCE_T + threadIdx.x;
   bool nvalid = cnext < ncell;
   if (FM::fp32) {
@@ -562,9 +561,16 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
   }
   if (nvalid) {
     nfirst = locate(cnext, nX, nY, nZ, nn, nw3, nmx, nmy, nmz);
-    nown = a.owner[nn];
-    nkey = a.fkey[nn];
+    fetch();
   }
+  // Links into the sphere start at fluid nodes within R + sqrt(2) of the
+  // centre (a covered node lies within R); the test below takes R + 1.5.  The
+  // box offsets X - r_p it measures are the minimum-image ones for every
+  // linked node once each edge is at least 2 R + 4 (a box cell lies within
+  // R + 2 of the centre along each axis); smaller lattices test every cell.
+  const bool gate = 2.0 * P.radius + 4.0 <= (double)min(g.nx, min(g.ny, g.nz));
+  const double rlink = P.radius + 1.5;
+  const float rlink2f = (float)(rlink * rlink);
   for (int k = 0; k < rows; ++k) {
     if (!nvalid) break;
     const int X = nX, Y = nY, Z = nZ;
@@ -574,6 +580,7 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
     const bool first = nfirst;
     const int own = nown;
     const unsigned long long key = nkey;
+    const float ifx = nif[0], ify = nif[1], ifz = nif[2];
     cnext = ((int)bk.y + (k + 1) * nb) * FORCE_T + threadIdx.x;
     nvalid = k + 1 < rows && cnext < ncell;
     if (FM::fp32) {
@@ -591,12 +598,23 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
     }
     if (nvalid) {
       nfirst = locate(cnext, nX, nY, nZ, nn, nw3, nmx, nmy, nmz);
-      nown = a.owner[nn];
-      nkey = a.fkey[nn];
+      fetch();
     }
     const bool in_box = X >= P.lo[0] && X < P.hi[0] && Y >= P.lo[1] && Y < P.hi[1] &&
                         Z >= P.lo[2] && Z < P.hi[2];
-    if (own == FLUID && in_box) {
+    bool near = own == FLUID && in_box;
+    if (near && gate) {
+      if (FM::fp32) {
+        const float ex = __fsub_rn((float)(X - P.ipos[0]), P.fpos[0]);
+        const float ey = __fsub_rn((float)(Y - P.ipos[1]), P.fpos[1]);
+        const float ez = __fsub_rn((float)(Z - P.ipos[2]), P.fpos[2]);
+        near = ex * ex + ey * ey + ez * ez < rlink2f;
+      } else {
+        const double ex = (double)X - P.pos[0], ey = (double)Y - P.pos[1], ez = (double)Z - P.pos[2];
+        near = ex * ex + ey * ey + ez * ez < rlink * rlink;
+      }
+    }
+    if (near) {
       // momentum exchange on every link from this fluid node into the particle
       // (Eq. 11): the links first (all 18 owner loads in flight together), the
       // FP64 arithmetic only at nodes next to the surface
@@ -684,9 +702,7 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
     if (mine && own == FLUID) {
       touched[1] = true;
       if (FM::fp32) {
-        const float ix = ((const float*)a.ifield)[n];
-        const float iy = ((const float*)a.ifield)[N + n];
-        const float iz = ((const float*)a.ifield)[2 * N + n];
+        const float ix = ifx, iy = ify, iz = ifz;
         // minimum-image offset of the wrapped node from the centre
         const float hx = 0.5f * (float)g.nx, hy = 0.5f * (float)g.ny, hz = 0.5f * (float)g.nz;
         float ox = (float)(w3[0] - cxi) - frx, oy = (float)(w3[1] - cyi) - fry, oz = (float)(w3[2] - czi) - frz;
@@ -1156,49 +1172,92 @@ __device__ __forceinline__ bool psi_test(const PsiCell& c, float gu, float gvw2,
   return psi_exact(&c, mu, mu1, j, l, far);
 }
 
+// count of the planes t >= 0 (offset e0 + t/16 from the near end, at most
+// tmax) with (e0 + t/16)^2 + S < R^2: ceil(v), v = 16 (sqrt(R^2 - S) - e0),
+// decided (sure) when v lies farther than its error bound from an integer;
+// a column beyond R^2 by more than twice the margin has none (every float
+// test of its planes exceeds R^2 plus the margin: its sum is at least S);
+// within twice the margin of R^2 it is left to the plane tests
+__device__ __forceinline__ int psi_count(float S, float R2f, float margin, float e0, int tmax, bool& sure) {
+  const float A = R2f - S;
+  const float ra = rsqrtf(A);
+  const float sa = A * ra;  // the root within a few ulp
+  const float v = (sa - e0) * 16.0f;
+  // |A - exact| < margin: the root off by < margin / sqrt(A) (ra within 1%);
+  // the approximate root, e0 and v off by less than 2^-21 (sqrt(A) + e0 + 1)
+  // together
+  const float err = 32.0f * (1.01f * margin * ra + 4.8e-7f * (sa + e0 + 1.0f));
+  const bool out = A < -2.0f * margin;
+  sure = out || (A > 2.0f * margin && fabsf(v - rintf(v)) > err);
+  return out ? 0 : min(max((int)ceilf(v), 0), tmax);
+}
+
+// the same count where psi_count is not sure: from the estimate, the planes
+// at the boundary are tested (float, with the FP64 test of the octree within
+// the margin of R^2) until the first plane outside
+__device__ __noinline__ int psi_settle(const PsiCell* c, float S, float e0, int tmax, int near, int step,
+                                       float bu, float fu, int j, int l, bool far) {
+  const float A = c->R2f - S;
+  int T;
+  if (A <= 2.0f * c->margin) {
+    T = A > 0.0f ? min(max((int)ceilf((sqrtf(A) - e0) * 16.0f), 0), tmax) : 0;
+  } else {
+    const float ra = rsqrtf(A);
+    T = min(max((int)ceilf((A * ra - e0) * 16.0f), 0), tmax);
+  }
+  auto off = [](float b, float f, int m) { return __fsub_rn(b + (0.0625f * (float)m - 0.5f), f); };
+  auto pin = [&](int t) {
+    const int m = near + step * t;
+    return psi_test(*c, fabsf(off(bu, fu, m)), S, m, -1, j, l, far);
+  };
+  while (T > 0 && !pin(T - 1)) --T;
+  while (T < tmax && pin(T)) ++T;
+  return T;
+}
+
 template <class FM>
 __device__ __forceinline__ void psi_surface_body(const PartArgs& a, const Blk bk) {
+  // per warp: the squared far and near offsets of the 16 slabs along w
+  __shared__ float wslab[PSI_CTA / 32][2][16];
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
   const int warp = (bk.x * PSI_CTA + threadIdx.x) >> 5;
   const int nwarps = (bk.nx * PSI_CTA) >> 5;
   const int count = min(*a.surf_count, a.surf_cap);
   for (int e = warp; e < count; e += nwarps) {
     const int2 pc = a.surf[e];
     const DevParticle& P = a.parts[pc.x];
-    PsiCell c;
-    c.P = &P;
-    box_coord(pc.y, P.lo, P.hi, c.X[0], c.X[1], c.X[2]);
-    for (int d = 0; d < 3; ++d) c.fb[d] = (float)(c.X[d] - P.ipos[d]);
-    c.R2f = P.r2f;
-    c.margin = P.psimargin;
-    c.R2 = __dmul_rn(P.radius, P.radius);
+    int X[3];
+    box_coord(pc.y, P.lo, P.hi, X[0], X[1], X[2]);
+    float fb[3];
+    for (int d = 0; d < 3; ++d) fb[d] = (float)(X[d] - P.ipos[d]);
+    const float R2f = P.r2f, margin = P.psimargin;
     // the column axis: the largest distance of the cell centre from the centre
     float best = -1.0f;
-    c.u = 0;
+    int u = 0;
     for (int d = 0; d < 3; ++d) {
-      const float o = fabsf(__fsub_rn(c.fb[d], P.fpos[d]));
+      const float o = fabsf(__fsub_rn(fb[d], P.fpos[d]));
       if (o > best) {
         best = o;
-        c.u = d;
+        u = d;
       }
     }
-    c.v = c.u == 0 ? 1 : 0;
-    c.w = c.u == 2 ? 1 : 2;
+    const int v = u == 0 ? 1 : 0;
+    const int w = u == 2 ? 1 : 2;
     // near end of the columns: the plane nearest the centre, when the centre
     // lies beyond the cell along u (exact comparisons in FP64)
-    const double lo_u = (double)c.X[c.u] - 0.5, hi_u = (double)c.X[c.u] + 0.5;
-    const int near = P.pos[c.u] <= lo_u ? 0 : (P.pos[c.u] >= hi_u ? 16 : -1);
+    const double lo_u = (double)X[u] - 0.5, hi_u = (double)X[u] + 0.5;
+    const int near = P.pos[u] <= lo_u ? 0 : (P.pos[u] >= hi_u ? 16 : -1);
     const int step = near == 0 ? 1 : -1;
     // per-axis constants of the float offsets (registers, not indexed)
-    const float bu = c.fb[c.u], bv = c.fb[c.v], bw = c.fb[c.w];
-    const float fu = P.fpos[c.u], fv_ = P.fpos[c.v], fw_ = P.fpos[c.w];
+    const float bu = fb[u], bv = fb[v], bw = fb[w];
+    const float fu = P.fpos[u], fv_ = P.fpos[v], fw_ = P.fpos[w];
     auto off = [](float b, float f, int m) { return __fsub_rn(b + (0.0625f * (float)m - 0.5f), f); };
     // the squared far and near offsets across the columns are separable: a
     // lane's columns share one v slab (j = lane mod 16) and take their w slabs
-    // (l) from the lane that holds slab l
-    int units = 0;
+    // (l) from the warp's table
     const int jl = lane & 15;
-    float FV2, NV2, FW2, NW2;
+    float FV2, NV2;
     {
       const float v0 = off(bv, fv_, jl), v1 = off(bv, fv_, jl + 1);
       const float w0 = off(bw, fw_, jl), w1 = off(bw, fw_, jl + 1);
@@ -1206,60 +1265,70 @@ __device__ __forceinline__ void psi_surface_body(const PartArgs& a, const Blk bk
       const float fw = slab_f(w0, w1, true), nw = slab_f(w0, w1, false);
       FV2 = fv * fv;
       NV2 = nv * nv;
-      FW2 = fw * fw;
-      NW2 = nw * nw;
+      if (lane < 16) {
+        wslab[wib][0][jl] = fw * fw;
+        wslab[wib][1][jl] = nw * nw;
+      }
     }
+    __syncwarp();
+    // the cell in the form the plane tests take (built where they run)
+    auto cell = [&]() {
+      PsiCell c;
+      c.P = &P;
+      for (int d = 0; d < 3; ++d) {
+        c.X[d] = X[d];
+        c.fb[d] = fb[d];
+      }
+      c.R2f = R2f;
+      c.margin = margin;
+      c.R2 = __dmul_rn(P.radius, P.radius);
+      c.u = u;
+      c.v = v;
+      c.w = w;
+      return c;
+    };
+    int units = 0;
     const float e0 = near >= 0 ? fabsf(off(bu, fu, near)) : 0.0f;
-#pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
-      const int j = jl, l = (lane >> 4) + 2 * q;
-      const float far2 = FV2 + __shfl_sync(0xffffffffu, FW2, l);
-      const float near2 = NV2 + __shfl_sync(0xffffffffu, NW2, l);
-      if (near >= 0) {
-        // the count of planes t (offset e0 + t/16 from the near end) with
-        // (e0 + t/16)^2 + S < R^2 is ceil(v), v = 16 (sqrt(R^2 - S) - e0),
-        // unless v lies within its error bound of an integer (or R^2 - S is
-        // within the margin of 0): then the planes at the boundary are tested
-        auto estimate = [&](float S, int tmax, bool& sure) {
-          const float A = c.R2f - S;
-          if (A <= 2.0f * c.margin) {
-            sure = false;
-            return A > 0.0f ? min(max((int)ceilf((sqrtf(A) - e0) * 16.0f), 0), tmax) : 0;
+    if (near >= 0) {
+      // T: planes t = 0..16 from the near end whose far corner is inside
+      // (T - 1 inside cubes); TN: cubes t = 0..15 whose near face is nearer
+      // than R.  Counts the float estimate cannot decide are marked and
+      // settled after the loop.
+      unsigned unsure = 0u;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int l = (lane >> 4) + 2 * q;
+        const float far2 = FV2 + wslab[wib][0][l];
+        const float near2 = NV2 + wslab[wib][1][l];
+        bool s1, s2;
+        const int T = psi_count(far2, R2f, margin, e0, 17, s1);
+        const int TN = psi_count(near2, R2f, margin, e0, 16, s2);
+        units += (s1 ? max(T - 1, 0) : 0) + (s2 ? TN : 0);
+        unsure |= (s1 ? 0u : 1u << (2 * q)) | (s2 ? 0u : 2u << (2 * q));
+      }
+      if (unsure) {
+        const PsiCell c = cell();
+        do {
+          const int b = __ffs(unsure) - 1;
+          unsure &= unsure - 1u;
+          const int q = b >> 1, l = (lane >> 4) + 2 * q;
+          if (b & 1) {
+            const float near2 = NV2 + wslab[wib][1][l];
+            units += psi_settle(&c, near2, e0, 16, near, step, bu, fu, jl, l, false);
+          } else {
+            const float far2 = FV2 + wslab[wib][0][l];
+            units += max(psi_settle(&c, far2, e0, 17, near, step, bu, fu, jl, l, true) - 1, 0);
           }
-          const float ra = rsqrtf(A);
-          const float sa = A * ra;  // the root within a few ulp
-          const float v = (sa - e0) * 16.0f;
-          // |A - exact| < margin: the root off by < margin / sqrt(A) (ra within
-          // 1%); the approximate root, e0 and v off by less than
-          // 2^-21 (sqrt(A) + e0 + 1) together
-          const float err = 32.0f * (1.01f * c.margin * ra + 4.8e-7f * (sa + e0 + 1.0f));
-          sure = fabsf(v - rintf(v)) > err;
-          return min(max((int)ceilf(v), 0), tmax);
-        };
-        bool sure;
-        // planes t = 0..16 from the near end whose far corner is inside
-        int T = estimate(far2, 17, sure);
-        if (!sure) {
-          auto pin = [&](int t) {
-            const int m = near + step * t;
-            return psi_test(c, fabsf(off(bu, fu, m)), far2, m, -1, j, l, true);
-          };
-          while (T > 0 && !pin(T - 1)) --T;
-          while (T < 17 && pin(T)) ++T;
-        }
-        // cubes t = 0..15 whose near face (plane t) is nearer than R
-        int TN = estimate(near2, 16, sure);
-        if (!sure) {
-          auto pnear = [&](int t) {
-            const int m = near + step * t;
-            return psi_test(c, fabsf(off(bu, fu, m)), near2, m, -1, j, l, false);
-          };
-          while (TN > 0 && !pnear(TN - 1)) --TN;
-          while (TN < 16 && pnear(TN)) ++TN;
-        }
-        units += max(T - 1, 0) + TN;
-      } else {
-        // the centre within the cell's extent along u: every cube
+        } while (unsure);
+      }
+    } else {
+      // the centre within the cell's extent along u: every cube
+      const PsiCell c = cell();
+#pragma unroll 1
+      for (int q = 0; q < 8; ++q) {
+        const int j = jl, l = (lane >> 4) + 2 * q;
+        const float far2 = FV2 + wslab[wib][0][l];
+        const float near2 = NV2 + wslab[wib][1][l];
         bool prev = psi_test(c, fabsf(off(bu, fu, 0)), far2, 0, -1, j, l, true);
         for (int k = 0; k < 16; ++k) {
           const float a0 = off(bu, fu, k), a1 = off(bu, fu, k + 1);
@@ -1275,13 +1344,14 @@ __device__ __forceinline__ void psi_surface_body(const PartArgs& a, const Blk bk
     if (lane == 0 && units > 0) {
       // dyadic with 13 fraction bits: every sum below is exact, in any order
       const double ps = (double)units / (double)PSI_UNITS;
-      const long long n = node_of(c.X[0], c.X[1], c.X[2], a.g);
+      const long long n = node_of(X[0], X[1], X[2], a.g);
       a.psibox[(long long)pc.x * a.boxmax + pc.y] = ps;
       real_add<FM>(a.psi, n, ps);
       // integer counts, spread over eight addresses (the total of one
       // particle would otherwise serialise the atomics of all its cells)
       atomicAdd(&a.parts[pc.x].psiunits[pc.y & 7], (unsigned long long)units);
     }
+    __syncwarp();  // the table is rewritten for the warp's next cell
   }
 }
 
