@@ -162,12 +162,11 @@ __device__ __forceinline__ int classify_f2(float ax, float ay, float az, float h
 // into 8 sub-cells, each classified as completely inside or completely
 // outside; undecided ones are split again, down to depth 4 (edge 1/16), where
 // an undecided cube counts half.  Level 0 (the cell itself) is decided by
-// k_claim; cells still undecided there go to k_psi_surface, where eight warps
-// share a cell, one per level-1 octant: a warp walks its octant's levels
-// breadth first, the sub-cubes of a level spread over the lanes and the
-// undecided ones compacted (ballot) into the next level's list.  Volumes are
-// counted in units of 1/8192 (half a level-4 cube), so the sums are exact in
-// any order.
+// k_claim; cells still undecided there go to k_psi_surface, which counts the
+// cell's level-4 cubes that are inside or undecided, column by column (one
+// warp per cell; a cube's status follows from its ancestors', so the counts
+// give the tree's result exactly).  Volumes are counted in units of 1/8192
+// (half a level-4 cube), so the sums are exact in any order.
 constexpr int PSI_UNITS = 8192;
 
 // sum of Psi_p over the particle's box (counts of 2^-13 units: exact)
