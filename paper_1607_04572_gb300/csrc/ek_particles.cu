@@ -177,6 +177,20 @@ __device__ __forceinline__ double psi_sum(const DevParticle& P) {
   return (double)u / (double)PSI_UNITS;
 }
 
+// u * 2^-13 (1 <= u < 2^20) as a double, assembled from its bits: exact,
+// and no FP64 instruction (the GPU's FP64 pipe is narrow and this runs once
+// per surface cell)
+__device__ __forceinline__ double dyadic13(unsigned u) {
+  const int e = 31 - __clz(u);  // u in [2^e, 2^(e+1))
+  const unsigned long long mant = ((unsigned long long)u << (52 - e)) & ((1ULL << 52) - 1ULL);
+  return __longlong_as_double((long long)(((unsigned long long)(1023 + e - 13) << 52) | mant));
+}
+// a Psi_p entry of the box (0 or u * 2^-13, u <= 8192: a normal float with at
+// most 14 significant bits) as a float, from its bits: exact
+__device__ __forceinline__ float psibox_float(unsigned long long bits) {
+  return bits ? __int_as_float((int)((bits >> 29) - (896ULL << 23))) : 0.0f;
+}
+
 // exact (double) centre of sub-cube `path` at level l of the cell centred
 // at (X, Y, Z); path holds 3 bits per level, level 1 highest
 __device__ __forceinline__ void subcube_centre_d(int path, int l, double X, double Y, double Z,
@@ -479,19 +493,39 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
   const int nb = (ncell + a.fcells - 1) / a.fcells;
   if ((int)bk.y >= nb) return;  // whole CTA beyond this particle's widened box
   const bool pv = a.ph.pv != 0;
+  // the charge per unit weight (FP64 form: every thread; FP32 form: one
+  // thread of the block, in float to the others, as the GPU's FP64 pipe is
+  // narrow)
+  auto charge_norm = [&]() {
+    if (pv)
+      return (a.ph.flags & EK_CHARGE_NORM_VP)
+                 ? P.charge / (4.0 / 3.0 * M_PI * P.radius * P.radius * P.radius)
+                 : (psi_sum(P) > 0.0 ? P.charge / psi_sum(P) : 0.0);
+    return P.nb > 0 ? P.charge / (double)P.nb : 0.0;
+  };
   double qnorm = 0.0;
-  if (pv) {
-    qnorm = (a.ph.flags & EK_CHARGE_NORM_VP)
-                ? P.charge / (4.0 / 3.0 * M_PI * P.radius * P.radius * P.radius)
-                : (psi_sum(P) > 0.0 ? P.charge / psi_sum(P) : 0.0);
+  float qnormf = 0.0f;
+  bool qnz = false;  // qnorm != 0
+  if (FM::fp32) {
+    __shared__ float s_qn;
+    __shared__ int s_qnz;
+    if (threadIdx.x == 0) {
+      const double q = charge_norm();
+      s_qn = (float)q;
+      s_qnz = q != 0.0;
+    }
+    __syncthreads();
+    qnormf = s_qn;
+    qnz = s_qnz != 0;
   } else {
-    qnorm = P.nb > 0 ? P.charge / (double)P.nb : 0.0;
+    qnorm = charge_norm();
   }
   const double rho0 = a.ph.rho0;
-  const float qnormf = (float)qnorm;
-  // the particle's velocities and rho0 in float, once (FP32 form)
-  const float vxf = (float)P.vel[0], vyf = (float)P.vel[1], vzf = (float)P.vel[2];
-  const float qxf = (float)P.omega[0], qyf = (float)P.omega[1], qzf = (float)P.omega[2];
+  // the particle's velocities, rho0 and centre in float (FP32 form; the
+  // particle record keeps float copies of the velocities and the centre's
+  // integer part and fraction)
+  const float vxf = P.velf[0], vyf = P.velf[1], vzf = P.velf[2];
+  const float qxf = P.omegaf[0], qyf = P.omegaf[1], qzf = P.omegaf[2];
   const float rho0f = (float)rho0;
   double acc[FPART];
 #pragma unroll
@@ -502,8 +536,8 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
   float racc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   // FP32 form: momentum exchange [0..5] and own charge [6..9] in float
   float macc[10] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-  const int cxi = (int)floor(P.pos[0]), cyi = (int)floor(P.pos[1]), czi = (int)floor(P.pos[2]);
-  const float frx = (float)(P.pos[0] - cxi), fry = (float)(P.pos[1] - cyi), frz = (float)(P.pos[2] - czi);
+  const int cxi = P.ipos[0], cyi = P.ipos[1], czi = P.ipos[2];  // floor(pos)
+  const float frx = P.fpos[0], fry = P.fpos[1], frz = P.fpos[2];  // pos - floor(pos), rounded
   bool touched[4] = {false, false, false, false};
   const int rows = a.fcells / FORCE_T;
   // FP32 form: a thread's cells are rows of FORCE_T apart in the widened
@@ -567,9 +601,19 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
   // box offsets X - r_p it measures are the minimum-image ones for every
   // linked node once each edge is at least 2 R + 4 (a box cell lies within
   // R + 2 of the centre along each axis); smaller lattices test every cell.
-  const bool gate = 2.0 * P.radius + 4.0 <= (double)min(g.nx, min(g.ny, g.nz));
-  const double rlink = P.radius + 1.5;
-  const float rlink2f = (float)(rlink * rlink);
+  const int nmin = min(g.nx, min(g.ny, g.nz));
+  bool gate;
+  double rlink = 0.0;
+  float rlink2f = 0.0f;
+  if (FM::fp32) {
+    // float suffices: the bounds leave margins of 0.5 and 0.086 lattice units
+    const float Rf = sqrtf(P.r2f);
+    gate = 2.0f * Rf + 4.0f <= (float)nmin;
+    rlink2f = (Rf + 1.5f) * (Rf + 1.5f);
+  } else {
+    gate = 2.0 * P.radius + 4.0 <= (double)nmin;
+    rlink = P.radius + 1.5;
+  }
   for (int k = 0; k < rows; ++k) {
     if (!nvalid) break;
     const int X = nX, Y = nY, Z = nZ;
@@ -730,18 +774,25 @@ __device__ __forceinline__ void particle_forces_body(const PartArgs& a, const Bl
     if (in_box) {
       double qq = 0.0;
       float psf = 0.0f;
+      bool has_q = false;
       if (pv) {
         const int bx = P.hi[0] - P.lo[0], by = P.hi[1] - P.lo[1];
         const int cb = (X - P.lo[0]) + bx * ((Y - P.lo[1]) + by * (Z - P.lo[2]));
         const double ps = a.psibox[(long long)p * a.boxmax + cb];
-        if (FM::fp32) qq = ps != 0.0 ? 1.0 : 0.0;  // the weight itself is applied in float below
-        else qq = qnorm * ps;
-        if (FM::fp32 && ps != 0.0) psf = (float)ps;
+        if (FM::fp32) {
+          // the weight itself is applied in float below
+          psf = psibox_float((unsigned long long)__double_as_longlong(ps));
+          has_q = psf != 0.0f;
+        } else {
+          qq = qnorm * ps;
+          has_q = qq != 0.0;
+        }
       } else if (own == p) {
         qq = qnorm;
         psf = 1.0f;
+        has_q = FM::fp32 ? qnz : qq != 0.0;
       }
-      if (qq != 0.0) {
+      if (has_q) {
         touched[2] = true;
         if (FM::fp32) {
           const float qf = qnormf * psf;
@@ -1244,9 +1295,16 @@ __device__ __forceinline__ void psi_surface_body(const PartArgs& a, const Blk bk
     const int v = u == 0 ? 1 : 0;
     const int w = u == 2 ? 1 : 2;
     // near end of the columns: the plane nearest the centre, when the centre
-    // lies beyond the cell along u (exact comparisons in FP64)
-    const double lo_u = (double)X[u] - 0.5, hi_u = (double)X[u] + 0.5;
-    const int near = P.pos[u] <= lo_u ? 0 : (P.pos[u] >= hi_u ? 16 : -1);
+    // lies beyond the cell along u.  Exact without FP64: the centre is
+    // ipos + frac with frac = fpos + fposlo (the residual's sign exact), so
+    // pos <= X - 1/2 iff m = X - ipos >= 2, or m = 1 and frac <= 1/2, and
+    // pos >= X + 1/2 iff m <= -1, or m = 0 and frac >= 1/2
+    const int mu_ = X[u] - P.ipos[u];
+    const float fh = P.fpos[u], fl = P.fposlo[u];
+    const bool le_half = fh < 0.5f || (fh == 0.5f && fl <= 0.0f);
+    const bool ge_half = fh > 0.5f || (fh == 0.5f && fl >= 0.0f);
+    const int near = (mu_ >= 2 || (mu_ == 1 && le_half)) ? 0
+                     : ((mu_ <= -1 || (mu_ == 0 && ge_half)) ? 16 : -1);
     const int step = near == 0 ? 1 : -1;
     // per-axis constants of the float offsets (registers, not indexed)
     const float bu = fb[u], bv = fb[v], bw = fb[w];
@@ -1342,10 +1400,10 @@ __device__ __forceinline__ void psi_surface_body(const PartArgs& a, const Blk bk
     for (int o = 16; o > 0; o >>= 1) units += __shfl_xor_sync(0xffffffffu, units, o);
     if (lane == 0 && units > 0) {
       // dyadic with 13 fraction bits: every sum below is exact, in any order
-      const double ps = (double)units / (double)PSI_UNITS;
       const long long n = node_of(X[0], X[1], X[2], a.g);
-      a.psibox[(long long)pc.x * a.boxmax + pc.y] = ps;
-      real_add<FM>(a.psi, n, ps);
+      a.psibox[(long long)pc.x * a.boxmax + pc.y] = dyadic13((unsigned)units);
+      if (FM::fp32) atomicAdd((float*)a.psi + n, (float)units * (1.0f / (float)PSI_UNITS));
+      else atomicAdd((double*)a.psi + n, dyadic13((unsigned)units));
       // integer counts, spread over eight addresses (the total of one
       // particle would otherwise serialise the atomics of all its cells)
       atomicAdd(&a.parts[pc.x].psiunits[pc.y & 7], (unsigned long long)units);
